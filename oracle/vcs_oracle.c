@@ -1,0 +1,1161 @@
+/*
+ * CPU oracle for the VCS hot path: TEST INFRASTRUCTURE ONLY (see the header).
+ *
+ * Machine readings where the paper is silent (each one is a constant of this
+ * oracle; the names A1..A12 are the design notes' labels):
+ *  A1 a frame ends (and the next begins, scanline 0) at a VSYNC write that
+ *     sets D1 while D1 was clear;
+ *  A2 a frame is also ended at an instruction boundary once 512 scanlines
+ *     have elapsed without VSYNC (the env's watchdog flag is raised);
+ *  A3 screen row r is scanline ystart + r; columns are line clocks 68..227;
+ *  A4 pixel = colour register & 0xFE; 0 while VBLANK D1 is set and for the
+ *     first 8 pixels of a line whose HMOVE strobe hit line clock <= 9;
+ *  A5 a write takes effect at colour clock 3 x (cycle count after the cycle
+ *     of the write is charged): clocks rendered before it see the old value;
+ *  A6 RESP0 -> position 3 during HBLANK, else (clock - 68 + 5) mod 160;
+ *     HMOVE subtracts the signed HMP0 high nibble; WSYNC halts the CPU until
+ *     the cycle count is a multiple of 76; playfield 20 bits x 4 clocks with
+ *     the right half repeated or reflected (CTRLPF bit 0); priority
+ *     P0 > PF > BK unless CTRLPF bit 2 (PF > P0 > BK);
+ *  A7 power-on: A=X=Y=0, SP=$FD, P=$34, PC from $1FFC/D, RAM and TIA zero,
+ *     the timer as if 0 had been written to T1024T at cycle 0, F8 in bank 1;
+ *  A8 timer: a write of V at cycle t_w makes INTIM = V - ceil(k / I) at
+ *     t_w + k until that would go negative; from k_u = V*I + 1 on it reads
+ *     (0xFF - (k - k_u)) & 0xFF and TIMINT bit 7 is set;
+ *  A9 only architectural accesses have side effects (dummy reads and the
+ *     RMW dummy write are idle cycles);
+ *  A10 undriven TIA read bits are 0; collision registers read 0;
+ *  A11 NMOS decimal mode per the published note on decimal mode;
+ *  A12 pushed P always has bits 4 and 5 set (PHP and BRK are the only
+ *     pushes of P on a 6507); BRK vectors through $1FFE.
+ *  Undocumented opcodes jam the CPU: from then on each instruction slot
+ *  idles to the next line start, so the frame ends by the 512-line cap.
+ */
+#include "vcs_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define LINE_CAP 512
+#define SCR_W 160
+#define SCR_H 210
+
+/* ------------------------------------------------------------------ */
+/* deviation graph                                                     */
+/* ------------------------------------------------------------------ */
+
+enum { NK_ZERO = 0, NK_LEAF, NK_LIN, NK_RROM, NK_RRAM };
+
+typedef struct {
+  uint8_t kind, n;
+  int16_t lo, a0;      /* read: first window cell, hard address (tensor index) */
+  int32_t base;        /* read_rom: ROM offset of the tensor */
+  int32_t in[4];
+  double c[4];
+  int64_t pool;        /* read_ram: offset of the window's cells in the pool */
+} onode;
+
+struct ogrf {
+  onode* nd;
+  double* seed;
+  int64_t n, cap;
+  int32_t* pnode;      /* read_ram window: node of each cell */
+  int64_t pn, pcap;
+  const uint8_t* rom;  /* the emulator's ROM copy (owned by ovcs) */
+  uint8_t* rom_copy;
+  int rom_size;
+  int32_t rom0, ram0, u0;
+  double ram0_val[128];
+  double* u_val;
+  int n_steps;
+  double tau, alpha;
+  int W;
+};
+
+/* ------------------------------------------------------------------ */
+/* machine                                                             */
+/* ------------------------------------------------------------------ */
+
+typedef struct { uint8_t v; int32_t n; } val;
+
+struct ovcs {
+  /* CPU */
+  uint8_t A, X, Y, SP, P;
+  uint16_t pc;
+  uint64_t cyc;
+  int jammed;
+  /* memory */
+  uint8_t ram[128];
+  uint8_t* rom;
+  uint32_t rom_size;
+  int mapper, bank;
+  /* RIOT */
+  uint8_t intim;
+  uint32_t interval, phase;
+  int underflow;
+  uint8_t swcha, swchb, inpt4;
+  /* TIA */
+  uint8_t vsync, vblank, colup0, colupf, colubk, ctrlpf, pf0, pf1, pf2, grp0, hmp0;
+  int p0pos;
+  int hclk, line;
+  int hmove_line;
+  int wsync;
+  int ystart;
+  uint8_t fb[SCR_H * SCR_W];
+  uint8_t last_fb[SCR_H * SCR_W];
+  int frames_in_step;
+  ovcs_counters cnt;
+  /* soft mode */
+  ogrf* g;
+  int32_t nA, nX, nY, nV, nC[3], nRAM[128];
+  int32_t u_leaf;
+  const double* gs_all;   /* grad_screen for all steps (or NULL) */
+  const double* gs;       /* grad_screen of the frame being rendered */
+  int soft_step, frame_skip;
+};
+
+/* ---------------- graph helpers ---------------- */
+
+static int32_t g_new(ovcs* s, int kind) {
+  ogrf* g = s->g;
+  if (g->n == g->cap) {
+    g->cap = g->cap ? g->cap * 2 : 4096;
+    g->nd = (onode*)realloc(g->nd, (size_t)g->cap * sizeof(onode));
+    g->seed = (double*)realloc(g->seed, (size_t)g->cap * sizeof(double));
+  }
+  int32_t id = (int32_t)g->n++;
+  memset(&g->nd[id], 0, sizeof(onode));
+  g->nd[id].kind = (uint8_t)kind;
+  g->seed[id] = 0.0;
+  return id;
+}
+
+/* Linear combination of up to four deviations; zero terms are dropped and a
+ * single unit-coefficient term returns its input node unchanged. */
+static int32_t g_lin(ovcs* s, int k, const int32_t* in, const double* c) {
+  if (!s->g) return 0;
+  int32_t ii[4];
+  double cc[4];
+  int m = 0;
+  for (int j = 0; j < k; j++)
+    if (in[j] != 0 && c[j] != 0.0) { ii[m] = in[j]; cc[m] = c[j]; m++; }
+  if (m == 0) return 0;
+  if (m == 1 && cc[0] == 1.0) return ii[0];
+  int32_t id = g_new(s, NK_LIN);
+  onode* nd = &s->g->nd[id];
+  nd->n = (uint8_t)m;
+  for (int j = 0; j < m; j++) { nd->in[j] = ii[j]; nd->c[j] = cc[j]; }
+  return id;
+}
+static int32_t lin1(ovcs* s, int32_t a, double ca) {
+  int32_t in[1] = {a}; double c[1] = {ca}; return g_lin(s, 1, in, c);
+}
+static int32_t lin2(ovcs* s, int32_t a, double ca, int32_t b, double cb) {
+  int32_t in[2] = {a, b}; double c[2] = {ca, cb}; return g_lin(s, 2, in, c);
+}
+static void window(int W, int M, int a0, int* lo, int* hi) {
+  *lo = a0 - W < 0 ? 0 : a0 - W;
+  *hi = a0 + W > M - 1 ? M - 1 : a0 + W;
+}
+
+static int32_t g_read_rom(ovcs* s, int base, int M, int a0) {
+  if (!s->g) return 0;
+  int lo, hi;
+  window(s->g->W, M, a0, &lo, &hi);
+  int32_t id = g_new(s, NK_RROM);
+  onode* nd = &s->g->nd[id];
+  nd->lo = (int16_t)lo; nd->n = (uint8_t)(hi - lo + 1); nd->a0 = (int16_t)a0;
+  nd->base = base;
+  return id;
+}
+
+static int32_t g_read_ram(ovcs* s, int a0) {
+  if (!s->g) return 0;
+  ogrf* g = s->g;
+  int lo, hi;
+  window(g->W, 128, a0, &lo, &hi);
+  int n = hi - lo + 1;
+  if (g->pn + n > g->pcap) {
+    g->pcap = g->pcap ? g->pcap * 2 : 65536;
+    g->pnode = (int32_t*)realloc(g->pnode, (size_t)g->pcap * sizeof(int32_t));
+  }
+  int32_t id = g_new(s, NK_RRAM);
+  onode* nd = &g->nd[id];
+  nd->lo = (int16_t)lo; nd->n = (uint8_t)n; nd->a0 = (int16_t)a0;
+  nd->pool = g->pn;
+  for (int i = 0; i < n; i++) g->pnode[g->pn + i] = s->nRAM[lo + i];
+  g->pn += n;
+  return id;
+}
+
+/* ---------------- TIA ---------------- */
+
+static void frame_end(ovcs* s);
+
+static int pf_bit(const ovcs* s, int x) {
+  int i = x < 80 ? x / 4 : (x - 80) / 4;
+  if (x >= 80 && (s->ctrlpf & 1)) i = 19 - i;
+  if (i < 4) return (s->pf0 >> (4 + i)) & 1;
+  if (i < 12) return (s->pf1 >> (7 - (i - 4))) & 1;
+  return (s->pf2 >> (i - 12)) & 1;
+}
+
+static int p0_bit(const ovcs* s, int x) {
+  int d = ((x - s->p0pos) % 160 + 160) % 160;
+  return d < 8 ? (s->grp0 >> (7 - d)) & 1 : 0;
+}
+
+/* Pixel at visible column x of the current scanline; *owner = 0 (P0),
+ * 1 (PF), 2 (BK) or -1 (blanked). */
+static uint8_t pixel(const ovcs* s, int x, int* owner) {
+  if (s->vblank & 2) { *owner = -1; return 0; }
+  if (s->hmove_line == s->line && x < 8) { *owner = -1; return 0; }
+  int pf = pf_bit(s, x), p0 = p0_bit(s, x);
+  int o;
+  if (s->ctrlpf & 4) o = pf ? 1 : (p0 ? 0 : 2);
+  else o = p0 ? 0 : (pf ? 1 : 2);
+  *owner = o;
+  uint8_t c = o == 0 ? s->colup0 : (o == 1 ? s->colupf : s->colubk);
+  return c & 0xFE;
+}
+
+static void tia_clock(ovcs* s) {
+  if (s->hclk >= 68) {
+    int x = s->hclk - 68, row = s->line - s->ystart;
+    if (row >= 0 && row < SCR_H) {
+      int owner;
+      s->fb[row * SCR_W + x] = pixel(s, x, &owner);
+      s->cnt.pixels++;
+      if (s->g && s->gs && owner >= 0) {
+        double w = s->gs[row * SCR_W + x];
+        if (s->nC[owner]) s->g->seed[s->nC[owner]] += w;
+      }
+    }
+  }
+  if (++s->hclk == 228) { s->hclk = 0; s->line++; }
+}
+
+static void tia_write(ovcs* s, int reg, val x) {
+  uint8_t v = x.v;
+  s->cnt.tia_writes++;
+  switch (reg) {
+    case 0x00:
+      if (!(s->vsync & 2) && (v & 2)) frame_end(s);
+      s->vsync = v;
+      break;
+    case 0x01: s->vblank = v; break;
+    case 0x02: s->wsync = 1; break;
+    case 0x06: s->colup0 = v; s->nC[0] = x.n; break;
+    case 0x08: s->colupf = v; s->nC[1] = x.n; break;
+    case 0x09: s->colubk = v; s->nC[2] = x.n; break;
+    case 0x0A: s->ctrlpf = v; break;
+    case 0x0D: s->pf0 = v; break;
+    case 0x0E: s->pf1 = v; break;
+    case 0x0F: s->pf2 = v; break;
+    case 0x10: s->p0pos = s->hclk < 68 ? 3 : (s->hclk - 68 + 5) % 160; break;
+    case 0x1B: s->grp0 = v; break;
+    case 0x20: s->hmp0 = v; break;
+    case 0x2A: {
+      int m = ((int8_t)s->hmp0) >> 4;
+      s->p0pos = ((s->p0pos - m) % 160 + 160) % 160;
+      if (s->hclk <= 9) s->hmove_line = s->line;
+      break;
+    }
+    case 0x2B: s->hmp0 = 0; break;
+    default: break;
+  }
+}
+
+/* ---------------- RIOT ---------------- */
+
+static void riot_tick(ovcs* s) {
+  if (s->underflow) {
+    s->intim--;
+  } else {
+    if (s->phase == 0) {
+      if (s->intim == 0) { s->intim = 0xFF; s->underflow = 1; }
+      else s->intim--;
+    }
+    s->phase = (s->phase + 1) % s->interval;
+  }
+}
+
+static void timer_write(ovcs* s, int sel, val x) {
+  static const uint32_t iv[4] = {1, 8, 64, 1024};
+  s->intim = x.v;
+  s->interval = iv[sel];
+  s->phase = 0;
+  s->underflow = 0;
+  s->nV = x.n;
+}
+
+/* ---------------- bus ---------------- */
+
+static void tick(ovcs* s) {
+  s->cyc++;
+  s->cnt.cycles++;
+  riot_tick(s);
+  tia_clock(s);
+  tia_clock(s);
+  tia_clock(s);
+}
+
+static void idle(ovcs* s) { tick(s); }
+
+static void hotspot(ovcs* s, uint16_t a) {
+  if (s->mapper == 2) {
+    if (a == 0x1FF8) s->bank = 0;
+    else if (a == 0x1FF9) s->bank = 1;
+  }
+}
+
+static void rom_map(const ovcs* s, uint16_t a, int* base, int* M, int* idx) {
+  if (s->mapper == 0) { *base = 0; *M = 2048; *idx = a & 0x7FF; }
+  else if (s->mapper == 1) { *base = 0; *M = 4096; *idx = a & 0xFFF; }
+  else { *base = s->bank * 4096; *M = 4096; *idx = a & 0xFFF; }
+}
+
+/* One bus read cycle. */
+static val rd(ovcs* s, uint16_t addr) {
+  tick(s);
+  uint16_t a = addr & 0x1FFF;
+  val r = {0, 0};
+  if (a & 0x1000) {
+    hotspot(s, a);
+    int base, M, idx;
+    rom_map(s, a, &base, &M, &idx);
+    r.v = s->rom[base + idx];
+    r.n = g_read_rom(s, base, M, idx);
+    s->cnt.rom_reads++;
+  } else if (!(a & 0x80)) {
+    switch (a & 0x0F) {
+      case 0x0C: r.v = s->inpt4; r.n = s->g ? lin1(s, s->u_leaf + 4, -128.0) : 0; break;
+      case 0x0D: r.v = 0x80; break;
+      default: r.v = 0; break;
+    }
+  } else if (!(a & 0x200)) {
+    r.v = s->ram[a & 0x7F];
+    r.n = g_read_ram(s, a & 0x7F);
+    s->cnt.ram_reads++;
+  } else if (!(a & 0x04)) {
+    switch (a & 3) {
+      case 0:
+        r.v = s->swcha;
+        if (s->g) {
+          int32_t in[4] = {s->u_leaf + 0, s->u_leaf + 1, s->u_leaf + 2, s->u_leaf + 3};
+          double c[4] = {-128.0, -64.0, -32.0, -16.0};
+          r.n = g_lin(s, 4, in, c);
+        }
+        break;
+      case 2: r.v = s->swchb; break;
+      default: r.v = 0; break;
+    }
+  } else if (a & 1) {
+    r.v = s->underflow ? 0x80 : 0x00;
+  } else {
+    r.v = s->intim;
+    r.n = s->underflow ? 0 : s->nV;
+  }
+  return r;
+}
+
+/* Side-effect-free read (opcode and debug); still a bus cycle when `cycle`. */
+static uint8_t peek_raw(ovcs* s, uint16_t addr) {
+  uint16_t a = addr & 0x1FFF;
+  if (a & 0x1000) {
+    int base, M, idx;
+    rom_map(s, a, &base, &M, &idx);
+    return s->rom[base + idx];
+  }
+  if (!(a & 0x80)) return (a & 0x0F) == 0x0C ? s->inpt4 : ((a & 0x0F) == 0x0D ? 0x80 : 0);
+  if (!(a & 0x200)) return s->ram[a & 0x7F];
+  if (!(a & 0x04)) return (a & 3) == 0 ? s->swcha : ((a & 3) == 2 ? s->swchb : 0);
+  return (a & 1) ? (s->underflow ? 0x80 : 0) : s->intim;
+}
+
+/* Opcode fetch: a full read cycle whose value is a switch (no deviation). */
+static uint8_t fetch_opcode(ovcs* s) {
+  tick(s);
+  uint16_t a = s->pc & 0x1FFF;
+  if (a & 0x1000) { hotspot(s, a); s->cnt.rom_reads++; }
+  uint8_t v = peek_raw(s, s->pc);
+  s->pc++;
+  return v;
+}
+
+static void wr(ovcs* s, uint16_t addr, val x) {
+  tick(s);
+  uint16_t a = addr & 0x1FFF;
+  if (a & 0x1000) { hotspot(s, a); return; }
+  if (!(a & 0x80)) {
+    tia_write(s, a & 0x3F, x);
+    if (s->wsync) {
+      s->wsync = 0;
+      while (s->cyc % 76 != 0) tick(s);
+    }
+    return;
+  }
+  if (!(a & 0x200)) {
+    s->ram[a & 0x7F] = x.v;
+    s->nRAM[a & 0x7F] = x.n;
+    s->cnt.ram_writes++;
+    return;
+  }
+  if ((a & 0x04) && (a & 0x10)) timer_write(s, a & 3, x);
+}
+
+/* ---------------- frames ---------------- */
+
+static void set_gs(ovcs* s) {
+  if (s->g && s->gs_all && s->frames_in_step == s->frame_skip - 1)
+    s->gs = s->gs_all + (size_t)s->soft_step * SCR_H * SCR_W;
+  else
+    s->gs = NULL;
+}
+
+static void frame_end(ovcs* s) {
+  memcpy(s->last_fb, s->fb, sizeof s->fb);
+  memset(s->fb, 0, sizeof s->fb);
+  s->line = 0;
+  s->hmove_line = -1;
+  s->frames_in_step++;
+  s->cnt.frames++;
+  set_gs(s);
+}
+
+/* ---------------- CPU ---------------- */
+
+#define FC 0x01
+#define FZ 0x02
+#define FI 0x04
+#define FD 0x08
+#define FV 0x40
+#define FN 0x80
+
+static void set_nz(ovcs* s, uint8_t v) {
+  s->P = (uint8_t)((s->P & ~(FN | FZ)) | (v & 0x80) | (v ? 0 : FZ));
+}
+
+static val fetch_operand(ovcs* s) {
+  val r = rd(s, s->pc);
+  s->pc++;
+  return r;
+}
+
+/* Effective address of the memory operand.  Addresses are indices and so
+ * stored switches in soft mode: they carry no deviation. */
+enum { M_IMP, M_ACC, M_IMM, M_ZP, M_ZPX, M_ZPY, M_ABS, M_ABX, M_ABY, M_INX, M_INY };
+enum { K_READ, K_WRITE, K_RMW };
+
+static uint16_t address(ovcs* s, int mode, int kind) {
+  uint16_t ea = 0;
+  switch (mode) {
+    case M_ZP:
+      ea = fetch_operand(s).v;
+      break;
+    case M_ZPX:
+    case M_ZPY: {
+      uint8_t o = fetch_operand(s).v;
+      idle(s);
+      ea = (uint8_t)(o + (mode == M_ZPX ? s->X : s->Y));
+      break;
+    }
+    case M_ABS: {
+      uint8_t lo = fetch_operand(s).v;
+      uint8_t hi = fetch_operand(s).v;
+      ea = (uint16_t)(lo | (hi << 8));
+      break;
+    }
+    case M_ABX:
+    case M_ABY: {
+      uint8_t lo = fetch_operand(s).v;
+      uint8_t hi = fetch_operand(s).v;
+      uint16_t base = (uint16_t)(lo | (hi << 8));
+      ea = (uint16_t)(base + (mode == M_ABX ? s->X : s->Y));
+      if (kind != K_READ || ((base & 0xFF00) != (ea & 0xFF00))) idle(s);
+      break;
+    }
+    case M_INX: {
+      uint8_t o = fetch_operand(s).v;
+      idle(s);
+      uint8_t p = (uint8_t)(o + s->X);
+      uint8_t lo = rd(s, p).v;
+      uint8_t hi = rd(s, (uint8_t)(p + 1)).v;
+      ea = (uint16_t)(lo | (hi << 8));
+      break;
+    }
+    case M_INY: {
+      uint8_t o = fetch_operand(s).v;
+      uint8_t lo = rd(s, o).v;
+      uint8_t hi = rd(s, (uint8_t)(o + 1)).v;
+      uint16_t base = (uint16_t)(lo | (hi << 8));
+      ea = (uint16_t)(base + s->Y);
+      if (kind != K_READ || ((base & 0xFF00) != (ea & 0xFF00))) idle(s);
+      break;
+    }
+    default: break;
+  }
+  return ea;
+}
+
+/* Operand value for read instructions (immediate or memory). */
+static val operand(ovcs* s, int mode) {
+  if (mode == M_IMM) return fetch_operand(s);
+  return rd(s, address(s, mode, K_READ));
+}
+
+static void push(ovcs* s, val x) {
+  wr(s, (uint16_t)(0x100 | s->SP), x);
+  s->SP--;
+}
+static val pull(ovcs* s) {
+  s->SP++;
+  return rd(s, (uint16_t)(0x100 | s->SP));
+}
+
+static void op_adc(ovcs* s, uint8_t m) {
+  int c = s->P & FC;
+  if (s->P & FD) {
+    uint8_t bin = (uint8_t)(s->A + m + c);
+    int al = (s->A & 0x0F) + (m & 0x0F) + c;
+    if (al >= 0x0A) al = ((al + 0x06) & 0x0F) + 0x10;
+    int sum = (s->A & 0xF0) + (m & 0xF0) + al;
+    int ssum = (int)(int8_t)(s->A & 0xF0) + (int)(int8_t)(m & 0xF0) + al;
+    uint8_t p = (uint8_t)(s->P & ~(FN | FV | FZ | FC));
+    if (ssum & 0x80) p |= FN;
+    if (ssum < -128 || ssum > 127) p |= FV;
+    if (bin == 0) p |= FZ;
+    if (sum >= 0xA0) sum += 0x60;
+    if (sum >= 0x100) p |= FC;
+    s->A = (uint8_t)sum;
+    s->P = p;
+  } else {
+    int t = s->A + m + c;
+    uint8_t r = (uint8_t)t;
+    uint8_t p = (uint8_t)(s->P & ~(FN | FV | FZ | FC));
+    if (t > 0xFF) p |= FC;
+    if (~(s->A ^ m) & (s->A ^ r) & 0x80) p |= FV;
+    s->A = r;
+    s->P = p;
+    set_nz(s, r);
+  }
+}
+
+static void op_sbc(ovcs* s, uint8_t m) {
+  int c = s->P & FC;
+  /* flags are those of the binary subtraction in both modes */
+  int t = s->A + (m ^ 0xFF) + c;
+  uint8_t r = (uint8_t)t;
+  uint8_t p = (uint8_t)(s->P & ~(FN | FV | FZ | FC));
+  if (t > 0xFF) p |= FC;
+  if (~(s->A ^ (m ^ 0xFF)) & (s->A ^ r) & 0x80) p |= FV;
+  if (r & 0x80) p |= FN;
+  if (r == 0) p |= FZ;
+  if (s->P & FD) {
+    int al = (s->A & 0x0F) - (m & 0x0F) + c - 1;
+    if (al < 0) al = ((al - 0x06) & 0x0F) - 0x10;
+    int sum = (s->A & 0xF0) - (m & 0xF0) + al;
+    if (sum < 0) sum -= 0x60;
+    r = (uint8_t)sum;
+  }
+  s->A = r;
+  s->P = p;
+}
+
+static void op_cmp(ovcs* s, uint8_t reg, uint8_t m) {
+  uint8_t t = (uint8_t)(reg - m);
+  s->P = (uint8_t)((s->P & ~FC) | (reg >= m ? FC : 0));
+  set_nz(s, t);
+}
+
+/* shift/rotate: kind 0 ASL, 1 ROL, 2 LSR, 3 ROR */
+static uint8_t op_shift(ovcs* s, int kind, uint8_t v) {
+  int cin = s->P & FC;
+  int cout;
+  uint8_t r;
+  switch (kind) {
+    case 0: cout = v >> 7; r = (uint8_t)(v << 1); break;
+    case 1: cout = v >> 7; r = (uint8_t)((v << 1) | cin); break;
+    case 2: cout = v & 1; r = (uint8_t)(v >> 1); break;
+    default: cout = v & 1; r = (uint8_t)((v >> 1) | (cin << 7)); break;
+  }
+  s->P = (uint8_t)((s->P & ~FC) | (cout ? FC : 0));
+  set_nz(s, r);
+  return r;
+}
+
+/* Conditional branch.  In soft mode the STE gate of Eq. s-branch returns the
+ * hard counter; the counter is an index (a stored switch), so the gate's
+ * derivative has no consumer among the gradient outputs. */
+static void branch(ovcs* s, int cond) {
+  uint8_t off = fetch_operand(s).v;
+  if (cond) {
+    uint16_t t = (uint16_t)(s->pc + (int8_t)off);
+    idle(s);
+    if ((t & 0xFF00) != (s->pc & 0xFF00)) idle(s);
+    s->pc = t;
+  }
+}
+
+/* group tables for the regular ALU column (cc = 01) */
+static const int mode01[8] = {M_INX, M_ZP, M_IMM, M_ABS, M_INY, M_ZPX, M_ABY, M_ABX};
+
+static void exec(ovcs* s) {
+  uint8_t op = fetch_opcode(s);
+  s->cnt.instructions++;
+  int aaa = op >> 5, bbb = (op >> 2) & 7, cc = op & 3;
+
+  if (cc == 1) {                       /* ORA AND EOR ADC STA LDA CMP SBC */
+    int mode = mode01[bbb];
+    if (aaa == 4) {                    /* STA */
+      if (mode == M_IMM) goto jam;
+      val x = {s->A, s->nA};
+      wr(s, address(s, mode, K_WRITE), x);
+      return;
+    }
+    val m = operand(s, mode);
+    switch (aaa) {
+      case 0: s->A |= m.v; s->nA = lin2(s, s->nA, 1.0, m.n, 1.0); set_nz(s, s->A); break;
+      case 1: s->A &= m.v; s->nA = lin2(s, s->nA, 1.0, m.n, 1.0); set_nz(s, s->A); break;
+      case 2: s->A ^= m.v; s->nA = lin2(s, s->nA, 1.0, m.n, 1.0); set_nz(s, s->A); break;
+      case 3: op_adc(s, m.v); s->nA = lin2(s, s->nA, 1.0, m.n, 1.0); break;
+      case 5: s->A = m.v; s->nA = m.n; set_nz(s, s->A); break;
+      case 6: op_cmp(s, s->A, m.v); break;
+      case 7: op_sbc(s, m.v); s->nA = lin2(s, s->nA, 1.0, m.n, -1.0); break;
+    }
+    return;
+  }
+
+  switch (op) {
+    /* ---- shifts / rotates / inc / dec on memory and A ---- */
+    case 0x0A: case 0x2A: case 0x4A: case 0x6A: {
+      idle(s);
+      s->A = op_shift(s, aaa, s->A);   /* straight-through: unit derivative */
+      return;
+    }
+    case 0x06: case 0x16: case 0x0E: case 0x1E:
+    case 0x26: case 0x36: case 0x2E: case 0x3E:
+    case 0x46: case 0x56: case 0x4E: case 0x5E:
+    case 0x66: case 0x76: case 0x6E: case 0x7E:
+    case 0xC6: case 0xD6: case 0xCE: case 0xDE:
+    case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
+      int mode = bbb == 1 ? M_ZP : bbb == 3 ? M_ABS : bbb == 5 ? M_ZPX : M_ABX;
+      uint16_t ea = address(s, mode, K_RMW);
+      val m = rd(s, ea);
+      idle(s);                         /* RMW dummy write (not modelled) */
+      val r;
+      if (aaa <= 3) {
+        r.v = op_shift(s, aaa, m.v);   /* straight-through: unit derivative */
+        r.n = m.n;
+      } else {
+        r.v = (uint8_t)(aaa == 6 ? m.v - 1 : m.v + 1);
+        r.n = m.n;
+        set_nz(s, r.v);
+      }
+      wr(s, ea, r);
+      return;
+    }
+    /* ---- loads / stores of X and Y ---- */
+    case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
+      int mode = op == 0xA2 ? M_IMM : op == 0xA6 ? M_ZP : op == 0xB6 ? M_ZPY : op == 0xAE ? M_ABS : M_ABY;
+      val m = operand(s, mode);
+      s->X = m.v; s->nX = m.n; set_nz(s, s->X);
+      return;
+    }
+    case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
+      int mode = op == 0xA0 ? M_IMM : op == 0xA4 ? M_ZP : op == 0xB4 ? M_ZPX : op == 0xAC ? M_ABS : M_ABX;
+      val m = operand(s, mode);
+      s->Y = m.v; s->nY = m.n; set_nz(s, s->Y);
+      return;
+    }
+    case 0x86: case 0x96: case 0x8E: {
+      val x = {s->X, s->nX};
+      wr(s, address(s, op == 0x86 ? M_ZP : op == 0x96 ? M_ZPY : M_ABS, K_WRITE), x);
+      return;
+    }
+    case 0x84: case 0x94: case 0x8C: {
+      val x = {s->Y, s->nY};
+      wr(s, address(s, op == 0x84 ? M_ZP : op == 0x94 ? M_ZPX : M_ABS, K_WRITE), x);
+      return;
+    }
+    /* ---- compares and BIT ---- */
+    case 0xE0: case 0xE4: case 0xEC: {
+      val m = operand(s, op == 0xE0 ? M_IMM : op == 0xE4 ? M_ZP : M_ABS);
+      op_cmp(s, s->X, m.v);
+      return;
+    }
+    case 0xC0: case 0xC4: case 0xCC: {
+      val m = operand(s, op == 0xC0 ? M_IMM : op == 0xC4 ? M_ZP : M_ABS);
+      op_cmp(s, s->Y, m.v);
+      return;
+    }
+    case 0x24: case 0x2C: {
+      val m = operand(s, op == 0x24 ? M_ZP : M_ABS);
+      s->P = (uint8_t)((s->P & ~(FN | FV | FZ)) | (m.v & (FN | FV)) | ((s->A & m.v) ? 0 : FZ));
+      return;
+    }
+    /* ---- branches ---- */
+    case 0x10: branch(s, !(s->P & FN)); return;
+    case 0x30: branch(s, (s->P & FN) != 0); return;
+    case 0x50: branch(s, !(s->P & FV)); return;
+    case 0x70: branch(s, (s->P & FV) != 0); return;
+    case 0x90: branch(s, !(s->P & FC)); return;
+    case 0xB0: branch(s, (s->P & FC) != 0); return;
+    case 0xD0: branch(s, !(s->P & FZ)); return;
+    case 0xF0: branch(s, (s->P & FZ) != 0); return;
+    /* ---- jumps and subroutines ---- */
+    case 0x4C: {
+      uint8_t lo = fetch_operand(s).v;
+      uint8_t hi = fetch_operand(s).v;
+      s->pc = (uint16_t)(lo | (hi << 8));
+      return;
+    }
+    case 0x6C: {
+      uint8_t lo = fetch_operand(s).v;
+      uint8_t hi = fetch_operand(s).v;
+      uint16_t p = (uint16_t)(lo | (hi << 8));
+      uint8_t l2 = rd(s, p).v;
+      uint8_t h2 = rd(s, (uint16_t)((p & 0xFF00) | ((p + 1) & 0xFF))).v;
+      s->pc = (uint16_t)(l2 | (h2 << 8));
+      return;
+    }
+    case 0x20: {
+      uint8_t lo = fetch_operand(s).v;
+      idle(s);
+      val ph = {(uint8_t)(s->pc >> 8), 0};
+      val pl = {(uint8_t)(s->pc & 0xFF), 0};
+      push(s, ph);
+      push(s, pl);
+      uint8_t hi = rd(s, s->pc).v;
+      s->pc = (uint16_t)(lo | (hi << 8));
+      return;
+    }
+    case 0x60: {
+      idle(s);
+      idle(s);
+      uint8_t lo = pull(s).v;
+      uint8_t hi = pull(s).v;
+      idle(s);
+      s->pc = (uint16_t)((lo | (hi << 8)) + 1);
+      return;
+    }
+    case 0x40: {
+      idle(s);
+      idle(s);
+      uint8_t p = pull(s).v;
+      uint8_t lo = pull(s).v;
+      uint8_t hi = pull(s).v;
+      s->P = (uint8_t)(p | 0x30);
+      s->pc = (uint16_t)(lo | (hi << 8));
+      return;
+    }
+    case 0x00: {
+      idle(s);                         /* padding byte */
+      s->pc++;
+      val ph = {(uint8_t)(s->pc >> 8), 0};
+      val pl = {(uint8_t)(s->pc & 0xFF), 0};
+      val pp = {(uint8_t)(s->P | 0x30), 0};
+      push(s, ph);
+      push(s, pl);
+      push(s, pp);
+      s->P |= FI;
+      uint8_t lo = rd(s, 0xFFFE).v;
+      uint8_t hi = rd(s, 0xFFFF).v;
+      s->pc = (uint16_t)(lo | (hi << 8));
+      return;
+    }
+    /* ---- stack ---- */
+    case 0x48: { idle(s); val x = {s->A, s->nA}; push(s, x); return; }
+    case 0x08: { idle(s); val x = {(uint8_t)(s->P | 0x30), 0}; push(s, x); return; }
+    case 0x68: { idle(s); idle(s); val m = pull(s); s->A = m.v; s->nA = m.n; set_nz(s, s->A); return; }
+    case 0x28: { idle(s); idle(s); val m = pull(s); s->P = (uint8_t)(m.v | 0x30); return; }
+    /* ---- implied ---- */
+    case 0x18: idle(s); s->P &= (uint8_t)~FC; return;
+    case 0x38: idle(s); s->P |= FC; return;
+    case 0x58: idle(s); s->P &= (uint8_t)~FI; return;
+    case 0x78: idle(s); s->P |= FI; return;
+    case 0xB8: idle(s); s->P &= (uint8_t)~FV; return;
+    case 0xD8: idle(s); s->P &= (uint8_t)~FD; return;
+    case 0xF8: idle(s); s->P |= FD; return;
+    case 0xEA: idle(s); return;
+    case 0xAA: idle(s); s->X = s->A; s->nX = s->nA; set_nz(s, s->X); return;
+    case 0x8A: idle(s); s->A = s->X; s->nA = s->nX; set_nz(s, s->A); return;
+    case 0xA8: idle(s); s->Y = s->A; s->nY = s->nA; set_nz(s, s->Y); return;
+    case 0x98: idle(s); s->A = s->Y; s->nA = s->nY; set_nz(s, s->A); return;
+    case 0xBA: idle(s); s->X = s->SP; s->nX = 0; set_nz(s, s->X); return;
+    case 0x9A: idle(s); s->SP = s->X; return;
+    case 0xE8: idle(s); s->X++; set_nz(s, s->X); return;
+    case 0xCA: idle(s); s->X--; set_nz(s, s->X); return;
+    case 0xC8: idle(s); s->Y++; set_nz(s, s->Y); return;
+    case 0x88: idle(s); s->Y--; set_nz(s, s->Y); return;
+    default: break;
+  }
+jam:
+  s->jammed = 1;
+  s->cnt.instructions--;
+}
+
+/* One instruction slot: an instruction, or a jammed idle to the next line. */
+static int step_instruction(ovcs* s) {
+  uint64_t c0 = s->cyc;
+  if (s->jammed) {
+    do tick(s); while (s->cyc % 76 != 0);
+  } else {
+    exec(s);
+  }
+  return (int)(s->cyc - c0);
+}
+
+/* ------------------------------------------------------------------ */
+/* public API                                                          */
+/* ------------------------------------------------------------------ */
+
+ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
+  static const uint32_t sz[3] = {2048, 4096, 8192};
+  if (mapper < 0 || mapper > 2 || rom_size != sz[mapper]) return NULL;
+  ovcs* s = (ovcs*)calloc(1, sizeof(ovcs));
+  s->rom = (uint8_t*)malloc(rom_size);
+  memcpy(s->rom, rom, rom_size);
+  s->rom_size = rom_size;
+  s->mapper = mapper;
+  s->ystart = ystart;
+  ovcs_reset(s);
+  return s;
+}
+
+void ovcs_free(ovcs* s) {
+  if (!s) return;
+  free(s->rom);
+  free(s);
+}
+
+void ovcs_reset(ovcs* s) {
+  s->A = s->X = s->Y = 0;
+  s->SP = 0xFD;
+  s->P = 0x34;
+  s->cyc = 0;
+  s->jammed = 0;
+  memset(s->ram, 0, sizeof s->ram);
+  s->bank = s->mapper == 2 ? 1 : 0;
+  s->intim = 0;
+  s->interval = 1024;
+  s->phase = 0;
+  s->underflow = 0;
+  s->swcha = 0xFF;
+  s->swchb = 0x0B;
+  s->inpt4 = 0x80;
+  s->vsync = s->vblank = s->colup0 = s->colupf = s->colubk = 0;
+  s->ctrlpf = s->pf0 = s->pf1 = s->pf2 = s->grp0 = s->hmp0 = 0;
+  s->p0pos = 0;
+  s->hclk = 0;
+  s->line = 0;
+  s->hmove_line = -1;
+  s->wsync = 0;
+  memset(s->fb, 0, sizeof s->fb);
+  memset(s->last_fb, 0, sizeof s->last_fb);
+  memset(&s->cnt, 0, sizeof s->cnt);
+  s->pc = (uint16_t)(peek_raw(s, 0x1FFC) | (peek_raw(s, 0x1FFD) << 8));
+  s->frames_in_step = 0;
+}
+
+static void set_inputs(ovcs* s, const int u[5]) {
+  s->swcha = (uint8_t)(0xFF - 128 * u[0] - 64 * u[1] - 32 * u[2] - 16 * u[3]);
+  s->inpt4 = (uint8_t)(u[4] ? 0x00 : 0x80);
+}
+
+static const char* const kActionNames[18] = {
+  "NOOP", "FIRE", "UP", "RIGHT", "LEFT", "DOWN", "UPRIGHT", "UPLEFT",
+  "DOWNRIGHT", "DOWNLEFT", "UPFIRE", "RIGHTFIRE", "LEFTFIRE", "DOWNFIRE",
+  "UPRIGHTFIRE", "UPLEFTFIRE", "DOWNRIGHTFIRE", "DOWNLEFTFIRE"};
+
+static void action_bits(int action, int u[5]) {
+  const char* n = kActionNames[action % 18];
+  u[0] = strstr(n, "RIGHT") != NULL;
+  u[1] = strstr(n, "LEFT") != NULL;
+  u[2] = strstr(n, "DOWN") != NULL;
+  u[3] = strstr(n, "UP") != NULL;
+  u[4] = strstr(n, "FIRE") != NULL;
+}
+
+static int run_frames(ovcs* s, int frame_skip) {
+  int status = 0;
+  s->frames_in_step = 0;
+  s->frame_skip = frame_skip;
+  set_gs(s);
+  while (s->frames_in_step < frame_skip) {
+    step_instruction(s);
+    if (s->line >= LINE_CAP) {
+      frame_end(s);
+      s->cnt.watchdog++;
+      status |= 1;
+    }
+  }
+  if (s->jammed) status |= 2;
+  return status;
+}
+
+int ovcs_step(ovcs* s, int action, int frame_skip, uint8_t* ram_out, uint8_t* screen_out) {
+  int u[5];
+  action_bits(action, u);
+  set_inputs(s, u);
+  int st = run_frames(s, frame_skip);
+  if (ram_out) memcpy(ram_out, s->ram, 128);
+  if (screen_out) memcpy(screen_out, s->last_fb, sizeof s->last_fb);
+  return st;
+}
+
+void ovcs_get_counters(const ovcs* s, ovcs_counters* out) { *out = s->cnt; }
+
+void ovcs_get_state(const ovcs* s, uint32_t* o) {
+  memset(o, 0, 32 * sizeof(uint32_t));
+  o[0] = s->A; o[1] = s->X; o[2] = s->Y; o[3] = s->SP; o[4] = s->P; o[5] = s->pc;
+  o[6] = (uint32_t)s->cyc; o[7] = (uint32_t)(s->cyc >> 32);
+  o[8] = s->bank; o[9] = s->intim; o[10] = s->interval; o[11] = s->phase; o[12] = s->underflow;
+  o[13] = s->vsync; o[14] = s->vblank; o[15] = s->colup0; o[16] = s->colupf; o[17] = s->colubk;
+  o[18] = s->ctrlpf; o[19] = s->pf0; o[20] = s->pf1; o[21] = s->pf2; o[22] = s->grp0;
+  o[23] = s->hmp0; o[24] = (uint32_t)s->p0pos; o[25] = (uint32_t)s->hclk; o[26] = (uint32_t)s->line;
+  o[27] = (uint32_t)s->hmove_line; o[28] = (uint32_t)s->jammed;
+}
+
+void ovcs_get_ram(const ovcs* s, uint8_t* out128) { memcpy(out128, s->ram, 128); }
+
+int ovcs_trace(ovcs* s, int action, int n, uint32_t* out) {
+  int u[5];
+  action_bits(action, u);
+  set_inputs(s, u);
+  int i;
+  for (i = 0; i < n; i++) {
+    uint32_t* o = out + 10 * i;
+    o[0] = s->pc; o[1] = peek_raw(s, s->pc); o[2] = s->A; o[3] = s->X; o[4] = s->Y;
+    o[5] = s->SP; o[6] = s->P; o[7] = (uint32_t)s->cyc; o[8] = (uint32_t)s->line; o[9] = (uint32_t)s->hclk;
+    step_instruction(s);
+    if (s->line >= LINE_CAP) frame_end(s);
+  }
+  return i;
+}
+
+void ovcs_set_regs(ovcs* s, int A, int X, int Y, int SP, int P, int PC) {
+  s->A = (uint8_t)A; s->X = (uint8_t)X; s->Y = (uint8_t)Y; s->SP = (uint8_t)SP;
+  s->P = (uint8_t)(P | 0x30); s->pc = (uint16_t)PC;
+}
+void ovcs_set_ram(ovcs* s, const uint8_t* ram128) { memcpy(s->ram, ram128, 128); }
+int ovcs_exec_one(ovcs* s) { return step_instruction(s); }
+uint8_t ovcs_peek(ovcs* s, uint16_t addr) { return peek_raw(s, addr); }
+int ovcs_bank(const ovcs* s) { return s->bank; }
+
+/* ------------------------------------------------------------------ */
+/* soft mode                                                           */
+/* ------------------------------------------------------------------ */
+
+static int half_width(double tau) {
+  int w = (int)ceil(12.0 * tau);
+  return w < 1 ? 1 : w;
+}
+
+/* Weights of the relaxed read over cells lo..lo+n-1 at real address a;
+ * returns the normaliser-free quantities via out arrays. */
+static void read_weights(int lo, int n, double a, double tau, double* w) {
+  double z = 0.0;
+  for (int i = 0; i < n; i++) {
+    w[i] = exp(-fabs((double)(lo + i) - a) / tau);
+    z += w[i];
+  }
+  for (int i = 0; i < n; i++) w[i] /= z;
+}
+
+static double sgn(double x) { return x > 0 ? 1.0 : (x < 0 ? -1.0 : 0.0); }
+
+double ovcs_relaxed_read(const double* r, int M, int a0, double a, double tau, double* d_da) {
+  int lo, hi;
+  window(half_width(tau), M, a0, &lo, &hi);
+  int n = hi - lo + 1;
+  double w[256];
+  read_weights(lo, n, a, tau, w);
+  double v = 0, sw = 0, swr = 0;
+  for (int i = 0; i < n; i++) {
+    double si = sgn((double)(lo + i) - a);
+    v += w[i] * r[lo + i];
+    sw += w[i] * si;
+    swr += w[i] * si * r[lo + i];
+  }
+  if (d_da) *d_da = (swr - v * sw) / tau;
+  return v;
+}
+
+double ovcs_gate_slope(double alpha, double z) {
+  double g = 1.0 / (1.0 + exp(-alpha * z));
+  return alpha * g * (1.0 - g);
+}
+
+ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
+                        double tau, double alpha,
+                        const double* grad_ram, const double* grad_screen,
+                        double* ram_out, double* screen_out) {
+  ogrf* g = (ogrf*)calloc(1, sizeof(ogrf));
+  g->tau = tau;
+  g->alpha = alpha;
+  g->W = half_width(tau);
+  g->n_steps = n_steps;
+  g->rom_size = (int)s->rom_size;
+  g->rom_copy = (uint8_t*)malloc(s->rom_size);
+  memcpy(g->rom_copy, s->rom, s->rom_size);
+  g->rom = g->rom_copy;
+  s->g = g;
+  g_new(s, NK_ZERO);
+  g->rom0 = (int32_t)g->n;
+  for (uint32_t i = 0; i < s->rom_size; i++) g_new(s, NK_LEAF);
+  g->ram0 = (int32_t)g->n;
+  for (int i = 0; i < 128; i++) g_new(s, NK_LEAF);
+  g->u0 = (int32_t)g->n;
+  for (int i = 0; i < 5 * n_steps; i++) g_new(s, NK_LEAF);
+  for (int i = 0; i < 128; i++) g->ram0_val[i] = s->ram[i];
+  g->u_val = (double*)malloc(sizeof(double) * (size_t)(5 * n_steps > 0 ? 5 * n_steps : 1));
+  for (int i = 0; i < 5 * n_steps; i++) g->u_val[i] = u[i];
+  /* ROM-read nodes address ROM leaves at rom0 + base + index */
+  for (int i = 0; i < 128; i++) s->nRAM[i] = g->ram0 + i;
+  s->nA = s->nX = s->nY = s->nV = 0;
+  s->nC[0] = s->nC[1] = s->nC[2] = 0;
+  s->gs_all = grad_screen;
+  for (int t = 0; t < n_steps; t++) {
+    int bits[5];
+    for (int k = 0; k < 5; k++) bits[k] = u[5 * t + k] >= 0.5;
+    set_inputs(s, bits);
+    s->u_leaf = g->u0 + 5 * t;
+    s->soft_step = t;
+    run_frames(s, frame_skip);
+    for (int i = 0; i < 128; i++) {
+      if (grad_ram && s->nRAM[i]) g->seed[s->nRAM[i]] += grad_ram[128 * t + i];
+      if (ram_out) ram_out[128 * t + i] = s->ram[i];
+    }
+    if (screen_out)
+      for (int i = 0; i < SCR_H * SCR_W; i++) screen_out[(size_t)SCR_H * SCR_W * t + i] = s->last_fb[i];
+  }
+  s->g = NULL;
+  s->gs = s->gs_all = NULL;
+  for (int i = 0; i < 128; i++) s->nRAM[i] = 0;
+  s->nA = s->nX = s->nY = s->nV = 0;
+  s->nC[0] = s->nC[1] = s->nC[2] = 0;
+  return g;
+}
+
+void ogrf_free(ogrf* g) {
+  if (!g) return;
+  free(g->nd); free(g->seed); free(g->pnode); free(g->u_val); free(g->rom_copy);
+  free(g);
+}
+
+int64_t ogrf_nodes(const ogrf* g) { return g->n; }
+
+/* node id of a read node's cell i */
+static int32_t cell_node(const ogrf* g, const onode* nd, int i) {
+  if (nd->kind == NK_RROM) return g->rom0 + nd->base + nd->lo + i;
+  return g->pnode[nd->pool + i];
+}
+
+void ogrf_reverse(ogrf* g, double* grad_rom, double* grad_ram0, double* grad_u) {
+  double* adj = (double*)malloc((size_t)g->n * sizeof(double));
+  memcpy(adj, g->seed, (size_t)g->n * sizeof(double));
+  double w[256];
+  for (int64_t k = g->n - 1; k > 0; k--) {
+    const onode* nd = &g->nd[k];
+    double a = adj[k];
+    if (a == 0.0) continue;
+    if (nd->kind == NK_LIN) {
+      for (int j = 0; j < nd->n; j++) adj[nd->in[j]] += nd->c[j] * a;
+    } else if (nd->kind == NK_RROM || nd->kind == NK_RRAM) {
+      read_weights(nd->lo, nd->n, (double)nd->a0, g->tau, w);
+      for (int i = 0; i < nd->n; i++) {
+        int32_t c = cell_node(g, nd, i);
+        if (c) adj[c] += w[i] * a;
+      }
+    }
+  }
+  for (int i = 0; i < g->rom_size; i++) grad_rom[i] = adj[g->rom0 + i];
+  for (int i = 0; i < 128; i++) grad_ram0[i] = adj[g->ram0 + i];
+  for (int i = 0; i < 5 * g->n_steps; i++) grad_u[i] = adj[g->u0 + i];
+  free(adj);
+}
+
+static void set_leaves(const ogrf* g, double* d, const double* d_rom, const double* d_ram0, const double* d_u) {
+  for (int i = 0; i < g->rom_size; i++) d[g->rom0 + i] = d_rom ? d_rom[i] : 0.0;
+  for (int i = 0; i < 128; i++) d[g->ram0 + i] = d_ram0 ? d_ram0[i] : 0.0;
+  for (int i = 0; i < 5 * g->n_steps; i++) d[g->u0 + i] = d_u ? d_u[i] : 0.0;
+}
+
+double ogrf_tangent(ogrf* g, const double* d_rom, const double* d_ram0, const double* d_u) {
+  double* d = (double*)calloc((size_t)g->n, sizeof(double));
+  set_leaves(g, d, d_rom, d_ram0, d_u);
+  double w[256];
+  double out = 0.0;
+  for (int64_t k = 1; k < g->n; k++) {
+    const onode* nd = &g->nd[k];
+    if (nd->kind == NK_LIN) {
+      double v = 0;
+      for (int j = 0; j < nd->n; j++) v += nd->c[j] * d[nd->in[j]];
+      d[k] = v;
+    } else if (nd->kind == NK_RROM || nd->kind == NK_RRAM) {
+      read_weights(nd->lo, nd->n, (double)nd->a0, g->tau, w);
+      double v = 0;
+      for (int i = 0; i < nd->n; i++) {
+        int32_t c = cell_node(g, nd, i);
+        if (c) v += w[i] * d[c];
+      }
+      d[k] = v;
+    }
+    out += g->seed[k] * d[k];
+  }
+  free(d);
+  return out;
+}
+
+/* Exact evaluation of L(x) - L(x_hard) of the frozen-switch relaxation.
+ * With addresses frozen every node is affine in its inputs, so this equals
+ * the tangent sweep up to rounding; it is kept as a separate, direct
+ * evaluation (hard + soft(x) - soft(x_hard) per node) for finite differences. */
+double ogrf_eval(ogrf* g, const double* d_rom, const double* d_ram0, const double* d_u) {
+  double* x = (double*)calloc((size_t)g->n, sizeof(double));   /* soft value of each node */
+  double* h = (double*)calloc((size_t)g->n, sizeof(double));   /* its value at the hard point */
+  for (int i = 0; i < g->rom_size; i++) {
+    h[g->rom0 + i] = g->rom[i];
+    x[g->rom0 + i] = g->rom[i] + (d_rom ? d_rom[i] : 0.0);
+  }
+  for (int i = 0; i < 128; i++) {
+    h[g->ram0 + i] = g->ram0_val[i];
+    x[g->ram0 + i] = g->ram0_val[i] + (d_ram0 ? d_ram0[i] : 0.0);
+  }
+  for (int i = 0; i < 5 * g->n_steps; i++) {
+    h[g->u0 + i] = g->u_val[i];
+    x[g->u0 + i] = g->u_val[i] + (d_u ? d_u[i] : 0.0);
+  }
+  double w[256];
+  double out = 0.0;
+  for (int64_t k = 1; k < g->n; k++) {
+    const onode* nd = &g->nd[k];
+    double sx = 0.0, sh = 0.0;
+    if (nd->kind == NK_LIN) {
+      for (int j = 0; j < nd->n; j++) {
+        sx += nd->c[j] * x[nd->in[j]];
+        sh += nd->c[j] * h[nd->in[j]];
+      }
+    } else if (nd->kind == NK_RROM || nd->kind == NK_RRAM) {
+      read_weights(nd->lo, nd->n, (double)nd->a0, g->tau, w);
+      for (int i = 0; i < nd->n; i++) {
+        int32_t c = cell_node(g, nd, i);
+        sx += w[i] * x[c];
+        sh += w[i] * h[c];
+      }
+    } else {
+      out += g->seed[k] * (x[k] - h[k]);    /* leaf seeded directly */
+      continue;
+    }
+    /* node value = hard + soft(x) - soft(x_hard); its hard value is
+     * represented by sh (the soft value at the hard point) */
+    x[k] = sx;
+    h[k] = sh;
+    out += g->seed[k] * (sx - sh);
+  }
+  free(x);
+  free(h);
+  return out;
+}

@@ -1,0 +1,112 @@
+/*
+ * CPU oracle for the VCS hot path: TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, cycle-by-cycle emulator of the Atari VCS (6507 CPU, RIOT,
+ * TIA video subset, 2K/4K/F8 cartridges) written from the paper's machine
+ * description (Section 2.2 and the architecture figure) and the public chip
+ * documentation (MOS 6500 manuals, 6532 datasheet, TIA programmer's guide,
+ * the published note on NMOS decimal mode).  Every CPU cycle is charged
+ * before its bus access; the RIOT timer ticks once per cycle and the TIA is
+ * advanced one colour clock at a time, three per cycle.
+ *
+ * Soft mode (SOFT-STE, Section 3.1; Theorem 1; Corollary 1): the same
+ * interpreter optionally records a deviation graph.  Every value carries a
+ * node whose value under perturbation is hard + (soft(x) - soft(x_hard)),
+ * with every discrete choice frozen (the stored-switch rule of Section 3.1).
+ * Surrogate rulebook: a ROM or RAM read takes the Jacobian of the relaxed
+ * read (Eq. s-read) with respect to the memory contents, i.e. weights
+ * w_i ~ exp(-|i - a| / tau) over the window |i - a| <= W = max(1,
+ * ceil(12 tau)) clipped to the tensor; addresses, the program counter and
+ * flags are indices or bits and so carry no gradient; writes move the
+ * cell's adjoint to the written value; ADC/SBC have derivatives (1, +-1),
+ * AND/ORA/EOR (1, 1), increments, transfers, shifts and rotates 1 (the
+ * straight-through rule for integer casts); SWCHA/INPT4 are linear in the
+ * joystick inputs and INTIM in the last timer value before underflow;
+ * pixels take the derivative 1 of the owning colour register.  Reverse
+ * mode, tangent mode and a direct re-evaluation (for finite differences)
+ * run over the graph in double precision.
+ *
+ * Only the test suite, the package's smoke check and the benchmark's CPU
+ * baseline call this library; the product path never does.
+ */
+#ifndef VCS_ORACLE_H
+#define VCS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ovcs ovcs;
+
+/* Counters accumulated over the emulator's lifetime (reset by ovcs_reset). */
+typedef struct {
+  uint64_t instructions;   /* executed instructions (jam steps excluded) */
+  uint64_t cycles;         /* CPU cycles */
+  uint64_t frames;         /* completed frames */
+  uint64_t tia_writes;     /* writes to TIA registers */
+  uint64_t ram_reads, ram_writes, rom_reads;
+  uint64_t pixels;         /* pixels composited into an output frame */
+  uint64_t watchdog;       /* frames ended by the line cap */
+} ovcs_counters;
+
+/* mapper: 0 = 2K, 1 = 4K, 2 = F8.  rom is copied.  NULL on a bad size. */
+ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart);
+void ovcs_free(ovcs* s);
+/* Power-on state (A7 of the design notes). */
+void ovcs_reset(ovcs* s);
+/* One env-step: set the joystick from `action` (ALE index 0..17), run
+ * `frame_skip` frames, copy RAM (128 B) and the last frame (210x160) out.
+ * Returns a status bit set: 1 = a frame ended by the line cap, 2 = jammed. */
+int ovcs_step(ovcs* s, int action, int frame_skip, uint8_t* ram_out, uint8_t* screen_out);
+void ovcs_get_counters(const ovcs* s, ovcs_counters* out);
+/* Machine state as 32 words (layout in the .c file). */
+void ovcs_get_state(const ovcs* s, uint32_t* out32);
+void ovcs_get_ram(const ovcs* s, uint8_t* out128);
+/* Run n instructions, recording per instruction: pc, opcode, A, X, Y, SP,
+ * P, cycle (low 32 bits), scanline, line clock.  Returns instructions run. */
+int ovcs_trace(ovcs* s, int action, int n, uint32_t* out10);
+
+/* Test hooks: set registers / RAM / memory state directly. */
+void ovcs_set_regs(ovcs* s, int A, int X, int Y, int SP, int P, int PC);
+void ovcs_set_ram(ovcs* s, const uint8_t* ram128);
+/* Execute exactly one instruction; returns its cycle count. */
+int ovcs_exec_one(ovcs* s);
+uint8_t ovcs_peek(ovcs* s, uint16_t addr);   /* side-effect-free debug read */
+int ovcs_bank(const ovcs* s);
+
+/* ---------------- soft mode (FP64 deviation graph) ---------------- */
+
+typedef struct ogrf ogrf;
+
+/* Run a soft rollout from the current state for n_steps env-steps.
+ * u[n_steps][5] are the joystick inputs (R, L, D, U, FIRE) in {0,1};
+ * tau > 0 is the read temperature and alpha the gate sharpness.
+ * grad_ram [n_steps][128] and grad_screen [n_steps][210*160] (either may be
+ * NULL) are the loss weights L = sum grad * output.  ram_out/screen_out
+ * (nullable) receive the forward outputs as doubles.  Returns the graph. */
+ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
+                        double tau, double alpha,
+                        const double* grad_ram, const double* grad_screen,
+                        double* ram_out, double* screen_out);
+void ogrf_free(ogrf* g);
+/* Reverse sweep: d L / d (ROM bytes [rom_size], initial RAM [128],
+ * inputs [n_steps][5]). */
+void ogrf_reverse(ogrf* g, double* grad_rom, double* grad_ram0, double* grad_u);
+/* Tangent sweep: directional derivative of L along (d_rom, d_ram0, d_u). */
+double ogrf_tangent(ogrf* g, const double* d_rom, const double* d_ram0, const double* d_u);
+/* Exact re-evaluation of L - L_hard of the frozen-switch relaxation at the
+ * hard inputs plus the given perturbation (finite differences). */
+double ogrf_eval(ogrf* g, const double* d_rom, const double* d_ram0, const double* d_u);
+int64_t ogrf_nodes(const ogrf* g);
+/* The relaxed read primitive on its own (Eq. s-read with the frozen window
+ * of half-width W = max(1, ceil(12 tau)) clipped to [0, M)): value and
+ * derivative with respect to the (real) address a around integer a0. */
+double ovcs_relaxed_read(const double* r, int M, int a0, double a, double tau, double* d_da);
+/* Gate derivative alpha * s(alpha z) (1 - s(alpha z)) of Eq. s-branch. */
+double ovcs_gate_slope(double alpha, double z);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,303 @@
+"""Pins of the oracle's bus, RIOT and TIA against fixed facts:
+
+* colour-clock invariants: 3 colour clocks per CPU cycle, 228 per scanline,
+  WSYNC resumes at line clock 0, a 262-WSYNC frame is 262 lines and 19,912
+  cycles (NTSC);
+* the RIOT timer against its closed form (reading A8);
+* F8 bank switching happens only on the two hotspot addresses;
+* hand-derived pixels for playfield, player and priority cases (A3-A6).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_22447_b300 import synth
+from tests.microrom import rom4k
+
+WSYNC, VSYNC, VBLANK = 0x02, 0x00, 0x01
+
+
+def _frame_rom():
+    def build(a):
+        a.op("LDA", "imm", 2)
+        a.op("LDY", "imm", 0)
+        a.op("STA", "zp", WSYNC)
+        a.label("FRAME")
+        a.op("STA", "zp", VSYNC)
+        a.op("STY", "zp", VSYNC)
+        a.op("LDX", "imm", 5)
+        a.label("L1")
+        a.op("STA", "zp", WSYNC)
+        a.op("DEX")
+        a.op("BNE", "rel", "L1")
+        a.label("L2")
+        a.op("STA", "zp", WSYNC)
+        a.op("DEX")
+        a.op("BNE", "rel", "L2")
+        a.op("STA", "zp", WSYNC)
+        a.op("JMP", "abs", "FRAME")
+    return rom4k(build)
+
+
+def test_ntsc_frame_262_lines_19912_cycles():
+    o = oracle.Oracle(_frame_rom(), synth.MAPPER_4K)
+    o.step(0, 1)
+    cyc = []
+    for _ in range(4):
+        o.step(0, 1)
+        s = o.state()
+        cyc.append(int(s[6]) | (int(s[7]) << 32))
+    assert np.all(np.diff(cyc) == 19912)
+    # at each frame end (just after the VSYNC write) the beam is at line 0
+    assert o.state()[26] == 0
+
+
+def test_colour_clocks_per_cycle_and_wsync():
+    o = oracle.Oracle(_frame_rom(), synth.MAPPER_4K)
+    tr = o.trace(0, 3000).astype(np.int64)
+    pc, op, cyc, line, hclk = tr[:, 0], tr[:, 1], tr[:, 7], tr[:, 8], tr[:, 9]
+    for i in range(1, len(tr)):
+        if line[i] >= line[i - 1]:          # same frame
+            assert (line[i] * 228 + hclk[i]) - (line[i - 1] * 228 + hclk[i - 1]) == 3 * (cyc[i] - cyc[i - 1])
+        assert 0 <= hclk[i] < 228 and hclk[i] % 3 == 0
+    # every instruction after STA WSYNC starts at line clock 0, and the
+    # absolute beam position is 3 x cycles modulo 228
+    after = np.where((op[:-1] == 0x85) & (np.arange(len(tr) - 1) >= 0))[0]
+    wsync_next = [i + 1 for i in after if o.rom[(pc[i] - 0xF000) + 1] == WSYNC]
+    assert len(wsync_next) > 100
+    assert np.all(hclk[wsync_next] == 0)
+    assert np.all((3 * cyc) % 228 == hclk)
+
+
+# ---------------------------------------------------------------------------
+# RIOT timer
+# ---------------------------------------------------------------------------
+
+def _timer_closed_form(V, I, k):
+    """INTIM and TIMINT bit 7 at k >= 1 cycles after writing V to an
+    interval-I register."""
+    if k <= V * I:
+        return V - (-(-k // I)), 0
+    ku = V * I + 1
+    return (0xFF - (k - ku)) & 0xFF, 0x80
+
+
+@pytest.mark.parametrize("V,reg,I", [(0, 0x294, 1), (1, 0x294, 1), (5, 0x295, 8), (43, 0x296, 64),
+                                     (2, 0x297, 1024), (255, 0x294, 1), (7, 0x296, 64), (1, 0x297, 1024)])
+def test_timer_closed_form(V, reg, I):
+    def build(a):
+        a.op("LDA", "imm", V)
+        a.op("STA", "abs", reg)       # write at cycle 4 of this instruction
+        a.label("LOOP")
+        a.op("LDA", "abs", 0x284)     # INTIM read at cycle 4
+        a.op("LDX", "abs", 0x285)     # TIMINT read at cycle 4
+        a.op("NOP")
+        a.op("JMP", "abs", "LOOP")
+    o = oracle.Oracle(rom4k(build), synth.MAPPER_4K)
+    n = min(3 * (V * I + 2000) // 13 + 50, 60000)
+    tr = o.trace(0, n).astype(np.int64)
+    pc, A, X, cyc = tr[:, 0], tr[:, 2], tr[:, 3], tr[:, 7]
+    tw = cyc[1] + 4
+    checked = 0
+    for i in range(2, len(tr) - 1):
+        if pc[i] == 0xF005:                    # LDA INTIM
+            k = cyc[i] + 4 - tw
+            assert A[i + 1] == _timer_closed_form(V, I, k)[0], (k, A[i + 1])
+            checked += 1
+        elif pc[i] == 0xF008:                  # LDX TIMINT
+            k = cyc[i] + 4 - tw
+            assert X[i + 1] == _timer_closed_form(V, I, k)[1], k
+    assert checked > 100
+
+
+def test_timer_power_on_state():
+    """Power-on behaves as a write of 0 to T1024T at cycle 0."""
+    def build(a):
+        a.label("LOOP")
+        a.op("LDA", "abs", 0x284)
+        a.op("JMP", "abs", "LOOP")
+    o = oracle.Oracle(rom4k(build), synth.MAPPER_4K)
+    tr = o.trace(0, 200).astype(np.int64)
+    for i in range(0, len(tr) - 1, 2):
+        k = tr[i, 7] + 4
+        assert tr[i + 1, 2] == _timer_closed_form(0, 1024, k)[0]
+
+
+# ---------------------------------------------------------------------------
+# F8 bank switching
+# ---------------------------------------------------------------------------
+
+def test_f8_switches_only_on_hotspots():
+    """Bank 1 runs reads of addresses next to the hotspots, then LDA $1FF8
+    (-> bank 0); bank 0 continues at the same offset and writes $1FF9."""
+    b1 = synth.Asm(0xF000, 4096)
+    b1.op("LDA", "abs", 0x1FF7)
+    b1.op("LDA", "abs", 0x1FFA)
+    b1.op("STA", "abs", 0x1FFB)
+    b1.op("LDA", "abs", 0x0FF8)      # not a cartridge address (A12 = 0)
+    b1.op("LDA", "abs", 0x1FF8)      # -> bank 0
+    b1.at(4096 - 6)
+    b1.word(0xF000), b1.word(0xF000), b1.word(0xF000)
+    b0 = synth.Asm(0xF000, 4096)
+    b0.at(15)
+    b0.op("STA", "abs", 0xFFF9)      # mirror of $1FF9 -> bank 1
+    b0.at(4096 - 6)
+    b0.word(0xF000), b0.word(0xF000), b0.word(0xF000)
+    rom = bytes(b0.resolve()) + bytes(b1.resolve())
+    o = oracle.Oracle(rom, synth.MAPPER_F8)
+    assert o.bank() == 1
+    for _ in range(4):
+        o.exec_one()
+        assert o.bank() == 1
+    o.exec_one()
+    assert o.bank() == 0
+    assert o.state()[5] == 0xF00F and o.peek(0xF00F) == 0x8D
+    o.exec_one()
+    assert o.bank() == 1
+
+
+# ---------------------------------------------------------------------------
+# pixels
+# ---------------------------------------------------------------------------
+
+def _screen_of(build_line, ystart=0, frames=2):
+    """Run a kernel where every scanline executes `build_line` after WSYNC;
+    return the last frame."""
+    def build(a):
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", VBLANK)
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", WSYNC)
+        a.op("STA", "zp", VSYNC)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", VSYNC)
+        a.op("LDX", "imm", 230)
+        a.label("LINE")
+        a.op("STA", "zp", WSYNC)
+        build_line(a)
+        a.op("DEX")
+        a.op("BNE", "rel", "LINE")
+        a.op("JMP", "abs", "FRAME")
+    o = oracle.Oracle(rom4k(build), synth.MAPPER_4K, ystart=ystart)
+    for _ in range(frames):
+        _, scr, st = o.step(0, 1)
+    assert st == 0
+    return scr
+
+
+def test_playfield_bits_and_reflection():
+    def line(a):
+        a.op("LDA", "imm", 0x44)
+        a.op("STA", "zp", 0x08)       # COLUPF
+        a.op("LDA", "imm", 0x12)
+        a.op("STA", "zp", 0x09)       # COLUBK
+        a.op("LDA", "imm", 0x10)
+        a.op("STA", "zp", 0x0D)       # PF0 bit 4 -> playfield bit 0
+        a.op("LDA", "imm", 0x40)
+        a.op("STA", "zp", 0x0E)       # PF1 bit 6 -> playfield bit 5
+        a.op("LDA", "imm", 0x80)
+        a.op("STA", "zp", 0x0F)       # PF2 bit 7 -> playfield bit 19
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x0A)       # no reflection
+    row = _screen_of(line)[20]
+    lit = set(np.where(row == 0x44)[0])
+    exp = set(range(0, 4)) | set(range(20, 24)) | set(range(76, 80))
+    exp |= {x + 80 for x in exp}
+    assert lit == exp
+    assert np.all(row[[x for x in range(160) if x not in exp]] == 0x12)
+
+    def line_r(a):
+        line(a)
+        a.op("LDA", "imm", 1)
+        a.op("STA", "zp", 0x0A)       # reflect right half
+    row = _screen_of(line_r)[20]
+    lit = set(np.where(row == 0x44)[0])
+    left = set(range(0, 4)) | set(range(20, 24)) | set(range(76, 80))
+    assert lit == left | {159 - x for x in left}
+
+
+def test_colour_write_mid_line_and_lsb_masked():
+    """STA COLUBK at line cycle c changes pixels from colour clock 3c on."""
+    def line(a):
+        a.op("LDA", "imm", 0x21)       # odd: the pixel keeps only bits 7..1
+        a.op("STA", "zp", 0x09)        # write at cycle 5 -> clock 15 (HBLANK)
+        a.op("LDA", "imm", 0x60)
+        for _ in range(12):
+            a.op("NOP")                # cycles 6..29
+        a.op("STA", "zp", 0x09)        # cycles 32..34 -> write at cycle 34 = clock 102
+    row = _screen_of(line)[30]
+    x0 = 3 * 34 - 68
+    assert np.all(row[:x0] == 0x20) and np.all(row[x0:] == 0x60)
+
+
+def _player_line(ctrlpf, nops):
+    def line(a):
+        a.op("LDA", "imm", 0x80)
+        a.op("STA", "zp", 0x06)    # COLUP0 = $80
+        a.op("LDA", "imm", 0xF0)
+        a.op("STA", "zp", 0x0D)    # PF0 = $F0: pixels 0..15 and 80..95
+        a.op("LDA", "imm", 0x40)
+        a.op("STA", "zp", 0x08)    # COLUPF
+        a.op("LDA", "imm", 0xA5)
+        a.op("STA", "zp", 0x1B)    # GRP0 = 10100101
+        a.op("LDA", "imm", ctrlpf)
+        a.op("STA", "zp", 0x0A)
+        for _ in range(nops):
+            a.op("NOP")
+        a.op("STA", "zp", 0x10)    # RESP0
+    return line
+
+
+def test_player_position_and_priority():
+    """RESP0 written at line cycle c puts P0 at (3c - 68 + 5) mod 160; GRP0
+    is drawn MSB first; P0 beats PF unless CTRLPF bit 2."""
+    bits = [1, 0, 1, 0, 0, 1, 0, 1]
+    # 5 x (LDA # + STA zp) = 25 cycles, NOPs, then STA RESP0 writes at +3
+    c = 25 + 2 * 5 + 3
+    pos = 3 * c - 68 + 5
+    assert pos == 51
+    row = _screen_of(_player_line(0, 5))[40]
+    for i, b in enumerate(bits):
+        assert row[pos + i] == (0x80 if b else 0x00), (i, row[pos + i])
+    assert row[pos - 1] == 0 and row[pos + 8] == 0
+    # 6 more NOPs: c = 50 -> position 87, inside the PF0 block 80..95
+    pos = 3 * (c + 12) - 68 + 5
+    assert pos == 87
+    r0 = _screen_of(_player_line(0, 11))[40]
+    r4 = _screen_of(_player_line(4, 11))[40]
+    for i, b in enumerate(bits):
+        assert r0[pos + i] == (0x80 if b else 0x40)
+        assert r4[pos + i] == 0x40
+
+
+def test_resp0_in_hblank_gives_position_3():
+    def line(a):
+        a.op("LDA", "imm", 0x80)
+        a.op("STA", "zp", 0x06)
+        a.op("LDA", "imm", 0xFF)
+        a.op("STA", "zp", 0x1B)
+        a.op("STA", "zp", 0x10)        # cycle 13 -> clock 39 < 68
+    row = _screen_of(line)[40]
+    assert set(np.where(row == 0x80)[0]) == set(range(3, 11))
+
+
+def test_hmove_blank_and_motion():
+    """HMOVE right after WSYNC blanks pixels 0..7 of that line and moves P0
+    left by the signed HMP0 nibble."""
+    def line(a):
+        a.op("STA", "zp", 0x2A)        # HMOVE at cycle 3 -> clock 9
+        a.op("LDA", "imm", 0x0E)
+        a.op("STA", "zp", 0x09)        # COLUBK = $0E
+    row = _screen_of(line)[10]
+    assert np.all(row[:8] == 0) and np.all(row[8:] == 0x0E)
+
+
+def test_vblank_blacks_out():
+    def line(a):
+        a.op("LDA", "imm", 0x3C)
+        a.op("STA", "zp", 0x09)
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x01)        # VBLANK on from cycle 10 -> clock 30
+    row = _screen_of(line)[10]
+    assert np.all(row == 0)

@@ -1,0 +1,214 @@
+"""Pins of the oracle's soft (SOFT-STE) mode.
+
+* the gate-gradient values and read/branch bounds the paper prints
+  (tests/golden/relaxation_constants.txt);
+* the relaxed read collapses to the one-hot read at small temperature and
+  its address derivative matches finite differences;
+* Theorem 1: the soft rollout's forward outputs equal the hard rollout's
+  bit for bit at tau in {1, 0.1, 0.01};
+* the reverse sweep equals the tangent sweep (transpose identity) and
+  central finite differences of the frozen-switch relaxation;
+* an analytic micro-program: d(sum of pixels)/d(ROM byte of LDA #k before
+  STA COLUP0) equals the number of P0-owned pixels.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_22447_b300 import synth
+from tests.microrom import rom4k
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "relaxation_constants.txt")
+
+
+def _golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("--")[0].strip()
+        if line and not line.startswith("#"):
+            name, v, tol = line.split()
+            out[name] = (float(v), float(tol))
+    return out
+
+
+def test_gate_gradient_study_values():
+    g = _golden()
+    s = {a: oracle.gate_slope(a, 0.25) for a in (2.0, 6.0, 20.0)}
+    peak = max(s.values())
+    for a, key in ((2.0, "gate_rel_peak_alpha2"), (6.0, "gate_rel_peak_alpha6"), (20.0, "gate_rel_peak_alpha20")):
+        v, tol = g[key]
+        assert abs(s[a] / peak - v) <= tol, (a, s[a] / peak)
+    v, tol = g["gate_abs_peak_alpha6"]
+    assert abs(s[6.0] - v) <= tol
+
+
+def _pull(T):
+    r = np.array([255.0, 255.0, 0.0, 255.0, 255.0])
+    v, _ = oracle.relaxed_read(r, 2, 2.0, T)
+    return v
+
+
+def test_read_pull_and_bounds():
+    g = _golden()
+    v, tol = g["read_pull_T014"]
+    assert abs(_pull(0.14) - v) <= tol
+    # the pull crosses 1/2 at the printed temperature bound
+    lo, hi = 0.12, 0.17
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if _pull(mid) < 0.5 else (lo, mid)
+    v, tol = g["read_bound_T"]
+    assert abs(lo - v) <= tol, lo
+    # branch: a taken gate with offset d rounds correctly iff d < (1 + e^a)/2
+    v, tol = g["branch_bound_alpha"]
+    alpha_min = math.log(2 * 127 - 1)
+    assert abs(alpha_min - v) <= tol
+    for a in (5.0, 6.0):
+        gate = 1.0 / (1.0 + math.exp(-a))
+        ok = all(abs((1 - gate) * d) < 0.5 for d in range(1, 128))
+        assert ok == (a >= alpha_min)
+
+
+def test_relaxed_read_limits_and_derivative():
+    rng = np.random.default_rng(1)
+    r = rng.integers(0, 256, 64).astype(np.float64)
+    for a0 in (0, 1, 30, 63):
+        v, d = oracle.relaxed_read(r, a0, float(a0), 0.01)
+        assert abs(v - r[a0]) < 1e-30 and abs(d) < 1e-30
+    for tau in (1.0, 0.3):
+        for a in (10.3, 20.6):
+            a0 = int(round(a))
+            h = 1e-5
+            vp, _ = oracle.relaxed_read(r, a0, a + h, tau)
+            vm, _ = oracle.relaxed_read(r, a0, a - h, tau)
+            _, d = oracle.relaxed_read(r, a0, a, tau)
+            assert abs((vp - vm) / (2 * h) - d) < 1e-6 * max(1.0, abs(d))
+    # weights are a normalised distance-softmax: a constant tensor reads back
+    c = np.full(16, 7.0)
+    v, d = oracle.relaxed_read(c, 5, 5.0, 1.0)
+    assert abs(v - 7.0) < 1e-12 and abs(d) < 1e-12
+
+
+def _cart(seed=3, mapper=synth.MAPPER_4K):
+    return synth.generate_cart(seed, 0, mapper)
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.1, 0.01])
+def test_theorem1_soft_forward_equals_hard(tau):
+    rom = _cart()
+    acts = synth.actions(5, 1, 6)[:, 0]
+    hard = oracle.Oracle(rom, synth.MAPPER_4K)
+    rams, scrs, _ = hard.rollout(acts, 1)
+    soft = oracle.Oracle(rom, synth.MAPPER_4K)
+    u = synth.action_inputs(acts).astype(np.float64)
+    g, ram_out, scr_out = soft.soft_rollout(u, 1, tau)
+    assert np.array_equal(ram_out, rams.astype(np.float64))
+    assert np.array_equal(scr_out, scrs.astype(np.float64))
+
+
+def _soft_case(tau, n_steps=3, frame_skip=1, mapper=synth.MAPPER_4K, seed=3):
+    rom = _cart(seed, mapper)
+    acts = synth.actions(seed, 1, n_steps)[:, 0]
+    o = oracle.Oracle(rom, mapper)
+    # start from a state a few frames in
+    o.rollout(synth.actions(seed + 1, 1, 2)[:, 0], 1, screens=False)
+    u = synth.action_inputs(acts).astype(np.float64)
+    gr = synth.normal_f32(seed, (n_steps, 128), 1).astype(np.float64)
+    gs = synth.normal_f32(seed, (n_steps, 210, 160), 2).astype(np.float64)
+    g, _, _ = o.soft_rollout(u, frame_skip, tau, 6.0, gr, gs, outputs=False)
+    return g
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.1])
+def test_reverse_equals_tangent(tau):
+    g = _soft_case(tau)
+    g_rom, g_ram0, g_u = g.reverse()
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        d_rom = rng.standard_normal(g.rom_size)
+        d_ram0 = rng.standard_normal(128)
+        d_u = rng.standard_normal((g.n_steps, 5))
+        lhs = float(g_rom @ d_rom + g_ram0 @ d_ram0 + (g_u * d_u).sum())
+        rhs = g.tangent(d_rom, d_ram0, d_u)
+        assert abs(lhs - rhs) <= 1e-9 * max(1.0, abs(lhs)), (lhs, rhs)
+
+
+@pytest.mark.parametrize("tau,mapper", [(1.0, synth.MAPPER_4K), (0.1, synth.MAPPER_4K),
+                                        (0.1, synth.MAPPER_F8), (0.3, synth.MAPPER_2K)])
+def test_reverse_equals_finite_differences(tau, mapper):
+    g = _soft_case(tau, mapper=mapper)
+    g_rom, g_ram0, g_u = g.reverse()
+    h = 1e-4
+    rng = np.random.default_rng(11)
+    idx = np.argsort(-np.abs(g_rom))[:12].tolist() + rng.integers(0, g.rom_size, 4).tolist()
+    for i in idx:
+        d = np.zeros(g.rom_size)
+        d[i] = h
+        fd = (g.eval(d_rom=d) - g.eval(d_rom=-d)) / (2 * h)
+        assert abs(fd - g_rom[i]) <= 1e-6 * max(1.0, abs(g_rom).max()), (i, fd, g_rom[i])
+    for i in np.argsort(-np.abs(g_ram0))[:6]:
+        d = np.zeros(128)
+        d[i] = h
+        fd = (g.eval(d_ram0=d) - g.eval(d_ram0=-d)) / (2 * h)
+        assert abs(fd - g_ram0[i]) <= 1e-6 * max(1.0, abs(g_ram0).max())
+    for t in range(g.n_steps):
+        for k in range(5):
+            d = np.zeros((g.n_steps, 5))
+            d[t, k] = h
+            fd = (g.eval(d_u=d) - g.eval(d_u=-d)) / (2 * h)
+            assert abs(fd - g_u[t, k]) <= 1e-6 * max(1.0, abs(g_u).max())
+    assert np.abs(g_rom).max() > 0 and np.abs(g_u).max() > 0
+
+
+def test_colour_gradient_counts_owned_pixels():
+    """LDA #k; STA COLUP0 with GRP0 = $FF at position 0 and no playfield:
+    each frame has 8 x 210 P0-owned pixels, so d(sum pixels)/d(ROM[imm])
+    is 1680 per frame whose COLUP0 came from that byte."""
+    def build(a):
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x01)
+        a.op("LDA", "imm", 0xFF)
+        a.op("STA", "zp", 0x1B)
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.label("IMM")
+        a.op("LDA", "imm", 0x57)
+        a.op("STA", "zp", 0x06)
+        a.op("LDX", "imm", 0)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("DEX")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "FRAME")
+        imm_addr.append(a.labels["IMM"] + 1)
+    imm_addr = []
+    rom = rom4k(build)
+    o = oracle.Oracle(rom, synth.MAPPER_4K)
+    n = 4
+    u = np.zeros((n, 5))
+    gs = np.ones((n, 210, 160))
+    for tau in (0.01, 1.0):
+        o.reset()
+        g, _, scr = o.soft_rollout(u, 1, tau, 6.0, None, gs)
+        assert (scr[1:] == 0x56).sum() == 3 * 1680
+        g_rom, _, _ = g.reverse()
+        i = imm_addr[0] - 0xF000
+        if tau == 0.01:
+            assert g_rom[i] == pytest.approx(3 * 1680, rel=1e-12)
+            g_rom[i] = 0
+            assert np.abs(g_rom).max() < 1e-20
+        else:
+            # the relaxed read spreads the same total over its window (W = 12)
+            lo, hi = i - 12, i + 12
+            assert g_rom[lo:hi + 1].sum() == pytest.approx(3 * 1680, rel=1e-12)
+            assert g_rom[i] > g_rom[i - 1] > g_rom[i - 2] > 0
+            assert g_rom[i - 1] == pytest.approx(g_rom[i + 1], rel=1e-12)
+            g_rom[lo:hi + 1] = 0
+            assert np.abs(g_rom).max() < 1e-12
