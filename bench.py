@@ -1,0 +1,274 @@
+"""Benchmark: env-steps/s of batched VCS emulation on one B300.
+
+Workload (N = 1): 4096 envs of one seed-generated 4 KB cartridge, frame-skip
+4, per-env uniform random ALE actions, uint8 RAM (128 B) and screen
+(210x160) written for every env at every step.  A "step" is one vcs_step
+over the whole batch (4096 env-steps).  Inputs and state stay resident in
+HBM; each step writes 138 MB of screens, and between timed steps a 256 MB
+buffer is rewritten to flush the 126 MB L2 (outside the timed events).
+
+Prints one JSON line.  `--impl reference` times the CPU oracle on a bounded
+sample of the same workload instead.  Under torchrun each rank runs an
+independent replica on its own GPU (the envs need no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ENVS = 4096
+FRAME_SKIP = 4
+SEED = 2
+METRIC = "env-steps/s per B300 (hard fwd; soft fwd+bwd), bit-exact vs CPU oracle"
+WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+screen per step"
+# algorithmic integer work per env-step (roofline section)
+OPS_PER_INSTRUCTION = 12
+OPS_PER_PIXEL = 6
+PIXELS_PER_STEP = 210 * 160
+INT_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower() in ("active", "1", "yes")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def oracle_sample(n_envs: int, n_steps: int, threads: int):
+    """CPU oracle over a bounded sample of the workload (one env per task,
+    ctypes releases the GIL so threads run in parallel).  Returns
+    (env-steps, seconds, instructions per env-step)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_2606_22447_b300 import synth
+    rom = synth.generate_cart(SEED, 0, synth.MAPPER_4K)
+    acts = synth.actions(SEED, n_envs, n_steps)
+    oracle.lib()
+
+    def run(e):
+        o = oracle.Oracle(rom, synth.MAPPER_4K)
+        for t in range(n_steps):
+            o.step(int(acts[t, e]), FRAME_SKIP)
+        return o.counters()["instructions"]
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        instr = list(ex.map(run, range(n_envs)))
+    dt = time.perf_counter() - t0
+    return n_envs * n_steps, dt, sum(instr) / (n_envs * n_steps)
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    steps = []
+    n_envs = 2 * cores
+    for _ in range(args.warmup):
+        oracle_sample(cores, 1, cores)
+    for _ in range(args.steps):
+        es, dt, _ = oracle_sample(n_envs, 4, cores)
+        steps.append((es, dt))
+    es = sum(s[0] for s in steps)
+    dt = sum(s[1] for s in steps)
+    value = es / dt
+    sample = f"{n_envs} envs x 4 env-steps per step of the same workload (frame-skip 4, RAM+screen per step)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_envs": n_envs, "frame_skip": FRAME_SKIP, "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def gpu_arm(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # CPU baseline first (bounded sample, all host cores), rank 0 at N = 1
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        es, dt, ipe = oracle_sample(4 * cores, 8, cores)
+        cpu = {"value": es / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{4 * cores} envs x 8 env-steps of the workload (frame-skip 4), {ipe:.0f} instr/env-step"}
+
+    from paper_2606_22447_b300 import Batch, build, default_config, synth
+    build.build()
+    rom = synth.generate_cart(SEED, 0, synth.MAPPER_4K)
+    n = args.envs
+    batch = Batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32), default_config())
+    total_steps = args.warmup + args.steps
+    acts = torch.from_numpy(synth.actions(SEED + rank, n, total_steps)).cuda()
+    ram = torch.empty((n, 128), dtype=torch.uint8, device="cuda")
+    scr = torch.empty((n, 210, 160), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for t in range(args.warmup):
+        batch.step(acts[t], FRAME_SKIP, ram, scr)
+    batch.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            batch.step(acts[args.warmup + k], FRAME_SKIP, ram, scr)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    batch.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    elapsed = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    value = world * n * args.steps / elapsed
+
+    # end to end through the host-pointer entry point (pinned host buffers)
+    a_h = torch.empty((n,), dtype=torch.uint8).pin_memory().numpy()
+    ram_h = torch.empty((n, 128), dtype=torch.uint8).pin_memory().numpy()
+    scr_h = torch.empty((n, 210, 160), dtype=torch.uint8).pin_memory().numpy()
+    acts_h = synth.actions(SEED + 7, n, args.steps)
+    batch.step_host(acts_h[0], FRAME_SKIP, ram_h, scr_h)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        a_h[:] = acts_h[k]
+        batch.step_host(a_h, FRAME_SKIP, ram_h, scr_h)
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": n * args.steps / e2e_dt, "unit": "env-steps/s", "h2d_bytes_per_step": n,
+           "d2h_bytes_per_step": n * (128 + 210 * 160)}
+
+    # roofline: algorithmic integer work of one launch / mean launch time
+    ipe = args.instr_per_step
+    if ipe is None:
+        import oracle
+        o = oracle.Oracle(rom, synth.MAPPER_4K)
+        for t in range(8):
+            o.step(int(synth.actions(SEED, 1, 8)[t, 0]), FRAME_SKIP)
+        ipe = o.counters()["instructions"] / 8
+    ops = n * (ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL)
+    mean_s = elapsed / args.steps
+    props = torch.cuda.get_device_properties(local)
+    peaks = _peaks()
+    clk = clocks.summary()
+    max_mhz = peaks.get("sm_max_mhz") or clk["sm_max_mhz"] or 2032.0
+    peak_ops = props.multi_processor_count * INT_LANES_PER_SM * max_mhz * 1e6
+    roofline = {"bound": "alu", "achieved": ops / mean_s / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": ops / mean_s / peak_ops, "traffic": None,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x {INT_LANES_PER_SM} int lanes x "
+                               f"{max_mhz:.0f} MHz (measured max clock)",
+                "ops_per_env_step": ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL,
+                "instructions_per_env_step": ipe,
+                "hbm_gbs_written": n * (128 + PIXELS_PER_STEP) / mean_s / 1e9}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_envs": n, "frame_skip": FRAME_SKIP, "seed": SEED,
+                       "envs_per_block": batch.envs_per_block,
+                       "l2": "256 MB flush between timed steps (outside the events)",
+                       "frames_per_s": value * FRAME_SKIP, "instructions_per_s": value * ipe,
+                       "parallelism": f"replicas x{world}"},
+            "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=N_ENVS)
+    ap.add_argument("--instr-per-step", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

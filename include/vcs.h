@@ -1,0 +1,161 @@
+/*
+ * libvcs: batched Atari VCS emulation on one GPU (sm_103a), hard and soft.
+ *
+ * The machine is the paper's VCS (Section 2.2, the architecture figure): a
+ * 6507 CPU executing a cartridge ROM (2K, 4K or F8 bank-switched), the RIOT
+ * (128 B of RAM, interval timer, joystick and console-switch ports) and the
+ * TIA, which turns register writes into 160x210 palette-index frames one
+ * colour clock at a time.  Many independent machines run in lockstep, one
+ * per CUDA thread.
+ *
+ * Modes (supplement, table of execution modes):
+ *  - HARD: bit-exact integer emulation (vcs_step, vcs_rollout);
+ *  - SOFT-STE: the same forward pass, bit-exact with HARD at every finite
+ *    temperature (Theorem 1), plus a hand-written backward pass giving
+ *    surrogate gradients (Corollary 1) with respect to ROM bytes, the RAM
+ *    at the start of the rollout and the per-step joystick inputs.
+ *
+ * Conventions
+ *  - Every call returns a vcs_status; 0 is success.  No C++ exception
+ *    crosses this interface.  vcs_last_error() describes the last failure
+ *    of a batch in words.
+ *  - "device pointer" arguments are CUDA device addresses owned by the
+ *    caller (for instance PyTorch tensors) and must stay valid until the
+ *    work queued on `stream` has finished.  "host pointer" arguments are
+ *    read or written before the call returns.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy stream.
+ *  - The library owns the machine state, its ROM copies, checkpoints and
+ *    tapes.  ROMs are copied at creation, so the caller may free them.
+ *  - One batch must not be used from two host threads or streams at once.
+ *  - Env order is the caller's: output row e always belongs to env e.
+ */
+#ifndef VCS_H
+#define VCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VCS_OK = 0,
+  VCS_ERR_ARG = 1,       /* bad argument (null pointer, size, range) */
+  VCS_ERR_ROM_SIZE = 2,  /* ROM size does not match its mapper */
+  VCS_ERR_MAPPER = 3,    /* unknown mapper code */
+  VCS_ERR_CUDA = 4,      /* a CUDA call failed; see vcs_last_error */
+  VCS_ERR_OOM = 5,       /* device allocation failed */
+  VCS_ERR_WATCHDOG = 6,  /* a device wait gave up (the batch is unusable) */
+  VCS_ERR_STATE = 7      /* call out of order (e.g. backward of a freed tape) */
+} vcs_status;
+
+/* Cartridge mappers (the 2K, 4K and F8 formats of the paper's per-game
+ * conformance table, supplement).  F8 = 8 KB in two 4 KB banks, selected by
+ * any access to $1FF8 (bank 0) or $1FF9 (bank 1); power-on selects bank 1. */
+enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2 };
+
+/* Per-env status bits reported by vcs_step / vcs_rollout. */
+enum {
+  VCS_ENV_WATCHDOG = 1,  /* a frame was ended by the 512-scanline cap */
+  VCS_ENV_JAMMED = 2,    /* the CPU met an undocumented opcode and halted */
+  VCS_ENV_DONE = 4       /* the episode ended at this step (auto-reset) */
+};
+
+#define VCS_SCREEN_H 210
+#define VCS_SCREEN_W 160
+#define VCS_RAM 128
+#define VCS_ROM_MAX 8192
+
+typedef struct vcs_config {
+  float alpha;              /* branch-gate sharpness (Eq. branch), default 6 */
+  int32_t ystart;           /* first scanline of screen row 0, default 34 */
+  int32_t boot_noop_frames; /* NOOP frames run by vcs_reset, default 0 */
+  int32_t envs_per_block;   /* 0 = automatic; else 8, 16, 32, 64 or 128 */
+  int32_t segment_frames;   /* soft checkpoint interval in frames, default 64 */
+} vcs_config;
+
+typedef struct vcs_batch vcs_batch;
+
+/* Fill *cfg with the defaults listed above. */
+vcs_status vcs_config_default(vcs_config* cfg);
+
+/* Create a batch of n_envs machines over n_carts cartridges (Section 2.2;
+ * "ROM as a weight tensor", Section 3.1).
+ *  roms[c]      host pointer to cart c's image (rom_sizes[c] bytes: 2048,
+ *               4096 or 8192 for mapper 2K, 4K, F8); copied.
+ *  mappers[c]   VCS_MAPPER_* of cart c.
+ *  env_cart     host int32[n_envs]: the cart of each env (0..n_carts-1).
+ *  cfg          nullable (defaults).
+ * The machines start in the power-on state (vcs_reset semantics).
+ * Errors: VCS_ERR_ARG, _ROM_SIZE, _MAPPER, _OOM, _CUDA.  On error *out is
+ * NULL and nothing is leaked. */
+vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_sizes,
+                            const uint8_t* mappers, int32_t n_carts,
+                            const int32_t* env_cart, int32_t n_envs,
+                            const vcs_config* cfg, vcs_batch** out);
+vcs_status vcs_destroy(vcs_batch* b);
+/* Human-readable description of the last error of `b` (or of the last
+ * failed vcs_create_batch when b is NULL).  Valid until the next call. */
+const char* vcs_last_error(const vcs_batch* b);
+vcs_status vcs_batch_info(const vcs_batch* b, int32_t* n_envs, int32_t* n_carts,
+                          int32_t* envs_per_block);
+
+/* Per-env episode lengths in frames for auto-reset: ep_len is a host
+ * uint32[n_envs][n_episodes]; env e's k-th episode ends at the end of the
+ * step in which its frame count reaches ep_len[e][k mod n_episodes]; the env
+ * then returns to the power-on state and reports VCS_ENV_DONE for that step.
+ * n_episodes = 0 disables auto-reset (the default).  The paper's protocol
+ * restarts games between episodes (Section 5); lengths are the caller's. */
+vcs_status vcs_set_episodes(vcs_batch* b, const uint32_t* ep_len, int32_t n_episodes);
+
+/* Power-on state (A=X=Y=0, SP=$FD, P=$34, PC from the reset vector, RAM
+ * and TIA registers zero, timer as written with 0 at T1024T, F8 bank 1),
+ * then cfg.boot_noop_frames frames with the NOOP action (the paper boots
+ * with NOOP frames, supplement settings table).
+ * env_mask: device uint8[n_envs] (nonzero = reset) or NULL for all. */
+vcs_status vcs_reset(vcs_batch* b, const uint8_t* env_mask, void* stream);
+
+/* One env-step for every env (the paper's conformance protocol, Section 5):
+ * set each joystick from actions[e] (device uint8[n_envs], ALE action index
+ * 0..17), run frame_skip >= 1 frames (a frame ends at the VSYNC write that
+ * sets D1, or after 512 scanlines), then write
+ *   ram_out     device uint8[n_envs][128]       (nullable)
+ *   screen_out  device uint8[n_envs][210][160]  (nullable) the last frame
+ *   status_out  device uint8[n_envs]            (nullable) VCS_ENV_* bits
+ * Pixel = colour register & 0xFE; row r is scanline ystart + r. */
+vcs_status vcs_step(vcs_batch* b, const uint8_t* actions, int32_t frame_skip,
+                    uint8_t* ram_out, uint8_t* screen_out, uint8_t* status_out,
+                    void* stream);
+
+/* n_steps env-steps in one launch: actions device uint8[n_steps][n_envs];
+ * ram_out [n_steps][n_envs][128], screen_out [n_steps][n_envs][210][160],
+ * status_out [n_steps][n_envs] (all nullable).  Equivalent to n_steps calls
+ * of vcs_step. */
+vcs_status vcs_rollout(vcs_batch* b, const uint8_t* actions, int32_t n_steps,
+                       int32_t frame_skip, uint8_t* ram_out, uint8_t* screen_out,
+                       uint8_t* status_out, void* stream);
+
+/* vcs_step through host memory: actions_host uint8[n_envs] is copied to
+ * the device, the step runs, and ram_out_host / screen_out_host (nullable,
+ * host) are filled before the call returns (the stream is synchronised).
+ * The library allocates its device staging buffers on the first call. */
+vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t frame_skip,
+                         uint8_t* ram_out_host, uint8_t* screen_out_host, void* stream);
+
+/* Wait for `stream` and report device-side failures: VCS_ERR_WATCHDOG if a
+ * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA
+ * for an asynchronous CUDA error. */
+vcs_status vcs_sync(vcs_batch* b, void* stream);
+
+/* Copy the machine state out / in as an opaque blob (checkpoint/resume).
+ * vcs_state_bytes gives the size; blob is a host pointer; both calls
+ * synchronise `stream`. */
+vcs_status vcs_state_bytes(const vcs_batch* b, size_t* bytes);
+vcs_status vcs_save_state(vcs_batch* b, void* blob_host, void* stream);
+vcs_status vcs_load_state(vcs_batch* b, const void* blob_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,133 @@
+"""B300-native batched Atari VCS emulation (hard and SOFT-STE modes).
+
+The emulation itself runs in libvcs.so (CUDA for sm_103a, C ABI declared in
+include/vcs.h).  This package holds the thin Python binding over that ABI,
+the PyTorch-facing wrappers (device memory and streams only) and the seeded
+synthetic-input generator.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import ENV_DONE, ENV_JAMMED, ENV_WATCHDOG, Config, VcsError
+from .synth import MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_SIZE
+
+SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
+
+__all__ = ["Batch", "Config", "VcsError", "default_config", "MAPPER_2K", "MAPPER_4K", "MAPPER_F8",
+           "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
+
+
+def default_config(**overrides) -> Config:
+    cfg = Config()
+    _lib.check(_lib.load().vcs_config_default(C.byref(cfg)))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(t):
+    """Device address of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Batch:
+    """A batch of n_envs VCS machines over a list of cartridges.
+
+    roms: list of bytes; mappers: list of MAPPER_* codes; env_cart: int array
+    [n_envs] giving each env's cart.  Device buffers passed to the methods are
+    torch CUDA tensors owned by the caller.
+    """
+
+    def __init__(self, roms, mappers, env_cart, config: Config | None = None):
+        L = _lib.load()
+        self.n_carts = len(roms)
+        self._roms = [np.frombuffer(bytes(r), dtype=np.uint8).copy() for r in roms]
+        ptrs = (_lib.u8p * self.n_carts)(*[r.ctypes.data_as(_lib.u8p) for r in self._roms])
+        sizes = (C.c_uint32 * self.n_carts)(*[len(r) for r in self._roms])
+        maps = np.ascontiguousarray(mappers, dtype=np.uint8)
+        ec = np.ascontiguousarray(env_cart, dtype=np.int32)
+        self.n_envs = int(ec.shape[0])
+        self.mappers = [int(m) for m in maps]
+        self.env_cart = ec.copy()
+        h = C.c_void_p()
+        cfg = config if config is not None else default_config()
+        st = L.vcs_create_batch(ptrs, sizes, maps.ctypes.data_as(_lib.u8p), self.n_carts,
+                                ec.ctypes.data_as(C.POINTER(C.c_int32)), self.n_envs, C.byref(cfg), C.byref(h))
+        _lib.check(st, None)
+        self.h = h
+        self.config = cfg
+        epb = C.c_int32()
+        L.vcs_batch_info(self.h, None, None, C.byref(epb))
+        self.envs_per_block = epb.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().vcs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        _lib.check(st, self.h)
+
+    def reset(self, env_mask=None, stream=None):
+        self._check(_lib.load().vcs_reset(self.h, _ptr(env_mask), _stream(stream)))
+
+    def set_episodes(self, ep_len):
+        ep = np.ascontiguousarray(ep_len, dtype=np.uint32)
+        n_ep = 0 if ep.size == 0 else int(ep.shape[1])
+        self._check(_lib.load().vcs_set_episodes(self.h, ep.ctypes.data_as(C.POINTER(C.c_uint32)), n_ep))
+
+    def step(self, actions, frame_skip: int, ram_out=None, screen_out=None, status_out=None, stream=None):
+        self._check(_lib.load().vcs_step(self.h, _ptr(actions), frame_skip, _ptr(ram_out), _ptr(screen_out),
+                                         _ptr(status_out), _stream(stream)))
+
+    def rollout(self, actions, frame_skip: int, ram_out=None, screen_out=None, status_out=None, stream=None):
+        n_steps = int(actions.shape[0])
+        self._check(_lib.load().vcs_rollout(self.h, _ptr(actions), n_steps, frame_skip, _ptr(ram_out),
+                                            _ptr(screen_out), _ptr(status_out), _stream(stream)))
+
+    def step_host(self, actions: np.ndarray, frame_skip: int, ram_out=None, screen_out=None, stream=None):
+        a = np.ascontiguousarray(actions, dtype=np.uint8)
+        p = lambda x: None if x is None else C.c_void_p(x.ctypes.data)
+        self._check(_lib.load().vcs_step_host(self.h, C.c_void_p(a.ctypes.data), frame_skip, p(ram_out),
+                                              p(screen_out), _stream(stream)))
+
+    def sync(self, stream=None):
+        self._check(_lib.load().vcs_sync(self.h, _stream(stream)))
+
+    def state_bytes(self) -> int:
+        n = C.c_size_t()
+        self._check(_lib.load().vcs_state_bytes(self.h, C.byref(n)))
+        return n.value
+
+    def save_state(self, stream=None) -> np.ndarray:
+        blob = np.zeros(self.state_bytes(), np.uint8)
+        self._check(_lib.load().vcs_save_state(self.h, C.c_void_p(blob.ctypes.data), _stream(stream)))
+        return blob
+
+    def load_state(self, blob: np.ndarray, stream=None):
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        if b.size != self.state_bytes():
+            raise ValueError("state blob size mismatch")
+        self._check(_lib.load().vcs_load_state(self.h, C.c_void_p(b.ctypes.data), _stream(stream)))

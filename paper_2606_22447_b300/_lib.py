@@ -1,0 +1,77 @@
+"""ctypes binding of libvcs (include/vcs.h).
+
+Argument marshalling only: every step of the emulation runs in the library's
+CUDA kernels.  The library is loaded from this package's directory; if it is
+missing the import of this module fails loudly (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvcs.so")
+
+VCS_OK, VCS_ERR_ARG, VCS_ERR_ROM_SIZE, VCS_ERR_MAPPER = 0, 1, 2, 3
+VCS_ERR_CUDA, VCS_ERR_OOM, VCS_ERR_WATCHDOG, VCS_ERR_STATE = 4, 5, 6, 7
+STATUS_NAMES = {0: "VCS_OK", 1: "VCS_ERR_ARG", 2: "VCS_ERR_ROM_SIZE", 3: "VCS_ERR_MAPPER",
+                4: "VCS_ERR_CUDA", 5: "VCS_ERR_OOM", 6: "VCS_ERR_WATCHDOG", 7: "VCS_ERR_STATE"}
+ENV_WATCHDOG, ENV_JAMMED, ENV_DONE = 1, 2, 4
+
+
+class VcsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("alpha", C.c_float), ("ystart", C.c_int32), ("boot_noop_frames", C.c_int32),
+                ("envs_per_block", C.c_int32), ("segment_frames", C.c_int32)]
+
+
+vp = C.c_void_p
+i32 = C.c_int32
+u8p = C.POINTER(C.c_uint8)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "vcs_config_default": (C.c_int, [C.POINTER(Config)]),
+    "vcs_create_batch": (C.c_int, [C.POINTER(u8p), C.POINTER(C.c_uint32), u8p, i32,
+                                   C.POINTER(C.c_int32), i32, C.POINTER(Config), C.POINTER(vp)]),
+    "vcs_destroy": (C.c_int, [vp]),
+    "vcs_last_error": (C.c_char_p, [vp]),
+    "vcs_batch_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    "vcs_set_episodes": (C.c_int, [vp, C.POINTER(C.c_uint32), i32]),
+    "vcs_reset": (C.c_int, [vp, vp, vp]),
+    "vcs_step": (C.c_int, [vp, vp, i32, vp, vp, vp, vp]),
+    "vcs_rollout": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, vp]),
+    "vcs_step_host": (C.c_int, [vp, vp, i32, vp, vp, vp]),
+    "vcs_sync": (C.c_int, [vp, vp]),
+    "vcs_state_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+    "vcs_save_state": (C.c_int, [vp, vp, vp]),
+    "vcs_load_state": (C.c_int, [vp, vp, vp]),
+}
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libvcs.so from the package directory (raises if absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libvcs.so is not built ({LIB_PATH}); run paper_2606_22447_b300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(status: int, handle=None):
+    if status != VCS_OK:
+        msg = load().vcs_last_error(handle)
+        raise VcsError(status, msg.decode() if msg else "")

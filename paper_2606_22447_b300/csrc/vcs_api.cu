@@ -1,0 +1,353 @@
+// C ABI of libvcs (include/vcs.h): batch set-up, memory ownership and launch
+// of the hard-mode kernels.  No exception crosses the interface; every entry
+// point returns a vcs_status and records a message for vcs_last_error.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/vcs.h"
+#include "vcs_api_internal.h"
+
+using namespace vcs;
+
+static thread_local std::string g_create_error;
+
+vcs_status vcs_fail(vcs_batch* b, vcs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (b)
+    b->last_error = buf;
+  else
+    g_create_error = buf;
+  return st;
+}
+
+vcs_status vcs_cuda_fail(vcs_batch* b, cudaError_t e, const char* what) {
+  return vcs_fail(b, e == cudaErrorMemoryAllocation ? VCS_ERR_OOM : VCS_ERR_CUDA, "%s: %s", what,
+                  cudaGetErrorString(e));
+}
+
+SoA vcs_batch::soa() const { return soa_of(state, n_envs); }
+
+SoA vcs::soa_of(uint32_t* state, int32_t n_envs) {
+  SoA s;
+  const size_t n = (size_t)n_envs;
+  uint32_t** f[kSoAFields] = {&s.reg, &s.pcp, &s.cyc, &s.fcs, &s.tw, &s.tv,
+                              &s.t0, &s.t1, &s.t2, &s.t3, &s.epf, &s.epi};
+  for (int i = 0; i < kSoAFields; i++) *f[i] = state + i * n;
+  s.ram = state + kSoAFields * n;
+  return s;
+}
+
+static int pick_envs_per_block(int n_envs, int sms) {
+  // enough blocks to cover every SM twice, blocks of 8..128 envs
+  int e = 128;
+  while (e > 8 && (n_envs + e - 1) / e < 2 * sms) e /= 2;
+  return e;
+}
+
+StepParams vcs_base_params(vcs_batch* b) {
+  StepParams p{};
+  p.s = b->soa();
+  p.n_envs = b->n_envs;
+  p.blocks = b->blocks;
+  p.perm = b->perm;
+  p.roms = b->roms;
+  p.cart_f8 = b->cart_f8;
+  p.dt = b->dt;
+  p.ystart = b->cfg.ystart;
+  p.err = b->err;
+  return p;
+}
+
+static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
+  int e = launch_step(p, b->n_blocks, b->E, stream);
+  if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
+  return VCS_OK;
+}
+
+static void free_batch(vcs_batch* b) {
+  if (!b) return;
+  cudaFree(b->state);
+  cudaFree(b->roms);
+  cudaFree(b->cart_f8);
+  cudaFree(b->dt);
+  cudaFree(b->blocks);
+  cudaFree(b->perm);
+  cudaFree(b->ep_len);
+  cudaFree(b->err);
+  cudaFree(b->h_actions);
+  cudaFree(b->h_ram);
+  cudaFree(b->h_screen);
+  delete b;
+}
+
+extern "C" {
+
+vcs_status vcs_config_default(vcs_config* cfg) {
+  if (!cfg) return VCS_ERR_ARG;
+  cfg->alpha = 6.0f;
+  cfg->ystart = 34;
+  cfg->boot_noop_frames = 0;
+  cfg->envs_per_block = 0;
+  cfg->segment_frames = 64;
+  return VCS_OK;
+}
+
+const char* vcs_last_error(const vcs_batch* b) { return b ? b->last_error.c_str() : g_create_error.c_str(); }
+
+vcs_status vcs_batch_info(const vcs_batch* b, int32_t* n_envs, int32_t* n_carts, int32_t* epb) {
+  if (!b) return VCS_ERR_ARG;
+  if (n_envs) *n_envs = b->n_envs;
+  if (n_carts) *n_carts = b->n_carts;
+  if (epb) *epb = b->E;
+  return VCS_OK;
+}
+
+vcs_status vcs_destroy(vcs_batch* b) {
+  if (!b) return VCS_ERR_ARG;
+  free_batch(b);
+  return VCS_OK;
+}
+
+vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_sizes, const uint8_t* mappers,
+                            int32_t n_carts, const int32_t* env_cart, int32_t n_envs, const vcs_config* cfg,
+                            vcs_batch** out) {
+  if (!out) return vcs_fail(nullptr, VCS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!roms || !rom_sizes || !mappers || !env_cart)
+    return vcs_fail(nullptr, VCS_ERR_ARG, "null roms / rom_sizes / mappers / env_cart");
+  if (n_carts <= 0 || n_envs <= 0) return vcs_fail(nullptr, VCS_ERR_ARG, "n_carts and n_envs must be positive");
+  static const uint32_t want[3] = {2048, 4096, 8192};
+  for (int c = 0; c < n_carts; c++) {
+    if (mappers[c] > VCS_MAPPER_F8)
+      return vcs_fail(nullptr, VCS_ERR_MAPPER, "cart %d: unknown mapper %d", c, mappers[c]);
+    if (rom_sizes[c] != want[mappers[c]])
+      return vcs_fail(nullptr, VCS_ERR_ROM_SIZE, "cart %d: %u bytes for mapper %d (want %u)", c, rom_sizes[c],
+                      mappers[c], want[mappers[c]]);
+    if (!roms[c]) return vcs_fail(nullptr, VCS_ERR_ARG, "cart %d: null ROM", c);
+  }
+  for (int e = 0; e < n_envs; e++)
+    if (env_cart[e] < 0 || env_cart[e] >= n_carts)
+      return vcs_fail(nullptr, VCS_ERR_ARG, "env %d: cart %d out of range", e, env_cart[e]);
+
+  vcs_batch* b = new (std::nothrow) vcs_batch;
+  if (!b) return vcs_fail(nullptr, VCS_ERR_OOM, "host allocation failed");
+  if (cfg)
+    b->cfg = *cfg;
+  else
+    vcs_config_default(&b->cfg);
+  if (b->cfg.ystart < 0 || b->cfg.ystart > 400 || b->cfg.boot_noop_frames < 0 || b->cfg.segment_frames < 1) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "config out of range (ystart 0..400, boot frames >= 0, segment >= 1)");
+  }
+  b->n_envs = n_envs;
+  b->n_carts = n_carts;
+  b->env_cart.assign(env_cart, env_cart + n_envs);
+  b->mapper.assign(mappers, mappers + n_carts);
+  b->rom_size.assign(rom_sizes, rom_sizes + n_carts);
+
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->sms = sms;
+  int E = b->cfg.envs_per_block;
+  if (E == 0) E = pick_envs_per_block(n_envs, sms);
+  if (E != 8 && E != 16 && E != 32 && E != 64 && E != 128) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "envs_per_block must be 0, 8, 16, 32, 64 or 128");
+  }
+  b->E = E;
+
+  // device images: 2K mirrored into 4 KB, F8 as two banks
+  std::vector<uint8_t> img((size_t)n_carts * 8192, 0);
+  std::vector<uint8_t> f8(n_carts);
+  for (int c = 0; c < n_carts; c++) {
+    uint8_t* d = img.data() + (size_t)c * 8192;
+    if (mappers[c] == VCS_MAPPER_2K) {
+      memcpy(d, roms[c], 2048);
+      memcpy(d + 2048, roms[c], 2048);
+    } else {
+      memcpy(d, roms[c], rom_sizes[c]);
+    }
+    f8[c] = mappers[c] == VCS_MAPPER_F8;
+  }
+  // group envs by cart (stable), cut each cart's run into blocks of E
+  std::vector<int32_t> perm(n_envs);
+  for (int e = 0; e < n_envs; e++) perm[e] = e;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int c) { return env_cart[a] < env_cart[c]; });
+  std::vector<int4> blocks;
+  for (int i = 0; i < n_envs;) {
+    int c = env_cart[perm[i]];
+    int j = i;
+    while (j < n_envs && env_cart[perm[j]] == c && j - i < E) j++;
+    blocks.push_back(make_int4(c, i, j - i, 0));
+    i = j;
+  }
+  b->n_blocks = (int)blocks.size();
+  b->perm_host = perm;
+  DecodeTables dt;
+  build_decode_tables(&dt);
+
+  cudaError_t e;
+  const size_t nst = (size_t)kStateWords * n_envs * sizeof(uint32_t);
+  if ((e = cudaMalloc(&b->state, nst)) || (e = cudaMalloc(&b->roms, img.size())) ||
+      (e = cudaMalloc(&b->cart_f8, n_carts)) || (e = cudaMalloc(&b->dt, sizeof(DecodeTables))) ||
+      (e = cudaMalloc(&b->blocks, blocks.size() * sizeof(int4))) ||
+      (e = cudaMalloc(&b->perm, n_envs * sizeof(int32_t))) || (e = cudaMalloc(&b->err, sizeof(int32_t)))) {
+    vcs_status st = vcs_cuda_fail(nullptr, e, "device allocation");
+    free_batch(b);
+    return st;
+  }
+  if ((e = cudaMemcpy(b->roms, img.data(), img.size(), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->cart_f8, f8.data(), n_carts, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dt, &dt, sizeof dt, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->blocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->perm, perm.data(), n_envs * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemset(b->err, 0, sizeof(int32_t))) || (e = cudaMemset(b->state, 0, nst))) {
+    vcs_status st = vcs_cuda_fail(nullptr, e, "device upload");
+    free_batch(b);
+    return st;
+  }
+  // power on every env (plus the configured boot frames)
+  StepParams p = vcs_base_params(b);
+  p.reset_all = 1;
+  p.n_steps = b->cfg.boot_noop_frames;
+  p.frame_skip = 1;
+  vcs_status st = launch(b, p, nullptr);
+  if (st == VCS_OK && (e = cudaDeviceSynchronize())) st = vcs_cuda_fail(b, e, "power-on");
+  if (st != VCS_OK) {
+    g_create_error = b->last_error;
+    free_batch(b);
+    return st;
+  }
+  *out = b;
+  return VCS_OK;
+}
+
+vcs_status vcs_set_episodes(vcs_batch* b, const uint32_t* ep_len, int32_t n_episodes) {
+  if (!b) return VCS_ERR_ARG;
+  if (n_episodes < 0 || (n_episodes > 0 && !ep_len)) return vcs_fail(b, VCS_ERR_ARG, "bad episode table");
+  cudaFree(b->ep_len);
+  b->ep_len = nullptr;
+  b->n_episodes = 0;
+  if (n_episodes == 0) return VCS_OK;
+  size_t bytes = (size_t)b->n_envs * n_episodes * sizeof(uint32_t);
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->ep_len, bytes))) return vcs_cuda_fail(b, e, "episode table");
+  if ((e = cudaMemcpy(b->ep_len, ep_len, bytes, cudaMemcpyHostToDevice))) return vcs_cuda_fail(b, e, "episode table");
+  b->n_episodes = n_episodes;
+  return VCS_OK;
+}
+
+vcs_status vcs_reset(vcs_batch* b, const uint8_t* env_mask, void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  StepParams p = vcs_base_params(b);
+  p.reset_all = env_mask ? 0 : 1;
+  p.reset_mask = env_mask;
+  p.n_steps = b->cfg.boot_noop_frames;
+  p.frame_skip = 1;
+  vcs_status st = launch(b, p, stream);
+  if (st != VCS_OK) return st;
+  if (!env_mask) {   // fresh episodes
+    SoA s = b->soa();
+    cudaMemsetAsync(s.epf, 0, b->n_envs * sizeof(uint32_t), (cudaStream_t)stream);
+    cudaMemsetAsync(s.epi, 0, b->n_envs * sizeof(uint32_t), (cudaStream_t)stream);
+  }
+  return VCS_OK;
+}
+
+vcs_status vcs_rollout(vcs_batch* b, const uint8_t* actions, int32_t n_steps, int32_t frame_skip,
+                       uint8_t* ram_out, uint8_t* screen_out, uint8_t* status_out, void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  if (!actions) return vcs_fail(b, VCS_ERR_ARG, "actions is NULL");
+  if (n_steps < 0 || frame_skip < 1) return vcs_fail(b, VCS_ERR_ARG, "n_steps >= 0 and frame_skip >= 1 required");
+  StepParams p = vcs_base_params(b);
+  p.actions = actions;
+  p.n_steps = n_steps;
+  p.frame_skip = frame_skip;
+  p.ram_out = ram_out;
+  p.screen_out = screen_out;
+  p.status_out = status_out;
+  p.ep_len = b->ep_len;
+  p.n_episodes = b->n_episodes;
+  return launch(b, p, stream);
+}
+
+vcs_status vcs_step(vcs_batch* b, const uint8_t* actions, int32_t frame_skip, uint8_t* ram_out,
+                    uint8_t* screen_out, uint8_t* status_out, void* stream) {
+  return vcs_rollout(b, actions, 1, frame_skip, ram_out, screen_out, status_out, stream);
+}
+
+vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t frame_skip, uint8_t* ram_out_host,
+                         uint8_t* screen_out_host, void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  if (!actions_host) return vcs_fail(b, VCS_ERR_ARG, "actions_host is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const size_t n = (size_t)b->n_envs;
+  if (!b->h_actions) {
+    if ((e = cudaMalloc(&b->h_actions, n)) || (e = cudaMalloc(&b->h_ram, n * 128)) ||
+        (e = cudaMalloc(&b->h_screen, n * kScreenH * kScreenW)))
+      return vcs_cuda_fail(b, e, "staging buffers");
+  }
+  if ((e = cudaMemcpyAsync(b->h_actions, actions_host, n, cudaMemcpyHostToDevice, s)))
+    return vcs_cuda_fail(b, e, "actions upload");
+  vcs_status st = vcs_step(b, b->h_actions, frame_skip, ram_out_host ? b->h_ram : nullptr,
+                           screen_out_host ? b->h_screen : nullptr, nullptr, stream);
+  if (st != VCS_OK) return st;
+  if (ram_out_host && (e = cudaMemcpyAsync(ram_out_host, b->h_ram, n * 128, cudaMemcpyDeviceToHost, s)))
+    return vcs_cuda_fail(b, e, "RAM download");
+  if (screen_out_host &&
+      (e = cudaMemcpyAsync(screen_out_host, b->h_screen, n * kScreenH * kScreenW, cudaMemcpyDeviceToHost, s)))
+    return vcs_cuda_fail(b, e, "screen download");
+  if ((e = cudaStreamSynchronize(s))) return vcs_cuda_fail(b, e, "step");
+  return VCS_OK;
+}
+
+vcs_status vcs_state_bytes(const vcs_batch* b, size_t* bytes) {
+  if (!b || !bytes) return VCS_ERR_ARG;
+  *bytes = (size_t)kStateWords * b->n_envs * sizeof(uint32_t);
+  return VCS_OK;
+}
+
+vcs_status vcs_save_state(vcs_batch* b, void* blob_host, void* stream) {
+  if (!b || !blob_host) return VCS_ERR_ARG;
+  size_t bytes = (size_t)kStateWords * b->n_envs * sizeof(uint32_t);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(blob_host, b->state, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream)) ||
+      (e = cudaStreamSynchronize((cudaStream_t)stream)))
+    return vcs_cuda_fail(b, e, "save state");
+  return VCS_OK;
+}
+
+vcs_status vcs_load_state(vcs_batch* b, const void* blob_host, void* stream) {
+  if (!b || !blob_host) return VCS_ERR_ARG;
+  size_t bytes = (size_t)kStateWords * b->n_envs * sizeof(uint32_t);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b->state, blob_host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream)) ||
+      (e = cudaStreamSynchronize((cudaStream_t)stream)))
+    return vcs_cuda_fail(b, e, "load state");
+  return VCS_OK;
+}
+
+vcs_status vcs_sync(vcs_batch* b, void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e) return vcs_cuda_fail(b, e, "synchronize");
+  int32_t err = 0;
+  if ((e = cudaMemcpy(&err, b->err, sizeof err, cudaMemcpyDeviceToHost))) return vcs_cuda_fail(b, e, "error word");
+  if (err) return vcs_fail(b, VCS_ERR_WATCHDOG, "a device wait gave up (code %d); batch unusable", err);
+  return VCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,41 @@
+// Host-side batch object shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vcs.h"
+#include "vcs_kernels.cuh"
+
+struct vcs_batch {
+  int32_t n_envs = 0, n_carts = 0, E = 32, n_blocks = 0, sms = 148;
+  vcs_config cfg{};
+  std::vector<int32_t> env_cart, perm_host;
+  std::vector<uint8_t> mapper;
+  std::vector<uint32_t> rom_size;
+  // device memory owned by the batch
+  uint32_t* state = nullptr;      // kStateWords x n_envs
+  uint8_t* roms = nullptr;        // n_carts x 8192
+  uint8_t* cart_f8 = nullptr;
+  vcs::DecodeTables* dt = nullptr;
+  int4* blocks = nullptr;
+  int32_t* perm = nullptr;
+  uint32_t* ep_len = nullptr;
+  int32_t n_episodes = 0;
+  int32_t* err = nullptr;
+  // staging for the host-pointer entry point
+  uint8_t* h_actions = nullptr;
+  uint8_t* h_ram = nullptr;
+  uint8_t* h_screen = nullptr;
+  std::string last_error;
+  vcs::SoA soa() const;
+};
+
+namespace vcs {
+SoA soa_of(uint32_t* state, int32_t n_envs);
+}
+
+vcs_status vcs_fail(vcs_batch* b, vcs_status st, const char* fmt, ...);
+vcs_status vcs_cuda_fail(vcs_batch* b, cudaError_t e, const char* what);
+vcs::StepParams vcs_base_params(vcs_batch* b);

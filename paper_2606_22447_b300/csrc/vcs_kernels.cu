@@ -1,0 +1,129 @@
+// Hard-mode step kernel: lockstep emulation of many independent VCS envs.
+//
+// One thread per env, one block per run of envs of the same cartridge (the
+// host groups envs by cart), so the block stages exactly one ROM image into
+// shared memory.  The image is brought in by one TMA bulk copy
+// (cp.async.bulk, completion tracked by an mbarrier with a bounded wait).
+// Each thread keeps its machine in registers for the whole launch, its RAM
+// and scanline buffer in shared memory, and writes RAM and finished
+// scanlines (16-byte stores) straight to the caller's buffers.
+#include <cuda_runtime.h>
+
+#include "vcs_exec.cuh"
+#include "vcs_kernels.cuh"
+#include "vcs_run.cuh"
+
+namespace vcs {
+
+// ---------------------------------------------------------------------------
+// decode table (MOS 6500 instruction set: addressing mode, base cycles)
+// ---------------------------------------------------------------------------
+
+void build_decode_tables(DecodeTables* t) {
+  for (int i = 0; i < 256; i++) t->mode_cyc[i] = AM_JAM | (1 << 4);
+  auto set = [&](int op, int mode, int cyc) { t->mode_cyc[op] = (uint8_t)(mode | (cyc << 4)); };
+  // the regular "cc = 01" column: ORA AND EOR ADC STA LDA CMP SBC
+  const int m01[8] = {AM_INX, AM_ZP, AM_IMM, AM_ABS, AM_INY, AM_ZPX, AM_ABY, AM_ABX};
+  const int c01[8] = {6, 3, 2, 4, 5, 4, 4, 4};
+  for (int aaa = 0; aaa < 8; aaa++)
+    for (int bbb = 0; bbb < 8; bbb++) {
+      int op = (aaa << 5) | (bbb << 2) | 1;
+      int cyc = c01[bbb];
+      if (aaa == 4) {            // STA: no immediate; indexed stores pay the fix-up cycle
+        if (m01[bbb] == AM_IMM) continue;
+        if (m01[bbb] == AM_INY) cyc = 6;
+        if (m01[bbb] == AM_ABX || m01[bbb] == AM_ABY) cyc = 5;
+      }
+      set(op, m01[bbb], cyc);
+    }
+  // shifts, rotates, DEC, INC
+  const int rmw[6] = {0x00, 0x20, 0x40, 0x60, 0xC0, 0xE0};
+  for (int k = 0; k < 6; k++) {
+    int b = rmw[k];
+    if (k < 4) set(b + 0x0A, AM_ACC, 2);
+    set(b + 0x06, AM_ZP, 5);
+    set(b + 0x16, AM_ZPX, 6);
+    set(b + 0x0E, AM_ABS, 6);
+    set(b + 0x1E, AM_ABX, 7);
+  }
+  set(0xA2, AM_IMM, 2); set(0xA6, AM_ZP, 3); set(0xB6, AM_ZPY, 4); set(0xAE, AM_ABS, 4); set(0xBE, AM_ABY, 4);
+  set(0xA0, AM_IMM, 2); set(0xA4, AM_ZP, 3); set(0xB4, AM_ZPX, 4); set(0xAC, AM_ABS, 4); set(0xBC, AM_ABX, 4);
+  set(0x86, AM_ZP, 3); set(0x96, AM_ZPY, 4); set(0x8E, AM_ABS, 4);
+  set(0x84, AM_ZP, 3); set(0x94, AM_ZPX, 4); set(0x8C, AM_ABS, 4);
+  set(0xE0, AM_IMM, 2); set(0xE4, AM_ZP, 3); set(0xEC, AM_ABS, 4);
+  set(0xC0, AM_IMM, 2); set(0xC4, AM_ZP, 3); set(0xCC, AM_ABS, 4);
+  set(0x24, AM_ZP, 3); set(0x2C, AM_ABS, 4);
+  for (int op : {0x10, 0x30, 0x50, 0x70, 0x90, 0xB0, 0xD0, 0xF0}) set(op, AM_REL, 2);
+  set(0x4C, AM_ABS, 3); set(0x6C, AM_IND, 5); set(0x20, AM_IND, 6);
+  set(0x60, AM_IMP, 6); set(0x40, AM_IMP, 6); set(0x00, AM_IMP, 7);
+  set(0x48, AM_IMP, 3); set(0x08, AM_IMP, 3); set(0x68, AM_IMP, 4); set(0x28, AM_IMP, 4);
+  for (int op : {0x18, 0x38, 0x58, 0x78, 0xB8, 0xD8, 0xF8, 0xEA, 0xAA, 0x8A, 0xA8, 0x98, 0xBA, 0x9A,
+                 0xE8, 0xCA, 0xC8, 0x88})
+    set(op, AM_IMP, 2);
+}
+
+__global__ void __launch_bounds__(128) k_step(StepParams p) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int E = blockDim.x, tid = threadIdx.x;
+  BlockSmem bs = carve_smem(smem, E);
+  const int4 bi = p.blocks[blockIdx.x];
+  const int cart = bi.x;
+  const uint32_t f8 = p.cart_f8[cart];
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * 8192, f8 ? 8192u : 4096u)) {
+    if (tid == 0) atomicExch(p.err, 1);
+    return;
+  }
+  if (tid >= bi.z) return;
+  const int env = p.perm[bi.y + tid];
+  const int n = p.n_envs;
+  Ctx c = make_ctx(bs, E, tid, f8, p.ystart);
+
+  Regs r;
+  load_env(p.s, n, env, c, r);
+  uint32_t epf = p.s.epf[env], epi = p.s.epi[env];
+  if (p.reset_all || (p.reset_mask && p.reset_mask[env])) {
+    power_on(c, r);
+    epf = 0;
+  }
+
+  NoTape tape;
+  Render rd;
+  rd.on = false;
+  rd.cur = 0;
+  rd.out_f32 = nullptr;
+  for (int t = 0; t < p.n_steps; t++) {
+    set_inputs(r, p.actions ? p.actions[(size_t)t * n + env] : 0u);
+    Step st;
+    st.frame_skip = p.frame_skip;
+    st.status = 0;
+    st.want_screen = p.screen_out != nullptr;
+    rd.out_u8 = p.screen_out ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+    run_frames(c, r, rd, st, tape);
+    normalise_timer(r);
+    if (p.ram_out) write_ram(c, p.ram_out + ((size_t)t * n + env) * 128);
+    if (p.n_episodes > 0) {
+      epf += (uint32_t)p.frame_skip;
+      uint32_t len = p.ep_len[(size_t)env * p.n_episodes + (epi % (uint32_t)p.n_episodes)];
+      if (epf >= len) {
+        st.status |= kStDone;
+        power_on(c, r);
+        epf = 0;
+        epi++;
+      }
+    }
+    if (p.status_out) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
+  }
+  store_env(p.s, n, env, c, r);
+  p.s.epf[env] = epf;
+  p.s.epi[env] = epi;
+}
+
+size_t step_smem_bytes(int E) { return smem_bytes(E); }
+
+int launch_step(const StepParams& p, int n_blocks, int E, void* stream) {
+  if (n_blocks <= 0) return 0;
+  k_step<<<n_blocks, E, step_smem_bytes(E), (cudaStream_t)stream>>>(p);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace vcs

@@ -1,0 +1,56 @@
+// Kernel-side declarations shared by the launchers and the C ABI.
+#pragma once
+#include <cstdint>
+
+#include "vcs_machine.cuh"
+
+namespace vcs {
+
+// Struct-of-arrays machine state: each pointer is one field for all envs
+// (u32 [n_envs]), so a warp's loads and stores of a field are coalesced.
+struct SoA {
+  uint32_t* reg;   // A | X << 8 | Y << 16 | SP << 24
+  uint32_t* pcp;   // PC | P << 16 | bank << 24 | jam << 25
+  uint32_t* cyc;   // CPU cycles mod 2^32
+  uint32_t* fcs;   // fc | fs << 16
+  uint32_t* tw;    // timer write cycle
+  uint32_t* tv;    // timer value | log2 interval << 8
+  uint32_t* t0;    // COLUP0 | COLUPF << 8 | COLUBK << 16 | CTRLPF << 24
+  uint32_t* t1;    // PF0 | PF1 << 8 | PF2 << 16 | GRP0 << 24
+  uint32_t* t2;    // HMP0 | P0 position << 8 | VBLANK << 16 | VSYNC << 24
+  uint32_t* t3;    // scanline of the last early HMOVE (int32, -1 = none)
+  uint32_t* epf;   // frames elapsed in the current episode
+  uint32_t* epi;   // episode index
+  uint32_t* ram;   // RAM words [32][n_envs]
+};
+constexpr int kSoAFields = 12;
+constexpr int kStateWords = kSoAFields + 32;   // per env
+
+struct StepParams {
+  SoA s;
+  int32_t n_envs;
+  const int4* blocks;       // per block: {cart, first slot, env count, 0}
+  const int32_t* perm;      // slot -> env (envs grouped by cart)
+  const uint8_t* roms;      // [n_carts][8192]; 2K images mirrored to 4 KB
+  const uint8_t* cart_f8;   // [n_carts] 1 = F8
+  const DecodeTables* dt;
+  const uint8_t* actions;   // [n_steps][n_envs] or null (NOOP)
+  int32_t n_steps;
+  int32_t frame_skip;
+  uint8_t* ram_out;         // [n_steps][n_envs][128] or null
+  uint8_t* screen_out;      // [n_steps][n_envs][210][160] or null
+  uint8_t* status_out;      // [n_steps][n_envs] or null
+  const uint32_t* ep_len;   // [n_envs][n_episodes] or null
+  int32_t n_episodes;
+  int32_t ystart;
+  const uint8_t* reset_mask;  // per env, or null
+  int32_t reset_all;        // power on every env before stepping
+  int32_t* err;             // device error word (nonzero after a failure)
+};
+
+void build_decode_tables(DecodeTables* t);
+size_t step_smem_bytes(int envs_per_block);
+// Launch the hard step kernel over `n_blocks` blocks of `envs_per_block`.
+int launch_step(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+
+}  // namespace vcs

@@ -1,0 +1,232 @@
+// Per-thread VCS machine for sm_103a: one thread emulates one env.
+//
+// The machine follows the paper's VCS (Section 2.2): 6507 CPU, RIOT (RAM,
+// timer, ports), TIA video, 2K/4K/F8 cartridges.  Where the paper is silent
+// the readings are: frames end at a VSYNC write that sets D1 or after 512
+// scanlines; screen row r is scanline ystart + r over line clocks 68..227;
+// pixel = colour & 0xFE, black under VBLANK D1 and for 8 pixels after an
+// HMOVE at line clock <= 9; a write at the k-th cycle of an instruction
+// starting at cycle t takes effect at colour clock 3 (t + k); RESP0 puts P0
+// at 3 in HBLANK else (clock - 68 + 5) mod 160; WSYNC halts to the next
+// multiple of 76 cycles; the RIOT timer reads V - ceil(k / I) k cycles after
+// a write of V, then (0xFF - (k - V I - 1)) & 0xFF with TIMINT bit 7 set;
+// power-on A=X=Y=0, SP=$FD, P=$34; NMOS decimal mode.
+//
+// Time is kept per thread as two counters: `cyc`, the CPU cycle count
+// modulo 2^32 (only differences are used, for the timer), and `fc`, the
+// cycle index within the current frame (76 * scanline + cycle in line).
+// The TIA is rendered lazily: on each write that changes what is drawn,
+// pixels from the render cursor up to the write's colour clock are drawn
+// with the old registers (span catch-up), and only on the frame a step
+// returns.  Memory lives in shared memory: the cart ROM image (4 or 8 KB,
+// 2K carts mirrored), RAM as 32 words per env interleaved across the block
+// (word w of env j at word w * E + j, so a warp touching the same address
+// hits 32 different banks), and a 160-byte line buffer per env laid out
+// the same way.
+#pragma once
+#include <cstdint>
+
+namespace vcs {
+
+constexpr int kLineCycles = 76;
+constexpr int kLineCap = 512;
+constexpr int kScreenH = 210;
+constexpr int kScreenW = 160;
+
+enum : uint32_t { kStWatchdog = 1, kStJammed = 2, kStDone = 4 };
+
+// Addressing modes of the documented opcodes.
+enum : uint8_t { AM_IMP, AM_ACC, AM_IMM, AM_ZP, AM_ZPX, AM_ZPY, AM_ABS, AM_ABX, AM_ABY,
+                 AM_INX, AM_INY, AM_REL, AM_IND, AM_JAM };
+
+// Per-opcode decode: mode (low 4 bits) | base cycles << 4.
+struct DecodeTables {
+  uint8_t mode_cyc[256];
+};
+
+// Machine registers of one env (kept in registers inside a launch).
+struct Regs {
+  uint32_t A, X, Y, SP, PC;
+  uint32_t fC, fV, fD, fI;   // flags as 0/1
+  uint32_t zsrc, nsrc;       // Z = (zsrc == 0), N = nsrc bit 7
+  uint32_t bank, jam;
+  uint32_t cyc;              // CPU cycles mod 2^32
+  int32_t fc;                // 76 * scanline + line cycle, frame relative
+  uint32_t fs;               // line cycle at which the current frame began
+  uint32_t tw, tv, tsh;      // timer: write cycle, value, log2 interval
+  uint32_t col0, colpf, colbk, ctrl, pf0, pf1, pf2, grp0, hmp0, pos, vblank, vsync;
+  int32_t hml;               // scanline of the last early HMOVE (-1 none)
+  uint32_t swcha, inpt4;
+};
+
+__device__ __forceinline__ uint32_t pack_p(const Regs& r) {
+  return (r.nsrc & 0x80) | (r.fV << 6) | 0x30 | (r.fD << 3) | (r.fI << 2) |
+         ((r.zsrc & 0xFF) == 0 ? 2u : 0u) | r.fC;
+}
+__device__ __forceinline__ void unpack_p(Regs& r, uint32_t p) {
+  r.nsrc = p & 0x80;
+  r.zsrc = (p & 2) ? 0u : 1u;
+  r.fV = (p >> 6) & 1;
+  r.fD = (p >> 3) & 1;
+  r.fI = (p >> 2) & 1;
+  r.fC = p & 1;
+}
+
+// Everything a thread needs besides its registers.
+struct Ctx {
+  const uint8_t* rom;        // shared: cart image (4 KB, or 8 KB for F8)
+  uint8_t* ram;              // shared: this env's RAM byte 0 (stride e4 per word)
+  uint32_t* line;            // shared: this env's line-buffer word 0 (stride E)
+  const DecodeTables* dt;    // shared
+  uint32_t e4;               // 4 * envs per block
+  uint32_t E;                // envs per block
+  uint32_t f8;               // 1 if the cart is F8
+  int32_t ystart;
+};
+
+__device__ __forceinline__ uint32_t ram_rd(const Ctx& c, uint32_t a) {
+  a &= 0x7F;
+  return c.ram[(a >> 2) * c.e4 + (a & 3)];
+}
+__device__ __forceinline__ void ram_wr(const Ctx& c, uint32_t a, uint32_t v) {
+  a &= 0x7F;
+  c.ram[(a >> 2) * c.e4 + (a & 3)] = (uint8_t)v;
+}
+
+__device__ __forceinline__ uint32_t div76(uint32_t x) { return x / 76u; }
+__device__ __forceinline__ uint32_t div228(uint32_t x) { return x / 228u; }
+
+// Timer value read k = t - tw cycles after the last write.
+__device__ __forceinline__ uint32_t intim_at(const Regs& r, uint32_t t) {
+  uint32_t k = t - r.tw;
+  uint32_t vi = r.tv << r.tsh;
+  if (k <= vi) return r.tv - ((k + (1u << r.tsh) - 1) >> r.tsh);
+  return (vi - k) & 0xFF;
+}
+__device__ __forceinline__ uint32_t timint_at(const Regs& r, uint32_t t) {
+  uint32_t k = t - r.tw;
+  return k > (r.tv << r.tsh) ? 0x80u : 0u;
+}
+
+// ----------------------------------------------------------------------------
+// TIA rendering (span catch-up)
+// ----------------------------------------------------------------------------
+
+struct Render {
+  bool on;                   // drawing the frame this step returns
+  int32_t cur;               // render cursor, colour clock in frame coordinates
+  uint8_t* out_u8;           // screen of this env (uint8 [210][160]) or null
+  float* out_f32;            // screen of this env (f32) or null
+};
+
+// 40-bit playfield mask, one bit per 4-pixel block (left half then right).
+__device__ __forceinline__ uint64_t pf_mask(const Regs& r) {
+  uint32_t p20 = ((r.pf0 >> 4) & 0xF) | ((__brev(r.pf1) >> 24) << 4) | ((r.pf2 & 0xFF) << 12);
+  uint32_t right = (r.ctrl & 1) ? (__brev(p20) >> 12) : p20;
+  return (uint64_t)p20 | ((uint64_t)right << 20);
+}
+
+__device__ __forceinline__ void line_put(const Ctx& c, uint32_t x, uint32_t v) {
+  reinterpret_cast<uint8_t*>(c.line)[(x >> 2) * c.e4 + (x & 3)] = (uint8_t)v;
+}
+
+__device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, uint32_t x0, uint32_t x1, int32_t line) {
+  if (r.vblank & 2) {
+    for (uint32_t x = x0; x < x1; x++) line_put(c, x, 0);
+    return;
+  }
+  const uint64_t pfm = pf_mask(r);
+  const uint32_t cp0 = r.col0 & 0xFE, cpf = r.colpf & 0xFE, cbk = r.colbk & 0xFE;
+  const bool pf_first = (r.ctrl & 4) != 0;
+  const uint32_t blank_end = (line == r.hml) ? 8u : 0u;
+  for (uint32_t x = x0; x < x1; x++) {
+    uint32_t v;
+    if (x < blank_end) {
+      v = 0;
+    } else {
+      uint32_t pf = (uint32_t)(pfm >> (x >> 2)) & 1u;
+      int32_t d = (int32_t)x - (int32_t)r.pos;
+      d += d < 0 ? 160 : 0;
+      uint32_t p0 = d < 8 ? (r.grp0 >> (7 - d)) & 1u : 0u;
+      if (pf_first)
+        v = pf ? cpf : (p0 ? cp0 : cbk);
+      else
+        v = p0 ? cp0 : (pf ? cpf : cbk);
+    }
+    line_put(c, x, v);
+  }
+}
+
+__device__ __forceinline__ void flush_row(const Ctx& c, Render& rd, int32_t row) {
+  if (rd.out_u8) {
+    uint4* dst = reinterpret_cast<uint4*>(rd.out_u8 + row * kScreenW);
+#pragma unroll
+    for (int q = 0; q < 10; q++) {
+      uint4 v;
+      v.x = c.line[(4 * q + 0) * c.E];
+      v.y = c.line[(4 * q + 1) * c.E];
+      v.z = c.line[(4 * q + 2) * c.E];
+      v.w = c.line[(4 * q + 3) * c.E];
+      dst[q] = v;
+    }
+  } else if (rd.out_f32) {
+    float4* dst = reinterpret_cast<float4*>(rd.out_f32 + row * kScreenW);
+#pragma unroll 4
+    for (int w = 0; w < 40; w++) {
+      uint32_t v = c.line[w * c.E];
+      dst[w] = make_float4((float)(v & 0xFF), (float)((v >> 8) & 0xFF), (float)((v >> 16) & 0xFF),
+                           (float)(v >> 24));
+    }
+  }
+#pragma unroll 8
+  for (int w = 0; w < 40; w++) c.line[w * c.E] = 0u;
+}
+
+__device__ __forceinline__ void zero_rows(Render& rd, int32_t row0) {
+  if (row0 < 0) row0 = 0;
+  for (int32_t row = row0; row < kScreenH; row++) {
+    if (rd.out_u8) {
+      uint4* dst = reinterpret_cast<uint4*>(rd.out_u8 + row * kScreenW);
+#pragma unroll
+      for (int q = 0; q < 10; q++) dst[q] = make_uint4(0, 0, 0, 0);
+    } else if (rd.out_f32) {
+      float4* dst = reinterpret_cast<float4*>(rd.out_f32 + row * kScreenW);
+#pragma unroll 8
+      for (int q = 0; q < 40; q++) dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// Draw colour clocks [rd.cur, target) of the current frame.
+__device__ __forceinline__ void render_to(const Ctx& c, const Regs& r, Render& rd, int32_t target) {
+  const int32_t top = 228 * c.ystart, bottom = 228 * (c.ystart + kScreenH);
+  if (rd.cur < top) rd.cur = target < top ? target : top;
+  if (target > bottom) target = bottom;
+  while (rd.cur < target) {
+    int32_t line = (int32_t)div228((uint32_t)rd.cur);
+    int32_t lbeg = 228 * line, lend = lbeg + 228;
+    int32_t seg = target < lend ? target : lend;
+    int32_t h0 = rd.cur - lbeg, h1 = seg - lbeg;
+    uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u;
+    uint32_t x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
+    if (x1 > x0) render_span(c, r, x0, x1, line);
+    if (seg == lend) flush_row(c, rd, line - c.ystart);
+    rd.cur = seg;
+  }
+}
+
+// Close the returned frame at colour clock `end`: draw up to it, flush the
+// partly drawn row and zero the rows the frame never reached.
+__device__ __forceinline__ void finish_frame(const Ctx& c, const Regs& r, Render& rd, int32_t end) {
+  render_to(c, r, rd, end);
+  if (rd.cur >= 228 * (c.ystart + kScreenH)) return;
+  int32_t row = (int32_t)div228((uint32_t)rd.cur) - c.ystart;
+  if (row >= 0) {
+    flush_row(c, rd, row);
+    zero_rows(rd, row + 1);
+  } else {
+    zero_rows(rd, 0);
+  }
+}
+
+}  // namespace vcs

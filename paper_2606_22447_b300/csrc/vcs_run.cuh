@@ -1,0 +1,223 @@
+// Block set-up, state load/store and the frame loop shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "vcs_exec.cuh"
+#include "vcs_kernels.cuh"
+
+namespace vcs {
+
+// Shared-memory layout of one block of E envs.
+struct BlockSmem {
+  uint8_t* rom;         // 8192 B cartridge image
+  DecodeTables* dt;     // 256 B
+  uint64_t* mbar;       // TMA completion barrier
+  uint32_t* ram;        // [32][E] words
+  uint32_t* line;       // [40][E] words
+};
+
+__host__ __device__ constexpr size_t smem_bytes(int E) { return 8192 + 256 + 16 + (size_t)(32 + 40) * 4 * E; }
+
+__device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E) {
+  BlockSmem b;
+  b.rom = smem;
+  b.dt = reinterpret_cast<DecodeTables*>(smem + 8192);
+  b.mbar = reinterpret_cast<uint64_t*>(smem + 8192 + 256);
+  b.ram = reinterpret_cast<uint32_t*>(smem + 8192 + 256 + 16);
+  b.line = b.ram + 32 * E;
+  return b;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Stage the decode table (plain loads) and the cartridge image (one TMA bulk
+// copy completing on an mbarrier).  Returns false if the copy did not land
+// within the wait budget; every thread then leaves the kernel.
+__device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTables* dt, const uint8_t* src,
+                                            uint32_t bytes) {
+  const uint32_t bar = smem_addr(b.mbar);
+  for (int i = threadIdx.x; i < 64; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(b.dt)[i] = reinterpret_cast<const uint32_t*>(dt)[i];
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(b.rom)),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+  }
+  uint32_t done = 0;
+  for (uint32_t spin = 0; spin < (1u << 24) && !done; spin++) {
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+  }
+  __syncthreads();
+  return done != 0;
+}
+
+__device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int tid, uint32_t f8, int32_t ystart) {
+  Ctx c;
+  c.rom = b.rom;
+  c.ram = reinterpret_cast<uint8_t*>(b.ram + tid);
+  c.line = b.line + tid;
+  c.dt = b.dt;
+  c.e4 = 4u * (uint32_t)E;
+  c.E = (uint32_t)E;
+  c.f8 = f8;
+  c.ystart = ystart;
+  return c;
+}
+
+__device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& c, Regs& r) {
+  uint32_t v = s.reg[e];
+  r.A = v & 0xFF; r.X = (v >> 8) & 0xFF; r.Y = (v >> 16) & 0xFF; r.SP = v >> 24;
+  v = s.pcp[e];
+  r.PC = v & 0xFFFF;
+  unpack_p(r, (v >> 16) & 0xFF);
+  r.bank = (v >> 24) & 1;
+  r.jam = (v >> 25) & 1;
+  r.cyc = s.cyc[e];
+  v = s.fcs[e];
+  r.fc = (int32_t)(v & 0xFFFF);
+  r.fs = v >> 16;
+  r.tw = s.tw[e];
+  v = s.tv[e];
+  r.tv = v & 0xFF; r.tsh = (v >> 8) & 0xFF;
+  v = s.t0[e];
+  r.col0 = v & 0xFF; r.colpf = (v >> 8) & 0xFF; r.colbk = (v >> 16) & 0xFF; r.ctrl = v >> 24;
+  v = s.t1[e];
+  r.pf0 = v & 0xFF; r.pf1 = (v >> 8) & 0xFF; r.pf2 = (v >> 16) & 0xFF; r.grp0 = v >> 24;
+  v = s.t2[e];
+  r.hmp0 = v & 0xFF; r.pos = (v >> 8) & 0xFF; r.vblank = (v >> 16) & 0xFF; r.vsync = v >> 24;
+  r.hml = (int32_t)s.t3[e];
+  uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
+  for (int i = 0; i < 32; i++) w[i * c.E] = s.ram[(size_t)i * n + e];
+  for (int i = 0; i < 40; i++) c.line[i * c.E] = 0;
+}
+
+__device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx& c, const Regs& r) {
+  s.reg[e] = r.A | (r.X << 8) | (r.Y << 16) | (r.SP << 24);
+  s.pcp[e] = r.PC | (pack_p(r) << 16) | (r.bank << 24) | (r.jam << 25);
+  s.cyc[e] = r.cyc;
+  s.fcs[e] = ((uint32_t)r.fc & 0xFFFF) | (r.fs << 16);
+  s.tw[e] = r.tw;
+  s.tv[e] = r.tv | (r.tsh << 8);
+  s.t0[e] = r.col0 | (r.colpf << 8) | (r.colbk << 16) | (r.ctrl << 24);
+  s.t1[e] = r.pf0 | (r.pf1 << 8) | (r.pf2 << 16) | (r.grp0 << 24);
+  s.t2[e] = r.hmp0 | (r.pos << 8) | (r.vblank << 16) | (r.vsync << 24);
+  s.t3[e] = (uint32_t)r.hml;
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(c.ram);
+  for (int i = 0; i < 32; i++) s.ram[(size_t)i * n + e] = w[i * c.E];
+}
+
+// Power-on state: A = X = Y = 0, SP = $FD, P = $34, RAM and TIA zero, timer
+// as if 0 had been written to T1024T at cycle 0, F8 in bank 1, PC from the
+// reset vector.
+__device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
+  r.A = r.X = r.Y = 0;
+  r.SP = 0xFD;
+  unpack_p(r, 0x34);
+  r.bank = c.f8 ? 1u : 0u;
+  r.jam = 0;
+  r.cyc = 0;
+  r.fc = 0;
+  r.fs = 0;
+  r.tw = 0; r.tv = 0; r.tsh = 10;
+  r.col0 = r.colpf = r.colbk = r.ctrl = r.pf0 = r.pf1 = r.pf2 = r.grp0 = r.hmp0 = 0;
+  r.pos = 0; r.vblank = 0; r.vsync = 0;
+  r.hml = -1;
+  uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
+  for (int i = 0; i < 32; i++) w[i * c.E] = 0;
+  r.PC = c.rom[(r.bank << 12) | 0xFFC] | ((uint32_t)c.rom[(r.bank << 12) | 0xFFD] << 8);
+}
+
+// ALE action -> joystick bits: bit0 right, bit1 left, bit2 down, bit3 up,
+// bit4 fire (ALE action order NOOP, FIRE, UP, RIGHT, LEFT, DOWN, UPRIGHT,
+// UPLEFT, DOWNRIGHT, DOWNLEFT, then the same eight with FIRE).
+__device__ __forceinline__ uint32_t action_bits(uint32_t action) {
+  // direction bits of actions 2..9 (and 10..17), one byte each
+  const uint64_t t0 = 0x06050A0904020108ull;    // actions 2..9 (R,L,D,U bits), low byte = action 2
+  uint32_t dir = 0, fire = 0;
+  if (action == 1) fire = 1;
+  else if (action >= 2 && action <= 9) dir = (uint32_t)(t0 >> (8 * (action - 2))) & 0xF;
+  else if (action >= 10 && action <= 17) {
+    fire = 1;
+    dir = (uint32_t)(t0 >> (8 * (action - 10))) & 0xF;
+  }
+  return dir | (fire << 4);
+}
+
+__device__ __forceinline__ void set_inputs(Regs& r, uint32_t action) {
+  uint32_t b = action_bits(action);
+  // SWCHA player-0 nibble, active low: bit7 right, bit6 left, bit5 down, bit4 up
+  r.swcha = 0xFFu - (((b & 1) << 7) | (((b >> 1) & 1) << 6) | (((b >> 2) & 1) << 5) | (((b >> 3) & 1) << 4));
+  r.inpt4 = (b & 0x10) ? 0x00u : 0x80u;
+}
+
+__device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Step& st, int32_t fcw) {
+  if (rd.on) {
+    finish_frame(c, r, rd, 3 * fcw);
+    rd.on = false;
+  }
+  st.frames_done++;
+  int32_t l = (int32_t)div76((uint32_t)fcw);
+  r.fc -= 76 * l;
+  r.fs = (uint32_t)(fcw - 76 * l);
+  r.hml = -1;
+  if (st.want_screen && st.frames_done == st.frame_skip - 1) {
+    rd.on = true;
+    rd.cur = 3 * (int32_t)r.fs;
+  }
+}
+
+// Run instruction slots until `frame_skip` frames have ended.
+template <class Tape>
+__device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape) {
+  st.frames_done = 0;
+  st.stall = 0;
+  st.fe_at = -1;
+  rd.on = st.want_screen && st.frame_skip == 1;
+  rd.cur = 3 * (int32_t)r.fs;
+  while (st.frames_done < st.frame_skip) {
+    exec_one(c, r, rd, st, tape);
+    int32_t fe = st.fe_at;
+    bool dog = false;
+    if (fe < 0 && r.fc >= kLineCap * kLineCycles) {
+      fe = r.fc;
+      dog = true;
+    }
+    if (fe >= 0) {
+      frame_end(c, r, rd, st, fe);
+      st.fe_at = -1;
+      if (dog) st.status |= kStWatchdog;
+    }
+  }
+  if (r.jam) st.status |= kStJammed;
+}
+
+// Keep the timer's elapsed count small once it has long underflowed, without
+// changing any value it can read (past underflow only k mod 256 matters).
+__device__ __forceinline__ void normalise_timer(Regs& r) {
+  uint32_t k = r.cyc - r.tw, vi = r.tv << r.tsh;
+  if (k > vi + 512u) r.tw += ((k - vi - 256u) & ~255u);
+}
+
+__device__ __forceinline__ void write_ram(const Ctx& c, uint8_t* dst8) {
+  uint4* dst = reinterpret_cast<uint4*>(dst8);
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(c.ram);
+#pragma unroll
+  for (int q = 0; q < 8; q++)
+    dst[q] = make_uint4(w[(4 * q) * c.E], w[(4 * q + 1) * c.E], w[(4 * q + 2) * c.E], w[(4 * q + 3) * c.E]);
+}
+
+}  // namespace vcs

@@ -1,0 +1,79 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point
+declared in include/vcs.h, and rejects bad arguments before touching the
+device (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2606_22447_b300 import _lib, build, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(vcs_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "vcs_create_batch" in names and "vcs_step" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    # the binding covers every declared entry point
+    assert names <= set(_lib.SIGNATURES), names - set(_lib.SIGNATURES)
+
+
+def test_config_defaults(lib):
+    cfg = _lib.Config()
+    assert lib.vcs_config_default(C.byref(cfg)) == 0
+    assert cfg.alpha == 6.0 and cfg.ystart == 34 and cfg.boot_noop_frames == 0
+    assert cfg.segment_frames == 64
+
+
+def _create(lib, roms, sizes, mappers, env_cart, n_carts=None, cfg=None):
+    n_carts = len(roms) if n_carts is None else n_carts
+    keep = [np.frombuffer(r, np.uint8).copy() if r is not None else None for r in roms]
+    ptrs = (_lib.u8p * max(1, len(roms)))(*[k.ctypes.data_as(_lib.u8p) if k is not None else None for k in keep])
+    sz = (C.c_uint32 * max(1, len(sizes)))(*sizes)
+    mp = np.array(mappers, np.uint8)
+    ec = np.array(env_cart, np.int32)
+    h = C.c_void_p()
+    st = lib.vcs_create_batch(ptrs, sz, mp.ctypes.data_as(_lib.u8p), n_carts,
+                              ec.ctypes.data_as(C.POINTER(C.c_int32)), len(env_cart), cfg, C.byref(h))
+    return st, h, lib.vcs_last_error(None).decode()
+
+
+def test_argument_errors_before_device_work(lib):
+    rom4 = synth.generate_cart(1, 0, synth.MAPPER_4K)
+    st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0, 1])
+    assert st == _lib.VCS_ERR_ARG and "out of range" in msg and not h.value
+    st, h, msg = _create(lib, [rom4], [4096], [7], [0])
+    assert st == _lib.VCS_ERR_MAPPER and not h.value
+    st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_2K], [0])
+    assert st == _lib.VCS_ERR_ROM_SIZE and "want 2048" in msg
+    st, h, msg = _create(lib, [None], [4096], [synth.MAPPER_4K], [0])
+    assert st == _lib.VCS_ERR_ARG
+    st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [])
+    assert st == _lib.VCS_ERR_ARG
+    cfg = _lib.Config()
+    lib.vcs_config_default(C.byref(cfg))
+    cfg.envs_per_block = 48
+    st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0], cfg=C.byref(cfg))
+    assert st == _lib.VCS_ERR_ARG and "envs_per_block" in msg
+    assert lib.vcs_step(None, None, 1, None, None, None, None) == _lib.VCS_ERR_ARG
+    assert lib.vcs_destroy(None) == _lib.VCS_ERR_ARG

@@ -1,0 +1,255 @@
+"""Parity of the CUDA hard path with the oracle, bit for bit, on RAM,
+screens and status, through the C ABI (HARD mode of the supplement's
+execution-mode table; the paper's RAM-exact / pixel-exact metrics of
+Section 5, with the oracle standing in for the reference emulator)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_22447_b300 import synth
+from tests.gpu_util import assert_env_equal, gpu_rollout, make_batch, oracle_rollout, torch_cuda
+from tests.microrom import rom4k
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_all(roms, mappers, env_cart, actions, frame_skip, screens=True, envs=None, **cfg):
+    b = make_batch(roms, mappers, env_cart, **cfg)
+    ram, scr, st = gpu_rollout(b, actions, frame_skip, screens)
+    envs = range(len(env_cart)) if envs is None else envs
+    for e in envs:
+        c = int(env_cart[e])
+        r2, s2, st2 = oracle_rollout(roms[c], mappers[c], actions[:, e], frame_skip, screens=screens)
+        assert_env_equal(e, ram[:, e], r2, "RAM")
+        if screens:
+            assert_env_equal(e, scr[:, e], s2, "screen")
+        assert_env_equal(e, st[:, e], st2, "status")
+    return b
+
+
+def test_single_env_2k_60_frames():
+    rom = synth.generate_cart(101, 0, synth.MAPPER_2K)
+    acts = synth.actions(101, 1, 60)
+    _check_all([rom], [synth.MAPPER_2K], [0], acts, 1)
+
+
+@pytest.mark.parametrize("mapper", [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8])
+def test_many_envs_one_cart_ragged(mapper):
+    rom = synth.generate_cart(202, 1, mapper)
+    n_envs = 75      # several blocks and a ragged tail
+    acts = synth.actions(202, n_envs, 8)
+    _check_all([rom], [mapper], [0] * n_envs, acts, 4)
+
+
+def test_mixed_carts_unsorted_envs():
+    roms = synth.config_carts(303, synth.MIX16)
+    env_cart = np.random.default_rng(3).permutation(np.arange(96) % 16).astype(np.int32)
+    acts = synth.actions(303, 96, 5)
+    _check_all(roms, synth.MIX16, env_cart, acts, 2)
+
+
+@pytest.mark.parametrize("epb", [8, 16, 32, 64, 128])
+def test_block_sizes_agree(epb):
+    rom = synth.generate_cart(404, 2, synth.MAPPER_4K)
+    acts = synth.actions(404, 40, 4)
+    b = make_batch([rom], [synth.MAPPER_4K], [0] * 40, envs_per_block=epb)
+    ram, scr, st = gpu_rollout(b, acts, 3)
+    for e in (0, 17, 39):
+        r2, s2, _ = oracle_rollout(rom, synth.MAPPER_4K, acts[:, e], 3)
+        assert_env_equal(e, ram[:, e], r2, "RAM")
+        assert_env_equal(e, scr[:, e], s2, "screen")
+
+
+def test_ystart_and_frame_skip_variants():
+    rom = synth.generate_cart(505, 0, synth.MAPPER_4K)
+    acts = synth.actions(505, 3, 6)
+    for fs in (1, 3):
+        b = make_batch([rom], [synth.MAPPER_4K], [0, 0, 0], ystart=0)
+        ram, scr, _ = gpu_rollout(b, acts, fs)
+        for e in range(3):
+            o = oracle.Oracle(rom, synth.MAPPER_4K, ystart=0)
+            r2, s2, _ = o.rollout(acts[:, e], fs)
+            assert_env_equal(e, ram[:, e], r2, "RAM")
+            assert_env_equal(e, scr[:, e], s2, "screen")
+
+
+# ---------------------------------------------------------------------------
+# edge cases on hand-made cartridges
+# ---------------------------------------------------------------------------
+
+def _jam_rom():
+    def build(a):
+        a.op("LDA", "imm", 0x42)
+        a.op("STA", "zp", 0x09)
+        a.byte(0x02)                  # undocumented opcode: the CPU halts
+    return rom4k(build)
+
+
+def _runaway_rom():
+    """Never writes VSYNC: every frame ends at the 512-line cap."""
+    def build(a):
+        a.label("L")
+        a.op("INC", "zp", 0x80)
+        a.op("LDA", "zp", 0x80)
+        a.op("STA", "zp", 0x09)
+        a.op("STA", "zp", 0x02)
+        a.op("JMP", "abs", "L")
+    return rom4k(build)
+
+
+def _timer_rom():
+    """Timer reads at every interval and odd cycle offsets stored to RAM and
+    the screen, plus mid-line RESP0/HMOVE/playfield writes."""
+    def build(a):
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x01)
+        a.label("F")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0x70)
+        a.op("STA", "zp", 0x20)       # HMP0: move by 7
+        a.op("LDY", "imm", 0)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x2A)       # early HMOVE
+        a.op("TYA")
+        a.op("STA", "abs", 0x0294 + (0 if True else 0))
+        a.op("LDA", "abs", 0x0284)
+        a.op("STA", "zp", 0x06)
+        a.op("STA", "zp", 0x1B)
+        a.op("LDX", "abs", 0x0285)
+        a.op("STX", "zp", 0x0E)
+        a.op("STA", "zp", 0x10)
+        a.op("TYA")
+        a.op("STA", "abs", 0x0296)
+        a.op("LDA", "abs", 0x0284)
+        a.op("STA", "zp", 0x08)
+        a.op("STA", "zp", 0x80)
+        a.op("INY")
+        a.op("CPY", "imm", 240)
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "F")
+    return rom4k(build)
+
+
+def _decimal_stack_rom():
+    """Decimal ADC/SBC, BRK/RTI, JSR/RTS, PHP/PLP, JMP (ind) in a frame loop."""
+    def build(a):
+        a.op("LDX", "imm", 0xFF)
+        a.op("TXS")
+        a.label("F")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("LDX", "imm", 200)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("SED")
+        a.op("TXA")
+        a.op("ADC", "zp", 0x81)
+        a.op("STA", "zp", 0x81)
+        a.op("SBC", "imm", 0x19)
+        a.op("STA", "zp", 0x09)
+        a.op("CLD")
+        a.op("PHP")
+        a.op("JSR", "abs", "S")
+        a.op("PLP")
+        a.op("BRK")
+        a.byte(0xEA)
+        a.op("JMP", "ind", "P")
+        a.label("BACK")
+        a.op("DEX")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "F")
+        a.label("S")
+        a.op("LDA", "abs", 0x0280)
+        a.op("EOR", "zp", 0x82)
+        a.op("STA", "zp", 0x82)
+        a.op("STA", "zp", 0x0F)
+        a.op("RTS")
+        a.label("P")
+        a.word("BACK")
+        a.label("IRQ")
+        a.op("INC", "zp", 0x83)
+        a.op("RTI")
+    a_img = bytearray(rom4k(build))
+    return bytes(a_img)
+
+
+def _with_irq(rom, target):
+    img = bytearray(rom)
+    img[0xFFE], img[0xFFF] = target & 0xFF, target >> 8
+    return bytes(img)
+
+
+def test_edge_case_carts():
+    rom_d = _decimal_stack_rom()
+    # BRK vector -> the IRQ label: find "INC $83" (E6 83) followed by RTI
+    irq = 0xF000 + bytes(rom_d).find(bytes([0xE6, 0x83, 0x40]))
+    rom_d = _with_irq(rom_d, irq)
+    roms = [_jam_rom(), _runaway_rom(), _timer_rom(), rom_d]
+    maps = [synth.MAPPER_4K] * 4
+    env_cart = np.arange(8) % 4
+    acts = synth.actions(606, 8, 5)
+    _check_all(roms, maps, env_cart, acts, 2)
+    b = make_batch(roms, maps, env_cart)
+    _, _, st = gpu_rollout(b, acts, 2, screens=False)
+    assert np.all(st[:, 0] & 2) and np.all(st[:, 1] & 1) and not np.any(st[:, 2:4])
+
+
+def test_generated_carts_cover_the_instruction_set():
+    """The seeded carts execute (nearly) every documented opcode."""
+    seen = set()
+    for mapper in (synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8):
+        for c in range(3):
+            o = oracle.Oracle(synth.generate_cart(707, c, mapper), mapper)
+            tr = o.trace(3, 30000)
+            seen |= set(int(x) for x in tr[:, 1])
+    assert len(seen) >= 140, len(seen)
+
+
+# ---------------------------------------------------------------------------
+# batching features
+# ---------------------------------------------------------------------------
+
+def test_auto_reset_episodes():
+    roms = synth.config_carts(808, [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8])
+    env_cart = np.array([0, 1, 2, 0, 1, 2], np.int32)
+    ep = np.array([[3, 9, 5], [4, 4, 4], [10, 2, 7], [1, 1, 20], [6, 30, 2], [2, 5, 3]], np.uint32)
+    b = make_batch(roms, [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8], env_cart)
+    b.set_episodes(ep)
+    acts = synth.actions(808, 6, 12)
+    ram, scr, st = gpu_rollout(b, acts, 2)
+    for e in range(6):
+        c = env_cart[e]
+        r2, s2, st2 = oracle_rollout(roms[c], [0, 1, 2][c], acts[:, e], 2, ep_len=list(ep[e]))
+        assert_env_equal(e, ram[:, e], r2, "RAM")
+        assert_env_equal(e, scr[:, e], s2, "screen")
+        assert_env_equal(e, st[:, e], st2, "status")
+
+
+def test_step_host_and_state_roundtrip():
+    torch = torch_cuda()
+    rom = synth.generate_cart(909, 0, synth.MAPPER_F8)
+    b = make_batch([rom], [synth.MAPPER_F8], [0] * 10)
+    acts = synth.actions(909, 10, 4)
+    blob = b.save_state()
+    ram, scr, _ = gpu_rollout(b, acts, 2)
+    b.load_state(blob)
+    for t in range(4):
+        rh = np.zeros((10, 128), np.uint8)
+        sh = np.zeros((10, 210, 160), np.uint8)
+        b.step_host(acts[t], 2, rh, sh)
+        assert np.array_equal(rh, ram[t]) and np.array_equal(sh, scr[t])
+    # reset of a subset
+    mask = torch.zeros(10, dtype=torch.uint8, device="cuda")
+    mask[3] = 1
+    b.reset(mask)
+    ram2, _, _ = gpu_rollout(b, acts[:1], 2, screens=False)
+    r3, _, _ = oracle_rollout(rom, synth.MAPPER_F8, acts[:1, 3], 2, screens=False)
+    assert np.array_equal(ram2[0, 3], r3[0])
