@@ -73,6 +73,12 @@ typedef struct vcs_config {
   int32_t boot_noop_frames; /* NOOP frames run by vcs_reset, default 0 */
   int32_t envs_per_block;   /* 0 = automatic; else 8, 16, 32, 64 or 128 */
   int32_t segment_frames;   /* soft checkpoint interval in frames, default 64 */
+  int32_t sched_policy;     /* which lanes of a warp execute each iteration:
+                               0 = the earliest frame's lowest program counter
+                               (default), 1 = emulated time within
+                               sched_window cycles of the earliest lane */
+  int32_t sched_window;     /* window of policy 1 in CPU cycles, -1 = any;
+                               default 4 */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

@@ -27,7 +27,8 @@ class VcsError(RuntimeError):
 
 class Config(C.Structure):
     _fields_ = [("alpha", C.c_float), ("ystart", C.c_int32), ("boot_noop_frames", C.c_int32),
-                ("envs_per_block", C.c_int32), ("segment_frames", C.c_int32)]
+                ("envs_per_block", C.c_int32), ("segment_frames", C.c_int32),
+                ("sched_policy", C.c_int32), ("sched_window", C.c_int32)]
 
 
 vp = C.c_void_p

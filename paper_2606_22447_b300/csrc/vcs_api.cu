@@ -66,6 +66,8 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.dt = b->dt;
   p.ystart = b->cfg.ystart;
   p.err = b->err;
+  p.sched_policy = b->sched_policy;
+  p.sched_window = b->sched_window;
   return p;
 }
 
@@ -100,6 +102,8 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->boot_noop_frames = 0;
   cfg->envs_per_block = 0;
   cfg->segment_frames = 64;
+  cfg->sched_policy = 0;
+  cfg->sched_window = 4;
   return VCS_OK;
 }
 
@@ -167,6 +171,12 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     return vcs_fail(nullptr, VCS_ERR_ARG, "envs_per_block must be 0, 8, 16, 32, 64 or 128");
   }
   b->E = E;
+  if (b->cfg.sched_policy < 0 || b->cfg.sched_policy > 1) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "sched_policy must be 0 or 1");
+  }
+  b->sched_policy = (uint32_t)b->cfg.sched_policy;
+  b->sched_window = b->cfg.sched_window < 0 ? 0xFFFFFFFFu : (uint32_t)b->cfg.sched_window;
 
   // device images: 2K mirrored into 4 KB, F8 as two banks
   std::vector<uint8_t> img((size_t)n_carts * 8192, 0);

@@ -73,17 +73,25 @@ __global__ void __launch_bounds__(128) k_step(StepParams p) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
   }
-  if (tid >= bi.z) return;
-  const int env = p.perm[bi.y + tid];
+  // lanes past the block's env count idle but stay for the warp reductions
+  const bool active = tid < bi.z;
+  const int env = active ? p.perm[bi.y + tid] : 0;
   const int n = p.n_envs;
+  const uint32_t lanes = warp_lanes(E);
   Ctx c = make_ctx(bs, E, tid, f8, p.ystart);
 
   Regs r;
-  load_env(p.s, n, env, c, r);
-  uint32_t epf = p.s.epf[env], epi = p.s.epi[env];
-  if (p.reset_all || (p.reset_mask && p.reset_mask[env])) {
+  uint32_t epf = 0, epi = 0;
+  if (active) {
+    load_env(p.s, n, env, c, r);
+    epf = p.s.epf[env];
+    epi = p.s.epi[env];
+    if (p.reset_all || (p.reset_mask && p.reset_mask[env])) {
+      power_on(c, r);
+      epf = 0;
+    }
+  } else {
     power_on(c, r);
-    epf = 0;
   }
 
   NoTape tape;
@@ -92,13 +100,14 @@ __global__ void __launch_bounds__(128) k_step(StepParams p) {
   rd.cur = 0;
   rd.out_f32 = nullptr;
   for (int t = 0; t < p.n_steps; t++) {
-    set_inputs(r, p.actions ? p.actions[(size_t)t * n + env] : 0u);
+    set_inputs(r, (p.actions && active) ? p.actions[(size_t)t * n + env] : 0u);
     Step st;
     st.frame_skip = p.frame_skip;
     st.status = 0;
     st.want_screen = p.screen_out != nullptr;
-    rd.out_u8 = p.screen_out ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
-    run_frames(c, r, rd, st, tape);
+    rd.out_u8 = (p.screen_out && active) ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+    run_frames(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
+    if (!active) continue;
     normalise_timer(r);
     if (p.ram_out) write_ram(c, p.ram_out + ((size_t)t * n + env) * 128);
     if (p.n_episodes > 0) {
@@ -113,6 +122,7 @@ __global__ void __launch_bounds__(128) k_step(StepParams p) {
     }
     if (p.status_out) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
   }
+  if (!active) return;
   store_env(p.s, n, env, c, r);
   p.s.epf[env] = epf;
   p.s.epi[env] = epi;

@@ -126,34 +126,40 @@ __device__ __forceinline__ uint64_t pf_mask(const Regs& r) {
   return (uint64_t)p20 | ((uint64_t)right << 20);
 }
 
-__device__ __forceinline__ void line_put(const Ctx& c, uint32_t x, uint32_t v) {
-  reinterpret_cast<uint8_t*>(c.line)[(x >> 2) * c.e4 + (x & 3)] = (uint8_t)v;
+// Four pixels of group g (pixels 4g..4g+3) as one word, pixel 4g in the low
+// byte.  Playfield bits cover whole groups; the player's eight pixels start
+// at `pos` and may wrap past column 159.
+__device__ __forceinline__ uint32_t group_pixels(uint32_t g, uint64_t pfm, uint32_t grev, uint32_t pos,
+                                                 uint32_t on_pf, uint32_t off_pf, uint32_t on_bk,
+                                                 uint32_t off_bk) {
+  int32_t d0 = (int32_t)(4 * g) - (int32_t)pos;
+  d0 += d0 < 0 ? 160 : 0;
+  uint32_t nib = d0 < 8 ? (grev >> d0) & 0xF : (d0 > 156 ? (grev << (160 - d0)) & 0xF : 0u);
+  bool pf = (pfm >> g) & 1;
+  uint32_t on = pf ? on_pf : on_bk, off = pf ? off_pf : off_bk;
+  uint32_t m = ((nib & 1) | ((nib & 2) << 7) | ((nib & 4) << 14) | ((nib & 8) << 21)) * 0xFFu;
+  return (on & m) | (off & ~m);
 }
 
+// Draw pixels [x0, x1) of one scanline into this env's line buffer.
 __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, uint32_t x0, uint32_t x1, int32_t line) {
-  if (r.vblank & 2) {
-    for (uint32_t x = x0; x < x1; x++) line_put(c, x, 0);
-    return;
-  }
+  const uint32_t g0 = x0 >> 2, g1 = (x1 + 3) >> 2;
+  const bool blank_all = (r.vblank & 2) != 0;
   const uint64_t pfm = pf_mask(r);
-  const uint32_t cp0 = r.col0 & 0xFE, cpf = r.colpf & 0xFE, cbk = r.colbk & 0xFE;
+  const uint32_t grev = __brev(r.grp0 & 0xFF) >> 24;   // bit k = player pixel k
+  const uint32_t cp0 = (r.col0 & 0xFE) * 0x01010101u, cpf = (r.colpf & 0xFE) * 0x01010101u,
+                 cbk = (r.colbk & 0xFE) * 0x01010101u;
+  // colour where the player bit is set / clear, over playfield / background
   const bool pf_first = (r.ctrl & 4) != 0;
-  const uint32_t blank_end = (line == r.hml) ? 8u : 0u;
-  for (uint32_t x = x0; x < x1; x++) {
-    uint32_t v;
-    if (x < blank_end) {
-      v = 0;
-    } else {
-      uint32_t pf = (uint32_t)(pfm >> (x >> 2)) & 1u;
-      int32_t d = (int32_t)x - (int32_t)r.pos;
-      d += d < 0 ? 160 : 0;
-      uint32_t p0 = d < 8 ? (r.grp0 >> (7 - d)) & 1u : 0u;
-      if (pf_first)
-        v = pf ? cpf : (p0 ? cp0 : cbk);
-      else
-        v = p0 ? cp0 : (pf ? cpf : cbk);
-    }
-    line_put(c, x, v);
+  const uint32_t on_pf = pf_first ? cpf : cp0, off_pf = cpf, on_bk = cp0, off_bk = cbk;
+  const uint32_t blank_g = (line == r.hml) ? 2u : 0u;
+  for (uint32_t g = g0; g < g1; g++) {
+    uint32_t w = (blank_all || g < blank_g) ? 0u : group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk);
+    uint32_t mask = 0xFFFFFFFFu;
+    if (g == g0) mask <<= 8 * (x0 & 3);
+    if (g == g1 - 1 && (x1 & 3)) mask &= 0xFFFFFFFFu >> (8 * (4 - (x1 & 3)));
+    uint32_t* dst = c.line + g * c.E;
+    *dst = mask == 0xFFFFFFFFu ? w : ((*dst & ~mask) | (w & mask));
   }
 }
 

@@ -181,14 +181,35 @@ __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Ste
 }
 
 // Run instruction slots until `frame_skip` frames have ended.
+//
+// Warp scheduling.  Envs of one cart run the same program, but after a
+// data-dependent branch or a timer poll loop they sit at different points of
+// it, and plain SIMT execution never brings them back together: every
+// iteration would then serialise over the lanes' different opcodes.  Each
+// iteration the warp therefore picks which lanes execute:
+//  - policy 0 (program order): the lanes in the earliest frame at the lowest
+//    program counter.  Lanes that skipped code wait at the join point while
+//    the others catch up, so they meet at the same instruction again.
+//  - policy 1 (emulated time): the lanes whose step-relative time is within
+//    `window` cycles of the earliest lane's.
+// Each lane's emulation is independent, so the order changes no result.
+// `lanes` is the mask of the warp's launched lanes; inactive lanes only take
+// part in the reduction.
 template <class Tape>
-__device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape) {
+__device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, bool active,
+                                           uint32_t lanes, uint32_t policy, uint32_t window) {
   st.frames_done = 0;
   st.stall = 0;
   st.fe_at = -1;
-  rd.on = st.want_screen && st.frame_skip == 1;
+  rd.on = active && st.want_screen && st.frame_skip == 1;
   rd.cur = 3 * (int32_t)r.fs;
-  while (st.frames_done < st.frame_skip) {
+  while (true) {
+    const bool live = active && st.frames_done < st.frame_skip;
+    const uint32_t pos = policy == 0 ? (r.jam ? 0xFFFFu : r.PC) : (uint32_t)r.fc;
+    const uint32_t key = live ? (((uint32_t)st.frames_done << 16) | pos) : 0xFFFFFFFFu;
+    const uint32_t kmin = __reduce_min_sync(lanes, key);
+    if (kmin == 0xFFFFFFFFu) break;
+    if (key - kmin > (policy == 0 ? 0u : window)) continue;
     exec_one(c, r, rd, st, tape);
     int32_t fe = st.fe_at;
     bool dog = false;
@@ -202,7 +223,11 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
       if (dog) st.status |= kStWatchdog;
     }
   }
-  if (r.jam) st.status |= kStJammed;
+  if (active && r.jam) st.status |= kStJammed;
+}
+
+__device__ __forceinline__ uint32_t warp_lanes(int E) {
+  return E >= 32 ? 0xFFFFFFFFu : ((1u << E) - 1u);
 }
 
 // Keep the timer's elapsed count small once it has long underflowed, without
