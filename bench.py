@@ -32,7 +32,8 @@ FRAME_SKIP = 4
 SEED = 2
 METRIC = "env-steps/s per B300 (hard fwd; soft fwd+bwd), bit-exact vs CPU oracle"
 WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+screen per step"
-# algorithmic integer work per env-step (roofline section)
+# algorithmic integer work per env-step: 12 operations per emulated instruction
+# and 6 per output pixel; peak = SMs x 128 integer lanes x maximum SM clock
 OPS_PER_INSTRUCTION = 12
 OPS_PER_PIXEL = 6
 PIXELS_PER_STEP = 210 * 160
@@ -165,7 +166,7 @@ def gpu_arm(args):
     build.build()
     rom = synth.generate_cart(SEED, 0, synth.MAPPER_4K)
     n = args.envs
-    batch = Batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32), default_config())
+    batch = Batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32), default_config(envs_per_block=args.epb))
     total_steps = args.warmup + args.steps
     acts = torch.from_numpy(synth.actions(SEED + rank, n, total_steps)).cuda()
     ram = torch.empty((n, 128), dtype=torch.uint8, device="cuda")
@@ -259,6 +260,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--envs", type=int, default=N_ENVS)
+    ap.add_argument("--epb", type=int, default=0, help="envs per block (0 = automatic)")
     ap.add_argument("--instr-per-step", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
