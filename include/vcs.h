@@ -82,6 +82,14 @@ typedef struct vcs_config {
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;
+typedef struct vcs_tape vcs_tape;
+
+/* Loss weights applied at every step of a rollout (device pointers, each
+ * nullable): L = sum over steps and envs of ram . ram_t + screen . screen_t. */
+typedef struct vcs_loss_weights {
+  const float* ram;      /* [128] */
+  const float* screen;   /* [210 * 160] */
+} vcs_loss_weights;
 
 /* Fill *cfg with the defaults listed above. */
 vcs_status vcs_config_default(vcs_config* cfg);
@@ -153,6 +161,47 @@ vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t fram
  * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA
  * for an asynchronous CUDA error. */
 vcs_status vcs_sync(vcs_batch* b, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * SOFT-STE mode (Section 3.1, Eq. peek / Eq. branch / Eq. ste / Eq. s-read;
+ * Theorem 1; Corollary 1).
+ *
+ * vcs_soft_rollout: n_steps env-steps from the batch's current state, like
+ * vcs_rollout, with the inputs of the relaxation as floats:
+ *   rom_f32  device float[n_carts][8192] (nullable: the batch's ROMs) - the
+ *            ROM as a weight tensor; the forward uses round(value) clamped
+ *            to 0..255 (2K images use bytes 0..2047);
+ *   ram0     device float[n_envs][128] (nullable: the current RAM) - the RAM
+ *            at the start of the rollout, rounded likewise;
+ *   u        device float[n_steps][n_envs][5] - joystick inputs (right,
+ *            left, down, up, fire), a button counts as pressed when >= 0.5;
+ *   tau      read temperature in (0, 10]: only the backward pass uses it.
+ * Outputs (device, nullable): ram_out float[n_steps][n_envs][128] and
+ * screen_out float[n_steps][n_envs][210][160]; they hold the hard values
+ * exactly (Theorem 1).  The batch state advances as in vcs_rollout (no
+ * episode auto-reset in soft mode).  The library checkpoints the state every
+ * cfg.segment_frames frames into *tape (owned by the caller until
+ * vcs_tape_free; it refers to the batch, which must outlive it). */
+vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const float* ram0,
+                            const float* u, int32_t n_steps, int32_t frame_skip,
+                            float* ram_out, float* screen_out, vcs_tape** tape, void* stream);
+
+/* Surrogate gradients of L = sum grad_ram . ram_out + sum grad_screen .
+ * screen_out (or of the broadcast loss weights `w`) with respect to
+ *   grad_rom           device float[n_envs][8192] per env (nullable)
+ *   grad_ram0          device float[n_envs][128] (nullable)
+ *   grad_u             device float[n_steps][n_envs][5] (nullable)
+ *   grad_rom_per_cart  device float[n_carts][8192] summed over each cart's
+ *                      envs (nullable)
+ * grad_ram [n_steps][n_envs][128] and grad_screen [n_steps][n_envs][210][160]
+ * are device pointers (each nullable); give either those or `w`.  The pass
+ * recomputes each checkpoint segment, so the forward's outputs need not be
+ * kept.  It may be called several times on one tape; the first call sizes
+ * and allocates the tape's scratch (after one stream synchronisation). */
+vcs_status vcs_backward(vcs_tape* tape, const float* grad_ram, const float* grad_screen,
+                        const vcs_loss_weights* w, float* grad_rom, float* grad_ram0,
+                        float* grad_u, float* grad_rom_per_cart, void* stream);
+vcs_status vcs_tape_free(vcs_tape* tape);
 
 /* Copy the machine state out / in as an opaque blob (checkpoint/resume).
  * vcs_state_bytes gives the size; blob is a host pointer; both calls

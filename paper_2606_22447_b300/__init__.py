@@ -17,7 +17,7 @@ from .synth import MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_SIZE
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 
-__all__ = ["Batch", "Config", "VcsError", "default_config", "MAPPER_2K", "MAPPER_4K", "MAPPER_F8",
+__all__ = ["Batch", "Tape", "Config", "VcsError", "default_config", "MAPPER_2K", "MAPPER_4K", "MAPPER_F8",
            "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
 
 
@@ -126,8 +126,49 @@ class Batch:
         self._check(_lib.load().vcs_save_state(self.h, C.c_void_p(blob.ctypes.data), _stream(stream)))
         return blob
 
+    def soft_rollout(self, tau: float, u, frame_skip: int, rom_f32=None, ram0=None, ram_out=None,
+                     screen_out=None, stream=None) -> "Tape":
+        """SOFT-STE forward over u [n_steps][n_envs][5] (float CUDA tensor);
+        returns the tape for backward().  Outputs are filled in place."""
+        h = C.c_void_p()
+        n_steps = int(u.shape[0])
+        self._check(_lib.load().vcs_soft_rollout(self.h, float(tau), _ptr(rom_f32), _ptr(ram0), _ptr(u), n_steps,
+                                                 frame_skip, _ptr(ram_out), _ptr(screen_out), C.byref(h),
+                                                 _stream(stream)))
+        return Tape(self, h, n_steps)
+
     def load_state(self, blob: np.ndarray, stream=None):
         b = np.ascontiguousarray(blob, dtype=np.uint8)
         if b.size != self.state_bytes():
             raise ValueError("state blob size mismatch")
         self._check(_lib.load().vcs_load_state(self.h, C.c_void_p(b.ctypes.data), _stream(stream)))
+
+
+class Tape:
+    """Checkpoints of one soft rollout; backward() may be called repeatedly."""
+
+    def __init__(self, batch: Batch, handle, n_steps: int):
+        self.batch = batch
+        self.h = handle
+        self.n_steps = n_steps
+
+    def backward(self, grad_ram=None, grad_screen=None, w_ram=None, w_screen=None, grad_rom=None,
+                 grad_ram0=None, grad_u=None, grad_rom_per_cart=None, stream=None):
+        w = None
+        if w_ram is not None or w_screen is not None:
+            w = _lib.LossWeights(_ptr(w_ram), _ptr(w_screen))
+        st = _lib.load().vcs_backward(self.h, _ptr(grad_ram), _ptr(grad_screen), C.byref(w) if w else None,
+                                      _ptr(grad_rom), _ptr(grad_ram0), _ptr(grad_u), _ptr(grad_rom_per_cart),
+                                      _stream(stream))
+        _lib.check(st, self.batch.h)
+
+    def free(self):
+        if getattr(self, "h", None):
+            _lib.load().vcs_tape_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -25,6 +25,10 @@ class VcsError(RuntimeError):
         self.status = status
 
 
+class LossWeights(C.Structure):
+    _fields_ = [("ram", C.c_void_p), ("screen", C.c_void_p)]
+
+
 class Config(C.Structure):
     _fields_ = [("alpha", C.c_float), ("ystart", C.c_int32), ("boot_noop_frames", C.c_int32),
                 ("envs_per_block", C.c_int32), ("segment_frames", C.c_int32),
@@ -52,6 +56,9 @@ SIGNATURES = {
     "vcs_state_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
     "vcs_save_state": (C.c_int, [vp, vp, vp]),
     "vcs_load_state": (C.c_int, [vp, vp, vp]),
+    "vcs_soft_rollout": (C.c_int, [vp, C.c_float, vp, vp, vp, i32, i32, vp, vp, C.POINTER(vp), vp]),
+    "vcs_backward": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "vcs_tape_free": (C.c_int, [vp]),
 }
 
 _lib = None

@@ -38,15 +38,7 @@ vcs_status vcs_cuda_fail(vcs_batch* b, cudaError_t e, const char* what) {
 
 SoA vcs_batch::soa() const { return soa_of(state, n_envs); }
 
-SoA vcs::soa_of(uint32_t* state, int32_t n_envs) {
-  SoA s;
-  const size_t n = (size_t)n_envs;
-  uint32_t** f[kSoAFields] = {&s.reg, &s.pcp, &s.cyc, &s.fcs, &s.tw, &s.tv,
-                              &s.t0, &s.t1, &s.t2, &s.t3, &s.epf, &s.epi};
-  for (int i = 0; i < kSoAFields; i++) *f[i] = state + i * n;
-  s.ram = state + kSoAFields * n;
-  return s;
-}
+SoA vcs::soa_of(uint32_t* state, int32_t n_envs) { return soa_at(state, n_envs); }
 
 static int pick_envs_per_block(int n_envs, int sms) {
   // enough blocks to cover every SM twice, blocks of 8..128 envs
@@ -82,6 +74,9 @@ static void free_batch(vcs_batch* b) {
   cudaFree(b->state);
   cudaFree(b->roms);
   cudaFree(b->cart_f8);
+  cudaFree(b->cart_2k);
+  cudaFree(b->env_cart_dev);
+  cudaFree(b->cart_begin);
   cudaFree(b->dt);
   cudaFree(b->blocks);
   cudaFree(b->perm);
@@ -180,7 +175,7 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
 
   // device images: 2K mirrored into 4 KB, F8 as two banks
   std::vector<uint8_t> img((size_t)n_carts * 8192, 0);
-  std::vector<uint8_t> f8(n_carts);
+  std::vector<uint8_t> f8(n_carts), is2k(n_carts);
   for (int c = 0; c < n_carts; c++) {
     uint8_t* d = img.data() + (size_t)c * 8192;
     if (mappers[c] == VCS_MAPPER_2K) {
@@ -190,6 +185,7 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
       memcpy(d, roms[c], rom_sizes[c]);
     }
     f8[c] = mappers[c] == VCS_MAPPER_F8;
+    is2k[c] = mappers[c] == VCS_MAPPER_2K;
   }
   // group envs by cart (stable), cut each cart's run into blocks of E
   std::vector<int32_t> perm(n_envs);
@@ -205,6 +201,9 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   }
   b->n_blocks = (int)blocks.size();
   b->perm_host = perm;
+  std::vector<int32_t> cart_begin(n_carts + 1, 0);
+  for (int e = 0; e < n_envs; e++) cart_begin[env_cart[e] + 1]++;
+  for (int c = 0; c < n_carts; c++) cart_begin[c + 1] += cart_begin[c];
   DecodeTables dt;
   build_decode_tables(&dt);
 
@@ -213,7 +212,9 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if ((e = cudaMalloc(&b->state, nst)) || (e = cudaMalloc(&b->roms, img.size())) ||
       (e = cudaMalloc(&b->cart_f8, n_carts)) || (e = cudaMalloc(&b->dt, sizeof(DecodeTables))) ||
       (e = cudaMalloc(&b->blocks, blocks.size() * sizeof(int4))) ||
-      (e = cudaMalloc(&b->perm, n_envs * sizeof(int32_t))) || (e = cudaMalloc(&b->err, sizeof(int32_t)))) {
+      (e = cudaMalloc(&b->perm, n_envs * sizeof(int32_t))) || (e = cudaMalloc(&b->err, sizeof(int32_t))) ||
+      (e = cudaMalloc(&b->cart_2k, n_carts)) || (e = cudaMalloc(&b->env_cart_dev, n_envs * sizeof(int32_t))) ||
+      (e = cudaMalloc(&b->cart_begin, (n_carts + 1) * sizeof(int32_t)))) {
     vcs_status st = vcs_cuda_fail(nullptr, e, "device allocation");
     free_batch(b);
     return st;
@@ -223,6 +224,9 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
       (e = cudaMemcpy(b->dt, &dt, sizeof dt, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->blocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->perm, perm.data(), n_envs * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->cart_2k, is2k.data(), n_carts, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->env_cart_dev, env_cart, n_envs * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->cart_begin, cart_begin.data(), (n_carts + 1) * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
       (e = cudaMemset(b->err, 0, sizeof(int32_t))) || (e = cudaMemset(b->state, 0, nst))) {
     vcs_status st = vcs_cuda_fail(nullptr, e, "device upload");
     free_batch(b);
@@ -356,6 +360,7 @@ vcs_status vcs_sync(vcs_batch* b, void* stream) {
   if (e) return vcs_cuda_fail(b, e, "synchronize");
   int32_t err = 0;
   if ((e = cudaMemcpy(&err, b->err, sizeof err, cudaMemcpyDeviceToHost))) return vcs_cuda_fail(b, e, "error word");
+  if (err == 2) return vcs_fail(b, VCS_ERR_STATE, "backward tape overflow (recompute diverged from the forward)");
   if (err) return vcs_fail(b, VCS_ERR_WATCHDOG, "a device wait gave up (code %d); batch unusable", err);
   return VCS_OK;
 }

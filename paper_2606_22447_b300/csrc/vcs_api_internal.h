@@ -18,6 +18,9 @@ struct vcs_batch {
   uint32_t* state = nullptr;      // kStateWords x n_envs
   uint8_t* roms = nullptr;        // n_carts x 8192
   uint8_t* cart_f8 = nullptr;
+  uint8_t* cart_2k = nullptr;
+  int32_t* env_cart_dev = nullptr;
+  int32_t* cart_begin = nullptr;  // [n_carts + 1] first perm slot of each cart
   vcs::DecodeTables* dt = nullptr;
   int4* blocks = nullptr;
   int32_t* perm = nullptr;

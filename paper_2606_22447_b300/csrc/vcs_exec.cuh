@@ -35,9 +35,10 @@ constexpr uint64_t kVisualRegs = (1ull << 0x01) | (1ull << 0x06) | (1ull << 0x08
                                  (1ull << 0x0A) | (1ull << 0x0D) | (1ull << 0x0E) | (1ull << 0x0F) |
                                  (1ull << 0x10) | (1ull << 0x1B) | (1ull << 0x2A);
 
-__device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, uint32_t reg, uint32_t v,
-                                          int32_t fcw) {
-  if (((kVisualRegs >> reg) & 1) && rd.on) render_to(c, r, rd, 3 * fcw);
+template <class Tape>
+__device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t reg,
+                                          uint32_t v, int32_t fcw) {
+  if (((kVisualRegs >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
   switch (reg) {
     case 0x00:
       if (!(r.vsync & 2) && (v & 2)) st.fe_at = fcw;
@@ -49,9 +50,9 @@ __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Ste
       if (m) st.stall += 76 - (int32_t)m;
       break;
     }
-    case 0x06: r.col0 = v; break;
-    case 0x08: r.colpf = v; break;
-    case 0x09: r.colbk = v; break;
+    case 0x06: tape.colour_write(0); r.col0 = v; break;
+    case 0x08: tape.colour_write(1); r.colpf = v; break;
+    case 0x09: tape.colour_write(2); r.colbk = v; break;
     case 0x0A: r.ctrl = v; break;
     case 0x0D: r.pf0 = v; break;
     case 0x0E: r.pf1 = v; break;
@@ -75,6 +76,9 @@ __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Ste
   }
 }
 
+// One bus read at cycle index idx of the current instruction.  A read of
+// INTIM also records whether the timer had underflowed (r.intim_live), which
+// the soft path's tape keeps for the backward sweep.
 __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& st, uint32_t addr, int idx) {
   uint32_t a = addr & 0x1FFF;
   if (a & 0x1000) {
@@ -91,10 +95,13 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
     return q == 0 ? r.swcha : (q == 2 ? 0x0Bu : 0u);
   }
   uint32_t t = r.cyc + (uint32_t)(idx + st.stall);
-  return (a & 1) ? timint_at(r, t) : intim_at(r, t);
+  if (a & 1) return timint_at(r, t);
+  r.intim_live = (t - r.tw) <= (r.tv << r.tsh) ? 1u : 0u;
+  return intim_at(r, t);
 }
 
-__device__ __forceinline__ void bus_write(const Ctx& c, Regs& r, Render& rd, Step& st, uint32_t addr,
+template <class Tape>
+__device__ __forceinline__ void bus_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t addr,
                                           uint32_t v, int idx) {
   uint32_t a = addr & 0x1FFF;
   if (a & 0x1000) {
@@ -102,7 +109,7 @@ __device__ __forceinline__ void bus_write(const Ctx& c, Regs& r, Render& rd, Ste
     return;
   }
   if (!(a & 0x80)) {
-    tia_write(c, r, rd, st, a & 0x3F, v & 0xFF, r.fc + idx + st.stall);
+    tia_write(c, r, rd, st, tape, a & 0x3F, v & 0xFF, r.fc + idx + st.stall);
     return;
   }
   if (!(a & 0x200)) {
@@ -191,7 +198,10 @@ __device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r, Step& st, int id
 // reference address and flag bits (the soft path records these; the hard
 // path compiles the hook away).
 struct NoTape {
+  static constexpr bool kAcc = false;
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) {}
+  __device__ __forceinline__ void colour_write(int) {}
+  __device__ __forceinline__ void pixels(float, float, float) {}
 };
 
 // Execute one instruction slot (an instruction, or for a jammed CPU an idle
@@ -205,6 +215,7 @@ __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step
     return;
   }
   const uint32_t opaddr = r.PC;
+  r.intim_live = 0;
   const uint32_t op = bus_read(c, r, st, opaddr, 1);
   const uint32_t mc = c.dt->mode_cyc[op];
   const uint32_t mode = mc & 15;
@@ -475,9 +486,9 @@ __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step
       addr = 0x100u | r.SP;
       r.SP = (r.SP - 1) & 0xFF;
     }
-    bus_write(c, r, rd, st, addr, (wv >> (8 * i)) & 0xFF, (int)(widx + i));
+    bus_write(c, r, rd, st, tape, addr, (wv >> (8 * i)) & 0xFF, (int)(widx + i));
   }
-  tape.rec(op, tref, tfl);
+  tape.rec(op, tref, tfl | (r.bank << 1) | (r.intim_live << 2));
   r.cyc += n + (uint32_t)st.stall;
   r.fc += (int32_t)n + st.stall;
   st.stall = 0;

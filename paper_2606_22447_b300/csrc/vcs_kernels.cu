@@ -1,4 +1,5 @@
-// Hard-mode step kernel: lockstep emulation of many independent VCS envs.
+// Step kernel: lockstep emulation of many independent VCS envs (hard mode,
+// and the SOFT-STE forward, which is the same machine on rounded inputs).
 //
 // One thread per env, one block per run of envs of the same cartridge (the
 // host groups envs by cart), so the block stages exactly one ROM image into
@@ -8,6 +9,8 @@
 // and scanline buffer in shared memory, and writes RAM and finished
 // scanlines (16-byte stores) straight to the caller's buffers.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "vcs_exec.cuh"
 #include "vcs_kernels.cuh"
@@ -62,7 +65,27 @@ void build_decode_tables(DecodeTables* t) {
     set(op, AM_IMP, 2);
 }
 
-__global__ void __launch_bounds__(128) k_step(StepParams p) {
+// Counts instructions and colour-register writes per checkpoint segment (the
+// soft forward sizes the backward's tape with these).
+struct CountTape {
+  static constexpr bool kAcc = false;
+  uint32_t n = 0, ncw = 0;
+  __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) { n++; }
+  __device__ __forceinline__ void colour_write(int) { ncw++; }
+  __device__ __forceinline__ void pixels(float, float, float) {}
+};
+
+__device__ __forceinline__ uint32_t round_byte(float v) {
+  float x = rintf(v);
+  return x <= 0.f ? 0u : (x >= 255.f ? 255u : (uint32_t)x);
+}
+
+// One launch = n_steps env-steps for every env.  SOFT selects the SOFT-STE
+// forward: joystick bits come from rounded float inputs, outputs are float,
+// the RAM may be overridden from float values first, and the full state is
+// checkpointed at the start of every segment of seg_steps steps.
+template <bool SOFT>
+__global__ void __launch_bounds__(128) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x, tid = threadIdx.x;
   BlockSmem bs = carve_smem(smem, E);
@@ -90,27 +113,68 @@ __global__ void __launch_bounds__(128) k_step(StepParams p) {
       power_on(c, r);
       epf = 0;
     }
+    if (SOFT && p.ram0) {
+      uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
+      const float* src = p.ram0 + (size_t)env * 128;
+      for (int i = 0; i < 32; i++)
+        w[i * c.E] = round_byte(src[4 * i]) | (round_byte(src[4 * i + 1]) << 8) |
+                     (round_byte(src[4 * i + 2]) << 16) | (round_byte(src[4 * i + 3]) << 24);
+    }
   } else {
     power_on(c, r);
   }
 
-  NoTape tape;
+  typename std::conditional<SOFT, CountTape, NoTape>::type tape;
   Render rd;
   rd.on = false;
   rd.cur = 0;
+  rd.out_u8 = nullptr;
   rd.out_f32 = nullptr;
+  rd.gs = nullptr;
   for (int t = 0; t < p.n_steps; t++) {
-    set_inputs(r, (p.actions && active) ? p.actions[(size_t)t * n + env] : 0u);
+    if constexpr (SOFT) {
+      if (t % p.seg_steps == 0) {
+        const int seg = t / p.seg_steps;
+        if (seg > 0 && active) {
+          atomicMax(p.seg_counts + 2 * (seg - 1), tape.n);
+          atomicMax(p.seg_counts + 2 * (seg - 1) + 1, tape.ncw);
+        }
+        tape.n = tape.ncw = 0;
+        if (active) store_env(soa_at(p.ckpt + (size_t)seg * kStateWords * n, n), n, env, c, r);
+      }
+    }
+    uint32_t bits = 0;
+    if (SOFT) {
+      if (active) {
+        const float* u = p.u + ((size_t)t * n + env) * 5;
+        bits = (u[0] >= 0.5f ? 1u : 0u) | (u[1] >= 0.5f ? 2u : 0u) | (u[2] >= 0.5f ? 4u : 0u) |
+               (u[3] >= 0.5f ? 8u : 0u) | (u[4] >= 0.5f ? 16u : 0u);
+        p.act_bits[(size_t)t * n + env] = (uint8_t)bits;
+      }
+      set_input_bits(r, bits);
+    } else {
+      set_inputs(r, (p.actions && active) ? p.actions[(size_t)t * n + env] : 0u);
+    }
     Step st;
     st.frame_skip = p.frame_skip;
     st.status = 0;
-    st.want_screen = p.screen_out != nullptr;
-    rd.out_u8 = (p.screen_out && active) ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+    if (SOFT) {
+      st.want_screen = p.screen_out_f != nullptr;
+      rd.out_f32 = (p.screen_out_f && active)
+                       ? p.screen_out_f + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+    } else {
+      st.want_screen = p.screen_out != nullptr;
+      rd.out_u8 = (p.screen_out && active) ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+    }
     run_frames(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
     if (!active) continue;
     normalise_timer(r);
-    if (p.ram_out) write_ram(c, p.ram_out + ((size_t)t * n + env) * 128);
-    if (p.n_episodes > 0) {
+    if (SOFT) {
+      if (p.ram_out_f) write_ram_f32(c, p.ram_out_f + ((size_t)t * n + env) * 128);
+    } else {
+      if (p.ram_out) write_ram(c, p.ram_out + ((size_t)t * n + env) * 128);
+    }
+    if (!SOFT && p.n_episodes > 0) {
       epf += (uint32_t)p.frame_skip;
       uint32_t len = p.ep_len[(size_t)env * p.n_episodes + (epi % (uint32_t)p.n_episodes)];
       if (epf >= len) {
@@ -123,6 +187,13 @@ __global__ void __launch_bounds__(128) k_step(StepParams p) {
     if (p.status_out) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
   }
   if (!active) return;
+  if constexpr (SOFT) {
+    if (p.n_steps > 0) {
+      const int seg = (p.n_steps - 1) / p.seg_steps;
+      atomicMax(p.seg_counts + 2 * seg, tape.n);
+      atomicMax(p.seg_counts + 2 * seg + 1, tape.ncw);
+    }
+  }
   store_env(p.s, n, env, c, r);
   p.s.epf[env] = epf;
   p.s.epi[env] = epi;
@@ -132,7 +203,13 @@ size_t step_smem_bytes(int E) { return smem_bytes(E); }
 
 int launch_step(const StepParams& p, int n_blocks, int E, void* stream) {
   if (n_blocks <= 0) return 0;
-  k_step<<<n_blocks, E, step_smem_bytes(E), (cudaStream_t)stream>>>(p);
+  k_run<false><<<n_blocks, E, step_smem_bytes(E), (cudaStream_t)stream>>>(p);
+  return (int)cudaGetLastError();
+}
+
+int launch_soft_forward(const StepParams& p, int n_blocks, int E, void* stream) {
+  if (n_blocks <= 0) return 0;
+  k_run<true><<<n_blocks, E, step_smem_bytes(E), (cudaStream_t)stream>>>(p);
   return (int)cudaGetLastError();
 }
 

@@ -48,11 +48,31 @@ struct StepParams {
   int32_t* err;             // device error word (nonzero after a failure)
   uint32_t sched_policy;    // warp scheduling: 0 program order, 1 emulated time (run_frames)
   uint32_t sched_window;    // time window in cycles for policy 1
+  // soft forward only
+  const float* u;           // joystick inputs [n_steps][n_envs][5] (R, L, D, U, FIRE)
+  const float* ram0;        // RAM at the start of the rollout [n_envs][128] or null
+  uint8_t* act_bits;        // rounded joystick bits per step [n_steps][n_envs]
+  float* ram_out_f;         // [n_steps][n_envs][128] or null
+  float* screen_out_f;      // [n_steps][n_envs][210][160] or null
+  uint32_t* ckpt;           // [n_segments][kStateWords][n_envs]
+  int32_t seg_steps;        // steps per checkpoint segment
+  uint32_t* seg_counts;     // [n_segments][2]: max instructions, max colour writes
 };
+
+__host__ __device__ inline SoA soa_at(uint32_t* base, int32_t n_envs) {
+  SoA s;
+  const size_t n = (size_t)n_envs;
+  s.reg = base; s.pcp = base + n; s.cyc = base + 2 * n; s.fcs = base + 3 * n; s.tw = base + 4 * n;
+  s.tv = base + 5 * n; s.t0 = base + 6 * n; s.t1 = base + 7 * n; s.t2 = base + 8 * n; s.t3 = base + 9 * n;
+  s.epf = base + 10 * n; s.epi = base + 11 * n; s.ram = base + kSoAFields * n;
+  return s;
+}
 
 void build_decode_tables(DecodeTables* t);
 size_t step_smem_bytes(int envs_per_block);
-// Launch the hard step kernel over `n_blocks` blocks of `envs_per_block`.
+// Launch the step kernel over `n_blocks` blocks of `envs_per_block`
+// (soft = the SOFT-STE forward: float inputs / outputs and checkpoints).
 int launch_step(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+int launch_soft_forward(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 
 }  // namespace vcs

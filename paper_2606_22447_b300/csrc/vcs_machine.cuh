@@ -57,6 +57,7 @@ struct Regs {
   uint32_t col0, colpf, colbk, ctrl, pf0, pf1, pf2, grp0, hmp0, pos, vblank, vsync;
   int32_t hml;               // scanline of the last early HMOVE (-1 none)
   uint32_t swcha, inpt4;
+  uint32_t intim_live;       // the last INTIM read came before underflow
 };
 
 __device__ __forceinline__ uint32_t pack_p(const Regs& r) {
@@ -117,6 +118,8 @@ struct Render {
   int32_t cur;               // render cursor, colour clock in frame coordinates
   uint8_t* out_u8;           // screen of this env (uint8 [210][160]) or null
   float* out_f32;            // screen of this env (f32) or null
+  const float* gs;           // pixel gradients of the returned frame [210][160]
+                             // (backward recompute only) or null
 };
 
 // 40-bit playfield mask, one bit per 4-pixel block (left half then right).
@@ -141,8 +144,12 @@ __device__ __forceinline__ uint32_t group_pixels(uint32_t g, uint64_t pfm, uint3
   return (on & m) | (off & ~m);
 }
 
-// Draw pixels [x0, x1) of one scanline into this env's line buffer.
-__device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, uint32_t x0, uint32_t x1, int32_t line) {
+// Draw pixels [x0, x1) of one scanline into this env's line buffer, or, when
+// the tape accumulates pixel gradients (backward recompute), add each pixel's
+// gradient to the colour register that owns it.
+template <class Tape>
+__device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const Render& rd, Tape& tape, uint32_t x0,
+                                            uint32_t x1, int32_t line) {
   const uint32_t g0 = x0 >> 2, g1 = (x1 + 3) >> 2;
   const bool blank_all = (r.vblank & 2) != 0;
   const uint64_t pfm = pf_mask(r);
@@ -153,6 +160,31 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, uint32_
   const bool pf_first = (r.ctrl & 4) != 0;
   const uint32_t on_pf = pf_first ? cpf : cp0, off_pf = cpf, on_bk = cp0, off_bk = cbk;
   const uint32_t blank_g = (line == r.hml) ? 2u : 0u;
+  if constexpr (Tape::kAcc) {
+    if (blank_all || !rd.gs) return;
+    const float* gl = rd.gs + (line - c.ystart) * kScreenW;
+    for (uint32_t g = g0 < blank_g ? blank_g : g0; g < g1; g++) {
+      int32_t d0 = (int32_t)(4 * g) - (int32_t)r.pos;
+      d0 += d0 < 0 ? 160 : 0;
+      uint32_t nib = d0 < 8 ? (grev >> d0) & 0xF : (d0 > 156 ? (grev << (160 - d0)) & 0xF : 0u);
+      bool pf = (pfm >> g) & 1;
+      float4 q = *reinterpret_cast<const float4*>(gl + 4 * g);
+      float v[4] = {q.x, q.y, q.z, q.w};
+      float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        uint32_t x = 4 * g + j;
+        if (x < x0 || x >= x1) continue;
+        bool p0 = (nib >> j) & 1;
+        int owner = pf_first ? (pf ? 1 : (p0 ? 0 : 2)) : (p0 ? 0 : (pf ? 1 : 2));
+        acc[0] += owner == 0 ? v[j] : 0.f;
+        acc[1] += owner == 1 ? v[j] : 0.f;
+        acc[2] += owner == 2 ? v[j] : 0.f;
+      }
+      tape.pixels(acc[0], acc[1], acc[2]);
+    }
+    return;
+  }
   for (uint32_t g = g0; g < g1; g++) {
     uint32_t w = (blank_all || g < blank_g) ? 0u : group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk);
     uint32_t mask = 0xFFFFFFFFu;
@@ -204,7 +236,8 @@ __device__ __forceinline__ void zero_rows(Render& rd, int32_t row0) {
 }
 
 // Draw colour clocks [rd.cur, target) of the current frame.
-__device__ __forceinline__ void render_to(const Ctx& c, const Regs& r, Render& rd, int32_t target) {
+template <class Tape>
+__device__ __forceinline__ void render_to(const Ctx& c, const Regs& r, Render& rd, Tape& tape, int32_t target) {
   const int32_t top = 228 * c.ystart, bottom = 228 * (c.ystart + kScreenH);
   if (rd.cur < top) rd.cur = target < top ? target : top;
   if (target > bottom) target = bottom;
@@ -215,17 +248,18 @@ __device__ __forceinline__ void render_to(const Ctx& c, const Regs& r, Render& r
     int32_t h0 = rd.cur - lbeg, h1 = seg - lbeg;
     uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u;
     uint32_t x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
-    if (x1 > x0) render_span(c, r, x0, x1, line);
-    if (seg == lend) flush_row(c, rd, line - c.ystart);
+    if (x1 > x0) render_span(c, r, rd, tape, x0, x1, line);
+    if (!Tape::kAcc && seg == lend) flush_row(c, rd, line - c.ystart);
     rd.cur = seg;
   }
 }
 
 // Close the returned frame at colour clock `end`: draw up to it, flush the
 // partly drawn row and zero the rows the frame never reached.
-__device__ __forceinline__ void finish_frame(const Ctx& c, const Regs& r, Render& rd, int32_t end) {
-  render_to(c, r, rd, end);
-  if (rd.cur >= 228 * (c.ystart + kScreenH)) return;
+template <class Tape>
+__device__ __forceinline__ void finish_frame(const Ctx& c, const Regs& r, Render& rd, Tape& tape, int32_t end) {
+  render_to(c, r, rd, tape, end);
+  if (Tape::kAcc || rd.cur >= 228 * (c.ystart + kScreenH)) return;
   int32_t row = (int32_t)div228((uint32_t)rd.cur) - c.ystart;
   if (row >= 0) {
     flush_row(c, rd, row);

@@ -157,16 +157,20 @@ __device__ __forceinline__ uint32_t action_bits(uint32_t action) {
   return dir | (fire << 4);
 }
 
-__device__ __forceinline__ void set_inputs(Regs& r, uint32_t action) {
-  uint32_t b = action_bits(action);
+// Joystick bits (bit0 right, bit1 left, bit2 down, bit3 up, bit4 fire) ->
+// SWCHA and INPT4.
+__device__ __forceinline__ void set_input_bits(Regs& r, uint32_t b) {
   // SWCHA player-0 nibble, active low: bit7 right, bit6 left, bit5 down, bit4 up
   r.swcha = 0xFFu - (((b & 1) << 7) | (((b >> 1) & 1) << 6) | (((b >> 2) & 1) << 5) | (((b >> 3) & 1) << 4));
   r.inpt4 = (b & 0x10) ? 0x00u : 0x80u;
 }
 
-__device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Step& st, int32_t fcw) {
+__device__ __forceinline__ void set_inputs(Regs& r, uint32_t action) { set_input_bits(r, action_bits(action)); }
+
+template <class Tape>
+__device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, int32_t fcw) {
   if (rd.on) {
-    finish_frame(c, r, rd, 3 * fcw);
+    finish_frame(c, r, rd, tape, 3 * fcw);
     rd.on = false;
   }
   st.frames_done++;
@@ -218,7 +222,7 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
       dog = true;
     }
     if (fe >= 0) {
-      frame_end(c, r, rd, st, fe);
+      frame_end(c, r, rd, st, tape, fe);
       st.fe_at = -1;
       if (dog) st.status |= kStWatchdog;
     }
@@ -235,6 +239,16 @@ __device__ __forceinline__ uint32_t warp_lanes(int E) {
 __device__ __forceinline__ void normalise_timer(Regs& r) {
   uint32_t k = r.cyc - r.tw, vi = r.tv << r.tsh;
   if (k > vi + 512u) r.tw += ((k - vi - 256u) & ~255u);
+}
+
+__device__ __forceinline__ void write_ram_f32(const Ctx& c, float* dst) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(c.ram);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll 8
+  for (int q = 0; q < 32; q++) {
+    uint32_t v = w[q * c.E];
+    d4[q] = make_float4((float)(v & 0xFF), (float)((v >> 8) & 0xFF), (float)((v >> 16) & 0xFF), (float)(v >> 24));
+  }
 }
 
 __device__ __forceinline__ void write_ram(const Ctx& c, uint8_t* dst8) {

@@ -1,0 +1,680 @@
+// SOFT-STE backward pass (Corollary 1) and the soft entry points of the C ABI.
+//
+// The forward pass of soft mode is the step kernel on rounded inputs (it
+// equals the hard machine, Theorem 1) plus a state checkpoint at the start of
+// every segment.  The backward pass runs the segments last to first; for each
+// one a kernel, one thread per env:
+//   1. recomputes the segment's forward from its checkpoint, recording one
+//      4-byte tape entry per instruction (opcode, reference address, flags)
+//      and, on the frames a step returns, the sum of the pixel gradients owned
+//      by each colour-register version (the stored priority switch);
+//   2. sweeps the tape backwards, carrying adjoints of A, X, Y, the timer
+//      value, the three colour registers and the 128 RAM cells (in shared
+//      memory), with the surrogate rules:
+//        reads   relaxed read of Eq. s-read w.r.t. memory contents: RAM reads
+//                spread the adjoint over |i - a| <= W with weights
+//                exp(-|i - a| / tau) normalised in the clipped window; ROM
+//                reads add an impulse at a, spread by the same weights later;
+//                SWCHA / INPT4 reads give the joystick inputs -128, -64, -32,
+//                -16 / -128; INTIM before underflow gives the timer value 1;
+//        writes  the cell's adjoint moves to the written register;
+//        ALU     ADC (1, 1), SBC (1, -1), AND/ORA/EOR (1, 1), shifts,
+//                rotates, increments and transfers 1, compares nothing;
+//        indices addresses, PC, SP and flags carry nothing;
+//   3. hands the adjoints at the segment start to the previous segment.
+// A final pass spreads the ROM impulses with the read window and optionally
+// sums the per-env ROM gradients per cartridge (a segmented reduction over
+// the envs of each cart, no atomics).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vcs_api_internal.h"
+#include "vcs_exec.cuh"
+#include "vcs_kernels.cuh"
+#include "vcs_run.cuh"
+
+namespace vcs {
+
+constexpr int kCarry = 7 + 256;   // aA aX aY aV aC0 aC1 aC2, aRAM[128] and its compensation
+constexpr int kMaxW = 120;        // window half-width limit (tau <= 10)
+
+// Compensated (Neumaier) sum: s + c carries the running total.
+__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
+  const float t = s + x;
+  c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
+
+struct RecTape {
+  static constexpr bool kAcc = true;
+  uint32_t* buf;
+  float* cw;
+  uint32_t n, cap, ncw, capcw;
+  int32_t slot0, slot1, slot2;     // float slot of each colour register's live version
+  float s0, s1, s2, c0, c1, c2;    // compensated pixel-gradient sums of the live versions
+  float p0, p1, p2;                // sums of the versions alive at the segment start
+  bool overflow;
+  __device__ __forceinline__ void rec(uint32_t op, uint32_t ref, uint32_t fl) {
+    if (n < cap) buf[n] = op | ((ref & 0xFFFF) << 8) | (fl << 24);
+    else overflow = true;
+    n++;
+  }
+  __device__ __forceinline__ void close_version(int32_t slot, float s, float& pinit) {
+    if (slot >= 0) cw[slot] = s;
+    else if (slot == -1) pinit += s;
+  }
+  __device__ __forceinline__ void colour_write(int r) {
+    int32_t fresh = ncw < capcw ? (int32_t)ncw : -2;
+    if (fresh == -2) overflow = true;
+    ncw++;
+    if (r == 0) { close_version(slot0, s0 + c0, p0); s0 = c0 = 0.f; slot0 = fresh; }
+    else if (r == 1) { close_version(slot1, s1 + c1, p1); s1 = c1 = 0.f; slot1 = fresh; }
+    else { close_version(slot2, s2 + c2, p2); s2 = c2 = 0.f; slot2 = fresh; }
+  }
+  // pixel-gradient partial sums of one 4-pixel group, per owner
+  __device__ __forceinline__ void pixels(float v0, float v1, float v2) {
+    comp_add(s0, c0, v0);
+    comp_add(s1, c1, v1);
+    comp_add(s2, c2, v2);
+  }
+  __device__ __forceinline__ void finish() {
+    close_version(slot0, s0 + c0, p0);
+    close_version(slot1, s1 + c1, p1);
+    close_version(slot2, s2 + c2, p2);
+    s0 = s1 = s2 = c0 = c1 = c2 = 0.f;
+  }
+};
+
+struct BwdParams {
+  int32_t n_envs, n_steps, frame_skip, seg, seg_steps, ystart, first;
+  const int4* blocks;
+  const int32_t* perm;
+  const uint8_t* roms;        // rounded ROM images of the rollout [n_carts][8192]
+  const uint8_t* cart_f8;
+  const uint8_t* cart_2k;
+  const DecodeTables* dt;
+  const uint32_t* ckpt;       // this segment's checkpoint [kStateWords][n_envs]
+  const uint8_t* act_bits;    // [n_steps][n_envs]
+  const float* grad_ram;      // [n_steps][n_envs][128] or null
+  const float* grad_screen;   // [n_steps][n_envs][210][160] or null
+  const float* w_ram;         // [128] weights on every step, or null
+  const float* w_screen;      // [210][160] weights on every step, or null
+  uint32_t* rec;              // [n_envs][cap_rec]
+  uint32_t cap_rec;
+  float* cw;                  // [n_envs][cap_cw]
+  uint32_t cap_cw;
+  uint32_t* step_end;         // [seg_steps][n_envs]
+  float* carry;               // [kCarry][n_envs]
+  float* imp;                 // ROM impulses [2][n_envs][8192]: value, compensation
+  float* grad_u;              // [n_steps][n_envs][5] or null
+  float* grad_ram0;           // [n_envs][128] or null (segment 0)
+  float tau;
+  int32_t W;
+  uint32_t sched_policy, sched_window;
+  int32_t* err;
+};
+
+struct Adj {
+  float A, X, Y, V, C0, C1, C2;
+  float u[5], uc[5];   // joystick-input adjoints of the current step (compensated)
+};
+
+// Adjoint of a value read from `ref` (13-bit bus address) flows back to the
+// memory it came from.  RAM cells, ROM impulses and joystick adjoints are
+// compensated sums (value + compensation), since long rollouts add many
+// terms of both signs into them.
+__device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
+                                             const float* izr, int W, float* imp, float* impc, uint32_t f8,
+                                             uint32_t is2k, uint32_t ref, uint32_t fl, float g) {
+  const uint32_t ad = ref & 0x1FFF;
+  if (g == 0.f) return;
+  if (ad & 0x1000) {
+    uint32_t idx = is2k ? (ad & 0x7FF) : ((f8 ? ((fl >> 1) & 1u) << 12 : 0u) | (ad & 0xFFF));
+    float sv = imp[idx], cv = impc[idx];
+    comp_add(sv, cv, g);
+    imp[idx] = sv;
+    impc[idx] = cv;
+  } else if (!(ad & 0x80)) {
+    if ((ad & 0xF) == 0xC) comp_add(a.u[4], a.uc[4], -128.f * g);
+  } else if (!(ad & 0x200)) {
+    const int i = (int)(ad & 0x7F);
+    const int lo = i - W < 0 ? 0 : i - W, hi = i + W > 127 ? 127 : i + W;
+    const float gz = g * izr[i];
+    for (int j = lo; j <= hi; j++) comp_add(aram[j * E], aramc[j * E], __fmul_rn(gz, ek[j > i ? j - i : i - j]));
+  } else if (!(ad & 4)) {
+    if ((ad & 3) == 0) {
+      comp_add(a.u[0], a.uc[0], -128.f * g);
+      comp_add(a.u[1], a.uc[1], -64.f * g);
+      comp_add(a.u[2], a.uc[2], -32.f * g);
+      comp_add(a.u[3], a.uc[3], -16.f * g);
+    }
+  } else if (!(ad & 1) && (fl & 4)) {
+    a.V += g;
+  }
+}
+
+// Adjoint of the value written to `ref`: taken from the cell (which is then
+// cleared, the write being one-hot).
+__device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
+                                            uint32_t& j, uint32_t ref) {
+  const uint32_t ad = ref & 0x1FFF;
+  if (ad & 0x1000) return 0.f;
+  if (!(ad & 0x80)) {
+    const uint32_t reg = ad & 0x3F;
+    float g;
+    if (reg == 0x06) { g = a.C0 + (j ? cw[--j] : 0.f); a.C0 = 0.f; return g; }
+    if (reg == 0x08) { g = a.C1 + (j ? cw[--j] : 0.f); a.C1 = 0.f; return g; }
+    if (reg == 0x09) { g = a.C2 + (j ? cw[--j] : 0.f); a.C2 = 0.f; return g; }
+    return 0.f;
+  }
+  if (!(ad & 0x200)) {
+    const uint32_t o = (ad & 0x7F) * E;
+    float g = aram[o] + aramc[o];
+    aram[o] = 0.f;
+    aramc[o] = 0.f;
+    return g;
+  }
+  if ((ad & 0x14) == 0x14) {
+    float g = a.V;
+    a.V = 0.f;
+    return g;
+  }
+  return 0.f;
+}
+
+__device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
+
+__device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
+                                            const float* izr, int W, float* imp, float* impc, uint32_t f8,
+                                            uint32_t is2k, const float* cw, uint32_t& j, uint32_t rec) {
+  const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
+  switch (op) {
+    case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
+      float g = a.A;
+      a.A = 0.f;
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      break;
+    }
+    case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
+      float g = a.X;
+      a.X = 0.f;
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      break;
+    }
+    case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
+      float g = a.Y;
+      a.Y = 0.f;
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      break;
+    }
+    case 0x09: case 0x05: case 0x15: case 0x0D: case 0x1D: case 0x19: case 0x01: case 0x11:
+    case 0x29: case 0x25: case 0x35: case 0x2D: case 0x3D: case 0x39: case 0x21: case 0x31:
+    case 0x49: case 0x45: case 0x55: case 0x4D: case 0x5D: case 0x59: case 0x41: case 0x51:
+    case 0x69: case 0x65: case 0x75: case 0x6D: case 0x7D: case 0x79: case 0x61: case 0x71:
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, a.A);
+      break;
+    case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, -a.A);
+      break;
+    case 0x85: case 0x95: case 0x8D: case 0x9D: case 0x99: case 0x81: case 0x91:
+      a.A += take_write(a, aram, aramc, E, cw, j, ref);
+      break;
+    case 0x86: case 0x96: case 0x8E:
+      a.X += take_write(a, aram, aramc, E, cw, j, ref);
+      break;
+    case 0x84: case 0x94: case 0x8C:
+      a.Y += take_write(a, aram, aramc, E, cw, j, ref);
+      break;
+    case 0x06: case 0x16: case 0x0E: case 0x1E:
+    case 0x26: case 0x36: case 0x2E: case 0x3E:
+    case 0x46: case 0x56: case 0x4E: case 0x5E:
+    case 0x66: case 0x76: case 0x6E: case 0x7E:
+    case 0xC6: case 0xD6: case 0xCE: case 0xDE:
+    case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
+      float g = take_write(a, aram, aramc, E, cw, j, ref);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      break;
+    }
+    case 0xAA: a.A += a.X; a.X = 0.f; break;   // TAX
+    case 0x8A: a.X += a.A; a.A = 0.f; break;   // TXA
+    case 0xA8: a.A += a.Y; a.Y = 0.f; break;   // TAY
+    case 0x98: a.Y += a.A; a.A = 0.f; break;   // TYA
+    case 0xBA: a.X = 0.f; break;               // TSX: SP carries nothing
+    case 0x48: a.A += take_write(a, aram, aramc, E, cw, j, ref); break;   // PHA
+    case 0x08: take_write(a, aram, aramc, E, cw, j, ref); break;           // PHP
+    case 0x68: {                                                    // PLA
+      float g = a.A;
+      a.A = 0.f;
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      break;
+    }
+    case 0x20:                                                      // JSR: two pushes
+      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
+      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
+      break;
+    case 0x00:                                                      // BRK: three pushes
+      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 2));
+      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
+      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
+      break;
+    default:
+      break;
+  }
+}
+
+// Shared tables of the relaxed read: ek[k] = exp(-k / tau) for k <= W and the
+// inverse window normaliser of every RAM cell.
+__device__ __forceinline__ void read_tables(float* ek, float* izr, float tau, int W) {
+  for (int k = threadIdx.x; k <= W; k += blockDim.x) ek[k] = expf(-(float)k / tau);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+    const int lo = i - W < 0 ? 0 : i - W, hi = i + W > 127 ? 127 : i + W;
+    float z = 0.f;
+    for (int q = lo; q <= hi; q++) z += ek[q > i ? q - i : i - q];
+    izr[i] = 1.f / z;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int E = blockDim.x, tid = threadIdx.x;
+  BlockSmem bs = carve_smem(smem, E);
+  float* aram_s = reinterpret_cast<float*>(smem + smem_bytes(E));   // [128][E]
+  float* aramc_s = aram_s + 128 * E;                                 // [128][E] compensation
+  float* ek = aramc_s + 128 * E;                                     // [kMaxW + 1]
+  float* izr = ek + (kMaxW + 1);                                     // [128]
+  const int4 bi = p.blocks[blockIdx.x];
+  const int cart = bi.x;
+  const uint32_t f8 = p.cart_f8[cart], is2k = p.cart_2k[cart];
+  read_tables(ek, izr, p.tau, p.W);
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * 8192, f8 ? 8192u : 4096u)) {
+    if (tid == 0) atomicExch(p.err, 1);
+    return;
+  }
+  const bool active = tid < bi.z;
+  const int env = active ? p.perm[bi.y + tid] : 0;
+  const int n = p.n_envs;
+  const uint32_t lanes = warp_lanes(E);
+  Ctx c = make_ctx(bs, E, tid, f8, p.ystart);
+  float* aram = aram_s + tid;
+  float* aramc = aramc_s + tid;
+
+  Regs r;
+  if (active) {
+    load_env(soa_at(const_cast<uint32_t*>(p.ckpt), n), n, env, c, r);
+  } else {
+    power_on(c, r);
+  }
+  RecTape tape;
+  tape.buf = p.rec + (size_t)env * p.cap_rec;
+  tape.cw = p.cw + (size_t)env * p.cap_cw;
+  tape.n = 0; tape.cap = p.cap_rec;
+  tape.ncw = 0; tape.capcw = p.cap_cw;
+  tape.slot0 = tape.slot1 = tape.slot2 = -1;
+  tape.s0 = tape.s1 = tape.s2 = 0.f;
+  tape.c0 = tape.c1 = tape.c2 = 0.f;
+  tape.p0 = tape.p1 = tape.p2 = 0.f;
+  tape.overflow = false;
+
+  // 1. recompute the segment, recording the tape
+  const int t0 = p.seg * p.seg_steps;
+  const int t1 = min(t0 + p.seg_steps, p.n_steps);
+  Render rd;
+  rd.on = false;
+  rd.cur = 0;
+  rd.out_u8 = nullptr;
+  rd.out_f32 = nullptr;
+  for (int t = t0; t < t1; t++) {
+    set_input_bits(r, active ? p.act_bits[(size_t)t * n + env] : 0u);
+    Step st;
+    st.frame_skip = p.frame_skip;
+    st.status = 0;
+    rd.gs = p.grad_screen ? p.grad_screen + ((size_t)t * n + env) * (kScreenH * kScreenW) : p.w_screen;
+    st.want_screen = rd.gs != nullptr;
+    run_frames(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
+    if (active) {
+      normalise_timer(r);
+      p.step_end[(size_t)(t - t0) * n + env] = tape.n;
+    }
+  }
+  if (!active) return;
+  tape.finish();
+  if (tape.overflow) {
+    atomicExch(p.err, 2);
+    return;
+  }
+
+  // 2. reverse sweep
+  Adj a;
+  if (p.first) {
+    a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = 0.f;
+    for (int i = 0; i < 128; i++) aram[i * E] = 0.f;
+    for (int i = 0; i < 128; i++) aramc[i * E] = 0.f;
+  } else {
+    const float* cr = p.carry;
+    a.A = cr[0 * n + env]; a.X = cr[1 * n + env]; a.Y = cr[2 * n + env]; a.V = cr[3 * n + env];
+    a.C0 = cr[4 * n + env]; a.C1 = cr[5 * n + env]; a.C2 = cr[6 * n + env];
+    for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
+    for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
+  }
+  float* imp = p.imp + (size_t)env * 8192;
+  float* impc = p.imp + ((size_t)n + env) * 8192;
+  const uint32_t* rec = p.rec + (size_t)env * p.cap_rec;
+  const float* cw = p.cw + (size_t)env * p.cap_cw;
+  uint32_t j = tape.ncw;
+  for (int t = t1 - 1; t >= t0; t--) {
+    const float* gr = p.grad_ram ? p.grad_ram + ((size_t)t * n + env) * 128 : p.w_ram;
+    if (gr)
+      for (int i = 0; i < 128; i++) comp_add(aram[i * E], aramc[i * E], gr[i]);
+    for (int q = 0; q < 5; q++) a.u[q] = a.uc[q] = 0.f;
+    const uint32_t k_end = p.step_end[(size_t)(t - t0) * n + env];
+    const uint32_t k_beg = t > t0 ? p.step_end[(size_t)(t - 1 - t0) * n + env] : 0u;
+    for (uint32_t k = k_end; k > k_beg; k--)
+      reverse_one(a, aram, aramc, E, ek, izr, p.W, imp, impc, f8, is2k, cw, j, rec[k - 1]);
+    if (p.grad_u) {
+      float* gu = p.grad_u + ((size_t)t * n + env) * 5;
+      for (int q = 0; q < 5; q++) gu[q] = a.u[q] + a.uc[q];
+    }
+  }
+  // versions alive at the segment start continue into the previous segment
+  a.C0 += tape.p0;
+  a.C1 += tape.p1;
+  a.C2 += tape.p2;
+  if (p.seg == 0) {
+    if (p.grad_ram0)
+      for (int i = 0; i < 128; i++) p.grad_ram0[(size_t)env * 128 + i] = aram[i * E] + aramc[i * E];
+  } else {
+    float* cr = p.carry;
+    cr[0 * n + env] = a.A; cr[1 * n + env] = a.X; cr[2 * n + env] = a.Y; cr[3 * n + env] = a.V;
+    cr[4 * n + env] = a.C0; cr[5 * n + env] = a.C1; cr[6 * n + env] = a.C2;
+    for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
+    for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
+  }
+}
+
+size_t bwd_smem_bytes(int E) { return smem_bytes(E) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4; }
+
+// ROM impulses -> ROM gradient: spread each impulse at a over the read
+// window of its tensor (the 2K image, the 4K image, or one F8 bank) with the
+// relaxed read's weights.  One thread per (env, ROM byte).
+__global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_cart, const uint8_t* cart_f8,
+                             const uint8_t* cart_2k, int32_t n_envs, float tau, int32_t W) {
+  __shared__ float ek[kMaxW + 2];
+  __shared__ float suf[kMaxW + 2];   // suf[k] = sum_{q = k..W} ek[q]
+  for (int k = threadIdx.x; k <= W; k += blockDim.x) ek[k] = expf(-(float)k / tau);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float acc = 0.f;
+    suf[W + 1] = 0.f;
+    for (int k = W; k >= 0; k--) {
+      acc += ek[k];
+      suf[k] = acc;
+    }
+  }
+  __syncthreads();
+  const int env = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (env >= n_envs || i >= 8192) return;
+  const int cart = env_cart[env];
+  const int M = cart_2k[cart] ? 2048 : 4096;
+  float* o = out + (size_t)env * 8192;
+  if (i >= (cart_f8[cart] ? 8192 : M)) {
+    o[i] = 0.f;
+    return;
+  }
+  const int base = i & ~(M - 1);
+  const int ii = i - base;
+  const float* im = imp + (size_t)env * 8192 + base;
+  const float* imc = imp + ((size_t)n_envs + env) * 8192 + base;
+  const int lo = ii - W < 0 ? 0 : ii - W, hi = ii + W > M - 1 ? M - 1 : ii + W;
+  const float zint = ek[0] + 2.f * suf[1];
+  float acc = 0.f;
+  for (int q = lo; q <= hi; q++) {
+    const float v = im[q] + imc[q];
+    if (v == 0.f) continue;
+    float z = zint;
+    if (q < W) z -= suf[q + 1];
+    if (M - 1 - q < W) z -= suf[M - q];
+    acc += v * ek[q > ii ? q - ii : ii - q] / z;
+  }
+  o[i] = acc;
+}
+
+// Per-cart sum of the per-env ROM gradients: envs of cart c are slots
+// cart_begin[c] .. cart_begin[c+1]-1 of perm; a fixed order, no atomics.
+__global__ void k_cart_reduce(const float* grad_rom, float* out, const int32_t* perm, const int32_t* cart_begin,
+                              int32_t n_carts) {
+  const int c = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_carts || i >= 8192) return;
+  float acc = 0.f;
+  for (int s = cart_begin[c]; s < cart_begin[c + 1]; s++) acc += grad_rom[(size_t)perm[s] * 8192 + i];
+  out[(size_t)c * 8192 + i] = acc;
+}
+
+// Rounded ROM bytes from the float ROM tensor (forward value of the STE
+// round), 2K images mirrored into 4 KB like the hard path's copy.
+__global__ void k_rom_round(const float* rom_f32, uint8_t* out, const uint8_t* cart_2k, int32_t n_carts) {
+  const int c = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_carts || i >= 8192) return;
+  const int src = cart_2k[c] ? (i & 2047) : i;
+  float v = rintf(rom_f32[(size_t)c * 8192 + src]);
+  out[(size_t)c * 8192 + i] = (uint8_t)(v <= 0.f ? 0.f : (v >= 255.f ? 255.f : v));
+}
+
+}  // namespace vcs
+
+using namespace vcs;
+
+struct vcs_tape {
+  vcs_batch* b = nullptr;
+  int32_t n_steps = 0, frame_skip = 1, seg_steps = 1, n_seg = 0, W = 1;
+  float tau = 1.f;
+  uint8_t* rom_bytes = nullptr;
+  uint32_t* ckpt = nullptr;
+  uint8_t* act_bits = nullptr;
+  uint32_t* seg_counts = nullptr;
+  // backward scratch (allocated by the first vcs_backward)
+  uint32_t* rec = nullptr;
+  size_t cap_rec = 0;
+  float* cw = nullptr;
+  size_t cap_cw = 0;
+  uint32_t* step_end = nullptr;
+  float* carry = nullptr;
+  float* imp = nullptr;
+  float* grad_rom_tmp = nullptr;
+};
+
+static void free_tape(vcs_tape* t) {
+  if (!t) return;
+  cudaFree(t->rom_bytes);
+  cudaFree(t->ckpt);
+  cudaFree(t->act_bits);
+  cudaFree(t->seg_counts);
+  cudaFree(t->rec);
+  cudaFree(t->cw);
+  cudaFree(t->step_end);
+  cudaFree(t->carry);
+  cudaFree(t->imp);
+  cudaFree(t->grad_rom_tmp);
+  delete t;
+}
+
+static int half_width(float tau) {
+  int w = (int)std::ceil(12.0 * (double)tau);
+  return w < 1 ? 1 : w;
+}
+
+extern "C" {
+
+vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const float* ram0, const float* u,
+                            int32_t n_steps, int32_t frame_skip, float* ram_out, float* screen_out,
+                            vcs_tape** tape_out, void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  if (!tape_out) return vcs_fail(b, VCS_ERR_ARG, "tape_out is NULL");
+  *tape_out = nullptr;
+  if (!u) return vcs_fail(b, VCS_ERR_ARG, "u (joystick inputs) is NULL");
+  if (!(tau > 0.f) || !(tau <= 10.f)) return vcs_fail(b, VCS_ERR_ARG, "tau must be in (0, 10]");
+  if (n_steps < 1 || frame_skip < 1) return vcs_fail(b, VCS_ERR_ARG, "n_steps >= 1 and frame_skip >= 1 required");
+  vcs_tape* t = new (std::nothrow) vcs_tape;
+  if (!t) return vcs_fail(b, VCS_ERR_OOM, "host allocation failed");
+  t->b = b;
+  t->n_steps = n_steps;
+  t->frame_skip = frame_skip;
+  t->tau = tau;
+  t->W = half_width(tau);
+  t->seg_steps = b->cfg.segment_frames / frame_skip > 0 ? b->cfg.segment_frames / frame_skip : 1;
+  t->n_seg = (n_steps + t->seg_steps - 1) / t->seg_steps;
+  const size_t n = (size_t)b->n_envs;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMalloc(&t->rom_bytes, (size_t)b->n_carts * 8192)) ||
+      (e = cudaMalloc(&t->ckpt, (size_t)t->n_seg * kStateWords * n * 4)) ||
+      (e = cudaMalloc(&t->act_bits, (size_t)n_steps * n)) ||
+      (e = cudaMalloc(&t->seg_counts, (size_t)t->n_seg * 2 * 4))) {
+    vcs_status st = vcs_cuda_fail(b, e, "tape allocation");
+    free_tape(t);
+    return st;
+  }
+  cudaMemsetAsync(t->seg_counts, 0, (size_t)t->n_seg * 2 * 4, s);
+  if (rom_f32) {
+    dim3 grid(8192 / 256, b->n_carts);
+    k_rom_round<<<grid, 256, 0, s>>>(rom_f32, t->rom_bytes, b->cart_2k, b->n_carts);
+  } else {
+    cudaMemcpyAsync(t->rom_bytes, b->roms, (size_t)b->n_carts * 8192, cudaMemcpyDeviceToDevice, s);
+  }
+  StepParams p = vcs_base_params(b);
+  p.roms = t->rom_bytes;
+  p.n_steps = n_steps;
+  p.frame_skip = frame_skip;
+  p.u = u;
+  p.ram0 = ram0;
+  p.act_bits = t->act_bits;
+  p.ram_out_f = ram_out;
+  p.screen_out_f = screen_out;
+  p.ckpt = t->ckpt;
+  p.seg_steps = t->seg_steps;
+  p.seg_counts = t->seg_counts;
+  int le = launch_soft_forward(p, b->n_blocks, b->E, stream);
+  if (le) {
+    vcs_status st = vcs_cuda_fail(b, (cudaError_t)le, "soft forward launch");
+    free_tape(t);
+    return st;
+  }
+  *tape_out = t;
+  return VCS_OK;
+}
+
+vcs_status vcs_tape_free(vcs_tape* t) {
+  if (!t) return VCS_ERR_ARG;
+  free_tape(t);
+  return VCS_OK;
+}
+
+vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_screen, const vcs_loss_weights* w,
+                        float* grad_rom, float* grad_ram0, float* grad_u, float* grad_rom_per_cart, void* stream) {
+  if (!t || !t->b) return VCS_ERR_ARG;
+  vcs_batch* b = t->b;
+  if ((grad_ram || grad_screen) && w && (w->ram || w->screen))
+    return vcs_fail(b, VCS_ERR_ARG, "give either per-step gradients or loss weights, not both");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const size_t n = (size_t)b->n_envs;
+  // size the tape from the forward's per-segment counts
+  std::vector<uint32_t> counts((size_t)t->n_seg * 2);
+  if ((e = cudaMemcpyAsync(counts.data(), t->seg_counts, counts.size() * 4, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return vcs_cuda_fail(b, e, "tape sizes");
+  size_t need_rec = 1, need_cw = 1;
+  for (int q = 0; q < t->n_seg; q++) {
+    need_rec = std::max<size_t>(need_rec, counts[2 * q]);
+    need_cw = std::max<size_t>(need_cw, counts[2 * q + 1]);
+  }
+  if (need_rec > t->cap_rec) {
+    cudaFree(t->rec);
+    t->rec = nullptr;
+    if ((e = cudaMalloc(&t->rec, need_rec * n * 4))) return vcs_cuda_fail(b, e, "tape allocation");
+    t->cap_rec = need_rec;
+  }
+  if (need_cw > t->cap_cw) {
+    cudaFree(t->cw);
+    t->cw = nullptr;
+    if ((e = cudaMalloc(&t->cw, need_cw * n * 4))) return vcs_cuda_fail(b, e, "tape allocation");
+    t->cap_cw = need_cw;
+  }
+  if (!t->step_end) {
+    if ((e = cudaMalloc(&t->step_end, (size_t)t->seg_steps * n * 4)) ||
+        (e = cudaMalloc(&t->carry, (size_t)kCarry * n * 4)) || (e = cudaMalloc(&t->imp, 2 * n * 8192 * 4)))
+      return vcs_cuda_fail(b, e, "backward scratch");
+  }
+  float* grom = grad_rom;
+  if (!grom && grad_rom_per_cart) {
+    if (!t->grad_rom_tmp && (e = cudaMalloc(&t->grad_rom_tmp, n * 8192 * 4)))
+      return vcs_cuda_fail(b, e, "backward scratch");
+    grom = t->grad_rom_tmp;
+  }
+  cudaMemsetAsync(t->imp, 0, 2 * n * 8192 * 4, s);
+
+  BwdParams p{};
+  p.n_envs = b->n_envs;
+  p.n_steps = t->n_steps;
+  p.frame_skip = t->frame_skip;
+  p.seg_steps = t->seg_steps;
+  p.ystart = b->cfg.ystart;
+  p.blocks = b->blocks;
+  p.perm = b->perm;
+  p.roms = t->rom_bytes;
+  p.cart_f8 = b->cart_f8;
+  p.cart_2k = b->cart_2k;
+  p.dt = b->dt;
+  p.act_bits = t->act_bits;
+  p.grad_ram = grad_ram;
+  p.grad_screen = grad_screen;
+  p.w_ram = w ? w->ram : nullptr;
+  p.w_screen = w ? w->screen : nullptr;
+  p.rec = t->rec;
+  p.cap_rec = (uint32_t)t->cap_rec;
+  p.cw = t->cw;
+  p.cap_cw = (uint32_t)t->cap_cw;
+  p.step_end = t->step_end;
+  p.carry = t->carry;
+  p.imp = t->imp;
+  p.grad_u = grad_u;
+  p.grad_ram0 = grad_ram0;
+  p.tau = t->tau;
+  p.W = t->W;
+  p.sched_policy = b->sched_policy;
+  p.sched_window = b->sched_window;
+  p.err = b->err;
+  const size_t smem = bwd_smem_bytes(b->E);
+  if ((e = cudaFuncSetAttribute(k_soft_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return vcs_cuda_fail(b, e, "backward shared memory");
+  for (int q = t->n_seg - 1; q >= 0; q--) {
+    p.seg = q;
+    p.first = q == t->n_seg - 1;
+    p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
+    k_soft_bwd<<<b->n_blocks, b->E, smem, s>>>(p);
+    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
+  }
+  if (grom) {
+    dim3 grid(8192 / 256, b->n_envs);
+    k_rom_spread<<<grid, 256, 0, s>>>(t->imp, grom, b->env_cart_dev, b->cart_f8, b->cart_2k, b->n_envs, t->tau,
+                                      t->W);
+    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "ROM spread launch");
+  }
+  if (grad_rom_per_cart) {
+    dim3 grid(8192 / 256, b->n_carts);
+    k_cart_reduce<<<grid, 256, 0, s>>>(grom, grad_rom_per_cart, b->perm, b->cart_begin, b->n_carts);
+    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "per-cart reduction launch");
+  }
+  return VCS_OK;
+}
+
+}  // extern "C"

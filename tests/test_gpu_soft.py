@@ -1,0 +1,189 @@
+"""SOFT-STE on the GPU against the oracle (FP64).
+
+* Theorem 1: the soft forward's RAM and screens equal the hard path's bit
+  for bit at tau in {1, 0.1, 0.01};
+* Corollary 1 / the surrogate rulebook: the CUDA backward (FP32) equals the
+  oracle's FP64 reverse sweep to 1e-5 relative, per output tensor and env:
+  max |g - g64| <= 1e-5 max(|g64|_inf, 1e-30) (normwise), and
+  |g - g64| <= 1e-5 |g64| wherever |g64| >= 1e-2 |g64|_inf (elementwise, for
+  entries within 100x of the largest: float32 adjoints carry an absolute
+  error of a few units in the last place of the largest terms they
+  combine, so smaller entries are held to the normwise bound only)
+  (ROM bytes per env, initial RAM, joystick inputs);
+* checkpoint/recompute over several segments gives the same gradient as one
+  segment; broadcast loss weights equal the dense gradients they expand to;
+  the autograd Function returns the C ABI's gradients.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_22447_b300 import synth
+from tests.gpu_util import gpu_rollout, make_batch, torch_cuda
+
+pytestmark = pytest.mark.gpu
+REL = 1e-5
+
+
+def assert_grad_close(got, want, what):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    scale = max(np.abs(want).max(), 1e-30)
+    err = np.abs(got - want)
+    assert err.max() <= REL * scale, f"{what}: max abs err {err.max():.3e} vs scale {scale:.3e}"
+    big = np.abs(want) >= 1e-2 * scale
+    if big.any():
+        r = np.where(big, err / np.where(big, np.abs(want), 1.0), 0.0)
+        k = np.unravel_index(np.argmax(r), r.shape)
+        assert r[k] <= REL, (f"{what}: elementwise rel err {r[k]:.3e} at {k}: got {got[k]:.9e} "
+                             f"want {want[k]:.9e} (scale {scale:.3e})")
+
+
+def _setup(mappers, n_envs, n_steps, seed, warm=2, frame_skip=1, **cfg):
+    torch = torch_cuda()
+    roms = synth.config_carts(seed, mappers)
+    env_cart = (np.arange(n_envs) % len(mappers)).astype(np.int32)
+    b = make_batch(roms, mappers, env_cart, **cfg)
+    wa = synth.actions(seed + 1, n_envs, warm)
+    gpu_rollout(b, wa, 1, screens=False)          # start from a state a few frames in
+    acts = synth.actions(seed, n_envs, n_steps)
+    u = synth.action_inputs(acts)                  # [n_steps][n_envs][5]
+    return torch, roms, env_cart, b, wa, acts, u
+
+
+def _oracle_grads(rom, mapper, warm_acts, u, frame_skip, tau, gr, gs):
+    o = oracle.Oracle(rom, mapper)
+    o.rollout(warm_acts, 1, screens=False)
+    g, ram_out, scr_out = o.soft_rollout(u.astype(np.float64), frame_skip, tau, 6.0,
+                                         None if gr is None else gr.astype(np.float64),
+                                         None if gs is None else gs.astype(np.float64))
+    return g.reverse(), ram_out, scr_out
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.1, 0.01])
+def test_theorem1_soft_forward_equals_hard(tau):
+    torch, roms, env_cart, b, wa, acts, u = _setup(synth.MIX16[::3], 24, 6, 31)
+    blob = b.save_state()
+    ram_h, scr_h, _ = gpu_rollout(b, acts, 2)
+    b.load_state(blob)
+    ram_s = torch.empty((6, 24, 128), device="cuda")
+    scr_s = torch.empty((6, 24, 210, 160), device="cuda")
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 2, ram_out=ram_s, screen_out=scr_s)
+    b.sync()
+    assert np.array_equal(ram_s.cpu().numpy(), ram_h.astype(np.float32))
+    assert np.array_equal(scr_s.cpu().numpy(), scr_h.astype(np.float32))
+    # and the batch state advanced exactly as the hard path's
+    blob_soft = b.save_state()
+    b.load_state(blob)
+    gpu_rollout(b, acts, 2, screens=False)
+    assert np.array_equal(b.save_state(), blob_soft)
+    tape.free()
+
+
+@pytest.mark.parametrize("tau,frame_skip", [(1.0, 1), (0.1, 1), (0.01, 1), (0.1, 2)])
+def test_gradients_match_fp64_oracle(tau, frame_skip):
+    mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
+    n_envs, n_steps = 6, 4
+    torch, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 41, frame_skip=frame_skip)
+    gr = synth.normal_f32(41, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(41, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), frame_skip)
+    g_rom = torch.empty((n_envs, 8192), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u)
+    b.sync()
+    g_rom, g_ram0, g_u = g_rom.cpu().numpy(), g_ram0.cpu().numpy(), g_u.cpu().numpy()
+    for e in range(n_envs):
+        c = env_cart[e]
+        (o_rom, o_ram0, o_u), _, _ = _oracle_grads(roms[c], mappers[c], wa[:, e], u[:, e], frame_skip, tau,
+                                                   gr[:, e], gs[:, e])
+        size = len(roms[c])
+        assert_grad_close(g_rom[e, :size], o_rom, f"grad_rom env {e}")
+        assert np.all(g_rom[e, size:] == 0)
+        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
+        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+        assert np.abs(o_rom).max() > 0
+
+
+def test_segments_and_loss_weights_and_per_cart_sum():
+    torch = torch_cuda()
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8]
+    n_envs, n_steps = 8, 9
+    seed = 51
+    res = {}
+    for seg in (64, 3):
+        _, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, seed, segment_frames=seg)
+        wr = synth.normal_f32(seed, (128,), 3)
+        ws = synth.normal_f32(seed, (210, 160), 4)
+        tape = b.soft_rollout(0.1, torch.from_numpy(u).cuda(), 1)
+        out = {}
+        for mode in ("weights", "dense"):
+            g_rom = torch.empty((n_envs, 8192), device="cuda")
+            g_pc = torch.empty((2, 8192), device="cuda")
+            g_ram0 = torch.empty((n_envs, 128), device="cuda")
+            g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+            if mode == "weights":
+                tape.backward(w_ram=torch.from_numpy(wr).cuda(), w_screen=torch.from_numpy(ws).cuda(),
+                              grad_rom=g_rom, grad_ram0=g_ram0, grad_u=g_u, grad_rom_per_cart=g_pc)
+            else:
+                gr = np.broadcast_to(wr, (n_steps, n_envs, 128)).copy()
+                gs = np.broadcast_to(ws, (n_steps, n_envs, 210, 160)).copy()
+                tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom,
+                              grad_ram0=g_ram0, grad_u=g_u, grad_rom_per_cart=g_pc)
+            b.sync()
+            out[mode] = [x.cpu().numpy() for x in (g_rom, g_ram0, g_u, g_pc)]
+        for x, y in zip(out["weights"], out["dense"]):
+            assert_grad_close(x, y, "weights vs dense")
+        # per-cart sum = sum of the per-env rows of that cart
+        g_rom, _, _, g_pc = out["dense"]
+        for c in range(2):
+            assert_grad_close(g_pc[c], g_rom[env_cart == c].sum(0), "per-cart sum")
+        res[seg] = out["dense"]
+        # oracle on two envs
+        for e in (0, 5):
+            c = env_cart[e]
+            (o_rom, o_ram0, o_u), _, _ = _oracle_grads(roms[c], mappers[c], wa[:, e], u[:, e], 1, 0.1,
+                                                       np.broadcast_to(wr, (n_steps, 128)),
+                                                       np.broadcast_to(ws, (n_steps, 210, 160)))
+            assert_grad_close(g_rom[e, :len(roms[c])], o_rom, "grad_rom")
+            assert_grad_close(res[seg][1][e], o_ram0, "grad_ram0")
+            assert_grad_close(res[seg][2][:, e], o_u, "grad_u")
+    for x, y in zip(res[64], res[3]):
+        assert_grad_close(x, y, "3-frame segments vs one segment")
+
+
+def test_autograd_function_and_float_inputs():
+    torch = torch_cuda()
+    from paper_2606_22447_b300.autograd import soft_rollout
+    mappers = [synth.MAPPER_2K, synth.MAPPER_4K]
+    n_envs, n_steps = 4, 3
+    _, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 61)
+    rom_f = np.zeros((2, 8192), np.float32)
+    for c, r in enumerate(roms):
+        rom_f[c, :len(r)] = np.frombuffer(r, np.uint8)
+    ram0 = synth.normal_f32(61, (n_envs, 128), 5) * 0 + np.arange(128, dtype=np.float32)[None] % 256
+    rom_t = torch.from_numpy(rom_f).cuda().requires_grad_()
+    ram0_t = torch.from_numpy(ram0.astype(np.float32)).cuda().requires_grad_()
+    u_t = torch.from_numpy(u).cuda().requires_grad_()
+    ram, scr = soft_rollout(b, rom_t, ram0_t, u_t, tau=0.1, frame_skip=1)
+    gr = synth.normal_f32(61, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(61, (n_steps, n_envs, 210, 160), 2)
+    loss = (ram * torch.from_numpy(gr).cuda()).sum() + (scr * torch.from_numpy(gs).cuda()).sum()
+    g_rom, g_ram0, g_u = torch.autograd.grad(loss, [rom_t, ram0_t, u_t])
+    g_rom, g_ram0, g_u = g_rom.cpu().numpy(), g_ram0.cpu().numpy(), g_u.cpu().numpy()
+    want_pc = np.zeros((2, 8192))
+    for e in range(n_envs):
+        c = env_cart[e]
+        o = oracle.Oracle(roms[c], mappers[c])
+        o.rollout(wa[:, e], 1, screens=False)
+        o.set_ram(ram0[e].astype(np.uint8))
+        g, ram_o, _ = o.soft_rollout(u[:, e].astype(np.float64), 1, 0.1, 6.0, gr[:, e].astype(np.float64),
+                                     gs[:, e].astype(np.float64))
+        assert np.array_equal(ram.detach().cpu().numpy()[:, e], ram_o.astype(np.float32))
+        o_rom, o_ram0, o_u = g.reverse()
+        want_pc[c, :len(roms[c])] += o_rom
+        assert_grad_close(g_ram0[e], o_ram0, "grad_ram0 through autograd")
+        assert_grad_close(g_u[:, e], o_u, "grad_u through autograd")
+    assert_grad_close(g_rom, want_pc, "per-cart ROM gradient through autograd")
