@@ -203,6 +203,30 @@ vcs_status vcs_backward(vcs_tape* tape, const float* grad_ram, const float* grad
                         float* grad_u, float* grad_rom_per_cart, void* stream);
 vcs_status vcs_tape_free(vcs_tape* tape);
 
+/* vcs_backward without any device allocation (the paper has no counterpart:
+ * this is a deployment variant).  For callers that cannot let a library
+ * allocate device memory: an application whose GPU memory is owned by an
+ * allocator it does not control (for instance a framework's caching pool
+ * that has reserved the device) or that runs under a fixed device-memory
+ * budget, where a cudaMalloc behind its back can fail or fragment the pool.
+ * Same arguments and results as vcs_backward; the caller passes the tape,
+ * inputs and outputs, and all scratch (tape entries, adjoint carries, ROM
+ * impulses) comes from one fixed 64 MiB array compiled into the library,
+ * which every GPU that loads the library keeps until the process exits.
+ *  - Problems whose scratch does not fit (roughly n_envs x instructions per
+ *    checkpoint segment x 4 bytes, plus 64 KB per env) are rejected with
+ *    VCS_ERR_ARG and a message giving the size needed.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the array and it keeps the last call's contents (the
+ *    call clears what must start at zero); calls whose GPU work overlaps,
+ *    on two streams or two host threads, race with each other.
+ *  - It synchronises `stream` once to read the tape's sizes. */
+vcs_status vcs_backward_static(vcs_tape* tape, const float* grad_ram, const float* grad_screen,
+                               const vcs_loss_weights* w, float* grad_rom, float* grad_ram0,
+                               float* grad_u, float* grad_rom_per_cart, void* stream);
+
 /* Copy the machine state out / in as an opaque blob (checkpoint/resume).
  * vcs_state_bytes gives the size; blob is a host pointer; both calls
  * synchronise `stream`. */

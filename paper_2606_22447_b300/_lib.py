@@ -59,6 +59,7 @@ SIGNATURES = {
     "vcs_soft_rollout": (C.c_int, [vp, C.c_float, vp, vp, vp, i32, i32, vp, vp, C.POINTER(vp), vp]),
     "vcs_backward": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "vcs_tape_free": (C.c_int, [vp]),
+    "vcs_backward_static": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
 }
 
 _lib = None

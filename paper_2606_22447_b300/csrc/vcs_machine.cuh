@@ -183,15 +183,15 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       }
       tape.pixels(acc[0], acc[1], acc[2]);
     }
-    return;
-  }
-  for (uint32_t g = g0; g < g1; g++) {
-    uint32_t w = (blank_all || g < blank_g) ? 0u : group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk);
-    uint32_t mask = 0xFFFFFFFFu;
-    if (g == g0) mask <<= 8 * (x0 & 3);
-    if (g == g1 - 1 && (x1 & 3)) mask &= 0xFFFFFFFFu >> (8 * (4 - (x1 & 3)));
-    uint32_t* dst = c.line + g * c.E;
-    *dst = mask == 0xFFFFFFFFu ? w : ((*dst & ~mask) | (w & mask));
+  } else {
+    for (uint32_t g = g0; g < g1; g++) {
+      uint32_t w = (blank_all || g < blank_g) ? 0u : group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk);
+      uint32_t mask = 0xFFFFFFFFu;
+      if (g == g0) mask <<= 8 * (x0 & 3);
+      if (g == g1 - 1 && (x1 & 3)) mask &= 0xFFFFFFFFu >> (8 * (4 - (x1 & 3)));
+      uint32_t* dst = c.line + g * c.E;
+      *dst = mask == 0xFFFFFFFFu ? w : ((*dst & ~mask) | (w & mask));
+    }
   }
 }
 

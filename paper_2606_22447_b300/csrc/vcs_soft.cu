@@ -27,8 +27,10 @@
 // the envs of each cart, no atomics).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -678,3 +680,146 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Backward pass that allocates nothing (vcs_backward_static).
+//
+// Some callers cannot let a library allocate device memory: an application
+// whose GPU memory is owned by an allocator it does not control (a
+// framework's caching pool that has reserved the device, say), or one held
+// to a fixed device-memory budget, where a cudaMalloc behind its back can
+// fail or fragment the pool.  This variant of the backward pass takes all of
+// its scratch (tape, adjoint carries, ROM impulses) from one fixed array
+// compiled into the library.  Every GPU that loads the library keeps this
+// array until the process exits.  All calls share it and it keeps the last
+// call's contents, so calls whose work overlaps on the GPU race with each
+// other.
+// ---------------------------------------------------------------------------
+
+static constexpr size_t kStaticScratchBytes = 64ull << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_backward_scratch[kStaticScratchBytes];
+
+static std::mutex g_scratch_mutex;
+static void* g_scratch_ptr[64] = {};
+
+// Device address of the static scratch on the current device; looked up once
+// per device (the array's host-side name is not a device address).
+static cudaError_t static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_backward_scratch);
+    if (e) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, const float* grad_screen,
+                                          const vcs_loss_weights* w, float* grad_rom, float* grad_ram0,
+                                          float* grad_u, float* grad_rom_per_cart, void* stream) {
+  if (!t || !t->b) return VCS_ERR_ARG;
+  vcs_batch* b = t->b;
+  if ((grad_ram || grad_screen) && w && (w->ram || w->screen))
+    return vcs_fail(b, VCS_ERR_ARG, "give either per-step gradients or loss weights, not both");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  void* base = nullptr;
+  if ((e = static_scratch(&base))) return vcs_cuda_fail(b, e, "static scratch address");
+  const size_t n = (size_t)b->n_envs;
+  // tape sizes from the forward's per-segment counts (a copy, no allocation)
+  uint32_t counts[2 * 64];
+  std::vector<uint32_t> counts_big;
+  uint32_t* cnt = counts;
+  if (t->n_seg > 64) {
+    counts_big.assign((size_t)t->n_seg * 2, 0);
+    cnt = counts_big.data();
+  }
+  if ((e = cudaMemcpyAsync(cnt, t->seg_counts, (size_t)t->n_seg * 2 * 4, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return vcs_cuda_fail(b, e, "tape sizes");
+  size_t cap_rec = 1, cap_cw = 1;
+  for (int q = 0; q < t->n_seg; q++) {
+    cap_rec = std::max<size_t>(cap_rec, cnt[2 * q]);
+    cap_cw = std::max<size_t>(cap_cw, cnt[2 * q + 1]);
+  }
+  const bool need_tmp = !grad_rom && grad_rom_per_cart;
+  const size_t o_carry = 0;
+  const size_t o_step = align256(o_carry + (size_t)kCarry * n * 4);
+  const size_t o_imp = align256(o_step + (size_t)t->seg_steps * n * 4);
+  const size_t o_tmp = align256(o_imp + 2 * n * 8192 * 4);
+  const size_t o_rec = align256(o_tmp + (need_tmp ? n * 8192 * 4 : 0));
+  const size_t o_cw = align256(o_rec + cap_rec * n * 4);
+  const size_t total = align256(o_cw + cap_cw * n * 4);
+  if (total > kStaticScratchBytes)
+    return vcs_fail(b, VCS_ERR_ARG,
+                    "vcs_backward_static needs %zu bytes of scratch for %zu envs (%zu instructions per segment), "
+                    "above its fixed %zu-byte array; use vcs_backward or fewer envs / shorter segments",
+                    total, n, cap_rec, kStaticScratchBytes);
+  unsigned char* sc = static_cast<unsigned char*>(base);
+  float* imp = reinterpret_cast<float*>(sc + o_imp);
+  float* grom = grad_rom ? grad_rom : (need_tmp ? reinterpret_cast<float*>(sc + o_tmp) : nullptr);
+  // the impulses are sums and must start at zero; everything else is
+  // written before it is read
+  if ((e = cudaMemsetAsync(imp, 0, 2 * n * 8192 * 4, s))) return vcs_cuda_fail(b, e, "scratch clear");
+
+  BwdParams p{};
+  p.n_envs = b->n_envs;
+  p.n_steps = t->n_steps;
+  p.frame_skip = t->frame_skip;
+  p.seg_steps = t->seg_steps;
+  p.ystart = b->cfg.ystart;
+  p.blocks = b->blocks;
+  p.perm = b->perm;
+  p.roms = t->rom_bytes;
+  p.cart_f8 = b->cart_f8;
+  p.cart_2k = b->cart_2k;
+  p.dt = b->dt;
+  p.act_bits = t->act_bits;
+  p.grad_ram = grad_ram;
+  p.grad_screen = grad_screen;
+  p.w_ram = w ? w->ram : nullptr;
+  p.w_screen = w ? w->screen : nullptr;
+  p.rec = reinterpret_cast<uint32_t*>(sc + o_rec);
+  p.cap_rec = (uint32_t)cap_rec;
+  p.cw = reinterpret_cast<float*>(sc + o_cw);
+  p.cap_cw = (uint32_t)cap_cw;
+  p.step_end = reinterpret_cast<uint32_t*>(sc + o_step);
+  p.carry = reinterpret_cast<float*>(sc + o_carry);
+  p.imp = imp;
+  p.grad_u = grad_u;
+  p.grad_ram0 = grad_ram0;
+  p.tau = t->tau;
+  p.W = t->W;
+  p.sched_policy = b->sched_policy;
+  p.sched_window = b->sched_window;
+  p.err = b->err;
+  const size_t smem = bwd_smem_bytes(b->E);
+  if ((e = cudaFuncSetAttribute(k_soft_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return vcs_cuda_fail(b, e, "backward shared memory");
+  for (int q = t->n_seg - 1; q >= 0; q--) {
+    p.seg = q;
+    p.first = q == t->n_seg - 1;
+    p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
+    k_soft_bwd<<<b->n_blocks, b->E, smem, s>>>(p);
+    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
+  }
+  if (grom) {
+    dim3 grid(8192 / 256, b->n_envs);
+    k_rom_spread<<<grid, 256, 0, s>>>(imp, grom, b->env_cart_dev, b->cart_f8, b->cart_2k, b->n_envs, t->tau, t->W);
+    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "ROM spread launch");
+  }
+  if (grad_rom_per_cart) {
+    dim3 grid(8192 / 256, b->n_carts);
+    k_cart_reduce<<<grid, 256, 0, s>>>(grom, grad_rom_per_cart, b->perm, b->cart_begin, b->n_carts);
+    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "per-cart reduction launch");
+  }
+  return VCS_OK;
+}

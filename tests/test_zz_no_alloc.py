@@ -1,0 +1,73 @@
+"""vcs_backward_static: the backward pass for callers that cannot let a
+library allocate device memory (an application whose GPU memory belongs to
+an allocator it does not control, or one held to a fixed device-memory
+budget).  It must give the same gradients as vcs_backward, on two calls in a
+row (the fixed scratch array keeps the previous call's contents), and reject
+problems whose scratch does not fit the array with a clear error.
+
+This file is named so that pytest collects it last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2606_22447_b300 import _lib, synth
+from tests.gpu_util import gpu_rollout, make_batch, torch_cuda
+
+pytestmark = pytest.mark.gpu
+REL = 1e-5
+
+
+def _close(got, want, what):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    scale = max(np.abs(want).max(), 1e-30)
+    assert np.abs(got - want).max() <= REL * scale, what
+
+
+def _grads(entry, tape, gr, gs, n_envs, n_steps, n_carts):
+    torch = torch_cuda()
+    out = [torch.full((n_envs, 8192), 7.0, device="cuda"), torch.full((n_envs, 128), 7.0, device="cuda"),
+           torch.full((n_steps, n_envs, 5), 7.0, device="cuda"), torch.full((n_carts, 8192), 7.0, device="cuda")]
+    p = lambda t: C.c_void_p(t.data_ptr())
+    st = getattr(_lib.load(), entry)(tape.h, p(gr), p(gs), None, *[p(t) for t in out],
+                                     C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _lib.check(st, tape.batch.h)
+    tape.batch.sync()
+    return [t.cpu().numpy() for t in out]
+
+
+def test_static_backward_matches_backward_on_two_calls():
+    torch = torch_cuda()
+    mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
+    n_envs, n_steps = 12, 5
+    roms = synth.config_carts(71, mappers)
+    env_cart = (np.arange(n_envs) % 3).astype(np.int32)
+    b = make_batch(roms, mappers, env_cart, segment_frames=2)
+    gpu_rollout(b, synth.actions(72, n_envs, 2), 1, screens=False)
+    u = torch.from_numpy(synth.action_inputs(synth.actions(71, n_envs, n_steps))).cuda()
+    tape = b.soft_rollout(0.3, u, 1)
+    gr = torch.from_numpy(synth.normal_f32(71, (n_steps, n_envs, 128), 1)).cuda()
+    gs = torch.from_numpy(synth.normal_f32(71, (n_steps, n_envs, 210, 160), 2)).cuda()
+    want = _grads("vcs_backward", tape, gr, gs, n_envs, n_steps, 3)
+    assert np.abs(want[0]).max() > 0 and np.abs(want[3]).max() > 0
+    for call in range(2):
+        got = _grads("vcs_backward_static", tape, gr, gs, n_envs, n_steps, 3)
+        for g, w, name in zip(got, want, ("grad_rom", "grad_ram0", "grad_u", "grad_rom_per_cart")):
+            _close(g, w, f"call {call}: {name}")
+
+
+def test_static_backward_rejects_oversized_problems():
+    torch = torch_cuda()
+    rom = synth.generate_cart(73, 0, synth.MAPPER_4K)
+    n_envs = 2048
+    b = make_batch([rom], [synth.MAPPER_4K], np.zeros(n_envs, np.int32))
+    u = torch.from_numpy(synth.action_inputs(synth.actions(73, n_envs, 8))).cuda()
+    tape = b.soft_rollout(0.1, u, 1)
+    b.sync()
+    g = torch.empty((n_envs, 128), device="cuda")
+    st = _lib.load().vcs_backward_static(tape.h, None, None, None, None, C.c_void_p(g.data_ptr()), None, None,
+                                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == _lib.VCS_ERR_ARG
+    assert "fixed" in _lib.load().vcs_last_error(b.h).decode()
