@@ -143,6 +143,49 @@ def reference_arm(args):
     }), flush=True)
 
 
+def soft_leg(n_envs, n_frames, mappers, reps, tau=0.1):
+    """SOFT-STE forward + backward over n_frames (frame-skip 1, 64-frame
+    checkpoint segments, loss weights on 8 RAM bytes and 256 pixels at every
+    step).  Returns env-steps/s of fwd+bwd, the split and the library's
+    device memory for the tape."""
+    import torch
+
+    from paper_2606_22447_b300 import Batch, default_config, synth
+    roms = synth.config_carts(SEED, mappers)
+    ec = synth.env_cart_round_robin(n_envs, len(mappers))
+    b = Batch(roms, mappers, ec, default_config(segment_frames=64))
+    u = torch.from_numpy(synth.action_inputs(synth.actions(SEED, n_envs, n_frames))).cuda()
+    rng = np.random.default_rng(SEED)
+    w_ram = torch.zeros(128, device="cuda")
+    w_ram[torch.from_numpy(rng.choice(128, 8, replace=False))] = 1.0
+    w_scr = torch.zeros(210 * 160, device="cuda")
+    w_scr[torch.from_numpy(rng.choice(210 * 160, 256, replace=False))] = 1.0
+    g_u = torch.empty((n_frames, n_envs, 5), device="cuda")
+    g_pc = torch.empty((len(mappers), 8192), device="cuda")
+    best = None
+    for r in range(reps):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        tape = b.soft_rollout(tau, u, 1)
+        e[1].record()
+        tape.backward(w_ram=w_ram, w_screen=w_scr, grad_u=g_u, grad_rom_per_cart=g_pc)
+        e[2].record()
+        torch.cuda.synchronize()
+        b.sync()
+        used = free0 - torch.cuda.mem_get_info()[0]
+        fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        tape.free()
+        if r > 0 or reps == 1:
+            if best is None or fwd + bwd < best[0] + best[1]:
+                best = (fwd, bwd, used)
+    fwd, bwd, used = best
+    return {"env_steps_per_s": n_envs * n_frames / ((fwd + bwd) / 1e3), "fwd_ms": fwd, "bwd_ms": bwd,
+            "n_envs": n_envs, "frames": n_frames, "tau": tau, "tape_device_gb": used / 1e9,
+            "gpu_launches": 1 + 2 * ((n_frames + 63) // 64) + 2}
+
+
 def gpu_arm(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -234,6 +277,12 @@ def gpu_arm(args):
                 "ops_per_env_step": ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL,
                 "instructions_per_env_step": ipe,
                 "hbm_gbs_written": n * (128 + PIXELS_PER_STEP) / mean_s / 1e9}
+    soft = None
+    if not args.no_soft:
+        from paper_2606_22447_b300 import synth as _s
+        soft = {"short_1024x64": soft_leg(1024, 64, [_s.MAPPER_4K], reps=3)}
+        if not args.no_soft_long:
+            soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, reps=1)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
@@ -247,6 +296,7 @@ def gpu_arm(args):
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+            "soft_fwd_bwd": soft,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -263,6 +313,9 @@ def main():
     ap.add_argument("--epb", type=int, default=0, help="envs per block (0 = automatic)")
     ap.add_argument("--instr-per-step", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-soft", action="store_true", help="skip the SOFT-STE fwd+bwd legs")
+    ap.add_argument("--no-soft-long", action="store_true",
+                    help="skip the 4096-env x 2048-frame soft rollout (about 20 s)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

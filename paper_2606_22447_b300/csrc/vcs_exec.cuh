@@ -204,8 +204,21 @@ struct NoTape {
   __device__ __forceinline__ void pixels(float, float, float) {}
 };
 
+// Instruction length of each addressing mode, two bits per mode.
+constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8) | (2u << 10) | (3u << 12) |
+                              (3u << 14) | (3u << 16) | (2u << 18) | (2u << 20) | (2u << 22) | (3u << 24) |
+                              (1u << 26);
+
 // Execute one instruction slot (an instruction, or for a jammed CPU an idle
 // to the next line start) and advance the clocks.
+//
+// Fetch: inside the cartridge and away from the F8 hotspots and the end of
+// the 4 KB window the opcode and both operand bytes are read at once (three
+// independent shared-memory loads; such reads have no side effect and do not
+// depend on time).  Elsewhere the operand bytes are real bus accesses and are
+// read one by one, only as many as the instruction has.  Each instruction
+// then makes at most one data read (read and read-modify-write classes) and
+// its writes, through single call sites.
 template <class Tape>
 __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape) {
   if (r.jam) {
@@ -216,175 +229,114 @@ __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step
   }
   const uint32_t opaddr = r.PC;
   r.intim_live = 0;
-  const uint32_t op = bus_read(c, r, st, opaddr, 1);
-  const uint32_t mc = c.dt->mode_cyc[op];
-  const uint32_t mode = mc & 15;
+  const uint32_t off = opaddr & 0xFFF;
+  const bool fast = (opaddr & 0x1000) != 0 && off <= 0xFF5;
+  uint32_t op, b1 = 0, b2 = 0;
+  if (fast) {
+    const uint8_t* q = c.rom + ((r.bank << 12) | off);
+    op = q[0];
+    b1 = q[1];
+    b2 = q[2];
+  } else {
+    op = bus_read(c, r, st, opaddr, 1);
+  }
+  const uint32_t mc = c.dt->mode_cyc[op], co = c.dt->cls_op[op];
+  const uint32_t mode = mc & 15, cls = co & 3, id = co >> 2;
   uint32_t n = mc >> 4;
+  const uint32_t len = (kModeLen >> (2 * mode)) & 3;
   const uint32_t pc1 = (opaddr + 1) & 0xFFFF;
+  if (!fast) {
+    if (len >= 2) b1 = bus_read(c, r, st, pc1, 2);
+    if (len >= 3) b2 = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, id == OP_JSR ? 6 : 3);
+  }
+  if (mode == AM_JAM) {   // undocumented opcode: the CPU jams after the fetch
+    r.PC = pc1;
+    r.jam = 1;
+    r.cyc += 1;
+    r.fc += 1;
+    return;
+  }
+  r.PC = (opaddr + len) & 0xFFFF;
   uint32_t ea = 0;
   bool cross = false;
   switch (mode) {
-    case AM_IMP:
-    case AM_ACC:
-      r.PC = pc1;
-      break;
-    case AM_IMM:
-      ea = pc1;
-      r.PC = (opaddr + 2) & 0xFFFF;
-      break;
-    case AM_ZP:
-      ea = bus_read(c, r, st, pc1, 2);
-      r.PC = (opaddr + 2) & 0xFFFF;
-      break;
-    case AM_ZPX:
-      ea = (bus_read(c, r, st, pc1, 2) + r.X) & 0xFF;
-      r.PC = (opaddr + 2) & 0xFFFF;
-      break;
-    case AM_ZPY:
-      ea = (bus_read(c, r, st, pc1, 2) + r.Y) & 0xFF;
-      r.PC = (opaddr + 2) & 0xFFFF;
-      break;
-    case AM_ABS:
+    case AM_IMM: ea = pc1; break;
+    case AM_ZP: ea = b1; break;
+    case AM_ZPX: ea = (b1 + r.X) & 0xFF; break;
+    case AM_ZPY: ea = (b1 + r.Y) & 0xFF; break;
+    case AM_ABS: ea = b1 | (b2 << 8); break;
     case AM_ABX:
     case AM_ABY: {
-      uint32_t lo = bus_read(c, r, st, pc1, 2);
-      uint32_t hi = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, 3);
-      uint32_t base = lo | (hi << 8);
-      ea = (base + (mode == AM_ABX ? r.X : (mode == AM_ABY ? r.Y : 0u))) & 0xFFFF;
+      const uint32_t base = b1 | (b2 << 8);
+      ea = (base + (mode == AM_ABX ? r.X : r.Y)) & 0xFFFF;
       cross = ((base ^ ea) & 0xFF00) != 0;
-      r.PC = (opaddr + 3) & 0xFFFF;
       break;
     }
     case AM_INX: {
-      uint32_t p = (bus_read(c, r, st, pc1, 2) + r.X) & 0xFF;
-      uint32_t lo = bus_read(c, r, st, p, 4);
-      uint32_t hi = bus_read(c, r, st, (p + 1) & 0xFF, 5);
+      const uint32_t p = (b1 + r.X) & 0xFF;
+      const uint32_t lo = bus_read(c, r, st, p, 4);
+      const uint32_t hi = bus_read(c, r, st, (p + 1) & 0xFF, 5);
       ea = lo | (hi << 8);
-      r.PC = (opaddr + 2) & 0xFFFF;
       break;
     }
     case AM_INY: {
-      uint32_t z = bus_read(c, r, st, pc1, 2);
-      uint32_t lo = bus_read(c, r, st, z, 3);
-      uint32_t hi = bus_read(c, r, st, (z + 1) & 0xFF, 4);
-      uint32_t base = lo | (hi << 8);
+      const uint32_t lo = bus_read(c, r, st, b1, 3);
+      const uint32_t hi = bus_read(c, r, st, (b1 + 1) & 0xFF, 4);
+      const uint32_t base = lo | (hi << 8);
       ea = (base + r.Y) & 0xFFFF;
       cross = ((base ^ ea) & 0xFF00) != 0;
-      r.PC = (opaddr + 2) & 0xFFFF;
       break;
     }
-    case AM_REL:
-    case AM_IND:
-      break;
-    default:  // undocumented opcode: the CPU jams after the fetch
-      r.PC = pc1;
-      r.jam = 1;
-      r.cyc += 1;
-      r.fc += 1;
-      return;
+    default: break;
   }
 
-  // read-class instructions pay the page-cross cycle and read last
-  const uint32_t rcyc = n + (cross ? 1u : 0u);
+  // the one data read: read-class instructions read on their last cycle
+  // (after any page-cross cycle), read-modify-write two cycles before the end
+  uint32_t m = 0;
+  if (cls == CL_READ) {
+    n += cross ? 1u : 0u;
+    m = mode == AM_IMM ? b1 : bus_read(c, r, st, ea, (int)n);
+  } else if (cls == CL_RMW) {
+    m = bus_read(c, r, st, ea, (int)n - 2);
+  }
   uint32_t tref = ea, tfl = 0;
   // pending writes: nw bytes of wv (low byte first) at cycles widx, widx+1,
-  // ... to wea, or to the stack (0x100 | SP, descending) when wstack
-  uint32_t nw = 0, wea = ea, wv = 0, widx = n;
+  // ... to ea, or to the stack (0x100 | SP, descending) when wstack
+  uint32_t nw = 0, wv = 0, widx = n;
   bool wstack = false;
-  switch (op) {
-    // ---- loads ----
-    case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1:
-      n = rcyc;
-      r.A = bus_read(c, r, st, ea, (int)n);
-      set_nz(r, r.A);
-      break;
-    case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE:
-      n = rcyc;
-      r.X = bus_read(c, r, st, ea, (int)n);
-      set_nz(r, r.X);
-      break;
-    case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC:
-      n = rcyc;
-      r.Y = bus_read(c, r, st, ea, (int)n);
-      set_nz(r, r.Y);
-      break;
-    // ---- ALU ----
-    case 0x09: case 0x05: case 0x15: case 0x0D: case 0x1D: case 0x19: case 0x01: case 0x11:
-      n = rcyc;
-      r.A |= bus_read(c, r, st, ea, (int)n);
-      set_nz(r, r.A);
-      break;
-    case 0x29: case 0x25: case 0x35: case 0x2D: case 0x3D: case 0x39: case 0x21: case 0x31:
-      n = rcyc;
-      r.A &= bus_read(c, r, st, ea, (int)n);
-      set_nz(r, r.A);
-      break;
-    case 0x49: case 0x45: case 0x55: case 0x4D: case 0x5D: case 0x59: case 0x41: case 0x51:
-      n = rcyc;
-      r.A ^= bus_read(c, r, st, ea, (int)n);
-      set_nz(r, r.A);
-      break;
-    case 0x69: case 0x65: case 0x75: case 0x6D: case 0x7D: case 0x79: case 0x61: case 0x71:
-      n = rcyc;
-      do_adc(r, bus_read(c, r, st, ea, (int)n));
-      break;
-    case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
-      n = rcyc;
-      do_sbc(r, bus_read(c, r, st, ea, (int)n));
-      break;
-    case 0xC9: case 0xC5: case 0xD5: case 0xCD: case 0xDD: case 0xD9: case 0xC1: case 0xD1:
-      n = rcyc;
-      do_cmp(r, r.A, bus_read(c, r, st, ea, (int)n));
-      break;
-    case 0xE0: case 0xE4: case 0xEC:
-      do_cmp(r, r.X, bus_read(c, r, st, ea, (int)n));
-      break;
-    case 0xC0: case 0xC4: case 0xCC:
-      do_cmp(r, r.Y, bus_read(c, r, st, ea, (int)n));
-      break;
-    case 0x24: case 0x2C: {
-      uint32_t m = bus_read(c, r, st, ea, (int)n);
+  switch (id) {
+    case OP_LDA: r.A = m; set_nz(r, m); break;
+    case OP_LDX: r.X = m; set_nz(r, m); break;
+    case OP_LDY: r.Y = m; set_nz(r, m); break;
+    case OP_ORA: r.A |= m; set_nz(r, r.A); break;
+    case OP_AND: r.A &= m; set_nz(r, r.A); break;
+    case OP_EOR: r.A ^= m; set_nz(r, r.A); break;
+    case OP_ADC: do_adc(r, m); break;
+    case OP_SBC: do_sbc(r, m); break;
+    case OP_CMP: do_cmp(r, r.A, m); break;
+    case OP_CPX: do_cmp(r, r.X, m); break;
+    case OP_CPY: do_cmp(r, r.Y, m); break;
+    case OP_BIT:
       r.nsrc = m & 0x80;
       r.fV = (m >> 6) & 1;
       r.zsrc = r.A & m;
       break;
-    }
-    // ---- stores ----
-    case 0x85: case 0x95: case 0x8D: case 0x9D: case 0x99: case 0x81: case 0x91:
-      nw = 1; wv = r.A;
-      break;
-    case 0x86: case 0x96: case 0x8E:
-      nw = 1; wv = r.X;
-      break;
-    case 0x84: case 0x94: case 0x8C:
-      nw = 1; wv = r.Y;
-      break;
-    // ---- read-modify-write ----
-    case 0x0A: r.A = do_shift(r, 0, r.A); break;
-    case 0x2A: r.A = do_shift(r, 1, r.A); break;
-    case 0x4A: r.A = do_shift(r, 2, r.A); break;
-    case 0x6A: r.A = do_shift(r, 3, r.A); break;
-    case 0x06: case 0x16: case 0x0E: case 0x1E:
-    case 0x26: case 0x36: case 0x2E: case 0x3E:
-    case 0x46: case 0x56: case 0x4E: case 0x5E:
-    case 0x66: case 0x76: case 0x6E: case 0x7E:
-    case 0xC6: case 0xD6: case 0xCE: case 0xDE:
-    case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
-      uint32_t m = bus_read(c, r, st, ea, (int)n - 2);
-      uint32_t k = op >> 5;
-      if (k < 4) {
-        wv = do_shift(r, k, m);
-      } else {
-        wv = (k == 6 ? m - 1 : m + 1) & 0xFF;
-        set_nz(r, wv);
-      }
+    case OP_STA: nw = 1; wv = r.A; break;
+    case OP_STX: nw = 1; wv = r.X; break;
+    case OP_STY: nw = 1; wv = r.Y; break;
+    case OP_ASL: case OP_ROL: case OP_LSR: case OP_ROR:
+      wv = do_shift(r, id - OP_ASL, m);
       nw = 1;
       break;
-    }
-    // ---- branches ----
-    case 0x10: case 0x30: case 0x50: case 0x70: case 0x90: case 0xB0: case 0xD0: case 0xF0: {
-      uint32_t off = bus_read(c, r, st, pc1, 2);
-      uint32_t next = (opaddr + 2) & 0xFFFF;
+    case OP_DEC: case OP_INC:
+      wv = (id == OP_DEC ? m - 1 : m + 1) & 0xFF;
+      set_nz(r, wv);
+      nw = 1;
+      break;
+    case OP_ASLA: case OP_ROLA: case OP_LSRA: case OP_RORA:
+      r.A = do_shift(r, id - OP_ASLA, r.A);
+      break;
+    case OP_BRANCH: {
       uint32_t flag;
       switch (op >> 6) {
         case 0: flag = (r.nsrc >> 7) & 1; break;
@@ -392,10 +344,10 @@ __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step
         case 2: flag = r.fC; break;
         default: flag = (r.zsrc & 0xFF) == 0 ? 1u : 0u; break;
       }
-      uint32_t taken = ((op >> 5) & 1) == flag ? 1u : 0u;
-      r.PC = next;
+      const uint32_t taken = ((op >> 5) & 1) == flag ? 1u : 0u;
       if (taken) {
-        uint32_t t = (next + (uint32_t)(int32_t)(int8_t)(uint8_t)off) & 0xFFFF;
+        const uint32_t next = r.PC;
+        const uint32_t t = (next + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF;
         n += 1 + (((t ^ next) & 0xFF00) ? 1u : 0u);
         r.PC = t;
       }
@@ -403,85 +355,73 @@ __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step
       tfl = taken;
       break;
     }
-    // ---- jumps / subroutines ----
-    case 0x4C:
-      r.PC = ea;
-      break;
-    case 0x6C: {
-      uint32_t lo = bus_read(c, r, st, pc1, 2);
-      uint32_t hi = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, 3);
-      uint32_t p = lo | (hi << 8);
-      uint32_t l2 = bus_read(c, r, st, p, 4);
-      uint32_t h2 = bus_read(c, r, st, (p & 0xFF00) | ((p + 1) & 0xFF), 5);
+    case OP_JMP: r.PC = ea; break;
+    case OP_JMPI: {
+      const uint32_t p = b1 | (b2 << 8);
+      const uint32_t l2 = bus_read(c, r, st, p, 4);
+      const uint32_t h2 = bus_read(c, r, st, (p & 0xFF00) | ((p + 1) & 0xFF), 5);
       r.PC = l2 | (h2 << 8);
       break;
     }
-    case 0x20: {
-      uint32_t lo = bus_read(c, r, st, pc1, 2);
-      uint32_t ret = (opaddr + 2) & 0xFFFF;
-      uint32_t hi = bus_read(c, r, st, ret, 6);
-      r.PC = lo | (hi << 8);
+    case OP_JSR: {
+      const uint32_t ret = (opaddr + 2) & 0xFFFF;
+      r.PC = b1 | (b2 << 8);
       nw = 2; wstack = true; wv = (ret >> 8) | ((ret & 0xFF) << 8); widx = 4;
       break;
     }
-    case 0x60: {
-      uint32_t lo = pull(c, r, st, 4);
-      uint32_t hi = pull(c, r, st, 5);
+    case OP_RTS: {
+      const uint32_t lo = pull(c, r, st, 4);
+      const uint32_t hi = pull(c, r, st, 5);
       r.PC = ((lo | (hi << 8)) + 1) & 0xFFFF;
       break;
     }
-    case 0x40: {
-      uint32_t p = pull(c, r, st, 4);
-      uint32_t lo = pull(c, r, st, 5);
-      uint32_t hi = pull(c, r, st, 6);
+    case OP_RTI: {
+      const uint32_t p = pull(c, r, st, 4);
+      const uint32_t lo = pull(c, r, st, 5);
+      const uint32_t hi = pull(c, r, st, 6);
       unpack_p(r, p | 0x30);
       r.PC = lo | (hi << 8);
       break;
     }
-    case 0x00: {
-      uint32_t ret = (opaddr + 2) & 0xFFFF;
+    case OP_BRK: {
+      const uint32_t ret = (opaddr + 2) & 0xFFFF;
       nw = 3; wstack = true; wv = (ret >> 8) | ((ret & 0xFF) << 8) | (pack_p(r) << 16); widx = 3;
       r.fI = 1;
-      uint32_t lo = bus_read(c, r, st, 0xFFFE, 6);
-      uint32_t hi = bus_read(c, r, st, 0xFFFF, 7);
+      const uint32_t lo = bus_read(c, r, st, 0xFFFE, 6);
+      const uint32_t hi = bus_read(c, r, st, 0xFFFF, 7);
       r.PC = lo | (hi << 8);
       break;
     }
-    // ---- stack ----
-    case 0x48: nw = 1; wstack = true; wv = r.A; widx = 3; break;
-    case 0x08: nw = 1; wstack = true; wv = pack_p(r); widx = 3; break;
-    case 0x68:
+    case OP_PHA: nw = 1; wstack = true; wv = r.A; widx = 3; break;
+    case OP_PHP: nw = 1; wstack = true; wv = pack_p(r); widx = 3; break;
+    case OP_PLA:
       r.A = pull(c, r, st, 4);
       set_nz(r, r.A);
       tref = 0x100u | r.SP;
       break;
-    case 0x28:
-      unpack_p(r, pull(c, r, st, 4) | 0x30);
-      break;
-    // ---- flags and register transfers ----
-    case 0x18: r.fC = 0; break;
-    case 0x38: r.fC = 1; break;
-    case 0x58: r.fI = 0; break;
-    case 0x78: r.fI = 1; break;
-    case 0xB8: r.fV = 0; break;
-    case 0xD8: r.fD = 0; break;
-    case 0xF8: r.fD = 1; break;
-    case 0xEA: break;
-    case 0xAA: r.X = r.A; set_nz(r, r.X); break;
-    case 0x8A: r.A = r.X; set_nz(r, r.A); break;
-    case 0xA8: r.Y = r.A; set_nz(r, r.Y); break;
-    case 0x98: r.A = r.Y; set_nz(r, r.A); break;
-    case 0xBA: r.X = r.SP; set_nz(r, r.X); break;
-    case 0x9A: r.SP = r.X; break;
-    case 0xE8: r.X = (r.X + 1) & 0xFF; set_nz(r, r.X); break;
-    case 0xCA: r.X = (r.X - 1) & 0xFF; set_nz(r, r.X); break;
-    case 0xC8: r.Y = (r.Y + 1) & 0xFF; set_nz(r, r.Y); break;
-    case 0x88: r.Y = (r.Y - 1) & 0xFF; set_nz(r, r.Y); break;
-    default: break;
+    case OP_PLP: unpack_p(r, pull(c, r, st, 4) | 0x30); break;
+    case OP_CLC: r.fC = 0; break;
+    case OP_SEC: r.fC = 1; break;
+    case OP_CLI: r.fI = 0; break;
+    case OP_SEI: r.fI = 1; break;
+    case OP_CLV: r.fV = 0; break;
+    case OP_CLD: r.fD = 0; break;
+    case OP_SED: r.fD = 1; break;
+    case OP_TAX: r.X = r.A; set_nz(r, r.X); break;
+    case OP_TXA: r.A = r.X; set_nz(r, r.A); break;
+    case OP_TAY: r.Y = r.A; set_nz(r, r.Y); break;
+    case OP_TYA: r.A = r.Y; set_nz(r, r.A); break;
+    case OP_TSX: r.X = r.SP; set_nz(r, r.X); break;
+    case OP_TXS: r.SP = r.X; break;
+    case OP_INX: r.X = (r.X + 1) & 0xFF; set_nz(r, r.X); break;
+    case OP_DEX: r.X = (r.X - 1) & 0xFF; set_nz(r, r.X); break;
+    case OP_INY: r.Y = (r.Y + 1) & 0xFF; set_nz(r, r.Y); break;
+    case OP_DEY: r.Y = (r.Y - 1) & 0xFF; set_nz(r, r.Y); break;
+    default: break;   // NOP
   }
   if (wstack) tref = 0x100u | r.SP;
   for (uint32_t i = 0; i < nw; i++) {
-    uint32_t addr = wea;
+    uint32_t addr = ea;
     if (wstack) {
       addr = 0x100u | r.SP;
       r.SP = (r.SP - 1) & 0xFF;

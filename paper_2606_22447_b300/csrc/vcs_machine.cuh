@@ -39,9 +39,25 @@ enum : uint32_t { kStWatchdog = 1, kStJammed = 2, kStDone = 4 };
 enum : uint8_t { AM_IMP, AM_ACC, AM_IMM, AM_ZP, AM_ZPX, AM_ZPY, AM_ABS, AM_ABX, AM_ABY,
                  AM_INX, AM_INY, AM_REL, AM_IND, AM_JAM };
 
-// Per-opcode decode: mode (low 4 bits) | base cycles << 4.
+// Instruction classes and compact operation ids of the decode table.
+enum : uint8_t { CL_OTHER = 0, CL_READ = 1, CL_STORE = 2, CL_RMW = 3 };
+enum : uint8_t {
+  OP_LDA, OP_LDX, OP_LDY, OP_ORA, OP_AND, OP_EOR, OP_ADC, OP_SBC, OP_CMP, OP_CPX, OP_CPY, OP_BIT,
+  OP_STA, OP_STX, OP_STY,
+  OP_ASL, OP_ROL, OP_LSR, OP_ROR, OP_DEC, OP_INC,
+  OP_ASLA, OP_ROLA, OP_LSRA, OP_RORA,
+  OP_BRANCH, OP_JMP, OP_JMPI, OP_JSR, OP_RTS, OP_RTI, OP_BRK,
+  OP_PHA, OP_PHP, OP_PLA, OP_PLP,
+  OP_CLC, OP_SEC, OP_CLI, OP_SEI, OP_CLV, OP_CLD, OP_SED, OP_NOP,
+  OP_TAX, OP_TXA, OP_TAY, OP_TYA, OP_TSX, OP_TXS, OP_INX, OP_DEX, OP_INY, OP_DEY,
+  OP_JAM = 63
+};
+
+// Per-opcode decode: mode (low 4 bits) | base cycles << 4, and
+// class (low 2 bits) | operation id << 2.
 struct DecodeTables {
   uint8_t mode_cyc[256];
+  uint8_t cls_op[256];
 };
 
 // Machine registers of one env (kept in registers inside a launch).

@@ -10,20 +10,20 @@ namespace vcs {
 // Shared-memory layout of one block of E envs.
 struct BlockSmem {
   uint8_t* rom;         // 8192 B cartridge image
-  DecodeTables* dt;     // 256 B
+  DecodeTables* dt;     // 512 B
   uint64_t* mbar;       // TMA completion barrier
   uint32_t* ram;        // [32][E] words
   uint32_t* line;       // [40][E] words
 };
 
-__host__ __device__ constexpr size_t smem_bytes(int E) { return 8192 + 256 + 16 + (size_t)(32 + 40) * 4 * E; }
+__host__ __device__ constexpr size_t smem_bytes(int E) { return 8192 + 512 + 16 + (size_t)(32 + 40) * 4 * E; }
 
 __device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E) {
   BlockSmem b;
   b.rom = smem;
   b.dt = reinterpret_cast<DecodeTables*>(smem + 8192);
-  b.mbar = reinterpret_cast<uint64_t*>(smem + 8192 + 256);
-  b.ram = reinterpret_cast<uint32_t*>(smem + 8192 + 256 + 16);
+  b.mbar = reinterpret_cast<uint64_t*>(smem + 8192 + 512);
+  b.ram = reinterpret_cast<uint32_t*>(smem + 8192 + 512 + 16);
   b.line = b.ram + 32 * E;
   return b;
 }
@@ -38,7 +38,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTables* dt, const uint8_t* src,
                                             uint32_t bytes) {
   const uint32_t bar = smem_addr(b.mbar);
-  for (int i = threadIdx.x; i < 64; i += blockDim.x)
+  for (int i = threadIdx.x; i < (int)(sizeof(DecodeTables) / 4); i += blockDim.x)
     reinterpret_cast<uint32_t*>(b.dt)[i] = reinterpret_cast<const uint32_t*>(dt)[i];
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
