@@ -35,92 +35,89 @@ constexpr uint64_t kVisualRegs = (1ull << 0x01) | (1ull << 0x06) | (1ull << 0x08
                                  (1ull << 0x0A) | (1ull << 0x0D) | (1ull << 0x0E) | (1ull << 0x0F) |
                                  (1ull << 0x10) | (1ull << 0x1B) | (1ull << 0x2A);
 
+// A TIA register write at frame cycle fcw.  A write that changes the picture
+// first draws the pending span with the old registers.  The register update
+// itself is a set of selects rather than a switch: one indirect branch per
+// write costs more than the few dozen independent integer operations.
 template <class Tape>
 __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t reg,
                                           uint32_t v, int32_t fcw) {
   if (((kVisualRegs >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
-  switch (reg) {
-    case 0x00:
-      if (!(r.vsync & 2) && (v & 2)) st.fe_at = fcw;
-      r.vsync = v;
-      break;
-    case 0x01: r.vblank = v; break;
-    case 0x02: {
-      uint32_t m = (uint32_t)fcw % 76u;
-      if (m) st.stall += 76 - (int32_t)m;
-      break;
-    }
-    case 0x06: tape.colour_write(0); r.col0 = v; break;
-    case 0x08: tape.colour_write(1); r.colpf = v; break;
-    case 0x09: tape.colour_write(2); r.colbk = v; break;
-    case 0x0A: r.ctrl = v; break;
-    case 0x0D: r.pf0 = v; break;
-    case 0x0E: r.pf1 = v; break;
-    case 0x0F: r.pf2 = v; break;
-    case 0x10: {
-      uint32_t h = 3u * ((uint32_t)fcw % 76u);
-      r.pos = h < 68 ? 3u : (h - 68u + 5u) % 160u;
-      break;
-    }
-    case 0x1B: r.grp0 = v; break;
-    case 0x20: r.hmp0 = v; break;
-    case 0x2A: {
-      int32_t m = ((int32_t)(int8_t)(uint8_t)r.hmp0) >> 4;
-      r.pos = (uint32_t)(((int32_t)r.pos - m + 160) % 160);
-      uint32_t h = 3u * ((uint32_t)fcw % 76u);
-      if (h <= 9) r.hml = (int32_t)div76((uint32_t)fcw);
-      break;
-    }
-    case 0x2B: r.hmp0 = 0; break;
-    default: break;
-  }
+  if (reg == 0x06) tape.colour_write(0);
+  else if (reg == 0x08) tape.colour_write(1);
+  else if (reg == 0x09) tape.colour_write(2);
+  const uint32_t line = div76((uint32_t)fcw);
+  const uint32_t m = (uint32_t)fcw - 76u * line;   // CPU cycle within the line
+  const uint32_t h = 3u * m;                       // colour clock within the line
+  st.fe_at = (reg == 0x00 && !(r.vsync & 2) && (v & 2)) ? fcw : st.fe_at;
+  st.stall += (reg == 0x02 && m != 0) ? (int32_t)(76u - m) : 0;
+  r.vsync = reg == 0x00 ? v : r.vsync;
+  r.vblank = reg == 0x01 ? v : r.vblank;
+  r.col0 = reg == 0x06 ? v : r.col0;
+  r.colpf = reg == 0x08 ? v : r.colpf;
+  r.colbk = reg == 0x09 ? v : r.colbk;
+  r.ctrl = reg == 0x0A ? v : r.ctrl;
+  r.pf0 = reg == 0x0D ? v : r.pf0;
+  r.pf1 = reg == 0x0E ? v : r.pf1;
+  r.pf2 = reg == 0x0F ? v : r.pf2;
+  r.grp0 = reg == 0x1B ? v : r.grp0;
+  // RESP0: colour clock 3 in HBLANK, else the beam position plus 5, mod 160
+  const uint32_t resp = h < 68 ? 3u : (h - 68u + 5u) % 160u;
+  // HMOVE: move by the signed high nibble of HMP0 (positive = left)
+  const int32_t mv = ((int32_t)(int8_t)(uint8_t)r.hmp0) >> 4;
+  const uint32_t hmov = (uint32_t)(((int32_t)r.pos - mv + 160) % 160);
+  r.pos = reg == 0x10 ? resp : (reg == 0x2A ? hmov : r.pos);
+  r.hml = (reg == 0x2A && h <= 9) ? (int32_t)line : r.hml;
+  r.hmp0 = reg == 0x20 ? v : (reg == 0x2B ? 0u : r.hmp0);
 }
 
-// One bus read at cycle index idx of the current instruction.  A read of
-// INTIM also records whether the timer had underflowed (r.intim_live), which
-// the soft path's tape keeps for the backward sweep.
+// One bus read at cycle index idx of the current instruction, for any
+// address.  Every source is read and the result selected, which costs fewer
+// cycles than branching on the address region.  Side effects: a read of an
+// F8 hotspot switches the bank, and a read of INTIM records whether the timer
+// had underflowed (r.intim_live, kept by the soft path's tape).
 __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& st, uint32_t addr, int idx) {
-  uint32_t a = addr & 0x1FFF;
-  if (a & 0x1000) {
-    if (c.f8 && (a & 0x1FFE) == 0x1FF8) r.bank = a & 1;
-    return c.rom[(r.bank << 12) | (a & 0xFFF)];
-  }
-  if (!(a & 0x80)) {
-    uint32_t q = a & 0xF;
-    return q == 0xC ? r.inpt4 : (q == 0xD ? 0x80u : 0u);
-  }
-  if (!(a & 0x200)) return ram_rd(c, a);
-  if (!(a & 4)) {
-    uint32_t q = a & 3;
-    return q == 0 ? r.swcha : (q == 2 ? 0x0Bu : 0u);
-  }
-  uint32_t t = r.cyc + (uint32_t)(idx + st.stall);
-  if (a & 1) return timint_at(r, t);
-  r.intim_live = (t - r.tw) <= (r.tv << r.tsh) ? 1u : 0u;
-  return intim_at(r, t);
+  const uint32_t a = addr & 0x1FFF;
+  r.bank = (c.f8 && (a & 0x1FFE) == 0x1FF8) ? (a & 1) : r.bank;
+  const uint32_t vrom = c.rom[(r.bank << 12) | (a & 0xFFF)];
+  const uint32_t vram = ram_rd(c, a);
+  const uint32_t q = a & 0xF;
+  const uint32_t vtia = q == 0xC ? r.inpt4 : (q == 0xD ? 0x80u : 0u);
+  const uint32_t q3 = a & 3;
+  const uint32_t vio = q3 == 0 ? r.swcha : (q3 == 2 ? 0x0Bu : 0u);
+  const uint32_t k = r.cyc + (uint32_t)(idx + st.stall) - r.tw;
+  const uint32_t vi = r.tv << r.tsh;
+  const bool live = k <= vi;
+  const uint32_t vint = live ? r.tv - ((k + (1u << r.tsh) - 1) >> r.tsh) : ((vi - k) & 0xFF);
+  const uint32_t vtim = (a & 1) ? (live ? 0u : 0x80u) : vint;
+  const bool timer = (a & 0x1284) == 0x0284;
+  r.intim_live = (timer && !(a & 1)) ? (live ? 1u : 0u) : r.intim_live;
+  return (a & 0x1000) ? vrom : !(a & 0x80) ? vtia : !(a & 0x200) ? vram : !(a & 4) ? vio : vtim;
+}
+
+// A read inside page zero or one (zero-page modes, the stack): RAM or the
+// TIA read registers, no side effects.
+__device__ __forceinline__ uint32_t zp_read(const Ctx& c, const Regs& r, uint32_t a) {
+  const uint32_t vram = ram_rd(c, a);
+  const uint32_t q = a & 0xF;
+  const uint32_t vtia = q == 0xC ? r.inpt4 : (q == 0xD ? 0x80u : 0u);
+  return (a & 0x80) ? vram : vtia;
 }
 
 template <class Tape>
 __device__ __forceinline__ void bus_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t addr,
                                           uint32_t v, int idx) {
-  uint32_t a = addr & 0x1FFF;
-  if (a & 0x1000) {
-    if (c.f8 && (a & 0x1FFE) == 0x1FF8) r.bank = a & 1;
-    return;
-  }
-  if (!(a & 0x80)) {
+  const uint32_t a = addr & 0x1FFF;
+  r.bank = (c.f8 && (a & 0x1FFE) == 0x1FF8) ? (a & 1) : r.bank;
+  if ((a & 0x1080) == 0) {   // TIA
     tia_write(c, r, rd, st, tape, a & 0x3F, v & 0xFF, r.fc + idx + st.stall);
     return;
   }
-  if (!(a & 0x200)) {
-    ram_wr(c, a, v);
-    return;
-  }
-  if ((a & 0x14) == 0x14) {
-    r.tw = r.cyc + (uint32_t)(idx + st.stall);
-    r.tv = v & 0xFF;
-    r.tsh = (0x0A060300u >> (8 * (a & 3))) & 0xFF;
-  }
+  if ((a & 0x1280) == 0x0080) ram_wr(c, a, v);
+  const bool timer = (a & 0x1294) == 0x0294;   // TIM1T, TIM8T, TIM64T, T1024T
+  r.tw = timer ? r.cyc + (uint32_t)(idx + st.stall) : r.tw;
+  r.tv = timer ? (v & 0xFF) : r.tv;
+  r.tsh = timer ? (0x0A060300u >> (8 * (a & 3))) & 0xFF : r.tsh;
 }
 
 __device__ __forceinline__ void set_nz(Regs& r, uint32_t v) {
@@ -189,9 +186,9 @@ __device__ __forceinline__ uint32_t do_shift(Regs& r, uint32_t k, uint32_t v) {
   return res;
 }
 
-__device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r, Step& st, int idx) {
+__device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r) {
   r.SP = (r.SP + 1) & 0xFF;
-  return bus_read(c, r, st, 0x100u | r.SP, idx);
+  return zp_read(c, r, 0x100u | r.SP);
 }
 
 // Tape hook: called once per executed instruction with its opcode, a
@@ -209,6 +206,203 @@ constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8)
                               (3u << 14) | (3u << 16) | (2u << 18) | (2u << 20) | (2u << 22) | (3u << 24) |
                               (1u << 26);
 
+// The 151 documented opcodes (op_info gives each one's mode, cycles and
+// operation); every other byte jams the CPU.
+#define VCS_DOCUMENTED_OPS(X) \
+  X(0x00) X(0x01) X(0x05) X(0x06) X(0x08) X(0x09) X(0x0A) X(0x0D) X(0x0E) X(0x10) X(0x11) X(0x15) \
+  X(0x16) X(0x18) X(0x19) X(0x1D) X(0x1E) X(0x20) X(0x21) X(0x24) X(0x25) X(0x26) X(0x28) X(0x29) \
+  X(0x2A) X(0x2C) X(0x2D) X(0x2E) X(0x30) X(0x31) X(0x35) X(0x36) X(0x38) X(0x39) X(0x3D) X(0x3E) \
+  X(0x40) X(0x41) X(0x45) X(0x46) X(0x48) X(0x49) X(0x4A) X(0x4C) X(0x4D) X(0x4E) X(0x50) X(0x51) \
+  X(0x55) X(0x56) X(0x58) X(0x59) X(0x5D) X(0x5E) X(0x60) X(0x61) X(0x65) X(0x66) X(0x68) X(0x69) \
+  X(0x6A) X(0x6C) X(0x6D) X(0x6E) X(0x70) X(0x71) X(0x75) X(0x76) X(0x78) X(0x79) X(0x7D) X(0x7E) \
+  X(0x81) X(0x84) X(0x85) X(0x86) X(0x88) X(0x8A) X(0x8C) X(0x8D) X(0x8E) X(0x90) X(0x91) X(0x94) \
+  X(0x95) X(0x96) X(0x98) X(0x99) X(0x9A) X(0x9D) X(0xA0) X(0xA1) X(0xA2) X(0xA4) X(0xA5) X(0xA6) \
+  X(0xA8) X(0xA9) X(0xAA) X(0xAC) X(0xAD) X(0xAE) X(0xB0) X(0xB1) X(0xB4) X(0xB5) X(0xB6) X(0xB8) \
+  X(0xB9) X(0xBA) X(0xBC) X(0xBD) X(0xBE) X(0xC0) X(0xC1) X(0xC4) X(0xC5) X(0xC6) X(0xC8) X(0xC9) \
+  X(0xCA) X(0xCC) X(0xCD) X(0xCE) X(0xD0) X(0xD1) X(0xD5) X(0xD6) X(0xD8) X(0xD9) X(0xDD) X(0xDE) \
+  X(0xE0) X(0xE1) X(0xE4) X(0xE5) X(0xE6) X(0xE8) X(0xE9) X(0xEA) X(0xEC) X(0xED) X(0xEE) X(0xF0) \
+  X(0xF1) X(0xF5) X(0xF6) X(0xF8) X(0xF9) X(0xFD) X(0xFE)
+
+// What an instruction leaves for the common tail of exec_one: its cycle
+// count, its writes (nw bytes of wv, low byte first, at cycle indices widx,
+// widx + 1, ... to ea, or pushed on the stack when wstack) and its tape
+// record (reference address and flag bits).
+struct Pend {
+  uint32_t n, ea, nw, wv, widx, tref, tfl;
+  bool wstack, rec;
+};
+
+template <uint32_t MODE>
+__host__ __device__ constexpr bool page_zero_mode() {
+  return MODE == AM_ZP || MODE == AM_ZPX || MODE == AM_ZPY;
+}
+
+// One documented instruction, specialised on its opcode: mode, class and
+// operation are compile-time constants, so the only run-time dispatch of an
+// instruction is the opcode switch in exec_one.
+template <uint32_t OP>
+__device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_t opaddr, uint32_t b1, uint32_t b2,
+                                        Pend& p) {
+  constexpr OpInfo I = op_info(OP);
+  constexpr uint32_t mode = I.mode, cls = I.cls, id = I.id;
+  constexpr uint32_t len = (kModeLen >> (2 * mode)) & 3;
+  uint32_t n = I.cyc;
+  const uint32_t pc1 = (opaddr + 1) & 0xFFFF;
+  r.PC = (opaddr + len) & 0xFFFF;
+  uint32_t ea = 0;
+  bool cross = false;
+  if constexpr (mode == AM_IMM) {
+    ea = pc1;
+  } else if constexpr (mode == AM_ZP) {
+    ea = b1;
+  } else if constexpr (mode == AM_ZPX) {
+    ea = (b1 + r.X) & 0xFF;
+  } else if constexpr (mode == AM_ZPY) {
+    ea = (b1 + r.Y) & 0xFF;
+  } else if constexpr (mode == AM_ABS) {
+    ea = b1 | (b2 << 8);
+  } else if constexpr (mode == AM_ABX || mode == AM_ABY) {
+    const uint32_t base = b1 | (b2 << 8);
+    ea = (base + (mode == AM_ABX ? r.X : r.Y)) & 0xFFFF;
+    cross = ((base ^ ea) & 0xFF00) != 0;
+  } else if constexpr (mode == AM_INX) {
+    const uint32_t q = (b1 + r.X) & 0xFF;
+    ea = zp_read(c, r, q) | (zp_read(c, r, (q + 1) & 0xFF) << 8);
+  } else if constexpr (mode == AM_INY) {
+    const uint32_t base = zp_read(c, r, b1) | (zp_read(c, r, (b1 + 1) & 0xFF) << 8);
+    ea = (base + r.Y) & 0xFFFF;
+    cross = ((base ^ ea) & 0xFF00) != 0;
+  }
+
+  // the one data read: read-class instructions read on their last cycle
+  // (after any page-cross cycle), read-modify-write two cycles before the end
+  uint32_t m = 0;
+  if constexpr (cls == CL_READ) {
+    if constexpr (mode == AM_IMM) {
+      m = b1;
+    } else {
+      n += cross ? 1u : 0u;
+      if constexpr (page_zero_mode<mode>()) m = zp_read(c, r, ea);
+      else m = bus_read(c, r, st, ea, (int)n);
+    }
+  } else if constexpr (cls == CL_RMW) {
+    if constexpr (page_zero_mode<mode>()) m = zp_read(c, r, ea);
+    else m = bus_read(c, r, st, ea, (int)n - 2);
+  }
+  p.tref = ea;
+  p.tfl = 0;
+  p.nw = 0;
+  p.wv = 0;
+  p.widx = n;
+  p.wstack = false;
+  p.rec = true;
+  if constexpr (id == OP_LDA) { r.A = m; set_nz(r, m); }
+  else if constexpr (id == OP_LDX) { r.X = m; set_nz(r, m); }
+  else if constexpr (id == OP_LDY) { r.Y = m; set_nz(r, m); }
+  else if constexpr (id == OP_ORA) { r.A |= m; set_nz(r, r.A); }
+  else if constexpr (id == OP_AND) { r.A &= m; set_nz(r, r.A); }
+  else if constexpr (id == OP_EOR) { r.A ^= m; set_nz(r, r.A); }
+  else if constexpr (id == OP_ADC) { do_adc(r, m); }
+  else if constexpr (id == OP_SBC) { do_sbc(r, m); }
+  else if constexpr (id == OP_CMP) { do_cmp(r, r.A, m); }
+  else if constexpr (id == OP_CPX) { do_cmp(r, r.X, m); }
+  else if constexpr (id == OP_CPY) { do_cmp(r, r.Y, m); }
+  else if constexpr (id == OP_BIT) {
+    r.nsrc = m & 0x80;
+    r.fV = (m >> 6) & 1;
+    r.zsrc = r.A & m;
+  }
+  else if constexpr (id == OP_STA) { p.nw = 1; p.wv = r.A; }
+  else if constexpr (id == OP_STX) { p.nw = 1; p.wv = r.X; }
+  else if constexpr (id == OP_STY) { p.nw = 1; p.wv = r.Y; }
+  else if constexpr (id == OP_ASL || id == OP_ROL || id == OP_LSR || id == OP_ROR) {
+    p.wv = do_shift(r, id - OP_ASL, m);
+    p.nw = 1;
+  }
+  else if constexpr (id == OP_DEC || id == OP_INC) {
+    p.wv = (id == OP_DEC ? m - 1 : m + 1) & 0xFF;
+    set_nz(r, p.wv);
+    p.nw = 1;
+  }
+  else if constexpr (id == OP_ASLA || id == OP_ROLA || id == OP_LSRA || id == OP_RORA) {
+    r.A = do_shift(r, id - OP_ASLA, r.A);
+  }
+  else if constexpr (id == OP_BRANCH) {
+    uint32_t flag;
+    if constexpr ((OP >> 6) == 0) flag = (r.nsrc >> 7) & 1;
+    else if constexpr ((OP >> 6) == 1) flag = r.fV;
+    else if constexpr ((OP >> 6) == 2) flag = r.fC;
+    else flag = (r.zsrc & 0xFF) == 0 ? 1u : 0u;
+    const bool taken = ((OP >> 5) & 1) == flag;
+    const uint32_t next = r.PC;
+    const uint32_t t = (next + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF;
+    n += taken ? 1u + (((t ^ next) & 0xFF00) ? 1u : 0u) : 0u;
+    r.PC = taken ? t : next;
+    p.tref = pc1;
+    p.tfl = taken ? 1u : 0u;
+  }
+  else if constexpr (id == OP_JMP) { r.PC = ea; }
+  else if constexpr (id == OP_JMPI) {
+    const uint32_t q = b1 | (b2 << 8);
+    const uint32_t l2 = bus_read(c, r, st, q, 4);
+    const uint32_t h2 = bus_read(c, r, st, (q & 0xFF00) | ((q + 1) & 0xFF), 5);
+    r.PC = l2 | (h2 << 8);
+  }
+  else if constexpr (id == OP_JSR) {
+    const uint32_t ret = (opaddr + 2) & 0xFFFF;
+    r.PC = b1 | (b2 << 8);
+    p.nw = 2; p.wstack = true; p.wv = (ret >> 8) | ((ret & 0xFF) << 8); p.widx = 4;
+  }
+  else if constexpr (id == OP_RTS) {
+    const uint32_t lo = pull(c, r);
+    const uint32_t hi = pull(c, r);
+    r.PC = ((lo | (hi << 8)) + 1) & 0xFFFF;
+  }
+  else if constexpr (id == OP_RTI) {
+    const uint32_t pp = pull(c, r);
+    const uint32_t lo = pull(c, r);
+    const uint32_t hi = pull(c, r);
+    unpack_p(r, pp | 0x30);
+    r.PC = lo | (hi << 8);
+  }
+  else if constexpr (id == OP_BRK) {
+    const uint32_t ret = (opaddr + 2) & 0xFFFF;
+    p.nw = 3; p.wstack = true; p.wv = (ret >> 8) | ((ret & 0xFF) << 8) | (pack_p(r) << 16); p.widx = 3;
+    r.fI = 1;
+    const uint32_t lo = bus_read(c, r, st, 0xFFFE, 6);
+    const uint32_t hi = bus_read(c, r, st, 0xFFFF, 7);
+    r.PC = lo | (hi << 8);
+  }
+  else if constexpr (id == OP_PHA) { p.nw = 1; p.wstack = true; p.wv = r.A; p.widx = 3; }
+  else if constexpr (id == OP_PHP) { p.nw = 1; p.wstack = true; p.wv = pack_p(r); p.widx = 3; }
+  else if constexpr (id == OP_PLA) {
+    r.A = pull(c, r);
+    set_nz(r, r.A);
+    p.tref = 0x100u | r.SP;
+  }
+  else if constexpr (id == OP_PLP) { unpack_p(r, pull(c, r) | 0x30); }
+  else if constexpr (id == OP_CLC) { r.fC = 0; }
+  else if constexpr (id == OP_SEC) { r.fC = 1; }
+  else if constexpr (id == OP_CLI) { r.fI = 0; }
+  else if constexpr (id == OP_SEI) { r.fI = 1; }
+  else if constexpr (id == OP_CLV) { r.fV = 0; }
+  else if constexpr (id == OP_CLD) { r.fD = 0; }
+  else if constexpr (id == OP_SED) { r.fD = 1; }
+  else if constexpr (id == OP_TAX) { r.X = r.A; set_nz(r, r.X); }
+  else if constexpr (id == OP_TXA) { r.A = r.X; set_nz(r, r.A); }
+  else if constexpr (id == OP_TAY) { r.Y = r.A; set_nz(r, r.Y); }
+  else if constexpr (id == OP_TYA) { r.A = r.Y; set_nz(r, r.A); }
+  else if constexpr (id == OP_TSX) { r.X = r.SP; set_nz(r, r.X); }
+  else if constexpr (id == OP_TXS) { r.SP = r.X; }
+  else if constexpr (id == OP_INX) { r.X = (r.X + 1) & 0xFF; set_nz(r, r.X); }
+  else if constexpr (id == OP_DEX) { r.X = (r.X - 1) & 0xFF; set_nz(r, r.X); }
+  else if constexpr (id == OP_INY) { r.Y = (r.Y + 1) & 0xFF; set_nz(r, r.Y); }
+  else if constexpr (id == OP_DEY) { r.Y = (r.Y - 1) & 0xFF; set_nz(r, r.Y); }
+  // OP_NOP: nothing
+  p.n = n;
+  p.ea = ea;
+}
+
 // Execute one instruction slot (an instruction, or for a jammed CPU an idle
 // to the next line start) and advance the clocks.
 //
@@ -216,221 +410,50 @@ constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8)
 // the 4 KB window the opcode and both operand bytes are read at once (three
 // independent shared-memory loads; such reads have no side effect and do not
 // depend on time).  Elsewhere the operand bytes are real bus accesses and are
-// read one by one, only as many as the instruction has.  Each instruction
-// then makes at most one data read (read and read-modify-write classes) and
-// its writes, through single call sites.
+// read one by one, only as many as the instruction has.  Then one switch on
+// the opcode runs the instruction's specialised handler, and its writes go
+// through the single write site below.
 template <class Tape>
 __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape) {
-  if (r.jam) {
-    uint32_t d = 76u - (uint32_t)r.fc % 76u;
-    r.cyc += d;
-    r.fc += (int32_t)d;
-    return;
-  }
   const uint32_t opaddr = r.PC;
   r.intim_live = 0;
   const uint32_t off = opaddr & 0xFFF;
   const bool fast = (opaddr & 0x1000) != 0 && off <= 0xFF5;
-  uint32_t op, b1 = 0, b2 = 0;
-  if (fast) {
-    const uint8_t* q = c.rom + ((r.bank << 12) | off);
-    op = q[0];
-    b1 = q[1];
-    b2 = q[2];
-  } else {
+  const uint8_t* q = c.rom + ((r.bank << 12) | (off <= 0xFF5 ? off : 0xFF5u));
+  uint32_t op = q[0], b1 = q[1], b2 = q[2];
+  if (!fast && !r.jam) {
     op = bus_read(c, r, st, opaddr, 1);
+    const uint32_t len = (kModeLen >> (2 * (c.dt->mode_cyc[op] & 15))) & 3;
+    if (len >= 2) b1 = bus_read(c, r, st, (opaddr + 1) & 0xFFFF, 2);
+    if (len >= 3) b2 = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, op == 0x20 ? 6 : 3);
   }
-  const uint32_t mc = c.dt->mode_cyc[op], co = c.dt->cls_op[op];
-  const uint32_t mode = mc & 15, cls = co & 3, id = co >> 2;
-  uint32_t n = mc >> 4;
-  const uint32_t len = (kModeLen >> (2 * mode)) & 3;
-  const uint32_t pc1 = (opaddr + 1) & 0xFFFF;
-  if (!fast) {
-    if (len >= 2) b1 = bus_read(c, r, st, pc1, 2);
-    if (len >= 3) b2 = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, id == OP_JSR ? 6 : 3);
+  Pend p;
+  switch (r.jam ? 0x100u : op) {
+#define VCS_CASE(x) \
+  case x: exec_op<x>(c, r, st, opaddr, b1, b2, p); break;
+    VCS_DOCUMENTED_OPS(VCS_CASE)
+#undef VCS_CASE
+    default:   // an undocumented opcode jams the CPU after its fetch; a jammed CPU idles to the next line
+      p.n = r.jam ? 76u - (uint32_t)r.fc % 76u : 1u;
+      r.PC = r.jam ? r.PC : (opaddr + 1) & 0xFFFF;
+      r.jam = 1;
+      p.nw = 0;
+      p.wstack = false;
+      p.rec = false;
+      break;
   }
-  if (mode == AM_JAM) {   // undocumented opcode: the CPU jams after the fetch
-    r.PC = pc1;
-    r.jam = 1;
-    r.cyc += 1;
-    r.fc += 1;
-    return;
-  }
-  r.PC = (opaddr + len) & 0xFFFF;
-  uint32_t ea = 0;
-  bool cross = false;
-  switch (mode) {
-    case AM_IMM: ea = pc1; break;
-    case AM_ZP: ea = b1; break;
-    case AM_ZPX: ea = (b1 + r.X) & 0xFF; break;
-    case AM_ZPY: ea = (b1 + r.Y) & 0xFF; break;
-    case AM_ABS: ea = b1 | (b2 << 8); break;
-    case AM_ABX:
-    case AM_ABY: {
-      const uint32_t base = b1 | (b2 << 8);
-      ea = (base + (mode == AM_ABX ? r.X : r.Y)) & 0xFFFF;
-      cross = ((base ^ ea) & 0xFF00) != 0;
-      break;
-    }
-    case AM_INX: {
-      const uint32_t p = (b1 + r.X) & 0xFF;
-      const uint32_t lo = bus_read(c, r, st, p, 4);
-      const uint32_t hi = bus_read(c, r, st, (p + 1) & 0xFF, 5);
-      ea = lo | (hi << 8);
-      break;
-    }
-    case AM_INY: {
-      const uint32_t lo = bus_read(c, r, st, b1, 3);
-      const uint32_t hi = bus_read(c, r, st, (b1 + 1) & 0xFF, 4);
-      const uint32_t base = lo | (hi << 8);
-      ea = (base + r.Y) & 0xFFFF;
-      cross = ((base ^ ea) & 0xFF00) != 0;
-      break;
-    }
-    default: break;
-  }
-
-  // the one data read: read-class instructions read on their last cycle
-  // (after any page-cross cycle), read-modify-write two cycles before the end
-  uint32_t m = 0;
-  if (cls == CL_READ) {
-    n += cross ? 1u : 0u;
-    m = mode == AM_IMM ? b1 : bus_read(c, r, st, ea, (int)n);
-  } else if (cls == CL_RMW) {
-    m = bus_read(c, r, st, ea, (int)n - 2);
-  }
-  uint32_t tref = ea, tfl = 0;
-  // pending writes: nw bytes of wv (low byte first) at cycles widx, widx+1,
-  // ... to ea, or to the stack (0x100 | SP, descending) when wstack
-  uint32_t nw = 0, wv = 0, widx = n;
-  bool wstack = false;
-  switch (id) {
-    case OP_LDA: r.A = m; set_nz(r, m); break;
-    case OP_LDX: r.X = m; set_nz(r, m); break;
-    case OP_LDY: r.Y = m; set_nz(r, m); break;
-    case OP_ORA: r.A |= m; set_nz(r, r.A); break;
-    case OP_AND: r.A &= m; set_nz(r, r.A); break;
-    case OP_EOR: r.A ^= m; set_nz(r, r.A); break;
-    case OP_ADC: do_adc(r, m); break;
-    case OP_SBC: do_sbc(r, m); break;
-    case OP_CMP: do_cmp(r, r.A, m); break;
-    case OP_CPX: do_cmp(r, r.X, m); break;
-    case OP_CPY: do_cmp(r, r.Y, m); break;
-    case OP_BIT:
-      r.nsrc = m & 0x80;
-      r.fV = (m >> 6) & 1;
-      r.zsrc = r.A & m;
-      break;
-    case OP_STA: nw = 1; wv = r.A; break;
-    case OP_STX: nw = 1; wv = r.X; break;
-    case OP_STY: nw = 1; wv = r.Y; break;
-    case OP_ASL: case OP_ROL: case OP_LSR: case OP_ROR:
-      wv = do_shift(r, id - OP_ASL, m);
-      nw = 1;
-      break;
-    case OP_DEC: case OP_INC:
-      wv = (id == OP_DEC ? m - 1 : m + 1) & 0xFF;
-      set_nz(r, wv);
-      nw = 1;
-      break;
-    case OP_ASLA: case OP_ROLA: case OP_LSRA: case OP_RORA:
-      r.A = do_shift(r, id - OP_ASLA, r.A);
-      break;
-    case OP_BRANCH: {
-      uint32_t flag;
-      switch (op >> 6) {
-        case 0: flag = (r.nsrc >> 7) & 1; break;
-        case 1: flag = r.fV; break;
-        case 2: flag = r.fC; break;
-        default: flag = (r.zsrc & 0xFF) == 0 ? 1u : 0u; break;
-      }
-      const uint32_t taken = ((op >> 5) & 1) == flag ? 1u : 0u;
-      if (taken) {
-        const uint32_t next = r.PC;
-        const uint32_t t = (next + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF;
-        n += 1 + (((t ^ next) & 0xFF00) ? 1u : 0u);
-        r.PC = t;
-      }
-      tref = pc1;
-      tfl = taken;
-      break;
-    }
-    case OP_JMP: r.PC = ea; break;
-    case OP_JMPI: {
-      const uint32_t p = b1 | (b2 << 8);
-      const uint32_t l2 = bus_read(c, r, st, p, 4);
-      const uint32_t h2 = bus_read(c, r, st, (p & 0xFF00) | ((p + 1) & 0xFF), 5);
-      r.PC = l2 | (h2 << 8);
-      break;
-    }
-    case OP_JSR: {
-      const uint32_t ret = (opaddr + 2) & 0xFFFF;
-      r.PC = b1 | (b2 << 8);
-      nw = 2; wstack = true; wv = (ret >> 8) | ((ret & 0xFF) << 8); widx = 4;
-      break;
-    }
-    case OP_RTS: {
-      const uint32_t lo = pull(c, r, st, 4);
-      const uint32_t hi = pull(c, r, st, 5);
-      r.PC = ((lo | (hi << 8)) + 1) & 0xFFFF;
-      break;
-    }
-    case OP_RTI: {
-      const uint32_t p = pull(c, r, st, 4);
-      const uint32_t lo = pull(c, r, st, 5);
-      const uint32_t hi = pull(c, r, st, 6);
-      unpack_p(r, p | 0x30);
-      r.PC = lo | (hi << 8);
-      break;
-    }
-    case OP_BRK: {
-      const uint32_t ret = (opaddr + 2) & 0xFFFF;
-      nw = 3; wstack = true; wv = (ret >> 8) | ((ret & 0xFF) << 8) | (pack_p(r) << 16); widx = 3;
-      r.fI = 1;
-      const uint32_t lo = bus_read(c, r, st, 0xFFFE, 6);
-      const uint32_t hi = bus_read(c, r, st, 0xFFFF, 7);
-      r.PC = lo | (hi << 8);
-      break;
-    }
-    case OP_PHA: nw = 1; wstack = true; wv = r.A; widx = 3; break;
-    case OP_PHP: nw = 1; wstack = true; wv = pack_p(r); widx = 3; break;
-    case OP_PLA:
-      r.A = pull(c, r, st, 4);
-      set_nz(r, r.A);
-      tref = 0x100u | r.SP;
-      break;
-    case OP_PLP: unpack_p(r, pull(c, r, st, 4) | 0x30); break;
-    case OP_CLC: r.fC = 0; break;
-    case OP_SEC: r.fC = 1; break;
-    case OP_CLI: r.fI = 0; break;
-    case OP_SEI: r.fI = 1; break;
-    case OP_CLV: r.fV = 0; break;
-    case OP_CLD: r.fD = 0; break;
-    case OP_SED: r.fD = 1; break;
-    case OP_TAX: r.X = r.A; set_nz(r, r.X); break;
-    case OP_TXA: r.A = r.X; set_nz(r, r.A); break;
-    case OP_TAY: r.Y = r.A; set_nz(r, r.Y); break;
-    case OP_TYA: r.A = r.Y; set_nz(r, r.A); break;
-    case OP_TSX: r.X = r.SP; set_nz(r, r.X); break;
-    case OP_TXS: r.SP = r.X; break;
-    case OP_INX: r.X = (r.X + 1) & 0xFF; set_nz(r, r.X); break;
-    case OP_DEX: r.X = (r.X - 1) & 0xFF; set_nz(r, r.X); break;
-    case OP_INY: r.Y = (r.Y + 1) & 0xFF; set_nz(r, r.Y); break;
-    case OP_DEY: r.Y = (r.Y - 1) & 0xFF; set_nz(r, r.Y); break;
-    default: break;   // NOP
-  }
-  if (wstack) tref = 0x100u | r.SP;
-  for (uint32_t i = 0; i < nw; i++) {
-    uint32_t addr = ea;
-    if (wstack) {
+  if (p.wstack) p.tref = 0x100u | r.SP;
+  for (uint32_t i = 0; i < p.nw; i++) {
+    uint32_t addr = p.ea;
+    if (p.wstack) {
       addr = 0x100u | r.SP;
       r.SP = (r.SP - 1) & 0xFF;
     }
-    bus_write(c, r, rd, st, tape, addr, (wv >> (8 * i)) & 0xFF, (int)(widx + i));
+    bus_write(c, r, rd, st, tape, addr, (p.wv >> (8 * i)) & 0xFF, (int)(p.widx + i));
   }
-  tape.rec(op, tref, tfl | (r.bank << 1) | (r.intim_live << 2));
-  r.cyc += n + (uint32_t)st.stall;
-  r.fc += (int32_t)n + st.stall;
+  if (p.rec) tape.rec(op, p.tref, p.tfl | (r.bank << 1) | (r.intim_live << 2));
+  r.cyc += p.n + (uint32_t)st.stall;
+  r.fc += (int32_t)p.n + st.stall;
   st.stall = 0;
 }
 

@@ -18,69 +18,15 @@
 
 namespace vcs {
 
-// ---------------------------------------------------------------------------
-// decode table (MOS 6500 instruction set: addressing mode, base cycles)
-// ---------------------------------------------------------------------------
+// Decode table for the paths that decode at run time (the operand fetch
+// outside the cartridge window), built from op_info.
 
 void build_decode_tables(DecodeTables* t) {
-  for (int i = 0; i < 256; i++) {
-    t->mode_cyc[i] = AM_JAM | (1 << 4);
-    t->cls_op[i] = CL_OTHER | (OP_JAM << 2);
+  for (uint32_t op = 0; op < 256; op++) {
+    const OpInfo i = op_info(op);
+    t->mode_cyc[op] = (uint8_t)(i.mode | (i.cyc << 4));
+    t->cls_op[op] = (uint8_t)(i.cls | (i.id << 2));
   }
-  auto set = [&](int op, int mode, int cyc, int cls, int id) {
-    t->mode_cyc[op] = (uint8_t)(mode | (cyc << 4));
-    t->cls_op[op] = (uint8_t)(cls | (id << 2));
-  };
-  // the regular "cc = 01" column: ORA AND EOR ADC STA LDA CMP SBC
-  const int m01[8] = {AM_INX, AM_ZP, AM_IMM, AM_ABS, AM_INY, AM_ZPX, AM_ABY, AM_ABX};
-  const int c01[8] = {6, 3, 2, 4, 5, 4, 4, 4};
-  const int id01[8] = {OP_ORA, OP_AND, OP_EOR, OP_ADC, OP_STA, OP_LDA, OP_CMP, OP_SBC};
-  for (int aaa = 0; aaa < 8; aaa++)
-    for (int bbb = 0; bbb < 8; bbb++) {
-      int op = (aaa << 5) | (bbb << 2) | 1;
-      int cyc = c01[bbb];
-      if (aaa == 4) {            // STA: no immediate; indexed stores pay the fix-up cycle
-        if (m01[bbb] == AM_IMM) continue;
-        if (m01[bbb] == AM_INY) cyc = 6;
-        if (m01[bbb] == AM_ABX || m01[bbb] == AM_ABY) cyc = 5;
-        set(op, m01[bbb], cyc, CL_STORE, OP_STA);
-      } else {
-        set(op, m01[bbb], cyc, CL_READ, id01[aaa]);
-      }
-    }
-  // shifts, rotates, DEC, INC
-  const int rmw[6] = {0x00, 0x20, 0x40, 0x60, 0xC0, 0xE0};
-  const int idm[6] = {OP_ASL, OP_ROL, OP_LSR, OP_ROR, OP_DEC, OP_INC};
-  const int ida[4] = {OP_ASLA, OP_ROLA, OP_LSRA, OP_RORA};
-  for (int k = 0; k < 6; k++) {
-    int b = rmw[k];
-    if (k < 4) set(b + 0x0A, AM_ACC, 2, CL_OTHER, ida[k]);
-    set(b + 0x06, AM_ZP, 5, CL_RMW, idm[k]);
-    set(b + 0x16, AM_ZPX, 6, CL_RMW, idm[k]);
-    set(b + 0x0E, AM_ABS, 6, CL_RMW, idm[k]);
-    set(b + 0x1E, AM_ABX, 7, CL_RMW, idm[k]);
-  }
-  set(0xA2, AM_IMM, 2, CL_READ, OP_LDX); set(0xA6, AM_ZP, 3, CL_READ, OP_LDX);
-  set(0xB6, AM_ZPY, 4, CL_READ, OP_LDX); set(0xAE, AM_ABS, 4, CL_READ, OP_LDX);
-  set(0xBE, AM_ABY, 4, CL_READ, OP_LDX);
-  set(0xA0, AM_IMM, 2, CL_READ, OP_LDY); set(0xA4, AM_ZP, 3, CL_READ, OP_LDY);
-  set(0xB4, AM_ZPX, 4, CL_READ, OP_LDY); set(0xAC, AM_ABS, 4, CL_READ, OP_LDY);
-  set(0xBC, AM_ABX, 4, CL_READ, OP_LDY);
-  set(0x86, AM_ZP, 3, CL_STORE, OP_STX); set(0x96, AM_ZPY, 4, CL_STORE, OP_STX); set(0x8E, AM_ABS, 4, CL_STORE, OP_STX);
-  set(0x84, AM_ZP, 3, CL_STORE, OP_STY); set(0x94, AM_ZPX, 4, CL_STORE, OP_STY); set(0x8C, AM_ABS, 4, CL_STORE, OP_STY);
-  set(0xE0, AM_IMM, 2, CL_READ, OP_CPX); set(0xE4, AM_ZP, 3, CL_READ, OP_CPX); set(0xEC, AM_ABS, 4, CL_READ, OP_CPX);
-  set(0xC0, AM_IMM, 2, CL_READ, OP_CPY); set(0xC4, AM_ZP, 3, CL_READ, OP_CPY); set(0xCC, AM_ABS, 4, CL_READ, OP_CPY);
-  set(0x24, AM_ZP, 3, CL_READ, OP_BIT); set(0x2C, AM_ABS, 4, CL_READ, OP_BIT);
-  for (int op : {0x10, 0x30, 0x50, 0x70, 0x90, 0xB0, 0xD0, 0xF0}) set(op, AM_REL, 2, CL_OTHER, OP_BRANCH);
-  set(0x4C, AM_ABS, 3, CL_OTHER, OP_JMP); set(0x6C, AM_IND, 5, CL_OTHER, OP_JMPI); set(0x20, AM_IND, 6, CL_OTHER, OP_JSR);
-  set(0x60, AM_IMP, 6, CL_OTHER, OP_RTS); set(0x40, AM_IMP, 6, CL_OTHER, OP_RTI); set(0x00, AM_IMP, 7, CL_OTHER, OP_BRK);
-  set(0x48, AM_IMP, 3, CL_OTHER, OP_PHA); set(0x08, AM_IMP, 3, CL_OTHER, OP_PHP);
-  set(0x68, AM_IMP, 4, CL_OTHER, OP_PLA); set(0x28, AM_IMP, 4, CL_OTHER, OP_PLP);
-  const int imp_ops[18][2] = {{0x18, OP_CLC}, {0x38, OP_SEC}, {0x58, OP_CLI}, {0x78, OP_SEI}, {0xB8, OP_CLV},
-                              {0xD8, OP_CLD}, {0xF8, OP_SED}, {0xEA, OP_NOP}, {0xAA, OP_TAX}, {0x8A, OP_TXA},
-                              {0xA8, OP_TAY}, {0x98, OP_TYA}, {0xBA, OP_TSX}, {0x9A, OP_TXS}, {0xE8, OP_INX},
-                              {0xCA, OP_DEX}, {0xC8, OP_INY}, {0x88, OP_DEY}};
-  for (auto& q : imp_ops) set(q[0], AM_IMP, 2, CL_OTHER, q[1]);
 }
 
 // Counts instructions and colour-register writes per checkpoint segment (the

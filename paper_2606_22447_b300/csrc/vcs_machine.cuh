@@ -60,6 +60,96 @@ struct DecodeTables {
   uint8_t cls_op[256];
 };
 
+// Addressing mode, base cycle count (MOS 6500 data sheet), class and
+// operation of one opcode; undocumented opcodes decode as AM_JAM.  This is
+// the one definition of the instruction set: the step kernel specialises its
+// handlers on it at compile time and the host builds DecodeTables from it.
+struct OpInfo {
+  uint8_t mode, cyc, cls, id;
+};
+
+__host__ __device__ constexpr OpInfo op_info(uint32_t op) {
+  if ((op & 3) == 1) {   // the regular column: ORA AND EOR ADC STA LDA CMP SBC over eight modes
+    const uint32_t aaa = op >> 5, bbb = (op >> 2) & 7;
+    const uint8_t modes[8] = {AM_INX, AM_ZP, AM_IMM, AM_ABS, AM_INY, AM_ZPX, AM_ABY, AM_ABX};
+    const uint8_t cyc[8] = {6, 3, 2, 4, 5, 4, 4, 4};
+    const uint8_t ids[8] = {OP_ORA, OP_AND, OP_EOR, OP_ADC, OP_STA, OP_LDA, OP_CMP, OP_SBC};
+    if (aaa == 4) {   // STA: no immediate form; indexed stores always pay the fix-up cycle
+      if (modes[bbb] == AM_IMM) return OpInfo{AM_JAM, 1, CL_OTHER, OP_JAM};
+      const uint8_t c = modes[bbb] == AM_INY ? 6 : (modes[bbb] == AM_ABX || modes[bbb] == AM_ABY) ? 5 : cyc[bbb];
+      return OpInfo{modes[bbb], c, CL_STORE, OP_STA};
+    }
+    return OpInfo{modes[bbb], cyc[bbb], CL_READ, ids[aaa]};
+  }
+  const uint32_t hi = op & 0xE0, lo = op & 0x1F;
+  if (hi <= 0x60 || hi == 0xC0 || hi == 0xE0) {   // shifts, rotates, DEC, INC
+    const uint8_t id = hi == 0x00 ? OP_ASL : hi == 0x20 ? OP_ROL : hi == 0x40 ? OP_LSR
+                     : hi == 0x60 ? OP_ROR : hi == 0xC0 ? OP_DEC : OP_INC;
+    if (lo == 0x0A && hi <= 0x60) return OpInfo{AM_ACC, 2, CL_OTHER, (uint8_t)(OP_ASLA + (id - OP_ASL))};
+    if (lo == 0x06) return OpInfo{AM_ZP, 5, CL_RMW, id};
+    if (lo == 0x16) return OpInfo{AM_ZPX, 6, CL_RMW, id};
+    if (lo == 0x0E) return OpInfo{AM_ABS, 6, CL_RMW, id};
+    if (lo == 0x1E) return OpInfo{AM_ABX, 7, CL_RMW, id};
+  }
+  switch (op) {
+    case 0xA2: return OpInfo{AM_IMM, 2, CL_READ, OP_LDX};
+    case 0xA6: return OpInfo{AM_ZP, 3, CL_READ, OP_LDX};
+    case 0xB6: return OpInfo{AM_ZPY, 4, CL_READ, OP_LDX};
+    case 0xAE: return OpInfo{AM_ABS, 4, CL_READ, OP_LDX};
+    case 0xBE: return OpInfo{AM_ABY, 4, CL_READ, OP_LDX};
+    case 0xA0: return OpInfo{AM_IMM, 2, CL_READ, OP_LDY};
+    case 0xA4: return OpInfo{AM_ZP, 3, CL_READ, OP_LDY};
+    case 0xB4: return OpInfo{AM_ZPX, 4, CL_READ, OP_LDY};
+    case 0xAC: return OpInfo{AM_ABS, 4, CL_READ, OP_LDY};
+    case 0xBC: return OpInfo{AM_ABX, 4, CL_READ, OP_LDY};
+    case 0x86: return OpInfo{AM_ZP, 3, CL_STORE, OP_STX};
+    case 0x96: return OpInfo{AM_ZPY, 4, CL_STORE, OP_STX};
+    case 0x8E: return OpInfo{AM_ABS, 4, CL_STORE, OP_STX};
+    case 0x84: return OpInfo{AM_ZP, 3, CL_STORE, OP_STY};
+    case 0x94: return OpInfo{AM_ZPX, 4, CL_STORE, OP_STY};
+    case 0x8C: return OpInfo{AM_ABS, 4, CL_STORE, OP_STY};
+    case 0xE0: return OpInfo{AM_IMM, 2, CL_READ, OP_CPX};
+    case 0xE4: return OpInfo{AM_ZP, 3, CL_READ, OP_CPX};
+    case 0xEC: return OpInfo{AM_ABS, 4, CL_READ, OP_CPX};
+    case 0xC0: return OpInfo{AM_IMM, 2, CL_READ, OP_CPY};
+    case 0xC4: return OpInfo{AM_ZP, 3, CL_READ, OP_CPY};
+    case 0xCC: return OpInfo{AM_ABS, 4, CL_READ, OP_CPY};
+    case 0x24: return OpInfo{AM_ZP, 3, CL_READ, OP_BIT};
+    case 0x2C: return OpInfo{AM_ABS, 4, CL_READ, OP_BIT};
+    case 0x10: case 0x30: case 0x50: case 0x70: case 0x90: case 0xB0: case 0xD0: case 0xF0:
+      return OpInfo{AM_REL, 2, CL_OTHER, OP_BRANCH};
+    case 0x4C: return OpInfo{AM_ABS, 3, CL_OTHER, OP_JMP};
+    case 0x6C: return OpInfo{AM_IND, 5, CL_OTHER, OP_JMPI};
+    case 0x20: return OpInfo{AM_IND, 6, CL_OTHER, OP_JSR};
+    case 0x60: return OpInfo{AM_IMP, 6, CL_OTHER, OP_RTS};
+    case 0x40: return OpInfo{AM_IMP, 6, CL_OTHER, OP_RTI};
+    case 0x00: return OpInfo{AM_IMP, 7, CL_OTHER, OP_BRK};
+    case 0x48: return OpInfo{AM_IMP, 3, CL_OTHER, OP_PHA};
+    case 0x08: return OpInfo{AM_IMP, 3, CL_OTHER, OP_PHP};
+    case 0x68: return OpInfo{AM_IMP, 4, CL_OTHER, OP_PLA};
+    case 0x28: return OpInfo{AM_IMP, 4, CL_OTHER, OP_PLP};
+    case 0x18: return OpInfo{AM_IMP, 2, CL_OTHER, OP_CLC};
+    case 0x38: return OpInfo{AM_IMP, 2, CL_OTHER, OP_SEC};
+    case 0x58: return OpInfo{AM_IMP, 2, CL_OTHER, OP_CLI};
+    case 0x78: return OpInfo{AM_IMP, 2, CL_OTHER, OP_SEI};
+    case 0xB8: return OpInfo{AM_IMP, 2, CL_OTHER, OP_CLV};
+    case 0xD8: return OpInfo{AM_IMP, 2, CL_OTHER, OP_CLD};
+    case 0xF8: return OpInfo{AM_IMP, 2, CL_OTHER, OP_SED};
+    case 0xEA: return OpInfo{AM_IMP, 2, CL_OTHER, OP_NOP};
+    case 0xAA: return OpInfo{AM_IMP, 2, CL_OTHER, OP_TAX};
+    case 0x8A: return OpInfo{AM_IMP, 2, CL_OTHER, OP_TXA};
+    case 0xA8: return OpInfo{AM_IMP, 2, CL_OTHER, OP_TAY};
+    case 0x98: return OpInfo{AM_IMP, 2, CL_OTHER, OP_TYA};
+    case 0xBA: return OpInfo{AM_IMP, 2, CL_OTHER, OP_TSX};
+    case 0x9A: return OpInfo{AM_IMP, 2, CL_OTHER, OP_TXS};
+    case 0xE8: return OpInfo{AM_IMP, 2, CL_OTHER, OP_INX};
+    case 0xCA: return OpInfo{AM_IMP, 2, CL_OTHER, OP_DEX};
+    case 0xC8: return OpInfo{AM_IMP, 2, CL_OTHER, OP_INY};
+    case 0x88: return OpInfo{AM_IMP, 2, CL_OTHER, OP_DEY};
+    default: return OpInfo{AM_JAM, 1, CL_OTHER, OP_JAM};
+  }
+}
+
 // Machine registers of one env (kept in registers inside a launch).
 struct Regs {
   uint32_t A, X, Y, SP, PC;
