@@ -17,6 +17,8 @@
 // writes that can follow a VSYNC write in one instruction land on TIA
 // register $3F or in RAM, neither of which is drawn.
 #pragma once
+#include <type_traits>
+
 #include "vcs_machine.cuh"
 
 namespace vcs {
@@ -237,12 +239,44 @@ __host__ __device__ constexpr bool page_zero_mode() {
   return MODE == AM_ZP || MODE == AM_ZPX || MODE == AM_ZPY;
 }
 
+// Timer poll loop "L: LDA INTIM; BNE L" (AD 84 02 D0 FB) entered at its LDA,
+// before the timer's underflow: advance the clocks over the iterations that
+// read a nonzero value, so that the LDA about to execute is the first one
+// that reads zero (or the last one before the scanline watchdog).  Exact:
+// the skipped iterations write nothing and every register they set is set
+// again by that LDA; the timer value read k cycles after the write of V with
+// interval I is V - ceil(k / I), zero for (V - 1) I < k <= V I.  A loop that
+// would step over that window (only possible for I = 1) or that starts after
+// the underflow is left to the interpreter.
+__device__ __forceinline__ void skip_timer_poll(Regs& r, uint32_t opaddr) {
+  const uint32_t period = 7u + ((((opaddr + 5u) ^ opaddr) & 0xFF00) ? 1u : 0u);   // LDA 4 + BNE taken 3 (+1 page cross)
+  const uint32_t vi = r.tv << r.tsh;
+  const uint32_t k0 = r.cyc + 4u - r.tw;   // the LDA reads on its fourth cycle
+  if (r.tv == 0 || k0 > vi) return;
+  const uint32_t lo = (r.tv - 1u) << r.tsh;
+  uint32_t j = k0 > lo ? 0u : (period == 7u ? (lo - k0) / 7u : (lo - k0) >> 3) + 1u;
+  if (k0 + j * period > vi) return;
+  const int32_t room = kLineCap * kLineCycles - 1 - r.fc;   // stay below the watchdog
+  const uint32_t jw = room > 0 ? (period == 7u ? (uint32_t)room / 7u : (uint32_t)room >> 3) : 0u;
+  j = j < jw ? j : jw;
+  r.cyc += j * period;
+  r.fc += (int32_t)(j * period);
+}
+
 // One documented instruction, specialised on its opcode: mode, class and
 // operation are compile-time constants, so the only run-time dispatch of an
-// instruction is the opcode switch in exec_one.
-template <uint32_t OP>
+// instruction is the opcode switch in exec_one.  kSkipPoll enables the timer
+// poll-loop skip (the hard path; the soft path records every instruction).
+template <uint32_t OP, bool kSkipPoll>
 __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_t opaddr, uint32_t b1, uint32_t b2,
                                         Pend& p) {
+  if constexpr (OP == 0xAD && kSkipPoll) {
+    const uint32_t off = opaddr & 0xFFF;
+    if (b1 == 0x84 && b2 == 0x02 && (opaddr & 0x1000) && off <= 0xFFA) {
+      const uint8_t* q = c.rom + ((r.bank << 12) | off);
+      if (q[3] == 0xD0 && q[4] == 0xFB) skip_timer_poll(r, opaddr);
+    }
+  }
   constexpr OpInfo I = op_info(OP);
   constexpr uint32_t mode = I.mode, cls = I.cls, id = I.id;
   constexpr uint32_t len = (kModeLen >> (2 * mode)) & 3;
@@ -403,58 +437,78 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
   p.ea = ea;
 }
 
+// Instruction bytes at the program counter, fetched ahead: opcode | first
+// operand << 8 | second operand << 16, or kSlowFetch when the bytes must be
+// read through the bus at execution time (outside the cartridge window, near
+// its end or the F8 hotspots).  Fetching from the cartridge has no side
+// effect and does not depend on time, so it may happen as soon as the
+// program counter and bank are known.
+constexpr uint32_t kSlowFetch = 1u << 24;
+
+__device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
+  const uint32_t off = r.PC & 0xFFF;
+  const bool fast = (r.PC & 0x1000) != 0 && off <= 0xFF5;
+  const uint8_t* q = c.rom + ((r.bank << 12) | (fast ? off : 0u));
+  return (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) | (fast ? 0u : kSlowFetch);
+}
+
 // Execute one instruction slot (an instruction, or for a jammed CPU an idle
-// to the next line start) and advance the clocks.
+// to the next line start), advance the clocks and prefetch the next
+// instruction's bytes into pf.
 //
-// Fetch: inside the cartridge and away from the F8 hotspots and the end of
-// the 4 KB window the opcode and both operand bytes are read at once (three
-// independent shared-memory loads; such reads have no side effect and do not
-// depend on time).  Elsewhere the operand bytes are real bus accesses and are
-// read one by one, only as many as the instruction has.  Then one switch on
-// the opcode runs the instruction's specialised handler, and its writes go
-// through the single write site below.
+// One switch runs the instruction's specialised handler; the two rare slots
+// (a fetch through the bus, a jammed CPU) are cases of the same switch, so
+// the common path has a single dispatch.  A bus fetch reads the operand
+// bytes one by one, only as many as the instruction has, and dispatches
+// again.  Writes go through the single write site below.
 template <class Tape>
-__device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape) {
+__device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t& pf) {
   const uint32_t opaddr = r.PC;
   r.intim_live = 0;
-  const uint32_t off = opaddr & 0xFFF;
-  const bool fast = (opaddr & 0x1000) != 0 && off <= 0xFF5;
-  const uint8_t* q = c.rom + ((r.bank << 12) | (off <= 0xFF5 ? off : 0xFF5u));
-  uint32_t op = q[0], b1 = q[1], b2 = q[2];
-  if (!fast && !r.jam) {
-    op = bus_read(c, r, st, opaddr, 1);
-    const uint32_t len = (kModeLen >> (2 * (c.dt->mode_cyc[op] & 15))) & 3;
-    if (len >= 2) b1 = bus_read(c, r, st, (opaddr + 1) & 0xFFFF, 2);
-    if (len >= 3) b2 = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, op == 0x20 ? 6 : 3);
-  }
+  uint32_t op = pf & 0xFF, b1 = (pf >> 8) & 0xFF, b2 = (pf >> 16) & 0xFF;
+  uint32_t sel = r.jam ? 0x100u : ((pf & kSlowFetch) ? 0x101u : op);
   Pend p;
-  switch (r.jam ? 0x100u : op) {
+  for (;;) {
+    switch (sel) {
 #define VCS_CASE(x) \
-  case x: exec_op<x>(c, r, st, opaddr, b1, b2, p); break;
-    VCS_DOCUMENTED_OPS(VCS_CASE)
+  case x: exec_op<x, std::is_same<Tape, NoTape>::value>(c, r, st, opaddr, b1, b2, p); break;
+      VCS_DOCUMENTED_OPS(VCS_CASE)
 #undef VCS_CASE
-    default:   // an undocumented opcode jams the CPU after its fetch; a jammed CPU idles to the next line
-      p.n = r.jam ? 76u - (uint32_t)r.fc % 76u : 1u;
-      r.PC = r.jam ? r.PC : (opaddr + 1) & 0xFFFF;
-      r.jam = 1;
-      p.nw = 0;
-      p.wstack = false;
-      p.rec = false;
-      break;
-  }
-  if (p.wstack) p.tref = 0x100u | r.SP;
-  for (uint32_t i = 0; i < p.nw; i++) {
-    uint32_t addr = p.ea;
-    if (p.wstack) {
-      addr = 0x100u | r.SP;
-      r.SP = (r.SP - 1) & 0xFF;
+      case 0x101: {   // fetch through the bus, then dispatch on what was read
+        op = bus_read(c, r, st, opaddr, 1);
+        const uint32_t len = (kModeLen >> (2 * (c.dt->mode_cyc[op] & 15))) & 3;
+        if (len >= 2) b1 = bus_read(c, r, st, (opaddr + 1) & 0xFFFF, 2);
+        if (len >= 3) b2 = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, op == 0x20 ? 6 : 3);
+        sel = op;
+        continue;
+      }
+      default:   // an undocumented opcode jams the CPU after its fetch; a jammed CPU idles to the next line
+        p.n = r.jam ? 76u - (uint32_t)r.fc % 76u : 1u;
+        r.PC = r.jam ? r.PC : (opaddr + 1) & 0xFFFF;
+        r.jam = 1;
+        p.nw = 0;
+        p.rec = false;
+        break;
     }
-    bus_write(c, r, rd, st, tape, addr, (p.wv >> (8 * i)) & 0xFF, (int)(p.widx + i));
+    break;
+  }
+  if (p.nw) {
+    if (p.wstack) p.tref = 0x100u | r.SP;
+    uint32_t i = 0;
+    do {
+      uint32_t addr = p.ea;
+      if (p.wstack) {
+        addr = 0x100u | r.SP;
+        r.SP = (r.SP - 1) & 0xFF;
+      }
+      bus_write(c, r, rd, st, tape, addr, (p.wv >> (8 * i)) & 0xFF, (int)(p.widx + i));
+    } while (++i < p.nw);
   }
   if (p.rec) tape.rec(op, p.tref, p.tfl | (r.bank << 1) | (r.intim_live << 2));
   r.cyc += p.n + (uint32_t)st.stall;
   r.fc += (int32_t)p.n + st.stall;
   st.stall = 0;
+  pf = prefetch(c, r);
 }
 
 }  // namespace vcs

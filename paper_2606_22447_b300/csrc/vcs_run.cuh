@@ -207,6 +207,7 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
   st.fe_at = -1;
   rd.on = active && st.want_screen && st.frame_skip == 1;
   rd.cur = 3 * (int32_t)r.fs;
+  uint32_t pf = prefetch(c, r);
   while (true) {
     const bool live = active && st.frames_done < st.frame_skip;
     const uint32_t pos = policy == 0 ? (r.jam ? 0xFFFFu : r.PC) : (uint32_t)r.fc;
@@ -214,15 +215,10 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
     const uint32_t kmin = __reduce_min_sync(lanes, key);
     if (kmin == 0xFFFFFFFFu) break;
     if (key - kmin > (policy == 0 ? 0u : window)) continue;
-    exec_one(c, r, rd, st, tape);
-    int32_t fe = st.fe_at;
-    bool dog = false;
-    if (fe < 0 && r.fc >= kLineCap * kLineCycles) {
-      fe = r.fc;
-      dog = true;
-    }
-    if (fe >= 0) {
-      frame_end(c, r, rd, st, tape, fe);
+    exec_one(c, r, rd, st, tape, pf);
+    if ((st.fe_at >= 0) | (r.fc >= kLineCap * kLineCycles)) {   // VSYNC frame end, else the watchdog
+      const bool dog = st.fe_at < 0;
+      frame_end(c, r, rd, st, tape, dog ? r.fc : st.fe_at);
       st.fe_at = -1;
       if (dog) st.status |= kStWatchdog;
     }

@@ -202,6 +202,58 @@ def test_edge_case_carts():
     assert np.all(st[:, 0] & 2) and np.all(st[:, 1] & 1) and not np.any(st[:, 2:4])
 
 
+def _poll_rom(timer_reg, value, page_cross=False):
+    """Frame loop around a timer poll "L: LDA INTIM; BNE L", entered after a
+    joystick-dependent delay, so envs and steps poll from different timer
+    phases.  timer_reg $94/$95/$96/$97 = TIM1T/TIM8T/TIM64T/T1024T."""
+    def build(a):
+        a.label("F")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "abs", 0x0280)       # SWCHA: delay of 0..15 loop turns
+        a.op("LSR", "acc"); a.op("LSR", "acc"); a.op("LSR", "acc"); a.op("LSR", "acc")
+        a.op("TAX")
+        a.label("D")
+        a.op("DEX")
+        a.op("BPL", "rel", "D")
+        a.op("LDA", "imm", value)
+        a.op("STA", "abs", 0x0200 | timer_reg)
+        a.op("JMP", "abs", "P")
+        if page_cross:
+            a.at(0x0FD)                   # LDA at $F0FD, BNE at $F100: the taken branch crosses a page
+        a.label("P")
+        a.op("LDA", "abs", 0x0284)
+        a.op("BNE", "rel", "P")
+        a.op("LDA", "abs", 0x0284)
+        a.op("STA", "zp", 0x80)
+        a.op("LDA", "abs", 0x0285)
+        a.op("STA", "zp", 0x81)
+        a.op("INC", "zp", 0x82)
+        a.op("LDA", "zp", 0x82)
+        a.op("STA", "zp", 0x09)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x08)
+        a.op("JMP", "abs", "F")
+    return rom4k(build)
+
+
+def test_timer_poll_loops():
+    """Poll loops at every timer interval: TIM64T and TIM8T (the loop lands in
+    the zero window), TIM1T (a 7-cycle loop can step over the 1-cycle zero
+    window and keeps polling after the underflow), T1024T with a wait longer
+    than the 512-line watchdog (frames end inside the loop), and a loop
+    whose taken branch crosses a page (8-cycle turns)."""
+    roms = [_poll_rom(0x96, 43), _poll_rom(0x95, 200), _poll_rom(0x94, 101), _poll_rom(0x94, 250),
+            _poll_rom(0x97, 100), _poll_rom(0x96, 37, page_cross=True), _poll_rom(0x97, 0)]
+    maps = [synth.MAPPER_4K] * len(roms)
+    env_cart = np.arange(3 * len(roms)) % len(roms)
+    acts = synth.actions(707, len(env_cart), 8)
+    _check_all(roms, maps, env_cart, acts, 2)
+
+
 def test_generated_carts_cover_the_instruction_set():
     """The seeded carts execute (nearly) every documented opcode."""
     seen = set()
