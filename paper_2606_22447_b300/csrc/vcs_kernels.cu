@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t round_byte(float v) {
 // the RAM may be overridden from float values first, and the full state is
 // checkpointed at the start of every segment of seg_steps steps.
 template <bool SOFT>
-__global__ void __launch_bounds__(128) k_run(StepParams p) {
+__global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x, tid = threadIdx.x;
   BlockSmem bs = carve_smem(smem, E);

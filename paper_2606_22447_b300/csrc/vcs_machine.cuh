@@ -290,14 +290,43 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       tape.pixels(acc[0], acc[1], acc[2]);
     }
   } else {
-    for (uint32_t g = g0; g < g1; g++) {
-      uint32_t w = (blank_all || g < blank_g) ? 0u : group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk);
-      uint32_t mask = 0xFFFFFFFFu;
-      if (g == g0) mask <<= 8 * (x0 & 3);
-      if (g == g1 - 1 && (x1 & 3)) mask &= 0xFFFFFFFFu >> (8 * (4 - (x1 & 3)));
-      uint32_t* dst = c.line + g * c.E;
+    // Groups g0 and gl may be partly inside [x0, x1); the ones between are
+    // whole words.  Background and playfield first (one select per group,
+    // the interior unrolled so independent stores overlap), then the
+    // player's two or three groups and the HMOVE blank redrawn on top.
+    uint32_t* const line = c.line;
+    const uint32_t E = c.E, gl = g1 - 1;
+    const uint32_t m0 = 0xFFFFFFFFu << (8 * (x0 & 3));
+    const uint32_t m1 = (x1 & 3) ? 0xFFFFFFFFu >> (8 * (4 - (x1 & 3))) : 0xFFFFFFFFu;
+    auto put = [&](uint32_t g, uint32_t w) {
+      const uint32_t mask = (g == g0 ? m0 : 0xFFFFFFFFu) & (g == gl ? m1 : 0xFFFFFFFFu);
+      uint32_t* dst = line + g * E;
       *dst = mask == 0xFFFFFFFFu ? w : ((*dst & ~mask) | (w & mask));
+    };
+    if (blank_all) {
+      for (uint32_t g = g0; g < g1; g++) put(g, 0u);
+      return;
     }
+    put(g0, ((pfm >> g0) & 1) ? cpf : cbk);
+    if (gl > g0) {
+      uint64_t pfs = pfm >> (g0 + 1);
+#pragma unroll 4
+      for (uint32_t g = g0 + 1; g < gl; g++) {
+        line[g * E] = (pfs & 1) ? cpf : cbk;
+        pfs >>= 1;
+      }
+      put(gl, ((pfm >> gl) & 1) ? cpf : cbk);
+    }
+    if (grev) {
+      const uint32_t gp = r.pos >> 2;
+#pragma unroll
+      for (uint32_t k = 0; k < 3; k++) {
+        uint32_t g = gp + k;
+        g -= g >= 40 ? 40u : 0u;
+        if (g >= g0 && g < g1) put(g, group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk));
+      }
+    }
+    for (uint32_t g = g0; g < blank_g && g < g1; g++) put(g, 0u);
   }
 }
 
