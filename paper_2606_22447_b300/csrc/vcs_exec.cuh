@@ -232,6 +232,7 @@ constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8)
 struct Pend {
   uint32_t n, ea, nw, wv, widx, tref, tfl;
   bool wstack, rec;
+  bool seq;   // the next instruction follows at a PC that every lane executing this one shares
 };
 
 template <uint32_t MODE>
@@ -330,6 +331,9 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
   p.widx = n;
   p.wstack = false;
   p.rec = true;
+  // JMP and JSR go to the same place for every lane; branches, RTS, RTI,
+  // JMP (ind) and BRK end a run of lockstep instructions
+  p.seq = !(id == OP_BRANCH || id == OP_JMPI || id == OP_RTS || id == OP_RTI || id == OP_BRK);
   if constexpr (id == OP_LDA) { r.A = m; set_nz(r, m); }
   else if constexpr (id == OP_LDX) { r.X = m; set_nz(r, m); }
   else if constexpr (id == OP_LDY) { r.Y = m; set_nz(r, m); }
@@ -454,7 +458,9 @@ __device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
 
 // Execute one instruction slot (an instruction, or for a jammed CPU an idle
 // to the next line start), advance the clocks and prefetch the next
-// instruction's bytes into pf.
+// instruction's bytes into pf.  Returns true when the next instruction is at
+// a program counter that every lane executing this one shares (no branch or
+// data-dependent jump), so the warp may go on without re-scheduling.
 //
 // One switch runs the instruction's specialised handler; the two rare slots
 // (a fetch through the bus, a jammed CPU) are cases of the same switch, so
@@ -462,7 +468,7 @@ __device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
 // bytes one by one, only as many as the instruction has, and dispatches
 // again.  Writes go through the single write site below.
 template <class Tape>
-__device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t& pf) {
+__device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t& pf) {
   const uint32_t opaddr = r.PC;
   r.intim_live = 0;
   uint32_t op = pf & 0xFF, b1 = (pf >> 8) & 0xFF, b2 = (pf >> 16) & 0xFF;
@@ -488,6 +494,7 @@ __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step
         r.jam = 1;
         p.nw = 0;
         p.rec = false;
+        p.seq = false;
         break;
     }
     break;
@@ -509,6 +516,7 @@ __device__ __forceinline__ void exec_one(const Ctx& c, Regs& r, Render& rd, Step
   r.fc += (int32_t)p.n + st.stall;
   st.stall = 0;
   pf = prefetch(c, r);
+  return p.seq && !(pf & kSlowFetch);
 }
 
 }  // namespace vcs

@@ -196,7 +196,9 @@ __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Ste
 //    the others catch up, so they meet at the same instruction again.
 //  - policy 1 (emulated time): the lanes whose step-relative time is within
 //    `window` cycles of the earliest lane's.
-// Each lane's emulation is independent, so the order changes no result.
+// The chosen lanes then run to the end of their basic block (exec_one says
+// when an instruction can change control flow).  Each lane's emulation is
+// independent, so the order changes no result.
 // `lanes` is the mask of the warp's launched lanes; inactive lanes only take
 // part in the reduction.
 template <class Tape>
@@ -215,13 +217,20 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
     const uint32_t kmin = __reduce_min_sync(lanes, key);
     if (kmin == 0xFFFFFFFFu) break;
     if (key - kmin > (policy == 0 ? 0u : window)) continue;
-    exec_one(c, r, rd, st, tape, pf);
-    if ((st.fe_at >= 0) | (r.fc >= kLineCap * kLineCycles)) {   // VSYNC frame end, else the watchdog
-      const bool dog = st.fe_at < 0;
-      frame_end(c, r, rd, st, tape, dog ? r.fc : st.fe_at);
-      st.fe_at = -1;
-      if (dog) st.status |= kStWatchdog;
-    }
+    // run the chosen lanes up to the end of their basic block: instructions
+    // that cannot change control flow leave lanes that were together at the
+    // same next instruction, so they need no new choice
+    bool more;
+    do {
+      more = exec_one(c, r, rd, st, tape, pf);
+      if ((st.fe_at >= 0) | (r.fc >= kLineCap * kLineCycles)) {   // VSYNC frame end, else the watchdog
+        const bool dog = st.fe_at < 0;
+        frame_end(c, r, rd, st, tape, dog ? r.fc : st.fe_at);
+        st.fe_at = -1;
+        if (dog) st.status |= kStWatchdog;
+        more = false;
+      }
+    } while (more);
   }
   if (active && r.jam) st.status |= kStJammed;
 }
