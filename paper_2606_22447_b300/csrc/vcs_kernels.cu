@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   rd.out_u8 = nullptr;
   rd.out_f32 = nullptr;
   rd.gs = nullptr;
+  rd.grow = nullptr;
+  rd.gline = -1;
   for (int t = 0; t < p.n_steps; t++) {
     if constexpr (SOFT) {
       if (t % p.seg_steps == 0) {

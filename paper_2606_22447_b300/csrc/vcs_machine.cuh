@@ -226,7 +226,25 @@ struct Render {
   float* out_f32;            // screen of this env (f32) or null
   const float* gs;           // pixel gradients of the returned frame [210][160]
                              // (backward recompute only) or null
+  float4* grow;              // shared: this env's staged gradient row, 40 float4 at stride E
+  int32_t gline;             // frame line held in grow, or -1
 };
+
+// Stage the gradient row of frame line `line` into shared memory: the 40
+// loads go out in four batches of ten, so a row costs a few memory latencies
+// instead of one per 4-pixel group.
+__device__ __forceinline__ void stage_grad_row(const Ctx& c, Render& rd, int32_t line) {
+  const float4* src = reinterpret_cast<const float4*>(rd.gs + (line - c.ystart) * kScreenW);
+#pragma unroll
+  for (int b = 0; b < 40; b += 10) {
+    float4 t[10];
+#pragma unroll
+    for (int k = 0; k < 10; k++) t[k] = __ldg(src + b + k);
+#pragma unroll
+    for (int k = 0; k < 10; k++) rd.grow[(b + k) * c.E] = t[k];
+  }
+  rd.gline = line;
+}
 
 // 40-bit playfield mask, one bit per 4-pixel block (left half then right).
 __device__ __forceinline__ uint64_t pf_mask(const Regs& r) {
@@ -267,28 +285,78 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
   const uint32_t on_pf = pf_first ? cpf : cp0, off_pf = cpf, on_bk = cp0, off_bk = cbk;
   const uint32_t blank_g = (line == r.hml) ? 2u : 0u;
   if constexpr (Tape::kAcc) {
+    // Sum the span's pixel gradients per owning colour register: plain FP32
+    // within the span (at most 160 terms), one compensated add per owner per
+    // span into the version sums.  A group without player pixels belongs
+    // wholly to the playfield or the background colour.
     if (blank_all || !rd.gs) return;
-    const float* gl = rd.gs + (line - c.ystart) * kScreenW;
-    for (uint32_t g = g0 < blank_g ? blank_g : g0; g < g1; g++) {
-      int32_t d0 = (int32_t)(4 * g) - (int32_t)r.pos;
+    const float4* gl = rd.grow;   // this line's gradients, staged by render_to
+    const uint32_t gs0 = g0 < blank_g ? blank_g : g0;
+    // Bulk pass: whole groups inside the span that hold no player pixel
+    // belong wholly to COLUPF (playfield bit set) or COLUBK; four groups per
+    // turn (g1 <= 40 keeps every guarded load inside the row).  The at most five other groups (the span's two
+    // edge groups, the player's three) are summed pixel by pixel below.
+    const uint32_t gp = r.pos >> 2;
+    auto special = [&](uint32_t g) {
+      uint32_t dp = g + 40u - gp;
+      dp -= dp >= 40u ? 40u : 0u;
+      const bool player = grev != 0 && dp < 3u;
+      return player || 4 * g < x0 || 4 * g + 4 > x1;
+    };
+    float s_p0 = 0.f, s_pf = 0.f, s_bk = 0.f, s_pf2 = 0.f, s_bk2 = 0.f;
+    for (uint32_t g = gs0; g < g1; g += 4) {
+      float4 q[4];
+#pragma unroll
+      for (uint32_t k = 0; k < 4; k++)
+        q[k] = g + k < g1 ? gl[(g + k) * c.E] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (uint32_t k = 0; k < 4; k++) {
+        const uint32_t gg = g + k;
+        const float t = (gg >= g1 || special(gg)) ? 0.f : (q[k].x + q[k].y) + (q[k].z + q[k].w);
+        const bool pf = (pfm >> gg) & 1;
+        if (k & 1) {
+          s_pf2 += pf ? t : 0.f;
+          s_bk2 += pf ? 0.f : t;
+        } else {
+          s_pf += pf ? t : 0.f;
+          s_bk += pf ? 0.f : t;
+        }
+      }
+    }
+    s_pf += s_pf2;
+    s_bk += s_bk2;
+    // special groups, each once: pixel ownership with the edge masks
+    uint32_t cand[5] = {g0, g1 - 1, gp, gp + 1 >= 40u ? gp + 1 - 40u : gp + 1, gp + 2 >= 40u ? gp + 2 - 40u : gp + 2};
+#pragma unroll
+    for (int ci = 0; ci < 5; ci++) {
+      const uint32_t g = cand[ci];
+      bool dup = false;
+#pragma unroll
+      for (int cj = 0; cj < ci; cj++) dup |= cand[cj] == g;
+      if (dup || g < gs0 || g >= g1 || !special(g)) continue;
+      const float4 q = gl[g * c.E];
+      const uint32_t xb = 4 * g;
+      const float v[4] = {(xb + 0 >= x0 && xb + 0 < x1) ? q.x : 0.f, (xb + 1 >= x0 && xb + 1 < x1) ? q.y : 0.f,
+                          (xb + 2 >= x0 && xb + 2 < x1) ? q.z : 0.f, (xb + 3 >= x0 && xb + 3 < x1) ? q.w : 0.f};
+      int32_t d0 = (int32_t)xb - (int32_t)r.pos;
       d0 += d0 < 0 ? 160 : 0;
-      uint32_t nib = d0 < 8 ? (grev >> d0) & 0xF : (d0 > 156 ? (grev << (160 - d0)) & 0xF : 0u);
-      bool pf = (pfm >> g) & 1;
-      float4 q = *reinterpret_cast<const float4*>(gl + 4 * g);
-      float v[4] = {q.x, q.y, q.z, q.w};
-      float acc[3] = {0.f, 0.f, 0.f};
+      const uint32_t nib = d0 < 8 ? (grev >> d0) & 0xF : (d0 > 156 ? (grev << (160 - d0)) & 0xF : 0u);
+      const bool pf = (pfm >> g) & 1;
+      // player pixels belong to COLUP0 unless the playfield has priority
+      // here; the others to COLUPF over the playfield, else to COLUBK
+      float tp = 0.f, tn = 0.f;
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        uint32_t x = 4 * g + j;
-        if (x < x0 || x >= x1) continue;
-        bool p0 = (nib >> j) & 1;
-        int owner = pf_first ? (pf ? 1 : (p0 ? 0 : 2)) : (p0 ? 0 : (pf ? 1 : 2));
-        acc[0] += owner == 0 ? v[j] : 0.f;
-        acc[1] += owner == 1 ? v[j] : 0.f;
-        acc[2] += owner == 2 ? v[j] : 0.f;
+        const bool p0 = (nib >> j) & 1;
+        tp += p0 ? v[j] : 0.f;
+        tn += p0 ? 0.f : v[j];
       }
-      tape.pixels(acc[0], acc[1], acc[2]);
+      const bool pf_wins = pf_first && pf;
+      s_p0 += pf_wins ? 0.f : tp;
+      s_pf += (pf ? tn : 0.f) + (pf_wins ? tp : 0.f);
+      s_bk += pf ? 0.f : tn;
     }
+    tape.pixels(s_p0, s_pf, s_bk);
   } else {
     // Groups g0 and gl may be partly inside [x0, x1); the ones between are
     // whole words.  Background and playfield first (one select per group,
@@ -383,6 +451,9 @@ __device__ __forceinline__ void render_to(const Ctx& c, const Regs& r, Render& r
     int32_t h0 = rd.cur - lbeg, h1 = seg - lbeg;
     uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u;
     uint32_t x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
+    if constexpr (Tape::kAcc) {
+      if (x1 > x0 && rd.gs && line != rd.gline) stage_grad_row(c, rd, line);
+    }
     if (x1 > x0) render_span(c, r, rd, tape, x0, x1, line);
     if (!Tape::kAcc && seg == lend) flush_row(c, rd, line - c.ystart);
     rd.cur = seg;

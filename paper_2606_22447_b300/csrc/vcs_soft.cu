@@ -62,7 +62,7 @@ struct RecTape {
   float p0, p1, p2;                // sums of the versions alive at the segment start
   bool overflow;
   __device__ __forceinline__ void rec(uint32_t op, uint32_t ref, uint32_t fl) {
-    if (n < cap) buf[n] = op | ((ref & 0xFFFF) << 8) | (fl << 24);
+    if (n < cap) __stcs(buf + n, op | ((ref & 0xFFFF) << 8) | (fl << 24));   // written once, read once: evict first
     else overflow = true;
     n++;
   }
@@ -78,7 +78,7 @@ struct RecTape {
     else if (r == 1) { close_version(slot1, s1 + c1, p1); s1 = c1 = 0.f; slot1 = fresh; }
     else { close_version(slot2, s2 + c2, p2); s2 = c2 = 0.f; slot2 = fresh; }
   }
-  // pixel-gradient partial sums of one 4-pixel group, per owner
+  // pixel-gradient sums of one drawn span, per owner
   __device__ __forceinline__ void pixels(float v0, float v1, float v2) {
     comp_add(s0, c0, v0);
     comp_add(s1, c1, v1);
@@ -283,6 +283,13 @@ __device__ __forceinline__ void read_tables(float* ek, float* izr, float tau, in
   __syncthreads();
 }
 
+// Backward shared memory: the step kernel's layout, the RAM adjoints and
+// their compensation [2][128][E], the read tables, then the staged gradient
+// rows (16-byte aligned).
+__host__ __device__ constexpr size_t bwd_row_offset(int E) {
+  return (smem_bytes(E) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
+}
+
 __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x, tid = threadIdx.x;
@@ -291,6 +298,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   float* aramc_s = aram_s + 128 * E;                                 // [128][E] compensation
   float* ek = aramc_s + 128 * E;                                     // [kMaxW + 1]
   float* izr = ek + (kMaxW + 1);                                     // [128]
+  float4* grow = reinterpret_cast<float4*>(smem + bwd_row_offset(E));  // [40][E] staged gradient rows
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
   const uint32_t f8 = p.cart_f8[cart], is2k = p.cart_2k[cart];
@@ -332,12 +340,14 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   rd.cur = 0;
   rd.out_u8 = nullptr;
   rd.out_f32 = nullptr;
+  rd.grow = grow + tid;
   for (int t = t0; t < t1; t++) {
     set_input_bits(r, active ? p.act_bits[(size_t)t * n + env] : 0u);
     Step st;
     st.frame_skip = p.frame_skip;
     st.status = 0;
     rd.gs = p.grad_screen ? p.grad_screen + ((size_t)t * n + env) * (kScreenH * kScreenW) : p.w_screen;
+    rd.gline = -1;
     st.want_screen = rd.gs != nullptr;
     run_frames(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
     if (active) {
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   }
   float* imp = p.imp + (size_t)env * 8192;
   float* impc = p.imp + ((size_t)n + env) * 8192;
-  const uint32_t* rec = p.rec + (size_t)env * p.cap_rec;
+  const uint4* rec4 = reinterpret_cast<const uint4*>(p.rec + (size_t)env * p.cap_rec);
   const float* cw = p.cw + (size_t)env * p.cap_cw;
   uint32_t j = tape.ncw;
   for (int t = t1 - 1; t >= t0; t--) {
@@ -377,8 +387,22 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     for (int q = 0; q < 5; q++) a.u[q] = a.uc[q] = 0.f;
     const uint32_t k_end = p.step_end[(size_t)(t - t0) * n + env];
     const uint32_t k_beg = t > t0 ? p.step_end[(size_t)(t - 1 - t0) * n + env] : 0u;
-    for (uint32_t k = k_end; k > k_beg; k--)
-      reverse_one(a, aram, aramc, E, ek, izr, p.W, imp, impc, f8, is2k, cw, j, rec[k - 1]);
+    // records are read backwards in aligned 4-record chunks (rows of the
+    // tape are 16-byte aligned), the next chunk in flight while one runs
+    uint32_t k = k_end;
+    uint4 ch = k > k_beg ? __ldcs(rec4 + ((k - 1) >> 2)) : make_uint4(0u, 0u, 0u, 0u);
+    while (k > k_beg) {
+      const uint32_t c4 = (k - 1) >> 2;
+      const uint32_t lo = c4 * 4 > k_beg ? c4 * 4 : k_beg;
+      const uint4 nx = lo > k_beg ? __ldcs(rec4 + (c4 - 1)) : ch;
+      for (uint32_t q = k; q > lo; q--) {
+        const uint32_t sl = (q - 1) & 3;
+        const uint32_t rv = sl == 0 ? ch.x : (sl == 1 ? ch.y : (sl == 2 ? ch.z : ch.w));
+        reverse_one(a, aram, aramc, E, ek, izr, p.W, imp, impc, f8, is2k, cw, j, rv);
+      }
+      ch = nx;
+      k = lo;
+    }
     if (p.grad_u) {
       float* gu = p.grad_u + ((size_t)t * n + env) * 5;
       for (int q = 0; q < 5; q++) gu[q] = a.u[q] + a.uc[q];
@@ -400,7 +424,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   }
 }
 
-size_t bwd_smem_bytes(int E) { return smem_bytes(E) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4; }
+size_t bwd_smem_bytes(int E) { return bwd_row_offset(E) + (size_t)40 * 16 * E; }
 
 // ROM impulses -> ROM gradient: spread each impulse at a over the read
 // window of its tensor (the 2K image, the 4K image, or one F8 bank) with the
@@ -599,6 +623,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
     need_rec = std::max<size_t>(need_rec, counts[2 * q]);
     need_cw = std::max<size_t>(need_cw, counts[2 * q + 1]);
   }
+  need_rec = (need_rec + 3) & ~(size_t)3;   // 16-byte rows: the reverse sweep reads 4 records at once
   if (need_rec > t->cap_rec) {
     cudaFree(t->rec);
     t->rec = nullptr;
@@ -750,6 +775,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
     cap_rec = std::max<size_t>(cap_rec, cnt[2 * q]);
     cap_cw = std::max<size_t>(cap_cw, cnt[2 * q + 1]);
   }
+  cap_rec = (cap_rec + 3) & ~(size_t)3;   // 16-byte rows, as in vcs_backward
   const bool need_tmp = !grad_rom && grad_rom_per_cart;
   const size_t o_carry = 0;
   const size_t o_step = align256(o_carry + (size_t)kCarry * n * 4);
