@@ -186,6 +186,48 @@ def soft_leg(n_envs, n_frames, mappers, reps, tau=0.1):
             "gpu_launches": 1 + 2 * ((n_frames + 63) // 64) + 2}
 
 
+def mixed_leg(n_envs, steps, reps):
+    """The batched mixed-cartridge workload: n_envs envs over 16 carts (6 x 2K,
+    6 x 4K, 4 x F8, round-robin then grouped by cart), geometric episode
+    lengths (mean 2,000 frames) with auto-reset, frame-skip 4, RAM + screen
+    written per step.  The launch geometry is autotuned on the workload
+    first (outside the timing); each timed unit is one replay of a CUDA graph
+    of `steps` env-steps.  Returns env-steps/s (median over reps)."""
+    import torch
+
+    from paper_2606_22447_b300 import Batch, synth
+    roms = synth.config_carts(SEED, synth.MIX16)
+    ec = synth.env_cart_round_robin(n_envs, len(synth.MIX16))
+    b = Batch(roms, synth.MIX16, ec)
+    b.set_episodes(synth.episode_lengths(SEED, n_envs, 16))
+    acts = torch.from_numpy(synth.actions(SEED + 3, n_envs, steps)).cuda()
+    ram = torch.empty((steps, n_envs, 128), dtype=torch.uint8, device="cuda")
+    scr = torch.empty((steps, n_envs, 210, 160), dtype=torch.uint8, device="cuda")
+    st = torch.empty((steps, n_envs), dtype=torch.uint8, device="cuda")
+    tune = b.autotune(FRAME_SKIP, 2, actions=acts[:2], ram_out=ram[:2], screen_out=scr[:2])
+    g = b.graph(acts, FRAME_SKIP, ram, scr, st)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    times, done = [], 0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        done += int((st & 4).count_nonzero().item())
+    b.sync()
+    ms = statistics.median(times)
+    k = tune["steps_per_launch"] or steps
+    g.destroy()
+    return {"env_steps_per_s": n_envs * steps / (ms / 1e3), "ms_per_graph": ms, "n_envs": n_envs,
+            "steps_per_graph": steps, "carts": "6x2K + 6x4K + 4xF8", "episodes_ended": done,
+            "autotune": tune, "gpu_launches_per_graph": -(-steps // k),
+            "outputs": "RAM + screen per step (2.2 GB per step at 65,536 envs), larger than L2"}
+
+
 def gpu_arm(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -283,6 +325,9 @@ def gpu_arm(args):
         soft = {"short_1024x64": soft_leg(1024, 64, [_s.MAPPER_4K], reps=3)}
         if not args.no_soft_long:
             soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, reps=1)
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_leg(args.mixed_envs, 8, 5)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
@@ -297,6 +342,7 @@ def gpu_arm(args):
             "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "soft_fwd_bwd": soft,
+            "mixed_carts": mixed,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -314,6 +360,8 @@ def main():
     ap.add_argument("--instr-per-step", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-soft", action="store_true", help="skip the SOFT-STE fwd+bwd legs")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 65,536-env mixed-cartridge leg")
+    ap.add_argument("--mixed-envs", type=int, default=65536)
     ap.add_argument("--no-soft-long", action="store_true",
                     help="skip the 4096-env x 2048-frame soft rollout (about 20 s)")
     args = ap.parse_args()

@@ -79,6 +79,8 @@ typedef struct vcs_config {
                                sched_window cycles of the earliest lane */
   int32_t sched_window;     /* window of policy 1 in CPU cycles, -1 = any;
                                default 4 */
+  int32_t steps_per_launch; /* vcs_rollout: env-steps per kernel launch, 0 =
+                               the whole rollout in one launch (default) */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;
@@ -142,10 +144,13 @@ vcs_status vcs_step(vcs_batch* b, const uint8_t* actions, int32_t frame_skip,
                     uint8_t* ram_out, uint8_t* screen_out, uint8_t* status_out,
                     void* stream);
 
-/* n_steps env-steps in one launch: actions device uint8[n_steps][n_envs];
- * ram_out [n_steps][n_envs][128], screen_out [n_steps][n_envs][210][160],
+/* n_steps env-steps: actions device uint8[n_steps][n_envs]; ram_out
+ * [n_steps][n_envs][128], screen_out [n_steps][n_envs][210][160],
  * status_out [n_steps][n_envs] (all nullable).  Equivalent to n_steps calls
- * of vcs_step. */
+ * of vcs_step.  The machine stays in registers for all the steps of one
+ * launch (a persistent kernel over steps, episodes auto-resetting inside
+ * it); cfg.steps_per_launch > 0 splits the rollout into launches of that
+ * many steps. */
 vcs_status vcs_rollout(vcs_batch* b, const uint8_t* actions, int32_t n_steps,
                        int32_t frame_skip, uint8_t* ram_out, uint8_t* screen_out,
                        uint8_t* status_out, void* stream);
@@ -156,6 +161,48 @@ vcs_status vcs_rollout(vcs_batch* b, const uint8_t* actions, int32_t n_steps,
  * The library allocates its device staging buffers on the first call. */
 vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t frame_skip,
                          uint8_t* ram_out_host, uint8_t* screen_out_host, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch geometry, autotuning and CUDA graphs (deployment features; the
+ * paper's batched rollouts have no counterpart: its GPU path is a traced
+ * program).  None of them changes a result: every geometry computes the
+ * same bits.
+ *
+ * vcs_autotune picks the batch's launch geometry by timing it: envs per
+ * block (8..128), the warp scheduling policy (program order, or emulated
+ * time with windows 4 and 32 cycles) and env-steps per launch (1, 4, or the
+ * whole rollout), by coordinate search in that order.  Each trial runs
+ * n_steps env-steps of frame_skip frames from the batch's current state
+ * with actions (device uint8[n_steps][n_envs], nullable = NOOP) and writes
+ * ram_out / screen_out (device, nullable, sized as for vcs_rollout); the
+ * state is restored after every trial, so the batch ends where it began.
+ * The winner is applied to the batch and described in *out (nullable).
+ * Allocates a state-sized scratch buffer for the call; synchronises
+ * `stream`.  Graphs made before the call must be made again (their launch
+ * then fails with VCS_ERR_STATE). */
+typedef struct vcs_tune {
+  int32_t envs_per_block;
+  int32_t sched_policy;
+  int32_t sched_window;
+  int32_t steps_per_launch;
+  float ms_per_step;        /* the winner's measured time per env-step */
+  int32_t n_trials;
+} vcs_tune;
+vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const uint8_t* actions,
+                        uint8_t* ram_out, uint8_t* screen_out, vcs_tune* out, void* stream);
+
+/* A CUDA graph of one vcs_rollout call (its launch sequence under the
+ * batch's current geometry), for loops that replay the same rollout shape
+ * on fixed buffers: refill `actions` in place, then vcs_graph_launch.  The
+ * buffers are the vcs_rollout arguments and must outlive the graph.  The
+ * graph is tied to the batch's geometry: after vcs_autotune its launch
+ * returns VCS_ERR_STATE.  Capture happens on a private stream. */
+typedef struct vcs_graph vcs_graph;
+vcs_status vcs_graph_create(vcs_batch* b, const uint8_t* actions, int32_t n_steps, int32_t frame_skip,
+                            uint8_t* ram_out, uint8_t* screen_out, uint8_t* status_out,
+                            vcs_graph** out);
+vcs_status vcs_graph_launch(vcs_graph* g, void* stream);
+vcs_status vcs_graph_destroy(vcs_graph* g);
 
 /* Wait for `stream` and report device-side failures: VCS_ERR_WATCHDOG if a
  * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA

@@ -17,8 +17,8 @@ from .synth import MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_SIZE
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 
-__all__ = ["Batch", "Tape", "Config", "VcsError", "default_config", "MAPPER_2K", "MAPPER_4K", "MAPPER_F8",
-           "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
+__all__ = ["Batch", "Tape", "Graph", "Config", "VcsError", "default_config", "MAPPER_2K", "MAPPER_4K",
+           "MAPPER_F8", "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
 
 
 def default_config(**overrides) -> Config:
@@ -137,6 +137,26 @@ class Batch:
                                                  _stream(stream)))
         return Tape(self, h, n_steps)
 
+    def autotune(self, frame_skip: int, n_steps: int, actions=None, ram_out=None, screen_out=None,
+                 stream=None) -> dict:
+        """Time launch geometries on the current state (restored after each
+        trial) and keep the fastest; returns the choice."""
+        t = _lib.Tune()
+        self._check(_lib.load().vcs_autotune(self.h, frame_skip, n_steps, _ptr(actions), _ptr(ram_out),
+                                             _ptr(screen_out), C.byref(t), _stream(stream)))
+        self.envs_per_block = t.envs_per_block
+        return {"envs_per_block": t.envs_per_block, "sched_policy": t.sched_policy,
+                "sched_window": t.sched_window, "steps_per_launch": t.steps_per_launch,
+                "ms_per_step": t.ms_per_step, "n_trials": t.n_trials}
+
+    def graph(self, actions, frame_skip: int, ram_out=None, screen_out=None, status_out=None) -> "Graph":
+        """Capture one rollout over these fixed buffers as a CUDA graph."""
+        h = C.c_void_p()
+        n_steps = int(actions.shape[0])
+        self._check(_lib.load().vcs_graph_create(self.h, _ptr(actions), n_steps, frame_skip, _ptr(ram_out),
+                                                 _ptr(screen_out), _ptr(status_out), C.byref(h)))
+        return Graph(self, h, (actions, ram_out, screen_out, status_out))
+
     def load_state(self, blob: np.ndarray, stream=None):
         b = np.ascontiguousarray(blob, dtype=np.uint8)
         if b.size != self.state_bytes():
@@ -170,5 +190,28 @@ class Tape:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A captured rollout; launch() replays it on the buffers given at capture."""
+
+    def __init__(self, batch: Batch, handle, buffers):
+        self.batch = batch
+        self.h = handle
+        self._buffers = buffers   # keep the captured tensors alive
+
+    def launch(self, stream=None):
+        _lib.check(_lib.load().vcs_graph_launch(self.h, _stream(stream)), self.batch.h)
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            _lib.load().vcs_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
         except Exception:
             pass

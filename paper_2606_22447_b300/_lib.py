@@ -32,7 +32,12 @@ class LossWeights(C.Structure):
 class Config(C.Structure):
     _fields_ = [("alpha", C.c_float), ("ystart", C.c_int32), ("boot_noop_frames", C.c_int32),
                 ("envs_per_block", C.c_int32), ("segment_frames", C.c_int32),
-                ("sched_policy", C.c_int32), ("sched_window", C.c_int32)]
+                ("sched_policy", C.c_int32), ("sched_window", C.c_int32), ("steps_per_launch", C.c_int32)]
+
+
+class Tune(C.Structure):
+    _fields_ = [("envs_per_block", C.c_int32), ("sched_policy", C.c_int32), ("sched_window", C.c_int32),
+                ("steps_per_launch", C.c_int32), ("ms_per_step", C.c_float), ("n_trials", C.c_int32)]
 
 
 vp = C.c_void_p
@@ -60,6 +65,10 @@ SIGNATURES = {
     "vcs_backward": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "vcs_tape_free": (C.c_int, [vp]),
     "vcs_backward_static": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "vcs_autotune": (C.c_int, [vp, i32, i32, vp, vp, vp, C.POINTER(Tune), vp]),
+    "vcs_graph_create": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, C.POINTER(vp)]),
+    "vcs_graph_launch": (C.c_int, [vp, vp]),
+    "vcs_graph_destroy": (C.c_int, [vp]),
 }
 
 _lib = None

@@ -63,6 +63,46 @@ StepParams vcs_base_params(vcs_batch* b) {
   return p;
 }
 
+// Group envs by cart (stable) and cut each cart's run into blocks of E, so
+// that a block stages one ROM image; upload the block table and the
+// permutation.  Replaces any previous geometry.
+static vcs_status set_geometry(vcs_batch* b, int E) {
+  const int n_envs = b->n_envs;
+  const std::vector<int32_t>& env_cart = b->env_cart;
+  std::vector<int32_t> perm(n_envs);
+  for (int e = 0; e < n_envs; e++) perm[e] = e;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int c) { return env_cart[a] < env_cart[c]; });
+  std::vector<int4> blocks;
+  for (int i = 0; i < n_envs;) {
+    const int c = env_cart[perm[i]];
+    int j = i;
+    while (j < n_envs && env_cart[perm[j]] == c && j - i < E) j++;
+    blocks.push_back(make_int4(c, i, j - i, 0));
+    i = j;
+  }
+  int4* dblocks = nullptr;
+  int32_t* dperm = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&dblocks, blocks.size() * sizeof(int4))) || (e = cudaMalloc(&dperm, n_envs * sizeof(int32_t))) ||
+      (e = cudaMemcpy(dblocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(dperm, perm.data(), n_envs * sizeof(int32_t), cudaMemcpyHostToDevice))) {
+    cudaFree(dblocks);
+    cudaFree(dperm);
+    return vcs_cuda_fail(b, e, "launch geometry");
+  }
+  cudaFree(b->blocks);
+  cudaFree(b->perm);
+  b->blocks = dblocks;
+  b->perm = dperm;
+  b->n_blocks = (int)blocks.size();
+  b->perm_host = perm;
+  b->E = E;
+  b->geometry_gen++;
+  return VCS_OK;
+}
+
+static bool valid_epb(int E) { return E == 8 || E == 16 || E == 32 || E == 64 || E == 128; }
+
 static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
   int e = launch_step(p, b->n_blocks, b->E, stream);
   if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
@@ -99,6 +139,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->segment_frames = 64;
   cfg->sched_policy = 0;
   cfg->sched_window = 4;
+  cfg->steps_per_launch = 0;
   return VCS_OK;
 }
 
@@ -161,11 +202,15 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   b->sms = sms;
   int E = b->cfg.envs_per_block;
   if (E == 0) E = pick_envs_per_block(n_envs, sms);
-  if (E != 8 && E != 16 && E != 32 && E != 64 && E != 128) {
+  if (!valid_epb(E)) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "envs_per_block must be 0, 8, 16, 32, 64 or 128");
   }
-  b->E = E;
+  if (b->cfg.steps_per_launch < 0) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "steps_per_launch must be >= 0");
+  }
+  b->steps_per_launch = b->cfg.steps_per_launch;
   if (b->cfg.sched_policy < 0 || b->cfg.sched_policy > 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "sched_policy must be 0 or 1");
@@ -187,20 +232,6 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     f8[c] = mappers[c] == VCS_MAPPER_F8;
     is2k[c] = mappers[c] == VCS_MAPPER_2K;
   }
-  // group envs by cart (stable), cut each cart's run into blocks of E
-  std::vector<int32_t> perm(n_envs);
-  for (int e = 0; e < n_envs; e++) perm[e] = e;
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int c) { return env_cart[a] < env_cart[c]; });
-  std::vector<int4> blocks;
-  for (int i = 0; i < n_envs;) {
-    int c = env_cart[perm[i]];
-    int j = i;
-    while (j < n_envs && env_cart[perm[j]] == c && j - i < E) j++;
-    blocks.push_back(make_int4(c, i, j - i, 0));
-    i = j;
-  }
-  b->n_blocks = (int)blocks.size();
-  b->perm_host = perm;
   std::vector<int32_t> cart_begin(n_carts + 1, 0);
   for (int e = 0; e < n_envs; e++) cart_begin[env_cart[e] + 1]++;
   for (int c = 0; c < n_carts; c++) cart_begin[c + 1] += cart_begin[c];
@@ -211,8 +242,7 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   const size_t nst = (size_t)kStateWords * n_envs * sizeof(uint32_t);
   if ((e = cudaMalloc(&b->state, nst)) || (e = cudaMalloc(&b->roms, img.size())) ||
       (e = cudaMalloc(&b->cart_f8, n_carts)) || (e = cudaMalloc(&b->dt, sizeof(DecodeTables))) ||
-      (e = cudaMalloc(&b->blocks, blocks.size() * sizeof(int4))) ||
-      (e = cudaMalloc(&b->perm, n_envs * sizeof(int32_t))) || (e = cudaMalloc(&b->err, sizeof(int32_t))) ||
+      (e = cudaMalloc(&b->err, sizeof(int32_t))) ||
       (e = cudaMalloc(&b->cart_2k, n_carts)) || (e = cudaMalloc(&b->env_cart_dev, n_envs * sizeof(int32_t))) ||
       (e = cudaMalloc(&b->cart_begin, (n_carts + 1) * sizeof(int32_t)))) {
     vcs_status st = vcs_cuda_fail(nullptr, e, "device allocation");
@@ -222,8 +252,6 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if ((e = cudaMemcpy(b->roms, img.data(), img.size(), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->cart_f8, f8.data(), n_carts, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->dt, &dt, sizeof dt, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(b->blocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(b->perm, perm.data(), n_envs * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->cart_2k, is2k.data(), n_carts, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->env_cart_dev, env_cart, n_envs * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->cart_begin, cart_begin.data(), (n_carts + 1) * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
@@ -231,6 +259,11 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     vcs_status st = vcs_cuda_fail(nullptr, e, "device upload");
     free_batch(b);
     return st;
+  }
+  if (set_geometry(b, E) != VCS_OK) {
+    g_create_error = b->last_error;
+    free_batch(b);
+    return VCS_ERR_CUDA;
   }
   // power on every env (plus the configured boot frames)
   StepParams p = vcs_base_params(b);
@@ -285,16 +318,22 @@ vcs_status vcs_rollout(vcs_batch* b, const uint8_t* actions, int32_t n_steps, in
   if (!b) return VCS_ERR_ARG;
   if (!actions) return vcs_fail(b, VCS_ERR_ARG, "actions is NULL");
   if (n_steps < 0 || frame_skip < 1) return vcs_fail(b, VCS_ERR_ARG, "n_steps >= 0 and frame_skip >= 1 required");
-  StepParams p = vcs_base_params(b);
-  p.actions = actions;
-  p.n_steps = n_steps;
-  p.frame_skip = frame_skip;
-  p.ram_out = ram_out;
-  p.screen_out = screen_out;
-  p.status_out = status_out;
-  p.ep_len = b->ep_len;
-  p.n_episodes = b->n_episodes;
-  return launch(b, p, stream);
+  const int32_t k = b->steps_per_launch > 0 ? b->steps_per_launch : (n_steps > 0 ? n_steps : 1);
+  const size_t n = (size_t)b->n_envs;
+  for (int32_t t0 = 0; t0 < n_steps; t0 += k) {
+    StepParams p = vcs_base_params(b);
+    p.actions = actions + (size_t)t0 * n;
+    p.n_steps = std::min(k, n_steps - t0);
+    p.frame_skip = frame_skip;
+    p.ram_out = ram_out ? ram_out + (size_t)t0 * n * 128 : nullptr;
+    p.screen_out = screen_out ? screen_out + (size_t)t0 * n * kScreenH * kScreenW : nullptr;
+    p.status_out = status_out ? status_out + (size_t)t0 * n : nullptr;
+    p.ep_len = b->ep_len;
+    p.n_episodes = b->n_episodes;
+    vcs_status st = launch(b, p, stream);
+    if (st != VCS_OK) return st;
+  }
+  return VCS_OK;
 }
 
 vcs_status vcs_step(vcs_batch* b, const uint8_t* actions, int32_t frame_skip, uint8_t* ram_out,
@@ -351,6 +390,160 @@ vcs_status vcs_load_state(vcs_batch* b, const void* blob_host, void* stream) {
   if ((e = cudaMemcpyAsync(b->state, blob_host, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream)) ||
       (e = cudaStreamSynchronize((cudaStream_t)stream)))
     return vcs_cuda_fail(b, e, "load state");
+  return VCS_OK;
+}
+
+vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const uint8_t* actions,
+                        uint8_t* ram_out, uint8_t* screen_out, vcs_tune* out, void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  if (frame_skip < 1 || n_steps < 1) return vcs_fail(b, VCS_ERR_ARG, "frame_skip >= 1 and n_steps >= 1 required");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)b->n_envs;
+  const size_t nst = (size_t)kStateWords * n * sizeof(uint32_t);
+  uint32_t* saved = nullptr;
+  uint8_t* noop = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  auto cleanup = [&]() {
+    cudaFree(saved);
+    cudaFree(noop);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if ((e = cudaMalloc(&saved, nst)) || (e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1)) ||
+      (e = cudaMemcpyAsync(saved, b->state, nst, cudaMemcpyDeviceToDevice, s))) {
+    cleanup();
+    return vcs_cuda_fail(b, e, "autotune set-up");
+  }
+  if (!actions) {
+    if ((e = cudaMalloc(&noop, (size_t)n_steps * n)) || (e = cudaMemsetAsync(noop, 0, (size_t)n_steps * n, s))) {
+      cleanup();
+      return vcs_cuda_fail(b, e, "autotune set-up");
+    }
+    actions = noop;
+  }
+  int32_t trials = 0;
+  // one timed trial of the batch's current geometry; the state is restored after it
+  auto trial = [&](float* ms) -> vcs_status {
+    vcs_status st;
+    if ((st = vcs_rollout(b, actions, n_steps, frame_skip, ram_out, screen_out, nullptr, stream)) != VCS_OK) return st;
+    if ((e = cudaMemcpyAsync(b->state, saved, nst, cudaMemcpyDeviceToDevice, s))) return vcs_cuda_fail(b, e, "autotune");
+    if ((e = cudaEventRecord(e0, s))) return vcs_cuda_fail(b, e, "autotune");
+    if ((st = vcs_rollout(b, actions, n_steps, frame_skip, ram_out, screen_out, nullptr, stream)) != VCS_OK) return st;
+    if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) || (e = cudaEventElapsedTime(ms, e0, e1)) ||
+        (e = cudaMemcpyAsync(b->state, saved, nst, cudaMemcpyDeviceToDevice, s)))
+      return vcs_cuda_fail(b, e, "autotune");
+    trials++;
+    return VCS_OK;
+  };
+  vcs_status st = VCS_OK;
+  float best = 1e30f, ms = 0.f;
+  // 1. envs per block, under program-order scheduling and one launch
+  b->sched_policy = 0;
+  b->steps_per_launch = 0;
+  int bestE = b->E;
+  const int cand_e[5] = {8, 16, 32, 64, 128};
+  for (int E : cand_e) {
+    if (E > 8 && (int)((n + E / 2 - 1) / (E / 2)) <= 1) break;   // no larger block helps a tiny batch
+    if ((st = set_geometry(b, E)) != VCS_OK || (st = trial(&ms)) != VCS_OK) break;
+    if (ms < best) { best = ms; bestE = E; }
+  }
+  if (st == VCS_OK && b->E != bestE) st = set_geometry(b, bestE);
+  // 2. scheduling policy
+  uint32_t bestP = 0, bestW = b->sched_window;
+  const uint32_t cand_w[2] = {4, 32};
+  for (int i = 0; st == VCS_OK && i < 2; i++) {
+    b->sched_policy = 1;
+    b->sched_window = cand_w[i];
+    if ((st = trial(&ms)) != VCS_OK) break;
+    if (ms < best) { best = ms; bestP = 1; bestW = cand_w[i]; }
+  }
+  b->sched_policy = bestP;
+  b->sched_window = bestW;
+  // 3. env-steps per launch
+  int32_t bestK = 0;
+  const int32_t cand_k[2] = {1, 4};
+  for (int i = 0; st == VCS_OK && i < 2; i++) {
+    if (cand_k[i] >= n_steps) continue;
+    b->steps_per_launch = cand_k[i];
+    if ((st = trial(&ms)) != VCS_OK) break;
+    if (ms < best) { best = ms; bestK = cand_k[i]; }
+  }
+  b->steps_per_launch = bestK;
+  cleanup();
+  if (st != VCS_OK) return st;
+  b->cfg.envs_per_block = b->E;
+  b->cfg.sched_policy = (int32_t)b->sched_policy;
+  b->cfg.sched_window = (int32_t)b->sched_window;
+  b->cfg.steps_per_launch = b->steps_per_launch;
+  if (out) {
+    out->envs_per_block = b->E;
+    out->sched_policy = (int32_t)b->sched_policy;
+    out->sched_window = (int32_t)b->sched_window;
+    out->steps_per_launch = b->steps_per_launch;
+    out->ms_per_step = best / (float)n_steps;
+    out->n_trials = trials;
+  }
+  return VCS_OK;
+}
+
+}  // extern "C"
+
+struct vcs_graph {
+  vcs_batch* b = nullptr;
+  uint32_t gen = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+vcs_status vcs_graph_create(vcs_batch* b, const uint8_t* actions, int32_t n_steps, int32_t frame_skip,
+                            uint8_t* ram_out, uint8_t* screen_out, uint8_t* status_out, vcs_graph** out) {
+  if (!b || !out) return VCS_ERR_ARG;
+  *out = nullptr;
+  if (!actions || n_steps < 1 || frame_skip < 1)
+    return vcs_fail(b, VCS_ERR_ARG, "actions, n_steps >= 1 and frame_skip >= 1 required");
+  vcs_graph* g = new (std::nothrow) vcs_graph;
+  if (!g) return vcs_fail(b, VCS_ERR_OOM, "host allocation failed");
+  cudaStream_t s = nullptr;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) ||
+      (e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) {
+    if (s) cudaStreamDestroy(s);
+    delete g;
+    return vcs_cuda_fail(b, e, "graph capture");
+  }
+  vcs_status st = vcs_rollout(b, actions, n_steps, frame_skip, ram_out, screen_out, status_out, s);
+  e = cudaStreamEndCapture(s, &g->graph);
+  if (st == VCS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  cudaStreamDestroy(s);
+  if (st != VCS_OK || e != cudaSuccess) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return st != VCS_OK ? st : vcs_cuda_fail(b, e, "graph capture");
+  }
+  g->b = b;
+  g->gen = b->geometry_gen;
+  *out = g;
+  return VCS_OK;
+}
+
+vcs_status vcs_graph_launch(vcs_graph* g, void* stream) {
+  if (!g || !g->b) return VCS_ERR_ARG;
+  if (g->gen != g->b->geometry_gen)
+    return vcs_fail(g->b, VCS_ERR_STATE, "graph made under an older launch geometry; create it again");
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e) return vcs_cuda_fail(g->b, e, "graph launch");
+  return VCS_OK;
+}
+
+vcs_status vcs_graph_destroy(vcs_graph* g) {
+  if (!g) return VCS_ERR_ARG;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
   return VCS_OK;
 }
 

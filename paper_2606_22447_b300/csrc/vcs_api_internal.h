@@ -28,6 +28,8 @@ struct vcs_batch {
   int32_t n_episodes = 0;
   uint32_t sched_policy = 0;       // warp scheduling policy (see vcs_config)
   uint32_t sched_window = 4;       // time window for policy 1 (cycles)
+  int32_t steps_per_launch = 0;    // vcs_rollout launch split (0 = one launch)
+  uint32_t geometry_gen = 0;       // bumped whenever blocks / perm are rebuilt
   int32_t* err = nullptr;
   // staging for the host-pointer entry point
   uint8_t* h_actions = nullptr;
