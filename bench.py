@@ -204,6 +204,9 @@ def mixed_leg(n_envs, steps, reps):
     ram = torch.empty((steps, n_envs, 128), dtype=torch.uint8, device="cuda")
     scr = torch.empty((steps, n_envs, 210, 160), dtype=torch.uint8, device="cuda")
     st = torch.empty((steps, n_envs), dtype=torch.uint8, device="cuda")
+    # advance 64 frames first, so that the envs have drifted apart as they do
+    # in a long run; the geometry is then timed from that state
+    b.rollout(torch.from_numpy(synth.actions(SEED + 5, n_envs, 16)).cuda(), FRAME_SKIP)
     tune = b.autotune(FRAME_SKIP, 2, actions=acts[:2], ram_out=ram[:2], screen_out=scr[:2])
     g = b.graph(acts, FRAME_SKIP, ram, scr, st)
     for _ in range(2):
@@ -262,6 +265,15 @@ def gpu_arm(args):
     for t in range(args.warmup):
         batch.step(acts[t], FRAME_SKIP, ram, scr)
     batch.sync()
+    # launch geometry: timed on this workload from the warmed-up state (which
+    # the autotuner restores), outside the timed region
+    tune = None
+    if args.epb == 0:
+        tune_acts = torch.from_numpy(synth.actions(SEED + 11, n, 2)).cuda()
+        tune_ram = torch.empty((2, n, 128), dtype=torch.uint8, device="cuda")
+        tune_scr = torch.empty((2, n, 210, 160), dtype=torch.uint8, device="cuda")
+        tune = batch.autotune(FRAME_SKIP, 2, actions=tune_acts, ram_out=tune_ram, screen_out=tune_scr)
+        del tune_ram, tune_scr
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
@@ -334,7 +346,7 @@ def gpu_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_envs": n, "frame_skip": FRAME_SKIP, "seed": SEED,
-                       "envs_per_block": batch.envs_per_block,
+                       "envs_per_block": batch.envs_per_block, "autotune": tune,
                        "l2": "256 MB flush between timed steps (outside the events)",
                        "frames_per_s": value * FRAME_SKIP, "instructions_per_s": value * ipe,
                        "parallelism": f"replicas x{world}"},

@@ -81,6 +81,10 @@ typedef struct vcs_config {
                                default 4 */
   int32_t steps_per_launch; /* vcs_rollout: env-steps per kernel launch, 0 =
                                the whole rollout in one launch (default) */
+  int32_t threads_per_env;  /* 0 = automatic (1); else 1, 2, 4 or 8 with
+                               envs_per_block x threads_per_env <= 128: that
+                               many lanes run each env in lockstep and share
+                               its rendering, output and pixel-gradient work */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;
@@ -169,9 +173,9 @@ vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t fram
  * same bits.
  *
  * vcs_autotune picks the batch's launch geometry by timing it: envs per
- * block (8..128), the warp scheduling policy (program order, or emulated
- * time with windows 4 and 32 cycles) and env-steps per launch (1, 4, or the
- * whole rollout), by coordinate search in that order.  Each trial runs
+ * block (8..128) jointly with threads per env (1, 2, 4), then the warp
+ * scheduling policy (program order, or emulated time with windows 4 and 32
+ * cycles), then env-steps per launch (1, 4, or the whole rollout).  Each trial runs
  * n_steps env-steps of frame_skip frames from the batch's current state
  * with actions (device uint8[n_steps][n_envs], nullable = NOOP) and writes
  * ram_out / screen_out (device, nullable, sized as for vcs_rollout); the
@@ -182,6 +186,7 @@ vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t fram
  * then fails with VCS_ERR_STATE). */
 typedef struct vcs_tune {
   int32_t envs_per_block;
+  int32_t threads_per_env;
   int32_t sched_policy;
   int32_t sched_window;
   int32_t steps_per_launch;

@@ -145,7 +145,8 @@ class Batch:
         self._check(_lib.load().vcs_autotune(self.h, frame_skip, n_steps, _ptr(actions), _ptr(ram_out),
                                              _ptr(screen_out), C.byref(t), _stream(stream)))
         self.envs_per_block = t.envs_per_block
-        return {"envs_per_block": t.envs_per_block, "sched_policy": t.sched_policy,
+        return {"envs_per_block": t.envs_per_block, "threads_per_env": t.threads_per_env,
+                "sched_policy": t.sched_policy,
                 "sched_window": t.sched_window, "steps_per_launch": t.steps_per_launch,
                 "ms_per_step": t.ms_per_step, "n_trials": t.n_trials}
 

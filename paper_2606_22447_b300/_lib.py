@@ -32,11 +32,13 @@ class LossWeights(C.Structure):
 class Config(C.Structure):
     _fields_ = [("alpha", C.c_float), ("ystart", C.c_int32), ("boot_noop_frames", C.c_int32),
                 ("envs_per_block", C.c_int32), ("segment_frames", C.c_int32),
-                ("sched_policy", C.c_int32), ("sched_window", C.c_int32), ("steps_per_launch", C.c_int32)]
+                ("sched_policy", C.c_int32), ("sched_window", C.c_int32), ("steps_per_launch", C.c_int32),
+                ("threads_per_env", C.c_int32)]
 
 
 class Tune(C.Structure):
-    _fields_ = [("envs_per_block", C.c_int32), ("sched_policy", C.c_int32), ("sched_window", C.c_int32),
+    _fields_ = [("envs_per_block", C.c_int32), ("threads_per_env", C.c_int32), ("sched_policy", C.c_int32),
+                ("sched_window", C.c_int32),
                 ("steps_per_launch", C.c_int32), ("ms_per_step", C.c_float), ("n_trials", C.c_int32)]
 
 

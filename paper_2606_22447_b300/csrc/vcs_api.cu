@@ -60,6 +60,7 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.err = b->err;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
+  p.tpe = b->tpe;
   return p;
 }
 
@@ -102,6 +103,9 @@ static vcs_status set_geometry(vcs_batch* b, int E) {
 }
 
 static bool valid_epb(int E) { return E == 8 || E == 16 || E == 32 || E == 64 || E == 128; }
+static bool valid_tpe(int E, int T) { return (T == 1 || T == 2 || T == 4 || T == 8) && E * T <= 128; }
+
+
 
 static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
   int e = launch_step(p, b->n_blocks, b->E, stream);
@@ -140,6 +144,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->sched_policy = 0;
   cfg->sched_window = 4;
   cfg->steps_per_launch = 0;
+  cfg->threads_per_env = 0;
   return VCS_OK;
 }
 
@@ -211,6 +216,15 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     return vcs_fail(nullptr, VCS_ERR_ARG, "steps_per_launch must be >= 0");
   }
   b->steps_per_launch = b->cfg.steps_per_launch;
+  // replicas only pay where rendering is a large share of the work, so the
+  // default is one thread per env; vcs_autotune measures the others
+  int T = b->cfg.threads_per_env;
+  if (T == 0) T = 1;
+  if (!valid_tpe(E, T)) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "threads_per_env must be 0, 1, 2, 4 or 8 with envs_per_block x it <= 128");
+  }
+  b->tpe = T;
   if (b->cfg.sched_policy < 0 || b->cfg.sched_policy > 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "sched_policy must be 0 or 1");
@@ -438,16 +452,22 @@ vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const
   };
   vcs_status st = VCS_OK;
   float best = 1e30f, ms = 0.f;
-  // 1. envs per block, under program-order scheduling and one launch
+  // 1. envs per block and threads per env, under program-order scheduling and one launch
   b->sched_policy = 0;
   b->steps_per_launch = 0;
-  int bestE = b->E;
+  int bestE = b->E, bestT = b->tpe;
   const int cand_e[5] = {8, 16, 32, 64, 128};
   for (int E : cand_e) {
     if (E > 8 && (int)((n + E / 2 - 1) / (E / 2)) <= 1) break;   // no larger block helps a tiny batch
-    if ((st = set_geometry(b, E)) != VCS_OK || (st = trial(&ms)) != VCS_OK) break;
-    if (ms < best) { best = ms; bestE = E; }
+    if ((st = set_geometry(b, E)) != VCS_OK) break;
+    for (int T = 1; st == VCS_OK && valid_tpe(E, T) && T <= 4; T *= 2) {
+      b->tpe = T;
+      if ((st = trial(&ms)) != VCS_OK) break;
+      if (ms < best) { best = ms; bestE = E; bestT = T; }
+    }
+    if (st != VCS_OK) break;
   }
+  b->tpe = bestT;
   if (st == VCS_OK && b->E != bestE) st = set_geometry(b, bestE);
   // 2. scheduling policy
   uint32_t bestP = 0, bestW = b->sched_window;
@@ -476,8 +496,10 @@ vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const
   b->cfg.sched_policy = (int32_t)b->sched_policy;
   b->cfg.sched_window = (int32_t)b->sched_window;
   b->cfg.steps_per_launch = b->steps_per_launch;
+  b->cfg.threads_per_env = b->tpe;
   if (out) {
     out->envs_per_block = b->E;
+    out->threads_per_env = b->tpe;
     out->sched_policy = (int32_t)b->sched_policy;
     out->sched_window = (int32_t)b->sched_window;
     out->steps_per_launch = b->steps_per_launch;

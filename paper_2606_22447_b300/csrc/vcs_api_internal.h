@@ -29,6 +29,7 @@ struct vcs_batch {
   uint32_t sched_policy = 0;       // warp scheduling policy (see vcs_config)
   uint32_t sched_window = 4;       // time window for policy 1 (cycles)
   int32_t steps_per_launch = 0;    // vcs_rollout launch split (0 = one launch)
+  int32_t tpe = 1;                 // threads per env
   uint32_t geometry_gen = 0;       // bumped whenever blocks / perm are rebuilt
   int32_t* err = nullptr;
   // staging for the host-pointer entry point

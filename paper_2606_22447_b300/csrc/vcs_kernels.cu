@@ -48,10 +48,12 @@ __device__ __forceinline__ uint32_t round_byte(float v) {
 // forward: joystick bits come from rounded float inputs, outputs are float,
 // the RAM may be overridden from float values first, and the full state is
 // checkpointed at the start of every segment of seg_steps steps.
-template <bool SOFT>
+template <bool SOFT, int T>
 __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
-  const int E = blockDim.x, tid = threadIdx.x;
+  // T threads per env (a compile-time constant, so T = 1 carries no replica
+  // logic): thread tid is replica tid % T of env slot tid / T
+  const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
   BlockSmem bs = carve_smem(smem, E);
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
@@ -61,11 +63,12 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
     return;
   }
   // lanes past the block's env count idle but stay for the warp reductions
-  const bool active = tid < bi.z;
-  const int env = active ? p.perm[bi.y + tid] : 0;
+  const bool active = slot < bi.z;
+  const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
-  const uint32_t lanes = warp_lanes(E);
-  Ctx c = make_ctx(bs, E, tid, f8, p.ystart);
+  const uint32_t lanes = warp_lanes(E * T);
+  Ctx c = make_ctx(bs, E, slot, rank, T, f8, p.ystart);
+  const bool lead = rank == 0;   // the replica that writes per-env results
 
   Regs r;
   uint32_t epf = 0, epi = 0;
@@ -101,12 +104,12 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
     if constexpr (SOFT) {
       if (t % p.seg_steps == 0) {
         const int seg = t / p.seg_steps;
-        if (seg > 0 && active) {
+        if (seg > 0 && active && lead) {
           atomicMax(p.seg_counts + 2 * (seg - 1), tape.n);
           atomicMax(p.seg_counts + 2 * (seg - 1) + 1, tape.ncw);
         }
         tape.n = tape.ncw = 0;
-        if (active) store_env(soa_at(p.ckpt + (size_t)seg * kStateWords * n, n), n, env, c, r);
+        if (active && lead) store_env(soa_at(p.ckpt + (size_t)seg * kStateWords * n, n), n, env, c, r);
       }
     }
     uint32_t bits = 0;
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
         const float* u = p.u + ((size_t)t * n + env) * 5;
         bits = (u[0] >= 0.5f ? 1u : 0u) | (u[1] >= 0.5f ? 2u : 0u) | (u[2] >= 0.5f ? 4u : 0u) |
                (u[3] >= 0.5f ? 8u : 0u) | (u[4] >= 0.5f ? 16u : 0u);
-        p.act_bits[(size_t)t * n + env] = (uint8_t)bits;
+        if (lead) p.act_bits[(size_t)t * n + env] = (uint8_t)bits;
       }
       set_input_bits(r, bits);
     } else {
@@ -150,9 +153,10 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
         epi++;
       }
     }
-    if (p.status_out) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
+    if (p.status_out && lead) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
   }
   if (!active) return;
+  if (!lead) return;
   if constexpr (SOFT) {
     if (p.n_steps > 0) {
       const int seg = (p.n_steps - 1) / p.seg_steps;
@@ -167,16 +171,28 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
 
 size_t step_smem_bytes(int E) { return smem_bytes(E); }
 
-int launch_step(const StepParams& p, int n_blocks, int E, void* stream) {
+template <bool SOFT>
+static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   if (n_blocks <= 0) return 0;
-  k_run<false><<<n_blocks, E, step_smem_bytes(E), (cudaStream_t)stream>>>(p);
+  const dim3 grid(n_blocks), block(E * p.tpe);
+  const size_t smem = step_smem_bytes(E);
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (p.tpe) {
+    case 1: k_run<SOFT, 1><<<grid, block, smem, s>>>(p); break;
+    case 2: k_run<SOFT, 2><<<grid, block, smem, s>>>(p); break;
+    case 4: k_run<SOFT, 4><<<grid, block, smem, s>>>(p); break;
+    case 8: k_run<SOFT, 8><<<grid, block, smem, s>>>(p); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
   return (int)cudaGetLastError();
 }
 
+int launch_step(const StepParams& p, int n_blocks, int E, void* stream) {
+  return launch_run<false>(p, n_blocks, E, stream);
+}
+
 int launch_soft_forward(const StepParams& p, int n_blocks, int E, void* stream) {
-  if (n_blocks <= 0) return 0;
-  k_run<true><<<n_blocks, E, step_smem_bytes(E), (cudaStream_t)stream>>>(p);
-  return (int)cudaGetLastError();
+  return launch_run<true>(p, n_blocks, E, stream);
 }
 
 }  // namespace vcs

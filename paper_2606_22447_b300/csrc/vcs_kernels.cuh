@@ -46,6 +46,7 @@ struct StepParams {
   const uint8_t* reset_mask;  // per env, or null
   int32_t reset_all;        // power on every env before stepping
   int32_t* err;             // device error word (nonzero after a failure)
+  int32_t tpe;              // threads per env (1, 2, 4 or 8)
   uint32_t sched_policy;    // warp scheduling: 0 program order, 1 emulated time (run_frames)
   uint32_t sched_window;    // time window in cycles for policy 1
   // soft forward only

@@ -189,7 +189,21 @@ struct Ctx {
   uint32_t E;                // envs per block
   uint32_t f8;               // 1 if the cart is F8
   int32_t ystart;
+  // Threads per env: T lanes run one env's machine in lockstep (identical
+  // registers; their identical shared-memory writes coincide) and split the
+  // data-parallel work by chunks of four 4-pixel groups (16 pixels): chunk q
+  // of a scanline belongs to replica q mod T, which alone draws, flushes,
+  // zeroes and sums it, so no replica reads what another wrote.
+  uint32_t rank, T;
+  uint32_t gmask;            // warp lanes of this env's replicas
 };
+
+__device__ __forceinline__ bool owns_chunk(const Ctx& c, uint32_t q) { return (q & (c.T - 1)) == c.rank; }
+
+// First chunk at or after q0 that this replica owns (T is a power of two).
+__device__ __forceinline__ uint32_t first_owned_chunk(const Ctx& c, uint32_t q0) {
+  return q0 + ((c.rank - q0) & (c.T - 1));
+}
 
 __device__ __forceinline__ uint32_t ram_rd(const Ctx& c, uint32_t a) {
   a &= 0x7F;
@@ -235,13 +249,20 @@ struct Render {
 // instead of one per 4-pixel group.
 __device__ __forceinline__ void stage_grad_row(const Ctx& c, Render& rd, int32_t line) {
   const float4* src = reinterpret_cast<const float4*>(rd.gs + (line - c.ystart) * kScreenW);
+  // this replica's chunks, two at a time (eight loads in flight)
+  for (uint32_t q = c.rank; q < 10; q += 2 * c.T) {
+    const uint32_t q2 = q + c.T;
+    float4 t[8];
 #pragma unroll
-  for (int b = 0; b < 40; b += 10) {
-    float4 t[10];
+    for (int k = 0; k < 4; k++) t[k] = __ldg(src + 4 * q + k);
 #pragma unroll
-    for (int k = 0; k < 10; k++) t[k] = __ldg(src + b + k);
+    for (int k = 0; k < 4; k++) t[4 + k] = q2 < 10 ? __ldg(src + 4 * q2 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 10; k++) rd.grow[(b + k) * c.E] = t[k];
+    for (int k = 0; k < 4; k++) rd.grow[(4 * q + k) * c.E] = t[k];
+    if (q2 < 10) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) rd.grow[(4 * q2 + k) * c.E] = t[4 + k];
+    }
   }
   rd.gline = line;
 }
@@ -304,15 +325,16 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       return player || 4 * g < x0 || 4 * g + 4 > x1;
     };
     float s_p0 = 0.f, s_pf = 0.f, s_bk = 0.f, s_pf2 = 0.f, s_bk2 = 0.f;
-    for (uint32_t g = gs0; g < g1; g += 4) {
+    for (uint32_t ch = first_owned_chunk(c, gs0 >> 2); 4 * ch < g1; ch += c.T) {
+      const uint32_t g = 4 * ch;
       float4 q[4];
 #pragma unroll
       for (uint32_t k = 0; k < 4; k++)
-        q[k] = g + k < g1 ? gl[(g + k) * c.E] : make_float4(0.f, 0.f, 0.f, 0.f);
+        q[k] = (g + k >= gs0 && g + k < g1) ? gl[(g + k) * c.E] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (uint32_t k = 0; k < 4; k++) {
         const uint32_t gg = g + k;
-        const float t = (gg >= g1 || special(gg)) ? 0.f : (q[k].x + q[k].y) + (q[k].z + q[k].w);
+        const float t = (gg < gs0 || gg >= g1 || special(gg)) ? 0.f : (q[k].x + q[k].y) + (q[k].z + q[k].w);
         const bool pf = (pfm >> gg) & 1;
         if (k & 1) {
           s_pf2 += pf ? t : 0.f;
@@ -333,7 +355,7 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       bool dup = false;
 #pragma unroll
       for (int cj = 0; cj < ci; cj++) dup |= cand[cj] == g;
-      if (dup || g < gs0 || g >= g1 || !special(g)) continue;
+      if (dup || g < gs0 || g >= g1 || !special(g) || !owns_chunk(c, g >> 2)) continue;
       const float4 q = gl[g * c.E];
       const uint32_t xb = 4 * g;
       const float v[4] = {(xb + 0 >= x0 && xb + 0 < x1) ? q.x : 0.f, (xb + 1 >= x0 && xb + 1 < x1) ? q.y : 0.f,
@@ -371,19 +393,30 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       uint32_t* dst = line + g * E;
       *dst = mask == 0xFFFFFFFFu ? w : ((*dst & ~mask) | (w & mask));
     };
+    // The two edge groups (partly inside the span) are masked; the interior
+    // ones are plain stores, this replica's chunks of four groups only.
     if (blank_all) {
-      for (uint32_t g = g0; g < g1; g++) put(g, 0u);
+      if (owns_chunk(c, g0 >> 2)) put(g0, 0u);
+      if (gl > g0 && owns_chunk(c, gl >> 2)) put(gl, 0u);
+      for (uint32_t ch = first_owned_chunk(c, (g0 + 1) >> 2); 4 * ch < gl; ch += c.T)
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++)
+          if (4 * ch + k > g0 && 4 * ch + k < gl) line[(4 * ch + k) * E] = 0u;
       return;
     }
-    put(g0, ((pfm >> g0) & 1) ? cpf : cbk);
-    if (gl > g0) {
-      uint64_t pfs = pfm >> (g0 + 1);
-#pragma unroll 4
-      for (uint32_t g = g0 + 1; g < gl; g++) {
-        line[g * E] = (pfs & 1) ? cpf : cbk;
-        pfs >>= 1;
+    if (owns_chunk(c, g0 >> 2)) put(g0, ((pfm >> g0) & 1) ? cpf : cbk);
+    if (gl > g0 && owns_chunk(c, gl >> 2)) put(gl, ((pfm >> gl) & 1) ? cpf : cbk);
+    for (uint32_t ch = first_owned_chunk(c, (g0 + 1) >> 2); 4 * ch < gl; ch += c.T) {
+      const uint32_t g = 4 * ch;
+      const uint32_t pfs = (uint32_t)(pfm >> g) & 0xF;
+      if (g > g0 && g + 4 <= gl) {   // the whole chunk is interior
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++) line[(g + k) * E] = ((pfs >> k) & 1) ? cpf : cbk;
+      } else {
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++)
+          if (g + k > g0 && g + k < gl) line[(g + k) * E] = ((pfs >> k) & 1) ? cpf : cbk;
       }
-      put(gl, ((pfm >> gl) & 1) ? cpf : cbk);
     }
     if (grev) {
       const uint32_t gp = r.pos >> 2;
@@ -391,10 +424,12 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       for (uint32_t k = 0; k < 3; k++) {
         uint32_t g = gp + k;
         g -= g >= 40 ? 40u : 0u;
-        if (g >= g0 && g < g1) put(g, group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk));
+        if (g >= g0 && g < g1 && owns_chunk(c, g >> 2))
+          put(g, group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk));
       }
     }
-    for (uint32_t g = g0; g < blank_g && g < g1; g++) put(g, 0u);
+    for (uint32_t g = g0; g < blank_g && g < g1; g++)
+      if (owns_chunk(c, g >> 2)) put(g, 0u);
   }
 }
 
@@ -402,7 +437,8 @@ __device__ __forceinline__ void flush_row(const Ctx& c, Render& rd, int32_t row)
   if (rd.out_u8) {
     uint4* dst = reinterpret_cast<uint4*>(rd.out_u8 + row * kScreenW);
 #pragma unroll
-    for (int q = 0; q < 10; q++) {
+    for (uint32_t q = 0; q < 10; q++) {
+      if (!owns_chunk(c, q)) continue;
       uint4 v;
       v.x = c.line[(4 * q + 0) * c.E];
       v.y = c.line[(4 * q + 1) * c.E];
@@ -412,28 +448,36 @@ __device__ __forceinline__ void flush_row(const Ctx& c, Render& rd, int32_t row)
     }
   } else if (rd.out_f32) {
     float4* dst = reinterpret_cast<float4*>(rd.out_f32 + row * kScreenW);
-#pragma unroll 4
-    for (int w = 0; w < 40; w++) {
-      uint32_t v = c.line[w * c.E];
-      dst[w] = make_float4((float)(v & 0xFF), (float)((v >> 8) & 0xFF), (float)((v >> 16) & 0xFF),
-                           (float)(v >> 24));
-    }
+#pragma unroll 2
+    for (uint32_t q = 0; q < 10; q++)
+#pragma unroll
+      for (uint32_t k = 0; k < 4; k++) {
+        if (!owns_chunk(c, q)) continue;
+        const uint32_t v = c.line[(4 * q + k) * c.E];
+        dst[4 * q + k] = make_float4((float)(v & 0xFF), (float)((v >> 8) & 0xFF), (float)((v >> 16) & 0xFF),
+                                     (float)(v >> 24));
+      }
   }
-#pragma unroll 8
-  for (int w = 0; w < 40; w++) c.line[w * c.E] = 0u;
+#pragma unroll
+  for (uint32_t q = 0; q < 10; q++)
+#pragma unroll
+    for (uint32_t k = 0; k < 4; k++)
+      if (owns_chunk(c, q)) c.line[(4 * q + k) * c.E] = 0u;
 }
 
-__device__ __forceinline__ void zero_rows(Render& rd, int32_t row0) {
+__device__ __forceinline__ void zero_rows(const Ctx& c, Render& rd, int32_t row0) {
   if (row0 < 0) row0 = 0;
   for (int32_t row = row0; row < kScreenH; row++) {
     if (rd.out_u8) {
       uint4* dst = reinterpret_cast<uint4*>(rd.out_u8 + row * kScreenW);
 #pragma unroll
-      for (int q = 0; q < 10; q++) dst[q] = make_uint4(0, 0, 0, 0);
+      for (uint32_t q = 0; q < 10; q++)
+        if (owns_chunk(c, q)) dst[q] = make_uint4(0, 0, 0, 0);
     } else if (rd.out_f32) {
       float4* dst = reinterpret_cast<float4*>(rd.out_f32 + row * kScreenW);
-#pragma unroll 8
-      for (int q = 0; q < 40; q++) dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (uint32_t q = c.rank; q < 10; q += c.T)
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++) dst[4 * q + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }
@@ -458,6 +502,7 @@ __device__ __forceinline__ void render_to(const Ctx& c, const Regs& r, Render& r
     if (!Tape::kAcc && seg == lend) flush_row(c, rd, line - c.ystart);
     rd.cur = seg;
   }
+  __syncwarp(c.gmask);   // replicas leave the split work together
 }
 
 // Close the returned frame at colour clock `end`: draw up to it, flush the
@@ -469,10 +514,11 @@ __device__ __forceinline__ void finish_frame(const Ctx& c, const Regs& r, Render
   int32_t row = (int32_t)div228((uint32_t)rd.cur) - c.ystart;
   if (row >= 0) {
     flush_row(c, rd, row);
-    zero_rows(rd, row + 1);
+    zero_rows(c, rd, row + 1);
   } else {
-    zero_rows(rd, 0);
+    zero_rows(c, rd, 0);
   }
+  __syncwarp(c.gmask);
 }
 
 }  // namespace vcs

@@ -65,16 +65,23 @@ __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTabl
   return done != 0;
 }
 
-__device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int tid, uint32_t f8, int32_t ystart) {
+// Context of one replica: env slot `slot` of the block (E envs), replica
+// `rank` of T.
+__device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int rank, int T, uint32_t f8,
+                                        int32_t ystart) {
   Ctx c;
   c.rom = b.rom;
-  c.ram = reinterpret_cast<uint8_t*>(b.ram + tid);
-  c.line = b.line + tid;
+  c.ram = reinterpret_cast<uint8_t*>(b.ram + slot);
+  c.line = b.line + slot;
   c.dt = b.dt;
   c.e4 = 4u * (uint32_t)E;
   c.E = (uint32_t)E;
   c.f8 = f8;
   c.ystart = ystart;
+  c.rank = (uint32_t)rank;
+  c.T = (uint32_t)T;
+  const uint32_t lane = threadIdx.x & 31;
+  c.gmask = ((1u << T) - 1u) << (lane & ~(uint32_t)(T - 1));
   return c;
 }
 
@@ -102,7 +109,9 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
   r.hml = (int32_t)s.t3[e];
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
   for (int i = 0; i < 32; i++) w[i * c.E] = s.ram[(size_t)i * n + e];
-  for (int i = 0; i < 40; i++) c.line[i * c.E] = 0;
+  for (uint32_t q = c.rank; q < 10; q += c.T)
+    for (uint32_t k = 0; k < 4; k++) c.line[(4 * q + k) * c.E] = 0;
+  __syncwarp(c.gmask);
 }
 
 __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx& c, const Regs& r) {
@@ -249,8 +258,7 @@ __device__ __forceinline__ void normalise_timer(Regs& r) {
 __device__ __forceinline__ void write_ram_f32(const Ctx& c, float* dst) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(c.ram);
   float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll 8
-  for (int q = 0; q < 32; q++) {
+  for (uint32_t q = c.rank; q < 32; q += c.T) {
     uint32_t v = w[q * c.E];
     d4[q] = make_float4((float)(v & 0xFF), (float)((v >> 8) & 0xFF), (float)((v >> 16) & 0xFF), (float)(v >> 24));
   }
@@ -260,8 +268,9 @@ __device__ __forceinline__ void write_ram(const Ctx& c, uint8_t* dst8) {
   uint4* dst = reinterpret_cast<uint4*>(dst8);
   const uint32_t* w = reinterpret_cast<const uint32_t*>(c.ram);
 #pragma unroll
-  for (int q = 0; q < 8; q++)
-    dst[q] = make_uint4(w[(4 * q) * c.E], w[(4 * q + 1) * c.E], w[(4 * q + 2) * c.E], w[(4 * q + 3) * c.E]);
+  for (uint32_t q = 0; q < 8; q++)
+    if (owns_chunk(c, q))
+      dst[q] = make_uint4(w[(4 * q) * c.E], w[(4 * q + 1) * c.E], w[(4 * q + 2) * c.E], w[(4 * q + 3) * c.E]);
 }
 
 }  // namespace vcs

@@ -61,14 +61,23 @@ struct RecTape {
   float s0, s1, s2, c0, c1, c2;    // compensated pixel-gradient sums of the live versions
   float p0, p1, p2;                // sums of the versions alive at the segment start
   bool overflow;
+  uint32_t T, gmask;               // replicas of this env and their warp lanes
+  // The replicas of an env each sum the pixel chunks they own; a version's
+  // total is their sum (a butterfly over the replicas' lanes, so every
+  // replica holds the same total).
+  __device__ __forceinline__ float replica_sum(float v) const {
+    for (uint32_t o = 1; o < T; o <<= 1) v += __shfl_xor_sync(gmask, v, o);
+    return v;
+  }
   __device__ __forceinline__ void rec(uint32_t op, uint32_t ref, uint32_t fl) {
     if (n < cap) __stcs(buf + n, op | ((ref & 0xFFFF) << 8) | (fl << 24));   // written once, read once: evict first
     else overflow = true;
     n++;
   }
   __device__ __forceinline__ void close_version(int32_t slot, float s, float& pinit) {
-    if (slot >= 0) cw[slot] = s;
-    else if (slot == -1) pinit += s;
+    const float tot = replica_sum(s);
+    if (slot >= 0) cw[slot] = tot;
+    else if (slot == -1) pinit += tot;
   }
   __device__ __forceinline__ void colour_write(int r) {
     int32_t fresh = ncw < capcw ? (int32_t)ncw : -2;
@@ -94,6 +103,7 @@ struct RecTape {
 
 struct BwdParams {
   int32_t n_envs, n_steps, frame_skip, seg, seg_steps, ystart, first;
+  int32_t tpe;                // threads per env
   const int4* blocks;
   const int32_t* perm;
   const uint8_t* roms;        // rounded ROM images of the rollout [n_carts][8192]
@@ -290,9 +300,10 @@ __host__ __device__ constexpr size_t bwd_row_offset(int E) {
   return (smem_bytes(E) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
 }
 
+template <int T>
 __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
-  const int E = blockDim.x, tid = threadIdx.x;
+  const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
   BlockSmem bs = carve_smem(smem, E);
   float* aram_s = reinterpret_cast<float*>(smem + smem_bytes(E));   // [128][E]
   float* aramc_s = aram_s + 128 * E;                                 // [128][E] compensation
@@ -307,13 +318,13 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
   }
-  const bool active = tid < bi.z;
-  const int env = active ? p.perm[bi.y + tid] : 0;
+  const bool active = slot < bi.z;
+  const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
-  const uint32_t lanes = warp_lanes(E);
-  Ctx c = make_ctx(bs, E, tid, f8, p.ystart);
-  float* aram = aram_s + tid;
-  float* aramc = aramc_s + tid;
+  const uint32_t lanes = warp_lanes(E * T);
+  Ctx c = make_ctx(bs, E, slot, rank, T, f8, p.ystart);
+  float* aram = aram_s + slot;
+  float* aramc = aramc_s + slot;
 
   Regs r;
   if (active) {
@@ -331,6 +342,8 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   tape.c0 = tape.c1 = tape.c2 = 0.f;
   tape.p0 = tape.p1 = tape.p2 = 0.f;
   tape.overflow = false;
+  tape.T = (uint32_t)T;
+  tape.gmask = c.gmask;
 
   // 1. recompute the segment, recording the tape
   const int t0 = p.seg * p.seg_steps;
@@ -340,7 +353,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   rd.cur = 0;
   rd.out_u8 = nullptr;
   rd.out_f32 = nullptr;
-  rd.grow = grow + tid;
+  rd.grow = grow + slot;
   for (int t = t0; t < t1; t++) {
     set_input_bits(r, active ? p.act_bits[(size_t)t * n + env] : 0u);
     Step st;
@@ -357,6 +370,8 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   }
   if (!active) return;
   tape.finish();
+  // the reverse sweep is sequential: one replica runs it
+  if (rank != 0) return;
   if (tape.overflow) {
     atomicExch(p.err, 2);
     return;
@@ -421,6 +436,25 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     cr[4 * n + env] = a.C0; cr[5 * n + env] = a.C1; cr[6 * n + env] = a.C2;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
+  }
+}
+
+static cudaError_t allow_bwd_smem(size_t smem) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_soft_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return e;
+  return cudaSuccess;
+}
+
+static void launch_bwd(const BwdParams& p, int n_blocks, int E, int T, size_t smem, cudaStream_t s) {
+  switch (T) {
+    case 1: k_soft_bwd<1><<<n_blocks, E, smem, s>>>(p); break;
+    case 2: k_soft_bwd<2><<<n_blocks, 2 * E, smem, s>>>(p); break;
+    case 4: k_soft_bwd<4><<<n_blocks, 4 * E, smem, s>>>(p); break;
+    default: k_soft_bwd<8><<<n_blocks, 8 * E, smem, s>>>(p); break;
   }
 }
 
@@ -677,17 +711,18 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.grad_ram0 = grad_ram0;
   p.tau = t->tau;
   p.W = t->W;
+  p.tpe = b->tpe;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
   const size_t smem = bwd_smem_bytes(b->E);
-  if ((e = cudaFuncSetAttribute(k_soft_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+  if ((e = allow_bwd_smem(smem)))
     return vcs_cuda_fail(b, e, "backward shared memory");
   for (int q = t->n_seg - 1; q >= 0; q--) {
     p.seg = q;
     p.first = q == t->n_seg - 1;
     p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
-    k_soft_bwd<<<b->n_blocks, b->E, smem, s>>>(p);
+    launch_bwd(p, b->n_blocks, b->E, b->tpe, smem, s);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
   }
   if (grom) {
@@ -824,17 +859,18 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.grad_ram0 = grad_ram0;
   p.tau = t->tau;
   p.W = t->W;
+  p.tpe = b->tpe;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
   const size_t smem = bwd_smem_bytes(b->E);
-  if ((e = cudaFuncSetAttribute(k_soft_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+  if ((e = allow_bwd_smem(smem)))
     return vcs_cuda_fail(b, e, "backward shared memory");
   for (int q = t->n_seg - 1; q >= 0; q--) {
     p.seg = q;
     p.first = q == t->n_seg - 1;
     p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
-    k_soft_bwd<<<b->n_blocks, b->E, smem, s>>>(p);
+    launch_bwd(p, b->n_blocks, b->E, b->tpe, smem, s);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
   }
   if (grom) {

@@ -48,11 +48,14 @@ def test_mixed_carts_unsorted_envs():
     _check_all(roms, synth.MIX16, env_cart, acts, 2)
 
 
-@pytest.mark.parametrize("epb", [8, 16, 32, 64, 128])
-def test_block_sizes_agree(epb):
+@pytest.mark.parametrize("epb,tpe", [(8, 1), (16, 1), (32, 1), (64, 1), (128, 1), (8, 2), (8, 4), (8, 8),
+                                     (16, 8), (32, 4), (64, 2)])
+def test_block_sizes_agree(epb, tpe):
+    """Every launch geometry (envs per block x threads per env) computes the
+    same bits; replicas split the drawing and the row writes."""
     rom = synth.generate_cart(404, 2, synth.MAPPER_4K)
     acts = synth.actions(404, 40, 4)
-    b = make_batch([rom], [synth.MAPPER_4K], [0] * 40, envs_per_block=epb)
+    b = make_batch([rom], [synth.MAPPER_4K], [0] * 40, envs_per_block=epb, threads_per_env=tpe)
     ram, scr, st = gpu_rollout(b, acts, 3)
     for e in (0, 17, 39):
         r2, s2, _ = oracle_rollout(rom, synth.MAPPER_4K, acts[:, e], 3)

@@ -80,11 +80,13 @@ def test_theorem1_soft_forward_equals_hard(tau):
     tape.free()
 
 
-@pytest.mark.parametrize("tau,frame_skip", [(1.0, 1), (0.1, 1), (0.01, 1), (0.1, 2)])
-def test_gradients_match_fp64_oracle(tau, frame_skip):
+@pytest.mark.parametrize("tau,frame_skip,tpe", [(1.0, 1, 4), (0.1, 1, 4), (0.01, 1, 4), (0.1, 2, 4), (0.1, 1, 1),
+                                                 (1.0, 1, 2)])
+def test_gradients_match_fp64_oracle(tau, frame_skip, tpe):
     mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
     n_envs, n_steps = 6, 4
-    torch, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 41, frame_skip=frame_skip)
+    torch, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 41, frame_skip=frame_skip,
+                                                   envs_per_block=8, threads_per_env=tpe)
     gr = synth.normal_f32(41, (n_steps, n_envs, 128), 1)
     gs = synth.normal_f32(41, (n_steps, n_envs, 210, 160), 2)
     tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), frame_skip)
