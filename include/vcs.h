@@ -183,7 +183,11 @@ vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t fram
  * The winner is applied to the batch and described in *out (nullable).
  * Allocates a state-sized scratch buffer for the call; synchronises
  * `stream`.  Graphs made before the call must be made again (their launch
- * then fails with VCS_ERR_STATE). */
+ * then fails with VCS_ERR_STATE).  Results are cached for the process per
+ * (GPU, SM count, n_envs, n_carts, envs per mapper, frame_skip, which
+ * outputs are written): a later call with the same key applies the cached
+ * choice without trials (n_trials = 0); vcs_autotune_cache_clear forgets
+ * them. */
 typedef struct vcs_tune {
   int32_t envs_per_block;
   int32_t threads_per_env;
@@ -195,6 +199,7 @@ typedef struct vcs_tune {
 } vcs_tune;
 vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const uint8_t* actions,
                         uint8_t* ram_out, uint8_t* screen_out, vcs_tune* out, void* stream);
+vcs_status vcs_autotune_cache_clear(void);
 
 /* A CUDA graph of one vcs_rollout call (its launch sequence under the
  * batch's current geometry), for loops that replay the same rollout shape
@@ -208,6 +213,16 @@ vcs_status vcs_graph_create(vcs_batch* b, const uint8_t* actions, int32_t n_step
                             vcs_graph** out);
 vcs_status vcs_graph_launch(vcs_graph* g, void* stream);
 vcs_status vcs_graph_destroy(vcs_graph* g);
+
+/* Digests of rollout outputs, for parity checks at scale (test
+ * infrastructure; the paper has none): out[t][e] (device uint64[n_steps]
+ * [n_envs]) = sum mod 2^64 over i of F((i << 32) | w_i), where w_i are the
+ * little-endian 32-bit words of ram[t][e] (128 bytes) followed by
+ * screen[t][e] (33,600 bytes; screen nullable = RAM only) and F is the
+ * splitmix64 finaliser (variant 13).  ram and screen are device buffers laid
+ * out as vcs_rollout writes them, 16-byte aligned. */
+vcs_status vcs_digest(vcs_batch* b, const uint8_t* ram, const uint8_t* screen, int32_t n_steps,
+                      uint64_t* out, void* stream);
 
 /* Wait for `stream` and report device-side failures: VCS_ERR_WATCHDOG if a
  * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA

@@ -73,6 +73,8 @@ def lib():
         L.ogrf_eval.argtypes = [vp, dp, dp, dp]
         L.ogrf_nodes.restype = C.c_int64
         L.ogrf_nodes.argtypes = [vp]
+        L.ovcs_digest.restype = C.c_uint64
+        L.ovcs_digest.argtypes = [u8p, u8p]
         L.ovcs_relaxed_read.restype = C.c_double
         L.ovcs_relaxed_read.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.c_double, dp]
         L.ovcs_gate_slope.restype = C.c_double
@@ -210,6 +212,16 @@ class Oracle:
         h = lib().ovcs_soft_rollout(self.h, _dp(u), n, frame_skip, float(tau), float(alpha),
                                     _dp(gr), _dp(gs), _dp(ram_out), _dp(scr_out))
         return SoftGraph(h, len(self.rom), n), ram_out, scr_out
+
+
+def digest(ram, screen=None) -> int:
+    """64-bit digest of one env-step's RAM [128] and screen [210][160]
+    (uint8 arrays; screen optional), as defined in vcs_oracle.h."""
+    r = np.ascontiguousarray(ram, dtype=np.uint8)
+    if screen is None:
+        return int(lib().ovcs_digest(_p(r, C.c_uint8), None))
+    sc = np.ascontiguousarray(screen, dtype=np.uint8)
+    return int(lib().ovcs_digest(_p(r, C.c_uint8), _p(sc, C.c_uint8)))
 
 
 def relaxed_read(r, a0: int, a: float, tau: float):

@@ -1159,3 +1159,25 @@ double ogrf_eval(ogrf* g, const double* d_rom, const double* d_ram0, const doubl
   free(h);
   return out;
 }
+
+/* ------------------------------------------------------------------------
+ * Output digest (declared in vcs_oracle.h): a plain loop over the words.
+ * ---------------------------------------------------------------------- */
+static uint64_t digest_fin(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static uint32_t le_word(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+uint64_t ovcs_digest(const uint8_t* ram128, const uint8_t* screen) {
+  uint64_t d = 0;
+  uint64_t i = 0;
+  for (int k = 0; k < 128; k += 4, i++) d += digest_fin((i << 32) | le_word(ram128 + k));
+  if (screen)
+    for (int k = 0; k < 210 * 160; k += 4, i++) d += digest_fin((i << 32) | le_word(screen + k));
+  return d;
+}

@@ -102,6 +102,14 @@ int64_t ogrf_nodes(const ogrf* g);
 /* The relaxed read primitive on its own (Eq. s-read with the frozen window
  * of half-width W = max(1, ceil(12 tau)) clipped to [0, M)): value and
  * derivative with respect to the (real) address a around integer a0. */
+/* Digest of one env-step's outputs, for parity checks at scale (test
+ * infrastructure, no counterpart in the paper): the 128 RAM bytes followed by
+ * the 33,600 screen bytes (screen may be NULL: RAM only) read as
+ * little-endian 32-bit words w_i, i = 0, 1, ...; the digest is the sum mod
+ * 2^64 over i of F((i << 32) | w_i), F the splitmix64 finaliser (Steele, Lea
+ * and Flood 2014, variant 13). */
+uint64_t ovcs_digest(const uint8_t* ram128, const uint8_t* screen);
+
 double ovcs_relaxed_read(const double* r, int M, int a0, double a, double tau, double* d_da);
 /* Gate derivative alpha * s(alpha z) (1 - s(alpha z)) of Eq. s-branch. */
 double ovcs_gate_slope(double alpha, double z);

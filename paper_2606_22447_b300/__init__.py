@@ -17,7 +17,7 @@ from .synth import MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_SIZE
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 
-__all__ = ["Batch", "Tape", "Graph", "Config", "VcsError", "default_config", "MAPPER_2K", "MAPPER_4K",
+__all__ = ["Batch", "Tape", "Graph", "Config", "VcsError", "default_config", "autotune_cache_clear", "MAPPER_2K",
            "MAPPER_F8", "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
 
 
@@ -27,6 +27,11 @@ def default_config(**overrides) -> Config:
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg
+
+
+def autotune_cache_clear():
+    """Forget the process's cached autotuning results."""
+    _lib.check(_lib.load().vcs_autotune_cache_clear(), None)
 
 
 def _ptr(t):
@@ -149,6 +154,17 @@ class Batch:
                 "sched_policy": t.sched_policy,
                 "sched_window": t.sched_window, "steps_per_launch": t.steps_per_launch,
                 "ms_per_step": t.ms_per_step, "n_trials": t.n_trials}
+
+    def digest(self, ram, screen=None, out=None, stream=None):
+        """uint64 digests [n_steps][n_envs] of rollout outputs (device
+        tensors laid out as rollout() writes them); returns a torch int64
+        tensor holding the 64-bit patterns."""
+        import torch
+        n_steps = int(ram.shape[0])
+        if out is None:
+            out = torch.empty((n_steps, self.n_envs), dtype=torch.int64, device=ram.device)
+        self._check(_lib.load().vcs_digest(self.h, _ptr(ram), _ptr(screen), n_steps, _ptr(out), _stream(stream)))
+        return out
 
     def graph(self, actions, frame_skip: int, ram_out=None, screen_out=None, status_out=None) -> "Graph":
         """Capture one rollout over these fixed buffers as a CUDA graph."""

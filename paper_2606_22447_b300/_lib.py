@@ -71,6 +71,8 @@ SIGNATURES = {
     "vcs_graph_create": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, C.POINTER(vp)]),
     "vcs_graph_launch": (C.c_int, [vp, vp]),
     "vcs_graph_destroy": (C.c_int, [vp]),
+    "vcs_digest": (C.c_int, [vp, vp, vp, i32, vp, vp]),
+    "vcs_autotune_cache_clear": (C.c_int, []),
 }
 
 _lib = None

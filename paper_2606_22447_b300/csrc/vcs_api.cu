@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -407,10 +409,69 @@ vcs_status vcs_load_state(vcs_batch* b, const void* blob_host, void* stream) {
   return VCS_OK;
 }
 
+}  // extern "C"
+
+// Tuning results of this process, keyed by GPU, batch shape and cartridge mix
+// (envs per mapper), frame-skip and which outputs the rollouts write.
+static std::mutex g_tune_mu;
+static std::map<std::string, vcs_tune> g_tune_cache;
+
+static std::string tune_key(const vcs_batch* b, int32_t frame_skip, bool ram, bool screen) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "?";
+  int per_mapper[3] = {0, 0, 0};
+  for (int e = 0; e < b->n_envs; e++) per_mapper[b->mapper[b->env_cart[e]] % 3]++;
+  char buf[256];
+  snprintf(buf, sizeof buf, "|%d|%d|%d|%d|%d|%d|%d|%d", b->sms, b->n_envs, b->n_carts, per_mapper[0], per_mapper[1],
+           per_mapper[2], frame_skip, (ram ? 1 : 0) | (screen ? 2 : 0));
+  return name + buf;
+}
+
+static vcs_status apply_tune(vcs_batch* b, const vcs_tune& t) {
+  if (b->E != t.envs_per_block) {
+    vcs_status st = set_geometry(b, t.envs_per_block);
+    if (st != VCS_OK) return st;
+  }
+  if (b->tpe != t.threads_per_env || b->steps_per_launch != t.steps_per_launch) b->geometry_gen++;   // graphs hold both
+  b->tpe = t.threads_per_env;
+  b->sched_policy = (uint32_t)t.sched_policy;
+  b->sched_window = (uint32_t)t.sched_window;
+  b->steps_per_launch = t.steps_per_launch;
+  b->cfg.envs_per_block = b->E;
+  b->cfg.threads_per_env = b->tpe;
+  b->cfg.sched_policy = t.sched_policy;
+  b->cfg.sched_window = t.sched_window;
+  b->cfg.steps_per_launch = t.steps_per_launch;
+  return VCS_OK;
+}
+
+extern "C" {
+
+vcs_status vcs_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_cache.clear();
+  return VCS_OK;
+}
+
 vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const uint8_t* actions,
                         uint8_t* ram_out, uint8_t* screen_out, vcs_tune* out, void* stream) {
   if (!b) return VCS_ERR_ARG;
   if (frame_skip < 1 || n_steps < 1) return vcs_fail(b, VCS_ERR_ARG, "frame_skip >= 1 and n_steps >= 1 required");
+  const std::string key = tune_key(b, frame_skip, ram_out != nullptr, screen_out != nullptr);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      vcs_tune t = it->second;
+      vcs_status st = apply_tune(b, t);
+      if (st != VCS_OK) return st;
+      t.n_trials = 0;
+      if (out) *out = t;
+      return VCS_OK;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)b->n_envs;
   const size_t nst = (size_t)kStateWords * n * sizeof(uint32_t);
@@ -492,20 +553,20 @@ vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const
   b->steps_per_launch = bestK;
   cleanup();
   if (st != VCS_OK) return st;
-  b->cfg.envs_per_block = b->E;
-  b->cfg.sched_policy = (int32_t)b->sched_policy;
-  b->cfg.sched_window = (int32_t)b->sched_window;
-  b->cfg.steps_per_launch = b->steps_per_launch;
-  b->cfg.threads_per_env = b->tpe;
-  if (out) {
-    out->envs_per_block = b->E;
-    out->threads_per_env = b->tpe;
-    out->sched_policy = (int32_t)b->sched_policy;
-    out->sched_window = (int32_t)b->sched_window;
-    out->steps_per_launch = b->steps_per_launch;
-    out->ms_per_step = best / (float)n_steps;
-    out->n_trials = trials;
+  vcs_tune t;
+  t.envs_per_block = b->E;
+  t.threads_per_env = b->tpe;
+  t.sched_policy = (int32_t)b->sched_policy;
+  t.sched_window = (int32_t)b->sched_window;
+  t.steps_per_launch = b->steps_per_launch;
+  t.ms_per_step = best / (float)n_steps;
+  t.n_trials = trials;
+  if ((st = apply_tune(b, t)) != VCS_OK) return st;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = t;
   }
+  if (out) *out = t;
   return VCS_OK;
 }
 
@@ -566,6 +627,17 @@ vcs_status vcs_graph_destroy(vcs_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   delete g;
+  return VCS_OK;
+}
+
+vcs_status vcs_digest(vcs_batch* b, const uint8_t* ram, const uint8_t* screen, int32_t n_steps, uint64_t* out,
+                      void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  if (!ram || !out || n_steps < 0) return vcs_fail(b, VCS_ERR_ARG, "ram and out are required, n_steps >= 0");
+  if (((uintptr_t)ram & 15) || ((uintptr_t)screen & 15) || ((uintptr_t)out & 7))
+    return vcs_fail(b, VCS_ERR_ARG, "ram and screen must be 16-byte aligned, out 8-byte aligned");
+  int e = launch_digest(ram, screen, (uint64_t)n_steps * (uint64_t)b->n_envs, out, stream);
+  if (e) return vcs_cuda_fail(b, (cudaError_t)e, "digest kernel launch");
   return VCS_OK;
 }
 

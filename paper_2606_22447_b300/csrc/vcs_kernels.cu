@@ -169,6 +169,46 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   p.s.epi[env] = epi;
 }
 
+// ---------------------------------------------------------------------------
+// Output digests for parity at scale: for each (step, env) the sum mod 2^64
+// of F((i << 32) | w_i) over the 32-bit little-endian words w_i of the RAM
+// row followed by the screen (F the splitmix64 finaliser).  One warp per
+// digest; the sum is order-free, so lanes take strided words and reduce.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t digest_fin(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests, uint64_t* out) {
+  const uint64_t d = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const uint32_t lane = threadIdx.x & 31;
+  if (d >= n_digests) return;   // whole warps leave together
+  uint64_t acc = 0;
+  const uint32_t rw = reinterpret_cast<const uint32_t*>(ram + d * 128)[lane];   // 32 RAM words
+  acc += digest_fin(((uint64_t)lane << 32) | rw);
+  if (screen) {
+    const uint4* sp = reinterpret_cast<const uint4*>(screen + d * (kScreenH * kScreenW));
+    for (uint32_t j = lane; j < kScreenH * kScreenW / 16; j += 32) {
+      const uint4 v = sp[j];
+      const uint64_t i0 = 32 + 4 * (uint64_t)j;
+      acc += digest_fin(((i0 + 0) << 32) | v.x) + digest_fin(((i0 + 1) << 32) | v.y) +
+             digest_fin(((i0 + 2) << 32) | v.z) + digest_fin(((i0 + 3) << 32) | v.w);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  if (lane == 0) out[d] = acc;
+}
+
+int launch_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests, uint64_t* out, void* stream) {
+  if (n_digests == 0) return 0;
+  const uint64_t blocks = (n_digests + 7) / 8;
+  k_digest<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(ram, screen, n_digests, out);
+  return (int)cudaGetLastError();
+}
+
 size_t step_smem_bytes(int E) { return smem_bytes(E); }
 
 template <bool SOFT>

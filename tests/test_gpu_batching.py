@@ -4,7 +4,7 @@ leaves the batch in the state it found it."""
 import numpy as np
 import pytest
 
-from paper_2606_22447_b300 import VcsError, synth
+from paper_2606_22447_b300 import VcsError, autotune_cache_clear, synth
 from paper_2606_22447_b300._lib import VCS_ERR_STATE
 from tests.gpu_util import assert_env_equal, gpu_rollout, make_batch, oracle_rollout, torch_cuda
 
@@ -26,6 +26,7 @@ def test_autotune_keeps_state_and_results():
     ref = make_batch(roms, MAPPERS, ec)
     ram1, scr1, st1 = gpu_rollout(ref, acts, 2)
     b = make_batch(roms, MAPPERS, ec)
+    autotune_cache_clear()
     before = b.save_state()
     tune_acts = torch.from_numpy(np.ascontiguousarray(synth.actions(809, 45, 3))).cuda()
     choice = b.autotune(2, 3, actions=tune_acts)
@@ -78,8 +79,25 @@ def test_graph_replay_equals_rollout():
         assert np.array_equal(scr.cpu().numpy(), s1)
         assert np.array_equal(st.cpu().numpy(), t1)
     # a new geometry invalidates the graph: refused on the host, nothing launched
+    autotune_cache_clear()   # the trials rebuild the block table
     b.autotune(2, 1)
     with pytest.raises(VcsError) as ei:
         g.launch()
     assert ei.value.status == VCS_ERR_STATE
     g.destroy()
+
+
+def test_autotune_cache_per_shape():
+    roms, ec = _setup(37)
+    autotune_cache_clear()
+    first = make_batch(roms, MAPPERS, ec).autotune(1, 1)
+    assert first["n_trials"] > 0
+    b = make_batch(roms, MAPPERS, ec)
+    again = b.autotune(1, 1)
+    assert again["n_trials"] == 0
+    assert {k: again[k] for k in again if k not in ("n_trials",)} == {k: first[k] for k in first if k != "n_trials"}
+    assert b.envs_per_block == first["envs_per_block"]
+    other = make_batch(roms, MAPPERS, ec).autotune(3, 1)   # another frame-skip is another key
+    assert other["n_trials"] > 0
+    autotune_cache_clear()
+    assert make_batch(roms, MAPPERS, ec).autotune(1, 1)["n_trials"] > 0
