@@ -153,7 +153,9 @@ def soft_leg(n_envs, n_frames, mappers, reps, tau=0.1):
     from paper_2606_22447_b300 import Batch, default_config, synth
     roms = synth.config_carts(SEED, mappers)
     ec = synth.env_cart_round_robin(n_envs, len(mappers))
-    b = Batch(roms, mappers, ec, default_config(segment_frames=64))
+    # four replicas per env: the backward's recompute draws every frame's
+    # pixel gradients, which the replicas share
+    b = Batch(roms, mappers, ec, default_config(segment_frames=64, threads_per_env=4))
     u = torch.from_numpy(synth.action_inputs(synth.actions(SEED, n_envs, n_frames))).cuda()
     rng = np.random.default_rng(SEED)
     w_ram = torch.zeros(128, device="cuda")

@@ -84,7 +84,9 @@ typedef struct vcs_config {
   int32_t threads_per_env;  /* 0 = automatic (1); else 1, 2, 4 or 8 with
                                envs_per_block x threads_per_env <= 128: that
                                many lanes run each env in lockstep and share
-                               its rendering, output and pixel-gradient work */
+                               its rendering, output and pixel-gradient work
+                               (4 suits soft rollouts with screen losses,
+                               whose backward sums every frame's pixels) */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;
