@@ -226,6 +226,16 @@ vcs_status vcs_graph_destroy(vcs_graph* g);
 vcs_status vcs_digest(vcs_batch* b, const uint8_t* ram, const uint8_t* screen, int32_t n_steps,
                       uint64_t* out, void* stream);
 
+/* vcs_rollout through host memory, pipelined: actions_host uint8[n_steps]
+ * [n_envs]; ram_host [n_steps][n_envs][128], screen_host [n_steps][n_envs]
+ * [210][160], status_host [n_steps][n_envs] (host, nullable).  Step t's
+ * outputs are copied to the host on a second stream while step t + 1 runs
+ * (two device buffer sets, allocated by the library on the first call); the
+ * call returns when every output is on the host.  Host buffers should be
+ * pinned (page-locked) for the copies to overlap. */
+vcs_status vcs_rollout_host(vcs_batch* b, const uint8_t* actions_host, int32_t n_steps, int32_t frame_skip,
+                            uint8_t* ram_host, uint8_t* screen_host, uint8_t* status_host, void* stream);
+
 /* Wait for `stream` and report device-side failures: VCS_ERR_WATCHDOG if a
  * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA
  * for an asynchronous CUDA error. */

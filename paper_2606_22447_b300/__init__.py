@@ -118,6 +118,18 @@ class Batch:
         self._check(_lib.load().vcs_step_host(self.h, C.c_void_p(a.ctypes.data), frame_skip, p(ram_out),
                                               p(screen_out), _stream(stream)))
 
+    def rollout_host(self, actions: np.ndarray, frame_skip: int, ram_out=None, screen_out=None, status_out=None,
+                     stream=None):
+        """Pipelined rollout through host (numpy) buffers: actions uint8
+        [n_steps][n_envs]; outputs [n_steps][n_envs][...] filled on return."""
+        a = np.ascontiguousarray(actions, dtype=np.uint8)
+        p = lambda x: None if x is None else C.c_void_p(x.ctypes.data)
+        for x in (ram_out, screen_out, status_out):
+            if x is not None and not (x.flags["C_CONTIGUOUS"] and x.dtype == np.uint8):
+                raise ValueError("host outputs must be C-contiguous uint8 arrays")
+        self._check(_lib.load().vcs_rollout_host(self.h, C.c_void_p(a.ctypes.data), int(a.shape[0]), frame_skip,
+                                                 p(ram_out), p(screen_out), p(status_out), _stream(stream)))
+
     def sync(self, stream=None):
         self._check(_lib.load().vcs_sync(self.h, _stream(stream)))
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "vcs_graph_destroy": (C.c_int, [vp]),
     "vcs_digest": (C.c_int, [vp, vp, vp, i32, vp, vp]),
     "vcs_autotune_cache_clear": (C.c_int, []),
+    "vcs_rollout_host": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, vp]),
 }
 
 _lib = None

@@ -131,6 +131,16 @@ static void free_batch(vcs_batch* b) {
   cudaFree(b->h_actions);
   cudaFree(b->h_ram);
   cudaFree(b->h_screen);
+  cudaFree(b->h2_actions);
+  cudaFree(b->h2_ram);
+  cudaFree(b->h2_screen);
+  cudaFree(b->h_status[0]);
+  cudaFree(b->h_status[1]);
+  for (int k = 0; k < 2; k++) {
+    if (b->ev_kernel[k]) cudaEventDestroy(b->ev_kernel[k]);
+    if (b->ev_copy[k]) cudaEventDestroy(b->ev_copy[k]);
+  }
+  if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
   delete b;
 }
 
@@ -380,6 +390,55 @@ vcs_status vcs_step_host(vcs_batch* b, const uint8_t* actions_host, int32_t fram
       (e = cudaMemcpyAsync(screen_out_host, b->h_screen, n * kScreenH * kScreenW, cudaMemcpyDeviceToHost, s)))
     return vcs_cuda_fail(b, e, "screen download");
   if ((e = cudaStreamSynchronize(s))) return vcs_cuda_fail(b, e, "step");
+  return VCS_OK;
+}
+
+vcs_status vcs_rollout_host(vcs_batch* b, const uint8_t* actions_host, int32_t n_steps, int32_t frame_skip,
+                            uint8_t* ram_host, uint8_t* screen_host, uint8_t* status_host, void* stream) {
+  if (!b) return VCS_ERR_ARG;
+  if (!actions_host || n_steps < 0 || frame_skip < 1)
+    return vcs_fail(b, VCS_ERR_ARG, "actions_host, n_steps >= 0 and frame_skip >= 1 required");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const size_t n = (size_t)b->n_envs, scr = n * kScreenH * kScreenW;
+  if (!b->h_actions && ((e = cudaMalloc(&b->h_actions, n)) || (e = cudaMalloc(&b->h_ram, n * 128)) ||
+                        (e = cudaMalloc(&b->h_screen, scr))))
+    return vcs_cuda_fail(b, e, "staging buffers");
+  if (!b->h2_actions) {
+    if ((e = cudaMalloc(&b->h2_actions, n)) || (e = cudaMalloc(&b->h2_ram, n * 128)) ||
+        (e = cudaMalloc(&b->h2_screen, scr)) || (e = cudaMalloc(&b->h_status[0], n)) ||
+        (e = cudaMalloc(&b->h_status[1], n)) ||
+        (e = cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking)))
+      return vcs_cuda_fail(b, e, "staging buffers");
+    for (int k = 0; k < 2; k++)
+      if ((e = cudaEventCreateWithFlags(&b->ev_kernel[k], cudaEventDisableTiming)) ||
+          (e = cudaEventCreateWithFlags(&b->ev_copy[k], cudaEventDisableTiming)))
+        return vcs_cuda_fail(b, e, "staging events");
+  }
+  uint8_t* act[2] = {b->h_actions, b->h2_actions};
+  uint8_t* ram[2] = {b->h_ram, b->h2_ram};
+  uint8_t* sc[2] = {b->h_screen, b->h2_screen};
+  const cudaStream_t c = b->copy_stream;
+  for (int32_t t = 0; t < n_steps; t++) {
+    const int k = t & 1;
+    // buffer set k is free once the download of step t - 2 has finished
+    if (t >= 2 && (e = cudaStreamWaitEvent(s, b->ev_copy[k], 0))) return vcs_cuda_fail(b, e, "rollout_host");
+    if ((e = cudaMemcpyAsync(act[k], actions_host + (size_t)t * n, n, cudaMemcpyHostToDevice, s)))
+      return vcs_cuda_fail(b, e, "actions upload");
+    vcs_status st = vcs_step(b, act[k], frame_skip, ram_host ? ram[k] : nullptr, screen_host ? sc[k] : nullptr,
+                             status_host ? b->h_status[k] : nullptr, stream);
+    if (st != VCS_OK) return st;
+    if ((e = cudaEventRecord(b->ev_kernel[k], s)) || (e = cudaStreamWaitEvent(c, b->ev_kernel[k], 0)))
+      return vcs_cuda_fail(b, e, "rollout_host");
+    if (ram_host && (e = cudaMemcpyAsync(ram_host + (size_t)t * n * 128, ram[k], n * 128, cudaMemcpyDeviceToHost, c)))
+      return vcs_cuda_fail(b, e, "RAM download");
+    if (screen_host && (e = cudaMemcpyAsync(screen_host + (size_t)t * scr, sc[k], scr, cudaMemcpyDeviceToHost, c)))
+      return vcs_cuda_fail(b, e, "screen download");
+    if (status_host && (e = cudaMemcpyAsync(status_host + (size_t)t * n, b->h_status[k], n, cudaMemcpyDeviceToHost, c)))
+      return vcs_cuda_fail(b, e, "status download");
+    if ((e = cudaEventRecord(b->ev_copy[k], c))) return vcs_cuda_fail(b, e, "rollout_host");
+  }
+  if ((e = cudaStreamSynchronize(c)) || (e = cudaStreamSynchronize(s))) return vcs_cuda_fail(b, e, "rollout_host");
   return VCS_OK;
 }
 

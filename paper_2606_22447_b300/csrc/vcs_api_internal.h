@@ -32,10 +32,17 @@ struct vcs_batch {
   int32_t tpe = 1;                 // threads per env
   uint32_t geometry_gen = 0;       // bumped whenever blocks / perm are rebuilt
   int32_t* err = nullptr;
-  // staging for the host-pointer entry point
+  // staging for the host-pointer entry points: vcs_step_host uses set 0,
+  // vcs_rollout_host alternates sets 0 and 1
   uint8_t* h_actions = nullptr;
   uint8_t* h_ram = nullptr;
   uint8_t* h_screen = nullptr;
+  uint8_t* h2_actions = nullptr;
+  uint8_t* h2_ram = nullptr;
+  uint8_t* h2_screen = nullptr;
+  uint8_t* h_status[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_kernel[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
   std::string last_error;
   vcs::SoA soa() const;
 };

@@ -301,6 +301,18 @@ def test_step_host_and_state_roundtrip():
         sh = np.zeros((10, 210, 160), np.uint8)
         b.step_host(acts[t], 2, rh, sh)
         assert np.array_equal(rh, ram[t]) and np.array_equal(sh, scr[t])
+    # the pipelined host rollout (two device buffer sets, copies overlapping
+    # the next step) gives the same outputs, on pinned and pageable buffers
+    for pinned in (True, False):
+        b.load_state(blob)
+        if pinned:
+            rh = torch.zeros((4, 10, 128), dtype=torch.uint8).pin_memory().numpy()
+            sh = torch.zeros((4, 10, 210, 160), dtype=torch.uint8).pin_memory().numpy()
+        else:
+            rh, sh = np.zeros((4, 10, 128), np.uint8), np.zeros((4, 10, 210, 160), np.uint8)
+        th = np.zeros((4, 10), np.uint8)
+        b.rollout_host(acts, 2, rh, sh, th)
+        assert np.array_equal(rh, ram) and np.array_equal(sh, scr) and not th.any()
     # reset of a subset
     mask = torch.zeros(10, dtype=torch.uint8, device="cuda")
     mask[3] = 1
