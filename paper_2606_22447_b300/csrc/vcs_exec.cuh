@@ -193,9 +193,9 @@ __device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r) {
   return zp_read(c, r, 0x100u | r.SP);
 }
 
-// Tape hook: called once per executed instruction with its opcode, a
-// reference address and flag bits (the soft path records these; the hard
-// path compiles the hook away).
+// Tape hook: called for each executed instruction the backward sweep acts on
+// (reverse_needed) with its opcode, a reference address and flag bits (the
+// soft path records these; the hard path compiles the hook away).
 struct NoTape {
   static constexpr bool kAcc = false;
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) {}
@@ -330,7 +330,7 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
   p.wv = 0;
   p.widx = n;
   p.wstack = false;
-  p.rec = true;
+  p.rec = reverse_needed(OP);   // a tape record only where the backward sweep acts
   // JMP and JSR go to the same place for every lane; branches, RTS, RTI,
   // JMP (ind) and BRK end a run of lockstep instructions
   p.seq = !(id == OP_BRANCH || id == OP_JMPI || id == OP_RTS || id == OP_RTI || id == OP_BRK);

@@ -150,6 +150,23 @@ __host__ __device__ constexpr OpInfo op_info(uint32_t op) {
   }
 }
 
+
+// Whether the backward sweep does anything for an instruction: moves an
+// adjoint between a register and memory (loads, stores, logic and
+// arithmetic reads, read-modify-writes, transfers) or clears a cell or
+// register it overwrites with a value that carries no gradient (pushes, TSX).
+// Branches, compares, BIT, flag operations, register increments, jumps,
+// returns, PLP, TXS and NOP leave every adjoint as it is, so the tape does
+// not record them.
+__host__ __device__ constexpr bool reverse_needed(uint32_t op) {
+  const uint32_t id = op_info(op).id;
+  return id == OP_LDA || id == OP_LDX || id == OP_LDY || id == OP_ORA || id == OP_AND || id == OP_EOR ||
+         id == OP_ADC || id == OP_SBC || id == OP_STA || id == OP_STX || id == OP_STY || id == OP_ASL ||
+         id == OP_ROL || id == OP_LSR || id == OP_ROR || id == OP_DEC || id == OP_INC || id == OP_TAX ||
+         id == OP_TXA || id == OP_TAY || id == OP_TYA || id == OP_TSX || id == OP_PHA || id == OP_PHP ||
+         id == OP_PLA || id == OP_JSR || id == OP_BRK;
+}
+
 // Machine registers of one env (kept in registers inside a launch).
 struct Regs {
   uint32_t A, X, Y, SP, PC;

@@ -5,7 +5,8 @@
 // every segment.  The backward pass runs the segments last to first; for each
 // one a kernel, one thread per env:
 //   1. recomputes the segment's forward from its checkpoint, recording one
-//      4-byte tape entry per instruction (opcode, reference address, flags)
+//      4-byte tape entry per instruction the sweep acts on (opcode,
+//      reference address, flags; reverse_needed)
 //      and, on the frames a step returns, the sum of the pixel gradients owned
 //      by each colour-register version (the stored priority switch);
 //   2. sweeps the tape backwards, carrying adjoints of A, X, Y, the timer
