@@ -266,12 +266,15 @@ __device__ __forceinline__ void skip_timer_poll(Regs& r, uint32_t opaddr) {
 
 // One documented instruction, specialised on its opcode: mode, class and
 // operation are compile-time constants, so the only run-time dispatch of an
-// instruction is the opcode switch in exec_one.  kSkipPoll enables the timer
-// poll-loop skip (the hard path; the soft path records every instruction).
-template <uint32_t OP, bool kSkipPoll>
+// instruction is the opcode switch in exec_one.  LDA absolute first checks
+// for the head of a timer poll loop.  The skip is exact in soft mode too:
+// every skipped LDA overwrites A before anything reads it, so in the
+// backward sweep each meets a zero adjoint of A and its tape record would do
+// nothing; the LDA that exits the loop is executed and recorded.
+template <uint32_t OP>
 __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_t opaddr, uint32_t b1, uint32_t b2,
                                         Pend& p) {
-  if constexpr (OP == 0xAD && kSkipPoll) {
+  if constexpr (OP == 0xAD) {
     const uint32_t off = opaddr & 0xFFF;
     if (b1 == 0x84 && b2 == 0x02 && (opaddr & 0x1000) && off <= 0xFFA) {
       const uint8_t* q = c.rom + ((r.bank << 12) | off);
@@ -477,7 +480,7 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
   for (;;) {
     switch (sel) {
 #define VCS_CASE(x) \
-  case x: exec_op<x, std::is_same<Tape, NoTape>::value>(c, r, st, opaddr, b1, b2, p); break;
+  case x: exec_op<x>(c, r, st, opaddr, b1, b2, p); break;
       VCS_DOCUMENTED_OPS(VCS_CASE)
 #undef VCS_CASE
       case 0x101: {   // fetch through the bus, then dispatch on what was read
