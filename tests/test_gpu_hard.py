@@ -257,6 +257,104 @@ def test_timer_poll_loops():
     _check_all(roms, maps, env_cart, acts, 2)
 
 
+def _ram_code_rom():
+    """Copies a routine into RAM and calls it every line (code executing from
+    $0080 takes the bus-fetch path), and runs code in the last bytes of the
+    cartridge window ($FFF0-$FFF9, also fetched through the bus)."""
+    routine = [0xA9, 0x2A, 0x65, 0x91, 0x85, 0x09, 0xE6, 0x90, 0xA5, 0x90, 0x85, 0x08, 0x60]  # LDA #; ADC; STA; INC; LDA; STA; RTS
+
+    def build(a):
+        a.op("LDX", "imm", 0xFF)
+        a.op("TXS")
+        a.op("LDX", "imm", 0)
+        a.label("C")
+        a.op("LDA", "absx", "TAB")
+        a.op("STA", "zpx", 0x80)
+        a.op("INX")
+        a.op("CPX", "imm", len(routine))
+        a.op("BNE", "rel", "C")
+        a.label("F")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "abs", 0x0280)
+        a.op("STA", "zp", 0x91)
+        a.op("LDY", "imm", 100)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("JSR", "abs", 0x0080)
+        a.op("JMP", "abs", 0xFFF0)
+        a.label("BACK")
+        a.op("DEY")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "F")
+        a.label("TAB")
+        for b in routine:
+            a.byte(b)
+        a.at(0xFF0)                       # $FFF0: INC $92; LDA $92; STA $0E; JMP BACK (ends at $FFF8)
+        a.op("INC", "zp", 0x92)
+        a.op("LDA", "zp", 0x92)
+        a.op("STA", "zp", 0x0E)
+        a.byte(0x4C)
+        a.word("BACK")
+    return rom4k(build, table=False)
+
+
+def _f8_window_end_rom():
+    """F8 image whose bank-1 code falls through $FFF4..$FFF7: the opcode
+    fetch at $FFF8 selects bank 0 (where it reads BNE), the operand fetch at
+    $FFF9 selects bank 1 again (the offset comes from there), and the branch
+    lands on a JMP back to the frame loop in bank 1."""
+    def bank(b):
+        a = synth.Asm(0xF000, 4096)
+        if b == 1:
+            a.label("F")
+            a.op("LDA", "imm", 2)
+            a.op("STA", "zp", 0x02)
+            a.op("STA", "zp", 0x00)
+            a.op("LDA", "imm", 0)
+            a.op("STA", "zp", 0x00)
+            a.op("LDX", "imm", 150)
+            a.label("L")
+            a.op("STA", "zp", 0x02)
+            a.op("INC", "zp", 0x80)
+            a.op("LDA", "zp", 0x80)
+            a.op("STA", "zp", 0x09)
+            a.op("DEX")
+            a.op("BNE", "rel", "L")
+            a.op("LDA", "imm", 1)              # Z clear: the BNE below is taken
+            a.op("JMP", "abs", 0xFFF4)
+            a.at(0xFE6)
+            a.op("JMP", "abs", "F")            # $FFE6, the branch target
+            a.at(0xFF4)
+            for _ in range(4):
+                a.op("NOP")                    # $FFF4-$FFF7
+            a.byte(0xEA)                       # $FFF8 (not reached in this bank)
+            a.byte(0xEC)                       # $FFF9: the branch offset, -20 -> $FFE6
+        else:
+            a.at(0xFF8)
+            a.byte(0xD0)                       # $FFF8 in bank 0: BNE
+            a.byte(0xEA)
+        a.at(0xFFA)
+        a.word(0xF000)
+        a.word(0xF000)
+        a.word(0xF000)
+        return bytes(a.resolve())
+    return bank(0) + bank(1)
+
+
+def test_code_fetched_through_the_bus():
+    """Code in RAM, in the last bytes of the 4 KB window and across the F8
+    hotspots runs through the bus-fetch path; it must match the oracle."""
+    roms = [_ram_code_rom(), _f8_window_end_rom()]
+    maps = [synth.MAPPER_4K, synth.MAPPER_F8]
+    env_cart = np.arange(8) % 2
+    acts = synth.actions(717, 8, 6)
+    _check_all(roms, maps, env_cart, acts, 2)
+
+
 def test_generated_carts_cover_the_instruction_set():
     """The seeded carts execute (nearly) every documented opcode."""
     seen = set()
