@@ -34,6 +34,10 @@ METRIC = "env-steps/s per B300 (hard fwd; soft fwd+bwd), bit-exact vs CPU oracle
 WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+screen per step"
 # algorithmic integer work per env-step: 12 operations per emulated instruction
 # and 6 per output pixel; peak = SMs x 128 integer lanes x maximum SM clock
+# DRAM bytes (read + write) of one step launch on the bench workload, from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
+# kernel; to be taken again whenever the kernel changes
+TRAFFIC_BYTES_PER_LAUNCH = 940_800 + 83_328_768
 OPS_PER_INSTRUCTION = 12
 OPS_PER_PIXEL = 6
 PIXELS_PER_STEP = 210 * 160
@@ -328,7 +332,9 @@ def gpu_arm(args):
     max_mhz = peaks.get("sm_max_mhz") or clk["sm_max_mhz"] or 2032.0
     peak_ops = props.multi_processor_count * INT_LANES_PER_SM * max_mhz * 1e6
     roofline = {"bound": "alu", "achieved": ops / mean_s / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": ops / mean_s / peak_ops, "traffic": None,
+                "frac": ops / mean_s / peak_ops, "traffic": TRAFFIC_BYTES_PER_LAUNCH if n == N_ENVS else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_run launch at 4096 envs; "
+                                  f"algorithmic bytes per launch {n * (PIXELS_PER_STEP + 128 + 1)}",
                 "peak_source": f"derived: {props.multi_processor_count} SMs x {INT_LANES_PER_SM} int lanes x "
                                f"{max_mhz:.0f} MHz (measured max clock)",
                 "ops_per_env_step": ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL,
