@@ -120,6 +120,27 @@ def oracle_sample(n_envs: int, n_steps: int, threads: int):
     return n_envs * n_steps, dt, sum(instr) / (n_envs * n_steps)
 
 
+def replica_seed(rank: int) -> int:
+    """Each rank is an independent replica with its own action stream."""
+    return SEED + rank
+
+
+def max_over_ranks(elapsed: float, dist, device: str) -> float:
+    """The job's time: the slowest rank's (all ranks return it)."""
+    if dist is None:
+        return elapsed
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(n_envs: int, steps: int, world: int, elapsed: float) -> float:
+    """Whole-job throughput: env-steps of every rank over the job's time."""
+    return world * n_envs * steps / elapsed
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -262,7 +283,7 @@ def gpu_arm(args):
     n = args.envs
     batch = Batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32), default_config(envs_per_block=args.epb))
     total_steps = args.warmup + args.steps
-    acts = torch.from_numpy(synth.actions(SEED + rank, n, total_steps)).cuda()
+    acts = torch.from_numpy(synth.actions(replica_seed(rank), n, total_steps)).cuda()
     ram = torch.empty((n, 128), dtype=torch.uint8, device="cuda")
     scr = torch.empty((n, 210, 160), dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -294,12 +315,8 @@ def gpu_arm(args):
     batch.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     elapsed = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        dist.barrier()
-    value = world * n * args.steps / elapsed
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
+    value = job_value(n, args.steps, world, elapsed)
 
     # end to end through the host-buffer entry point: each step's actions go
     # up from pinned host memory and its RAM and screen come back into pinned
