@@ -236,6 +236,13 @@ vcs_status vcs_digest(vcs_batch* b, const uint8_t* ram, const uint8_t* screen, i
 vcs_status vcs_rollout_host(vcs_batch* b, const uint8_t* actions_host, int32_t n_steps, int32_t frame_skip,
                             uint8_t* ram_host, uint8_t* screen_host, uint8_t* status_host, void* stream);
 
+/* Measured integer issue rate of the current device (the roofline
+ * denominator of the integer-bound emulator; a measurement utility with no
+ * counterpart in the paper): a kernel at full occupancy running independent
+ * chains of 32-bit add, shift and logic operations, timed with CUDA events;
+ * *ops_per_s receives operations per second.  Synchronises `stream`. */
+vcs_status vcs_int_peak(double* ops_per_s, void* stream);
+
 /* Wait for `stream` and report device-side failures: VCS_ERR_WATCHDOG if a
  * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA
  * for an asynchronous CUDA error. */

@@ -34,6 +34,13 @@ def autotune_cache_clear():
     _lib.check(_lib.load().vcs_autotune_cache_clear(), None)
 
 
+def int_peak(stream=None) -> float:
+    """Measured integer operations per second of the current GPU."""
+    v = C.c_double()
+    _lib.check(_lib.load().vcs_int_peak(C.byref(v), _stream(stream)), None)
+    return v.value
+
+
 def _ptr(t):
     """Device address of a CUDA tensor (None -> NULL)."""
     if t is None:

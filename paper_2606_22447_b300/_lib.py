@@ -74,6 +74,7 @@ SIGNATURES = {
     "vcs_digest": (C.c_int, [vp, vp, vp, i32, vp, vp]),
     "vcs_autotune_cache_clear": (C.c_int, []),
     "vcs_rollout_host": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, vp]),
+    "vcs_int_peak": (C.c_int, [C.POINTER(C.c_double), vp]),
 }
 
 _lib = None

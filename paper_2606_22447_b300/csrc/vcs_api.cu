@@ -689,6 +689,35 @@ vcs_status vcs_graph_destroy(vcs_graph* g) {
   return VCS_OK;
 }
 
+vcs_status vcs_int_peak(double* ops_per_s, void* stream) {
+  if (!ops_per_s) return VCS_ERR_ARG;
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+    return vcs_cuda_fail(nullptr, e, "device query");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int32_t iters = 4096;
+  float ms = 0.f;
+  if (!(e = cudaMalloc(&sink, (size_t)sms * 2 * sizeof(uint32_t))) && !(e = cudaEventCreate(&e0)) &&
+      !(e = cudaEventCreate(&e1))) {
+    launch_int_peak(sms, iters, sink, stream);   // warm-up
+    if (!(e = cudaEventRecord(e0, s))) {
+      int le = launch_int_peak(sms, iters, sink, stream);
+      if (le) e = (cudaError_t)le;
+      else if (!(e = cudaEventRecord(e1, s)) && !(e = cudaEventSynchronize(e1))) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+  }
+  cudaFree(sink);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e) return vcs_cuda_fail(nullptr, e, "integer peak");
+  // 72 operations per thread per loop turn (k_int_peak)
+  *ops_per_s = (double)sms * 2 * 1024 * (double)iters * 72.0 / (ms * 1e-3);
+  return VCS_OK;
+}
+
 vcs_status vcs_digest(vcs_batch* b, const uint8_t* ram, const uint8_t* screen, int32_t n_steps, uint64_t* out,
                       void* stream) {
   if (!b) return VCS_ERR_ARG;

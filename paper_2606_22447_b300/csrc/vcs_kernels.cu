@@ -209,6 +209,39 @@ int launch_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests,
   return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Integer issue peak: every thread runs eight independent chains of 32-bit
+// add, shift and logic operations (the instruction kinds the emulator issues
+// most), at full occupancy, so the measured rate is the SMs' integer
+// throughput.  Each chain does nine operations per loop turn as written (72
+// per thread); the compiler fuses some of them (three-input adds and logic),
+// as it does in the emulator.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_int_peak(uint32_t seed, int32_t iters, uint32_t* sink) {
+  uint32_t a[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) a[k] = seed + 0x9E3779B9u * (threadIdx.x * 8 + k + 1);
+  const uint32_t m = seed | 1u;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      a[k] = a[k] + (a[k] >> 3) + m;     // add of three operands
+      a[k] = (a[k] ^ m) & (a[k] | 0x5A5A5A5Au);   // a three-input logic operation
+      a[k] = a[k] + 0x3C6EF372u;
+      a[k] = a[k] ^ (a[k] << 5);
+    }
+  }
+  uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) x ^= a[k];
+  if (x == seed) sink[blockIdx.x] = x;   // keeps the work alive; practically never taken
+}
+
+int launch_int_peak(int sms, int32_t iters, uint32_t* sink, void* stream) {
+  k_int_peak<<<sms * 2, 1024, 0, (cudaStream_t)stream>>>(0x1234567u, iters, sink);
+  return (int)cudaGetLastError();
+}
+
 size_t step_smem_bytes(int E) { return smem_bytes(E); }
 
 template <bool SOFT>

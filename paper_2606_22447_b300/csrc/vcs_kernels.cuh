@@ -71,6 +71,7 @@ __host__ __device__ inline SoA soa_at(uint32_t* base, int32_t n_envs) {
 
 void build_decode_tables(DecodeTables* t);
 size_t step_smem_bytes(int envs_per_block);
+int launch_int_peak(int sms, int32_t iters, uint32_t* sink, void* stream);
 int launch_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests, uint64_t* out, void* stream);
 // Launch the step kernel over `n_blocks` blocks of `envs_per_block`
 // (soft = the SOFT-STE forward: float inputs / outputs and checkpoints).

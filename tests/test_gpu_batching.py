@@ -101,3 +101,14 @@ def test_autotune_cache_per_shape():
     assert other["n_trials"] > 0
     autotune_cache_clear()
     assert make_batch(roms, MAPPERS, ec).autotune(1, 1)["n_trials"] > 0
+
+
+def test_int_peak_is_a_plausible_rate():
+    """The roofline denominator: measured integer operations per second, within
+    a factor of two of the SM count x 128 lanes x the clock."""
+    import torch
+    from paper_2606_22447_b300 import int_peak
+    v = int_peak()
+    props = torch.cuda.get_device_properties(0)
+    derived = props.multi_processor_count * 128 * 2.032e9
+    assert 0.5 * derived < v < 2.0 * derived
