@@ -168,7 +168,15 @@ def reference_arm(args):
     }), flush=True)
 
 
-def soft_leg(n_envs, n_frames, mappers, reps, tau=0.1):
+def bench_counts() -> dict:
+    """Emulated instructions of the bench workloads, counted by the oracle
+    ahead of time (stored next to the tests' golden files; a CPU test checks
+    that they are current)."""
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "bench_counts.json")) as f:
+        return json.load(f)
+
+
+def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1):
     """SOFT-STE forward + backward over n_frames (frame-skip 1, 64-frame
     checkpoint segments, loss weights on 8 RAM bytes and 256 pixels at every
     step).  Returns env-steps/s of fwd+bwd, the split and the library's
@@ -208,7 +216,10 @@ def soft_leg(n_envs, n_frames, mappers, reps, tau=0.1):
             if best is None or fwd + bwd < best[0] + best[1]:
                 best = (fwd, bwd, used)
     fwd, bwd, used = best
-    return {"env_steps_per_s": n_envs * n_frames / ((fwd + bwd) / 1e3), "fwd_ms": fwd, "bwd_ms": bwd,
+    ipf = bench_counts()[count_key]
+    return {"env_steps_per_s": n_envs * n_frames / ((fwd + bwd) / 1e3),
+            "instructions_per_s": n_envs * n_frames * ipf / ((fwd + bwd) / 1e3),
+            "instructions_per_frame": ipf, "fwd_ms": fwd, "bwd_ms": bwd,
             "n_envs": n_envs, "frames": n_frames, "tau": tau, "tape_device_gb": used / 1e9,
             "gpu_launches": 1 + 2 * ((n_frames + 63) // 64) + 2}
 
@@ -336,11 +347,7 @@ def gpu_arm(args):
     # roofline: algorithmic integer work of one launch / mean launch time
     ipe = args.instr_per_step
     if ipe is None:
-        import oracle
-        o = oracle.Oracle(rom, synth.MAPPER_4K)
-        for t in range(8):
-            o.step(int(synth.actions(SEED, 1, 8)[t, 0]), FRAME_SKIP)
-        ipe = o.counters()["instructions"] / 8
+        ipe = bench_counts()["hard_4096x4k_instructions_per_env_step"]
     ops = n * (ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL)
     mean_s = elapsed / args.steps
     props = torch.cuda.get_device_properties(local)
@@ -365,9 +372,9 @@ def gpu_arm(args):
     soft = None
     if not args.no_soft:
         from paper_2606_22447_b300 import synth as _s
-        soft = {"short_1024x64": soft_leg(1024, 64, [_s.MAPPER_4K], reps=3)}
+        soft = {"short_1024x64": soft_leg(1024, 64, [_s.MAPPER_4K], 3, "soft_short_1024x4k_instructions_per_frame")}
         if not args.no_soft_long:
-            soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, reps=1)
+            soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, 1, "soft_long_4096xmix8_instructions_per_frame")
     mixed = None
     if not args.no_mixed:
         mixed = mixed_leg(args.mixed_envs, 8, 5)

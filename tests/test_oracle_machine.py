@@ -301,3 +301,17 @@ def test_vblank_blacks_out():
         a.op("STA", "zp", 0x01)        # VBLANK on from cycle 10 -> clock 30
     row = _screen_of(line)[10]
     assert np.all(row == 0)
+
+
+def test_stored_bench_counts_are_current():
+    """bench.py reads its instruction counts from tests/golden/bench_counts.json
+    (the roofline's work and the paper's unit); they must be what the
+    committed script computes from the oracle today."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    import make_bench_counts
+    stored = json.load(open(os.path.join(here, "bench_counts.json")))
+    assert stored == make_bench_counts.counts()
