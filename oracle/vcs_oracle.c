@@ -28,7 +28,9 @@
  *  A11 NMOS decimal mode per the published note on decimal mode;
  *  A12 pushed P always has bits 4 and 5 set (PHP and BRK are the only
  *     pushes of P on a 6507); BRK vectors through $1FFE.
- *  Undocumented opcodes jam the CPU: from then on each instruction slot
+ *  The paper's 38 extra opcode bytes (USBC, the unofficial NOPs, LAX, SAX)
+ *  are executed; every other undocumented opcode jams the CPU: from then on
+ *  each instruction slot
  *  idles to the next line start, so the frame ends by the 512-line cap.
  */
 #include "vcs_oracle.h"
@@ -609,7 +611,10 @@ static void exec(ovcs* s) {
   if (cc == 1) {                       /* ORA AND EOR ADC STA LDA CMP SBC */
     int mode = mode01[bbb];
     if (aaa == 4) {                    /* STA */
-      if (mode == M_IMM) goto jam;
+      if (mode == M_IMM) {             /* $89: no STA #imm; one of the extra NOP #imm bytes */
+        (void)operand(s, M_IMM);
+        return;
+      }
       val x = {s->A, s->nA};
       wr(s, address(s, mode, K_WRITE), x);
       return;
@@ -789,6 +794,46 @@ static void exec(ovcs* s) {
     case 0xCA: idle(s); s->X--; set_nz(s, s->X); return;
     case 0xC8: idle(s); s->Y++; set_nz(s, s->Y); return;
     case 0x88: idle(s); s->Y--; set_nz(s, s->Y); return;
+    /* ---- the paper's 38 extra opcode bytes (unofficial NMOS opcodes) ---- */
+    case 0xEB: {                       /* USBC #imm: SBC's alias */
+      val m = operand(s, M_IMM);
+      op_sbc(s, m.v);
+      s->nA = lin2(s, s->nA, 1.0, m.n, -1.0);
+      return;
+    }
+    case 0x1A: case 0x3A: case 0x5A: case 0x7A: case 0xDA: case 0xFA:
+      idle(s);                         /* NOP */
+      return;
+    case 0x80: case 0x82: case 0x89: case 0xC2: case 0xE2:
+      (void)operand(s, M_IMM);         /* NOP #imm */
+      return;
+    case 0x04: case 0x44: case 0x64:   /* NOP zp: the operand is read and dropped */
+      (void)operand(s, M_ZP);
+      return;
+    case 0x14: case 0x34: case 0x54: case 0x74: case 0xD4: case 0xF4:
+      (void)operand(s, M_ZPX);
+      return;
+    case 0x0C:
+      (void)operand(s, M_ABS);
+      return;
+    case 0x1C: case 0x3C: case 0x5C: case 0x7C: case 0xDC: case 0xFC:
+      (void)operand(s, M_ABX);
+      return;
+    case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   /* LAX: A = X = M */
+      int mode = op == 0xA7 ? M_ZP : op == 0xB7 ? M_ZPY : op == 0xAF ? M_ABS : op == 0xBF ? M_ABY
+               : op == 0xA3 ? M_INX : M_INY;
+      val m = operand(s, mode);
+      s->A = s->X = m.v;
+      s->nA = s->nX = m.n;
+      set_nz(s, m.v);
+      return;
+    }
+    case 0x87: case 0x97: case 0x8F: case 0x83: {                         /* SAX: M = A & X */
+      int mode = op == 0x87 ? M_ZP : op == 0x97 ? M_ZPY : op == 0x8F ? M_ABS : M_INX;
+      val x = {(uint8_t)(s->A & s->X), lin2(s, s->nA, 1.0, s->nX, 1.0)};
+      wr(s, address(s, mode, K_WRITE), x);
+      return;
+    }
     default: break;
   }
 jam:

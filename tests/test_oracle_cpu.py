@@ -214,8 +214,29 @@ FLAGS = {"ADC": FN | FV | FZ | FC, "SBC": FN | FV | FZ | FC, "AND": FN | FZ, "OR
          "CLV": FV, "BRK": FI}
 
 
+# The paper's 38 extra opcode bytes (unofficial NMOS opcodes; lengths and
+# cycle counts from the public unofficial-opcode documentation): USBC, the
+# NOPs with and without operands, LAX and SAX.
+EXTRA = {0xEB: ("USBC", "imm", 2, 2, 0)}
+EXTRA.update({c: ("NOP", "imp", 1, 2, 0) for c in (0x1A, 0x3A, 0x5A, 0x7A, 0xDA, 0xFA)})
+EXTRA.update({c: ("NOPR", "imm", 2, 2, 0) for c in (0x80, 0x82, 0x89, 0xC2, 0xE2)})
+EXTRA.update({c: ("NOPR", "zp", 2, 3, 0) for c in (0x04, 0x44, 0x64)})
+EXTRA.update({c: ("NOPR", "zpx", 2, 4, 0) for c in (0x14, 0x34, 0x54, 0x74, 0xD4, 0xF4)})
+EXTRA.update({0x0C: ("NOPR", "abs", 3, 4, 0)})
+EXTRA.update({c: ("NOPR", "absx", 3, 4, 1) for c in (0x1C, 0x3C, 0x5C, 0x7C, 0xDC, 0xFC)})
+EXTRA.update({0xA7: ("LAX", "zp", 2, 3, 0), 0xB7: ("LAX", "zpy", 2, 4, 0), 0xAF: ("LAX", "abs", 3, 4, 0),
+              0xBF: ("LAX", "absy", 3, 4, 1), 0xA3: ("LAX", "indx", 2, 6, 0), 0xB3: ("LAX", "indy", 2, 5, 1),
+              0x87: ("SAX", "zp", 2, 3, 0), 0x97: ("SAX", "zpy", 2, 4, 0), 0x8F: ("SAX", "abs", 3, 4, 0),
+              0x83: ("SAX", "indx", 2, 6, 0)})
+FLAGS.update({"USBC": FN | FV | FZ | FC, "LAX": FN | FZ})
+
+
 def test_table_has_151_documented_opcodes():
     assert len(MOS) == 151
+
+
+def test_extra_table_has_the_papers_38_bytes():
+    assert len(EXTRA) == 38 and not set(EXTRA) & set(MOS)
 
 
 def _operand_bytes(mode, cross):
@@ -238,7 +259,7 @@ def _operand_bytes(mode, cross):
 
 
 def _exec_opcode(op, cross=False, regs=None, ram=None):
-    m, mode, n, _, _ = MOS[op]
+    m, mode, n, _, _ = MOS.get(op) or EXTRA[op]
     body = [op] + _operand_bytes(mode, cross) if mode != "rel" else [op, 0x10]
     if m == "JSR" or (m == "JMP" and mode == "abs"):
         body = [op, 0x00, 0xF8]
@@ -263,9 +284,12 @@ def _exec_opcode(op, cross=False, regs=None, ram=None):
     return o, s0, o.state(), cyc
 
 
-@pytest.mark.parametrize("op", sorted(k for k, v in MOS.items() if v[1] != "rel"))
+ALL = {**MOS, **EXTRA}
+
+
+@pytest.mark.parametrize("op", sorted(k for k, v in ALL.items() if v[1] != "rel"))
 def test_opcode_cycles_and_length(op):
-    m, mode, n, cyc, pen = MOS[op]
+    m, mode, n, cyc, pen = ALL[op]
     o, s0, s1, c = _exec_opcode(op)
     assert c == cyc, (hex(op), m, mode, c, cyc)
     if m not in ("JMP", "JSR", "RTS", "RTI", "BRK"):
@@ -299,9 +323,9 @@ def test_branch_cycles(op):
                 assert pc1 == pc + 2 and c == 2
 
 
-@pytest.mark.parametrize("op", sorted(k for k, v in MOS.items() if v[0] not in ("PLP", "RTI")))
+@pytest.mark.parametrize("op", sorted(k for k, v in ALL.items() if v[0] not in ("PLP", "RTI")))
 def test_opcode_flag_effects(op):
-    m, mode = MOS[op][:2]
+    m, mode = ALL[op][:2]
     allowed = FLAGS.get(m, 0)
     rng = np.random.default_rng(op)
     changed = 0
@@ -362,3 +386,57 @@ def test_stack_and_subroutines():
     ram = o.ram()
     assert (ram[0x7E], ram[0x7D]) == (0xF0, 0x06)
     assert o.exec_one() == 6 and o.state()[5] == 0xF006
+
+
+def test_extra_opcode_behaviour():
+    """LAX loads A and X with the operand; SAX stores A & X and leaves the
+    flags; USBC is SBC immediate for every A, operand, carry and decimal
+    flag; the NOPs change no register or RAM."""
+    rng = np.random.default_rng(38)
+    for _ in range(64):
+        ram = rng.integers(0, 256, 128).astype(np.uint8)
+        a, x = int(rng.integers(256)), int(rng.integers(256))
+        p = int(rng.integers(256)) | 0x30
+        o, s0, s1, _ = _exec_opcode(0xA7, regs=dict(A=a, X=x, Y=0, SP=0xFF, P=p, PC=0xF000), ram=ram)
+        assert s1[0] == s1[1] == 0x98               # LAX $90: cell $10, which the set-up points at $0098
+        o, s0, s1, _ = _exec_opcode(0x87, regs=dict(A=a, X=x, Y=0, SP=0xFF, P=p, PC=0xF000), ram=ram)
+        assert o.ram()[0x10] == a & x and s1[4] == s0[4] and s1[0] == a and s1[1] == x
+        set_up = ram.copy()
+        set_up[0x10], set_up[0x11], set_up[0x20], set_up[0x21] = 0x98, 0x00, 0x00, 0xFE   # _exec_opcode's pointers
+        for op in (0x1A, 0x80, 0x04, 0x14, 0x0C, 0x1C):
+            o, s0, s1, _ = _exec_opcode(op, regs=dict(A=a, X=x, Y=0, SP=0xFF, P=p, PC=0xF000), ram=ram)
+            assert list(s1[:5]) == list(s0[:5]) and np.array_equal(o.ram(), set_up)
+
+    def build(a):
+        a.byte(0xEB, 0x00)       # $F000: USBC #$00 (operand patched per case below)
+        a.at(0x10)
+        a.byte(0xE9, 0x00)       # $F010: SBC #$00
+    for m in (0x00, 0x01, 0x09, 0x10, 0x7F, 0x80, 0x99, 0xFF):
+        img = bytearray(rom4k(build))
+        img[1] = img[0x11] = m
+        o = oracle.Oracle(bytes(img), synth.MAPPER_4K)
+        for a in range(0, 256, 7):
+            for p in (0x30, 0x31, 0x38, 0x39):
+                o.set_regs(A=a, P=p, PC=0xF000)
+                o.exec_one()
+                r1 = o.state()[[0, 4]]
+                o.set_regs(A=a, P=p, PC=0xF010)
+                o.exec_one()
+                assert np.array_equal(r1, o.state()[[0, 4]])
+
+
+def test_extra_nop_reads_have_side_effects():
+    """An unofficial NOP with an absolute operand reads it like a load: a
+    read of $1FF8 selects F8 bank 0."""
+    def bank(b):
+        a = synth.Asm(0xF000, 4096)
+        a.byte(0x0C, 0xF8, 0xFF)   # NOP $FFF8
+        a.at(0xFFA)
+        a.word(0xF000)
+        a.word(0xF000)
+        a.word(0xF000)
+        return bytes(a.resolve())
+    o = oracle.Oracle(bank(0) + bank(1), synth.MAPPER_F8)
+    assert o.bank() == 1
+    o.exec_one()
+    assert o.bank() == 0
