@@ -58,7 +58,8 @@ enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2 };
 /* Per-env status bits reported by vcs_step / vcs_rollout. */
 enum {
   VCS_ENV_WATCHDOG = 1,  /* a frame was ended by the 512-scanline cap */
-  VCS_ENV_JAMMED = 2,    /* the CPU met an undocumented opcode and halted */
+  VCS_ENV_JAMMED = 2,    /* the CPU met an opcode outside the documented set and the
+                            paper's 38 extra bytes, and halted */
   VCS_ENV_DONE = 4       /* the episode ended at this step (auto-reset) */
 };
 

@@ -208,9 +208,14 @@ constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8)
                               (3u << 14) | (3u << 16) | (2u << 18) | (2u << 20) | (2u << 22) | (3u << 24) |
                               (1u << 26);
 
-// The 151 documented opcodes (op_info gives each one's mode, cycles and
-// operation); every other byte jams the CPU.
-#define VCS_DOCUMENTED_OPS(X) \
+// The implemented opcodes: the 151 documented ones and the paper's 38 extra
+// bytes (op_info gives each one's mode, cycles and operation); every other
+// byte jams the CPU.
+#define VCS_IMPLEMENTED_OPS(X) \
+  X(0xEB) X(0x1A) X(0x3A) X(0x5A) X(0x7A) X(0xDA) X(0xFA) X(0x80) X(0x82) X(0x89) X(0xC2) X(0xE2) \
+  X(0x04) X(0x44) X(0x64) X(0x14) X(0x34) X(0x54) X(0x74) X(0xD4) X(0xF4) X(0x0C) X(0x1C) X(0x3C) \
+  X(0x5C) X(0x7C) X(0xDC) X(0xFC) X(0xA7) X(0xB7) X(0xAF) X(0xBF) X(0xA3) X(0xB3) X(0x87) X(0x97) \
+  X(0x8F) X(0x83) \
   X(0x00) X(0x01) X(0x05) X(0x06) X(0x08) X(0x09) X(0x0A) X(0x0D) X(0x0E) X(0x10) X(0x11) X(0x15) \
   X(0x16) X(0x18) X(0x19) X(0x1D) X(0x1E) X(0x20) X(0x21) X(0x24) X(0x25) X(0x26) X(0x28) X(0x29) \
   X(0x2A) X(0x2C) X(0x2D) X(0x2E) X(0x30) X(0x31) X(0x35) X(0x36) X(0x38) X(0x39) X(0x3D) X(0x3E) \
@@ -353,6 +358,8 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     r.fV = (m >> 6) & 1;
     r.zsrc = r.A & m;
   }
+  else if constexpr (id == OP_LAX) { r.A = m; r.X = m; set_nz(r, m); }
+  else if constexpr (id == OP_SAX) { p.nw = 1; p.wv = r.A & r.X; }
   else if constexpr (id == OP_STA) { p.nw = 1; p.wv = r.A; }
   else if constexpr (id == OP_STX) { p.nw = 1; p.wv = r.X; }
   else if constexpr (id == OP_STY) { p.nw = 1; p.wv = r.Y; }
@@ -439,7 +446,7 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
   else if constexpr (id == OP_DEX) { r.X = (r.X - 1) & 0xFF; set_nz(r, r.X); }
   else if constexpr (id == OP_INY) { r.Y = (r.Y + 1) & 0xFF; set_nz(r, r.Y); }
   else if constexpr (id == OP_DEY) { r.Y = (r.Y - 1) & 0xFF; set_nz(r, r.Y); }
-  // OP_NOP: nothing
+  // OP_NOP and OP_NOPR (its operand read above): nothing
   p.n = n;
   p.ea = ea;
 }
@@ -481,7 +488,7 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
     switch (sel) {
 #define VCS_CASE(x) \
   case x: exec_op<x>(c, r, st, opaddr, b1, b2, p); break;
-      VCS_DOCUMENTED_OPS(VCS_CASE)
+      VCS_IMPLEMENTED_OPS(VCS_CASE)
 #undef VCS_CASE
       case 0x101: {   // fetch through the bus, then dispatch on what was read
         op = bus_read(c, r, st, opaddr, 1);

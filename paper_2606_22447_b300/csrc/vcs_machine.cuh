@@ -50,6 +50,7 @@ enum : uint8_t {
   OP_PHA, OP_PHP, OP_PLA, OP_PLP,
   OP_CLC, OP_SEC, OP_CLI, OP_SEI, OP_CLV, OP_CLD, OP_SED, OP_NOP,
   OP_TAX, OP_TXA, OP_TAY, OP_TYA, OP_TSX, OP_TXS, OP_INX, OP_DEX, OP_INY, OP_DEY,
+  OP_LAX, OP_SAX, OP_NOPR,   // of the paper's extra opcode bytes (NOPR: a NOP that reads its operand)
   OP_JAM = 63
 };
 
@@ -60,10 +61,13 @@ struct DecodeTables {
   uint8_t cls_op[256];
 };
 
-// Addressing mode, base cycle count (MOS 6500 data sheet), class and
-// operation of one opcode; undocumented opcodes decode as AM_JAM.  This is
-// the one definition of the instruction set: the step kernel specialises its
-// handlers on it at compile time and the host builds DecodeTables from it.
+// Addressing mode, base cycle count (MOS 6500 data sheet; the unofficial-
+// opcode tables for the extra bytes), class and operation of one opcode.
+// Implemented: the 151 documented opcodes and the paper's 38 extra bytes
+// (USBC = SBC #imm, the unofficial NOPs, LAX, SAX); every other byte decodes
+// as AM_JAM.  This is the one definition of the instruction set: the step
+// kernel specialises its handlers on it at compile time and the host builds
+// DecodeTables from it.
 struct OpInfo {
   uint8_t mode, cyc, cls, id;
 };
@@ -74,8 +78,8 @@ __host__ __device__ constexpr OpInfo op_info(uint32_t op) {
     const uint8_t modes[8] = {AM_INX, AM_ZP, AM_IMM, AM_ABS, AM_INY, AM_ZPX, AM_ABY, AM_ABX};
     const uint8_t cyc[8] = {6, 3, 2, 4, 5, 4, 4, 4};
     const uint8_t ids[8] = {OP_ORA, OP_AND, OP_EOR, OP_ADC, OP_STA, OP_LDA, OP_CMP, OP_SBC};
-    if (aaa == 4) {   // STA: no immediate form; indexed stores always pay the fix-up cycle
-      if (modes[bbb] == AM_IMM) return OpInfo{AM_JAM, 1, CL_OTHER, OP_JAM};
+    if (aaa == 4) {   // STA: no immediate form ($89 is an extra NOP #imm); indexed stores pay the fix-up cycle
+      if (modes[bbb] == AM_IMM) return OpInfo{AM_IMM, 2, CL_READ, OP_NOPR};
       const uint8_t c = modes[bbb] == AM_INY ? 6 : (modes[bbb] == AM_ABX || modes[bbb] == AM_ABY) ? 5 : cyc[bbb];
       return OpInfo{modes[bbb], c, CL_STORE, OP_STA};
     }
@@ -146,6 +150,25 @@ __host__ __device__ constexpr OpInfo op_info(uint32_t op) {
     case 0xCA: return OpInfo{AM_IMP, 2, CL_OTHER, OP_DEX};
     case 0xC8: return OpInfo{AM_IMP, 2, CL_OTHER, OP_INY};
     case 0x88: return OpInfo{AM_IMP, 2, CL_OTHER, OP_DEY};
+    // the paper's extra opcode bytes
+    case 0xEB: return OpInfo{AM_IMM, 2, CL_READ, OP_SBC};   // USBC
+    case 0x1A: case 0x3A: case 0x5A: case 0x7A: case 0xDA: case 0xFA:
+      return OpInfo{AM_IMP, 2, CL_OTHER, OP_NOP};
+    case 0x80: case 0x82: case 0xC2: case 0xE2: return OpInfo{AM_IMM, 2, CL_READ, OP_NOPR};
+    case 0x04: case 0x44: case 0x64: return OpInfo{AM_ZP, 3, CL_READ, OP_NOPR};
+    case 0x14: case 0x34: case 0x54: case 0x74: case 0xD4: case 0xF4: return OpInfo{AM_ZPX, 4, CL_READ, OP_NOPR};
+    case 0x0C: return OpInfo{AM_ABS, 4, CL_READ, OP_NOPR};
+    case 0x1C: case 0x3C: case 0x5C: case 0x7C: case 0xDC: case 0xFC: return OpInfo{AM_ABX, 4, CL_READ, OP_NOPR};
+    case 0xA7: return OpInfo{AM_ZP, 3, CL_READ, OP_LAX};
+    case 0xB7: return OpInfo{AM_ZPY, 4, CL_READ, OP_LAX};
+    case 0xAF: return OpInfo{AM_ABS, 4, CL_READ, OP_LAX};
+    case 0xBF: return OpInfo{AM_ABY, 4, CL_READ, OP_LAX};
+    case 0xA3: return OpInfo{AM_INX, 6, CL_READ, OP_LAX};
+    case 0xB3: return OpInfo{AM_INY, 5, CL_READ, OP_LAX};
+    case 0x87: return OpInfo{AM_ZP, 3, CL_STORE, OP_SAX};
+    case 0x97: return OpInfo{AM_ZPY, 4, CL_STORE, OP_SAX};
+    case 0x8F: return OpInfo{AM_ABS, 4, CL_STORE, OP_SAX};
+    case 0x83: return OpInfo{AM_INX, 6, CL_STORE, OP_SAX};
     default: return OpInfo{AM_JAM, 1, CL_OTHER, OP_JAM};
   }
 }
@@ -164,7 +187,7 @@ __host__ __device__ constexpr bool reverse_needed(uint32_t op) {
          id == OP_ADC || id == OP_SBC || id == OP_STA || id == OP_STX || id == OP_STY || id == OP_ASL ||
          id == OP_ROL || id == OP_LSR || id == OP_ROR || id == OP_DEC || id == OP_INC || id == OP_TAX ||
          id == OP_TXA || id == OP_TAY || id == OP_TYA || id == OP_TSX || id == OP_PHA || id == OP_PHP ||
-         id == OP_PLA || id == OP_JSR || id == OP_BRK;
+         id == OP_PLA || id == OP_JSR || id == OP_BRK || id == OP_LAX || id == OP_SAX;
 }
 
 // Machine registers of one env (kept in registers inside a launch).

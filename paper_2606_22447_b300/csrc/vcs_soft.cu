@@ -232,8 +232,22 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
       scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, a.A);
       break;
     case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
+    case 0xEB:                                                      // USBC: SBC's alias
       scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, -a.A);
       break;
+    case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   // LAX: A = X = M
+      float g = a.A + a.X;
+      a.A = 0.f;
+      a.X = 0.f;
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      break;
+    }
+    case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
+      const float g = take_write(a, aram, aramc, E, cw, j, ref);
+      a.A += g;
+      a.X += g;
+      break;
+    }
     case 0x85: case 0x95: case 0x8D: case 0x9D: case 0x99: case 0x81: case 0x91:
       a.A += take_write(a, aram, aramc, E, cw, j, ref);
       break;

@@ -16,3 +16,101 @@ def rom4k(build, origin=0xF000, table=True):
     a.word(0xF000)
     a.word(0xF000)
     return bytes(a.resolve())
+
+
+# The paper's 38 extra opcode bytes, by addressing mode (raw bytes: the
+# assembler knows the documented opcodes only).
+EXTRA_IMP = (0x1A, 0x3A, 0x5A, 0x7A, 0xDA, 0xFA)
+EXTRA_IMM = (0x80, 0x82, 0x89, 0xC2, 0xE2, 0xEB)          # NOPs #imm and USBC #imm
+EXTRA_ZP = (0x04, 0x44, 0x64, 0xA7, 0x87)                 # NOP zp, LAX zp, SAX zp
+EXTRA_ZPXY = (0x14, 0x34, 0x54, 0x74, 0xD4, 0xF4, 0xB7, 0x97)   # NOP zp,X; LAX zp,Y; SAX zp,Y
+EXTRA_ABS = (0x0C, 0xAF, 0x8F)                            # NOP abs, LAX abs, SAX abs
+EXTRA_ABSXY = (0x1C, 0x3C, 0x5C, 0x7C, 0xDC, 0xFC, 0xBF)  # NOP abs,X; LAX abs,Y
+EXTRA_IND = (0xA3, 0xB3, 0x83)                            # LAX (zp,X), LAX (zp),Y, SAX (zp,X)
+
+
+def extra_ops_rom():
+    """A frame loop that runs all 38 extra opcode bytes on joystick-dependent
+    data each line and shows the results in the colour registers: LAX / SAX
+    on RAM and TIA addresses, USBC in binary and decimal mode, NOPs reading
+    RAM, INTIM and SWCHA (page-crossing abs,X included).  Index registers are
+    masked before indexed and indirect accesses so that every store lands in
+    RAM or a colour register."""
+    def build(a):
+        a.op("LDX", "imm", 0xFF)
+        a.op("TXS")
+        for k, target in enumerate((0x90, 0x94, 0x98, 0x9C, 0x90)):   # pointers $80.. and $88
+            a.op("LDA", "imm", target)
+            a.op("STA", "zp", 0x80 + 2 * k)
+            a.op("LDA", "imm", 0x00)
+            a.op("STA", "zp", 0x81 + 2 * k)
+        a.label("F")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "abs", 0x0280)     # joystick into $90
+        a.op("STA", "zp", 0x90)
+        a.op("LDA", "imm", 80)
+        a.op("STA", "zp", 0x8A)        # loop turns (about 2.5 lines each)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.byte(0xA7, 0x90)             # LAX $90
+        a.op("INX")
+        a.byte(0x87, 0x91)             # SAX $91
+        a.byte(0x87, 0x09)             # SAX COLUBK (a TIA write)
+        a.op("SEC")
+        a.byte(0xEB, 0x07)             # USBC #7 (binary)
+        a.op("STA", "zp", 0x90)
+        a.op("SED")
+        a.byte(0xEB, 0x15)             # USBC #$15 (decimal)
+        a.op("CLD")
+        a.op("STA", "zp", 0x08)
+        for op in EXTRA_IMP:
+            a.byte(op)
+        for op in EXTRA_IMM[:-1]:
+            a.byte(op, 0x5A)
+        a.byte(0x04, 0x90)
+        a.byte(0x44, 0x91)
+        a.byte(0x64, 0x92)
+        a.op("TXA")                    # X in {0, 2, 4, 6}
+        a.op("AND", "imm", 0x06)
+        a.op("TAX")
+        for op in EXTRA_ZPXY[:6]:
+            a.byte(op, 0x90)           # NOP $90,X
+        a.op("LDA", "zp", 0x91)        # Y in 0..31
+        a.op("AND", "imm", 0x1F)
+        a.op("TAY")
+        a.byte(0xB7, 0x8E)             # LAX $8E,Y
+        a.op("TXA")
+        a.op("AND", "imm", 0x06)
+        a.op("TAX")
+        a.byte(0x97, 0xC0)             # SAX $C0,Y
+        a.byte(0x0C, 0x84, 0x02)       # NOP INTIM
+        a.byte(0xAF, 0x80, 0x02)       # LAX SWCHA
+        a.op("TXA")
+        a.op("AND", "imm", 0x06)
+        a.op("TAX")
+        a.byte(0x8F, 0x94, 0x00)       # SAX $0094
+        a.op("LDX", "zp", 0x91)
+        for op in EXTRA_ABSXY[:6]:
+            a.byte(op, 0xF8, 0xFE)     # NOP $FEF8,X (crosses a page for X >= 8)
+        a.byte(0xBF, 0x10, 0xFE)       # LAX $FE10,Y
+        a.op("TXA")
+        a.op("AND", "imm", 0x06)
+        a.op("TAX")
+        a.byte(0xA3, 0x80)             # LAX ($80,X)
+        a.op("TXA")
+        a.op("AND", "imm", 0x06)
+        a.op("TAX")
+        a.byte(0xB3, 0x88)             # LAX ($88),Y
+        a.byte(0x83, 0x80)             # SAX ($80,X)
+        a.op("STA", "zp", 0x06)
+        a.op("STY", "zp", 0x1B)
+        a.op("DEC", "zp", 0x8A)
+        a.op("BEQ", "rel", "D")
+        a.op("JMP", "abs", "L")
+        a.label("D")
+        a.op("JMP", "abs", "F")
+    return rom4k(build)

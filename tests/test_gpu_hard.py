@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_2606_22447_b300 import synth
 from tests.gpu_util import assert_env_equal, gpu_rollout, make_batch, oracle_rollout, torch_cuda
-from tests.microrom import rom4k
+from tests.microrom import extra_ops_rom, rom4k
 
 pytestmark = pytest.mark.gpu
 
@@ -353,6 +353,48 @@ def test_code_fetched_through_the_bus():
     env_cart = np.arange(8) % 2
     acts = synth.actions(717, 8, 6)
     _check_all(roms, maps, env_cart, acts, 2)
+
+
+def _f8_nop_hotspot_rom():
+    """An unofficial NOP absolute read of $1FF8 / $1FF9 switches F8 banks."""
+    def bank(b):
+        a = synth.Asm(0xF000, 4096)
+        a.label("F")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("LDX", "imm", 100)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("INC", "zp", 0x80 + b)
+        a.op("LDA", "zp", 0x80 + b)
+        a.op("STA", "zp", 0x09 if b else 0x08)
+        a.op("DEX")
+        a.op("BNE", "rel", "L")
+        a.byte(0x0C, 0xF8 + (1 - b), 0xFF)   # NOP $FFF8 / $FFF9: switch to the other bank
+        a.op("JMP", "abs", "F")
+        a.at(0xFFA)
+        a.word(0xF000)
+        a.word(0xF000)
+        a.word(0xF000)
+        return bytes(a.resolve())
+    return bank(0) + bank(1)
+
+
+def test_extra_opcode_bytes():
+    """The paper's 38 extra opcode bytes (USBC, unofficial NOPs, LAX, SAX)
+    against the oracle, bit for bit, including an F8 bank switch by a NOP
+    read."""
+    roms = [extra_ops_rom(), _f8_nop_hotspot_rom()]
+    maps = [synth.MAPPER_4K, synth.MAPPER_F8]
+    env_cart = np.arange(10) % 2
+    acts = synth.actions(738, 10, 6)
+    _check_all(roms, maps, env_cart, acts, 2)
+    b = make_batch(roms, maps, env_cart)
+    _, _, st = gpu_rollout(b, acts, 2, screens=False)
+    assert not np.any(st & 2), "no slot may jam"
 
 
 def test_generated_carts_cover_the_instruction_set():

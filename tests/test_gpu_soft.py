@@ -189,3 +189,36 @@ def test_autograd_function_and_float_inputs():
         assert_grad_close(g_ram0[e], o_ram0, "grad_ram0 through autograd")
         assert_grad_close(g_u[:, e], o_u, "grad_u through autograd")
     assert_grad_close(g_rom, want_pc, "per-cart ROM gradient through autograd")
+
+
+def test_gradients_through_the_extra_opcode_bytes():
+    """LAX, SAX and USBC carry adjoints by their rules (LAX: both registers to
+    the operand; SAX: the cell to A and X; USBC: as SBC); the unofficial NOPs
+    carry none.  GPU gradients against the FP64 oracle on the extra-opcode
+    cart."""
+    from tests.microrom import extra_ops_rom
+    torch = torch_cuda()
+    rom = extra_ops_rom()
+    n_envs, n_steps, tau = 4, 3, 0.1
+    b = make_batch([rom], [synth.MAPPER_4K], [0] * n_envs)
+    wa = synth.actions(39, n_envs, 2)
+    gpu_rollout(b, wa, 1, screens=False)
+    acts = synth.actions(38, n_envs, n_steps)
+    u = synth.action_inputs(acts)
+    gr = synth.normal_f32(38, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(38, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, 8192), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u)
+    b.sync()
+    g_rom, g_ram0, g_u = g_rom.cpu().numpy(), g_ram0.cpu().numpy(), g_u.cpu().numpy()
+    for e in range(n_envs):
+        (o_rom, o_ram0, o_u), _, _ = _oracle_grads(rom, synth.MAPPER_4K, wa[:, e], u[:, e], 1, tau,
+                                                   gr[:, e], gs[:, e])
+        assert np.abs(o_ram0).max() > 0 and np.abs(o_rom).max() > 0
+        assert_grad_close(g_rom[e, :4096], o_rom, f"grad_rom env {e}")
+        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
+        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
