@@ -71,7 +71,11 @@ enum {
 typedef struct vcs_config {
   float alpha;              /* branch-gate sharpness (Eq. branch), default 6 */
   int32_t ystart;           /* first scanline of screen row 0, default 34 */
-  int32_t boot_noop_frames; /* NOOP frames run by vcs_reset, default 0 */
+  int32_t boot_noop_frames; /* boot: NOOP frames after each power-on, default 0
+                               (the paper's protocol: 60) */
+  int32_t boot_reset_frames;/* boot: then frames with the console RESET switch
+                               pressed (SWCHB bit 0 low), default 0 (the
+                               paper: 4) */
   int32_t envs_per_block;   /* 0 = automatic; else 8, 16, 32, 64 or 128 */
   int32_t segment_frames;   /* soft checkpoint interval in frames, default 64 */
   int32_t sched_policy;     /* which lanes of a warp execute each iteration:
@@ -134,10 +138,20 @@ vcs_status vcs_set_episodes(vcs_batch* b, const uint32_t* ep_len, int32_t n_epis
 
 /* Power-on state (A=X=Y=0, SP=$FD, P=$34, PC from the reset vector, RAM
  * and TIA registers zero, timer as written with 0 at T1024T, F8 bank 1),
- * then cfg.boot_noop_frames frames with the NOOP action (the paper boots
- * with NOOP frames, supplement settings table).
- * env_mask: device uint8[n_envs] (nonzero = reset) or NULL for all. */
+ * then the boot sequence of the paper's protocol (supplement, settings
+ * table): cfg.boot_noop_frames NOOP frames, cfg.boot_reset_frames frames with
+ * RESET pressed, then the env's start-NOOP count for its episode (below).
+ * Every power-on runs it: at creation, here, and at each episode auto-reset.
+ * env_mask: device uint8[n_envs] (nonzero = reset) or NULL for all (which
+ * also starts every env's episode count again). */
 vcs_status vcs_reset(vcs_batch* b, const uint8_t* env_mask, void* stream);
+
+/* Episode-start randomisation (the paper: 0-30 random NOOPs): counts is a
+ * host uint8[n_envs][n_per_env]; env e's k-th episode starts with
+ * counts[e][k mod n_per_env] NOOP frames after the boot frames.  The random
+ * draw is the caller's (the library draws nothing).  n_per_env = 0 removes
+ * the table (the default: no extra frames). */
+vcs_status vcs_set_start_noops(vcs_batch* b, const uint8_t* counts, int32_t n_per_env);
 
 /* One env-step for every env (the paper's conformance protocol, Section 5):
  * set each joystick from actions[e] (device uint8[n_envs], ALE action index

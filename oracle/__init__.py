@@ -73,6 +73,7 @@ def lib():
         L.ogrf_eval.argtypes = [vp, dp, dp, dp]
         L.ogrf_nodes.restype = C.c_int64
         L.ogrf_nodes.argtypes = [vp]
+        L.ovcs_set_switches.argtypes = [vp, C.c_uint8]
         L.ovcs_digest.restype = C.c_uint64
         L.ovcs_digest.argtypes = [u8p, u8p]
         L.ovcs_relaxed_read.restype = C.c_double
@@ -145,6 +146,19 @@ class Oracle:
 
     def reset(self):
         lib().ovcs_reset(self.h)
+
+    def boot(self, noop_frames: int, reset_frames: int, extra_noops: int = 0):
+        """The paper's boot protocol after a power-on (supplement, settings
+        table): NOOP frames, frames with the console RESET switch held, then
+        the episode's extra NOOP frames."""
+        for _ in range(noop_frames):
+            self.step(0, 1)
+        lib().ovcs_set_switches(self.h, 0x0A)
+        for _ in range(reset_frames):
+            self.step(0, 1)
+        lib().ovcs_set_switches(self.h, 0x0B)
+        for _ in range(extra_noops):
+            self.step(0, 1)
 
     def step(self, action: int, frame_skip: int = 1):
         ram = np.zeros(128, np.uint8)

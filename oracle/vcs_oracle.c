@@ -869,6 +869,8 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
   return s;
 }
 
+void ovcs_set_switches(ovcs* s, uint8_t swchb) { s->swchb = swchb; }
+
 void ovcs_free(ovcs* s) {
   if (!s) return;
   free(s->rom);

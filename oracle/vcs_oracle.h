@@ -55,6 +55,9 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart);
 void ovcs_free(ovcs* s);
 /* Power-on state (A7 of the design notes). */
 void ovcs_reset(ovcs* s);
+/* Console switches as SWCHB reads them (power-on: $0B = colour, difficulty
+ * B, RESET and SELECT released; $0A holds RESET down). */
+void ovcs_set_switches(ovcs* s, uint8_t swchb);
 /* One env-step: set the joystick from `action` (ALE index 0..17), run
  * `frame_skip` frames, copy RAM (128 B) and the last frame (210x160) out.
  * Returns a status bit set: 1 = a frame ended by the line cap, 2 = jammed. */

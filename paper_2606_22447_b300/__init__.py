@@ -102,6 +102,12 @@ class Batch:
     def _check(self, st):
         _lib.check(st, self.h)
 
+    def set_start_noops(self, counts):
+        """NOOP frames starting each episode: uint8 [n_envs][n_per_env]."""
+        c = np.ascontiguousarray(counts, dtype=np.uint8)
+        n = 0 if c.size == 0 else int(c.shape[1])
+        self._check(_lib.load().vcs_set_start_noops(self.h, c.ctypes.data_as(_lib.u8p), n))
+
     def reset(self, env_mask=None, stream=None):
         self._check(_lib.load().vcs_reset(self.h, _ptr(env_mask), _stream(stream)))
 

@@ -31,6 +31,7 @@ class LossWeights(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("alpha", C.c_float), ("ystart", C.c_int32), ("boot_noop_frames", C.c_int32),
+                ("boot_reset_frames", C.c_int32),
                 ("envs_per_block", C.c_int32), ("segment_frames", C.c_int32),
                 ("sched_policy", C.c_int32), ("sched_window", C.c_int32), ("steps_per_launch", C.c_int32),
                 ("threads_per_env", C.c_int32)]
@@ -75,6 +76,7 @@ SIGNATURES = {
     "vcs_autotune_cache_clear": (C.c_int, []),
     "vcs_rollout_host": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, vp]),
     "vcs_int_peak": (C.c_int, [C.POINTER(C.c_double), vp]),
+    "vcs_set_start_noops": (C.c_int, [vp, u8p, i32]),
 }
 
 _lib = None

@@ -63,6 +63,11 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.tpe = b->tpe;
+  p.boot_noop = b->cfg.boot_noop_frames;
+  p.boot_reset = b->cfg.boot_reset_frames;
+  p.start_noops = b->start_noops;
+  p.n_start = b->n_start;
+  p.boot_frames = (p.boot_noop + p.boot_reset > 0 || b->start_noops) ? 1 : 0;
   return p;
 }
 
@@ -127,6 +132,7 @@ static void free_batch(vcs_batch* b) {
   cudaFree(b->blocks);
   cudaFree(b->perm);
   cudaFree(b->ep_len);
+  cudaFree(b->start_noops);
   cudaFree(b->err);
   cudaFree(b->h_actions);
   cudaFree(b->h_ram);
@@ -151,6 +157,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->alpha = 6.0f;
   cfg->ystart = 34;
   cfg->boot_noop_frames = 0;
+  cfg->boot_reset_frames = 0;
   cfg->envs_per_block = 0;
   cfg->segment_frames = 64;
   cfg->sched_policy = 0;
@@ -203,7 +210,8 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     b->cfg = *cfg;
   else
     vcs_config_default(&b->cfg);
-  if (b->cfg.ystart < 0 || b->cfg.ystart > 400 || b->cfg.boot_noop_frames < 0 || b->cfg.segment_frames < 1) {
+  if (b->cfg.ystart < 0 || b->cfg.ystart > 400 || b->cfg.boot_noop_frames < 0 || b->cfg.boot_reset_frames < 0 ||
+      b->cfg.segment_frames < 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "config out of range (ystart 0..400, boot frames >= 0, segment >= 1)");
   }
@@ -294,7 +302,7 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   // power on every env (plus the configured boot frames)
   StepParams p = vcs_base_params(b);
   p.reset_all = 1;
-  p.n_steps = b->cfg.boot_noop_frames;
+  p.n_steps = 0;        // the launch powers on and boots; no env-step
   p.frame_skip = 1;
   vcs_status st = launch(b, p, nullptr);
   if (st == VCS_OK && (e = cudaDeviceSynchronize())) st = vcs_cuda_fail(b, e, "power-on");
@@ -322,12 +330,27 @@ vcs_status vcs_set_episodes(vcs_batch* b, const uint32_t* ep_len, int32_t n_epis
   return VCS_OK;
 }
 
+vcs_status vcs_set_start_noops(vcs_batch* b, const uint8_t* counts, int32_t n_per_env) {
+  if (!b) return VCS_ERR_ARG;
+  if (n_per_env < 0 || (n_per_env > 0 && !counts)) return vcs_fail(b, VCS_ERR_ARG, "bad start-noop table");
+  cudaFree(b->start_noops);
+  b->start_noops = nullptr;
+  b->n_start = 0;
+  if (n_per_env == 0) return VCS_OK;
+  const size_t bytes = (size_t)b->n_envs * n_per_env;
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->start_noops, bytes))) return vcs_cuda_fail(b, e, "start-noop table");
+  if ((e = cudaMemcpy(b->start_noops, counts, bytes, cudaMemcpyHostToDevice))) return vcs_cuda_fail(b, e, "start-noop table");
+  b->n_start = n_per_env;
+  return VCS_OK;
+}
+
 vcs_status vcs_reset(vcs_batch* b, const uint8_t* env_mask, void* stream) {
   if (!b) return VCS_ERR_ARG;
   StepParams p = vcs_base_params(b);
   p.reset_all = env_mask ? 0 : 1;
   p.reset_mask = env_mask;
-  p.n_steps = b->cfg.boot_noop_frames;
+  p.n_steps = 0;        // the launch powers on and boots; no env-step
   p.frame_skip = 1;
   vcs_status st = launch(b, p, stream);
   if (st != VCS_OK) return st;

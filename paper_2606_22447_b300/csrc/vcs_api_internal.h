@@ -26,6 +26,8 @@ struct vcs_batch {
   int32_t* perm = nullptr;
   uint32_t* ep_len = nullptr;
   int32_t n_episodes = 0;
+  uint8_t* start_noops = nullptr;  // [n_envs][n_start] NOOP frames starting each episode
+  int32_t n_start = 0;
   uint32_t sched_policy = 0;       // warp scheduling policy (see vcs_config)
   uint32_t sched_window = 4;       // time window for policy 1 (cycles)
   int32_t steps_per_launch = 0;    // vcs_rollout launch split (0 = one launch)

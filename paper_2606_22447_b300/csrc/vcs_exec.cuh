@@ -86,7 +86,7 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
   const uint32_t q = a & 0xF;
   const uint32_t vtia = q == 0xC ? r.inpt4 : (q == 0xD ? 0x80u : 0u);
   const uint32_t q3 = a & 3;
-  const uint32_t vio = q3 == 0 ? r.swcha : (q3 == 2 ? 0x0Bu : 0u);
+  const uint32_t vio = q3 == 0 ? r.swcha : (q3 == 2 ? r.swchb : 0u);
   const uint32_t k = r.cyc + (uint32_t)(idx + st.stall) - r.tw;
   const uint32_t vi = r.tv << r.tsh;
   const bool live = k <= vi;

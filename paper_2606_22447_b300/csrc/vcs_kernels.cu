@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
 
   Regs r;
   uint32_t epf = 0, epi = 0;
+  bool booting = false;
   if (active) {
     load_env(p.s, n, env, c, r);
     epf = p.s.epf[env];
@@ -79,6 +80,8 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
     if (p.reset_all || (p.reset_mask && p.reset_mask[env])) {
       power_on(c, r);
       epf = 0;
+      if (p.reset_all) epi = 0;
+      booting = true;
     }
     if (SOFT && p.ram0) {
       uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
@@ -100,6 +103,18 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   rd.gs = nullptr;
   rd.grow = nullptr;
   rd.gline = -1;
+  // the boot sequence of the envs this launch powers on (hard mode)
+  auto boot = [&](bool b) {
+    if constexpr (!SOFT) {
+      if (p.boot_frames && __any_sync(lanes, b)) {
+        const uint32_t extra =
+            (b && p.start_noops) ? p.start_noops[(size_t)env * p.n_start + epi % (uint32_t)p.n_start] : 0u;
+        boot_frames(c, r, rd, tape, b, (uint32_t)p.boot_noop, (uint32_t)p.boot_reset, extra, lanes, p.sched_policy,
+                    p.sched_window);
+      }
+    }
+  };
+  boot(booting);
   for (int t = 0; t < p.n_steps; t++) {
     if constexpr (SOFT) {
       if (t % p.seg_steps == 0) {
@@ -136,24 +151,28 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
       rd.out_u8 = (p.screen_out && active) ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
     }
     run_frames(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
-    if (!active) continue;
-    normalise_timer(r);
-    if (SOFT) {
-      if (p.ram_out_f) write_ram_f32(c, p.ram_out_f + ((size_t)t * n + env) * 128);
-    } else {
-      if (p.ram_out) write_ram(c, p.ram_out + ((size_t)t * n + env) * 128);
-    }
-    if (!SOFT && p.n_episodes > 0) {
-      epf += (uint32_t)p.frame_skip;
-      uint32_t len = p.ep_len[(size_t)env * p.n_episodes + (epi % (uint32_t)p.n_episodes)];
-      if (epf >= len) {
-        st.status |= kStDone;
-        power_on(c, r);
-        epf = 0;
-        epi++;
+    booting = false;
+    if (active) {
+      normalise_timer(r);
+      if (SOFT) {
+        if (p.ram_out_f) write_ram_f32(c, p.ram_out_f + ((size_t)t * n + env) * 128);
+      } else {
+        if (p.ram_out) write_ram(c, p.ram_out + ((size_t)t * n + env) * 128);
       }
+      if (!SOFT && p.n_episodes > 0) {
+        epf += (uint32_t)p.frame_skip;
+        uint32_t len = p.ep_len[(size_t)env * p.n_episodes + (epi % (uint32_t)p.n_episodes)];
+        if (epf >= len) {   // auto-reset: power on and boot before the next step
+          st.status |= kStDone;
+          power_on(c, r);
+          epf = 0;
+          epi++;
+          booting = true;
+        }
+      }
+      if (p.status_out && lead) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
     }
-    if (p.status_out && lead) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
+    boot(booting);
   }
   if (!active) return;
   if (!lead) return;

@@ -47,6 +47,10 @@ struct StepParams {
   int32_t reset_all;        // power on every env before stepping
   int32_t* err;             // device error word (nonzero after a failure)
   int32_t tpe;              // threads per env (1, 2, 4 or 8)
+  int32_t boot_frames;      // nonzero if powered-on envs run a boot sequence
+  int32_t boot_noop, boot_reset;   // boot: NOOP frames, then frames with RESET pressed
+  const uint8_t* start_noops;      // [n_envs][n_start] NOOP frames starting each episode, or null
+  int32_t n_start;
   uint32_t sched_policy;    // warp scheduling: 0 program order, 1 emulated time (run_frames)
   uint32_t sched_window;    // time window in cycles for policy 1
   // soft forward only

@@ -141,6 +141,16 @@ def episode_lengths(seed: int, n_envs: int, n_episodes: int, mean_frames: float 
     return np.clip(length, 1, 2 ** 31).astype(np.uint32)
 
 
+def start_noops(seed: int, n_envs: int, n_episodes: int, most: int = 30) -> np.ndarray:
+    """uint8 [n_envs][n_episodes] NOOP frames starting each episode, uniform in
+    0..most (the paper's episode-start randomisation)."""
+    env = np.arange(n_envs, dtype=np.uint64)[:, None]
+    ep = np.arange(n_episodes, dtype=np.uint64)[None, :]
+    with np.errstate(over="ignore"):
+        k = _np_mix64(np_key3(seed ^ 0x5707, env, ep) + np.uint64(GAMMA))
+    return (k % np.uint64(most + 1)).astype(np.uint8)
+
+
 def normal_f32(seed: int, shape, stream: int = 0) -> np.ndarray:
     """Seeded standard normal float32 array (Box-Muller over splitmix64)."""
     n = int(np.prod(shape))

@@ -24,10 +24,19 @@ def gpu_rollout(batch, actions, frame_skip, screens=True):
     return ram.cpu().numpy(), (scr.cpu().numpy() if screens else None), st.cpu().numpy()
 
 
-def oracle_rollout(rom, mapper, actions, frame_skip, ystart=34, ep_len=None, screens=True):
+def oracle_rollout(rom, mapper, actions, frame_skip, ystart=34, ep_len=None, screens=True, boot=None,
+                   start=None):
     """One env through the oracle; ep_len (frames per episode, cyclic)
-    reproduces the library's auto-reset at step ends."""
+    reproduces the library's auto-reset at step ends; boot = (noop frames,
+    reset frames) and start (this env's start-NOOP counts, cyclic) reproduce
+    the boot sequence after every power-on."""
     o = oracle.Oracle(rom, mapper, ystart)
+
+    def do_boot(episode):
+        if boot is not None or start is not None:
+            nb, rb = boot if boot is not None else (0, 0)
+            o.boot(nb, rb, 0 if start is None else int(start[episode % len(start)]))
+    do_boot(0)
     n = len(actions)
     rams = np.zeros((n, 128), np.uint8)
     scrs = np.zeros((n, 210, 160), np.uint8) if screens else None
@@ -44,6 +53,7 @@ def oracle_rollout(rom, mapper, actions, frame_skip, ystart=34, ep_len=None, scr
                 st |= 4
                 o.reset()
                 epf, epi = 0, epi + 1
+                do_boot(epi)
         status[t] = st
     return rams, scrs, status
 

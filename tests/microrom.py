@@ -114,3 +114,42 @@ def extra_ops_rom():
         a.label("D")
         a.op("JMP", "abs", "F")
     return rom4k(build)
+
+
+def switches_rom():
+    """Counts frames in $80, keeps the AND of every SWCHB read in $81 (bit 0
+    clears once RESET has been seen) and the last SWCHB in $82, and draws
+    the frame count in the background colour."""
+    def build(a):
+        a.op("SEI")
+        a.op("CLD")
+        a.op("LDX", "imm", 0xFF)
+        a.op("TXS")
+        a.op("LDA", "imm", 0xFF)
+        a.op("STA", "zp", 0x81)
+        a.label("F")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("INC", "zp", 0x80)
+        a.op("LDA", "abs", 0x0282)
+        a.op("AND", "zp", 0x81)
+        a.op("STA", "zp", 0x81)
+        a.op("LDA", "abs", 0x0282)
+        a.op("STA", "zp", 0x82)
+        a.op("LDA", "abs", 0x0280)
+        a.op("EOR", "zp", 0x80)
+        a.op("STA", "zp", 0x83)
+        a.op("LDY", "imm", 100)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("LDA", "zp", 0x80)
+        a.op("STA", "zp", 0x09)
+        a.op("LDA", "zp", 0x83)
+        a.op("STA", "zp", 0x08)
+        a.op("DEY")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "F")
+    return rom4k(build)

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_2606_22447_b300 import synth
 from tests.gpu_util import assert_env_equal, gpu_rollout, make_batch, oracle_rollout, torch_cuda
-from tests.microrom import extra_ops_rom, rom4k
+from tests.microrom import extra_ops_rom, rom4k, switches_rom
 
 pytestmark = pytest.mark.gpu
 
@@ -395,6 +395,44 @@ def test_extra_opcode_bytes():
     b = make_batch(roms, maps, env_cart)
     _, _, st = gpu_rollout(b, acts, 2, screens=False)
     assert not np.any(st & 2), "no slot may jam"
+
+
+def test_boot_protocol_and_episode_starts():
+    """The paper's protocol on the GPU: 60 NOOP + 4 RESET boot frames after
+    every power-on (creation, auto-reset, a masked reset), then each
+    episode's own number of random start NOOPs; bit for bit against the
+    oracle running the same sequence."""
+    torch = torch_cuda()
+    roms = [switches_rom(), synth.generate_cart(818, 1, synth.MAPPER_F8)]
+    maps = [synth.MAPPER_4K, synth.MAPPER_F8]
+    n = 12
+    env_cart = np.arange(n) % 2
+    acts = synth.actions(818, n, 12)
+    ep = synth.episode_lengths(818, n, 4, mean_frames=10.0)
+    starts = synth.start_noops(818, n, 4)
+    b = make_batch(roms, maps, env_cart, boot_noop_frames=60, boot_reset_frames=4)
+    b.set_start_noops(starts)
+    b.reset()            # boot again, now with the start-noop table
+    b.set_episodes(ep)
+    ram, scr, st = gpu_rollout(b, acts, 2)
+    assert np.any(st & 4), "some episodes must end inside the rollout"
+    for e in range(n):
+        c = int(env_cart[e])
+        r2, s2, st2 = oracle_rollout(roms[c], maps[c], acts[:, e], 2, ep_len=ep[e], boot=(60, 4), start=starts[e])
+        assert_env_equal(e, ram[:, e], r2, "RAM")
+        assert_env_equal(e, scr[:, e], s2, "screen")
+        assert_env_equal(e, st[:, e], st2, "status")
+    # a masked reset powers on and boots env 0 alone, with the start count of
+    # its current episode (a masked reset keeps the episode count)
+    epi0 = int(np.count_nonzero(st[:, 0] & 4))
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    mask[0] = 1
+    b.reset(mask)
+    ram2, _, _ = gpu_rollout(b, acts[:1], 2, screens=False)
+    o = oracle.Oracle(roms[0], maps[0])
+    o.boot(60, 4, int(starts[0][epi0 % 4]))
+    r3, _, _ = o.step(int(acts[0, 0]), 2)
+    assert np.array_equal(ram2[0, 0], r3)
 
 
 def test_generated_carts_cover_the_instruction_set():

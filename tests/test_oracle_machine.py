@@ -315,3 +315,22 @@ def test_stored_bench_counts_are_current():
     import make_bench_counts
     stored = json.load(open(os.path.join(here, "bench_counts.json")))
     assert stored == make_bench_counts.counts()
+
+
+def test_boot_protocol_frames_and_reset_switch():
+    """The boot protocol (60 NOOP + 4 RESET frames, then the episode's extra
+    NOOPs) as the cart sees it: the frame counter advances by the number of
+    boot frames, SWCHB reads $0A exactly during the RESET frames and $0B
+    otherwise."""
+    from paper_2606_22447_b300 import synth
+    from tests.microrom import switches_rom
+    o = oracle.Oracle(switches_rom(), synth.MAPPER_4K)
+    o.boot(60, 4, 7)
+    ram = o.ram()
+    # the power-on frame ends at the cart's first VSYNC, before its first
+    # increment; every later boot frame adds one
+    assert ram[0x00] == 60 + 4 + 7 - 1
+    assert ram[0x01] == 0x0A and ram[0x02] == 0x0B      # RESET was seen, and released again
+    o2 = oracle.Oracle(switches_rom(), synth.MAPPER_4K)
+    o2.boot(60, 0, 0)
+    assert o2.ram()[0x00] == 60 - 1 and o2.ram()[0x01] == 0x0B   # no RESET frames: never pressed
