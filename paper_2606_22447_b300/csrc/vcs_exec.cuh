@@ -84,9 +84,9 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
   const uint32_t vrom = c.rom[(r.bank << 12) | (a & 0xFFF)];
   const uint32_t vram = ram_rd(c, a);
   const uint32_t q = a & 0xF;
-  const uint32_t vtia = q == 0xC ? r.inpt4 : (q == 0xD ? 0x80u : 0u);
+  const uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
   const uint32_t q3 = a & 3;
-  const uint32_t vio = q3 == 0 ? r.swcha : (q3 == 2 ? r.swchb : 0u);
+  const uint32_t vio = q3 == 0 ? r.swcha : (q3 == 2 ? 0x0Bu ^ (r.inpt4 >> 8) : 0u);
   const uint32_t k = r.cyc + (uint32_t)(idx + st.stall) - r.tw;
   const uint32_t vi = r.tv << r.tsh;
   const bool live = k <= vi;
@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
 __device__ __forceinline__ uint32_t zp_read(const Ctx& c, const Regs& r, uint32_t a) {
   const uint32_t vram = ram_rd(c, a);
   const uint32_t q = a & 0xF;
-  const uint32_t vtia = q == 0xC ? r.inpt4 : (q == 0xD ? 0x80u : 0u);
+  const uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
   return (a & 0x80) ? vram : vtia;
 }
 
@@ -208,14 +208,15 @@ constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8)
                               (3u << 14) | (3u << 16) | (2u << 18) | (2u << 20) | (2u << 22) | (3u << 24) |
                               (1u << 26);
 
-// The implemented opcodes: the 151 documented ones and the paper's 38 extra
-// bytes (op_info gives each one's mode, cycles and operation); every other
-// byte jams the CPU.
-#define VCS_IMPLEMENTED_OPS(X) \
-  X(0xEB) X(0x1A) X(0x3A) X(0x5A) X(0x7A) X(0xDA) X(0xFA) X(0x80) X(0x82) X(0x89) X(0xC2) X(0xE2) \
-  X(0x04) X(0x44) X(0x64) X(0x14) X(0x34) X(0x54) X(0x74) X(0xD4) X(0xF4) X(0x0C) X(0x1C) X(0x3C) \
-  X(0x5C) X(0x7C) X(0xDC) X(0xFC) X(0xA7) X(0xB7) X(0xAF) X(0xBF) X(0xA3) X(0xB3) X(0x87) X(0x97) \
-  X(0x8F) X(0x83) \
+// The implemented opcodes (op_info gives each one's mode, cycles and
+// operation): the 151 documented ones, dispatched by the main switch, and
+// the paper's 38 extra bytes, dispatched on the cold path (real programs
+// seldom use them, and keeping their handlers out of the main switch keeps
+// its code as compact as before).  Every other byte jams the CPU.
+#define VCS_LAX_SAX_OPS(X) \
+  X(0xA7) X(0xB7) X(0xAF) X(0xBF) X(0xA3) X(0xB3) X(0x87) X(0x97) X(0x8F) X(0x83)
+
+#define VCS_DOCUMENTED_OPS(X) \
   X(0x00) X(0x01) X(0x05) X(0x06) X(0x08) X(0x09) X(0x0A) X(0x0D) X(0x0E) X(0x10) X(0x11) X(0x15) \
   X(0x16) X(0x18) X(0x19) X(0x1D) X(0x1E) X(0x20) X(0x21) X(0x24) X(0x25) X(0x26) X(0x28) X(0x29) \
   X(0x2A) X(0x2C) X(0x2D) X(0x2E) X(0x30) X(0x31) X(0x35) X(0x36) X(0x38) X(0x39) X(0x3D) X(0x3E) \
@@ -488,8 +489,7 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
     switch (sel) {
 #define VCS_CASE(x) \
   case x: exec_op<x>(c, r, st, opaddr, b1, b2, p); break;
-      VCS_IMPLEMENTED_OPS(VCS_CASE)
-#undef VCS_CASE
+      VCS_DOCUMENTED_OPS(VCS_CASE)
       case 0x101: {   // fetch through the bus, then dispatch on what was read
         op = bus_read(c, r, st, opaddr, 1);
         const uint32_t len = (kModeLen >> (2 * (c.dt->mode_cyc[op] & 15))) & 3;
@@ -498,14 +498,30 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
         sel = op;
         continue;
       }
-      default:   // an undocumented opcode jams the CPU after its fetch; a jammed CPU idles to the next line
-        p.n = r.jam ? 76u - (uint32_t)r.fc % 76u : 1u;
-        r.PC = r.jam ? r.PC : (opaddr + 1) & 0xFFFF;
-        r.jam = 1;
-        p.nw = 0;
-        p.rec = false;
-        p.seq = false;
+      default:
+        switch (sel) {   // the paper's extra bytes (equal semantics share a handler); anything else jams
+          case 0xEB: exec_op<0xE9>(c, r, st, opaddr, b1, b2, p); break;   // USBC = SBC #imm
+          case 0x1A: case 0x3A: case 0x5A: case 0x7A: case 0xDA: case 0xFA:
+            exec_op<0xEA>(c, r, st, opaddr, b1, b2, p); break;
+          case 0x80: case 0x82: case 0x89: case 0xC2: case 0xE2: exec_op<0x80>(c, r, st, opaddr, b1, b2, p); break;
+          case 0x04: case 0x44: case 0x64: exec_op<0x04>(c, r, st, opaddr, b1, b2, p); break;
+          case 0x14: case 0x34: case 0x54: case 0x74: case 0xD4: case 0xF4:
+            exec_op<0x14>(c, r, st, opaddr, b1, b2, p); break;
+          case 0x0C: exec_op<0x0C>(c, r, st, opaddr, b1, b2, p); break;
+          case 0x1C: case 0x3C: case 0x5C: case 0x7C: case 0xDC: case 0xFC:
+            exec_op<0x1C>(c, r, st, opaddr, b1, b2, p); break;
+          VCS_LAX_SAX_OPS(VCS_CASE)
+          default:   // the CPU jams after the fetch; a jammed CPU idles to the next line
+            p.n = r.jam ? 76u - (uint32_t)r.fc % 76u : 1u;
+            r.PC = r.jam ? r.PC : (opaddr + 1) & 0xFFFF;
+            r.jam = 1;
+            p.nw = 0;
+            p.rec = false;
+            p.seq = false;
+            break;
+        }
         break;
+#undef VCS_CASE
     }
     break;
   }

@@ -48,7 +48,7 @@ __device__ __forceinline__ uint32_t round_byte(float v) {
 // forward: joystick bits come from rounded float inputs, outputs are float,
 // the RAM may be overridden from float values first, and the full state is
 // checkpointed at the start of every segment of seg_steps steps.
-template <bool SOFT, int T>
+template <bool SOFT, int T, bool BOOT>
 __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   // T threads per env (a compile-time constant, so T = 1 carries no replica
@@ -103,55 +103,81 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   rd.gs = nullptr;
   rd.grow = nullptr;
   rd.gline = -1;
-  // the boot sequence of the envs this launch powers on (hard mode)
-  auto boot = [&](bool b) {
-    if constexpr (!SOFT) {
-      if (p.boot_frames && __any_sync(lanes, b)) {
-        const uint32_t extra =
-            (b && p.start_noops) ? p.start_noops[(size_t)env * p.n_start + epi % (uint32_t)p.n_start] : 0u;
-        boot_frames(c, r, rd, tape, b, (uint32_t)p.boot_noop, (uint32_t)p.boot_reset, extra, lanes, p.sched_policy,
-                    p.sched_window);
-      }
-    }
+  // One loop, one frame-loop call site (the interpreter is inlined once):
+  // each turn is either a boot frame for the lanes that just powered on
+  // (hard mode: n_noop NOOP frames, n_reset frames with RESET pressed, then
+  // the episode's start NOOPs), with the other lanes idle, or an env-step.
+  const uint32_t n_noop = (uint32_t)p.boot_noop, n_reset = (uint32_t)p.boot_reset;
+  auto boot_len = [&](bool b) -> uint32_t {
+    if (!BOOT || !b) return 0u;
+    const uint32_t extra = p.start_noops ? p.start_noops[(size_t)env * p.n_start + epi % (uint32_t)p.n_start] : 0u;
+    return n_noop + n_reset + extra;
   };
-  boot(booting);
-  for (int t = 0; t < p.n_steps; t++) {
-    if constexpr (SOFT) {
-      if (t % p.seg_steps == 0) {
-        const int seg = t / p.seg_steps;
-        if (seg > 0 && active && lead) {
-          atomicMax(p.seg_counts + 2 * (seg - 1), tape.n);
-          atomicMax(p.seg_counts + 2 * (seg - 1) + 1, tape.ncw);
-        }
-        tape.n = tape.ncw = 0;
-        if (active && lead) store_env(soa_at(p.ckpt + (size_t)seg * kStateWords * n, n), n, env, c, r);
-      }
-    }
-    uint32_t bits = 0;
-    if (SOFT) {
-      if (active) {
-        const float* u = p.u + ((size_t)t * n + env) * 5;
-        bits = (u[0] >= 0.5f ? 1u : 0u) | (u[1] >= 0.5f ? 2u : 0u) | (u[2] >= 0.5f ? 4u : 0u) |
-               (u[3] >= 0.5f ? 8u : 0u) | (u[4] >= 0.5f ? 16u : 0u);
-        if (lead) p.act_bits[(size_t)t * n + env] = (uint8_t)bits;
-      }
-      set_input_bits(r, bits);
-    } else {
-      set_inputs(r, (p.actions && active) ? p.actions[(size_t)t * n + env] : 0u);
-    }
+  uint32_t boot_left = boot_len(booting), boot_f = 0;
+  int t = 0;
+  while (true) {
+    const bool boot_turn = BOOT && __any_sync(lanes, boot_left > 0);
+    if (!boot_turn && t >= p.n_steps) break;
     Step st;
-    st.frame_skip = p.frame_skip;
     st.status = 0;
-    if (SOFT) {
-      st.want_screen = p.screen_out_f != nullptr;
-      rd.out_f32 = (p.screen_out_f && active)
-                       ? p.screen_out_f + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+    bool run_active;
+    if (boot_turn) {
+      run_active = boot_left > 0;
+      if (run_active) {
+        set_input_bits(r, 0);
+        r.inpt4 |= (boot_f >= n_noop && boot_f < n_noop + n_reset) ? 0x100u : 0u;   // RESET held
+      }
+      st.frame_skip = 1;
+      st.want_screen = false;
+      rd.out_u8 = nullptr;
+      rd.out_f32 = nullptr;
     } else {
-      st.want_screen = p.screen_out != nullptr;
-      rd.out_u8 = (p.screen_out && active) ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+      if constexpr (SOFT) {
+        if (t % p.seg_steps == 0) {
+          const int seg = t / p.seg_steps;
+          if (seg > 0 && active && lead) {
+            atomicMax(p.seg_counts + 2 * (seg - 1), tape.n);
+            atomicMax(p.seg_counts + 2 * (seg - 1) + 1, tape.ncw);
+          }
+          tape.n = tape.ncw = 0;
+          if (active && lead) store_env(soa_at(p.ckpt + (size_t)seg * kStateWords * n, n), n, env, c, r);
+        }
+      }
+      uint32_t bits = 0;
+      if (SOFT) {
+        if (active) {
+          const float* u = p.u + ((size_t)t * n + env) * 5;
+          bits = (u[0] >= 0.5f ? 1u : 0u) | (u[1] >= 0.5f ? 2u : 0u) | (u[2] >= 0.5f ? 4u : 0u) |
+                 (u[3] >= 0.5f ? 8u : 0u) | (u[4] >= 0.5f ? 16u : 0u);
+          if (lead) p.act_bits[(size_t)t * n + env] = (uint8_t)bits;
+        }
+        set_input_bits(r, bits);
+      } else {
+        set_inputs(r, (p.actions && active) ? p.actions[(size_t)t * n + env] : 0u);
+      }
+      st.frame_skip = p.frame_skip;
+      if (SOFT) {
+        st.want_screen = p.screen_out_f != nullptr;
+        rd.out_f32 = (p.screen_out_f && active)
+                         ? p.screen_out_f + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+      } else {
+        st.want_screen = p.screen_out != nullptr;
+        rd.out_u8 = (p.screen_out && active) ? p.screen_out + ((size_t)t * n + env) * (kScreenH * kScreenW) : nullptr;
+      }
+      run_active = active;
     }
-    run_frames(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
-    booting = false;
+    run_frames(c, r, rd, st, tape, run_active, lanes, p.sched_policy, p.sched_window);
+    if (boot_turn) {
+      if (boot_left > 0) {
+        boot_left--;
+        boot_f++;
+        if (boot_left == 0) {
+          r.inpt4 &= 0xFF;
+          normalise_timer(r);
+        }
+      }
+      continue;
+    }
     if (active) {
       normalise_timer(r);
       if (SOFT) {
@@ -162,17 +188,18 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
       if (!SOFT && p.n_episodes > 0) {
         epf += (uint32_t)p.frame_skip;
         uint32_t len = p.ep_len[(size_t)env * p.n_episodes + (epi % (uint32_t)p.n_episodes)];
-        if (epf >= len) {   // auto-reset: power on and boot before the next step
+        if (epf >= len) {   // auto-reset: power on, boot before the next step
           st.status |= kStDone;
           power_on(c, r);
           epf = 0;
           epi++;
-          booting = true;
+          boot_left = boot_len(true);
+          boot_f = 0;
         }
       }
       if (p.status_out && lead) p.status_out[(size_t)t * n + env] = (uint8_t)st.status;
     }
-    boot(booting);
+    t++;
   }
   if (!active) return;
   if (!lead) return;
@@ -269,11 +296,18 @@ static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   const dim3 grid(n_blocks), block(E * p.tpe);
   const size_t smem = step_smem_bytes(E);
   cudaStream_t s = (cudaStream_t)stream;
-  switch (p.tpe) {
-    case 1: k_run<SOFT, 1><<<grid, block, smem, s>>>(p); break;
-    case 2: k_run<SOFT, 2><<<grid, block, smem, s>>>(p); break;
-    case 4: k_run<SOFT, 4><<<grid, block, smem, s>>>(p); break;
-    case 8: k_run<SOFT, 8><<<grid, block, smem, s>>>(p); break;
+  // the boot sequence exists in the hard step kernel only when a batch asks
+  // for it, so that default launches carry none of its code
+  const bool boot = !SOFT && p.boot_frames;
+  switch (p.tpe * 2 + (boot ? 1 : 0)) {
+    case 2: k_run<SOFT, 1, false><<<grid, block, smem, s>>>(p); break;
+    case 4: k_run<SOFT, 2, false><<<grid, block, smem, s>>>(p); break;
+    case 8: k_run<SOFT, 4, false><<<grid, block, smem, s>>>(p); break;
+    case 16: k_run<SOFT, 8, false><<<grid, block, smem, s>>>(p); break;
+    case 3: k_run<false, 1, true><<<grid, block, smem, s>>>(p); break;
+    case 5: k_run<false, 2, true><<<grid, block, smem, s>>>(p); break;
+    case 9: k_run<false, 4, true><<<grid, block, smem, s>>>(p); break;
+    case 17: k_run<false, 8, true><<<grid, block, smem, s>>>(p); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

@@ -202,7 +202,9 @@ struct Regs {
   uint32_t tw, tv, tsh;      // timer: write cycle, value, log2 interval
   uint32_t col0, colpf, colbk, ctrl, pf0, pf1, pf2, grp0, hmp0, pos, vblank, vsync;
   int32_t hml;               // scanline of the last early HMOVE (-1 none)
-  uint32_t swcha, swchb, inpt4;
+  uint32_t swcha;
+  uint32_t inpt4;            // INPT4 in bits 0-7; bit 8 holds the console RESET switch down
+                             // (SWCHB then reads $0A instead of $0B)
   uint32_t intim_live;       // the last INTIM read came before underflow
 };
 

@@ -107,7 +107,6 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
   v = s.t2[e];
   r.hmp0 = v & 0xFF; r.pos = (v >> 8) & 0xFF; r.vblank = (v >> 16) & 0xFF; r.vsync = v >> 24;
   r.hml = (int32_t)s.t3[e];
-  r.swchb = 0x0B;   // console switches: colour, difficulty B, RESET and SELECT released
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
   for (int i = 0; i < 32; i++) w[i * c.E] = s.ram[(size_t)i * n + e];
   for (uint32_t q = c.rank; q < 10; q += c.T)
@@ -146,7 +145,6 @@ __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.col0 = r.colpf = r.colbk = r.ctrl = r.pf0 = r.pf1 = r.pf2 = r.grp0 = r.hmp0 = 0;
   r.pos = 0; r.vblank = 0; r.vsync = 0;
   r.hml = -1;
-  r.swchb = 0x0B;
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
   for (int i = 0; i < 32; i++) w[i * c.E] = 0;
   r.PC = c.rom[(r.bank << 12) | 0xFFC] | ((uint32_t)c.rom[(r.bank << 12) | 0xFFD] << 8);
@@ -173,7 +171,7 @@ __device__ __forceinline__ uint32_t action_bits(uint32_t action) {
 __device__ __forceinline__ void set_input_bits(Regs& r, uint32_t b) {
   // SWCHA player-0 nibble, active low: bit7 right, bit6 left, bit5 down, bit4 up
   r.swcha = 0xFFu - (((b & 1) << 7) | (((b >> 1) & 1) << 6) | (((b >> 2) & 1) << 5) | (((b >> 3) & 1) << 4));
-  r.inpt4 = (b & 0x10) ? 0x00u : 0x80u;
+  r.inpt4 = (b & 0x10) ? 0x00u : 0x80u;   // and the RESET switch released
 }
 
 __device__ __forceinline__ void set_inputs(Regs& r, uint32_t action) { set_input_bits(r, action_bits(action)); }
@@ -255,32 +253,6 @@ __device__ __forceinline__ uint32_t warp_lanes(int E) {
 __device__ __forceinline__ void normalise_timer(Regs& r) {
   uint32_t k = r.cyc - r.tw, vi = r.tv << r.tsh;
   if (k > vi + 512u) r.tw += ((k - vi - 256u) & ~255u);
-}
-
-// Boot sequence of the lanes that just powered on (`booting`): n_noop NOOP
-// frames, n_reset frames with the console RESET switch pressed (SWCHB bit 0
-// low), then `extra` NOOP frames (the episode's random start).  Every lane of
-// the warp takes part, since the frame loop schedules lanes with warp
-// reductions; lanes not booting stay idle.  Screens are not drawn.
-template <class Tape>
-__device__ __forceinline__ void boot_frames(const Ctx& c, Regs& r, Render& rd, Tape& tape, bool booting,
-                                            uint32_t n_noop, uint32_t n_reset, uint32_t extra, uint32_t lanes,
-                                            uint32_t policy, uint32_t window) {
-  const uint32_t total = booting ? n_noop + n_reset + extra : 0u;
-  const uint32_t most = __reduce_max_sync(lanes, total);
-  if (booting) set_input_bits(r, 0);
-  for (uint32_t f = 0; f < most; f++) {
-    if (booting) r.swchb = (f >= n_noop && f < n_noop + n_reset) ? 0x0Au : 0x0Bu;
-    Step st;
-    st.frame_skip = 1;
-    st.status = 0;
-    st.want_screen = false;
-    run_frames(c, r, rd, st, tape, f < total, lanes, policy, window);
-  }
-  if (booting) {
-    r.swchb = 0x0B;
-    normalise_timer(r);
-  }
 }
 
 __device__ __forceinline__ void write_ram_f32(const Ctx& c, float* dst) {
