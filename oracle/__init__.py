@@ -74,6 +74,7 @@ def lib():
         L.ogrf_nodes.restype = C.c_int64
         L.ogrf_nodes.argtypes = [vp]
         L.ovcs_set_switches.argtypes = [vp, C.c_uint8]
+        L.ovcs_set_sampler.argtypes = [vp, C.c_int]
         L.ovcs_digest.restype = C.c_uint64
         L.ovcs_digest.argtypes = [u8p, u8p]
         L.ovcs_relaxed_read.restype = C.c_double
@@ -159,6 +160,11 @@ class Oracle:
         lib().ovcs_set_switches(self.h, 0x0B)
         for _ in range(extra_noops):
             self.step(0, 1)
+
+    def set_sampler(self, on: bool):
+        """Switch the differentiable position sampler (Section 3) on or off for
+        the soft rollouts that follow."""
+        lib().ovcs_set_sampler(self.h, 1 if on else 0)
 
     def step(self, action: int, frame_skip: int = 1):
         ram = np.zeros(128, np.uint8)

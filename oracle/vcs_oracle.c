@@ -32,6 +32,10 @@
  *  are executed; every other undocumented opcode jams the CPU: from then on
  *  each instruction slot
  *  idles to the next line start, so the frame ends by the 512-line cap.
+ *  With the position sampler on (ovcs_set_sampler), soft rollouts also carry
+ *  the deviation of player 0's position: zero at each RESP0, minus a
+ *  sixteenth of HMP0's deviation added at each HMOVE, and its pixels take the
+ *  slope of the triangular coverage kernel (sampler_slope).
  */
 #include "vcs_oracle.h"
 
@@ -111,6 +115,8 @@ struct ovcs {
   /* soft mode */
   ogrf* g;
   int32_t nA, nX, nY, nV, nC[3], nRAM[128];
+  int32_t nPos, nHM;       /* deviations of the P0 position and of HMP0 (sampler) */
+  int sampler;             /* 1: the differentiable position sampler is on */
   int32_t u_leaf;
   const double* gs_all;   /* grad_screen for all steps (or NULL) */
   const double* gs;       /* grad_screen of the frame being rendered */
@@ -208,6 +214,29 @@ static int p0_bit(const ovcs* s, int x) {
   return d < 8 ? (s->grp0 >> (7 - d)) & 1 : 0;
 }
 
+/* Differentiable position sampler (Section 3, the sub-pixel bilinear kernel
+ * over sprite position): the player's coverage of column x relaxed with a
+ * triangular kernel, cov(x) = sum_k b_k tri(x - pos - k).  Its derivative
+ * with respect to pos at the integer hard point, taken symmetrically, is
+ * (b(d - 1) - b(d + 1)) / 2 with d = x - pos (mod 160), so
+ * d pixel / d pos = (C_P0 - C_under) (b(d - 1) - b(d + 1)) / 2, where
+ * C_under is the colour the pixel has without the player.  Zero where the
+ * playfield has priority over a playfield pixel (the player is hidden
+ * there), and on blanked pixels (the caller skips those). */
+static int p0_bit_at(const ovcs* s, int d) {
+  d = ((d % 160) + 160) % 160;
+  return d < 8 ? (s->grp0 >> (7 - d)) & 1 : 0;
+}
+static double sampler_slope(const ovcs* s, int x) {
+  int pf = pf_bit(s, x);
+  if ((s->ctrlpf & 4) && pf) return 0.0;
+  int d = x - s->p0pos;
+  int db = p0_bit_at(s, d - 1) - p0_bit_at(s, d + 1);
+  if (!db) return 0.0;
+  int under = (pf ? s->colupf : s->colubk) & 0xFE;
+  return 0.5 * (double)db * (double)((s->colup0 & 0xFE) - under);
+}
+
 /* Pixel at visible column x of the current scanline; *owner = 0 (P0),
  * 1 (PF), 2 (BK) or -1 (blanked). */
 static uint8_t pixel(const ovcs* s, int x, int* owner) {
@@ -232,6 +261,7 @@ static void tia_clock(ovcs* s) {
       if (s->g && s->gs && owner >= 0) {
         double w = s->gs[row * SCR_W + x];
         if (s->nC[owner]) s->g->seed[s->nC[owner]] += w;
+        if (s->sampler && s->nPos) s->g->seed[s->nPos] += w * sampler_slope(s, x);
       }
     }
   }
@@ -255,16 +285,22 @@ static void tia_write(ovcs* s, int reg, val x) {
     case 0x0D: s->pf0 = v; break;
     case 0x0E: s->pf1 = v; break;
     case 0x0F: s->pf2 = v; break;
-    case 0x10: s->p0pos = s->hclk < 68 ? 3 : (s->hclk - 68 + 5) % 160; break;
+    case 0x10:   /* RESP0: a position from strobe timing carries no deviation */
+      s->p0pos = s->hclk < 68 ? 3 : (s->hclk - 68 + 5) % 160;
+      s->nPos = 0;
+      break;
     case 0x1B: s->grp0 = v; break;
-    case 0x20: s->hmp0 = v; break;
+    case 0x20: s->hmp0 = v; s->nHM = x.n; break;
     case 0x2A: {
       int m = ((int8_t)s->hmp0) >> 4;
       s->p0pos = ((s->p0pos - m) % 160 + 160) % 160;
+      /* the motion is minus the high nibble of HMP0: a deviation of HMP0
+       * moves the player by minus a sixteenth of it (straight-through) */
+      if (s->sampler) s->nPos = lin2(s, s->nPos, 1.0, s->nHM, -1.0 / 16.0);
       if (s->hclk <= 9) s->hmove_line = s->line;
       break;
     }
-    case 0x2B: s->hmp0 = 0; break;
+    case 0x2B: s->hmp0 = 0; s->nHM = 0; break;
     default: break;
   }
 }
@@ -870,6 +906,7 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
 }
 
 void ovcs_set_switches(ovcs* s, uint8_t swchb) { s->swchb = swchb; }
+void ovcs_set_sampler(ovcs* s, int on) { s->sampler = on != 0; }
 
 void ovcs_free(ovcs* s) {
   if (!s) return;
@@ -1063,6 +1100,7 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   for (int i = 0; i < 128; i++) s->nRAM[i] = g->ram0 + i;
   s->nA = s->nX = s->nY = s->nV = 0;
   s->nC[0] = s->nC[1] = s->nC[2] = 0;
+  s->nPos = s->nHM = 0;
   s->gs_all = grad_screen;
   for (int t = 0; t < n_steps; t++) {
     int bits[5];
@@ -1083,6 +1121,7 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   for (int i = 0; i < 128; i++) s->nRAM[i] = 0;
   s->nA = s->nX = s->nY = s->nV = 0;
   s->nC[0] = s->nC[1] = s->nC[2] = 0;
+  s->nPos = s->nHM = 0;
   return g;
 }
 

@@ -58,6 +58,9 @@ void ovcs_reset(ovcs* s);
 /* Console switches as SWCHB reads them (power-on: $0B = colour, difficulty
  * B, RESET and SELECT released; $0A holds RESET down). */
 void ovcs_set_switches(ovcs* s, uint8_t swchb);
+/* Differentiable position sampler (Section 3) in soft rollouts: 1 = on.
+ * Off by default; the hard outputs do not depend on it. */
+void ovcs_set_sampler(ovcs* s, int on);
 /* One env-step: set the joystick from `action` (ALE index 0..17), run
  * `frame_skip` frames, copy RAM (128 B) and the last frame (210x160) out.
  * Returns a status bit set: 1 = a frame ended by the line cap, 2 = jammed. */

@@ -153,3 +153,60 @@ def switches_rom():
         a.op("BNE", "rel", "L")
         a.op("JMP", "abs", "F")
     return rom4k(build)
+
+
+SAMPLER_COLOURS = {"bk": 0x20, "pf": 0x44, "p0": 0x86}
+SAMPLER_GRP0 = 0xB7
+SAMPLER_PF2 = 0x30
+
+
+def sampler_rom(resp_each_frame=True, ctrlpf=0):
+    """Player 0 (GRP0 = $B7) over a background with a two-block playfield
+    (PF2 = $30, columns 64..71 and 144..151); every frame copies SWCHA into
+    HMP0 and strobes HMOVE at the start of scanline 2, above the visible
+    rows.  With `resp_each_frame` RESP0 is strobed mid-way through scanline 1
+    of every frame (so each frame's position depends on that frame's input
+    only), otherwise once before the first frame (positions accumulate the
+    motions of every frame)."""
+    def resp0(a):
+        a.op("STA", "zp", 0x02)            # WSYNC
+        for _ in range(20):
+            a.op("NOP")
+        a.op("STA", "zp", 0x10)            # RESP0
+
+    def build(a):
+        a.op("LDA", "imm", SAMPLER_COLOURS["bk"])
+        a.op("STA", "zp", 0x09)
+        a.op("LDA", "imm", SAMPLER_COLOURS["pf"])
+        a.op("STA", "zp", 0x08)
+        a.op("LDA", "imm", SAMPLER_COLOURS["p0"])
+        a.op("STA", "zp", 0x06)
+        a.op("LDA", "imm", SAMPLER_GRP0)
+        a.op("STA", "zp", 0x1B)
+        a.op("LDA", "imm", SAMPLER_PF2)
+        a.op("STA", "zp", 0x0F)
+        a.op("LDA", "imm", ctrlpf)
+        a.op("STA", "zp", 0x0A)
+        if not resp_each_frame:
+            resp0(a)
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)            # VSYNC on: the frame boundary
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        if resp_each_frame:
+            resp0(a)
+        else:
+            a.op("STA", "zp", 0x02)
+        a.op("LDA", "abs", 0x0280)         # SWCHA
+        a.op("STA", "zp", 0x20)            # HMP0
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x2A)            # HMOVE at the start of scanline 2
+        a.op("LDX", "imm", 0)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("DEX")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "FRAME")
+    return rom4k(build, table=False)
