@@ -92,6 +92,17 @@ typedef struct vcs_config {
                                its rendering, output and pixel-gradient work
                                (4 suits soft rollouts with screen losses,
                                whose backward sums every frame's pixels) */
+  int32_t position_sampler; /* 1 = the differentiable position sampler of
+                               Section 3 in soft backward passes: player 0's
+                               position carries a deviation (zero at each
+                               RESP0; an HMOVE adds minus a sixteenth of
+                               HMP0's deviation) and each drawn pixel within
+                               one column of a sprite edge adds
+                               (C_P0 - C_under)(b(d-1) - b(d+1))/2 times its
+                               gradient to it, d = x - pos and b the player's
+                               pixel bits (the symmetric derivative of the
+                               triangular-kernel coverage).  0 = off
+                               (default).  Forward outputs do not depend on it. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

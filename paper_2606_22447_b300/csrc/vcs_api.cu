@@ -164,6 +164,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->sched_window = 4;
   cfg->steps_per_launch = 0;
   cfg->threads_per_env = 0;
+  cfg->position_sampler = 0;
   return VCS_OK;
 }
 
@@ -245,6 +246,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     return vcs_fail(nullptr, VCS_ERR_ARG, "threads_per_env must be 0, 1, 2, 4 or 8 with envs_per_block x it <= 128");
   }
   b->tpe = T;
+  if (b->cfg.position_sampler < 0 || b->cfg.position_sampler > 1) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "position_sampler must be 0 or 1");
+  }
   if (b->cfg.sched_policy < 0 || b->cfg.sched_policy > 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "sched_policy must be 0 or 1");

@@ -37,6 +37,11 @@ constexpr uint64_t kVisualRegs = (1ull << 0x01) | (1ull << 0x06) | (1ull << 0x08
                                  (1ull << 0x0A) | (1ull << 0x0D) | (1ull << 0x0E) | (1ull << 0x0F) |
                                  (1ull << 0x10) | (1ull << 0x1B) | (1ull << 0x2A);
 
+// TIA write registers whose write opens a new version of a differentiable
+// quantity (the soft path's tapes): the three colour registers, and player
+// 0's position (RESP0, HMOVE) for the position sampler.
+constexpr uint64_t kVersionRegs = (1ull << 0x06) | (1ull << 0x08) | (1ull << 0x09) | (1ull << 0x10) | (1ull << 0x2A);
+
 // A TIA register write at frame cycle fcw.  A write that changes the picture
 // first draws the pending span with the old registers.  The register update
 // itself is a set of selects rather than a switch: one indirect branch per
@@ -45,9 +50,7 @@ template <class Tape>
 __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t reg,
                                           uint32_t v, int32_t fcw) {
   if (((kVisualRegs >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
-  if (reg == 0x06) tape.colour_write(0);
-  else if (reg == 0x08) tape.colour_write(1);
-  else if (reg == 0x09) tape.colour_write(2);
+  tape.version_write(reg);
   const uint32_t line = div76((uint32_t)fcw);
   const uint32_t m = (uint32_t)fcw - 76u * line;   // CPU cycle within the line
   const uint32_t h = 3u * m;                       // colour clock within the line
@@ -198,9 +201,10 @@ __device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r) {
 // soft path records these; the hard path compiles the hook away).
 struct NoTape {
   static constexpr bool kAcc = false;
+  static constexpr bool sampler = false;
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) {}
-  __device__ __forceinline__ void colour_write(int) {}
-  __device__ __forceinline__ void pixels(float, float, float) {}
+  __device__ __forceinline__ void version_write(uint32_t) {}
+  __device__ __forceinline__ void pixels(float, float, float, float) {}
 };
 
 // Instruction length of each addressing mode, two bits per mode.
@@ -452,6 +456,72 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
   p.ea = ea;
 }
 
+// The paper's 38 extra opcode bytes (USBC, the unofficial NOPs, LAX, SAX)
+// and the jam of every other undocumented byte, decoded at run time from
+// the decode tables.  Real programs seldom execute them, so one compact
+// handler serves all of them: specialised handlers for each would add
+// instruction-cache pressure to every other instruction.
+__device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint32_t op, uint32_t opaddr,
+                                           uint32_t b1, uint32_t b2, Pend& p) {
+  const uint32_t mc = c.dt->mode_cyc[op & 0xFF], co = c.dt->cls_op[op & 0xFF];   // op = 0x100: jammed
+  const uint32_t mode = mc & 15, id = co >> 2;
+  p.nw = 0;
+  p.wv = 0;
+  p.wstack = false;
+  p.tfl = 0;
+  p.seq = true;
+  if (r.jam || mode == AM_JAM) {   // the CPU jams after the fetch; a jammed CPU idles to the next line
+    p.n = r.jam ? 76u - (uint32_t)r.fc % 76u : 1u;
+    r.PC = r.jam ? r.PC : (opaddr + 1) & 0xFFFF;
+    r.jam = 1;
+    p.rec = false;
+    p.seq = false;
+    p.ea = 0;
+    p.tref = 0;
+    return;
+  }
+  uint32_t n = mc >> 4;
+  r.PC = (opaddr + ((kModeLen >> (2 * mode)) & 3)) & 0xFFFF;
+  // effective address: zero-page modes wrap in page zero; (zp,X) and (zp),Y
+  // read their pointer from page zero
+  const uint32_t idx = mode == AM_ZPX || mode == AM_ABX ? r.X : (mode == AM_ZPY || mode == AM_ABY ? r.Y : 0u);
+  uint32_t ea;
+  bool cross = false;
+  if (mode == AM_ZP || mode == AM_ZPX || mode == AM_ZPY) {
+    ea = (b1 + idx) & 0xFF;
+  } else if (mode == AM_INX || mode == AM_INY) {
+    const uint32_t q = mode == AM_INX ? (b1 + r.X) & 0xFF : b1;
+    const uint32_t base = zp_read(c, r, q) | (zp_read(c, r, (q + 1) & 0xFF) << 8);
+    ea = (base + (mode == AM_INY ? r.Y : 0u)) & 0xFFFF;
+    cross = mode == AM_INY && ((base ^ ea) & 0xFF00) != 0;
+  } else {
+    const uint32_t base = b1 | (b2 << 8);
+    ea = (base + idx) & 0xFFFF;
+    cross = (mode == AM_ABX || mode == AM_ABY) && ((base ^ ea) & 0xFF00) != 0;
+  }
+  uint32_t m = b1;
+  if (id != OP_NOP && id != OP_SAX && mode != AM_IMM) {   // the data read on the last cycle
+    n += cross ? 1u : 0u;
+    m = (mode == AM_ZP || mode == AM_ZPX || mode == AM_ZPY) ? zp_read(c, r, ea) : bus_read(c, r, st, ea, (int)n);
+  }
+  if (mode == AM_IMM) ea = (opaddr + 1) & 0xFFFF;
+  if (id == OP_SBC) do_sbc(r, m);   // USBC
+  if (id == OP_LAX) {
+    r.A = m;
+    r.X = m;
+    set_nz(r, m);
+  }
+  if (id == OP_SAX) {
+    p.nw = 1;
+    p.wv = r.A & r.X;
+  }
+  p.widx = n;
+  p.rec = id == OP_SBC || id == OP_LAX || id == OP_SAX;   // reverse_needed of the extra bytes
+  p.tref = ea;
+  p.n = n;
+  p.ea = ea;
+}
+
 // Instruction bytes at the program counter, fetched ahead: opcode | first
 // operand << 8 | second operand << 16, or kSlowFetch when the bytes must be
 // read through the bus at execution time (outside the cartridge window, near
@@ -499,27 +569,7 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
         continue;
       }
       default:
-        switch (sel) {   // the paper's extra bytes (equal semantics share a handler); anything else jams
-          case 0xEB: exec_op<0xE9>(c, r, st, opaddr, b1, b2, p); break;   // USBC = SBC #imm
-          case 0x1A: case 0x3A: case 0x5A: case 0x7A: case 0xDA: case 0xFA:
-            exec_op<0xEA>(c, r, st, opaddr, b1, b2, p); break;
-          case 0x80: case 0x82: case 0x89: case 0xC2: case 0xE2: exec_op<0x80>(c, r, st, opaddr, b1, b2, p); break;
-          case 0x04: case 0x44: case 0x64: exec_op<0x04>(c, r, st, opaddr, b1, b2, p); break;
-          case 0x14: case 0x34: case 0x54: case 0x74: case 0xD4: case 0xF4:
-            exec_op<0x14>(c, r, st, opaddr, b1, b2, p); break;
-          case 0x0C: exec_op<0x0C>(c, r, st, opaddr, b1, b2, p); break;
-          case 0x1C: case 0x3C: case 0x5C: case 0x7C: case 0xDC: case 0xFC:
-            exec_op<0x1C>(c, r, st, opaddr, b1, b2, p); break;
-          VCS_LAX_SAX_OPS(VCS_CASE)
-          default:   // the CPU jams after the fetch; a jammed CPU idles to the next line
-            p.n = r.jam ? 76u - (uint32_t)r.fc % 76u : 1u;
-            r.PC = r.jam ? r.PC : (opaddr + 1) & 0xFFFF;
-            r.jam = 1;
-            p.nw = 0;
-            p.rec = false;
-            p.seq = false;
-            break;
-        }
+        exec_extra(c, r, st, sel, opaddr, b1, b2, p);
         break;
 #undef VCS_CASE
     }

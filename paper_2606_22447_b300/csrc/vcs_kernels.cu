@@ -35,8 +35,9 @@ struct CountTape {
   static constexpr bool kAcc = false;
   uint32_t n = 0, ncw = 0;
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) { n++; }
-  __device__ __forceinline__ void colour_write(int) { ncw++; }
-  __device__ __forceinline__ void pixels(float, float, float) {}
+  static constexpr bool sampler = false;
+  __device__ __forceinline__ void version_write(uint32_t reg) { ncw += (uint32_t)(kVersionRegs >> reg) & 1u; }
+  __device__ __forceinline__ void pixels(float, float, float, float) {}
 };
 
 __device__ __forceinline__ uint32_t round_byte(float v) {

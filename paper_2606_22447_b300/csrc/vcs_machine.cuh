@@ -420,7 +420,36 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       s_pf += (pf ? tn : 0.f) + (pf_wins ? tp : 0.f);
       s_bk += pf ? 0.f : tn;
     }
-    tape.pixels(s_p0, s_pf, s_bk);
+    // Position sampler (Section 3): the player's coverage relaxed with a
+    // triangular kernel has, at the integer position, the symmetric slope
+    // (b(d - 1) - b(d + 1)) / 2 in pos at column x = pos + d, nonzero only
+    // for d in -1..8.  Each such drawn, unblanked column where the player is
+    // not behind a playfield pixel adds (C_P0 - C_under) x slope x gradient.
+    float s_pos = 0.f;
+    if (tape.sampler && grev) {
+      const uint32_t xb = 4 * blank_g > x0 ? 4 * blank_g : x0;
+      const int32_t cp = (int32_t)(r.col0 & 0xFE);
+#pragma unroll 1
+      for (int32_t i = 0; i < 10; i++) {
+        int32_t x = (int32_t)r.pos - 1 + i;
+        x += x < 0 ? 160 : 0;
+        x -= x >= 160 ? 160 : 0;
+        const uint32_t ux = (uint32_t)x;
+        const int32_t d = i - 1;
+        const int32_t bl = d >= 1 ? (int32_t)((grev >> (d - 1)) & 1) : 0;
+        const int32_t br = d + 1 < 8 ? (int32_t)((grev >> (d + 1)) & 1) : 0;
+        if (bl == br || ux < xb || ux >= x1 || !owns_chunk(c, ux >> 4)) continue;
+        const uint32_t g = ux >> 2;
+        const bool pf = (pfm >> g) & 1;
+        if (pf_first && pf) continue;
+        const float4 q = gl[g * c.E];
+        const uint32_t k = ux & 3;
+        const float w = k == 0 ? q.x : (k == 1 ? q.y : (k == 2 ? q.z : q.w));
+        const int32_t under = (int32_t)((pf ? r.colpf : r.colbk) & 0xFE);
+        s_pos += (0.5f * (float)((bl - br) * (cp - under))) * w;
+      }
+    }
+    tape.pixels(s_p0, s_pf, s_bk, s_pos);
   } else {
     // Groups g0 and gl may be partly inside [x0, x1); the ones between are
     // whole words.  Background and playfield first (one select per group,

@@ -42,7 +42,10 @@
 
 namespace vcs {
 
-constexpr int kCarry = 7 + 256;   // aA aX aY aV aC0 aC1 aC2, aRAM[128] and its compensation
+// carried adjoints: aA aX aY aV aC0 aC1 aC2, aRAM[128] and its compensation,
+// then those of player 0's position and of HMP0 (position sampler)
+constexpr int kCarry = 7 + 256 + 2;
+constexpr int kCarryPos = 7 + 256;
 constexpr int kMaxW = 120;        // window half-width limit (tau <= 10)
 
 // Compensated (Neumaier) sum: s + c carries the running total.
@@ -53,14 +56,20 @@ __device__ __forceinline__ void comp_add(float& s, float& c, float x) {
 }
 
 
+// SAMPLER: the position sampler is on (its pixel sums are compiled out of
+// the other instantiation, which then carries zero position adjoints).
+template <bool SAMPLER>
 struct RecTape {
   static constexpr bool kAcc = true;
+  static constexpr bool sampler = SAMPLER;
   uint32_t* buf;
   float* cw;
   uint32_t n, cap, ncw, capcw;
-  int32_t slot0, slot1, slot2;     // float slot of each colour register's live version
-  float s0, s1, s2, c0, c1, c2;    // compensated pixel-gradient sums of the live versions
-  float p0, p1, p2;                // sums of the versions alive at the segment start
+  // versions 0..2: the colour registers COLUP0, COLUPF, COLUBK; version 3:
+  // player 0's position (its pixel sums are the sampler's, zero when off)
+  int32_t slot0, slot1, slot2, slot3;  // float slot of each live version
+  float s0, s1, s2, s3, c0, c1, c2, c3;  // compensated pixel-gradient sums of the live versions
+  float p0, p1, p2, p3;            // sums of the versions alive at the segment start
   bool overflow;
   uint32_t T, gmask;               // replicas of this env and their warp lanes
   // The replicas of an env each sum the pixel chunks they own; a version's
@@ -86,19 +95,28 @@ struct RecTape {
     ncw++;
     if (r == 0) { close_version(slot0, s0 + c0, p0); s0 = c0 = 0.f; slot0 = fresh; }
     else if (r == 1) { close_version(slot1, s1 + c1, p1); s1 = c1 = 0.f; slot1 = fresh; }
-    else { close_version(slot2, s2 + c2, p2); s2 = c2 = 0.f; slot2 = fresh; }
+    else if (r == 2) { close_version(slot2, s2 + c2, p2); s2 = c2 = 0.f; slot2 = fresh; }
+    else { close_version(slot3, s3 + c3, p3); s3 = c3 = 0.f; slot3 = fresh; }
   }
-  // pixel-gradient sums of one drawn span, per owner
-  __device__ __forceinline__ void pixels(float v0, float v1, float v2) {
+  __device__ __forceinline__ void version_write(uint32_t reg) {
+    if (reg == 0x06) colour_write(0);
+    else if (reg == 0x08) colour_write(1);
+    else if (reg == 0x09) colour_write(2);
+    else if (reg == 0x10 || reg == 0x2A) colour_write(3);
+  }
+  // pixel-gradient sums of one drawn span, per owner, and the sampler's sum
+  __device__ __forceinline__ void pixels(float v0, float v1, float v2, float v3) {
     comp_add(s0, c0, v0);
     comp_add(s1, c1, v1);
     comp_add(s2, c2, v2);
+    if constexpr (SAMPLER) comp_add(s3, c3, v3);
   }
   __device__ __forceinline__ void finish() {
     close_version(slot0, s0 + c0, p0);
     close_version(slot1, s1 + c1, p1);
     close_version(slot2, s2 + c2, p2);
-    s0 = s1 = s2 = c0 = c1 = c2 = 0.f;
+    close_version(slot3, s3 + c3, p3);
+    s0 = s1 = s2 = s3 = c0 = c1 = c2 = c3 = 0.f;
   }
 };
 
@@ -129,11 +147,13 @@ struct BwdParams {
   float tau;
   int32_t W;
   uint32_t sched_policy, sched_window;
+  int32_t sampler;            // the position sampler is on
   int32_t* err;
 };
 
 struct Adj {
   float A, X, Y, V, C0, C1, C2;
+  float P, H;          // player 0's position and HMP0 (position sampler)
   float u[5], uc[5];   // joystick-input adjoints of the current step (compensated)
 };
 
@@ -173,6 +193,7 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
 
 // Adjoint of the value written to `ref`: taken from the cell (which is then
 // cleared, the write being one-hot).
+template <bool SAMPLER>
 __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
                                             uint32_t& j, uint32_t ref) {
   const uint32_t ad = ref & 0x1FFF;
@@ -183,6 +204,23 @@ __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, u
     if (reg == 0x06) { g = a.C0 + (j ? cw[--j] : 0.f); a.C0 = 0.f; return g; }
     if (reg == 0x08) { g = a.C1 + (j ? cw[--j] : 0.f); a.C1 = 0.f; return g; }
     if (reg == 0x09) { g = a.C2 + (j ? cw[--j] : 0.f); a.C2 = 0.f; return g; }
+    // RESP0 and HMOVE open a position version (its slot pops either way)
+    if (reg == 0x2A || reg == 0x10) {
+      const float sv = j ? cw[--j] : 0.f;
+      if constexpr (SAMPLER) {
+        if (reg == 0x2A) {   // HMOVE: pos' = pos - HMP0 / 16 (the written value is ignored)
+          a.P += sv;
+          a.H -= 0.0625f * a.P;
+        } else {             // RESP0: the new position is a constant
+          a.P = 0.f;
+        }
+      }
+      return 0.f;
+    }
+    if constexpr (SAMPLER) {
+      if (reg == 0x20) { g = a.H; a.H = 0.f; return g; }   // HMP0
+      if (reg == 0x2B) { a.H = 0.f; return 0.f; }           // HMCLR
+    }
     return 0.f;
   }
   if (!(ad & 0x200)) {
@@ -202,6 +240,7 @@ __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, u
 
 __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
 
+template <bool SAMPLER>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                             const float* izr, int W, float* imp, float* impc, uint32_t f8,
                                             uint32_t is2k, const float* cw, uint32_t& j, uint32_t rec) {
@@ -243,19 +282,19 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
-      const float g = take_write(a, aram, aramc, E, cw, j, ref);
+      const float g = take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
       a.A += g;
       a.X += g;
       break;
     }
     case 0x85: case 0x95: case 0x8D: case 0x9D: case 0x99: case 0x81: case 0x91:
-      a.A += take_write(a, aram, aramc, E, cw, j, ref);
+      a.A += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
       break;
     case 0x86: case 0x96: case 0x8E:
-      a.X += take_write(a, aram, aramc, E, cw, j, ref);
+      a.X += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
       break;
     case 0x84: case 0x94: case 0x8C:
-      a.Y += take_write(a, aram, aramc, E, cw, j, ref);
+      a.Y += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
       break;
     case 0x06: case 0x16: case 0x0E: case 0x1E:
     case 0x26: case 0x36: case 0x2E: case 0x3E:
@@ -263,7 +302,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x66: case 0x76: case 0x6E: case 0x7E:
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
-      float g = take_write(a, aram, aramc, E, cw, j, ref);
+      float g = take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
       scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
       break;
     }
@@ -272,8 +311,8 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xA8: a.A += a.Y; a.Y = 0.f; break;   // TAY
     case 0x98: a.Y += a.A; a.A = 0.f; break;   // TYA
     case 0xBA: a.X = 0.f; break;               // TSX: SP carries nothing
-    case 0x48: a.A += take_write(a, aram, aramc, E, cw, j, ref); break;   // PHA
-    case 0x08: take_write(a, aram, aramc, E, cw, j, ref); break;           // PHP
+    case 0x48: a.A += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref); break;   // PHA
+    case 0x08: take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref); break;           // PHP
     case 0x68: {                                                    // PLA
       float g = a.A;
       a.A = 0.f;
@@ -281,13 +320,13 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
       break;
     }
     case 0x20:                                                      // JSR: two pushes
-      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
-      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
+      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
+      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
       break;
     case 0x00:                                                      // BRK: three pushes
-      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 2));
-      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
-      take_write(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
+      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 2));
+      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
+      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
       break;
     default:
       break;
@@ -315,7 +354,7 @@ __host__ __device__ constexpr size_t bwd_row_offset(int E) {
   return (smem_bytes(E) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
 }
 
-template <int T>
+template <int T, bool SAMPLER>
 __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
@@ -347,15 +386,15 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   } else {
     power_on(c, r);
   }
-  RecTape tape;
+  RecTape<SAMPLER> tape;
   tape.buf = p.rec + (size_t)env * p.cap_rec;
   tape.cw = p.cw + (size_t)env * p.cap_cw;
   tape.n = 0; tape.cap = p.cap_rec;
   tape.ncw = 0; tape.capcw = p.cap_cw;
-  tape.slot0 = tape.slot1 = tape.slot2 = -1;
-  tape.s0 = tape.s1 = tape.s2 = 0.f;
-  tape.c0 = tape.c1 = tape.c2 = 0.f;
-  tape.p0 = tape.p1 = tape.p2 = 0.f;
+  tape.slot0 = tape.slot1 = tape.slot2 = tape.slot3 = -1;
+  tape.s0 = tape.s1 = tape.s2 = tape.s3 = 0.f;
+  tape.c0 = tape.c1 = tape.c2 = tape.c3 = 0.f;
+  tape.p0 = tape.p1 = tape.p2 = tape.p3 = 0.f;
   tape.overflow = false;
   tape.T = (uint32_t)T;
   tape.gmask = c.gmask;
@@ -395,13 +434,15 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   // 2. reverse sweep
   Adj a;
   if (p.first) {
-    a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = 0.f;
+    a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.P = a.H = 0.f;
     for (int i = 0; i < 128; i++) aram[i * E] = 0.f;
     for (int i = 0; i < 128; i++) aramc[i * E] = 0.f;
   } else {
     const float* cr = p.carry;
     a.A = cr[0 * n + env]; a.X = cr[1 * n + env]; a.Y = cr[2 * n + env]; a.V = cr[3 * n + env];
     a.C0 = cr[4 * n + env]; a.C1 = cr[5 * n + env]; a.C2 = cr[6 * n + env];
+    a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
+    a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
     for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
     for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
   }
@@ -428,7 +469,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
       for (uint32_t q = k; q > lo; q--) {
         const uint32_t sl = (q - 1) & 3;
         const uint32_t rv = sl == 0 ? ch.x : (sl == 1 ? ch.y : (sl == 2 ? ch.z : ch.w));
-        reverse_one(a, aram, aramc, E, ek, izr, p.W, imp, impc, f8, is2k, cw, j, rv);
+        reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, imp, impc, f8, is2k, cw, j, rv);
       }
       ch = nx;
       k = lo;
@@ -442,6 +483,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   a.C0 += tape.p0;
   a.C1 += tape.p1;
   a.C2 += tape.p2;
+  if constexpr (SAMPLER) a.P += tape.p3;
   if (p.seg == 0) {
     if (p.grad_ram0)
       for (int i = 0; i < 128; i++) p.grad_ram0[(size_t)env * 128 + i] = aram[i * E] + aramc[i * E];
@@ -449,6 +491,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     float* cr = p.carry;
     cr[0 * n + env] = a.A; cr[1 * n + env] = a.X; cr[2 * n + env] = a.Y; cr[3 * n + env] = a.V;
     cr[4 * n + env] = a.C0; cr[5 * n + env] = a.C1; cr[6 * n + env] = a.C2;
+    cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
   }
@@ -456,20 +499,37 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
 
 static cudaError_t allow_bwd_smem(size_t smem) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_soft_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+  const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((e = cudaFuncSetAttribute(k_soft_bwd<1, false>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<2, false>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<4, false>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<8, false>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<1, true>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<2, true>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<4, true>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<8, true>, (cudaFuncAttribute)a, (int)smem)))
     return e;
   return cudaSuccess;
 }
 
 static void launch_bwd(const BwdParams& p, int n_blocks, int E, int T, size_t smem, cudaStream_t s) {
   switch (T) {
-    case 1: k_soft_bwd<1><<<n_blocks, E, smem, s>>>(p); break;
-    case 2: k_soft_bwd<2><<<n_blocks, 2 * E, smem, s>>>(p); break;
-    case 4: k_soft_bwd<4><<<n_blocks, 4 * E, smem, s>>>(p); break;
-    default: k_soft_bwd<8><<<n_blocks, 8 * E, smem, s>>>(p); break;
+    case 1:
+      if (p.sampler) k_soft_bwd<1, true><<<n_blocks, E, smem, s>>>(p);
+      else k_soft_bwd<1, false><<<n_blocks, E, smem, s>>>(p);
+      break;
+    case 2:
+      if (p.sampler) k_soft_bwd<2, true><<<n_blocks, 2 * E, smem, s>>>(p);
+      else k_soft_bwd<2, false><<<n_blocks, 2 * E, smem, s>>>(p);
+      break;
+    case 4:
+      if (p.sampler) k_soft_bwd<4, true><<<n_blocks, 4 * E, smem, s>>>(p);
+      else k_soft_bwd<4, false><<<n_blocks, 4 * E, smem, s>>>(p);
+      break;
+    default:
+      if (p.sampler) k_soft_bwd<8, true><<<n_blocks, 8 * E, smem, s>>>(p);
+      else k_soft_bwd<8, false><<<n_blocks, 8 * E, smem, s>>>(p);
+      break;
   }
 }
 
@@ -727,6 +787,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.tau = t->tau;
   p.W = t->W;
   p.tpe = b->tpe;
+  p.sampler = b->cfg.position_sampler;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
@@ -875,6 +936,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.tau = t->tau;
   p.W = t->W;
   p.tpe = b->tpe;
+  p.sampler = b->cfg.position_sampler;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;

@@ -51,9 +51,10 @@ def _setup(mappers, n_envs, n_steps, seed, warm=2, frame_skip=1, **cfg):
     return torch, roms, env_cart, b, wa, acts, u
 
 
-def _oracle_grads(rom, mapper, warm_acts, u, frame_skip, tau, gr, gs):
+def _oracle_grads(rom, mapper, warm_acts, u, frame_skip, tau, gr, gs, sampler=False):
     o = oracle.Oracle(rom, mapper)
     o.rollout(warm_acts, 1, screens=False)
+    o.set_sampler(sampler)
     g, ram_out, scr_out = o.soft_rollout(u.astype(np.float64), frame_skip, tau, 6.0,
                                          None if gr is None else gr.astype(np.float64),
                                          None if gs is None else gs.astype(np.float64))
@@ -222,3 +223,49 @@ def test_gradients_through_the_extra_opcode_bytes():
         assert_grad_close(g_rom[e, :4096], o_rom, f"grad_rom env {e}")
         assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
         assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+
+
+@pytest.mark.parametrize("cart,tpe,seg", [("synthetic", 4, 64), ("synthetic", 1, 2), ("resp_each_frame", 4, 64),
+                                          ("resp_each_frame_pf_first", 2, 64), ("resp_once", 4, 2),
+                                          ("resp_once", 1, 64)])
+def test_position_sampler_gradients_match_oracle(cart, tpe, seg):
+    """The position sampler (Section 3) on the GPU against the FP64 oracle:
+    synthetic carts (RESP0, HMP0 and HMOVE among their writes, three
+    mappers) and the sampler carts, whose joystick moves player 0 through
+    HMP0 each frame; with two-frame segments the position and HMP0 adjoints
+    cross segment boundaries."""
+    from tests.microrom import sampler_rom
+    torch = torch_cuda()
+    if cart == "synthetic":
+        mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
+        roms = synth.config_carts(61, mappers)
+    else:
+        mappers = [synth.MAPPER_4K]
+        roms = [sampler_rom(cart != "resp_once", 4 if cart.endswith("pf_first") else 0)]
+    n_envs, n_steps, tau = 6, 5, 0.1
+    env_cart = (np.arange(n_envs) % len(mappers)).astype(np.int32)
+    b = make_batch(roms, mappers, env_cart, envs_per_block=8, threads_per_env=tpe, segment_frames=seg,
+                   position_sampler=1)
+    wa = synth.actions(62, n_envs, 2)
+    gpu_rollout(b, wa, 1, screens=False)
+    u = synth.action_inputs(synth.actions(63, n_envs, n_steps))
+    gr = synth.normal_f32(63, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(63, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, 8192), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u)
+    b.sync()
+    g_rom, g_ram0, g_u = g_rom.cpu().numpy(), g_ram0.cpu().numpy(), g_u.cpu().numpy()
+    for e in range(n_envs):
+        c = env_cart[e]
+        (o_rom, o_ram0, o_u), _, _ = _oracle_grads(roms[c], mappers[c], wa[:, e], u[:, e], 1, tau,
+                                                   gr[:, e], gs[:, e], sampler=True)
+        size = len(roms[c])
+        assert_grad_close(g_rom[e, :size], o_rom, f"grad_rom env {e}")
+        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
+        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+        if cart != "synthetic":
+            assert np.abs(o_u).max() > 100, "the joystick must move the sprite"
