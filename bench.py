@@ -176,11 +176,12 @@ def bench_counts() -> dict:
         return json.load(f)
 
 
-def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1):
+def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False):
     """SOFT-STE forward + backward over n_frames (frame-skip 1, 64-frame
     checkpoint segments, loss weights on 8 RAM bytes and 256 pixels at every
-    step).  Returns env-steps/s of fwd+bwd, the split and the library's
-    device memory for the tape."""
+    step), optionally with the differentiable position sampler.  Returns
+    env-steps/s of fwd+bwd, the split and the library's device memory for
+    the tape."""
     import torch
 
     from paper_2606_22447_b300 import Batch, default_config, synth
@@ -188,7 +189,8 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1):
     ec = synth.env_cart_round_robin(n_envs, len(mappers))
     # four replicas per env: the backward's recompute draws every frame's
     # pixel gradients, which the replicas share
-    b = Batch(roms, mappers, ec, default_config(segment_frames=64, threads_per_env=4))
+    b = Batch(roms, mappers, ec, default_config(segment_frames=64, threads_per_env=4,
+                                                position_sampler=1 if sampler else 0))
     u = torch.from_numpy(synth.action_inputs(synth.actions(SEED, n_envs, n_frames))).cuda()
     rng = np.random.default_rng(SEED)
     w_ram = torch.zeros(128, device="cuda")
@@ -220,7 +222,8 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1):
     return {"env_steps_per_s": n_envs * n_frames / ((fwd + bwd) / 1e3),
             "instructions_per_s": n_envs * n_frames * ipf / ((fwd + bwd) / 1e3),
             "instructions_per_frame": ipf, "fwd_ms": fwd, "bwd_ms": bwd,
-            "n_envs": n_envs, "frames": n_frames, "tau": tau, "tape_device_gb": used / 1e9,
+            "n_envs": n_envs, "frames": n_frames, "tau": tau, "position_sampler": sampler,
+            "tape_device_gb": used / 1e9,
             "gpu_launches": 1 + 2 * ((n_frames + 63) // 64) + 2}
 
 
@@ -372,7 +375,9 @@ def gpu_arm(args):
     soft = None
     if not args.no_soft:
         from paper_2606_22447_b300 import synth as _s
-        soft = {"short_1024x64": soft_leg(1024, 64, [_s.MAPPER_4K], 3, "soft_short_1024x4k_instructions_per_frame")}
+        soft = {"short_1024x64": soft_leg(1024, 64, [_s.MAPPER_4K], 3, "soft_short_1024x4k_instructions_per_frame"),
+                "short_1024x64_sampler": soft_leg(1024, 64, [_s.MAPPER_4K], 3,
+                                                  "soft_short_1024x4k_instructions_per_frame", sampler=True)}
         if not args.no_soft_long:
             soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, 1, "soft_long_4096xmix8_instructions_per_frame")
     mixed = None

@@ -75,6 +75,7 @@ def lib():
         L.ogrf_nodes.argtypes = [vp]
         L.ovcs_set_switches.argtypes = [vp, C.c_uint8]
         L.ovcs_set_sampler.argtypes = [vp, C.c_int]
+        L.ovcs_set_step_instructions.argtypes = [vp, C.c_int]
         L.ovcs_digest.restype = C.c_uint64
         L.ovcs_digest.argtypes = [u8p, u8p]
         L.ovcs_relaxed_read.restype = C.c_double
@@ -165,6 +166,11 @@ class Oracle:
         """Switch the differentiable position sampler (Section 3) on or off for
         the soft rollouts that follow."""
         lib().ovcs_set_sampler(self.h, 1 if on else 0)
+
+    def set_step_instructions(self, n: int):
+        """Make every following step run n instruction slots (n > 0) instead
+        of frame_skip frames (n = 0)."""
+        lib().ovcs_set_step_instructions(self.h, int(n))
 
     def step(self, action: int, frame_skip: int = 1):
         ram = np.zeros(128, np.uint8)

@@ -117,6 +117,7 @@ struct ovcs {
   int32_t nA, nX, nY, nV, nC[3], nRAM[128];
   int32_t nPos, nHM;       /* deviations of the P0 position and of HMP0 (sampler) */
   int sampler;             /* 1: the differentiable position sampler is on */
+  int step_instr;          /* > 0: a step is this many instruction slots, not frames */
   int32_t u_leaf;
   const double* gs_all;   /* grad_screen for all steps (or NULL) */
   const double* gs;       /* grad_screen of the frame being rendered */
@@ -446,7 +447,9 @@ static void wr(ovcs* s, uint16_t addr, val x) {
 /* ---------------- frames ---------------- */
 
 static void set_gs(ovcs* s) {
-  if (s->g && s->gs_all && s->frames_in_step == s->frame_skip - 1)
+  /* pixel gradients weigh the frame a frame step returns (none in
+   * instruction-granular steps) */
+  if (s->g && s->gs_all && s->step_instr == 0 && s->frames_in_step == s->frame_skip - 1)
     s->gs = s->gs_all + (size_t)s->soft_step * SCR_H * SCR_W;
   else
     s->gs = NULL;
@@ -907,6 +910,7 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
 
 void ovcs_set_switches(ovcs* s, uint8_t swchb) { s->swchb = swchb; }
 void ovcs_set_sampler(ovcs* s, int on) { s->sampler = on != 0; }
+void ovcs_set_step_instructions(ovcs* s, int n) { s->step_instr = n > 0 ? n : 0; }
 
 void ovcs_free(ovcs* s) {
   if (!s) return;
@@ -962,12 +966,16 @@ static void action_bits(int action, int u[5]) {
   u[4] = strstr(n, "FIRE") != NULL;
 }
 
+/* One env-step: frame_skip frames, or, in instruction-granular mode (the
+ * paper's throughput unit, Section 6: one step = one emulated instruction),
+ * step_instr instruction slots (an instruction, or a jammed CPU's idle to the
+ * next line), frames ending inside the step as they come. */
 static int run_frames(ovcs* s, int frame_skip) {
   int status = 0;
   s->frames_in_step = 0;
   s->frame_skip = frame_skip;
   set_gs(s);
-  while (s->frames_in_step < frame_skip) {
+  for (long k = 0; s->step_instr > 0 ? k < s->step_instr : s->frames_in_step < frame_skip; k++) {
     step_instruction(s);
     if (s->line >= LINE_CAP) {
       frame_end(s);

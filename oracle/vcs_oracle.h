@@ -61,6 +61,12 @@ void ovcs_set_switches(ovcs* s, uint8_t swchb);
 /* Differentiable position sampler (Section 3) in soft rollouts: 1 = on.
  * Off by default; the hard outputs do not depend on it. */
 void ovcs_set_sampler(ovcs* s, int on);
+/* Instruction-granular steps (the paper's throughput unit: one step = one
+ * emulated instruction): n > 0 makes every following step (ovcs_step, soft
+ * rollouts) run n instruction slots (an executed instruction, or a jammed
+ * CPU's idle to the next line) instead of frame_skip frames; 0 restores
+ * frame steps.  The screen of such a step is the last frame completed. */
+void ovcs_set_step_instructions(ovcs* s, int n);
 /* One env-step: set the joystick from `action` (ALE index 0..17), run
  * `frame_skip` frames, copy RAM (128 B) and the last frame (210x160) out.
  * Returns a status bit set: 1 = a frame ended by the line cap, 2 = jammed. */
