@@ -227,6 +227,54 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False)
             "gpu_launches": 1 + 2 * ((n_frames + 63) // 64) + 2}
 
 
+def instr_leg(env_counts, n_instr=3000, reps=3):
+    """The paper's own throughput unit (Section 6, Table s-gpu): rollouts of
+    n_instr emulated instructions per env from power-on, one instruction-
+    granular step, on the 4 KB synthetic cart, for each env count: hard
+    forward, SOFT-STE forward, and SOFT-STE forward + backward (loss
+    weights on 8 RAM bytes of the final state).  Returns instructions/s per
+    env count (best of reps; each rep starts from power-on)."""
+    import torch
+
+    from paper_2606_22447_b300 import Batch, default_config, synth
+    roms = synth.config_carts(SEED, [synth.MAPPER_4K])
+    rng = np.random.default_rng(SEED)
+    w_ram = torch.zeros(128, device="cuda")
+    w_ram[torch.from_numpy(rng.choice(128, 8, replace=False))] = 1.0
+    out = {}
+    for n in env_counts:
+        b = Batch(roms, [synth.MAPPER_4K], np.zeros(n, np.int32), default_config(step_instructions=n_instr))
+        acts = torch.from_numpy(synth.actions(SEED, n, 1)).cuda()
+        u = torch.from_numpy(synth.action_inputs(synth.actions(SEED, n, 1))).cuda()
+        ram = torch.empty((1, n, 128), dtype=torch.uint8, device="cuda")
+        g_u = torch.empty((1, n, 5), device="cuda")
+        best = {"hard": 1e30, "soft_fwd": 1e30, "soft_fwd_bwd": 1e30}
+        for r in range(reps + 1):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            b.reset()
+            e[0].record()
+            b.rollout(acts, 1, ram)
+            e[1].record()
+            b.reset()
+            e[2].record()
+            tape = b.soft_rollout(0.1, u, 1)
+            e[3].record()
+            tape.backward(w_ram=w_ram, grad_u=g_u)
+            e[4].record()
+            torch.cuda.synchronize()
+            b.sync()
+            tape.free()
+            if r == 0:
+                continue   # first pass: module load and allocations
+            best["hard"] = min(best["hard"], e[0].elapsed_time(e[1]))
+            best["soft_fwd"] = min(best["soft_fwd"], e[2].elapsed_time(e[3]))
+            best["soft_fwd_bwd"] = min(best["soft_fwd_bwd"], e[2].elapsed_time(e[4]))
+        out[str(n)] = {k + "_instructions_per_s": n * n_instr / (v / 1e3) for k, v in best.items()}
+        b.close()
+    return {"instructions_per_rollout": n_instr, "cart": "4 KB synthetic (seed-generated), from power-on",
+            "by_n_envs": out}
+
+
 def mixed_leg(n_envs, steps, reps):
     """The batched mixed-cartridge workload: n_envs envs over 16 carts (6 x 2K,
     6 x 4K, 4 x F8, round-robin then grouped by cart), geometric episode
@@ -383,6 +431,9 @@ def gpu_arm(args):
     mixed = None
     if not args.no_mixed:
         mixed = mixed_leg(args.mixed_envs, 8, 5)
+    instr = None
+    if not args.no_instr:
+        instr = instr_leg([1, 64, 256, 1024, 4096, 16384, 65536])
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
@@ -398,6 +449,7 @@ def gpu_arm(args):
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "soft_fwd_bwd": soft,
             "mixed_carts": mixed,
+            "instruction_granular": instr,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -417,6 +469,8 @@ def main():
     ap.add_argument("--no-soft", action="store_true", help="skip the SOFT-STE fwd+bwd legs")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 65,536-env mixed-cartridge leg")
     ap.add_argument("--mixed-envs", type=int, default=65536)
+    ap.add_argument("--no-instr", action="store_true",
+                    help="skip the 3,000-instruction rollouts at 1..65,536 envs (the paper's throughput unit)")
     ap.add_argument("--no-soft-long", action="store_true",
                     help="skip the 4096-env x 2048-frame soft rollout (about 20 s)")
     args = ap.parse_args()

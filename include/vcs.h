@@ -103,6 +103,21 @@ typedef struct vcs_config {
                                pixel bits (the symmetric derivative of the
                                triangular-kernel coverage).  0 = off
                                (default).  Forward outputs do not depend on it. */
+  int32_t step_instructions;/* 0 = frame steps (default): a step runs
+                               frame_skip frames.  n > 0 = instruction-
+                               granular steps, the paper's throughput unit
+                               (Section 6, one step = one emulated
+                               instruction): every step of vcs_step,
+                               vcs_rollout and vcs_soft_rollout runs n
+                               instruction slots (an executed instruction, or
+                               a jammed CPU's idle to the next line), frames
+                               ending inside a step as they come, and
+                               frame_skip is ignored.  Such steps return RAM
+                               only: screen outputs, screen gradients and
+                               screen loss weights, boot frames, start NOOPs
+                               and episode tables are refused
+                               (VCS_ERR_ARG), and soft checkpoints are taken
+                               every segment_frames steps. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

@@ -68,6 +68,7 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.start_noops = b->start_noops;
   p.n_start = b->n_start;
   p.boot_frames = (p.boot_noop + p.boot_reset > 0 || b->start_noops) ? 1 : 0;
+  p.step_instr = b->cfg.step_instructions;
   return p;
 }
 
@@ -80,27 +81,40 @@ static vcs_status set_geometry(vcs_batch* b, int E) {
   std::vector<int32_t> perm(n_envs);
   for (int e = 0; e < n_envs; e++) perm[e] = e;
   std::stable_sort(perm.begin(), perm.end(), [&](int a, int c) { return env_cart[a] < env_cart[c]; });
-  std::vector<int4> blocks;
-  for (int i = 0; i < n_envs;) {
-    const int c = env_cart[perm[i]];
-    int j = i;
-    while (j < n_envs && env_cart[perm[j]] == c && j - i < E) j++;
-    blocks.push_back(make_int4(c, i, j - i, 0));
-    i = j;
-  }
+  auto cut = [&](int per_block) {
+    std::vector<int4> blocks;
+    for (int i = 0; i < n_envs;) {
+      const int c = env_cart[perm[i]];
+      int j = i;
+      while (j < n_envs && env_cart[perm[j]] == c && j - i < per_block) j++;
+      blocks.push_back(make_int4(c, i, j - i, 0));
+      i = j;
+    }
+    return blocks;
+  };
+  const std::vector<int4> blocks = cut(E);
+  const std::vector<int4> bwd = E > kBwdMaxEnvsPerBlock ? cut(kBwdMaxEnvsPerBlock) : std::vector<int4>();
   int4* dblocks = nullptr;
+  int4* dbwd = nullptr;
   int32_t* dperm = nullptr;
   cudaError_t e;
   if ((e = cudaMalloc(&dblocks, blocks.size() * sizeof(int4))) || (e = cudaMalloc(&dperm, n_envs * sizeof(int32_t))) ||
+      (!bwd.empty() && (e = cudaMalloc(&dbwd, bwd.size() * sizeof(int4)))) ||
       (e = cudaMemcpy(dblocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
+      (!bwd.empty() && (e = cudaMemcpy(dbwd, bwd.data(), bwd.size() * sizeof(int4), cudaMemcpyHostToDevice))) ||
       (e = cudaMemcpy(dperm, perm.data(), n_envs * sizeof(int32_t), cudaMemcpyHostToDevice))) {
     cudaFree(dblocks);
+    cudaFree(dbwd);
     cudaFree(dperm);
     return vcs_cuda_fail(b, e, "launch geometry");
   }
   cudaFree(b->blocks);
+  cudaFree(b->bwd_blocks);
   cudaFree(b->perm);
   b->blocks = dblocks;
+  b->bwd_blocks = dbwd;
+  b->bwd_n_blocks = (int)bwd.size();
+  b->bwd_E = bwd.empty() ? 0 : kBwdMaxEnvsPerBlock;
   b->perm = dperm;
   b->n_blocks = (int)blocks.size();
   b->perm_host = perm;
@@ -130,6 +144,7 @@ static void free_batch(vcs_batch* b) {
   cudaFree(b->cart_begin);
   cudaFree(b->dt);
   cudaFree(b->blocks);
+  cudaFree(b->bwd_blocks);
   cudaFree(b->perm);
   cudaFree(b->ep_len);
   cudaFree(b->start_noops);
@@ -165,6 +180,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->steps_per_launch = 0;
   cfg->threads_per_env = 0;
   cfg->position_sampler = 0;
+  cfg->step_instructions = 0;
   return VCS_OK;
 }
 
@@ -246,6 +262,11 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     return vcs_fail(nullptr, VCS_ERR_ARG, "threads_per_env must be 0, 1, 2, 4 or 8 with envs_per_block x it <= 128");
   }
   b->tpe = T;
+  if (b->cfg.step_instructions < 0 ||
+      (b->cfg.step_instructions > 0 && b->cfg.boot_noop_frames + b->cfg.boot_reset_frames > 0)) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "step_instructions must be >= 0, and 0 with boot frames");
+  }
   if (b->cfg.position_sampler < 0 || b->cfg.position_sampler > 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "position_sampler must be 0 or 1");
@@ -323,6 +344,8 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
 vcs_status vcs_set_episodes(vcs_batch* b, const uint32_t* ep_len, int32_t n_episodes) {
   if (!b) return VCS_ERR_ARG;
   if (n_episodes < 0 || (n_episodes > 0 && !ep_len)) return vcs_fail(b, VCS_ERR_ARG, "bad episode table");
+  if (n_episodes > 0 && b->cfg.step_instructions > 0)
+    return vcs_fail(b, VCS_ERR_ARG, "episode tables need frame steps (step_instructions = 0)");
   cudaFree(b->ep_len);
   b->ep_len = nullptr;
   b->n_episodes = 0;
@@ -338,6 +361,8 @@ vcs_status vcs_set_episodes(vcs_batch* b, const uint32_t* ep_len, int32_t n_epis
 vcs_status vcs_set_start_noops(vcs_batch* b, const uint8_t* counts, int32_t n_per_env) {
   if (!b) return VCS_ERR_ARG;
   if (n_per_env < 0 || (n_per_env > 0 && !counts)) return vcs_fail(b, VCS_ERR_ARG, "bad start-noop table");
+  if (n_per_env > 0 && b->cfg.step_instructions > 0)
+    return vcs_fail(b, VCS_ERR_ARG, "start NOOPs need frame steps (step_instructions = 0)");
   cudaFree(b->start_noops);
   b->start_noops = nullptr;
   b->n_start = 0;
@@ -372,6 +397,8 @@ vcs_status vcs_rollout(vcs_batch* b, const uint8_t* actions, int32_t n_steps, in
   if (!b) return VCS_ERR_ARG;
   if (!actions) return vcs_fail(b, VCS_ERR_ARG, "actions is NULL");
   if (n_steps < 0 || frame_skip < 1) return vcs_fail(b, VCS_ERR_ARG, "n_steps >= 0 and frame_skip >= 1 required");
+  if (screen_out && b->cfg.step_instructions > 0)
+    return vcs_fail(b, VCS_ERR_ARG, "instruction steps return no screens");
   const int32_t k = b->steps_per_launch > 0 ? b->steps_per_launch : (n_steps > 0 ? n_steps : 1);
   const size_t n = (size_t)b->n_envs;
   for (int32_t t0 = 0; t0 < n_steps; t0 += k) {
@@ -511,8 +538,8 @@ static std::string tune_key(const vcs_batch* b, int32_t frame_skip, bool ram, bo
   int per_mapper[3] = {0, 0, 0};
   for (int e = 0; e < b->n_envs; e++) per_mapper[b->mapper[b->env_cart[e]] % 3]++;
   char buf[256];
-  snprintf(buf, sizeof buf, "|%d|%d|%d|%d|%d|%d|%d|%d", b->sms, b->n_envs, b->n_carts, per_mapper[0], per_mapper[1],
-           per_mapper[2], frame_skip, (ram ? 1 : 0) | (screen ? 2 : 0));
+  snprintf(buf, sizeof buf, "|%d|%d|%d|%d|%d|%d|%d|%d|%d", b->sms, b->n_envs, b->n_carts, per_mapper[0], per_mapper[1],
+           per_mapper[2], frame_skip, (ram ? 1 : 0) | (screen ? 2 : 0), b->cfg.step_instructions);
   return name + buf;
 }
 

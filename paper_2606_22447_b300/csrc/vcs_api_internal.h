@@ -24,6 +24,10 @@ struct vcs_batch {
   vcs::DecodeTables* dt = nullptr;
   int4* blocks = nullptr;
   int32_t* perm = nullptr;
+  // the backward's blocks when envs_per_block is above what its shared
+  // memory holds (kBwdMaxEnvsPerBlock envs; same permutation), else null
+  int4* bwd_blocks = nullptr;
+  int32_t bwd_n_blocks = 0, bwd_E = 0;
   uint32_t* ep_len = nullptr;
   int32_t n_episodes = 0;
   uint8_t* start_noops = nullptr;  // [n_envs][n_start] NOOP frames starting each episode
@@ -56,3 +60,15 @@ SoA soa_of(uint32_t* state, int32_t n_envs);
 vcs_status vcs_fail(vcs_batch* b, vcs_status st, const char* fmt, ...);
 vcs_status vcs_cuda_fail(vcs_batch* b, cudaError_t e, const char* what);
 vcs::StepParams vcs_base_params(vcs_batch* b);
+
+// Largest envs per block whose backward shared memory (about 9.7 KB +
+// 1.9 KB per env) fits in a block.
+constexpr int kBwdMaxEnvsPerBlock = 64;
+
+// The backward's launch geometry (its own block table past
+// kBwdMaxEnvsPerBlock envs per block).
+inline void vcs_bwd_geometry(const vcs_batch* b, const int4** blocks, int* n_blocks, int* E) {
+  *blocks = b->bwd_blocks ? b->bwd_blocks : b->blocks;
+  *n_blocks = b->bwd_blocks ? b->bwd_n_blocks : b->n_blocks;
+  *E = b->bwd_blocks ? b->bwd_E : b->E;
+}

@@ -30,6 +30,7 @@ struct Step {
   int32_t fe_at;       // frame cycle of a VSYNC frame end in this instruction, or -1
   uint32_t status;     // kSt* bits of this step
   bool want_screen;
+  int32_t instr_left;  // instruction-granular steps: slots left in the step
 };
 
 // TIA write registers whose value changes the picture.
@@ -258,8 +259,10 @@ __host__ __device__ constexpr bool page_zero_mode() {
 // again by that LDA; the timer value read k cycles after the write of V with
 // interval I is V - ceil(k / I), zero for (V - 1) I < k <= V I.  A loop that
 // would step over that window (only possible for I = 1) or that starts after
-// the underflow is left to the interpreter.
-__device__ __forceinline__ void skip_timer_poll(Regs& r, uint32_t opaddr) {
+// the underflow is left to the interpreter.  An instruction-granular step
+// skips at most the whole iterations its remaining slots hold (two each, the
+// LDA about to execute counted in the step), and `budget` loses them.
+__device__ __forceinline__ void skip_timer_poll(Regs& r, uint32_t opaddr, int32_t& budget) {
   const uint32_t period = 7u + ((((opaddr + 5u) ^ opaddr) & 0xFF00) ? 1u : 0u);   // LDA 4 + BNE taken 3 (+1 page cross)
   const uint32_t vi = r.tv << r.tsh;
   const uint32_t k0 = r.cyc + 4u - r.tw;   // the LDA reads on its fourth cycle
@@ -270,6 +273,9 @@ __device__ __forceinline__ void skip_timer_poll(Regs& r, uint32_t opaddr) {
   const int32_t room = kLineCap * kLineCycles - 1 - r.fc;   // stay below the watchdog
   const uint32_t jw = room > 0 ? (period == 7u ? (uint32_t)room / 7u : (uint32_t)room >> 3) : 0u;
   j = j < jw ? j : jw;
+  const uint32_t jb = budget > 0 ? (uint32_t)(budget - 1) >> 1 : 0u;
+  j = j < jb ? j : jb;
+  budget -= (int32_t)(2 * j);
   r.cyc += j * period;
   r.fc += (int32_t)(j * period);
 }
@@ -288,7 +294,7 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     const uint32_t off = opaddr & 0xFFF;
     if (b1 == 0x84 && b2 == 0x02 && (opaddr & 0x1000) && off <= 0xFFA) {
       const uint8_t* q = c.rom + ((r.bank << 12) | off);
-      if (q[3] == 0xD0 && q[4] == 0xFB) skip_timer_poll(r, opaddr);
+      if (q[3] == 0xD0 && q[4] == 0xFB) skip_timer_poll(r, opaddr, st.instr_left);
     }
   }
   constexpr OpInfo I = op_info(OP);

@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t round_byte(float v) {
 // forward: joystick bits come from rounded float inputs, outputs are float,
 // the RAM may be overridden from float values first, and the full state is
 // checkpointed at the start of every segment of seg_steps steps.
-template <bool SOFT, int T, bool BOOT>
+template <bool SOFT, int T, bool BOOT, bool INSTR = false>
 __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   // T threads per env (a compile-time constant, so T = 1 carries no replica
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
       }
       run_active = active;
     }
-    run_frames(c, r, rd, st, tape, run_active, lanes, p.sched_policy, p.sched_window);
+    st.instr_left = p.step_instr;
+    run_frames<INSTR>(c, r, rd, st, tape, run_active, lanes, p.sched_policy, p.sched_window);
     if (boot_turn) {
       if (boot_left > 0) {
         boot_left--;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
       } else {
         if (p.ram_out) write_ram(c, p.ram_out + ((size_t)t * n + env) * 128);
       }
-      if (!SOFT && p.n_episodes > 0) {
+      if (!SOFT && !INSTR && p.n_episodes > 0) {
         epf += (uint32_t)p.frame_skip;
         uint32_t len = p.ep_len[(size_t)env * p.n_episodes + (epi % (uint32_t)p.n_episodes)];
         if (epf >= len) {   // auto-reset: power on, boot before the next step
@@ -297,6 +298,11 @@ static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   const dim3 grid(n_blocks), block(E * p.tpe);
   const size_t smem = step_smem_bytes(E);
   cudaStream_t s = (cudaStream_t)stream;
+  // instruction-granular steps draw nothing, so one lane per env serves them
+  if (p.step_instr > 0) {
+    k_run<SOFT, 1, false, true><<<grid, dim3(E), smem, s>>>(p);
+    return (int)cudaGetLastError();
+  }
   // the boot sequence exists in the hard step kernel only when a batch asks
   // for it, so that default launches carry none of its code
   const bool boot = !SOFT && p.boot_frames;

@@ -51,6 +51,7 @@ struct StepParams {
   int32_t boot_noop, boot_reset;   // boot: NOOP frames, then frames with RESET pressed
   const uint8_t* start_noops;      // [n_envs][n_start] NOOP frames starting each episode, or null
   int32_t n_start;
+  int32_t step_instr;       // > 0: a step is this many instruction slots (not frames)
   uint32_t sched_policy;    // warp scheduling: 0 program order, 1 emulated time (run_frames)
   uint32_t sched_window;    // time window in cycles for policy 1
   // soft forward only

@@ -193,7 +193,8 @@ __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Ste
   }
 }
 
-// Run instruction slots until `frame_skip` frames have ended.
+// Run instruction slots until `frame_skip` frames have ended, or, for
+// instruction-granular steps (INSTR), until the step's slots have run.
 //
 // Warp scheduling.  Envs of one cart run the same program, but after a
 // data-dependent branch or a timer poll loop they sit at different points of
@@ -210,17 +211,21 @@ __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Ste
 // independent, so the order changes no result.
 // `lanes` is the mask of the warp's launched lanes; inactive lanes only take
 // part in the reduction.
-template <class Tape>
+template <bool INSTR = false, class Tape>
 __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, bool active,
                                            uint32_t lanes, uint32_t policy, uint32_t window) {
+  // INSTR: the step is st.instr_left instruction slots (frames end inside it
+  // as they come); otherwise st.frame_skip frames, and the slot budget that
+  // caps the timer-poll skip is unbounded
   st.frames_done = 0;
   st.stall = 0;
   st.fe_at = -1;
+  if constexpr (!INSTR) st.instr_left = 0x7FFFFFFF;
   rd.on = active && st.want_screen && st.frame_skip == 1;
   rd.cur = 3 * (int32_t)r.fs;
   uint32_t pf = prefetch(c, r);
   while (true) {
-    const bool live = active && st.frames_done < st.frame_skip;
+    const bool live = active && (INSTR ? st.instr_left > 0 : st.frames_done < st.frame_skip);
     const uint32_t pos = policy == 0 ? (r.jam ? 0xFFFFu : r.PC) : (uint32_t)r.fc;
     const uint32_t key = live ? (((uint32_t)st.frames_done << 16) | pos) : 0xFFFFFFFFu;
     const uint32_t kmin = __reduce_min_sync(lanes, key);
@@ -232,6 +237,7 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
     bool more;
     do {
       more = exec_one(c, r, rd, st, tape, pf);
+      if constexpr (INSTR) more = (--st.instr_left > 0) && more;
       if ((st.fe_at >= 0) | (r.fc >= kLineCap * kLineCycles)) {   // VSYNC frame end, else the watchdog
         const bool dog = st.fe_at < 0;
         frame_end(c, r, rd, st, tape, dog ? r.fc : st.fe_at);

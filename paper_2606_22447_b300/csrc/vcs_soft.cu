@@ -148,6 +148,7 @@ struct BwdParams {
   int32_t W;
   uint32_t sched_policy, sched_window;
   int32_t sampler;            // the position sampler is on
+  int32_t step_instr;         // > 0: instruction-granular steps of this many slots
   int32_t* err;
 };
 
@@ -354,7 +355,7 @@ __host__ __device__ constexpr size_t bwd_row_offset(int E) {
   return (smem_bytes(E) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
 }
 
-template <int T, bool SAMPLER>
+template <int T, bool SAMPLER, bool INSTR = false>
 __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
@@ -416,7 +417,8 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     rd.gs = p.grad_screen ? p.grad_screen + ((size_t)t * n + env) * (kScreenH * kScreenW) : p.w_screen;
     rd.gline = -1;
     st.want_screen = rd.gs != nullptr;
-    run_frames(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
+    st.instr_left = p.step_instr;
+    run_frames<INSTR>(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
     if (active) {
       normalise_timer(r);
       p.step_end[(size_t)(t - t0) * n + env] = tape.n;
@@ -507,12 +509,19 @@ static cudaError_t allow_bwd_smem(size_t smem) {
       (e = cudaFuncSetAttribute(k_soft_bwd<1, true>, (cudaFuncAttribute)a, (int)smem)) ||
       (e = cudaFuncSetAttribute(k_soft_bwd<2, true>, (cudaFuncAttribute)a, (int)smem)) ||
       (e = cudaFuncSetAttribute(k_soft_bwd<4, true>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<8, true>, (cudaFuncAttribute)a, (int)smem)))
+      (e = cudaFuncSetAttribute(k_soft_bwd<8, true>, (cudaFuncAttribute)a, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_soft_bwd<1, false, true>, (cudaFuncAttribute)a, (int)smem)))
     return e;
   return cudaSuccess;
 }
 
 static void launch_bwd(const BwdParams& p, int n_blocks, int E, int T, size_t smem, cudaStream_t s) {
+  // instruction-granular steps draw nothing (no pixel sums, no position
+  // sampler), so one lane per env serves them
+  if (p.step_instr > 0) {
+    k_soft_bwd<1, false, true><<<n_blocks, E, smem, s>>>(p);
+    return;
+  }
   switch (T) {
     case 1:
       if (p.sampler) k_soft_bwd<1, true><<<n_blocks, E, smem, s>>>(p);
@@ -658,6 +667,8 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
   if (!u) return vcs_fail(b, VCS_ERR_ARG, "u (joystick inputs) is NULL");
   if (!(tau > 0.f) || !(tau <= 10.f)) return vcs_fail(b, VCS_ERR_ARG, "tau must be in (0, 10]");
   if (n_steps < 1 || frame_skip < 1) return vcs_fail(b, VCS_ERR_ARG, "n_steps >= 1 and frame_skip >= 1 required");
+  if (screen_out && b->cfg.step_instructions > 0)
+    return vcs_fail(b, VCS_ERR_ARG, "instruction steps return no screens");
   vcs_tape* t = new (std::nothrow) vcs_tape;
   if (!t) return vcs_fail(b, VCS_ERR_OOM, "host allocation failed");
   t->b = b;
@@ -665,7 +676,10 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
   t->frame_skip = frame_skip;
   t->tau = tau;
   t->W = half_width(tau);
-  t->seg_steps = b->cfg.segment_frames / frame_skip > 0 ? b->cfg.segment_frames / frame_skip : 1;
+  // a checkpoint segment is segment_frames frames, or segment_frames
+  // instruction-granular steps
+  const int32_t seg_div = b->cfg.step_instructions > 0 ? 1 : frame_skip;
+  t->seg_steps = b->cfg.segment_frames / seg_div > 0 ? b->cfg.segment_frames / seg_div : 1;
   t->n_seg = (n_steps + t->seg_steps - 1) / t->seg_steps;
   const size_t n = (size_t)b->n_envs;
   cudaStream_t s = (cudaStream_t)stream;
@@ -719,6 +733,8 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   vcs_batch* b = t->b;
   if ((grad_ram || grad_screen) && w && (w->ram || w->screen))
     return vcs_fail(b, VCS_ERR_ARG, "give either per-step gradients or loss weights, not both");
+  if (b->cfg.step_instructions > 0 && (grad_screen || (w && w->screen)))
+    return vcs_fail(b, VCS_ERR_ARG, "instruction steps return no screens: no screen gradients");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   const size_t n = (size_t)b->n_envs;
@@ -764,7 +780,10 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.frame_skip = t->frame_skip;
   p.seg_steps = t->seg_steps;
   p.ystart = b->cfg.ystart;
-  p.blocks = b->blocks;
+  const int4* bwd_blocks;
+  int bwd_nb, bwd_E;
+  vcs_bwd_geometry(b, &bwd_blocks, &bwd_nb, &bwd_E);
+  p.blocks = bwd_blocks;
   p.perm = b->perm;
   p.roms = t->rom_bytes;
   p.cart_f8 = b->cart_f8;
@@ -788,17 +807,18 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.W = t->W;
   p.tpe = b->tpe;
   p.sampler = b->cfg.position_sampler;
+  p.step_instr = b->cfg.step_instructions;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
-  const size_t smem = bwd_smem_bytes(b->E);
+  const size_t smem = bwd_smem_bytes(bwd_E);
   if ((e = allow_bwd_smem(smem)))
     return vcs_cuda_fail(b, e, "backward shared memory");
   for (int q = t->n_seg - 1; q >= 0; q--) {
     p.seg = q;
     p.first = q == t->n_seg - 1;
     p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
-    launch_bwd(p, b->n_blocks, b->E, b->tpe, smem, s);
+    launch_bwd(p, bwd_nb, bwd_E, b->tpe, smem, s);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
   }
   if (grom) {
@@ -865,6 +885,8 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   vcs_batch* b = t->b;
   if ((grad_ram || grad_screen) && w && (w->ram || w->screen))
     return vcs_fail(b, VCS_ERR_ARG, "give either per-step gradients or loss weights, not both");
+  if (b->cfg.step_instructions > 0 && (grad_screen || (w && w->screen)))
+    return vcs_fail(b, VCS_ERR_ARG, "instruction steps return no screens: no screen gradients");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   void* base = nullptr;
@@ -913,7 +935,10 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.frame_skip = t->frame_skip;
   p.seg_steps = t->seg_steps;
   p.ystart = b->cfg.ystart;
-  p.blocks = b->blocks;
+  const int4* bwd_blocks;
+  int bwd_nb, bwd_E;
+  vcs_bwd_geometry(b, &bwd_blocks, &bwd_nb, &bwd_E);
+  p.blocks = bwd_blocks;
   p.perm = b->perm;
   p.roms = t->rom_bytes;
   p.cart_f8 = b->cart_f8;
@@ -937,17 +962,18 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.W = t->W;
   p.tpe = b->tpe;
   p.sampler = b->cfg.position_sampler;
+  p.step_instr = b->cfg.step_instructions;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
-  const size_t smem = bwd_smem_bytes(b->E);
+  const size_t smem = bwd_smem_bytes(bwd_E);
   if ((e = allow_bwd_smem(smem)))
     return vcs_cuda_fail(b, e, "backward shared memory");
   for (int q = t->n_seg - 1; q >= 0; q--) {
     p.seg = q;
     p.first = q == t->n_seg - 1;
     p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
-    launch_bwd(p, b->n_blocks, b->E, b->tpe, smem, s);
+    launch_bwd(p, bwd_nb, bwd_E, b->tpe, smem, s);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
   }
   if (grom) {

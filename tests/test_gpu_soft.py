@@ -269,3 +269,24 @@ def test_position_sampler_gradients_match_oracle(cart, tpe, seg):
         assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
         if cart != "synthetic":
             assert np.abs(o_u).max() > 100, "the joystick must move the sprite"
+
+
+def test_backward_geometry_past_its_shared_memory():
+    """128 envs per block: the backward runs on its own 64-env block table
+    (same permutation) and gives the gradients of an 8-env geometry, bit for
+    bit (each env's arithmetic does not depend on the blocking)."""
+    torch = torch_cuda()
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8]
+    n_envs, n_steps = 150, 3
+    res = []
+    for epb in (8, 128):
+        _, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 91, envs_per_block=epb)
+        gr = synth.normal_f32(91, (n_steps, n_envs, 128), 1)
+        tape = b.soft_rollout(0.1, torch.from_numpy(u).cuda(), 1)
+        g_rom = torch.empty((n_envs, 8192), device="cuda")
+        g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+        tape.backward(torch.from_numpy(gr).cuda(), None, grad_rom=g_rom, grad_u=g_u)
+        b.sync()
+        res.append((g_rom.cpu().numpy(), g_u.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.abs(res[1][0]).max() > 0
