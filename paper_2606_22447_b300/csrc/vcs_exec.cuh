@@ -214,12 +214,12 @@ constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8)
                               (1u << 26);
 
 // The implemented opcodes (op_info gives each one's mode, cycles and
-// operation): the 151 documented ones, dispatched by the main switch, and
-// the paper's 38 extra bytes, dispatched on the cold path (real programs
-// seldom use them, and keeping their handlers out of the main switch keeps
-// its code as compact as before).  Every other byte jams the CPU.
-#define VCS_LAX_SAX_OPS(X) \
-  X(0xA7) X(0xB7) X(0xAF) X(0xBF) X(0xA3) X(0xB3) X(0x87) X(0x97) X(0x8F) X(0x83)
+// operation): the 151 documented ones, dispatched by the main switch (the
+// list below, then SBC #imm and NOP, whose handlers also serve USBC and the
+// implied extra NOPs), and the rest of the paper's 38 extra bytes, run by
+// exec_extra from the switch's default (real programs seldom use them, and
+// one compact run-time-decoded handler keeps the switch's code as compact as
+// without them).  Every other byte jams the CPU.
 
 #define VCS_DOCUMENTED_OPS(X) \
   X(0x00) X(0x01) X(0x05) X(0x06) X(0x08) X(0x09) X(0x0A) X(0x0D) X(0x0E) X(0x10) X(0x11) X(0x15) \
@@ -233,7 +233,7 @@ constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8)
   X(0xA8) X(0xA9) X(0xAA) X(0xAC) X(0xAD) X(0xAE) X(0xB0) X(0xB1) X(0xB4) X(0xB5) X(0xB6) X(0xB8) \
   X(0xB9) X(0xBA) X(0xBC) X(0xBD) X(0xBE) X(0xC0) X(0xC1) X(0xC4) X(0xC5) X(0xC6) X(0xC8) X(0xC9) \
   X(0xCA) X(0xCC) X(0xCD) X(0xCE) X(0xD0) X(0xD1) X(0xD5) X(0xD6) X(0xD8) X(0xD9) X(0xDD) X(0xDE) \
-  X(0xE0) X(0xE1) X(0xE4) X(0xE5) X(0xE6) X(0xE8) X(0xE9) X(0xEA) X(0xEC) X(0xED) X(0xEE) X(0xF0) \
+  X(0xE0) X(0xE1) X(0xE4) X(0xE5) X(0xE6) X(0xE8) X(0xEC) X(0xED) X(0xEE) X(0xF0) \
   X(0xF1) X(0xF5) X(0xF6) X(0xF8) X(0xF9) X(0xFD) X(0xFE)
 
 // What an instruction leaves for the common tail of exec_one: its cycle
@@ -462,11 +462,13 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
   p.ea = ea;
 }
 
-// The paper's 38 extra opcode bytes (USBC, the unofficial NOPs, LAX, SAX)
-// and the jam of every other undocumented byte, decoded at run time from
-// the decode tables.  Real programs seldom execute them, so one compact
-// handler serves all of them: specialised handlers for each would add
-// instruction-cache pressure to every other instruction.
+// The rest of the paper's 38 extra opcode bytes (the unofficial NOPs with an
+// operand, LAX, SAX) and the jam of every other undocumented byte, decoded
+// at run time from the decode tables.  Real programs seldom execute them,
+// so one compact handler serves all of them: specialised handlers for each
+// would add instruction-cache pressure to every other instruction.  A NOP's
+// operand read has no effect but an F8 hotspot's bank switch (page-zero
+// reads and INTIM reads change nothing), so NOPs read nothing.
 __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint32_t op, uint32_t opaddr,
                                            uint32_t b1, uint32_t b2, Pend& p) {
   const uint32_t mc = c.dt->mode_cyc[op & 0xFF], co = c.dt->cls_op[op & 0xFF];   // op = 0x100: jammed
@@ -505,24 +507,20 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
     ea = (base + idx) & 0xFFFF;
     cross = (mode == AM_ABX || mode == AM_ABY) && ((base ^ ea) & 0xFF00) != 0;
   }
-  uint32_t m = b1;
-  if (id != OP_NOP && id != OP_SAX && mode != AM_IMM) {   // the data read on the last cycle
-    n += cross ? 1u : 0u;
-    m = (mode == AM_ZP || mode == AM_ZPX || mode == AM_ZPY) ? zp_read(c, r, ea) : bus_read(c, r, st, ea, (int)n);
-  }
-  if (mode == AM_IMM) ea = (opaddr + 1) & 0xFFFF;
-  if (id == OP_SBC) do_sbc(r, m);   // USBC
-  if (id == OP_LAX) {
+  if (mode != AM_IMM && mode != AM_IMP && id != OP_SAX) n += cross ? 1u : 0u;   // reads pay the page cross
+  if (id == OP_LAX) {   // the data read on the last cycle
+    const uint32_t m = (mode == AM_ZP || mode == AM_ZPY) ? zp_read(c, r, ea) : bus_read(c, r, st, ea, (int)n);
     r.A = m;
     r.X = m;
     set_nz(r, m);
-  }
-  if (id == OP_SAX) {
+  } else if (id == OP_SAX) {
     p.nw = 1;
     p.wv = r.A & r.X;
+  } else if (mode == AM_ABS || mode == AM_ABX) {   // NOP abs / abs,X: only a hotspot read matters
+    r.bank = (c.f8 && (ea & 0x1FFE) == 0x1FF8) ? (ea & 1) : r.bank;
   }
   p.widx = n;
-  p.rec = id == OP_SBC || id == OP_LAX || id == OP_SAX;   // reverse_needed of the extra bytes
+  p.rec = id == OP_LAX || id == OP_SAX;   // reverse_needed of these bytes
   p.tref = ea;
   p.n = n;
   p.ea = ea;
@@ -566,6 +564,11 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
 #define VCS_CASE(x) \
   case x: exec_op<x>(c, r, st, opaddr, b1, b2, p); break;
       VCS_DOCUMENTED_OPS(VCS_CASE)
+      // SBC #imm and NOP share their handlers with the extra bytes of the
+      // same semantics (USBC; the implied NOPs): one inlined body each
+      case 0xE9: case 0xEB: exec_op<0xE9>(c, r, st, opaddr, b1, b2, p); break;
+      case 0xEA: case 0x1A: case 0x3A: case 0x5A: case 0x7A: case 0xDA: case 0xFA:
+        exec_op<0xEA>(c, r, st, opaddr, b1, b2, p); break;
       case 0x101: {   // fetch through the bus, then dispatch on what was read
         op = bus_read(c, r, st, opaddr, 1);
         const uint32_t len = (kModeLen >> (2 * (c.dt->mode_cyc[op] & 15))) & 3;
