@@ -32,7 +32,8 @@ def build(force: bool = False) -> str:
 class Counters(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "instructions", "cycles", "frames", "tia_writes", "ram_reads", "ram_writes",
-        "rom_reads", "pixels", "watchdog")]
+        "rom_reads", "pixels", "watchdog", "relaxed_reads", "relaxed_reads_exact", "branches",
+        "branches_exact")]
 
 
 _lib = None
@@ -76,6 +77,7 @@ def lib():
         L.ovcs_set_switches.argtypes = [vp, C.c_uint8]
         L.ovcs_set_sampler.argtypes = [vp, C.c_int]
         L.ovcs_set_step_instructions.argtypes = [vp, C.c_int]
+        L.ovcs_set_full.argtypes = [vp, C.c_int, C.c_double, C.c_double]
         L.ovcs_digest.restype = C.c_uint64
         L.ovcs_digest.argtypes = [u8p, u8p]
         L.ovcs_relaxed_read.restype = C.c_double
@@ -171,6 +173,11 @@ class Oracle:
         """Make every following step run n instruction slots (n > 0) instead
         of frame_skip frames (n = 0)."""
         lib().ovcs_set_step_instructions(self.h, int(n))
+
+    def set_full(self, mode: int, T: float = 0.0, alpha: float = 6.0):
+        """Fully relaxed casts: 2 = FULL (executed), 1 = probe (counted
+        only), 0 = off."""
+        lib().ovcs_set_full(self.h, int(mode), float(T), float(alpha))
 
     def step(self, action: int, frame_skip: int = 1):
         ram = np.zeros(128, np.uint8)

@@ -118,6 +118,13 @@ struct ovcs {
   int32_t nPos, nHM;       /* deviations of the P0 position and of HMP0 (sampler) */
   int sampler;             /* 1: the differentiable position sampler is on */
   int step_instr;          /* > 0: a step is this many instruction slots, not frames */
+  /* fully relaxed casts (Section 4's temperature-limit study): 0 = off,
+   * 1 = probe (count the casts that would round off the hard value), 2 =
+   * FULL (execute the relaxed casts) */
+  int full;
+  int full_W;
+  float full_ek[256];      /* float32 weights e^{-k/T} of the relaxed read */
+  float full_g1, full_g0;  /* float32 gate values sigma(alpha), sigma(-alpha) */
   int32_t u_leaf;
   const double* gs_all;   /* grad_screen for all steps (or NULL) */
   const double* gs;       /* grad_screen of the frame being rendered */
@@ -355,6 +362,35 @@ static void rom_map(const ovcs* s, uint16_t a, int* base, int* M, int* idx) {
   else { *base = s->bank * 4096; *M = 4096; *idx = a & 0xFFF; }
 }
 
+/* FULL mode's temperature read (Section 4, the fully relaxed forward): the
+ * byte at index a of a memory tensor t[0..M) read as
+ * round(sum_k w_k t[k] / sum_k w_k) with w_k = e^{-|k - a| / T} over the
+ * frozen window |k - a| <= W clipped to the tensor, in float32 (the soft
+ * state's precision), terms added in index order, rounded half to even. */
+static uint8_t full_read(const ovcs* s, const uint8_t* t, int M, int a) {
+  const int lo = a - s->full_W < 0 ? 0 : a - s->full_W;
+  const int hi = a + s->full_W > M - 1 ? M - 1 : a + s->full_W;
+  float num = 0.0f, den = 0.0f;
+  for (int k = lo; k <= hi; k++) {
+    const float w = s->full_ek[k > a ? k - a : a - k];
+    num += w * (float)t[k];
+    den += w;
+  }
+  float v = rintf(num / den);
+  if (v < 0.0f) v = 0.0f;
+  if (v > 255.0f) v = 255.0f;
+  return (uint8_t)v;
+}
+
+/* A read of a memory tensor through the relaxed cast: counted in probe and
+ * FULL modes, applied in FULL mode. */
+static uint8_t full_cast(ovcs* s, const uint8_t* t, int M, int a) {
+  const uint8_t v = full_read(s, t, M, a);
+  s->cnt.relaxed_reads++;
+  if (v == t[a]) s->cnt.relaxed_reads_exact++;
+  return s->full == 2 ? v : t[a];
+}
+
 /* One bus read cycle. */
 static val rd(ovcs* s, uint16_t addr) {
   tick(s);
@@ -364,7 +400,7 @@ static val rd(ovcs* s, uint16_t addr) {
     hotspot(s, a);
     int base, M, idx;
     rom_map(s, a, &base, &M, &idx);
-    r.v = s->rom[base + idx];
+    r.v = s->full ? full_cast(s, s->rom + base, M, idx) : s->rom[base + idx];
     r.n = g_read_rom(s, base, M, idx);
     s->cnt.rom_reads++;
   } else if (!(a & 0x80)) {
@@ -374,7 +410,7 @@ static val rd(ovcs* s, uint16_t addr) {
       default: r.v = 0; break;
     }
   } else if (!(a & 0x200)) {
-    r.v = s->ram[a & 0x7F];
+    r.v = s->full ? full_cast(s, s->ram, 128, a & 0x7F) : s->ram[a & 0x7F];
     r.n = g_read_ram(s, a & 0x7F);
     s->cnt.ram_reads++;
   } else if (!(a & 0x04)) {
@@ -631,6 +667,28 @@ static uint8_t op_shift(ovcs* s, int kind, uint8_t v) {
  * derivative has no consumer among the gradient outputs. */
 static void branch(ovcs* s, int cond) {
   uint8_t off = fetch_operand(s).v;
+  if (s->full) {
+    /* Eq. branch without the straight-through correction: the crisp flag
+     * gives z = +1 (condition holds) or -1, gate g = sigma(alpha z), and the
+     * counter is the blend rounded back to an integer, in float32:
+     * round(pc_fall + g delta).  A taken branch pays its cycle, and the page
+     * cross is between the fall-through and the new counter. */
+    const uint16_t fall = s->pc;
+    const float g = cond ? s->full_g1 : s->full_g0;
+    const float pcf = (float)fall + g * (float)(int8_t)off;
+    const uint16_t rel = (uint16_t)(long)rintf(pcf);
+    const uint16_t hard = cond ? (uint16_t)(fall + (int8_t)off) : fall;
+    s->cnt.branches++;
+    if (rel == hard) s->cnt.branches_exact++;
+    if (s->full == 2) {
+      if (cond) {
+        idle(s);
+        if ((rel & 0xFF00) != (fall & 0xFF00)) idle(s);
+      }
+      s->pc = rel;
+      return;
+    }
+  }
   if (cond) {
     uint16_t t = (uint16_t)(s->pc + (int8_t)off);
     idle(s);
@@ -911,6 +969,16 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
 void ovcs_set_switches(ovcs* s, uint8_t swchb) { s->swchb = swchb; }
 void ovcs_set_sampler(ovcs* s, int on) { s->sampler = on != 0; }
 void ovcs_set_step_instructions(ovcs* s, int n) { s->step_instr = n > 0 ? n : 0; }
+
+static int half_width(double tau);
+void ovcs_set_full(ovcs* s, int mode, double T, double alpha) {
+  s->full = mode >= 0 && mode <= 2 && T > 0.0 ? mode : 0;
+  if (!s->full) return;
+  s->full_W = half_width(T);
+  for (int k = 0; k <= s->full_W && k < 256; k++) s->full_ek[k] = (float)exp(-(double)k / T);
+  s->full_g1 = (float)(1.0 / (1.0 + exp(-alpha)));
+  s->full_g0 = (float)(1.0 / (1.0 + exp(alpha)));
+}
 
 void ovcs_free(ovcs* s) {
   if (!s) return;

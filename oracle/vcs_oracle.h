@@ -48,6 +48,11 @@ typedef struct {
   uint64_t ram_reads, ram_writes, rom_reads;
   uint64_t pixels;         /* pixels composited into an output frame */
   uint64_t watchdog;       /* frames ended by the line cap */
+  /* casts of the fully relaxed forward (ovcs_set_full modes 1 and 2): ROM
+   * and RAM reads by instructions (opcode fetches excluded) and the ones
+   * whose temperature read rounds to the stored byte; executed conditional
+   * branches and the ones whose relaxed counter rounds to the hard one */
+  uint64_t relaxed_reads, relaxed_reads_exact, branches, branches_exact;
 } ovcs_counters;
 
 /* mapper: 0 = 2K, 1 = 4K, 2 = F8.  rom is copied.  NULL on a bad size. */
@@ -67,6 +72,17 @@ void ovcs_set_sampler(ovcs* s, int on);
  * CPU's idle to the next line) instead of frame_skip frames; 0 restores
  * frame steps.  The screen of such a step is the last frame completed. */
 void ovcs_set_step_instructions(ovcs* s, int n);
+/* Fully relaxed casts (Section 4's temperature-limit study, Theorem 2):
+ * mode 2 = FULL: every ROM and RAM read by an instruction (operand bytes,
+ * data, pointers, stack; not the opcode fetch) returns the temperature-T
+ * read round(sum w_k t[k] / sum w_k), w_k = e^{-|k-a|/T} in the window
+ * |k - a| <= max(1, ceil(12 T)) clipped to the tensor, and a conditional
+ * branch sets pc = round(pc_fall + sigma(alpha z) delta) with z = +1 when
+ * its condition holds, else -1; all in float32 (weights and gate values the
+ * float32 roundings of e^{-k/T} and sigma(+-alpha)).  Mode 1 = probe: the
+ * machine stays hard and only counts which casts would round off the hard
+ * value (the counters' relaxed_* and branches* fields).  Mode 0 = off. */
+void ovcs_set_full(ovcs* s, int mode, double T, double alpha);
 /* One env-step: set the joystick from `action` (ALE index 0..17), run
  * `frame_skip` frames, copy RAM (128 B) and the last frame (210x160) out.
  * Returns a status bit set: 1 = a frame ended by the line cap, 2 = jammed. */

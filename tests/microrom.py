@@ -210,3 +210,47 @@ def sampler_rom(resp_each_frame=True, ctrlpf=0):
         a.op("BNE", "rel", "L")
         a.op("JMP", "abs", "FRAME")
     return rom4k(build, table=False)
+
+
+FULL_T_LOOP = 0xF09E     # the loop of the temperature cart
+FULL_T_DATA = 0xF8D2     # its max-contrast byte
+
+
+def full_temperature_rom():
+    """NOPs from $F000 to the loop at $F09E, then `LDA $F8D2; STA $80;
+    JMP $F09E`: the byte at $F8D2 is 0 with $FF on every side (the largest
+    pull a temperature read can see), while every operand byte of the loop
+    sits between neighbours that nearly balance (low byte $D2 between $AD
+    and $F8, $9E between $4C and $F0, ...), so that the loop's own reads
+    stay exact up to T = 0.17."""
+    a = synth.Asm(0xF000, 4096)
+    for _ in range(FULL_T_LOOP - 0xF000):
+        a.op("NOP")
+    a.op("LDA", "abs", FULL_T_DATA)
+    a.op("STA", "zp", 0x80)
+    a.op("JMP", "abs", FULL_T_LOOP)
+    a.at(0xF8C0 - 0xF000)
+    for i in range(0x40):
+        a.byte(0x00 if 0xF8C0 + i == FULL_T_DATA else 0xFF)
+    a.at(4096 - 6)
+    a.word(0xF000)
+    a.word(0xF000)
+    a.word(0xF000)
+    return bytes(a.resolve())
+
+
+def full_branch_rom(offset, taken):
+    """`LDX #1` (Z clear), then a branch of signed offset `offset` that is
+    taken (BNE) or not (BEQ), landing on NOPs; NOPs all around."""
+    a = synth.Asm(0xF000, 4096)
+    for _ in range(0x100):
+        a.op("NOP")
+    a.op("LDX", "imm", 1)
+    a.byte(0xD0 if taken else 0xF0, offset & 0xFF)
+    for _ in range(0x300):
+        a.op("NOP")
+    a.at(4096 - 6)
+    a.word(0xF000)
+    a.word(0xF000)
+    a.word(0xF000)
+    return bytes(a.resolve())
