@@ -275,6 +275,46 @@ def instr_leg(env_counts, n_instr=3000, reps=3):
             "by_n_envs": out}
 
 
+def full_leg(n_envs=4096, n_instr=3000):
+    """The fully relaxed forward's bit-exactness grid (the supplement's
+    table: alpha 2..6 at T = 0.14, T 0.08..0.20 at alpha = 6): n_envs envs of
+    the 4 KB synthetic cart from power-on, each holding a random joystick
+    action, n_instr instruction slots of the hard and the FULL machine side
+    by side.  Per setting: the envs whose FULL trajectory stayed exact, the
+    median first divergence of the others, and the cast-margin model's
+    prediction from the hard trajectory's casts (P_step = p_read^rho
+    p_branch^f_b)."""
+    import torch
+
+    from paper_2606_22447_b300 import Batch, synth
+    roms = synth.config_carts(SEED, [synth.MAPPER_4K])
+    b = Batch(roms, [synth.MAPPER_4K], np.zeros(n_envs, np.int32))
+    acts = torch.from_numpy(synth.actions(SEED + 7, n_envs, 1)[0]).cuda()
+    grid = [(a, 0.14) for a in (2.0, 3.0, 4.0, 5.0, 6.0)] + [(6.0, t) for t in (0.08, 0.10, 0.12, 0.15, 0.18, 0.20)]
+    rows = []
+    for alpha, T in grid:
+        b.full_divergence(T, alpha, 10, actions=acts)   # warm-up
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        n_div, cnt, _ = b.full_divergence(T, alpha, n_instr, actions=acts, ram=False)
+        e[1].record()
+        torch.cuda.synchronize()
+        nd = n_div.cpu().numpy()
+        c = cnt.cpu().numpy().view(np.uint32).astype(np.float64).sum(axis=0)
+        rho, fb = c[0] / (n_envs * n_instr), c[2] / (n_envs * n_instr)
+        p_read, p_branch = c[1] / max(c[0], 1), c[3] / max(c[2], 1)
+        div = nd[nd > 0]
+        rows.append({"alpha": alpha, "T": T, "exact_fraction": float((nd == 0).mean()),
+                     "median_first_divergence": float(np.median(div)) if div.size else None,
+                     "min_first_divergence": int(div.min()) if div.size else None,
+                     "p_read": p_read, "p_branch": p_branch, "rho": rho, "f_b": fb,
+                     "p_step_predicted": p_read ** rho * p_branch ** fb,
+                     "ms": e[0].elapsed_time(e[1])})
+    b.close()
+    return {"n_envs": n_envs, "instructions": n_instr, "cart": "4 KB synthetic (seed-generated), from power-on",
+            "grid": rows}
+
+
 def mixed_leg(n_envs, steps, reps):
     """The batched mixed-cartridge workload: n_envs envs over 16 carts (6 x 2K,
     6 x 4K, 4 x F8, round-robin then grouped by cart), geometric episode
@@ -434,6 +474,9 @@ def gpu_arm(args):
     instr = None
     if not args.no_instr:
         instr = instr_leg([1, 64, 256, 1024, 4096, 16384, 65536])
+    full = None
+    if not args.no_full:
+        full = full_leg()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
@@ -450,6 +493,7 @@ def gpu_arm(args):
             "soft_fwd_bwd": soft,
             "mixed_carts": mixed,
             "instruction_granular": instr,
+            "full_relaxed": full,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -469,6 +513,8 @@ def main():
     ap.add_argument("--no-soft", action="store_true", help="skip the SOFT-STE fwd+bwd legs")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 65,536-env mixed-cartridge leg")
     ap.add_argument("--mixed-envs", type=int, default=65536)
+    ap.add_argument("--no-full", action="store_true",
+                    help="skip the fully relaxed forward's bit-exactness grid")
     ap.add_argument("--no-instr", action="store_true",
                     help="skip the 3,000-instruction rollouts at 1..65,536 envs (the paper's throughput unit)")
     ap.add_argument("--no-soft-long", action="store_true",

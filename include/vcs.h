@@ -284,6 +284,38 @@ vcs_status vcs_rollout_host(vcs_batch* b, const uint8_t* actions_host, int32_t n
  * *ops_per_s receives operations per second.  Synchronises `stream`. */
 vcs_status vcs_int_peak(double* ops_per_s, void* stream);
 
+/* Fully relaxed forward, the temperature-limit study of Section 4 (Theorem 2
+ * and the supplement's forward bit-exactness table).  From each env's
+ * current state (read, not modified) two machines run n_instr instruction
+ * slots side by side with the joystick held at actions[env] (device uint8
+ * [n_envs], ALE actions; nullable = NOOP):
+ *   - the hard machine, which also counts the casts that would round off:
+ *     counts[env] (device uint32[n_envs][4], nullable) = {ROM and RAM reads
+ *     by instructions (operand bytes, data, pointers, stack; not opcode
+ *     fetches), those whose temperature read equals the byte, conditional
+ *     branches, those whose relaxed counter equals the hard one}: the
+ *     quantities of the paper's cast-margin model (rho, p_read, f_b,
+ *     p_branch);
+ *   - the FULL machine, without the straight-through correction: each such
+ *     read returns round(sum_k w_k t_k / sum_k w_k), w_k = e^{-|k - a| / T}
+ *     over |k - a| <= max(1, ceil(12 T)) clipped to the tensor (the 2K
+ *     image, the 4K image, or the current F8 bank; RAM 128 bytes), and a
+ *     conditional branch sets pc = round(pc_fall + sigma(alpha z) delta),
+ *     z = +1 when its condition holds else -1; float32 throughout, weights
+ *     and gate values the float32 roundings of e^{-k/T} and
+ *     sigma(+-alpha), terms summed in index order, no fused multiply-add,
+ *     rounding half to even.  A taken branch pays its cycle and a page
+ *     cross between the fall-through and the new counter.
+ * n_div[env] (device int32[n_envs]) receives the first slot (1-based) after
+ * which the two machines' states differ (registers, flags, clocks, timer,
+ * TIA registers, bank, jam flag, RAM), 0 if they agree throughout;
+ * ram_full[env] (device uint8[n_envs][128], nullable) the FULL machine's
+ * RAM after the last slot.  The relaxed path is forward only (no tape).
+ * Errors: VCS_ERR_ARG (T outside (0, 10], n_instr < 0, alpha not finite,
+ * n_div NULL), VCS_ERR_CUDA. */
+vcs_status vcs_full_divergence(vcs_batch* b, float T, float alpha, const uint8_t* actions, int32_t n_instr,
+                               int32_t* n_div, uint32_t* counts, uint8_t* ram_full, void* stream);
+
 /* Wait for `stream` and report device-side failures: VCS_ERR_WATCHDOG if a
  * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA
  * for an asynchronous CUDA error. */

@@ -191,6 +191,19 @@ class Batch:
         self._check(_lib.load().vcs_digest(self.h, _ptr(ram), _ptr(screen), n_steps, _ptr(out), _stream(stream)))
         return out
 
+    def full_divergence(self, T: float, alpha: float, n_instr: int, actions=None, counts=True, ram=True,
+                        stream=None):
+        """The fully relaxed forward study (vcs_full_divergence): returns
+        (n_div int32 [n_envs], counts uint32 [n_envs][4] or None, the FULL
+        machine's RAM uint8 [n_envs][128] or None) as torch CUDA tensors."""
+        import torch
+        n_div = torch.empty(self.n_envs, dtype=torch.int32, device="cuda")
+        cnt = torch.empty((self.n_envs, 4), dtype=torch.int32, device="cuda") if counts else None
+        rf = torch.empty((self.n_envs, 128), dtype=torch.uint8, device="cuda") if ram else None
+        self._check(_lib.load().vcs_full_divergence(self.h, float(T), float(alpha), _ptr(actions), int(n_instr),
+                                                    _ptr(n_div), _ptr(cnt), _ptr(rf), _stream(stream)))
+        return n_div, cnt, rf
+
     def graph(self, actions, frame_skip: int, ram_out=None, screen_out=None, status_out=None) -> "Graph":
         """Capture one rollout over these fixed buffers as a CUDA graph."""
         h = C.c_void_p()

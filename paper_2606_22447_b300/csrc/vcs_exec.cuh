@@ -77,11 +77,53 @@ __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Ste
   r.hmp0 = reg == 0x20 ? v : (reg == 0x2B ? 0u : r.hmp0);
 }
 
+// Fully relaxed casts (FM template argument of the interpreter): 0 = the
+// hard machine; 1 = probe: the hard machine that also counts which casts
+// would round off the hard value; 2 = FULL: the fully relaxed forward of
+// Section 4, whose ROM and RAM reads by instructions (operand bytes, data,
+// pointers, stack; not the opcode fetch) are temperature reads cast back to
+// bytes and whose conditional branches take the rounded blend of Eq. branch.
+//
+// Temperature read of index a of a tensor of M bytes (get(k) = byte k):
+// round(sum_k w_k t_k / sum_k w_k), w_k = ek[|k - a|], over |k - a| <= W
+// clipped to the tensor, in float32 with the terms added in index order and
+// no fused multiply-add, rounded half to even, clamped to 0..255.
+template <class Get>
+__device__ __forceinline__ uint32_t relaxed_byte(const FullParams& fp, int32_t M, int32_t a, Get get) {
+  const int32_t lo = a - fp.W < 0 ? 0 : a - fp.W, hi = a + fp.W > M - 1 ? M - 1 : a + fp.W;
+  float num = 0.f, den = 0.f;
+  for (int32_t k = lo; k <= hi; k++) {
+    const float w = fp.ek[k > a ? k - a : a - k];
+    num = __fadd_rn(num, __fmul_rn(w, (float)get(k)));
+    den = __fadd_rn(den, w);
+  }
+  const float v = rintf(__fdiv_rn(num, den));
+  return (uint32_t)fminf(fmaxf(v, 0.f), 255.f);
+}
+// The ROM tensor is the cart image (2K) or the current 4K bank.
+__device__ __forceinline__ uint32_t rom_relaxed(const Ctx& c, const Regs& r, uint32_t addr) {
+  const int32_t M = c.fp->rom_m;
+  const uint32_t base = c.f8 ? (r.bank << 12) : 0u;
+  return relaxed_byte(*c.fp, M, (int32_t)(addr & (uint32_t)(M - 1)), [&](int32_t k) { return (uint32_t)c.rom[base | (uint32_t)k]; });
+}
+__device__ __forceinline__ uint32_t ram_relaxed(const Ctx& c, uint32_t addr) {
+  return relaxed_byte(*c.fp, 128, (int32_t)(addr & 0x7F), [&](int32_t k) { return ram_rd(c, (uint32_t)k); });
+}
+// A cast of a read whose hard value is `exact`: counted in probe and FULL
+// machines, applied in FULL.
+template <int FM>
+__device__ __forceinline__ uint32_t cast_read(Regs& r, uint32_t exact, uint32_t relaxed) {
+  r.fr_reads++;
+  r.fr_exact += relaxed == exact ? 1u : 0u;
+  return FM == 2 ? relaxed : exact;
+}
+
 // One bus read at cycle index idx of the current instruction, for any
 // address.  Every source is read and the result selected, which costs fewer
 // cycles than branching on the address region.  Side effects: a read of an
 // F8 hotspot switches the bank, and a read of INTIM records whether the timer
 // had underflowed (r.intim_live, kept by the soft path's tape).
+template <int FM = 0>
 __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& st, uint32_t addr, int idx) {
   const uint32_t a = addr & 0x1FFF;
   r.bank = (c.f8 && (a & 0x1FFE) == 0x1FF8) ? (a & 1) : r.bank;
@@ -98,15 +140,23 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
   const uint32_t vtim = (a & 1) ? (live ? 0u : 0x80u) : vint;
   const bool timer = (a & 0x1284) == 0x0284;
   r.intim_live = (timer && !(a & 1)) ? (live ? 1u : 0u) : r.intim_live;
+  if constexpr (FM >= 1) {
+    if (a & 0x1000) return cast_read<FM>(r, vrom, rom_relaxed(c, r, a));
+    if ((a & 0x280) == 0x080) return cast_read<FM>(r, vram, ram_relaxed(c, a));
+  }
   return (a & 0x1000) ? vrom : !(a & 0x80) ? vtia : !(a & 0x200) ? vram : !(a & 4) ? vio : vtim;
 }
 
 // A read inside page zero or one (zero-page modes, the stack): RAM or the
 // TIA read registers, no side effects.
-__device__ __forceinline__ uint32_t zp_read(const Ctx& c, const Regs& r, uint32_t a) {
+template <int FM = 0>
+__device__ __forceinline__ uint32_t zp_read(const Ctx& c, Regs& r, uint32_t a) {
   const uint32_t vram = ram_rd(c, a);
   const uint32_t q = a & 0xF;
   const uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
+  if constexpr (FM >= 1) {
+    if (a & 0x80) return cast_read<FM>(r, vram, ram_relaxed(c, a));
+  }
   return (a & 0x80) ? vram : vtia;
 }
 
@@ -192,9 +242,10 @@ __device__ __forceinline__ uint32_t do_shift(Regs& r, uint32_t k, uint32_t v) {
   return res;
 }
 
+template <int FM = 0>
 __device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r) {
   r.SP = (r.SP + 1) & 0xFF;
-  return zp_read(c, r, 0x100u | r.SP);
+  return zp_read<FM>(c, r, 0x100u | r.SP);
 }
 
 // Tape hook: called for each executed instruction the backward sweep acts on
@@ -287,10 +338,10 @@ __device__ __forceinline__ void skip_timer_poll(Regs& r, uint32_t opaddr, int32_
 // every skipped LDA overwrites A before anything reads it, so in the
 // backward sweep each meets a zero adjoint of A and its tape record would do
 // nothing; the LDA that exits the loop is executed and recorded.
-template <uint32_t OP>
+template <uint32_t OP, int FM = 0>
 __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_t opaddr, uint32_t b1, uint32_t b2,
                                         Pend& p) {
-  if constexpr (OP == 0xAD) {
+  if constexpr (OP == 0xAD && FM == 0) {   // the skip assumes exact operand bytes
     const uint32_t off = opaddr & 0xFFF;
     if (b1 == 0x84 && b2 == 0x02 && (opaddr & 0x1000) && off <= 0xFFA) {
       const uint8_t* q = c.rom + ((r.bank << 12) | off);
@@ -321,9 +372,9 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     cross = ((base ^ ea) & 0xFF00) != 0;
   } else if constexpr (mode == AM_INX) {
     const uint32_t q = (b1 + r.X) & 0xFF;
-    ea = zp_read(c, r, q) | (zp_read(c, r, (q + 1) & 0xFF) << 8);
+    ea = zp_read<FM>(c, r, q) | (zp_read<FM>(c, r, (q + 1) & 0xFF) << 8);
   } else if constexpr (mode == AM_INY) {
-    const uint32_t base = zp_read(c, r, b1) | (zp_read(c, r, (b1 + 1) & 0xFF) << 8);
+    const uint32_t base = zp_read<FM>(c, r, b1) | (zp_read<FM>(c, r, (b1 + 1) & 0xFF) << 8);
     ea = (base + r.Y) & 0xFFFF;
     cross = ((base ^ ea) & 0xFF00) != 0;
   }
@@ -336,12 +387,12 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
       m = b1;
     } else {
       n += cross ? 1u : 0u;
-      if constexpr (page_zero_mode<mode>()) m = zp_read(c, r, ea);
-      else m = bus_read(c, r, st, ea, (int)n);
+      if constexpr (page_zero_mode<mode>()) m = zp_read<FM>(c, r, ea);
+      else m = bus_read<FM>(c, r, st, ea, (int)n);
     }
   } else if constexpr (cls == CL_RMW) {
-    if constexpr (page_zero_mode<mode>()) m = zp_read(c, r, ea);
-    else m = bus_read(c, r, st, ea, (int)n - 2);
+    if constexpr (page_zero_mode<mode>()) m = zp_read<FM>(c, r, ea);
+    else m = bus_read<FM>(c, r, st, ea, (int)n - 2);
   }
   p.tref = ea;
   p.tfl = 0;
@@ -395,16 +446,27 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     const bool taken = ((OP >> 5) & 1) == flag;
     const uint32_t next = r.PC;
     const uint32_t t = (next + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF;
-    n += taken ? 1u + (((t ^ next) & 0xFF00) ? 1u : 0u) : 0u;
-    r.PC = taken ? t : next;
+    uint32_t to = taken ? t : next;
+    if constexpr (FM >= 1) {
+      // Eq. branch without the straight-through correction: z = +1 when the
+      // condition holds, else -1; pc = round(pc_fall + sigma(alpha z) delta)
+      const float g = taken ? c.fp->g1 : c.fp->g0;
+      const float pcf = __fadd_rn((float)next, __fmul_rn(g, (float)(int32_t)(int8_t)(uint8_t)b1));
+      const uint32_t rel = (uint32_t)(int32_t)rintf(pcf) & 0xFFFF;
+      r.fr_br++;
+      r.fr_br_exact += rel == to ? 1u : 0u;
+      if constexpr (FM == 2) to = rel;
+    }
+    n += taken ? 1u + (((to ^ next) & 0xFF00) ? 1u : 0u) : 0u;
+    r.PC = to;
     p.tref = pc1;
     p.tfl = taken ? 1u : 0u;
   }
   else if constexpr (id == OP_JMP) { r.PC = ea; }
   else if constexpr (id == OP_JMPI) {
     const uint32_t q = b1 | (b2 << 8);
-    const uint32_t l2 = bus_read(c, r, st, q, 4);
-    const uint32_t h2 = bus_read(c, r, st, (q & 0xFF00) | ((q + 1) & 0xFF), 5);
+    const uint32_t l2 = bus_read<FM>(c, r, st, q, 4);
+    const uint32_t h2 = bus_read<FM>(c, r, st, (q & 0xFF00) | ((q + 1) & 0xFF), 5);
     r.PC = l2 | (h2 << 8);
   }
   else if constexpr (id == OP_JSR) {
@@ -413,14 +475,14 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     p.nw = 2; p.wstack = true; p.wv = (ret >> 8) | ((ret & 0xFF) << 8); p.widx = 4;
   }
   else if constexpr (id == OP_RTS) {
-    const uint32_t lo = pull(c, r);
-    const uint32_t hi = pull(c, r);
+    const uint32_t lo = pull<FM>(c, r);
+    const uint32_t hi = pull<FM>(c, r);
     r.PC = ((lo | (hi << 8)) + 1) & 0xFFFF;
   }
   else if constexpr (id == OP_RTI) {
-    const uint32_t pp = pull(c, r);
-    const uint32_t lo = pull(c, r);
-    const uint32_t hi = pull(c, r);
+    const uint32_t pp = pull<FM>(c, r);
+    const uint32_t lo = pull<FM>(c, r);
+    const uint32_t hi = pull<FM>(c, r);
     unpack_p(r, pp | 0x30);
     r.PC = lo | (hi << 8);
   }
@@ -428,18 +490,18 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     const uint32_t ret = (opaddr + 2) & 0xFFFF;
     p.nw = 3; p.wstack = true; p.wv = (ret >> 8) | ((ret & 0xFF) << 8) | (pack_p(r) << 16); p.widx = 3;
     r.fI = 1;
-    const uint32_t lo = bus_read(c, r, st, 0xFFFE, 6);
-    const uint32_t hi = bus_read(c, r, st, 0xFFFF, 7);
+    const uint32_t lo = bus_read<FM>(c, r, st, 0xFFFE, 6);
+    const uint32_t hi = bus_read<FM>(c, r, st, 0xFFFF, 7);
     r.PC = lo | (hi << 8);
   }
   else if constexpr (id == OP_PHA) { p.nw = 1; p.wstack = true; p.wv = r.A; p.widx = 3; }
   else if constexpr (id == OP_PHP) { p.nw = 1; p.wstack = true; p.wv = pack_p(r); p.widx = 3; }
   else if constexpr (id == OP_PLA) {
-    r.A = pull(c, r);
+    r.A = pull<FM>(c, r);
     set_nz(r, r.A);
     p.tref = 0x100u | r.SP;
   }
-  else if constexpr (id == OP_PLP) { unpack_p(r, pull(c, r) | 0x30); }
+  else if constexpr (id == OP_PLP) { unpack_p(r, pull<FM>(c, r) | 0x30); }
   else if constexpr (id == OP_CLC) { r.fC = 0; }
   else if constexpr (id == OP_SEC) { r.fC = 1; }
   else if constexpr (id == OP_CLI) { r.fI = 0; }
@@ -469,6 +531,7 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
 // would add instruction-cache pressure to every other instruction.  A NOP's
 // operand read has no effect but an F8 hotspot's bank switch (page-zero
 // reads and INTIM reads change nothing), so NOPs read nothing.
+template <int FM = 0>
 __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint32_t op, uint32_t opaddr,
                                            uint32_t b1, uint32_t b2, Pend& p) {
   const uint32_t mc = c.dt->mode_cyc[op & 0xFF], co = c.dt->cls_op[op & 0xFF];   // op = 0x100: jammed
@@ -499,7 +562,7 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
     ea = (b1 + idx) & 0xFF;
   } else if (mode == AM_INX || mode == AM_INY) {
     const uint32_t q = mode == AM_INX ? (b1 + r.X) & 0xFF : b1;
-    const uint32_t base = zp_read(c, r, q) | (zp_read(c, r, (q + 1) & 0xFF) << 8);
+    const uint32_t base = zp_read<FM>(c, r, q) | (zp_read<FM>(c, r, (q + 1) & 0xFF) << 8);
     ea = (base + (mode == AM_INY ? r.Y : 0u)) & 0xFFFF;
     cross = mode == AM_INY && ((base ^ ea) & 0xFF00) != 0;
   } else {
@@ -509,7 +572,7 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
   }
   if (mode != AM_IMM && mode != AM_IMP && id != OP_SAX) n += cross ? 1u : 0u;   // reads pay the page cross
   if (id == OP_LAX) {   // the data read on the last cycle
-    const uint32_t m = (mode == AM_ZP || mode == AM_ZPY) ? zp_read(c, r, ea) : bus_read(c, r, st, ea, (int)n);
+    const uint32_t m = (mode == AM_ZP || mode == AM_ZPY) ? zp_read<FM>(c, r, ea) : bus_read<FM>(c, r, st, ea, (int)n);
     r.A = m;
     r.X = m;
     set_nz(r, m);
@@ -517,7 +580,10 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
     p.nw = 1;
     p.wv = r.A & r.X;
   } else if (mode == AM_ABS || mode == AM_ABX) {   // NOP abs / abs,X: only a hotspot read matters
-    r.bank = (c.f8 && (ea & 0x1FFE) == 0x1FF8) ? (ea & 1) : r.bank;
+    if constexpr (FM >= 1) (void)bus_read<FM>(c, r, st, ea, (int)n);   // the read is a cast to count
+    else r.bank = (c.f8 && (ea & 0x1FFE) == 0x1FF8) ? (ea & 1) : r.bank;
+  } else if (FM >= 1 && (mode == AM_ZP || mode == AM_ZPX)) {
+    (void)zp_read<FM>(c, r, ea);
   }
   p.widx = n;
   p.rec = id == OP_LAX || id == OP_SAX;   // reverse_needed of these bytes
@@ -541,6 +607,14 @@ __device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
   return (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) | (fast ? 0u : kSlowFetch);
 }
 
+// Probe and FULL machines: the temperature reads of the two operand bytes
+// after the opcode (fetched ahead with it; counted only for the bytes the
+// instruction takes).
+__device__ __forceinline__ uint32_t prefetch_relaxed(const Ctx& c, const Regs& r, uint32_t pf) {
+  if (pf & kSlowFetch) return 0u;
+  return rom_relaxed(c, r, (r.PC + 1) & 0xFFFF) | (rom_relaxed(c, r, (r.PC + 2) & 0xFFFF) << 8);
+}
+
 // Execute one instruction slot (an instruction, or for a jammed CPU an idle
 // to the next line start), advance the clocks and prefetch the next
 // instruction's bytes into pf.  Returns true when the next instruction is at
@@ -552,33 +626,40 @@ __device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
 // the common path has a single dispatch.  A bus fetch reads the operand
 // bytes one by one, only as many as the instruction has, and dispatches
 // again.  Writes go through the single write site below.
-template <class Tape>
+template <class Tape, int FM = 0>
 __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t& pf) {
   const uint32_t opaddr = r.PC;
   r.intim_live = 0;
   uint32_t op = pf & 0xFF, b1 = (pf >> 8) & 0xFF, b2 = (pf >> 16) & 0xFF;
+  if constexpr (FM >= 1) {   // the operand bytes fetched ahead are casts
+    if (!(pf & kSlowFetch) && !r.jam) {
+      const uint32_t len = (kModeLen >> (2 * (c.dt->mode_cyc[op] & 15))) & 3;
+      if (len >= 2) b1 = cast_read<FM>(r, b1, r.pfr & 0xFF);
+      if (len >= 3) b2 = cast_read<FM>(r, b2, (r.pfr >> 8) & 0xFF);
+    }
+  }
   uint32_t sel = r.jam ? 0x100u : ((pf & kSlowFetch) ? 0x101u : op);
   Pend p;
   for (;;) {
     switch (sel) {
 #define VCS_CASE(x) \
-  case x: exec_op<x>(c, r, st, opaddr, b1, b2, p); break;
+  case x: exec_op<x, FM>(c, r, st, opaddr, b1, b2, p); break;
       VCS_DOCUMENTED_OPS(VCS_CASE)
       // SBC #imm and NOP share their handlers with the extra bytes of the
       // same semantics (USBC; the implied NOPs): one inlined body each
-      case 0xE9: case 0xEB: exec_op<0xE9>(c, r, st, opaddr, b1, b2, p); break;
+      case 0xE9: case 0xEB: exec_op<0xE9, FM>(c, r, st, opaddr, b1, b2, p); break;
       case 0xEA: case 0x1A: case 0x3A: case 0x5A: case 0x7A: case 0xDA: case 0xFA:
-        exec_op<0xEA>(c, r, st, opaddr, b1, b2, p); break;
+        exec_op<0xEA, FM>(c, r, st, opaddr, b1, b2, p); break;
       case 0x101: {   // fetch through the bus, then dispatch on what was read
-        op = bus_read(c, r, st, opaddr, 1);
+        op = bus_read(c, r, st, opaddr, 1);   // the opcode fetch is never a cast
         const uint32_t len = (kModeLen >> (2 * (c.dt->mode_cyc[op] & 15))) & 3;
-        if (len >= 2) b1 = bus_read(c, r, st, (opaddr + 1) & 0xFFFF, 2);
-        if (len >= 3) b2 = bus_read(c, r, st, (opaddr + 2) & 0xFFFF, op == 0x20 ? 6 : 3);
+        if (len >= 2) b1 = bus_read<FM>(c, r, st, (opaddr + 1) & 0xFFFF, 2);
+        if (len >= 3) b2 = bus_read<FM>(c, r, st, (opaddr + 2) & 0xFFFF, op == 0x20 ? 6 : 3);
         sel = op;
         continue;
       }
       default:
-        exec_extra(c, r, st, sel, opaddr, b1, b2, p);
+        exec_extra<FM>(c, r, st, sel, opaddr, b1, b2, p);
         break;
 #undef VCS_CASE
     }
@@ -601,6 +682,7 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
   r.fc += (int32_t)p.n + st.stall;
   st.stall = 0;
   pf = prefetch(c, r);
+  if constexpr (FM >= 1) r.pfr = prefetch_relaxed(c, r, pf);
   return p.seq && !(pf & kSlowFetch);
 }
 

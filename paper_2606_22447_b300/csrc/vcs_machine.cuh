@@ -206,6 +206,11 @@ struct Regs {
   uint32_t inpt4;            // INPT4 in bits 0-7; bit 8 holds the console RESET switch down
                              // (SWCHB then reads $0A instead of $0B)
   uint32_t intim_live;       // the last INTIM read came before underflow
+  // fully relaxed casts only (probe and FULL machines): the relaxed operand
+  // bytes fetched ahead, and the cast counts (ROM/RAM reads by instructions
+  // and the exact ones, conditional branches and the exact ones)
+  uint32_t pfr;
+  uint32_t fr_reads, fr_exact, fr_br, fr_br_exact;
 };
 
 __device__ __forceinline__ uint32_t pack_p(const Regs& r) {
@@ -220,6 +225,19 @@ __device__ __forceinline__ void unpack_p(Regs& r, uint32_t p) {
   r.fI = (p >> 2) & 1;
   r.fC = p & 1;
 }
+
+// The fully relaxed forward's constants (Section 4's temperature-limit
+// study): float32 weights e^{-k/T} of the temperature read for k <= W, the
+// float32 gate values sigma(alpha) and sigma(-alpha) of a crisp-flag branch,
+// and the size of the block's ROM tensor (2048 for 2K carts, else 4096: an
+// F8 read is relaxed within its bank).
+constexpr int kMaxFullW = 120;
+struct FullParams {
+  float ek[kMaxFullW + 1];
+  int32_t W;
+  float g1, g0;
+  int32_t rom_m;
+};
 
 // Everything a thread needs besides its registers.
 struct Ctx {
@@ -238,6 +256,7 @@ struct Ctx {
   // zeroes and sums it, so no replica reads what another wrote.
   uint32_t rank, T;
   uint32_t gmask;            // warp lanes of this env's replicas
+  const FullParams* fp;      // shared: the relaxed casts' constants (FULL study kernel only)
 };
 
 __device__ __forceinline__ bool owns_chunk(const Ctx& c, uint32_t q) { return (q & (c.T - 1)) == c.rank; }

@@ -82,6 +82,7 @@ __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int
   c.T = (uint32_t)T;
   const uint32_t lane = threadIdx.x & 31;
   c.gmask = ((1u << T) - 1u) << (lane & ~(uint32_t)(T - 1));
+  c.fp = nullptr;
   return c;
 }
 
