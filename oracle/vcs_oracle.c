@@ -18,7 +18,8 @@
  *     the right half repeated or reflected (CTRLPF bit 0); priority
  *     P0 > PF > BK unless CTRLPF bit 2 (PF > P0 > BK);
  *  A7 power-on: A=X=Y=0, SP=$FD, P=$34, PC from $1FFC/D, RAM and TIA zero,
- *     the timer as if 0 had been written to T1024T at cycle 0, F8 in bank 1;
+ *     the timer as if 0 had been written to T1024T at cycle 0, banked carts
+ *     (F8, F6, F4) in their last bank;
  *  A8 timer: a write of V at cycle t_w makes INTIM = V - ceil(k / I) at
  *     t_w + k until that would go negative; from k_u = V*I + 1 on it reads
  *     (0xFF - (k - k_u)) & 0xFF and TIMINT bit 7 is set;
@@ -350,9 +351,10 @@ static void tick(ovcs* s) {
 static void idle(ovcs* s) { tick(s); }
 
 static void hotspot(ovcs* s, uint16_t a) {
-  if (s->mapper == 2) {
-    if (a == 0x1FF8) s->bank = 0;
-    else if (a == 0x1FF9) s->bank = 1;
+  /* F8: $1FF8-$1FF9, F6: $1FF6-$1FF9, F4: $1FF4-$1FFB select banks 0.. */
+  static const int first[5] = {0, 0, 0x1FF8, 0x1FF6, 0x1FF4}, count[5] = {0, 0, 2, 4, 8};
+  if (a >= first[s->mapper] && a < first[s->mapper] + count[s->mapper]) {
+    s->bank = a - first[s->mapper];
   }
 }
 
@@ -954,8 +956,8 @@ static int step_instruction(ovcs* s) {
 /* ------------------------------------------------------------------ */
 
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
-  static const uint32_t sz[3] = {2048, 4096, 8192};
-  if (mapper < 0 || mapper > 2 || rom_size != sz[mapper]) return NULL;
+  static const uint32_t sz[5] = {2048, 4096, 8192, 16384, 32768};
+  if (mapper < 0 || mapper > 4 || rom_size != sz[mapper]) return NULL;
   ovcs* s = (ovcs*)calloc(1, sizeof(ovcs));
   s->rom = (uint8_t*)malloc(rom_size);
   memcpy(s->rom, rom, rom_size);
@@ -993,7 +995,7 @@ void ovcs_reset(ovcs* s) {
   s->cyc = 0;
   s->jammed = 0;
   memset(s->ram, 0, sizeof s->ram);
-  s->bank = s->mapper == 2 ? 1 : 0;
+  s->bank = s->mapper >= 2 ? (int)(s->rom_size / 4096) - 1 : 0;   /* banked carts: the last bank */
   s->intim = 0;
   s->interval = 1024;
   s->phase = 0;

@@ -55,7 +55,9 @@ typedef struct {
   uint64_t relaxed_reads, relaxed_reads_exact, branches, branches_exact;
 } ovcs_counters;
 
-/* mapper: 0 = 2K, 1 = 4K, 2 = F8.  rom is copied.  NULL on a bad size. */
+/* mapper: 0 = 2K, 1 = 4K, 2 = F8 (8 KB, hotspots $1FF8-9), 3 = F6 (16 KB,
+ * $1FF6-9), 4 = F4 (32 KB, $1FF4-B): any access to hotspot j selects 4 KB
+ * bank j.  rom is copied.  NULL on a bad size. */
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart);
 void ovcs_free(ovcs* s);
 /* Power-on state (A7 of the design notes). */

@@ -26,8 +26,11 @@ import numpy as np
 MASK64 = (1 << 64) - 1
 GAMMA = 0x9E3779B97F4A7C15
 
-MAPPER_2K, MAPPER_4K, MAPPER_F8 = 0, 1, 2
-MAPPER_SIZE = {MAPPER_2K: 2048, MAPPER_4K: 4096, MAPPER_F8: 8192}
+MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_F6, MAPPER_F4 = 0, 1, 2, 3, 4
+MAPPER_SIZE = {MAPPER_2K: 2048, MAPPER_4K: 4096, MAPPER_F8: 8192, MAPPER_F6: 16384, MAPPER_F4: 32768}
+# banked mappers: number of 4 KB banks and the first hotspot (bank j at hot + j)
+MAPPER_BANKS = {MAPPER_F8: 2, MAPPER_F6: 4, MAPPER_F4: 8}
+MAPPER_HOTSPOT = {MAPPER_F8: 0x1FF8, MAPPER_F6: 0x1FF6, MAPPER_F4: 0x1FF4}
 
 # ALE action order (18 actions) and their joystick components
 # (right, left, down, up, fire).
@@ -634,7 +637,7 @@ def _emit_table(a: Asm, r: SplitMix64):
 
 
 def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
-    """Seed -> ROM image (2048, 4096 or 8192 bytes) of a well-formed frame loop.
+    """Seed -> ROM image (2048, 4096, 8192, 16384 or 32768 bytes) of a well-formed frame loop.
 
     Layout: reset vector -> init (SEI, CLD, stack, RAM clear, pointers) ->
     frame loop: VSYNC for 3 lines; TIM64T=43 and random work over RAM,
@@ -644,6 +647,8 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     place the visible kernel in bank 0 and switch banks through trampolines
     at the same offsets in both banks.
     """
+    if mapper in (MAPPER_F6, MAPPER_F4):
+        return _generate_multibank(seed, cart, mapper)
     r = SplitMix64(seed, cart, 0x0CA7)
     origin = 0xF800 if mapper == MAPPER_2K else 0xF000
     bank_size = 2048 if mapper == MAPPER_2K else 4096
@@ -774,6 +779,146 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     b.word("IRQ")
     bank0 = b.resolve()
     return bytes(bank0) + bytes(bank1)
+
+
+def _generate_multibank(seed: int, cart: int, mapper: int) -> bytes:
+    """F6 / F4 images: the last bank (where the machine powers on) holds the
+    init, VBLANK and overscan code; each other bank k holds its own visible
+    kernel.  Every frame the main bank picks a kernel bank from the
+    joystick's high nibble and a work cell (low bits; the values past the
+    last kernel bank pick bank 0) and enters it through a
+    trampoline: BIT of hotspot k at offset tramp + 3k, bank k continuing at
+    tramp + 3k + 3 with a JMP to its kernel; bank k returns with BIT of the
+    main bank's hotspot at ret + 3k, the main bank continuing at ret + 3k + 3
+    with a JMP to the overscan."""
+    nb, hot = MAPPER_BANKS[mapper], MAPPER_HOTSPOT[mapper]
+    main = nb - 1
+    bank_size, origin = 4096, 0xF000
+    tramp, ret, stub, irq = bank_size - 0x80, bank_size - 0x60, bank_size - 0x30, bank_size - 0x20
+    r = SplitMix64(seed, cart, 0x0CA7)
+    n_lines, vb_budget, vb_loops, os_budget = 16, 1000, 2, 900
+    a = Asm(origin, bank_size)
+    g = _Gen(r, a)
+    g.emit_subs(4)
+    a.label("RESET")
+    a.op("SEI")
+    a.op("CLD")
+    a.op("LDX", "imm", 0xFF)
+    a.op("TXS")
+    a.op("LDA", "imm", 0)
+    a.op("LDX", "imm", 0x7F)
+    a.label("CLR")
+    a.op("STA", "zpx", 0x80)
+    a.op("DEX")
+    a.op("BPL", "rel", "CLR")
+    a.op("LDA", "imm", RAM_PTR_TARGET & 0xFF)
+    a.op("STA", "zp", RAM_PTR)
+    a.op("LDA", "imm", RAM_PTR_TARGET >> 8)
+    a.op("STA", "zp", RAM_PTR + 1)
+    a.op("LDA", "imm", ("<", "TABLE"))
+    a.op("STA", "zp", ROM_PTR)
+    a.op("LDA", "imm", (">", "TABLE"))
+    a.op("STA", "zp", ROM_PTR + 1)
+    for _ in range(r.range(4, 10)):
+        a.op("LDA", "imm", r.below(256))
+        a.op("STA", "zp", g.work_cell())
+    for reg in (COLUP0, COLUPF, COLUBK):
+        a.op("LDA", "imm", r.below(256))
+        a.op("STA", "zp", reg)
+    a.op("LDA", "imm", r.pick((0, 1, 4, 5)))
+    a.op("STA", "zp", CTRLPF)
+    a.label("FRAME")
+    a.op("LDA", "imm", 2)
+    a.op("STA", "zp", VBLANK)
+    a.op("STA", "zp", WSYNC)
+    a.op("STA", "zp", VSYNC)
+    for _ in range(3):
+        a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 0)
+    a.op("STA", "zp", VSYNC)
+    a.op("LDA", "imm", VBLANK_TIMER)
+    a.op("STA", "abs", TIM64T)
+    a.op("LDA", "imm", vb_loops)
+    a.op("STA", "zp", WORK_CTR)
+    a.label("VBL")
+    a.op("JSR", "abs", "VBWORK")
+    a.op("DEC", "zp", WORK_CTR)
+    a.op("BNE", "rel", "VBL")
+    a.label("VBWAIT")
+    a.op("LDA", "abs", INTIM)
+    a.op("BNE", "rel", "VBWAIT")
+    a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 0)
+    a.op("STA", "zp", VBLANK)
+    # pick this frame's kernel bank from the joystick and a work cell
+    a.op("LDA", "abs", SWCHA)
+    for _ in range(4):
+        a.op("LSR", "acc")
+    a.op("EOR", "zp", WORK_LO)
+    a.op("AND", "imm", 7 if nb == 8 else 3)
+    for k in range(1, nb - 1):
+        a.op("CMP", "imm", k)
+        a.op("BNE", "rel", f"SEL{k}")
+        a.op("JMP", "abs", origin + tramp + 3 * k)
+        a.label(f"SEL{k}")
+    a.op("JMP", "abs", origin + tramp)
+    a.label("OVERSCAN")
+    a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 2)
+    a.op("STA", "zp", VBLANK)
+    a.op("LDA", "imm", OVERSCAN_TIMER)
+    a.op("STA", "abs", TIM64T)
+    a.cycles = 0
+    g.random_work(os_budget)
+    a.label("OSWAIT")
+    a.op("LDA", "abs", INTIM)
+    a.op("BNE", "rel", "OSWAIT")
+    a.op("JMP", "abs", "FRAME")
+    a.label("VBWORK")
+    a.cycles = 0
+    g.random_work(vb_budget)
+    a.op("RTS")
+    g.emit_ptrs()
+    _emit_table(a, r)
+    for k in range(nb - 1):
+        a.at(tramp + 3 * k)
+        a.op("BIT", "abs", hot + k)
+    for k in range(nb - 1):
+        a.at(ret + 3 * k + 3)
+        a.op("JMP", "abs", "OVERSCAN")
+    a.at(stub + 3)
+    a.op("JMP", "abs", "RESET")
+    a.at(irq)
+    a.label("IRQ")
+    a.op("RTI")
+    a.at(bank_size - 6)
+    a.word("IRQ")
+    a.word("RESET")
+    a.word("IRQ")
+    banks = {main: bytes(a.resolve())}
+    for k in range(nb - 1):
+        b = Asm(origin, bank_size)
+        gk = _Gen(SplitMix64(seed, cart, 0x0CA8 + k), b)
+        b.label("KERNEL")
+        _emit_kernel(b, gk, n_lines, "RET")
+        _emit_table(b, gk.r)
+        b.at(tramp + 3 * k + 3)
+        b.op("JMP", "abs", "KERNEL")
+        b.at(ret + 3 * k)
+        b.label("RET")
+        b.op("BIT", "abs", hot + main)
+        b.at(stub)
+        b.label("STUB")
+        b.op("BIT", "abs", hot + main)
+        b.at(irq)
+        b.label("IRQ")
+        b.op("RTI")
+        b.at(bank_size - 6)
+        b.word("IRQ")
+        b.word("STUB")
+        b.word("IRQ")
+        banks[k] = bytes(b.resolve())
+    return b"".join(banks[k] for k in range(nb))
 
 
 def config_carts(seed: int, mappers) -> list:

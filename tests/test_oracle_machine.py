@@ -156,6 +156,62 @@ def test_f8_switches_only_on_hotspots():
     assert o.bank() == 1
 
 
+@pytest.mark.parametrize("mapper", [synth.MAPPER_F6, synth.MAPPER_F4])
+def test_f6_f4_hotspots_select_each_bank(mapper):
+    """Power-on in the last bank; a read or write of hotspot j selects bank
+    j (reads in even banks, writes in odd ones), the neighbours of the
+    hotspot range and the range's image below A12 select nothing.  Bank j
+    holds at offset 3 j the access to hotspot j + 1, so the chain visits
+    every bank in order and wraps back to the last."""
+    nb, hot = synth.MAPPER_BANKS[mapper], synth.MAPPER_HOTSPOT[mapper]
+    banks = []
+    for j in range(nb):
+        a = synth.Asm(0xF000, 4096)
+        if j == nb - 1:
+            a.op("LDA", "abs", hot - 1)            # below the range
+            a.op("LDA", "abs", hot + nb)           # above it
+            a.op("LDA", "abs", hot - 0x1000)       # A12 = 0: not the cartridge
+            a.op("LDA", "abs", hot)                # -> bank 0 at offset 12
+        else:
+            a.at(12 + 3 * j)
+            target = hot + j + 1
+            if j % 2:
+                a.op("STA", "abs", target)
+            else:
+                a.op("LDA", "abs", target)
+        a.at(4096 - 6)
+        a.word(0xF000), a.word(0xF000), a.word(0xF000)
+        banks.append(bytes(a.resolve()))
+    o = oracle.Oracle(b"".join(banks), mapper)
+    assert o.bank() == nb - 1
+    for _ in range(3):
+        o.exec_one()
+        assert o.bank() == nb - 1
+    for j in range(nb):
+        o.exec_one()
+        assert o.bank() == j, j
+        assert o.state()[5] == 0xF000 + 12 + 3 * j
+
+
+def test_f6_f4_carts_visit_their_banks():
+    """The generated F6 / F4 carts run frames of a few thousand instructions
+    (no jam, no watchdog) and enter several kernel banks under random
+    joystick input."""
+    for mapper in (synth.MAPPER_F6, synth.MAPPER_F4):
+        rom = synth.config_carts(17, [mapper])[0]
+        assert len(rom) == synth.MAPPER_SIZE[mapper]
+        o = oracle.Oracle(rom, mapper)
+        seen = set()
+        for a in synth.actions(18, 1, 40)[:, 0]:
+            for _ in range(600):
+                o.trace(int(a), 1)
+                seen.add(int(o.state()[8]))
+        c = o.counters()
+        assert c["watchdog"] == 0 and o.state()[28] == 0
+        assert 1500 < c["instructions"] / c["frames"] < 4000
+        assert len(seen) >= 3 and synth.MAPPER_BANKS[mapper] - 1 in seen
+
+
 # ---------------------------------------------------------------------------
 # pixels
 # ---------------------------------------------------------------------------
