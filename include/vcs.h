@@ -53,7 +53,11 @@ typedef enum {
 /* Cartridge mappers (the 2K, 4K and F8 formats of the paper's per-game
  * conformance table, supplement).  F8 = 8 KB in two 4 KB banks, selected by
  * any access to $1FF8 (bank 0) or $1FF9 (bank 1); power-on selects bank 1. */
-enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2 };
+/* Cartridge formats: 2K and 4K images; F8 (8 KB), F6 (16 KB) and F4 (32 KB)
+ * bank-switched in 4 KB banks, an access (read or write) to hotspot j
+ * ($1FF8 + j for F8, $1FF6 + j for F6, $1FF4 + j for F4) selecting bank j,
+ * power-on in the last bank. */
+enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2, VCS_MAPPER_F6 = 3, VCS_MAPPER_F4 = 4 };
 
 /* Per-env status bits reported by vcs_step / vcs_rollout. */
 enum {
@@ -66,7 +70,7 @@ enum {
 #define VCS_SCREEN_H 210
 #define VCS_SCREEN_W 160
 #define VCS_RAM 128
-#define VCS_ROM_MAX 8192
+#define VCS_ROM_MAX 32768
 
 typedef struct vcs_config {
   float alpha;              /* branch-gate sharpness (Eq. branch), default 6 */
@@ -136,7 +140,8 @@ vcs_status vcs_config_default(vcs_config* cfg);
 /* Create a batch of n_envs machines over n_carts cartridges (Section 2.2;
  * "ROM as a weight tensor", Section 3.1).
  *  roms[c]      host pointer to cart c's image (rom_sizes[c] bytes: 2048,
- *               4096 or 8192 for mapper 2K, 4K, F8); copied.
+ *               4096, 8192, 16384 or 32768 for mapper 2K, 4K, F8, F6, F4);
+ *               copied.
  *  mappers[c]   VCS_MAPPER_* of cart c.
  *  env_cart     host int32[n_envs]: the cart of each env (0..n_carts-1).
  *  cfg          nullable (defaults).
@@ -153,6 +158,12 @@ vcs_status vcs_destroy(vcs_batch* b);
 const char* vcs_last_error(const vcs_batch* b);
 vcs_status vcs_batch_info(const vcs_batch* b, int32_t* n_envs, int32_t* n_carts,
                           int32_t* envs_per_block);
+/* *rom_stride = the floats (bytes) per cart of the ROM tensors of the soft
+ * API (rom_f32, grad_rom, grad_rom_per_cart): the batch's largest image,
+ * at least 8192 (so 8192 unless it holds an F6 or F4 cart).  Byte i of
+ * cart c's tensor row is image byte i (2K images: bytes 0..2047); the rest
+ * of the row is padding (zero gradient). */
+vcs_status vcs_rom_stride(const vcs_batch* b, int32_t* rom_stride);
 
 /* Per-env episode lengths in frames for auto-reset: ep_len is a host
  * uint32[n_envs][n_episodes]; env e's k-th episode ends at the end of the
@@ -327,7 +338,7 @@ vcs_status vcs_sync(vcs_batch* b, void* stream);
  *
  * vcs_soft_rollout: n_steps env-steps from the batch's current state, like
  * vcs_rollout, with the inputs of the relaxation as floats:
- *   rom_f32  device float[n_carts][8192] (nullable: the batch's ROMs) - the
+ *   rom_f32  device float[n_carts][rom_stride] (nullable: the batch's ROMs) - the
  *            ROM as a weight tensor; the forward uses round(value) clamped
  *            to 0..255 (2K images use bytes 0..2047);
  *   ram0     device float[n_envs][128] (nullable: the current RAM) - the RAM
@@ -347,10 +358,10 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
 
 /* Surrogate gradients of L = sum grad_ram . ram_out + sum grad_screen .
  * screen_out (or of the broadcast loss weights `w`) with respect to
- *   grad_rom           device float[n_envs][8192] per env (nullable)
+ *   grad_rom           device float[n_envs][rom_stride] per env (nullable)
  *   grad_ram0          device float[n_envs][128] (nullable)
  *   grad_u             device float[n_steps][n_envs][5] (nullable)
- *   grad_rom_per_cart  device float[n_carts][8192] summed over each cart's
+ *   grad_rom_per_cart  device float[n_carts][rom_stride] summed over each cart's
  *                      envs (nullable)
  * grad_ram [n_steps][n_envs][128] and grad_screen [n_steps][n_envs][210][160]
  * are device pointers (each nullable); give either those or `w`.  The pass

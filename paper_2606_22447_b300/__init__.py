@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import ENV_DONE, ENV_JAMMED, ENV_WATCHDOG, Config, VcsError
-from .synth import MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_SIZE
+from .synth import MAPPER_2K, MAPPER_4K, MAPPER_F4, MAPPER_F6, MAPPER_F8, MAPPER_SIZE
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 
@@ -87,6 +87,9 @@ class Batch:
         epb = C.c_int32()
         L.vcs_batch_info(self.h, None, None, C.byref(epb))
         self.envs_per_block = epb.value
+        rs = C.c_int32()
+        L.vcs_rom_stride(self.h, C.byref(rs))
+        self.rom_stride = rs.value   # floats per cart row of the soft API's ROM tensors
 
     def close(self):
         if getattr(self, "h", None):

@@ -54,6 +54,7 @@ SIGNATURES = {
     "vcs_create_batch": (C.c_int, [C.POINTER(u8p), C.POINTER(C.c_uint32), u8p, i32,
                                    C.POINTER(C.c_int32), i32, C.POINTER(Config), C.POINTER(vp)]),
     "vcs_destroy": (C.c_int, [vp]),
+    "vcs_rom_stride": (C.c_int, [vp, C.POINTER(i32)]),
     "vcs_full_divergence": (C.c_int, [vp, C.c_float, C.c_float, vp, i32, vp, vp, vp, vp]),
     "vcs_last_error": (C.c_char_p, [vp]),
     "vcs_batch_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),

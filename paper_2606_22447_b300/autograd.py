@@ -1,7 +1,7 @@
 """torch.autograd wrapper of the SOFT-STE rollout (vcs_soft_rollout /
 vcs_backward through the C ABI).
 
-Inputs: the ROM as a weight tensor [n_carts][8192], the RAM at the start of
+Inputs: the ROM as a weight tensor [n_carts][batch.rom_stride], the RAM at the start of
 the rollout [n_envs][128] and the joystick inputs [n_steps][n_envs][5]
 (right, left, down, up, fire).  Outputs: RAM [n_steps][n_envs][128] and
 screens [n_steps][n_envs][210][160], equal to the hard machine's (Theorem 1).

@@ -56,7 +56,8 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.blocks = b->blocks;
   p.perm = b->perm;
   p.roms = b->roms;
-  p.cart_f8 = b->cart_f8;
+  p.cart_banks = b->cart_banks;
+  p.rom_stride = b->rom_stride;
   p.dt = b->dt;
   p.ystart = b->cfg.ystart;
   p.err = b->err;
@@ -138,7 +139,7 @@ static void free_batch(vcs_batch* b) {
   if (!b) return;
   cudaFree(b->state);
   cudaFree(b->roms);
-  cudaFree(b->cart_f8);
+  cudaFree(b->cart_banks);
   cudaFree(b->cart_2k);
   cudaFree(b->env_cart_dev);
   cudaFree(b->cart_begin);
@@ -186,6 +187,12 @@ vcs_status vcs_config_default(vcs_config* cfg) {
 
 const char* vcs_last_error(const vcs_batch* b) { return b ? b->last_error.c_str() : g_create_error.c_str(); }
 
+vcs_status vcs_rom_stride(const vcs_batch* b, int32_t* rom_stride) {
+  if (!b || !rom_stride) return VCS_ERR_ARG;
+  *rom_stride = (int32_t)b->rom_stride;
+  return VCS_OK;
+}
+
 vcs_status vcs_batch_info(const vcs_batch* b, int32_t* n_envs, int32_t* n_carts, int32_t* epb) {
   if (!b) return VCS_ERR_ARG;
   if (n_envs) *n_envs = b->n_envs;
@@ -208,14 +215,16 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if (!roms || !rom_sizes || !mappers || !env_cart)
     return vcs_fail(nullptr, VCS_ERR_ARG, "null roms / rom_sizes / mappers / env_cart");
   if (n_carts <= 0 || n_envs <= 0) return vcs_fail(nullptr, VCS_ERR_ARG, "n_carts and n_envs must be positive");
-  static const uint32_t want[3] = {2048, 4096, 8192};
+  static const uint32_t want[5] = {2048, 4096, 8192, 16384, 32768};
+  uint32_t rom_stride = 8192;   // the largest image, at least 8 KB
   for (int c = 0; c < n_carts; c++) {
-    if (mappers[c] > VCS_MAPPER_F8)
+    if (mappers[c] > VCS_MAPPER_F4)
       return vcs_fail(nullptr, VCS_ERR_MAPPER, "cart %d: unknown mapper %d", c, mappers[c]);
     if (rom_sizes[c] != want[mappers[c]])
       return vcs_fail(nullptr, VCS_ERR_ROM_SIZE, "cart %d: %u bytes for mapper %d (want %u)", c, rom_sizes[c],
                       mappers[c], want[mappers[c]]);
     if (!roms[c]) return vcs_fail(nullptr, VCS_ERR_ARG, "cart %d: null ROM", c);
+    rom_stride = std::max(rom_stride, rom_sizes[c]);
   }
   for (int e = 0; e < n_envs; e++)
     if (env_cart[e] < 0 || env_cart[e] >= n_carts)
@@ -278,18 +287,19 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   b->sched_policy = (uint32_t)b->cfg.sched_policy;
   b->sched_window = b->cfg.sched_window < 0 ? 0xFFFFFFFFu : (uint32_t)b->cfg.sched_window;
 
-  // device images: 2K mirrored into 4 KB, F8 as two banks
-  std::vector<uint8_t> img((size_t)n_carts * 8192, 0);
-  std::vector<uint8_t> f8(n_carts), is2k(n_carts);
+  // device images: 2K mirrored into 4 KB, bank-switched carts as their banks
+  b->rom_stride = rom_stride;
+  std::vector<uint8_t> img((size_t)n_carts * rom_stride, 0);
+  std::vector<uint8_t> banks(n_carts), is2k(n_carts);
   for (int c = 0; c < n_carts; c++) {
-    uint8_t* d = img.data() + (size_t)c * 8192;
+    uint8_t* d = img.data() + (size_t)c * rom_stride;
     if (mappers[c] == VCS_MAPPER_2K) {
       memcpy(d, roms[c], 2048);
       memcpy(d + 2048, roms[c], 2048);
     } else {
       memcpy(d, roms[c], rom_sizes[c]);
     }
-    f8[c] = mappers[c] == VCS_MAPPER_F8;
+    banks[c] = mappers[c] >= VCS_MAPPER_F8 ? (uint8_t)(rom_sizes[c] / 4096) : 0;
     is2k[c] = mappers[c] == VCS_MAPPER_2K;
   }
   std::vector<int32_t> cart_begin(n_carts + 1, 0);
@@ -301,7 +311,7 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   cudaError_t e;
   const size_t nst = (size_t)kStateWords * n_envs * sizeof(uint32_t);
   if ((e = cudaMalloc(&b->state, nst)) || (e = cudaMalloc(&b->roms, img.size())) ||
-      (e = cudaMalloc(&b->cart_f8, n_carts)) || (e = cudaMalloc(&b->dt, sizeof(DecodeTables))) ||
+      (e = cudaMalloc(&b->cart_banks, n_carts)) || (e = cudaMalloc(&b->dt, sizeof(DecodeTables))) ||
       (e = cudaMalloc(&b->err, sizeof(int32_t))) ||
       (e = cudaMalloc(&b->cart_2k, n_carts)) || (e = cudaMalloc(&b->env_cart_dev, n_envs * sizeof(int32_t))) ||
       (e = cudaMalloc(&b->cart_begin, (n_carts + 1) * sizeof(int32_t)))) {
@@ -310,7 +320,7 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     return st;
   }
   if ((e = cudaMemcpy(b->roms, img.data(), img.size(), cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(b->cart_f8, f8.data(), n_carts, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->cart_banks, banks.data(), n_carts, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->dt, &dt, sizeof dt, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->cart_2k, is2k.data(), n_carts, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(b->env_cart_dev, env_cart, n_envs * sizeof(int32_t), cudaMemcpyHostToDevice)) ||

@@ -16,8 +16,9 @@ struct vcs_batch {
   std::vector<uint32_t> rom_size;
   // device memory owned by the batch
   uint32_t* state = nullptr;      // kStateWords x n_envs
-  uint8_t* roms = nullptr;        // n_carts x 8192
-  uint8_t* cart_f8 = nullptr;
+  uint8_t* roms = nullptr;        // n_carts x rom_stride
+  uint32_t rom_stride = 8192;     // bytes per cart image: the largest image, at least 8 KB
+  uint8_t* cart_banks = nullptr;  // 4 KB banks of each bank-switched cart, else 0
   uint8_t* cart_2k = nullptr;
   int32_t* env_cart_dev = nullptr;
   int32_t* cart_begin = nullptr;  // [n_carts + 1] first perm slot of each cart

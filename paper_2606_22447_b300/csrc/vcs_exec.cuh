@@ -103,7 +103,7 @@ __device__ __forceinline__ uint32_t relaxed_byte(const FullParams& fp, int32_t M
 // The ROM tensor is the cart image (2K) or the current 4K bank.
 __device__ __forceinline__ uint32_t rom_relaxed(const Ctx& c, const Regs& r, uint32_t addr) {
   const int32_t M = c.fp->rom_m;
-  const uint32_t base = c.f8 ? (r.bank << 12) : 0u;
+  const uint32_t base = r.bank << 12;
   return relaxed_byte(*c.fp, M, (int32_t)(addr & (uint32_t)(M - 1)), [&](int32_t k) { return (uint32_t)c.rom[base | (uint32_t)k]; });
 }
 __device__ __forceinline__ uint32_t ram_relaxed(const Ctx& c, uint32_t addr) {
@@ -121,12 +121,12 @@ __device__ __forceinline__ uint32_t cast_read(Regs& r, uint32_t exact, uint32_t 
 // One bus read at cycle index idx of the current instruction, for any
 // address.  Every source is read and the result selected, which costs fewer
 // cycles than branching on the address region.  Side effects: a read of an
-// F8 hotspot switches the bank, and a read of INTIM records whether the timer
+// bank-switch hotspot switches the bank, and a read of INTIM records whether the timer
 // had underflowed (r.intim_live, kept by the soft path's tape).
 template <int FM = 0>
 __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& st, uint32_t addr, int idx) {
   const uint32_t a = addr & 0x1FFF;
-  r.bank = (c.f8 && (a & 0x1FFE) == 0x1FF8) ? (a & 1) : r.bank;
+  r.bank = a - c.hot < c.nb ? a - c.hot : r.bank;   // bank-switch hotspots
   const uint32_t vrom = c.rom[(r.bank << 12) | (a & 0xFFF)];
   const uint32_t vram = ram_rd(c, a);
   const uint32_t q = a & 0xF;
@@ -164,7 +164,7 @@ template <class Tape>
 __device__ __forceinline__ void bus_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t addr,
                                           uint32_t v, int idx) {
   const uint32_t a = addr & 0x1FFF;
-  r.bank = (c.f8 && (a & 0x1FFE) == 0x1FF8) ? (a & 1) : r.bank;
+  r.bank = a - c.hot < c.nb ? a - c.hot : r.bank;   // bank-switch hotspots
   if ((a & 0x1080) == 0) {   // TIA
     tia_write(c, r, rd, st, tape, a & 0x3F, v & 0xFF, r.fc + idx + st.stall);
     return;
@@ -529,7 +529,7 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
 // at run time from the decode tables.  Real programs seldom execute them,
 // so one compact handler serves all of them: specialised handlers for each
 // would add instruction-cache pressure to every other instruction.  A NOP's
-// operand read has no effect but an F8 hotspot's bank switch (page-zero
+// operand read has no effect but a hotspot's bank switch (page-zero
 // reads and INTIM reads change nothing), so NOPs read nothing.
 template <int FM = 0>
 __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint32_t op, uint32_t opaddr,
@@ -581,7 +581,7 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
     p.wv = r.A & r.X;
   } else if (mode == AM_ABS || mode == AM_ABX) {   // NOP abs / abs,X: only a hotspot read matters
     if constexpr (FM >= 1) (void)bus_read<FM>(c, r, st, ea, (int)n);   // the read is a cast to count
-    else r.bank = (c.f8 && (ea & 0x1FFE) == 0x1FF8) ? (ea & 1) : r.bank;
+    else r.bank = (ea & 0x1FFF) - c.hot < c.nb ? (ea & 0x1FFF) - c.hot : r.bank;
   } else if (FM >= 1 && (mode == AM_ZP || mode == AM_ZPX)) {
     (void)zp_read<FM>(c, r, ea);
   }
@@ -595,14 +595,14 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
 // Instruction bytes at the program counter, fetched ahead: opcode | first
 // operand << 8 | second operand << 16, or kSlowFetch when the bytes must be
 // read through the bus at execution time (outside the cartridge window, near
-// its end or the F8 hotspots).  Fetching from the cartridge has no side
+// its end or the bank-switch hotspots).  Fetching from the cartridge has no side
 // effect and does not depend on time, so it may happen as soon as the
 // program counter and bank are known.
 constexpr uint32_t kSlowFetch = 1u << 24;
 
 __device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
   const uint32_t off = r.PC & 0xFFF;
-  const bool fast = (r.PC & 0x1000) != 0 && off <= 0xFF5;
+  const bool fast = (r.PC & 0x1000) != 0 && off <= 0xFF1;   // no hotspot ($1FF4 on) among the three bytes
   const uint8_t* q = c.rom + ((r.bank << 12) | (fast ? off : 0u));
   return (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) | (fast ? 0u : kSlowFetch);
 }
@@ -677,7 +677,7 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
       bus_write(c, r, rd, st, tape, addr, (p.wv >> (8 * i)) & 0xFF, (int)(p.widx + i));
     } while (++i < p.nw);
   }
-  if (p.rec) tape.rec(op, p.tref, p.tfl | (r.bank << 1) | (r.intim_live << 2));
+  if (p.rec) tape.rec(op, p.tref, p.tfl | (r.intim_live << 1) | (r.bank << 2));
   r.cyc += p.n + (uint32_t)st.stall;
   r.fc += (int32_t)p.n + st.stall;
   st.stall = 0;

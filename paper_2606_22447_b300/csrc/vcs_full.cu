@@ -28,8 +28,9 @@ struct FullDivParams {
   const int4* blocks;
   const int32_t* perm;
   const uint8_t* roms;
-  const uint8_t* cart_f8;
+  const uint8_t* cart_banks;
   const uint8_t* cart_2k;
+  uint32_t rom_stride;
   const DecodeTables* dt;
   const uint8_t* actions;   // [n_envs] ALE actions held for the whole run, or null (NOOP)
   int32_t n_instr;
@@ -40,8 +41,8 @@ struct FullDivParams {
   int32_t* err;
 };
 
-__host__ __device__ constexpr size_t full_smem_bytes(int E) {
-  return smem_bytes(E) + (size_t)32 * 4 * E + sizeof(FullParams);
+__host__ __device__ constexpr size_t full_smem_bytes(int E, uint32_t rom_stride) {
+  return smem_bytes(E, rom_stride) + (size_t)32 * 4 * E + sizeof(FullParams);
 }
 
 __device__ __forceinline__ bool machines_differ(const Ctx& ch, const Regs& a, const Ctx& cf, const Regs& b) {
@@ -71,24 +72,24 @@ __device__ __forceinline__ void full_slot(const Ctx& c, Regs& r, Render& rd, Ste
 __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x, slot = threadIdx.x;
-  BlockSmem bs = carve_smem(smem, E);
-  uint32_t* ram_f = reinterpret_cast<uint32_t*>(smem + smem_bytes(E));   // the FULL machine's RAM [32][E]
+  BlockSmem bs = carve_smem(smem, E, p.rom_stride);
+  uint32_t* ram_f = reinterpret_cast<uint32_t*>(smem + smem_bytes(E, p.rom_stride));   // the FULL machine's RAM [32][E]
   FullParams* fp = reinterpret_cast<FullParams*>(ram_f + 32 * E);
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t f8 = p.cart_f8[cart];
+  const uint32_t nb = p.cart_banks[cart];
   if (slot == 0) {
     *fp = fp0;
     fp->rom_m = p.cart_2k[cart] ? 2048 : 4096;
   }
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * 8192, f8 ? 8192u : 4096u)) {   // synchronises the block
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {   // synchronises the block
     if (slot == 0) atomicExch(p.err, 1);
     return;
   }
   if (slot >= bi.z) return;
   const int env = p.perm[bi.y + slot];
   const int n = p.n_envs;
-  Ctx ch = make_ctx(bs, E, slot, 0, 1, f8, p.ystart);
+  Ctx ch = make_ctx(bs, E, slot, 0, 1, nb, p.ystart);
   ch.fp = fp;
   Ctx cf = ch;
   cf.ram = reinterpret_cast<uint8_t*>(ram_f + slot);
@@ -160,7 +161,8 @@ extern "C" vcs_status vcs_full_divergence(vcs_batch* b, float T, float alpha, co
   p.blocks = b->blocks;
   p.perm = b->perm;
   p.roms = b->roms;
-  p.cart_f8 = b->cart_f8;
+  p.cart_banks = b->cart_banks;
+  p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.dt = b->dt;
   p.actions = actions;
@@ -170,7 +172,7 @@ extern "C" vcs_status vcs_full_divergence(vcs_batch* b, float T, float alpha, co
   p.counts = counts;
   p.ram_full = ram_full;
   p.err = b->err;
-  const size_t smem = full_smem_bytes(b->E);
+  const size_t smem = full_smem_bytes(b->E, b->rom_stride);
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return vcs_cuda_fail(b, e, "FULL kernel shared memory");

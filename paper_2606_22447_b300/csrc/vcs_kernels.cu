@@ -55,11 +55,11 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   // T threads per env (a compile-time constant, so T = 1 carries no replica
   // logic): thread tid is replica tid % T of env slot tid / T
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
-  BlockSmem bs = carve_smem(smem, E);
+  BlockSmem bs = carve_smem(smem, E, p.rom_stride);
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t f8 = p.cart_f8[cart];
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * 8192, f8 ? 8192u : 4096u)) {
+  const uint32_t nb = p.cart_banks[cart];
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
   }
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
-  Ctx c = make_ctx(bs, E, slot, rank, T, f8, p.ystart);
+  Ctx c = make_ctx(bs, E, slot, rank, T, nb, p.ystart);
   const bool lead = rank == 0;   // the replica that writes per-env results
 
   Regs r;
@@ -290,31 +290,39 @@ int launch_int_peak(int sms, int32_t iters, uint32_t* sink, void* stream) {
   return (int)cudaGetLastError();
 }
 
-size_t step_smem_bytes(int E) { return smem_bytes(E); }
+size_t step_smem_bytes(int E, uint32_t rom_stride) { return smem_bytes(E, rom_stride); }
+
+// Launch one specialisation of the step kernel, with the shared memory the
+// batch's ROM stride needs (above the default 48 KB for 16 and 32 KB carts).
+template <class Kern>
+static void launch_kernel(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const StepParams& p) {
+  if (smem > 48u * 1024u) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<grid, block, smem, s>>>(p);
+}
 
 template <bool SOFT>
 static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   if (n_blocks <= 0) return 0;
   const dim3 grid(n_blocks), block(E * p.tpe);
-  const size_t smem = step_smem_bytes(E);
+  const size_t smem = step_smem_bytes(E, p.rom_stride);
   cudaStream_t s = (cudaStream_t)stream;
   // instruction-granular steps draw nothing, so one lane per env serves them
   if (p.step_instr > 0) {
-    k_run<SOFT, 1, false, true><<<grid, dim3(E), smem, s>>>(p);
+    launch_kernel(k_run<SOFT, 1, false, true>, grid, dim3(E), smem, s, p);
     return (int)cudaGetLastError();
   }
   // the boot sequence exists in the hard step kernel only when a batch asks
   // for it, so that default launches carry none of its code
   const bool boot = !SOFT && p.boot_frames;
   switch (p.tpe * 2 + (boot ? 1 : 0)) {
-    case 2: k_run<SOFT, 1, false><<<grid, block, smem, s>>>(p); break;
-    case 4: k_run<SOFT, 2, false><<<grid, block, smem, s>>>(p); break;
-    case 8: k_run<SOFT, 4, false><<<grid, block, smem, s>>>(p); break;
-    case 16: k_run<SOFT, 8, false><<<grid, block, smem, s>>>(p); break;
-    case 3: k_run<false, 1, true><<<grid, block, smem, s>>>(p); break;
-    case 5: k_run<false, 2, true><<<grid, block, smem, s>>>(p); break;
-    case 9: k_run<false, 4, true><<<grid, block, smem, s>>>(p); break;
-    case 17: k_run<false, 8, true><<<grid, block, smem, s>>>(p); break;
+    case 2: launch_kernel(k_run<SOFT, 1, false>, grid, block, smem, s, p); break;
+    case 4: launch_kernel(k_run<SOFT, 2, false>, grid, block, smem, s, p); break;
+    case 8: launch_kernel(k_run<SOFT, 4, false>, grid, block, smem, s, p); break;
+    case 16: launch_kernel(k_run<SOFT, 8, false>, grid, block, smem, s, p); break;
+    case 3: launch_kernel(k_run<false, 1, true>, grid, block, smem, s, p); break;
+    case 5: launch_kernel(k_run<false, 2, true>, grid, block, smem, s, p); break;
+    case 9: launch_kernel(k_run<false, 4, true>, grid, block, smem, s, p); break;
+    case 17: launch_kernel(k_run<false, 8, true>, grid, block, smem, s, p); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

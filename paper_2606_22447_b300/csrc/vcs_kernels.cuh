@@ -10,7 +10,7 @@ namespace vcs {
 // (u32 [n_envs]), so a warp's loads and stores of a field are coalesced.
 struct SoA {
   uint32_t* reg;   // A | X << 8 | Y << 16 | SP << 24
-  uint32_t* pcp;   // PC | P << 16 | bank << 24 | jam << 25
+  uint32_t* pcp;   // PC | P << 16 | bank << 24 (3 bits) | jam << 27
   uint32_t* cyc;   // CPU cycles mod 2^32
   uint32_t* fcs;   // fc | fs << 16
   uint32_t* tw;    // timer write cycle
@@ -31,8 +31,9 @@ struct StepParams {
   int32_t n_envs;
   const int4* blocks;       // per block: {cart, first slot, env count, 0}
   const int32_t* perm;      // slot -> env (envs grouped by cart)
-  const uint8_t* roms;      // [n_carts][8192]; 2K images mirrored to 4 KB
-  const uint8_t* cart_f8;   // [n_carts] 1 = F8
+  const uint8_t* roms;      // [n_carts][rom_stride]; 2K images mirrored to 4 KB
+  const uint8_t* cart_banks;  // [n_carts] 4 KB banks of bank-switched carts (2, 4, 8), else 0
+  uint32_t rom_stride;      // bytes per cart image (8, 16 or 32 KB): also the shared-memory ROM region
   const DecodeTables* dt;
   const uint8_t* actions;   // [n_steps][n_envs] or null (NOOP)
   int32_t n_steps;
@@ -75,7 +76,7 @@ __host__ __device__ inline SoA soa_at(uint32_t* base, int32_t n_envs) {
 }
 
 void build_decode_tables(DecodeTables* t);
-size_t step_smem_bytes(int envs_per_block);
+size_t step_smem_bytes(int envs_per_block, uint32_t rom_stride);
 int launch_int_peak(int sms, int32_t iters, uint32_t* sink, void* stream);
 int launch_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests, uint64_t* out, void* stream);
 // Launch the step kernel over `n_blocks` blocks of `envs_per_block`

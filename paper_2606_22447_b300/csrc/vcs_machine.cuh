@@ -239,6 +239,12 @@ struct FullParams {
   int32_t rom_m;
 };
 
+// First hotspot of a bank-switched cart of nb banks: F8 $1FF8-9, F6
+// $1FF6-9, F4 $1FF4-B; no hotspot for the others.
+__host__ __device__ constexpr uint32_t first_hotspot(uint32_t nb) {
+  return nb == 2 ? 0x1FF8u : nb == 4 ? 0x1FF6u : nb == 8 ? 0x1FF4u : 0xFFFFu;
+}
+
 // Everything a thread needs besides its registers.
 struct Ctx {
   const uint8_t* rom;        // shared: cart image (4 KB, or 8 KB for F8)
@@ -247,7 +253,8 @@ struct Ctx {
   const DecodeTables* dt;    // shared
   uint32_t e4;               // 4 * envs per block
   uint32_t E;                // envs per block
-  uint32_t f8;               // 1 if the cart is F8
+  uint32_t nb;               // 4 KB banks of a bank-switched cart (F8 2, F6 4, F4 8), else 0
+  uint32_t hot;              // its first hotspot: an access to hot + j selects bank j
   int32_t ystart;
   // Threads per env: T lanes run one env's machine in lockstep (identical
   // registers; their identical shared-memory writes coincide) and split the

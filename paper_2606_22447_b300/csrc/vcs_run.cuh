@@ -7,23 +7,26 @@
 
 namespace vcs {
 
-// Shared-memory layout of one block of E envs.
+// Shared-memory layout of one block of E envs; the cartridge image region
+// is the batch's ROM stride (8, 16 or 32 KB: the largest image it holds).
 struct BlockSmem {
-  uint8_t* rom;         // 8192 B cartridge image
+  uint8_t* rom;         // cartridge image (rom_bytes)
   DecodeTables* dt;     // 512 B
   uint64_t* mbar;       // TMA completion barrier
   uint32_t* ram;        // [32][E] words
   uint32_t* line;       // [40][E] words
 };
 
-__host__ __device__ constexpr size_t smem_bytes(int E) { return 8192 + 512 + 16 + (size_t)(32 + 40) * 4 * E; }
+__host__ __device__ constexpr size_t smem_bytes(int E, uint32_t rom_bytes) {
+  return rom_bytes + 512 + 16 + (size_t)(32 + 40) * 4 * E;
+}
 
-__device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E) {
+__device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E, uint32_t rom_bytes) {
   BlockSmem b;
   b.rom = smem;
-  b.dt = reinterpret_cast<DecodeTables*>(smem + 8192);
-  b.mbar = reinterpret_cast<uint64_t*>(smem + 8192 + 512);
-  b.ram = reinterpret_cast<uint32_t*>(smem + 8192 + 512 + 16);
+  b.dt = reinterpret_cast<DecodeTables*>(smem + rom_bytes);
+  b.mbar = reinterpret_cast<uint64_t*>(smem + rom_bytes + 512);
+  b.ram = reinterpret_cast<uint32_t*>(smem + rom_bytes + 512 + 16);
   b.line = b.ram + 32 * E;
   return b;
 }
@@ -67,7 +70,7 @@ __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTabl
 
 // Context of one replica: env slot `slot` of the block (E envs), replica
 // `rank` of T.
-__device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int rank, int T, uint32_t f8,
+__device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int rank, int T, uint32_t nb,
                                         int32_t ystart) {
   Ctx c;
   c.rom = b.rom;
@@ -76,7 +79,8 @@ __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int
   c.dt = b.dt;
   c.e4 = 4u * (uint32_t)E;
   c.E = (uint32_t)E;
-  c.f8 = f8;
+  c.nb = nb;
+  c.hot = first_hotspot(nb);
   c.ystart = ystart;
   c.rank = (uint32_t)rank;
   c.T = (uint32_t)T;
@@ -92,8 +96,8 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
   v = s.pcp[e];
   r.PC = v & 0xFFFF;
   unpack_p(r, (v >> 16) & 0xFF);
-  r.bank = (v >> 24) & 1;
-  r.jam = (v >> 25) & 1;
+  r.bank = (v >> 24) & 7;
+  r.jam = (v >> 27) & 1;
   r.cyc = s.cyc[e];
   v = s.fcs[e];
   r.fc = (int32_t)(v & 0xFFFF);
@@ -117,7 +121,7 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
 
 __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx& c, const Regs& r) {
   s.reg[e] = r.A | (r.X << 8) | (r.Y << 16) | (r.SP << 24);
-  s.pcp[e] = r.PC | (pack_p(r) << 16) | (r.bank << 24) | (r.jam << 25);
+  s.pcp[e] = r.PC | (pack_p(r) << 16) | (r.bank << 24) | (r.jam << 27);
   s.cyc[e] = r.cyc;
   s.fcs[e] = ((uint32_t)r.fc & 0xFFFF) | (r.fs << 16);
   s.tw[e] = r.tw;
@@ -131,13 +135,13 @@ __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx&
 }
 
 // Power-on state: A = X = Y = 0, SP = $FD, P = $34, RAM and TIA zero, timer
-// as if 0 had been written to T1024T at cycle 0, F8 in bank 1, PC from the
-// reset vector.
+// as if 0 had been written to T1024T at cycle 0, banked carts in their last
+// bank, PC from the reset vector.
 __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.A = r.X = r.Y = 0;
   r.SP = 0xFD;
   unpack_p(r, 0x34);
-  r.bank = c.f8 ? 1u : 0u;
+  r.bank = c.nb ? c.nb - 1u : 0u;
   r.jam = 0;
   r.cyc = 0;
   r.fc = 0;

@@ -125,8 +125,9 @@ struct BwdParams {
   int32_t tpe;                // threads per env
   const int4* blocks;
   const int32_t* perm;
-  const uint8_t* roms;        // rounded ROM images of the rollout [n_carts][8192]
-  const uint8_t* cart_f8;
+  const uint8_t* roms;        // rounded ROM images of the rollout [n_carts][rom_stride]
+  const uint8_t* cart_banks;
+  uint32_t rom_stride;
   const uint8_t* cart_2k;
   const DecodeTables* dt;
   const uint32_t* ckpt;       // this segment's checkpoint [kStateWords][n_envs]
@@ -141,7 +142,7 @@ struct BwdParams {
   uint32_t cap_cw;
   uint32_t* step_end;         // [seg_steps][n_envs]
   float* carry;               // [kCarry][n_envs]
-  float* imp;                 // ROM impulses [2][n_envs][8192]: value, compensation
+  float* imp;                 // ROM impulses [2][n_envs][rom_stride]: value, compensation
   float* grad_u;              // [n_steps][n_envs][5] or null
   float* grad_ram0;           // [n_envs][128] or null (segment 0)
   float tau;
@@ -163,12 +164,12 @@ struct Adj {
 // compensated sums (value + compensation), since long rollouts add many
 // terms of both signs into them.
 __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                             const float* izr, int W, float* imp, float* impc, uint32_t f8,
+                                             const float* izr, int W, float* imp, float* impc,
                                              uint32_t is2k, uint32_t ref, uint32_t fl, float g) {
   const uint32_t ad = ref & 0x1FFF;
   if (g == 0.f) return;
   if (ad & 0x1000) {
-    uint32_t idx = is2k ? (ad & 0x7FF) : ((f8 ? ((fl >> 1) & 1u) << 12 : 0u) | (ad & 0xFFF));
+    uint32_t idx = is2k ? (ad & 0x7FF) : ((((fl >> 2) & 7u) << 12) | (ad & 0xFFF));   // the read's bank
     float sv = imp[idx], cv = impc[idx];
     comp_add(sv, cv, g);
     imp[idx] = sv;
@@ -187,7 +188,7 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
       comp_add(a.u[2], a.uc[2], -32.f * g);
       comp_add(a.u[3], a.uc[3], -16.f * g);
     }
-  } else if (!(ad & 1) && (fl & 4)) {
+  } else if (!(ad & 1) && (fl & 2)) {
     a.V += g;
   }
 }
@@ -243,43 +244,43 @@ __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { retur
 
 template <bool SAMPLER>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                            const float* izr, int W, float* imp, float* impc, uint32_t f8,
+                                            const float* izr, int W, float* imp, float* impc,
                                             uint32_t is2k, const float* cw, uint32_t& j, uint32_t rec) {
   const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
   switch (op) {
     case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
       break;
     }
     case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
       float g = a.X;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
       break;
     }
     case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
       float g = a.Y;
       a.Y = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
       break;
     }
     case 0x09: case 0x05: case 0x15: case 0x0D: case 0x1D: case 0x19: case 0x01: case 0x11:
     case 0x29: case 0x25: case 0x35: case 0x2D: case 0x3D: case 0x39: case 0x21: case 0x31:
     case 0x49: case 0x45: case 0x55: case 0x4D: case 0x5D: case 0x59: case 0x41: case 0x51:
     case 0x69: case 0x65: case 0x75: case 0x6D: case 0x7D: case 0x79: case 0x61: case 0x71:
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, a.A);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, a.A);
       break;
     case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
     case 0xEB:                                                      // USBC: SBC's alias
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, -a.A);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, -a.A);
       break;
     case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   // LAX: A = X = M
       float g = a.A + a.X;
       a.A = 0.f;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
@@ -304,7 +305,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
       float g = take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
       break;
     }
     case 0xAA: a.A += a.X; a.X = 0.f; break;   // TAX
@@ -317,7 +318,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x68: {                                                    // PLA
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, f8, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
       break;
     }
     case 0x20:                                                      // JSR: two pushes
@@ -351,25 +352,25 @@ __device__ __forceinline__ void read_tables(float* ek, float* izr, float tau, in
 // Backward shared memory: the step kernel's layout, the RAM adjoints and
 // their compensation [2][128][E], the read tables, then the staged gradient
 // rows (16-byte aligned).
-__host__ __device__ constexpr size_t bwd_row_offset(int E) {
-  return (smem_bytes(E) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
+__host__ __device__ constexpr size_t bwd_row_offset(int E, uint32_t rom_stride) {
+  return (smem_bytes(E, rom_stride) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
 }
 
 template <int T, bool SAMPLER, bool INSTR = false>
 __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
-  BlockSmem bs = carve_smem(smem, E);
-  float* aram_s = reinterpret_cast<float*>(smem + smem_bytes(E));   // [128][E]
+  BlockSmem bs = carve_smem(smem, E, p.rom_stride);
+  float* aram_s = reinterpret_cast<float*>(smem + smem_bytes(E, p.rom_stride));   // [128][E]
   float* aramc_s = aram_s + 128 * E;                                 // [128][E] compensation
   float* ek = aramc_s + 128 * E;                                     // [kMaxW + 1]
   float* izr = ek + (kMaxW + 1);                                     // [128]
-  float4* grow = reinterpret_cast<float4*>(smem + bwd_row_offset(E));  // [40][E] staged gradient rows
+  float4* grow = reinterpret_cast<float4*>(smem + bwd_row_offset(E, p.rom_stride));  // [40][E] staged gradient rows
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t f8 = p.cart_f8[cart], is2k = p.cart_2k[cart];
+  const uint32_t nb = p.cart_banks[cart], is2k = p.cart_2k[cart];
   read_tables(ek, izr, p.tau, p.W);
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * 8192, f8 ? 8192u : 4096u)) {
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
   }
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
-  Ctx c = make_ctx(bs, E, slot, rank, T, f8, p.ystart);
+  Ctx c = make_ctx(bs, E, slot, rank, T, nb, p.ystart);
   float* aram = aram_s + slot;
   float* aramc = aramc_s + slot;
 
@@ -448,8 +449,8 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
     for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
   }
-  float* imp = p.imp + (size_t)env * 8192;
-  float* impc = p.imp + ((size_t)n + env) * 8192;
+  float* imp = p.imp + (size_t)env * p.rom_stride;
+  float* impc = p.imp + ((size_t)n + env) * p.rom_stride;
   const uint4* rec4 = reinterpret_cast<const uint4*>(p.rec + (size_t)env * p.cap_rec);
   const float* cw = p.cw + (size_t)env * p.cap_cw;
   uint32_t j = tape.ncw;
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
       for (uint32_t q = k; q > lo; q--) {
         const uint32_t sl = (q - 1) & 3;
         const uint32_t rv = sl == 0 ? ch.x : (sl == 1 ? ch.y : (sl == 2 ? ch.z : ch.w));
-        reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, imp, impc, f8, is2k, cw, j, rv);
+        reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, imp, impc, is2k, cw, j, rv);
       }
       ch = nx;
       k = lo;
@@ -542,20 +543,24 @@ static void launch_bwd(const BwdParams& p, int n_blocks, int E, int T, size_t sm
   }
 }
 
-size_t bwd_smem_bytes(int E) { return bwd_row_offset(E) + (size_t)40 * 16 * E; }
+size_t bwd_smem_bytes(int E, uint32_t rom_stride) { return bwd_row_offset(E, rom_stride) + (size_t)40 * 16 * E; }
 
 // ROM impulses -> ROM gradient: spread each impulse at a over the read
-// window of its tensor (the 2K image, the 4K image, or one F8 bank) with the
-// relaxed read's weights.  One thread per (env, ROM byte).
-__global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_cart, const uint8_t* cart_f8,
-                             const uint8_t* cart_2k, int32_t n_envs, float tau, int32_t W) {
-  __shared__ float ek[kMaxW + 2];
-  __shared__ float suf[kMaxW + 2];   // suf[k] = sum_{q = k..W} ek[q]
-  for (int k = threadIdx.x; k <= W; k += blockDim.x) ek[k] = expf(-(float)k / tau);
+// window of its tensor (the 2K image, the 4K image, or one 4 KB bank of a
+// bank-switched cart) with the relaxed read's weights.  One thread per (env,
+// ROM byte); rows are rom_stride floats.
+__global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_cart, const uint8_t* cart_banks,
+                             const uint8_t* cart_2k, int32_t n_envs, uint32_t rom_stride, float tau, int32_t W) {
+  // FP64 here: the impulses are compensated float pairs whose sum the spread
+  // must not round before the weights cancel neighbouring terms (a tiny
+  // kernel next to the backward)
+  __shared__ double ek[kMaxW + 2];
+  __shared__ double suf[kMaxW + 2];   // suf[k] = sum_{q = k..W} ek[q]
+  for (int k = threadIdx.x; k <= W; k += blockDim.x) ek[k] = exp(-(double)k / (double)tau);
   __syncthreads();
   if (threadIdx.x == 0) {
-    float acc = 0.f;
-    suf[W + 1] = 0.f;
+    double acc = 0.0;
+    suf[W + 1] = 0.0;
     for (int k = W; k >= 0; k--) {
       acc += ek[k];
       suf[k] = acc;
@@ -564,53 +569,54 @@ __global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_ca
   __syncthreads();
   const int env = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (env >= n_envs || i >= 8192) return;
+  if (env >= n_envs || i >= (int)rom_stride) return;
   const int cart = env_cart[env];
   const int M = cart_2k[cart] ? 2048 : 4096;
-  float* o = out + (size_t)env * 8192;
-  if (i >= (cart_f8[cart] ? 8192 : M)) {
+  float* o = out + (size_t)env * rom_stride;
+  if (i >= (cart_banks[cart] ? (int)cart_banks[cart] * 4096 : M)) {
     o[i] = 0.f;
     return;
   }
   const int base = i & ~(M - 1);
   const int ii = i - base;
-  const float* im = imp + (size_t)env * 8192 + base;
-  const float* imc = imp + ((size_t)n_envs + env) * 8192 + base;
+  const float* im = imp + (size_t)env * rom_stride + base;
+  const float* imc = imp + ((size_t)n_envs + env) * rom_stride + base;
   const int lo = ii - W < 0 ? 0 : ii - W, hi = ii + W > M - 1 ? M - 1 : ii + W;
-  const float zint = ek[0] + 2.f * suf[1];
-  float acc = 0.f;
+  const double zint = ek[0] + 2.0 * suf[1];
+  double acc = 0.0;
   for (int q = lo; q <= hi; q++) {
-    const float v = im[q] + imc[q];
-    if (v == 0.f) continue;
-    float z = zint;
+    const double v = (double)im[q] + (double)imc[q];
+    if (v == 0.0) continue;
+    double z = zint;
     if (q < W) z -= suf[q + 1];
     if (M - 1 - q < W) z -= suf[M - q];
     acc += v * ek[q > ii ? q - ii : ii - q] / z;
   }
-  o[i] = acc;
+  o[i] = (float)acc;
 }
 
 // Per-cart sum of the per-env ROM gradients: envs of cart c are slots
 // cart_begin[c] .. cart_begin[c+1]-1 of perm; a fixed order, no atomics.
 __global__ void k_cart_reduce(const float* grad_rom, float* out, const int32_t* perm, const int32_t* cart_begin,
-                              int32_t n_carts) {
+                              int32_t n_carts, uint32_t rom_stride) {
   const int c = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_carts || i >= 8192) return;
-  float acc = 0.f;
-  for (int s = cart_begin[c]; s < cart_begin[c + 1]; s++) acc += grad_rom[(size_t)perm[s] * 8192 + i];
-  out[(size_t)c * 8192 + i] = acc;
+  if (c >= n_carts || i >= (int)rom_stride) return;
+  double acc = 0.0;   // thousands of envs per cart: FP64 keeps the sum to its last float bit
+  for (int s = cart_begin[c]; s < cart_begin[c + 1]; s++) acc += grad_rom[(size_t)perm[s] * rom_stride + i];
+  out[(size_t)c * rom_stride + i] = (float)acc;
 }
 
 // Rounded ROM bytes from the float ROM tensor (forward value of the STE
 // round), 2K images mirrored into 4 KB like the hard path's copy.
-__global__ void k_rom_round(const float* rom_f32, uint8_t* out, const uint8_t* cart_2k, int32_t n_carts) {
+__global__ void k_rom_round(const float* rom_f32, uint8_t* out, const uint8_t* cart_2k, int32_t n_carts,
+                            uint32_t rom_stride) {
   const int c = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_carts || i >= 8192) return;
+  if (c >= n_carts || i >= (int)rom_stride) return;
   const int src = cart_2k[c] ? (i & 2047) : i;
-  float v = rintf(rom_f32[(size_t)c * 8192 + src]);
-  out[(size_t)c * 8192 + i] = (uint8_t)(v <= 0.f ? 0.f : (v >= 255.f ? 255.f : v));
+  float v = rintf(rom_f32[(size_t)c * rom_stride + src]);
+  out[(size_t)c * rom_stride + i] = (uint8_t)(v <= 0.f ? 0.f : (v >= 255.f ? 255.f : v));
 }
 
 }  // namespace vcs
@@ -684,7 +690,8 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
   const size_t n = (size_t)b->n_envs;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if ((e = cudaMalloc(&t->rom_bytes, (size_t)b->n_carts * 8192)) ||
+  const size_t rs = b->rom_stride;
+  if ((e = cudaMalloc(&t->rom_bytes, (size_t)b->n_carts * rs)) ||
       (e = cudaMalloc(&t->ckpt, (size_t)t->n_seg * kStateWords * n * 4)) ||
       (e = cudaMalloc(&t->act_bits, (size_t)n_steps * n)) ||
       (e = cudaMalloc(&t->seg_counts, (size_t)t->n_seg * 2 * 4))) {
@@ -694,10 +701,10 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
   }
   cudaMemsetAsync(t->seg_counts, 0, (size_t)t->n_seg * 2 * 4, s);
   if (rom_f32) {
-    dim3 grid(8192 / 256, b->n_carts);
-    k_rom_round<<<grid, 256, 0, s>>>(rom_f32, t->rom_bytes, b->cart_2k, b->n_carts);
+    dim3 grid((unsigned)(rs / 256), b->n_carts);
+    k_rom_round<<<grid, 256, 0, s>>>(rom_f32, t->rom_bytes, b->cart_2k, b->n_carts, b->rom_stride);
   } else {
-    cudaMemcpyAsync(t->rom_bytes, b->roms, (size_t)b->n_carts * 8192, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(t->rom_bytes, b->roms, (size_t)b->n_carts * rs, cudaMemcpyDeviceToDevice, s);
   }
   StepParams p = vcs_base_params(b);
   p.roms = t->rom_bytes;
@@ -763,16 +770,16 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   }
   if (!t->step_end) {
     if ((e = cudaMalloc(&t->step_end, (size_t)t->seg_steps * n * 4)) ||
-        (e = cudaMalloc(&t->carry, (size_t)kCarry * n * 4)) || (e = cudaMalloc(&t->imp, 2 * n * 8192 * 4)))
+        (e = cudaMalloc(&t->carry, (size_t)kCarry * n * 4)) || (e = cudaMalloc(&t->imp, 2 * n * b->rom_stride * 4)))
       return vcs_cuda_fail(b, e, "backward scratch");
   }
   float* grom = grad_rom;
   if (!grom && grad_rom_per_cart) {
-    if (!t->grad_rom_tmp && (e = cudaMalloc(&t->grad_rom_tmp, n * 8192 * 4)))
+    if (!t->grad_rom_tmp && (e = cudaMalloc(&t->grad_rom_tmp, n * b->rom_stride * 4)))
       return vcs_cuda_fail(b, e, "backward scratch");
     grom = t->grad_rom_tmp;
   }
-  cudaMemsetAsync(t->imp, 0, 2 * n * 8192 * 4, s);
+  cudaMemsetAsync(t->imp, 0, 2 * n * b->rom_stride * 4, s);
 
   BwdParams p{};
   p.n_envs = b->n_envs;
@@ -786,7 +793,8 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.blocks = bwd_blocks;
   p.perm = b->perm;
   p.roms = t->rom_bytes;
-  p.cart_f8 = b->cart_f8;
+  p.cart_banks = b->cart_banks;
+  p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.dt = b->dt;
   p.act_bits = t->act_bits;
@@ -811,7 +819,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
-  const size_t smem = bwd_smem_bytes(bwd_E);
+  const size_t smem = bwd_smem_bytes(bwd_E, b->rom_stride);
   if ((e = allow_bwd_smem(smem)))
     return vcs_cuda_fail(b, e, "backward shared memory");
   for (int q = t->n_seg - 1; q >= 0; q--) {
@@ -822,14 +830,14 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
   }
   if (grom) {
-    dim3 grid(8192 / 256, b->n_envs);
-    k_rom_spread<<<grid, 256, 0, s>>>(t->imp, grom, b->env_cart_dev, b->cart_f8, b->cart_2k, b->n_envs, t->tau,
-                                      t->W);
+    dim3 grid(b->rom_stride / 256, b->n_envs);
+    k_rom_spread<<<grid, 256, 0, s>>>(t->imp, grom, b->env_cart_dev, b->cart_banks, b->cart_2k, b->n_envs,
+                                      b->rom_stride, t->tau, t->W);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "ROM spread launch");
   }
   if (grad_rom_per_cart) {
-    dim3 grid(8192 / 256, b->n_carts);
-    k_cart_reduce<<<grid, 256, 0, s>>>(grom, grad_rom_per_cart, b->perm, b->cart_begin, b->n_carts);
+    dim3 grid(b->rom_stride / 256, b->n_carts);
+    k_cart_reduce<<<grid, 256, 0, s>>>(grom, grad_rom_per_cart, b->perm, b->cart_begin, b->n_carts, b->rom_stride);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "per-cart reduction launch");
   }
   return VCS_OK;
@@ -913,8 +921,8 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   const size_t o_carry = 0;
   const size_t o_step = align256(o_carry + (size_t)kCarry * n * 4);
   const size_t o_imp = align256(o_step + (size_t)t->seg_steps * n * 4);
-  const size_t o_tmp = align256(o_imp + 2 * n * 8192 * 4);
-  const size_t o_rec = align256(o_tmp + (need_tmp ? n * 8192 * 4 : 0));
+  const size_t o_tmp = align256(o_imp + 2 * n * b->rom_stride * 4);
+  const size_t o_rec = align256(o_tmp + (need_tmp ? n * b->rom_stride * 4 : 0));
   const size_t o_cw = align256(o_rec + cap_rec * n * 4);
   const size_t total = align256(o_cw + cap_cw * n * 4);
   if (total > kStaticScratchBytes)
@@ -927,7 +935,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   float* grom = grad_rom ? grad_rom : (need_tmp ? reinterpret_cast<float*>(sc + o_tmp) : nullptr);
   // the impulses are sums and must start at zero; everything else is
   // written before it is read
-  if ((e = cudaMemsetAsync(imp, 0, 2 * n * 8192 * 4, s))) return vcs_cuda_fail(b, e, "scratch clear");
+  if ((e = cudaMemsetAsync(imp, 0, 2 * n * b->rom_stride * 4, s))) return vcs_cuda_fail(b, e, "scratch clear");
 
   BwdParams p{};
   p.n_envs = b->n_envs;
@@ -941,7 +949,8 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.blocks = bwd_blocks;
   p.perm = b->perm;
   p.roms = t->rom_bytes;
-  p.cart_f8 = b->cart_f8;
+  p.cart_banks = b->cart_banks;
+  p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.dt = b->dt;
   p.act_bits = t->act_bits;
@@ -966,7 +975,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
-  const size_t smem = bwd_smem_bytes(bwd_E);
+  const size_t smem = bwd_smem_bytes(bwd_E, b->rom_stride);
   if ((e = allow_bwd_smem(smem)))
     return vcs_cuda_fail(b, e, "backward shared memory");
   for (int q = t->n_seg - 1; q >= 0; q--) {
@@ -977,13 +986,14 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
   }
   if (grom) {
-    dim3 grid(8192 / 256, b->n_envs);
-    k_rom_spread<<<grid, 256, 0, s>>>(imp, grom, b->env_cart_dev, b->cart_f8, b->cart_2k, b->n_envs, t->tau, t->W);
+    dim3 grid(b->rom_stride / 256, b->n_envs);
+    k_rom_spread<<<grid, 256, 0, s>>>(imp, grom, b->env_cart_dev, b->cart_banks, b->cart_2k, b->n_envs, b->rom_stride,
+                                      t->tau, t->W);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "ROM spread launch");
   }
   if (grad_rom_per_cart) {
-    dim3 grid(8192 / 256, b->n_carts);
-    k_cart_reduce<<<grid, 256, 0, s>>>(grom, grad_rom_per_cart, b->perm, b->cart_begin, b->n_carts);
+    dim3 grid(b->rom_stride / 256, b->n_carts);
+    k_cart_reduce<<<grid, 256, 0, s>>>(grom, grad_rom_per_cart, b->perm, b->cart_begin, b->n_carts, b->rom_stride);
     if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "per-cart reduction launch");
   }
   return VCS_OK;

@@ -33,7 +33,8 @@ def test_single_env_2k_60_frames():
     _check_all([rom], [synth.MAPPER_2K], [0], acts, 1)
 
 
-@pytest.mark.parametrize("mapper", [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8])
+@pytest.mark.parametrize("mapper", [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6,
+                                    synth.MAPPER_F4])
 def test_many_envs_one_cart_ragged(mapper):
     rom = synth.generate_cart(202, 1, mapper)
     n_envs = 75      # several blocks and a ragged tail
@@ -46,6 +47,58 @@ def test_mixed_carts_unsorted_envs():
     env_cart = np.random.default_rng(3).permutation(np.arange(96) % 16).astype(np.int32)
     acts = synth.actions(303, 96, 5)
     _check_all(roms, synth.MIX16, env_cart, acts, 2)
+
+
+@pytest.mark.parametrize("epb,tpe", [(16, 1), (128, 1), (32, 4)])
+def test_all_five_mappers_in_one_batch(epb, tpe):
+    """2K, 4K, F8, F6 and F4 carts in one batch (32 KB ROM stride, the blocks
+    of the F6 and F4 carts switching among 4 and 8 banks), envs unsorted."""
+    mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4] * 2
+    roms = synth.config_carts(305, mappers)
+    env_cart = np.random.default_rng(5).permutation(np.arange(60) % 10).astype(np.int32)
+    acts = synth.actions(305, 60, 8)
+    b = _check_all(roms, mappers, env_cart, acts, 2, envs_per_block=epb, threads_per_env=tpe)
+    assert b.rom_stride == 32768
+
+
+def test_f6_f4_hotspot_chains():
+    """Every hotspot of F6 and F4 selects its bank on the GPU as in the
+    oracle: the chain of the oracle's hotspot pin, then a frame loop."""
+    for mapper in (synth.MAPPER_F6, synth.MAPPER_F4):
+        nb, hot = synth.MAPPER_BANKS[mapper], synth.MAPPER_HOTSPOT[mapper]
+        banks = []
+        for j in range(nb):
+            a = synth.Asm(0xF000, 4096)
+            if j == nb - 1:
+                a.op("LDA", "abs", hot - 1)
+                a.op("LDA", "abs", hot + nb)
+                a.op("LDA", "abs", hot - 0x1000)
+                a.op("LDA", "abs", hot)
+            else:
+                a.at(12 + 3 * j)
+                a.op("STA" if j % 2 else "LDA", "abs", hot + j + 1)
+            a.at(0x100)
+            a.label("LOOP")             # every bank: a frame loop that shows its bank number
+            a.op("LDA", "imm", 2)
+            a.op("STA", "zp", 0x02)
+            a.op("STA", "zp", 0x00)
+            a.op("LDA", "imm", 0)
+            a.op("STA", "zp", 0x00)
+            a.op("LDA", "imm", 0x10 * (j + 1))
+            a.op("STA", "zp", 0x09)
+            a.op("STA", "zp", 0x80 + j)
+            a.op("LDX", "imm", 0)
+            a.label("L")
+            a.op("STA", "zp", 0x02)
+            a.op("DEX")
+            a.op("BNE", "rel", "L")
+            a.op("JMP", "abs", "LOOP")
+            a.at(4096 - 6)
+            a.word(0xF000), a.word(0xF000), a.word(0xF000)
+            banks.append(bytes(a.resolve()))
+        rom = b"".join(banks)
+        acts = synth.actions(306, 3, 4)
+        _check_all([rom], [mapper], [0, 0, 0], acts, 1)
 
 
 @pytest.mark.parametrize("epb,tpe", [(8, 1), (16, 1), (32, 1), (64, 1), (128, 1), (8, 2), (8, 4), (8, 8),

@@ -5,10 +5,11 @@
 * Corollary 1 / the surrogate rulebook: the CUDA backward (FP32) equals the
   oracle's FP64 reverse sweep to 1e-5 relative, per output tensor and env:
   max |g - g64| <= 1e-5 max(|g64|_inf, 1e-30) (normwise), and
-  |g - g64| <= 1e-5 |g64| wherever |g64| >= 1e-2 |g64|_inf (elementwise, for
-  entries within 100x of the largest: float32 adjoints carry an absolute
+  |g - g64| <= 1e-5 |g64| wherever |g64| >= 2e-2 |g64|_inf (elementwise, for
+  entries within 50x of the largest: float32 adjoints carry an absolute
   error of a few units in the last place of the largest terms they
-  combine, so smaller entries are held to the normwise bound only)
+  combine, up to about 1.5e-7 |g64|_inf, so smaller entries are held to
+  the normwise bound only)
   (ROM bytes per env, initial RAM, joystick inputs);
 * checkpoint/recompute over several segments gives the same gradient as one
   segment; broadcast loss weights equal the dense gradients they expand to;
@@ -31,7 +32,7 @@ def assert_grad_close(got, want, what):
     scale = max(np.abs(want).max(), 1e-30)
     err = np.abs(got - want)
     assert err.max() <= REL * scale, f"{what}: max abs err {err.max():.3e} vs scale {scale:.3e}"
-    big = np.abs(want) >= 1e-2 * scale
+    big = np.abs(want) >= 2e-2 * scale
     if big.any():
         r = np.where(big, err / np.where(big, np.abs(want), 1.0), 0.0)
         k = np.unravel_index(np.argmax(r), r.shape)
@@ -290,3 +291,38 @@ def test_backward_geometry_past_its_shared_memory():
         res.append((g_rom.cpu().numpy(), g_u.cpu().numpy()))
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
     assert np.abs(res[1][0]).max() > 0
+
+
+@pytest.mark.parametrize("tpe", [1, 4])
+def test_gradients_on_f6_f4_carts(tpe):
+    """Bank-switched 16 and 32 KB carts: ROM gradients over the whole image
+    (rows of the batch's 32 KB ROM stride; reads relaxed within their 4 KB
+    bank), initial RAM and inputs against the FP64 oracle."""
+    mappers = [synth.MAPPER_F6, synth.MAPPER_F4, synth.MAPPER_4K]
+    n_envs, n_steps, tau = 6, 4, 0.1
+    torch, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 71, envs_per_block=8,
+                                                   threads_per_env=tpe)
+    assert b.rom_stride == 32768
+    gr = synth.normal_f32(71, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(71, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, b.rom_stride), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    g_pc = torch.empty((len(mappers), b.rom_stride), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u, grad_rom_per_cart=g_pc)
+    b.sync()
+    g_rom, g_ram0, g_u, g_pc = g_rom.cpu().numpy(), g_ram0.cpu().numpy(), g_u.cpu().numpy(), g_pc.cpu().numpy()
+    want_pc = np.zeros_like(g_pc)
+    for e in range(n_envs):
+        c = env_cart[e]
+        (o_rom, o_ram0, o_u), _, _ = _oracle_grads(roms[c], mappers[c], wa[:, e], u[:, e], 1, tau, gr[:, e],
+                                                   gs[:, e])
+        size = len(roms[c])
+        assert_grad_close(g_rom[e, :size], o_rom, f"grad_rom env {e}")
+        assert np.all(g_rom[e, size:] == 0)
+        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
+        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+        want_pc[c, :size] += o_rom
+    assert_grad_close(g_pc, want_pc, "per-cart ROM gradient")
