@@ -122,6 +122,14 @@ typedef struct vcs_config {
                                and episode tables are refused
                                (VCS_ERR_ARG), and soft checkpoints are taken
                                every segment_frames steps. */
+  int32_t tape_budget_mb;   /* device memory in MB for the backward's tapes,
+                               0 = a quarter of the free device memory at the
+                               first vcs_backward (default).  The backward recomputes as
+                               many checkpoint segments at once as fit (at
+                               least one), then sweeps them last to first:
+                               more segments per group, more parallel
+                               recompute.  vcs_backward_static uses its fixed
+                               array instead. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

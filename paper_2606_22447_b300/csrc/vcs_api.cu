@@ -182,6 +182,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->threads_per_env = 0;
   cfg->position_sampler = 0;
   cfg->step_instructions = 0;
+  cfg->tape_budget_mb = 0;
   return VCS_OK;
 }
 

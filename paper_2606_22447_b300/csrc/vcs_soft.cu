@@ -122,6 +122,7 @@ struct RecTape {
 
 struct BwdParams {
   int32_t n_envs, n_steps, frame_skip, seg, seg_steps, ystart, first;
+  int32_t seg0;               // first segment of the group whose tapes are held (slot = seg - seg0)
   int32_t tpe;                // threads per env
   const int4* blocks;
   const int32_t* perm;
@@ -129,20 +130,22 @@ struct BwdParams {
   const uint8_t* cart_banks;
   uint32_t rom_stride;
   const uint8_t* cart_2k;
+  const int32_t* env_cart;    // [n_envs]
   const DecodeTables* dt;
-  const uint32_t* ckpt;       // this segment's checkpoint [kStateWords][n_envs]
+  const uint32_t* ckpt;       // every segment's checkpoint [n_seg][kStateWords][n_envs]
   const uint8_t* act_bits;    // [n_steps][n_envs]
   const float* grad_ram;      // [n_steps][n_envs][128] or null
   const float* grad_screen;   // [n_steps][n_envs][210][160] or null
   const float* w_ram;         // [128] weights on every step, or null
   const float* w_screen;      // [210][160] weights on every step, or null
-  uint32_t* rec;              // [n_envs][cap_rec]
+  uint32_t* rec;              // [G][n_envs][cap_rec]
   uint32_t cap_rec;
-  float* cw;                  // [n_envs][cap_cw]
+  float* cw;                  // [G][n_envs][cap_cw]
   uint32_t cap_cw;
-  uint32_t* step_end;         // [seg_steps][n_envs]
+  uint32_t* step_end;         // [G][seg_steps][n_envs]
+  float* meta;                // [G][n_envs][kMeta]
   float* carry;               // [kCarry][n_envs]
-  float* imp;                 // ROM impulses [2][n_envs][rom_stride]: value, compensation
+  float* imp;                 // ROM impulses [n_envs][rom_stride] x (value, compensation) pairs
   float* grad_u;              // [n_steps][n_envs][5] or null
   float* grad_ram0;           // [n_envs][128] or null (segment 0)
   float tau;
@@ -164,16 +167,15 @@ struct Adj {
 // compensated sums (value + compensation), since long rollouts add many
 // terms of both signs into them.
 __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                             const float* izr, int W, float* imp, float* impc,
+                                             const float* izr, int W, float2* imp,
                                              uint32_t is2k, uint32_t ref, uint32_t fl, float g) {
   const uint32_t ad = ref & 0x1FFF;
   if (g == 0.f) return;
   if (ad & 0x1000) {
     uint32_t idx = is2k ? (ad & 0x7FF) : ((((fl >> 2) & 7u) << 12) | (ad & 0xFFF));   // the read's bank
-    float sv = imp[idx], cv = impc[idx];
-    comp_add(sv, cv, g);
-    imp[idx] = sv;
-    impc[idx] = cv;
+    float2 v = imp[idx];   // value and compensation in one 8-byte access
+    comp_add(v.x, v.y, g);
+    imp[idx] = v;
   } else if (!(ad & 0x80)) {
     if ((ad & 0xF) == 0xC) comp_add(a.u[4], a.uc[4], -128.f * g);
   } else if (!(ad & 0x200)) {
@@ -244,43 +246,43 @@ __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { retur
 
 template <bool SAMPLER>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                            const float* izr, int W, float* imp, float* impc,
+                                            const float* izr, int W, float2* imp,
                                             uint32_t is2k, const float* cw, uint32_t& j, uint32_t rec) {
   const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
   switch (op) {
     case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
       break;
     }
     case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
       float g = a.X;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
       break;
     }
     case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
       float g = a.Y;
       a.Y = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
       break;
     }
     case 0x09: case 0x05: case 0x15: case 0x0D: case 0x1D: case 0x19: case 0x01: case 0x11:
     case 0x29: case 0x25: case 0x35: case 0x2D: case 0x3D: case 0x39: case 0x21: case 0x31:
     case 0x49: case 0x45: case 0x55: case 0x4D: case 0x5D: case 0x59: case 0x41: case 0x51:
     case 0x69: case 0x65: case 0x75: case 0x6D: case 0x7D: case 0x79: case 0x61: case 0x71:
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, a.A);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, a.A);
       break;
     case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
     case 0xEB:                                                      // USBC: SBC's alias
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, -a.A);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, -a.A);
       break;
     case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   // LAX: A = X = M
       float g = a.A + a.X;
       a.A = 0.f;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
@@ -305,7 +307,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
       float g = take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
       break;
     }
     case 0xAA: a.A += a.X; a.X = 0.f; break;   // TAX
@@ -318,7 +320,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x68: {                                                    // PLA
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, impc, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
       break;
     }
     case 0x20:                                                      // JSR: two pushes
@@ -349,27 +351,42 @@ __device__ __forceinline__ void read_tables(float* ek, float* izr, float tau, in
   __syncthreads();
 }
 
-// Backward shared memory: the step kernel's layout, the RAM adjoints and
-// their compensation [2][128][E], the read tables, then the staged gradient
-// rows (16-byte aligned).
-__host__ __device__ constexpr size_t bwd_row_offset(int E, uint32_t rom_stride) {
-  return (smem_bytes(E, rom_stride) + (size_t)2 * 128 * 4 * E + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
+// The backward runs in two kernels.  The recompute of a segment needs only
+// its checkpoint, so a group of segments is recomputed at once (one grid
+// row per segment: many more independent machines than envs, which the
+// latency-bound interpreter turns into throughput); the reverse sweeps then
+// run one segment at a time, last to first, each handing its adjoints to
+// the next.  Per (segment slot g, env) the recompute leaves the tape rows,
+// the colour / position version sums, the step ends and a small record
+// (kMeta words: version count, overflow flag, the sums of the versions
+// alive at the segment start).
+constexpr int kMeta = 8;
+
+// Recompute shared memory: the step kernel's layout, then the staged
+// gradient rows (16-byte aligned).
+__host__ __device__ constexpr size_t rc_row_offset(int E, uint32_t rom_stride) {
+  return (smem_bytes(E, rom_stride) + 15) & ~(size_t)15;
 }
+size_t rc_smem_bytes(int E, uint32_t rom_stride) { return rc_row_offset(E, rom_stride) + (size_t)40 * 16 * E; }
+// The sweep runs one env per warp: envs' tapes differ, so lanes of one warp
+// walking different tapes would serialise over their different records,
+// while one env per warp lets each SM sub-partition interleave several envs
+// (hiding the latency of the global ROM-impulse updates).
+constexpr int kSweepEnvs = 4;   // envs (warps) per block
+// Sweep shared memory: the RAM adjoints and their compensation
+// [2][128][kSweepEnvs], then the read tables.
+constexpr size_t sw_smem_bytes() { return (size_t)2 * 128 * 4 * kSweepEnvs + (kMaxW + 1 + 128) * 4; }
 
 template <int T, bool SAMPLER, bool INSTR = false>
-__global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
+__global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
   BlockSmem bs = carve_smem(smem, E, p.rom_stride);
-  float* aram_s = reinterpret_cast<float*>(smem + smem_bytes(E, p.rom_stride));   // [128][E]
-  float* aramc_s = aram_s + 128 * E;                                 // [128][E] compensation
-  float* ek = aramc_s + 128 * E;                                     // [kMaxW + 1]
-  float* izr = ek + (kMaxW + 1);                                     // [128]
-  float4* grow = reinterpret_cast<float4*>(smem + bwd_row_offset(E, p.rom_stride));  // [40][E] staged gradient rows
+  float4* grow = reinterpret_cast<float4*>(smem + rc_row_offset(E, p.rom_stride));  // [40][E] staged gradient rows
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t nb = p.cart_banks[cart], is2k = p.cart_2k[cart];
-  read_tables(ek, izr, p.tau, p.W);
+  const uint32_t nb = p.cart_banks[cart];
+  const int g = blockIdx.y, seg = p.seg0 + g;
   if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
@@ -379,18 +396,15 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
   Ctx c = make_ctx(bs, E, slot, rank, T, nb, p.ystart);
-  float* aram = aram_s + slot;
-  float* aramc = aramc_s + slot;
-
   Regs r;
   if (active) {
-    load_env(soa_at(const_cast<uint32_t*>(p.ckpt), n), n, env, c, r);
+    load_env(soa_at(const_cast<uint32_t*>(p.ckpt + (size_t)seg * kStateWords * n), n), n, env, c, r);
   } else {
     power_on(c, r);
   }
   RecTape<SAMPLER> tape;
-  tape.buf = p.rec + (size_t)env * p.cap_rec;
-  tape.cw = p.cw + (size_t)env * p.cap_cw;
+  tape.buf = p.rec + ((size_t)g * n + env) * p.cap_rec;
+  tape.cw = p.cw + ((size_t)g * n + env) * p.cap_cw;
   tape.n = 0; tape.cap = p.cap_rec;
   tape.ncw = 0; tape.capcw = p.cap_cw;
   tape.slot0 = tape.slot1 = tape.slot2 = tape.slot3 = -1;
@@ -400,10 +414,9 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   tape.overflow = false;
   tape.T = (uint32_t)T;
   tape.gmask = c.gmask;
-
-  // 1. recompute the segment, recording the tape
-  const int t0 = p.seg * p.seg_steps;
+  const int t0 = seg * p.seg_steps;
   const int t1 = min(t0 + p.seg_steps, p.n_steps);
+  uint32_t* step_end = p.step_end + (size_t)g * p.seg_steps * n;
   Render rd;
   rd.on = false;
   rd.cur = 0;
@@ -422,19 +435,44 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     run_frames<INSTR>(c, r, rd, st, tape, active, lanes, p.sched_policy, p.sched_window);
     if (active) {
       normalise_timer(r);
-      p.step_end[(size_t)(t - t0) * n + env] = tape.n;
+      step_end[(size_t)(t - t0) * n + env] = tape.n;
     }
   }
   if (!active) return;
   tape.finish();
-  // the reverse sweep is sequential: one replica runs it
   if (rank != 0) return;
-  if (tape.overflow) {
-    atomicExch(p.err, 2);
-    return;
-  }
+  float* m = p.meta + ((size_t)g * n + env) * kMeta;
+  m[0] = __uint_as_float(tape.ncw);
+  m[1] = tape.overflow ? 1.f : 0.f;
+  m[2] = tape.p0;
+  m[3] = tape.p1;
+  m[4] = tape.p2;
+  m[5] = tape.p3;
+  if (tape.overflow) atomicExch(p.err, 2);
+}
 
-  // 2. reverse sweep
+// The reverse sweep of segment p.seg (slot p.seg - p.seg0 of the group), one
+// env per warp (lane 0): adjoints of A, X, Y, the timer value, the colour
+// registers, player 0's position and HMP0 in registers, the 128 RAM cells
+// (compensated) in shared memory.
+template <bool SAMPLER>
+__global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr int E = kSweepEnvs;
+  const int slot = threadIdx.x >> 5;
+  float* aram_s = reinterpret_cast<float*>(smem);   // [128][E]
+  float* aramc_s = aram_s + 128 * E;                 // [128][E] compensation
+  float* ek = aramc_s + 128 * E;                     // [kMaxW + 1]
+  float* izr = ek + (kMaxW + 1);                     // [128]
+  read_tables(ek, izr, p.tau, p.W);
+  const int env = blockIdx.x * E + slot;
+  if ((threadIdx.x & 31) != 0 || env >= p.n_envs) return;
+  const uint32_t is2k = p.cart_2k[p.env_cart[env]];
+  const int n = p.n_envs, g = p.seg - p.seg0;
+  const float* m = p.meta + ((size_t)g * n + env) * kMeta;
+  if (m[1] != 0.f) return;   // overflow: the error word is set
+  float* aram = aram_s + slot;
+  float* aramc = aramc_s + slot;
   Adj a;
   if (p.first) {
     a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.P = a.H = 0.f;
@@ -449,18 +487,20 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
     for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
   }
-  float* imp = p.imp + (size_t)env * p.rom_stride;
-  float* impc = p.imp + ((size_t)n + env) * p.rom_stride;
-  const uint4* rec4 = reinterpret_cast<const uint4*>(p.rec + (size_t)env * p.cap_rec);
-  const float* cw = p.cw + (size_t)env * p.cap_cw;
-  uint32_t j = tape.ncw;
+  float2* imp = reinterpret_cast<float2*>(p.imp) + (size_t)env * p.rom_stride;
+  const uint4* rec4 = reinterpret_cast<const uint4*>(p.rec + ((size_t)g * n + env) * p.cap_rec);
+  const float* cw = p.cw + ((size_t)g * n + env) * p.cap_cw;
+  const uint32_t* step_end = p.step_end + (size_t)g * p.seg_steps * n;
+  uint32_t j = __float_as_uint(m[0]);
+  const int t0 = p.seg * p.seg_steps;
+  const int t1 = min(t0 + p.seg_steps, p.n_steps);
   for (int t = t1 - 1; t >= t0; t--) {
     const float* gr = p.grad_ram ? p.grad_ram + ((size_t)t * n + env) * 128 : p.w_ram;
     if (gr)
       for (int i = 0; i < 128; i++) comp_add(aram[i * E], aramc[i * E], gr[i]);
     for (int q = 0; q < 5; q++) a.u[q] = a.uc[q] = 0.f;
-    const uint32_t k_end = p.step_end[(size_t)(t - t0) * n + env];
-    const uint32_t k_beg = t > t0 ? p.step_end[(size_t)(t - 1 - t0) * n + env] : 0u;
+    const uint32_t k_end = step_end[(size_t)(t - t0) * n + env];
+    const uint32_t k_beg = t > t0 ? step_end[(size_t)(t - 1 - t0) * n + env] : 0u;
     // records are read backwards in aligned 4-record chunks (rows of the
     // tape are 16-byte aligned), the next chunk in flight while one runs
     uint32_t k = k_end;
@@ -472,7 +512,7 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
       for (uint32_t q = k; q > lo; q--) {
         const uint32_t sl = (q - 1) & 3;
         const uint32_t rv = sl == 0 ? ch.x : (sl == 1 ? ch.y : (sl == 2 ? ch.z : ch.w));
-        reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, imp, impc, is2k, cw, j, rv);
+        reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, imp, is2k, cw, j, rv);
       }
       ch = nx;
       k = lo;
@@ -483,10 +523,10 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
     }
   }
   // versions alive at the segment start continue into the previous segment
-  a.C0 += tape.p0;
-  a.C1 += tape.p1;
-  a.C2 += tape.p2;
-  if constexpr (SAMPLER) a.P += tape.p3;
+  a.C0 += m[2];
+  a.C1 += m[3];
+  a.C2 += m[4];
+  if constexpr (SAMPLER) a.P += m[5];
   if (p.seg == 0) {
     if (p.grad_ram0)
       for (int i = 0; i < 128; i++) p.grad_ram0[(size_t)env * 128 + i] = aram[i * E] + aramc[i * E];
@@ -500,50 +540,49 @@ __global__ void __launch_bounds__(128) k_soft_bwd(BwdParams p) {
   }
 }
 
-static cudaError_t allow_bwd_smem(size_t smem) {
-  cudaError_t e;
-  const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if ((e = cudaFuncSetAttribute(k_soft_bwd<1, false>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<2, false>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<4, false>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<8, false>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<1, true>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<2, true>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<4, true>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<8, true>, (cudaFuncAttribute)a, (int)smem)) ||
-      (e = cudaFuncSetAttribute(k_soft_bwd<1, false, true>, (cudaFuncAttribute)a, (int)smem)))
-    return e;
-  return cudaSuccess;
+template <class Kern>
+static cudaError_t allow_smem(Kern kern, size_t smem) {
+  return smem > 48u * 1024u ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaSuccess;
 }
 
-static void launch_bwd(const BwdParams& p, int n_blocks, int E, int T, size_t smem, cudaStream_t s) {
+// Recompute segments seg0 .. seg0 + G - 1 (grid rows), envs in blocks of E
+// with T lanes each.
+static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int E, int T, size_t smem,
+                                    cudaStream_t s) {
+  const dim3 grid(n_blocks, G);
+  cudaError_t e = cudaSuccess;
+  auto go = [&](auto kern, int threads) {
+    if ((e = allow_smem(kern, smem)) == cudaSuccess) kern<<<grid, threads, smem, s>>>(p);
+  };
   // instruction-granular steps draw nothing (no pixel sums, no position
   // sampler), so one lane per env serves them
   if (p.step_instr > 0) {
-    k_soft_bwd<1, false, true><<<n_blocks, E, smem, s>>>(p);
-    return;
+    go(k_soft_recompute<1, false, true>, E);
+  } else if (p.sampler) {
+    switch (T) {
+      case 1: go(k_soft_recompute<1, true>, E); break;
+      case 2: go(k_soft_recompute<2, true>, 2 * E); break;
+      case 4: go(k_soft_recompute<4, true>, 4 * E); break;
+      default: go(k_soft_recompute<8, true>, 8 * E); break;
+    }
+  } else {
+    switch (T) {
+      case 1: go(k_soft_recompute<1, false>, E); break;
+      case 2: go(k_soft_recompute<2, false>, 2 * E); break;
+      case 4: go(k_soft_recompute<4, false>, 4 * E); break;
+      default: go(k_soft_recompute<8, false>, 8 * E); break;
+    }
   }
-  switch (T) {
-    case 1:
-      if (p.sampler) k_soft_bwd<1, true><<<n_blocks, E, smem, s>>>(p);
-      else k_soft_bwd<1, false><<<n_blocks, E, smem, s>>>(p);
-      break;
-    case 2:
-      if (p.sampler) k_soft_bwd<2, true><<<n_blocks, 2 * E, smem, s>>>(p);
-      else k_soft_bwd<2, false><<<n_blocks, 2 * E, smem, s>>>(p);
-      break;
-    case 4:
-      if (p.sampler) k_soft_bwd<4, true><<<n_blocks, 4 * E, smem, s>>>(p);
-      else k_soft_bwd<4, false><<<n_blocks, 4 * E, smem, s>>>(p);
-      break;
-    default:
-      if (p.sampler) k_soft_bwd<8, true><<<n_blocks, 8 * E, smem, s>>>(p);
-      else k_soft_bwd<8, false><<<n_blocks, 8 * E, smem, s>>>(p);
-      break;
-  }
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-size_t bwd_smem_bytes(int E, uint32_t rom_stride) { return bwd_row_offset(E, rom_stride) + (size_t)40 * 16 * E; }
+static cudaError_t launch_sweep(const BwdParams& p, cudaStream_t s) {
+  const int n_blocks = (p.n_envs + kSweepEnvs - 1) / kSweepEnvs;
+  if (p.sampler && p.step_instr <= 0) k_soft_sweep<true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  else k_soft_sweep<false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  return cudaGetLastError();
+}
 
 // ROM impulses -> ROM gradient: spread each impulse at a over the read
 // window of its tensor (the 2K image, the 4K image, or one 4 KB bank of a
@@ -579,13 +618,12 @@ __global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_ca
   }
   const int base = i & ~(M - 1);
   const int ii = i - base;
-  const float* im = imp + (size_t)env * rom_stride + base;
-  const float* imc = imp + ((size_t)n_envs + env) * rom_stride + base;
+  const float2* im = reinterpret_cast<const float2*>(imp) + (size_t)env * rom_stride + base;
   const int lo = ii - W < 0 ? 0 : ii - W, hi = ii + W > M - 1 ? M - 1 : ii + W;
   const double zint = ek[0] + 2.0 * suf[1];
   double acc = 0.0;
   for (int q = lo; q <= hi; q++) {
-    const double v = (double)im[q] + (double)imc[q];
+    const double v = (double)im[q].x + (double)im[q].y;
     if (v == 0.0) continue;
     double z = zint;
     if (q < W) z -= suf[q + 1];
@@ -631,12 +669,15 @@ struct vcs_tape {
   uint32_t* ckpt = nullptr;
   uint8_t* act_bits = nullptr;
   uint32_t* seg_counts = nullptr;
-  // backward scratch (allocated by the first vcs_backward)
+  // backward scratch (allocated by the first vcs_backward): the tapes of a
+  // group of G segments
+  int32_t G = 0;
   uint32_t* rec = nullptr;
   size_t cap_rec = 0;
   float* cw = nullptr;
   size_t cap_cw = 0;
   uint32_t* step_end = nullptr;
+  float* meta = nullptr;
   float* carry = nullptr;
   float* imp = nullptr;
   float* grad_rom_tmp = nullptr;
@@ -651,6 +692,7 @@ static void free_tape(vcs_tape* t) {
   cudaFree(t->rec);
   cudaFree(t->cw);
   cudaFree(t->step_end);
+  cudaFree(t->meta);
   cudaFree(t->carry);
   cudaFree(t->imp);
   cudaFree(t->grad_rom_tmp);
@@ -660,6 +702,34 @@ static void free_tape(vcs_tape* t) {
 static int half_width(float tau) {
   int w = (int)std::ceil(12.0 * (double)tau);
   return w < 1 ? 1 : w;
+}
+
+// Segments last to first in groups of G: recompute the group's segments at
+// once, then sweep them one by one (p's tape pointers hold G slots).
+static vcs_status run_backward_groups(vcs_batch* b, const vcs_tape* t, BwdParams& p, int G, cudaStream_t s) {
+  const int4* blocks;
+  int nbl, E;
+  vcs_bwd_geometry(b, &blocks, &nbl, &E);
+  p.blocks = blocks;
+  p.ckpt = t->ckpt;
+  const size_t smem = rc_smem_bytes(E, b->rom_stride);
+  cudaError_t e;
+  for (int hi = t->n_seg - 1; hi >= 0; hi -= G) {
+    const int lo = hi - G + 1 > 0 ? hi - G + 1 : 0;
+    p.seg0 = lo;
+    if ((e = launch_recompute(p, hi - lo + 1, nbl, E, b->tpe, smem, s))) return vcs_cuda_fail(b, e, "recompute launch");
+    for (int q = hi; q >= lo; q--) {
+      p.seg = q;
+      p.first = q == t->n_seg - 1;
+      if ((e = launch_sweep(p, s))) return vcs_cuda_fail(b, e, "reverse sweep launch");
+    }
+  }
+  return VCS_OK;
+}
+
+// Tape bytes of one segment (records, version sums, step ends, meta).
+static size_t segment_tape_bytes(size_t n, size_t cap_rec, size_t cap_cw, int seg_steps) {
+  return n * (cap_rec + cap_cw + (size_t)seg_steps + kMeta) * 4;
 }
 
 extern "C" {
@@ -756,21 +826,36 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
     need_cw = std::max<size_t>(need_cw, counts[2 * q + 1]);
   }
   need_rec = (need_rec + 3) & ~(size_t)3;   // 16-byte rows: the reverse sweep reads 4 records at once
-  if (need_rec > t->cap_rec) {
+  // as many segments per group as the tape budget holds
+  size_t budget = (size_t)b->cfg.tape_budget_mb << 20;
+  if (budget == 0) {   // default: a quarter of the free device memory
+    size_t free_b = 0, total_b = 0;
+    if ((e = cudaMemGetInfo(&free_b, &total_b))) return vcs_cuda_fail(b, e, "device memory query");
+    budget = free_b / 4;
+  }
+  const size_t per_seg = segment_tape_bytes(n, need_rec, need_cw, t->seg_steps);
+  int G = (int)std::min<size_t>((size_t)t->n_seg, std::max<size_t>(1, budget / per_seg));
+  if (need_rec > t->cap_rec || need_cw > t->cap_cw || G > t->G) {
     cudaFree(t->rec);
-    t->rec = nullptr;
-    if ((e = cudaMalloc(&t->rec, need_rec * n * 4))) return vcs_cuda_fail(b, e, "tape allocation");
-    t->cap_rec = need_rec;
-  }
-  if (need_cw > t->cap_cw) {
     cudaFree(t->cw);
+    cudaFree(t->step_end);
+    cudaFree(t->meta);
+    t->rec = nullptr;
     t->cw = nullptr;
-    if ((e = cudaMalloc(&t->cw, need_cw * n * 4))) return vcs_cuda_fail(b, e, "tape allocation");
+    t->step_end = nullptr;
+    t->meta = nullptr;
+    t->G = 0;
+    if ((e = cudaMalloc(&t->rec, (size_t)G * need_rec * n * 4)) || (e = cudaMalloc(&t->cw, (size_t)G * need_cw * n * 4)) ||
+        (e = cudaMalloc(&t->step_end, (size_t)G * t->seg_steps * n * 4)) ||
+        (e = cudaMalloc(&t->meta, (size_t)G * n * kMeta * 4)))
+      return vcs_cuda_fail(b, e, "tape allocation");
+    t->cap_rec = need_rec;
     t->cap_cw = need_cw;
+    t->G = G;
   }
-  if (!t->step_end) {
-    if ((e = cudaMalloc(&t->step_end, (size_t)t->seg_steps * n * 4)) ||
-        (e = cudaMalloc(&t->carry, (size_t)kCarry * n * 4)) || (e = cudaMalloc(&t->imp, 2 * n * b->rom_stride * 4)))
+  G = t->G;
+  if (!t->carry) {
+    if ((e = cudaMalloc(&t->carry, (size_t)kCarry * n * 4)) || (e = cudaMalloc(&t->imp, 2 * n * b->rom_stride * 4)))
       return vcs_cuda_fail(b, e, "backward scratch");
   }
   float* grom = grad_rom;
@@ -787,15 +872,12 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.frame_skip = t->frame_skip;
   p.seg_steps = t->seg_steps;
   p.ystart = b->cfg.ystart;
-  const int4* bwd_blocks;
-  int bwd_nb, bwd_E;
-  vcs_bwd_geometry(b, &bwd_blocks, &bwd_nb, &bwd_E);
-  p.blocks = bwd_blocks;
   p.perm = b->perm;
   p.roms = t->rom_bytes;
   p.cart_banks = b->cart_banks;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
+  p.env_cart = b->env_cart_dev;
   p.dt = b->dt;
   p.act_bits = t->act_bits;
   p.grad_ram = grad_ram;
@@ -807,6 +889,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.cw = t->cw;
   p.cap_cw = (uint32_t)t->cap_cw;
   p.step_end = t->step_end;
+  p.meta = t->meta;
   p.carry = t->carry;
   p.imp = t->imp;
   p.grad_u = grad_u;
@@ -819,16 +902,8 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
-  const size_t smem = bwd_smem_bytes(bwd_E, b->rom_stride);
-  if ((e = allow_bwd_smem(smem)))
-    return vcs_cuda_fail(b, e, "backward shared memory");
-  for (int q = t->n_seg - 1; q >= 0; q--) {
-    p.seg = q;
-    p.first = q == t->n_seg - 1;
-    p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
-    launch_bwd(p, bwd_nb, bwd_E, b->tpe, smem, s);
-    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
-  }
+  vcs_status st = run_backward_groups(b, t, p, G, s);
+  if (st != VCS_OK) return st;
   if (grom) {
     dim3 grid(b->rom_stride / 256, b->n_envs);
     k_rom_spread<<<grid, 256, 0, s>>>(t->imp, grom, b->env_cart_dev, b->cart_banks, b->cart_2k, b->n_envs,
@@ -919,12 +994,18 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   cap_rec = (cap_rec + 3) & ~(size_t)3;   // 16-byte rows, as in vcs_backward
   const bool need_tmp = !grad_rom && grad_rom_per_cart;
   const size_t o_carry = 0;
-  const size_t o_step = align256(o_carry + (size_t)kCarry * n * 4);
-  const size_t o_imp = align256(o_step + (size_t)t->seg_steps * n * 4);
+  const size_t o_imp = align256(o_carry + (size_t)kCarry * n * 4);
   const size_t o_tmp = align256(o_imp + 2 * n * b->rom_stride * 4);
-  const size_t o_rec = align256(o_tmp + (need_tmp ? n * b->rom_stride * 4 : 0));
-  const size_t o_cw = align256(o_rec + cap_rec * n * 4);
-  const size_t total = align256(o_cw + cap_cw * n * 4);
+  const size_t o_tapes = align256(o_tmp + (need_tmp ? n * b->rom_stride * 4 : 0));
+  // as many segments per group as the rest of the array holds (at least one)
+  const size_t per_seg = segment_tape_bytes(n, cap_rec, cap_cw, t->seg_steps) + 4 * 256;
+  const size_t room = kStaticScratchBytes > o_tapes ? kStaticScratchBytes - o_tapes : 0;
+  const int G = (int)std::max<size_t>(1, std::min<size_t>((size_t)t->n_seg, room / per_seg));
+  const size_t o_step = o_tapes;
+  const size_t o_meta = align256(o_step + (size_t)G * t->seg_steps * n * 4);
+  const size_t o_rec = align256(o_meta + (size_t)G * n * kMeta * 4);
+  const size_t o_cw = align256(o_rec + (size_t)G * cap_rec * n * 4);
+  const size_t total = align256(o_cw + (size_t)G * cap_cw * n * 4);
   if (total > kStaticScratchBytes)
     return vcs_fail(b, VCS_ERR_ARG,
                     "vcs_backward_static needs %zu bytes of scratch for %zu envs (%zu instructions per segment), "
@@ -943,15 +1024,12 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.frame_skip = t->frame_skip;
   p.seg_steps = t->seg_steps;
   p.ystart = b->cfg.ystart;
-  const int4* bwd_blocks;
-  int bwd_nb, bwd_E;
-  vcs_bwd_geometry(b, &bwd_blocks, &bwd_nb, &bwd_E);
-  p.blocks = bwd_blocks;
   p.perm = b->perm;
   p.roms = t->rom_bytes;
   p.cart_banks = b->cart_banks;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
+  p.env_cart = b->env_cart_dev;
   p.dt = b->dt;
   p.act_bits = t->act_bits;
   p.grad_ram = grad_ram;
@@ -963,6 +1041,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.cw = reinterpret_cast<float*>(sc + o_cw);
   p.cap_cw = (uint32_t)cap_cw;
   p.step_end = reinterpret_cast<uint32_t*>(sc + o_step);
+  p.meta = reinterpret_cast<float*>(sc + o_meta);
   p.carry = reinterpret_cast<float*>(sc + o_carry);
   p.imp = imp;
   p.grad_u = grad_u;
@@ -975,16 +1054,8 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
-  const size_t smem = bwd_smem_bytes(bwd_E, b->rom_stride);
-  if ((e = allow_bwd_smem(smem)))
-    return vcs_cuda_fail(b, e, "backward shared memory");
-  for (int q = t->n_seg - 1; q >= 0; q--) {
-    p.seg = q;
-    p.first = q == t->n_seg - 1;
-    p.ckpt = t->ckpt + (size_t)q * kStateWords * n;
-    launch_bwd(p, bwd_nb, bwd_E, b->tpe, smem, s);
-    if ((e = cudaGetLastError())) return vcs_cuda_fail(b, e, "backward launch");
-  }
+  vcs_status st = run_backward_groups(b, t, p, G, s);
+  if (st != VCS_OK) return st;
   if (grom) {
     dim3 grid(b->rom_stride / 256, b->n_envs);
     k_rom_spread<<<grid, 256, 0, s>>>(imp, grom, b->env_cart_dev, b->cart_banks, b->cart_2k, b->n_envs, b->rom_stride,
