@@ -162,20 +162,28 @@ struct Adj {
   float u[5], uc[5];   // joystick-input adjoints of the current step (compensated)
 };
 
+// ROM impulses waiting to be added to the env's impulse row: the sweep's
+// lane queues (index, adjoint) pairs and the warp adds them in order after
+// each block of records (shared memory, one queue per env).
+struct RomQueue {
+  uint32_t* idx;
+  float* g;
+  uint32_t n;
+};
+
 // Adjoint of a value read from `ref` (13-bit bus address) flows back to the
 // memory it came from.  RAM cells, ROM impulses and joystick adjoints are
 // compensated sums (value + compensation), since long rollouts add many
 // terms of both signs into them.
 __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                             const float* izr, int W, float2* imp,
+                                             const float* izr, int W, RomQueue& rq,
                                              uint32_t is2k, uint32_t ref, uint32_t fl, float g) {
   const uint32_t ad = ref & 0x1FFF;
   if (g == 0.f) return;
   if (ad & 0x1000) {
-    uint32_t idx = is2k ? (ad & 0x7FF) : ((((fl >> 2) & 7u) << 12) | (ad & 0xFFF));   // the read's bank
-    float2 v = imp[idx];   // value and compensation in one 8-byte access
-    comp_add(v.x, v.y, g);
-    imp[idx] = v;
+    rq.idx[rq.n] = is2k ? (ad & 0x7FF) : ((((fl >> 2) & 7u) << 12) | (ad & 0xFFF));   // the read's bank
+    rq.g[rq.n] = g;
+    rq.n++;
   } else if (!(ad & 0x80)) {
     if ((ad & 0xF) == 0xC) comp_add(a.u[4], a.uc[4], -128.f * g);
   } else if (!(ad & 0x200)) {
@@ -246,43 +254,43 @@ __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { retur
 
 template <bool SAMPLER>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                            const float* izr, int W, float2* imp,
+                                            const float* izr, int W, RomQueue& rq,
                                             uint32_t is2k, const float* cw, uint32_t& j, uint32_t rec) {
   const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
   switch (op) {
     case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
       break;
     }
     case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
       float g = a.X;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
       break;
     }
     case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
       float g = a.Y;
       a.Y = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
       break;
     }
     case 0x09: case 0x05: case 0x15: case 0x0D: case 0x1D: case 0x19: case 0x01: case 0x11:
     case 0x29: case 0x25: case 0x35: case 0x2D: case 0x3D: case 0x39: case 0x21: case 0x31:
     case 0x49: case 0x45: case 0x55: case 0x4D: case 0x5D: case 0x59: case 0x41: case 0x51:
     case 0x69: case 0x65: case 0x75: case 0x6D: case 0x7D: case 0x79: case 0x61: case 0x71:
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, a.A);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, a.A);
       break;
     case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
     case 0xEB:                                                      // USBC: SBC's alias
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, -a.A);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, -a.A);
       break;
     case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   // LAX: A = X = M
       float g = a.A + a.X;
       a.A = 0.f;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
@@ -307,7 +315,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
       float g = take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
       break;
     }
     case 0xAA: a.A += a.X; a.X = 0.f; break;   // TAX
@@ -320,7 +328,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x68: {                                                    // PLA
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, imp, is2k, ref, fl, g);
+      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
       break;
     }
     case 0x20:                                                      // JSR: two pushes
@@ -373,9 +381,12 @@ size_t rc_smem_bytes(int E, uint32_t rom_stride) { return rc_row_offset(E, rom_s
 // while one env per warp lets each SM sub-partition interleave several envs
 // (hiding the latency of the global ROM-impulse updates).
 constexpr int kSweepEnvs = 4;   // envs (warps) per block
+constexpr int kSweepBlock = 128;   // records a warp stages at a time (32 lanes x 4)
+constexpr int kSweepWarpWords = 3 * kSweepBlock;   // staged records, then the ROM queue's indices and adjoints
 // Sweep shared memory: the RAM adjoints and their compensation
-// [2][128][kSweepEnvs], then the read tables.
-constexpr size_t sw_smem_bytes() { return (size_t)2 * 128 * 4 * kSweepEnvs + (kMaxW + 1 + 128) * 4; }
+// [2][128][kSweepEnvs], the read tables, then each warp's staging words.
+__host__ __device__ constexpr size_t sw_tables_end() { return ((size_t)2 * 128 * 4 * kSweepEnvs + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15; }
+__host__ __device__ constexpr size_t sw_smem_bytes() { return sw_tables_end() + (size_t)kSweepEnvs * kSweepWarpWords * 4; }
 
 template <int T, bool SAMPLER, bool INSTR = false>
 __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
@@ -459,33 +470,42 @@ template <bool SAMPLER>
 __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr int E = kSweepEnvs;
-  const int slot = threadIdx.x >> 5;
+  const int slot = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* aram_s = reinterpret_cast<float*>(smem);   // [128][E]
   float* aramc_s = aram_s + 128 * E;                 // [128][E] compensation
   float* ek = aramc_s + 128 * E;                     // [kMaxW + 1]
   float* izr = ek + (kMaxW + 1);                     // [128]
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem + sw_tables_end()) + slot * kSweepWarpWords;
+  uint32_t* recs = wbuf;                             // [kSweepBlock] records of the current block
+  RomQueue rq;
+  rq.idx = wbuf + kSweepBlock;                       // [kSweepBlock]
+  rq.g = reinterpret_cast<float*>(wbuf + 2 * kSweepBlock);   // [kSweepBlock]
+  rq.n = 0;
   read_tables(ek, izr, p.tau, p.W);
   const int env = blockIdx.x * E + slot;
-  if ((threadIdx.x & 31) != 0 || env >= p.n_envs) return;
+  if (env >= p.n_envs) return;   // whole warps leave together
   const uint32_t is2k = p.cart_2k[p.env_cart[env]];
   const int n = p.n_envs, g = p.seg - p.seg0;
   const float* m = p.meta + ((size_t)g * n + env) * kMeta;
   if (m[1] != 0.f) return;   // overflow: the error word is set
+  const bool lead = lane == 0;   // lane 0 runs the sweep; the warp loads records and adds ROM impulses
   float* aram = aram_s + slot;
   float* aramc = aramc_s + slot;
   Adj a;
-  if (p.first) {
-    a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.P = a.H = 0.f;
-    for (int i = 0; i < 128; i++) aram[i * E] = 0.f;
-    for (int i = 0; i < 128; i++) aramc[i * E] = 0.f;
-  } else {
-    const float* cr = p.carry;
-    a.A = cr[0 * n + env]; a.X = cr[1 * n + env]; a.Y = cr[2 * n + env]; a.V = cr[3 * n + env];
-    a.C0 = cr[4 * n + env]; a.C1 = cr[5 * n + env]; a.C2 = cr[6 * n + env];
-    a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
-    a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
-    for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
-    for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
+  if (lead) {
+    if (p.first) {
+      a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.P = a.H = 0.f;
+      for (int i = 0; i < 128; i++) aram[i * E] = 0.f;
+      for (int i = 0; i < 128; i++) aramc[i * E] = 0.f;
+    } else {
+      const float* cr = p.carry;
+      a.A = cr[0 * n + env]; a.X = cr[1 * n + env]; a.Y = cr[2 * n + env]; a.V = cr[3 * n + env];
+      a.C0 = cr[4 * n + env]; a.C1 = cr[5 * n + env]; a.C2 = cr[6 * n + env];
+      a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
+      a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
+      for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
+      for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
+    }
   }
   float2* imp = reinterpret_cast<float2*>(p.imp) + (size_t)env * p.rom_stride;
   const uint4* rec4 = reinterpret_cast<const uint4*>(p.rec + ((size_t)g * n + env) * p.cap_rec);
@@ -494,34 +514,65 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   uint32_t j = __float_as_uint(m[0]);
   const int t0 = p.seg * p.seg_steps;
   const int t1 = min(t0 + p.seg_steps, p.n_steps);
+  constexpr uint32_t kChunks = kSweepBlock / 4;   // 4-record chunks per block (one per lane)
   for (int t = t1 - 1; t >= t0; t--) {
-    const float* gr = p.grad_ram ? p.grad_ram + ((size_t)t * n + env) * 128 : p.w_ram;
-    if (gr)
-      for (int i = 0; i < 128; i++) comp_add(aram[i * E], aramc[i * E], gr[i]);
-    for (int q = 0; q < 5; q++) a.u[q] = a.uc[q] = 0.f;
+    if (lead) {
+      const float* gr = p.grad_ram ? p.grad_ram + ((size_t)t * n + env) * 128 : p.w_ram;
+      if (gr)
+        for (int i = 0; i < 128; i++) comp_add(aram[i * E], aramc[i * E], gr[i]);
+      for (int q = 0; q < 5; q++) a.u[q] = a.uc[q] = 0.f;
+    }
     const uint32_t k_end = step_end[(size_t)(t - t0) * n + env];
     const uint32_t k_beg = t > t0 ? step_end[(size_t)(t - 1 - t0) * n + env] : 0u;
-    // records are read backwards in aligned 4-record chunks (rows of the
-    // tape are 16-byte aligned), the next chunk in flight while one runs
+    // records are read backwards a block of 32 aligned 4-record chunks at a
+    // time (tape rows are 16-byte aligned), each lane loading one chunk, the
+    // next block in flight while lane 0 sweeps the current one
+    const uint32_t cb = k_beg >> 2;
+    auto block_base = [&](uint32_t k) {   // first chunk of the block that ends at record k
+      const uint32_t ct = (k - 1) >> 2;
+      return ct >= cb + (kChunks - 1) ? ct - (kChunks - 1) : cb;
+    };
+    auto load = [&](uint32_t k, uint32_t c0) {
+      return c0 + lane <= ((k - 1) >> 2) ? __ldcs(rec4 + c0 + lane) : make_uint4(0u, 0u, 0u, 0u);
+    };
     uint32_t k = k_end;
-    uint4 ch = k > k_beg ? __ldcs(rec4 + ((k - 1) >> 2)) : make_uint4(0u, 0u, 0u, 0u);
+    uint32_t c0 = k > k_beg ? block_base(k) : 0u;
+    uint4 v = k > k_beg ? load(k, c0) : make_uint4(0u, 0u, 0u, 0u);
     while (k > k_beg) {
-      const uint32_t c4 = (k - 1) >> 2;
-      const uint32_t lo = c4 * 4 > k_beg ? c4 * 4 : k_beg;
-      const uint4 nx = lo > k_beg ? __ldcs(rec4 + (c4 - 1)) : ch;
-      for (uint32_t q = k; q > lo; q--) {
-        const uint32_t sl = (q - 1) & 3;
-        const uint32_t rv = sl == 0 ? ch.x : (sl == 1 ? ch.y : (sl == 2 ? ch.z : ch.w));
-        reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, imp, is2k, cw, j, rv);
+      reinterpret_cast<uint4*>(recs)[lane] = v;
+      __syncwarp();
+      const uint32_t lo = 4 * c0 > k_beg ? 4 * c0 : k_beg;
+      uint32_t c1 = 0;
+      if (lo > k_beg) {
+        c1 = block_base(lo);
+        v = load(lo, c1);
       }
-      ch = nx;
+      if (lead)
+        for (uint32_t q = k; q > lo; q--)
+          reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, rq, is2k, cw, j, recs[q - 1 - 4 * c0]);
+      // the warp adds the block's ROM impulses: lane l takes the indices
+      // congruent to l mod 32, each in queue order
+      const uint32_t qn = __shfl_sync(0xFFFFFFFFu, rq.n, 0);
+      __syncwarp();
+      for (uint32_t e = 0; e < qn; e++) {
+        const uint32_t ix = rq.idx[e];
+        if ((ix & 31) == (uint32_t)lane) {
+          float2 w = imp[ix];   // value and compensation in one 8-byte access
+          comp_add(w.x, w.y, rq.g[e]);
+          imp[ix] = w;
+        }
+      }
+      __syncwarp();
+      rq.n = 0;
       k = lo;
+      c0 = c1;
     }
-    if (p.grad_u) {
+    if (lead && p.grad_u) {
       float* gu = p.grad_u + ((size_t)t * n + env) * 5;
       for (int q = 0; q < 5; q++) gu[q] = a.u[q] + a.uc[q];
     }
   }
+  if (!lead) return;
   // versions alive at the segment start continue into the previous segment
   a.C0 += m[2];
   a.C1 += m[3];
