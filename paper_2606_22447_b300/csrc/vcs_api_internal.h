@@ -29,6 +29,10 @@ struct vcs_batch {
   // memory holds (kBwdMaxEnvsPerBlock envs; same permutation), else null
   int4* bwd_blocks = nullptr;
   int32_t bwd_n_blocks = 0, bwd_E = 0;
+  // blocks of kWideEnvsPerBlock envs (same permutation): the backward's
+  // recompute of a large group of segments, one lane per env
+  int4* wide_blocks = nullptr;
+  int32_t wide_n_blocks = 0;
   uint32_t* ep_len = nullptr;
   int32_t n_episodes = 0;
   uint8_t* start_noops = nullptr;  // [n_envs][n_start] NOOP frames starting each episode
@@ -65,6 +69,7 @@ vcs::StepParams vcs_base_params(vcs_batch* b);
 // Largest envs per block whose backward shared memory (about 9.7 KB +
 // 1.9 KB per env) fits in a block.
 constexpr int kBwdMaxEnvsPerBlock = 64;
+constexpr int kWideEnvsPerBlock = 32;
 
 // The backward's launch geometry (its own block table past
 // kBwdMaxEnvsPerBlock envs per block).

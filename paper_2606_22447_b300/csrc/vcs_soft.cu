@@ -755,12 +755,26 @@ static int half_width(float tau) {
   return w < 1 ? 1 : w;
 }
 
+// Machines (segments x envs) from which a recompute group runs one lane per
+// env rather than the batch's replicas.
+constexpr size_t kWideRecomputeMachines = 16384;
+
 // Segments last to first in groups of G: recompute the group's segments at
 // once, then sweep them one by one (p's tape pointers hold G slots).
 static vcs_status run_backward_groups(vcs_batch* b, const vcs_tape* t, BwdParams& p, int G, cudaStream_t s) {
   const int4* blocks;
-  int nbl, E;
+  int nbl, E, T = b->tpe;
   vcs_bwd_geometry(b, &blocks, &nbl, &E);
+  // A group of many machines (segments x envs) keeps every SM sub-partition
+  // busy: issue slots, not one lane's latency, then bound the recompute, and
+  // one lane per env in blocks of kWideEnvsPerBlock spends a quarter of the
+  // slots that replicated lanes would on the interpreter.
+  if ((size_t)G * (size_t)b->n_envs >= kWideRecomputeMachines) {
+    blocks = b->wide_blocks;
+    nbl = b->wide_n_blocks;
+    E = kWideEnvsPerBlock;
+    T = 1;
+  }
   p.blocks = blocks;
   p.ckpt = t->ckpt;
   const size_t smem = rc_smem_bytes(E, b->rom_stride);
@@ -768,7 +782,7 @@ static vcs_status run_backward_groups(vcs_batch* b, const vcs_tape* t, BwdParams
   for (int hi = t->n_seg - 1; hi >= 0; hi -= G) {
     const int lo = hi - G + 1 > 0 ? hi - G + 1 : 0;
     p.seg0 = lo;
-    if ((e = launch_recompute(p, hi - lo + 1, nbl, E, b->tpe, smem, s))) return vcs_cuda_fail(b, e, "recompute launch");
+    if ((e = launch_recompute(p, hi - lo + 1, nbl, E, T, smem, s))) return vcs_cuda_fail(b, e, "recompute launch");
     for (int q = hi; q >= lo; q--) {
       p.seg = q;
       p.first = q == t->n_seg - 1;

@@ -326,3 +326,31 @@ def test_gradients_on_f6_f4_carts(tpe):
         assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
         want_pc[c, :size] += o_rom
     assert_grad_close(g_pc, want_pc, "per-cart ROM gradient")
+
+
+def test_wide_recompute_of_a_large_segment_group():
+    """32 one-frame segments x 512 envs = 16,384 machines: the group's
+    recompute runs one lane per env (blocks of 32) instead of the batch's 4
+    replicas; the gradients match the FP64 oracle and a one-segment-at-a-time
+    backward (tape budget of 1 MB)."""
+    torch = torch_cuda()
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8]
+    n_envs, n_steps, tau = 512, 32, 0.1
+    res = []
+    for budget in (0, 1):
+        _, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 93, segment_frames=1,
+                                                   threads_per_env=4, tape_budget_mb=budget)
+        gr = synth.normal_f32(93, (n_steps, n_envs, 128), 1)
+        wscr = synth.normal_f32(94, (210 * 160,), 1)
+        tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+        g_rom = torch.empty((n_envs, 8192), device="cuda")
+        g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+        tape.backward(torch.from_numpy(gr).cuda(), None, grad_rom=g_rom, grad_u=g_u)
+        b.sync()
+        res.append((g_rom.cpu().numpy(), g_u.cpu().numpy()))
+    for e in (0, 1, 257, 511):
+        c = env_cart[e]
+        (o_rom, _, o_u), _, _ = _oracle_grads(roms[c], mappers[c], wa[:, e], u[:, e], 1, tau, gr[:, e], None)
+        for g_rom, g_u in res:
+            assert_grad_close(g_rom[e, :len(roms[c])], o_rom, f"grad_rom env {e}")
+            assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
