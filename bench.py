@@ -37,7 +37,7 @@ WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+sc
 # DRAM bytes (read + write) of one step launch on the bench workload, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernel; to be taken again whenever the kernel changes
-TRAFFIC_BYTES_PER_LAUNCH = 954_368 + 83_410_944
+TRAFFIC_BYTES_PER_LAUNCH = 1_022_464 + 83_100_672
 OPS_PER_INSTRUCTION = 12
 OPS_PER_PIXEL = 6
 PIXELS_PER_STEP = 210 * 160
