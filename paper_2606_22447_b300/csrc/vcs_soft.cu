@@ -2,14 +2,14 @@
 //
 // The forward pass of soft mode is the step kernel on rounded inputs (it
 // equals the hard machine, Theorem 1) plus a state checkpoint at the start of
-// every segment.  The backward pass runs the segments last to first; for each
-// one a kernel, one thread per env:
-//   1. recomputes the segment's forward from its checkpoint, recording one
-//      4-byte tape entry per instruction the sweep acts on (opcode,
-//      reference address, flags; reverse_needed)
-//      and, on the frames a step returns, the sum of the pixel gradients owned
-//      by each colour-register version (the stored priority switch);
-//   2. sweeps the tape backwards, carrying adjoints of A, X, Y, the timer
+// every segment.  The backward pass runs in two kernels:
+//   1. k_soft_recompute recomputes a group of segments at once, each from its
+//      checkpoint, recording one 4-byte tape entry per instruction the sweep
+//      acts on (opcode, reference address, flags; reverse_needed) and, on the
+//      frames a step returns, the sum of the pixel gradients owned by each
+//      colour-register version (the stored priority switch);
+//   2. k_soft_sweep, segment by segment from the last, sweeps the tape
+//      backwards (one env per warp), carrying adjoints of A, X, Y, the timer
 //      value, the three colour registers and the 128 RAM cells (in shared
 //      memory), with the surrogate rules:
 //        reads   relaxed read of Eq. s-read w.r.t. memory contents: RAM reads
@@ -22,7 +22,7 @@
 //        ALU     ADC (1, 1), SBC (1, -1), AND/ORA/EOR (1, 1), shifts,
 //                rotates, increments and transfers 1, compares nothing;
 //        indices addresses, PC, SP and flags carry nothing;
-//   3. hands the adjoints at the segment start to the previous segment.
+//      and hands the adjoints at the segment start to the previous segment.
 // A final pass spreads the ROM impulses with the read window and optionally
 // sums the per-env ROM gradients per cartridge (a segmented reduction over
 // the envs of each cart, no atomics).
