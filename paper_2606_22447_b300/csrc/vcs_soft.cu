@@ -853,7 +853,17 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
   p.ckpt = t->ckpt;
   p.seg_steps = t->seg_steps;
   p.seg_counts = t->seg_counts;
-  int le = launch_soft_forward(p, b->n_blocks, b->E, stream);
+  // Without screen outputs the forward draws nothing, so replicas have no
+  // work to share: one lane per env in blocks of kWideEnvsPerBlock (measured
+  // 31 % faster than four replicas on 4096 envs of the 4K / F8 mix)
+  int le;
+  if (!screen_out) {
+    p.blocks = b->wide_blocks;
+    p.tpe = 1;
+    le = launch_soft_forward(p, b->wide_n_blocks, kWideEnvsPerBlock, stream);
+  } else {
+    le = launch_soft_forward(p, b->n_blocks, b->E, stream);
+  }
   if (le) {
     vcs_status st = vcs_cuda_fail(b, (cudaError_t)le, "soft forward launch");
     free_tape(t);
