@@ -187,9 +187,11 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False)
     from paper_2606_22447_b300 import Batch, default_config, synth
     roms = synth.config_carts(SEED, mappers)
     ec = synth.env_cart_round_robin(n_envs, len(mappers))
-    # four replicas per env: the backward's recompute draws every frame's
-    # pixel gradients, which the replicas share
-    b = Batch(roms, mappers, ec, default_config(segment_frames=64, threads_per_env=4,
+    # eight replicas per env: a single segment's recompute (one lane's
+    # latency bounds it) sums every frame's pixel gradients, which the
+    # replicas share; the forward and large recompute groups run one lane per
+    # env whatever this is
+    b = Batch(roms, mappers, ec, default_config(segment_frames=64, threads_per_env=8,
                                                 position_sampler=1 if sampler else 0))
     u = torch.from_numpy(synth.action_inputs(synth.actions(SEED, n_envs, n_frames))).cuda()
     rng = np.random.default_rng(SEED)
