@@ -14,6 +14,7 @@ from tests.gpu_util import gpu_rollout, make_batch, torch_cuda
 pytestmark = pytest.mark.gpu
 
 MAPPERS = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
+BANKED = [synth.MAPPER_F6, synth.MAPPER_F4, synth.MAPPER_F8]
 
 
 def _oracle_study(rom, mapper, warm, action, T, alpha, n):
@@ -37,10 +38,14 @@ def _oracle_study(rom, mapper, warm, action, T, alpha, n):
     return n_div, [c["relaxed_reads"], c["relaxed_reads_exact"], c["branches"], c["branches_exact"]], f.ram()
 
 
-@pytest.mark.parametrize("T,alpha,warm", [(0.14, 6.0, 0), (0.15, 6.0, 0), (0.2, 6.0, 2), (0.14, 2.0, 0),
-                                          (0.14, 3.0, 2), (0.01, 20.0, 0), (1.0, 6.0, 0)])
-def test_full_divergence_matches_oracle(T, alpha, warm):
+@pytest.mark.parametrize("T,alpha,warm,mappers", [(0.14, 6.0, 0, MAPPERS), (0.15, 6.0, 0, MAPPERS),
+                                                  (0.2, 6.0, 2, MAPPERS), (0.14, 2.0, 0, MAPPERS),
+                                                  (0.14, 3.0, 2, MAPPERS), (0.01, 20.0, 0, MAPPERS),
+                                                  (1.0, 6.0, 0, MAPPERS), (0.15, 6.0, 2, BANKED),
+                                                  (0.14, 2.0, 0, BANKED)])
+def test_full_divergence_matches_oracle(T, alpha, warm, mappers):
     torch = torch_cuda()
+    MAPPERS = mappers
     n_envs, n = 9, 3000
     roms = synth.config_carts(95, MAPPERS)
     ec = (np.arange(n_envs) % 3).astype(np.int32)

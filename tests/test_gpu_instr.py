@@ -29,17 +29,19 @@ def _oracle_steps(rom, mapper, actions, n_instr):
     return rams, status
 
 
-@pytest.mark.parametrize("n_instr,spl,epb", [(1000, 0, 0), (997, 2, 8), (3001, 0, 32), (1, 0, 0)])
-def test_hard_instruction_steps_match_oracle(n_instr, spl, epb):
+@pytest.mark.parametrize("n_instr,spl,epb,banked", [(1000, 0, 0, False), (997, 2, 8, False), (3001, 0, 32, False),
+                                                    (1, 0, 0, False), (1999, 0, 0, True)])
+def test_hard_instruction_steps_match_oracle(n_instr, spl, epb, banked):
     n_envs = 33
     steps = 6 if n_instr > 1 else 40
-    roms = synth.config_carts(81, MAPPERS)
+    mappers = [synth.MAPPER_F6, synth.MAPPER_F4, synth.MAPPER_F8] if banked else MAPPERS
+    roms = synth.config_carts(81, mappers)
     ec = (np.arange(n_envs) % 3).astype(np.int32)
-    b = make_batch(roms, MAPPERS, ec, step_instructions=n_instr, steps_per_launch=spl, envs_per_block=epb)
+    b = make_batch(roms, mappers, ec, step_instructions=n_instr, steps_per_launch=spl, envs_per_block=epb)
     acts = synth.actions(82, n_envs, steps)
     ram, _, st = gpu_rollout(b, acts, 1, screens=False)
     for e in range(n_envs):
-        r, s = _oracle_steps(roms[ec[e]], MAPPERS[ec[e]], acts[:, e], n_instr)
+        r, s = _oracle_steps(roms[ec[e]], mappers[ec[e]], acts[:, e], n_instr)
         assert_env_equal(e, ram[:, e], r, "RAM")
         assert_env_equal(e, st[:, e], s, "status")
 
