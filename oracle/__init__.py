@@ -53,6 +53,7 @@ def lib():
         L.ovcs_get_counters.argtypes = [vp, C.POINTER(Counters)]
         L.ovcs_get_state.argtypes = [vp, u32p]
         L.ovcs_get_ram.argtypes = [vp, u8p]
+        L.ovcs_get_cart_ram.argtypes = [vp, u8p]
         L.ovcs_trace.restype = C.c_int
         L.ovcs_trace.argtypes = [vp, C.c_int, C.c_int, u32p]
         L.ovcs_set_regs.argtypes = [vp] + [C.c_int] * 6
@@ -113,16 +114,26 @@ class SoftGraph:
     def n_nodes(self) -> int:
         return lib().ogrf_nodes(self.h)
 
-    def reverse(self):
+    def reverse(self, cart_ram: bool = False):
+        """(grad ROM, grad initial RAM [128], grad inputs [n_steps][5]), and
+        with cart_ram the gradient of the initial Superchip RAM [128] too."""
         g_rom = np.zeros(self.rom_size)
-        g_ram0 = np.zeros(128)
+        g_ram0 = np.zeros(256)
         g_u = np.zeros((self.n_steps, 5))
         lib().ogrf_reverse(self.h, _dp(g_rom), _dp(g_ram0), _dp(g_u))
-        return g_rom, g_ram0, g_u
+        if cart_ram:
+            return g_rom, g_ram0[:128], g_u, g_ram0[128:]
+        return g_rom, g_ram0[:128], g_u
 
     def _args(self, d_rom, d_ram0, d_u):
+        """d_ram0: 128 RIOT cells, or 256 (then the Superchip's RAM)."""
         f = lambda a, n: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(n)
-        return (f(d_rom, self.rom_size), f(d_ram0, 128), f(d_u, self.n_steps * 5))
+        if d_ram0 is not None:
+            d = np.zeros(256)
+            r = np.asarray(d_ram0, dtype=np.float64).reshape(-1)
+            d[:len(r)] = r
+            d_ram0 = d
+        return (f(d_rom, self.rom_size), f(d_ram0, 256), f(d_u, self.n_steps * 5))
 
     def tangent(self, d_rom=None, d_ram0=None, d_u=None) -> float:
         a = self._args(d_rom, d_ram0, d_u)
@@ -211,6 +222,12 @@ class Oracle:
     def ram(self) -> np.ndarray:
         o = np.zeros(128, np.uint8)
         lib().ovcs_get_ram(self.h, _p(o, C.c_uint8))
+        return o
+
+    def cart_ram(self) -> np.ndarray:
+        """The Superchip's 128 bytes of cartridge RAM (zero for other carts)."""
+        o = np.zeros(128, np.uint8)
+        lib().ovcs_get_cart_ram(self.h, _p(o, C.c_uint8))
         return o
 
     def trace(self, action: int, n: int) -> np.ndarray:

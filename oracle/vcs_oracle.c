@@ -19,7 +19,8 @@
  *     P0 > PF > BK unless CTRLPF bit 2 (PF > P0 > BK);
  *  A7 power-on: A=X=Y=0, SP=$FD, P=$34, PC from $1FFC/D, RAM and TIA zero,
  *     the timer as if 0 had been written to T1024T at cycle 0, banked carts
- *     (F8, F6, F4) in their last bank;
+ *     (F8, F6, F4 and their Superchip variants) in their last bank, the
+ *     Superchip's RAM zero;
  *  A8 timer: a write of V at cycle t_w makes INTIM = V - ceil(k / I) at
  *     t_w + k until that would go negative; from k_u = V*I + 1 on it reads
  *     (0xFF - (k - k_u)) & 0xFF and TIMINT bit 7 is set;
@@ -29,6 +30,12 @@
  *  A11 NMOS decimal mode per the published note on decimal mode;
  *  A12 pushed P always has bits 4 and 5 set (PHP and BRK are the only
  *     pushes of P on a 6507); BRK vectors through $1FFE.
+ *  Superchip carts (F8SC, F6SC, F4SC: the banked formats plus 128 bytes of
+ *  cartridge RAM) write that RAM at $1000-$107F and read it at $1080-$10FF
+ *  of the cartridge window, in every bank; a read of the write port returns
+ *  the ROM byte under it and writes nothing (no bus-contention model).  In
+ *  soft mode the cartridge RAM is a second 128-cell memory tensor: its
+ *  reads are relaxed within it and its writes are one-hot, like RIOT RAM.
  *  The paper's 38 extra opcode bytes (USBC, the unofficial NOPs, LAX, SAX)
  *  are executed; every other undocumented opcode jams the CPU: from then on
  *  each instruction slot
@@ -73,7 +80,7 @@ struct ogrf {
   uint8_t* rom_copy;
   int rom_size;
   int32_t rom0, ram0, u0;
-  double ram0_val[128];
+  double ram0_val[256];   /* RIOT RAM, then cartridge RAM */
   double* u_val;
   int n_steps;
   double tau, alpha;
@@ -93,10 +100,11 @@ struct ovcs {
   uint64_t cyc;
   int jammed;
   /* memory */
-  uint8_t ram[128];
+  uint8_t ram[256];        /* RIOT RAM, then the Superchip's cartridge RAM */
   uint8_t* rom;
   uint32_t rom_size;
   int mapper, bank;
+  int sc;                  /* Superchip variant (cartridge RAM at $1000-$10FF) */
   /* RIOT */
   uint8_t intim;
   uint32_t interval, phase;
@@ -115,7 +123,7 @@ struct ovcs {
   ovcs_counters cnt;
   /* soft mode */
   ogrf* g;
-  int32_t nA, nX, nY, nV, nC[3], nRAM[128];
+  int32_t nA, nX, nY, nV, nC[3], nRAM[256];
   int32_t nPos, nHM;       /* deviations of the P0 position and of HMP0 (sampler) */
   int sampler;             /* 1: the differentiable position sampler is on */
   int step_instr;          /* > 0: a step is this many instruction slots, not frames */
@@ -187,7 +195,9 @@ static int32_t g_read_rom(ovcs* s, int base, int M, int a0) {
   return id;
 }
 
-static int32_t g_read_ram(ovcs* s, int a0) {
+/* Relaxed read of cell a0 of the 128-cell RAM tensor whose cells start at
+ * index tb of the RAM nodes (0: RIOT RAM, 128: the Superchip's RAM). */
+static int32_t g_read_ram(ovcs* s, int tb, int a0) {
   if (!s->g) return 0;
   ogrf* g = s->g;
   int lo, hi;
@@ -201,7 +211,7 @@ static int32_t g_read_ram(ovcs* s, int a0) {
   onode* nd = &g->nd[id];
   nd->lo = (int16_t)lo; nd->n = (uint8_t)n; nd->a0 = (int16_t)a0;
   nd->pool = g->pn;
-  for (int i = 0; i < n; i++) g->pnode[g->pn + i] = s->nRAM[lo + i];
+  for (int i = 0; i < n; i++) g->pnode[g->pn + i] = s->nRAM[tb + lo + i];
   g->pn += n;
   return id;
 }
@@ -350,17 +360,30 @@ static void tick(ovcs* s) {
 
 static void idle(ovcs* s) { tick(s); }
 
+/* The banked format under a Superchip variant (F8SC -> F8, ...). */
+static int base_mapper(const ovcs* s) { return s->sc ? s->mapper - 3 : s->mapper; }
+
 static void hotspot(ovcs* s, uint16_t a) {
   /* F8: $1FF8-$1FF9, F6: $1FF6-$1FF9, F4: $1FF4-$1FFB select banks 0.. */
   static const int first[5] = {0, 0, 0x1FF8, 0x1FF6, 0x1FF4}, count[5] = {0, 0, 2, 4, 8};
-  if (a >= first[s->mapper] && a < first[s->mapper] + count[s->mapper]) {
-    s->bank = a - first[s->mapper];
+  const int m = base_mapper(s);
+  if (a >= first[m] && a < first[m] + count[m]) {
+    s->bank = a - first[m];
   }
 }
 
+/* Superchip ports: cell of the cartridge RAM read (write) at cartridge
+ * address a, or -1. */
+static int sc_read_cell(const ovcs* s, uint16_t a) {
+  return s->sc && (a & 0x1F80) == 0x1080 ? 128 + (a & 0x7F) : -1;
+}
+static int sc_write_cell(const ovcs* s, uint16_t a) {
+  return s->sc && (a & 0x1F80) == 0x1000 ? 128 + (a & 0x7F) : -1;
+}
+
 static void rom_map(const ovcs* s, uint16_t a, int* base, int* M, int* idx) {
-  if (s->mapper == 0) { *base = 0; *M = 2048; *idx = a & 0x7FF; }
-  else if (s->mapper == 1) { *base = 0; *M = 4096; *idx = a & 0xFFF; }
+  if (base_mapper(s) == 0) { *base = 0; *M = 2048; *idx = a & 0x7FF; }
+  else if (base_mapper(s) == 1) { *base = 0; *M = 4096; *idx = a & 0xFFF; }
   else { *base = s->bank * 4096; *M = 4096; *idx = a & 0xFFF; }
 }
 
@@ -398,7 +421,12 @@ static val rd(ovcs* s, uint16_t addr) {
   tick(s);
   uint16_t a = addr & 0x1FFF;
   val r = {0, 0};
-  if (a & 0x1000) {
+  if (sc_read_cell(s, a) >= 0) {   /* the Superchip's read port */
+    const int i = a & 0x7F;
+    r.v = s->full ? full_cast(s, s->ram + 128, 128, i) : s->ram[128 + i];
+    r.n = g_read_ram(s, 128, i);
+    s->cnt.ram_reads++;
+  } else if (a & 0x1000) {
     hotspot(s, a);
     int base, M, idx;
     rom_map(s, a, &base, &M, &idx);
@@ -413,7 +441,7 @@ static val rd(ovcs* s, uint16_t addr) {
     }
   } else if (!(a & 0x200)) {
     r.v = s->full ? full_cast(s, s->ram, 128, a & 0x7F) : s->ram[a & 0x7F];
-    r.n = g_read_ram(s, a & 0x7F);
+    r.n = g_read_ram(s, 0, a & 0x7F);
     s->cnt.ram_reads++;
   } else if (!(a & 0x04)) {
     switch (a & 3) {
@@ -440,6 +468,7 @@ static val rd(ovcs* s, uint16_t addr) {
 /* Side-effect-free read (opcode and debug); still a bus cycle when `cycle`. */
 static uint8_t peek_raw(ovcs* s, uint16_t addr) {
   uint16_t a = addr & 0x1FFF;
+  if (sc_read_cell(s, a) >= 0) return s->ram[sc_read_cell(s, a)];
   if (a & 0x1000) {
     int base, M, idx;
     rom_map(s, a, &base, &M, &idx);
@@ -464,7 +493,16 @@ static uint8_t fetch_opcode(ovcs* s) {
 static void wr(ovcs* s, uint16_t addr, val x) {
   tick(s);
   uint16_t a = addr & 0x1FFF;
-  if (a & 0x1000) { hotspot(s, a); return; }
+  if (a & 0x1000) {
+    hotspot(s, a);
+    const int cell = sc_write_cell(s, a);
+    if (cell >= 0) {   /* the Superchip's write port */
+      s->ram[cell] = x.v;
+      s->nRAM[cell] = x.n;
+      s->cnt.ram_writes++;
+    }
+    return;
+  }
   if (!(a & 0x80)) {
     tia_write(s, a & 0x3F, x);
     if (s->wsync) {
@@ -956,13 +994,14 @@ static int step_instruction(ovcs* s) {
 /* ------------------------------------------------------------------ */
 
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
-  static const uint32_t sz[5] = {2048, 4096, 8192, 16384, 32768};
-  if (mapper < 0 || mapper > 4 || rom_size != sz[mapper]) return NULL;
+  static const uint32_t sz[8] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768};
+  if (mapper < 0 || mapper > 7 || rom_size != sz[mapper]) return NULL;
   ovcs* s = (ovcs*)calloc(1, sizeof(ovcs));
   s->rom = (uint8_t*)malloc(rom_size);
   memcpy(s->rom, rom, rom_size);
   s->rom_size = rom_size;
   s->mapper = mapper;
+  s->sc = mapper >= 5;
   s->ystart = ystart;
   ovcs_reset(s);
   return s;
@@ -1081,6 +1120,7 @@ void ovcs_get_state(const ovcs* s, uint32_t* o) {
 }
 
 void ovcs_get_ram(const ovcs* s, uint8_t* out128) { memcpy(out128, s->ram, 128); }
+void ovcs_get_cart_ram(const ovcs* s, uint8_t* out128) { memcpy(out128, s->ram + 128, 128); }
 
 int ovcs_trace(ovcs* s, int action, int n, uint32_t* out) {
   int u[5];
@@ -1168,14 +1208,14 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   g->rom0 = (int32_t)g->n;
   for (uint32_t i = 0; i < s->rom_size; i++) g_new(s, NK_LEAF);
   g->ram0 = (int32_t)g->n;
-  for (int i = 0; i < 128; i++) g_new(s, NK_LEAF);
+  for (int i = 0; i < 256; i++) g_new(s, NK_LEAF);   /* RIOT RAM, then cartridge RAM */
   g->u0 = (int32_t)g->n;
   for (int i = 0; i < 5 * n_steps; i++) g_new(s, NK_LEAF);
-  for (int i = 0; i < 128; i++) g->ram0_val[i] = s->ram[i];
+  for (int i = 0; i < 256; i++) g->ram0_val[i] = s->ram[i];
   g->u_val = (double*)malloc(sizeof(double) * (size_t)(5 * n_steps > 0 ? 5 * n_steps : 1));
   for (int i = 0; i < 5 * n_steps; i++) g->u_val[i] = u[i];
   /* ROM-read nodes address ROM leaves at rom0 + base + index */
-  for (int i = 0; i < 128; i++) s->nRAM[i] = g->ram0 + i;
+  for (int i = 0; i < 256; i++) s->nRAM[i] = g->ram0 + i;
   s->nA = s->nX = s->nY = s->nV = 0;
   s->nC[0] = s->nC[1] = s->nC[2] = 0;
   s->nPos = s->nHM = 0;
@@ -1196,7 +1236,7 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   }
   s->g = NULL;
   s->gs = s->gs_all = NULL;
-  for (int i = 0; i < 128; i++) s->nRAM[i] = 0;
+  for (int i = 0; i < 256; i++) s->nRAM[i] = 0;
   s->nA = s->nX = s->nY = s->nV = 0;
   s->nC[0] = s->nC[1] = s->nC[2] = 0;
   s->nPos = s->nHM = 0;
@@ -1236,14 +1276,14 @@ void ogrf_reverse(ogrf* g, double* grad_rom, double* grad_ram0, double* grad_u) 
     }
   }
   for (int i = 0; i < g->rom_size; i++) grad_rom[i] = adj[g->rom0 + i];
-  for (int i = 0; i < 128; i++) grad_ram0[i] = adj[g->ram0 + i];
+  for (int i = 0; i < 256; i++) grad_ram0[i] = adj[g->ram0 + i];
   for (int i = 0; i < 5 * g->n_steps; i++) grad_u[i] = adj[g->u0 + i];
   free(adj);
 }
 
 static void set_leaves(const ogrf* g, double* d, const double* d_rom, const double* d_ram0, const double* d_u) {
   for (int i = 0; i < g->rom_size; i++) d[g->rom0 + i] = d_rom ? d_rom[i] : 0.0;
-  for (int i = 0; i < 128; i++) d[g->ram0 + i] = d_ram0 ? d_ram0[i] : 0.0;
+  for (int i = 0; i < 256; i++) d[g->ram0 + i] = d_ram0 ? d_ram0[i] : 0.0;
   for (int i = 0; i < 5 * g->n_steps; i++) d[g->u0 + i] = d_u ? d_u[i] : 0.0;
 }
 
@@ -1284,7 +1324,7 @@ double ogrf_eval(ogrf* g, const double* d_rom, const double* d_ram0, const doubl
     h[g->rom0 + i] = g->rom[i];
     x[g->rom0 + i] = g->rom[i] + (d_rom ? d_rom[i] : 0.0);
   }
-  for (int i = 0; i < 128; i++) {
+  for (int i = 0; i < 256; i++) {
     h[g->ram0 + i] = g->ram0_val[i];
     x[g->ram0 + i] = g->ram0_val[i] + (d_ram0 ? d_ram0[i] : 0.0);
   }

@@ -57,7 +57,9 @@ typedef struct {
 
 /* mapper: 0 = 2K, 1 = 4K, 2 = F8 (8 KB, hotspots $1FF8-9), 3 = F6 (16 KB,
  * $1FF6-9), 4 = F4 (32 KB, $1FF4-B): any access to hotspot j selects 4 KB
- * bank j.  rom is copied.  NULL on a bad size. */
+ * bank j; 5, 6, 7 = F8SC, F6SC, F4SC: the same with 128 bytes of cartridge
+ * RAM written at $1000-$107F and read at $1080-$10FF.  rom is copied.  NULL
+ * on a bad size. */
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart);
 void ovcs_free(ovcs* s);
 /* Power-on state (A7 of the design notes). */
@@ -93,6 +95,7 @@ void ovcs_get_counters(const ovcs* s, ovcs_counters* out);
 /* Machine state as 32 words (layout in the .c file). */
 void ovcs_get_state(const ovcs* s, uint32_t* out32);
 void ovcs_get_ram(const ovcs* s, uint8_t* out128);
+void ovcs_get_cart_ram(const ovcs* s, uint8_t* out128);   /* Superchip RAM (zero otherwise) */
 /* Run n instructions, recording per instruction: pc, opcode, A, X, Y, SP,
  * P, cycle (low 32 bits), scanline, line clock.  Returns instructions run. */
 int ovcs_trace(ovcs* s, int action, int n, uint32_t* out10);
@@ -120,8 +123,9 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
                         const double* grad_ram, const double* grad_screen,
                         double* ram_out, double* screen_out);
 void ogrf_free(ogrf* g);
-/* Reverse sweep: d L / d (ROM bytes [rom_size], initial RAM [128],
- * inputs [n_steps][5]). */
+/* Reverse sweep: d L / d (ROM bytes [rom_size], initial RAM [256]: the
+ * RIOT RAM then the Superchip's cartridge RAM, inputs [n_steps][5]).  The
+ * tangent and evaluation sweeps take d_ram0 in the same 256-cell layout. */
 void ogrf_reverse(ogrf* g, double* grad_rom, double* grad_ram0, double* grad_u);
 /* Tangent sweep: directional derivative of L along (d_rom, d_ram0, d_u). */
 double ogrf_tangent(ogrf* g, const double* d_rom, const double* d_ram0, const double* d_u);

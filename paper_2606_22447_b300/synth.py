@@ -27,10 +27,17 @@ MASK64 = (1 << 64) - 1
 GAMMA = 0x9E3779B97F4A7C15
 
 MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_F6, MAPPER_F4 = 0, 1, 2, 3, 4
-MAPPER_SIZE = {MAPPER_2K: 2048, MAPPER_4K: 4096, MAPPER_F8: 8192, MAPPER_F6: 16384, MAPPER_F4: 32768}
+# Superchip variants: the banked format plus 128 bytes of cartridge RAM,
+# written at $1000-$107F and read at $1080-$10FF
+MAPPER_F8SC, MAPPER_F6SC, MAPPER_F4SC = 5, 6, 7
+MAPPER_SC_BASE = {MAPPER_F8SC: MAPPER_F8, MAPPER_F6SC: MAPPER_F6, MAPPER_F4SC: MAPPER_F4}
+MAPPER_SIZE = {MAPPER_2K: 2048, MAPPER_4K: 4096, MAPPER_F8: 8192, MAPPER_F6: 16384, MAPPER_F4: 32768,
+               MAPPER_F8SC: 8192, MAPPER_F6SC: 16384, MAPPER_F4SC: 32768}
 # banked mappers: number of 4 KB banks and the first hotspot (bank j at hot + j)
-MAPPER_BANKS = {MAPPER_F8: 2, MAPPER_F6: 4, MAPPER_F4: 8}
-MAPPER_HOTSPOT = {MAPPER_F8: 0x1FF8, MAPPER_F6: 0x1FF6, MAPPER_F4: 0x1FF4}
+MAPPER_BANKS = {MAPPER_F8: 2, MAPPER_F6: 4, MAPPER_F4: 8, MAPPER_F8SC: 2, MAPPER_F6SC: 4, MAPPER_F4SC: 8}
+MAPPER_HOTSPOT = {MAPPER_F8: 0x1FF8, MAPPER_F6: 0x1FF6, MAPPER_F4: 0x1FF4,
+                  MAPPER_F8SC: 0x1FF8, MAPPER_F6SC: 0x1FF6, MAPPER_F4SC: 0x1FF4}
+SC_WRITE, SC_READ = 0x1000, 0x1080
 
 # ALE action order (18 actions) and their joystick components
 # (right, left, down, up, fire).
@@ -366,6 +373,7 @@ class _Gen:
         self.ptrs = []          # (pointer label, target label) for JMP (ind)
         self.n_lbl = 0
         self.allow_brk = True
+        self.cram = False       # Superchip cart: also read and write its RAM
 
     def lbl(self, prefix="L"):
         self.n_lbl += 1
@@ -389,14 +397,18 @@ class _Gen:
             a.op(mnem, mode, r.range(0x80, 0xFF))
         elif mode == "abs":
             c = r.below(10)
-            if c < 4:
+            if self.cram and r.chance(0.3):
+                a.op(mnem, "abs", SC_READ + r.below(128))
+            elif c < 4:
                 a.op(mnem, "abs", r.range(0x0080, 0x00FF))
             elif c < 7 or not allow_io:
                 a.op(mnem, "abs", ("TABLE", r.below(TABLE_LEN)))
             else:
                 a.op(mnem, "abs", r.pick((SWCHA, SWCHB, INTIM, TIMINT, INPT4)))
         elif mode in ("absx", "absy"):
-            if r.chance(0.5):
+            if self.cram and r.chance(0.3):
+                a.op(mnem, mode, SC_READ + r.below(128))
+            elif r.chance(0.5):
                 a.op(mnem, mode, ("TABLE", r.below(64)))
             else:
                 a.op(mnem, mode, r.range(0x0080, 0x00FF))
@@ -411,6 +423,16 @@ class _Gen:
         """Emit a store of the register named by `mnem` into the work area."""
         r, a = self.r, self.a
         reg = mnem[2]
+        if self.cram and r.chance(0.3):   # into the Superchip's RAM (write port)
+            j = r.below(128)
+            if reg == "A" and r.chance(0.5):
+                k = r.below(j + 1)
+                ix = r.pick(("X", "Y"))
+                a.op("LD" + ix, "imm", k)
+                a.op(mnem, "abs" + ix.lower(), SC_WRITE + j - k)
+            else:
+                a.op(mnem, "abs", SC_WRITE + j)
+            return
         choices = ["zp", "abs"] + {"A": ["zpx", "absx", "absy", "indx", "indy"],
                                    "X": ["zpy"], "Y": ["zpx"]}[reg]
         mode = r.pick(choices)
@@ -645,10 +667,14 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     lines of WSYNC + random block + stores to colour / playfield / player
     registers; overscan with TIM64T=35 and more work; JMP back.  F8 images
     place the visible kernel in bank 0 and switch banks through trampolines
-    at the same offsets in both banks.
+    at the same offsets in both banks.  Superchip variants (F8SC, F6SC,
+    F4SC) are the banked images with their code moved past the cartridge
+    RAM ports ($1000-$10FF) and random reads and stores of that RAM.
     """
+    sc = mapper in MAPPER_SC_BASE
+    mapper = MAPPER_SC_BASE.get(mapper, mapper)
     if mapper in (MAPPER_F6, MAPPER_F4):
-        return _generate_multibank(seed, cart, mapper)
+        return _generate_multibank(seed, cart, mapper, sc)
     r = SplitMix64(seed, cart, 0x0CA7)
     origin = 0xF800 if mapper == MAPPER_2K else 0xF000
     bank_size = 2048 if mapper == MAPPER_2K else 4096
@@ -661,6 +687,9 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
 
     a = Asm(origin, bank_size)
     g = _Gen(r, a)
+    if sc:   # the Superchip's RAM ports hide the first 256 bytes of each bank
+        a.at(0x100)
+        g.cram = True
     # leaf subroutines first: only reachable through JSR
     g.emit_subs(4)
     a.label("RESET")
@@ -760,6 +789,9 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
 
     b = Asm(origin, bank_size)
     g0 = _Gen(SplitMix64(seed, cart, 0x0CA8), b)
+    if sc:
+        b.at(0x100)
+        g0.cram = True
     b.label("KERNEL0")
     _emit_kernel(b, g0, n_lines, "TRAMP0")
     _emit_table(b, g0.r)
@@ -781,7 +813,7 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     return bytes(bank0) + bytes(bank1)
 
 
-def _generate_multibank(seed: int, cart: int, mapper: int) -> bytes:
+def _generate_multibank(seed: int, cart: int, mapper: int, sc: bool = False) -> bytes:
     """F6 / F4 images: the last bank (where the machine powers on) holds the
     init, VBLANK and overscan code; each other bank k holds its own visible
     kernel.  Every frame the main bank picks a kernel bank from the
@@ -790,7 +822,8 @@ def _generate_multibank(seed: int, cart: int, mapper: int) -> bytes:
     trampoline: BIT of hotspot k at offset tramp + 3k, bank k continuing at
     tramp + 3k + 3 with a JMP to its kernel; bank k returns with BIT of the
     main bank's hotspot at ret + 3k, the main bank continuing at ret + 3k + 3
-    with a JMP to the overscan."""
+    with a JMP to the overscan.  Superchip images (sc) start their code past
+    the RAM ports' 256 bytes and use the cartridge RAM."""
     nb, hot = MAPPER_BANKS[mapper], MAPPER_HOTSPOT[mapper]
     main = nb - 1
     bank_size, origin = 4096, 0xF000
@@ -799,6 +832,9 @@ def _generate_multibank(seed: int, cart: int, mapper: int) -> bytes:
     n_lines, vb_budget, vb_loops, os_budget = 16, 1000, 2, 900
     a = Asm(origin, bank_size)
     g = _Gen(r, a)
+    if sc:
+        a.at(0x100)
+        g.cram = True
     g.emit_subs(4)
     a.label("RESET")
     a.op("SEI")
@@ -899,6 +935,9 @@ def _generate_multibank(seed: int, cart: int, mapper: int) -> bytes:
     for k in range(nb - 1):
         b = Asm(origin, bank_size)
         gk = _Gen(SplitMix64(seed, cart, 0x0CA8 + k), b)
+        if sc:
+            b.at(0x100)
+            gk.cram = True
         b.label("KERNEL")
         _emit_kernel(b, gk, n_lines, "RET")
         _emit_table(b, gk.r)

@@ -390,3 +390,111 @@ def test_boot_protocol_frames_and_reset_switch():
     o2 = oracle.Oracle(switches_rom(), synth.MAPPER_4K)
     o2.boot(60, 0, 0)
     assert o2.ram()[0x00] == 60 - 1 and o2.ram()[0x01] == 0x0B   # no RESET frames: never pressed
+
+
+# ---------------------------------------------------------------------------
+# Superchip cartridge RAM
+# ---------------------------------------------------------------------------
+
+def _superchip_image(mapper):
+    """Banked image whose last bank writes the cartridge RAM through the
+    write port, reads it back through the read port (plain and indexed),
+    reads the write port (ROM), writes the read port (nothing), copies a
+    three-byte routine into the RAM and calls it there, then switches to
+    bank 0, which reads the RAM again.  Each bank's byte at offset $005 is
+    $77 + bank and its bytes at $080-$0FF are $E0 + bank, so a read that
+    reaches the ROM instead of the RAM is recognisable."""
+    nb, hot = synth.MAPPER_BANKS[mapper], synth.MAPPER_HOTSPOT[mapper]
+
+    def header(a, j):
+        a.at(0x005)
+        a.byte(0x77 + j)
+        a.at(0x080)
+        for _ in range(0x80):
+            a.byte(0xE0 + j)
+        a.at(0x100)
+
+    def vectors(a):
+        a.at(4096 - 6)
+        a.word(0xF100), a.word(0xF100), a.word(0xF100)
+        return bytes(a.resolve())
+
+    a = synth.Asm(0xF000, 4096)
+    header(a, nb - 1)
+    a.op("LDA", "imm", 0x5A)
+    a.op("STA", "abs", 0x1005)        # cart RAM[5] = $5A
+    a.op("LDA", "imm", 0xC3)
+    a.op("LDX", "imm", 2)
+    a.op("STA", "absx", 0x1010)       # cart RAM[$12] = $C3
+    a.op("LDA", "abs", 0x1085)
+    a.op("STA", "zp", 0x80)           # RAM[0] = cart RAM[5]
+    a.op("LDY", "imm", 0x0D)
+    a.op("LDA", "absy", 0x1085)
+    a.op("STA", "zp", 0x81)           # RAM[1] = cart RAM[$12]
+    a.op("LDA", "abs", 0x1005)
+    a.op("STA", "zp", 0x82)           # RAM[2] = the ROM under the write port
+    a.op("LDA", "imm", 0x99)
+    a.op("STA", "abs", 0x1080)        # a write to the read port: nothing
+    a.op("LDA", "abs", 0x1080)
+    a.op("STA", "zp", 0x83)           # RAM[3] = cart RAM[0]
+    for k, v in enumerate((0xA9, 0x42, 0x60)):   # LDA #$42; RTS
+        a.op("LDA", "imm", v)
+        a.op("STA", "abs", 0x1020 + k)
+    a.op("JSR", "abs", 0x10A0)        # run it from the cartridge RAM
+    a.op("STA", "zp", 0x84)
+    a.op("LDA", "abs", hot)           # -> bank 0, which resumes at the next offset
+    resume = a.pc - 0xF000
+    last = vectors(a)
+    banks = []
+    for j in range(nb - 1):
+        b = synth.Asm(0xF000, 4096)
+        header(b, j)
+        b.at(resume)
+        b.op("LDA", "abs", 0x1085)
+        b.op("STA", "zp", 0x85)
+        b.label("HALT")
+        b.op("JMP", "abs", "HALT")
+        banks.append(vectors(b))
+    return b"".join(banks) + last
+
+
+@pytest.mark.parametrize("mapper", [synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC])
+def test_superchip_ram_ports(mapper):
+    """Writes at $1000-$107F store into the cartridge RAM, reads at
+    $1080-$10FF return it (in every bank, and as code), a read of the write
+    port returns the ROM byte there and a write to the read port changes
+    nothing.  The same image as a plain banked cart reads ROM throughout."""
+    nb = synth.MAPPER_BANKS[mapper]
+    rom = _superchip_image(mapper)
+    o = oracle.Oracle(rom, mapper)
+    for _ in range(200):
+        o.exec_one()
+    ram, cram = o.ram(), o.cart_ram()
+    assert o.bank() == 0
+    assert list(ram[:6]) == [0x5A, 0xC3, 0x77 + nb - 1, 0x00, 0x42, 0x5A]
+    want = np.zeros(128, np.uint8)
+    want[0x05], want[0x12], want[0x20:0x23] = 0x5A, 0xC3, (0xA9, 0x42, 0x60)
+    assert np.array_equal(cram, want)
+    base = synth.MAPPER_SC_BASE[mapper]
+    p = oracle.Oracle(rom, base)
+    for _ in range(200):
+        p.exec_one()
+    top = 0xE0 + nb - 1
+    # the plain cart: reads of $1085, $1092 and $1080 return ROM; its JSR
+    # then runs ROM bytes, so only the first four cells are pinned
+    assert list(p.ram()[:4]) == [top, top, 0x77 + nb - 1, top]
+    assert not p.cart_ram().any()
+
+
+def test_superchip_carts_use_their_ram():
+    """The generated Superchip carts run well-formed frames, keep code out of
+    the RAM ports' 256 bytes and leave values in the cartridge RAM."""
+    for mapper in (synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC):
+        rom = synth.config_carts(19, [mapper])[0]
+        assert len(rom) == synth.MAPPER_SIZE[mapper]
+        o = oracle.Oracle(rom, mapper)
+        for a in synth.actions(20, 1, 12)[:, 0]:
+            assert o.step(int(a), 2)[2] == 0
+        c = o.counters()
+        assert c["watchdog"] == 0 and c["frames"] == 24
+        assert np.count_nonzero(o.cart_ram()) >= 4

@@ -212,3 +212,72 @@ def test_colour_gradient_counts_owned_pixels():
             assert g_rom[i - 1] == pytest.approx(g_rom[i + 1], rel=1e-12)
             g_rom[lo:hi + 1] = 0
             assert np.abs(g_rom).max() < 1e-12
+
+
+def test_superchip_ram_is_a_second_read_tensor():
+    """LDA #k; STA $1005; LDA $1085; STA $80; LDA $1086; STA $81 on an F8SC
+    cart, L = RAM[$80] + 2 RAM[$81]: the cartridge RAM is a 128-cell tensor
+    of its own, so the reads of cells 5 and 6 are relaxed within it
+    (weights e^{-|i - a| / tau} over |i - a| <= W, renormalised), the write
+    of cell 5 is one-hot (the imm byte's read takes cell 5's weight) and the
+    initial cartridge RAM takes the other cells' weights."""
+    tau = 0.5
+    W = max(1, math.ceil(12 * tau))
+    def weights(a):
+        w = np.array([math.exp(-abs(i - a) / tau) if abs(i - a) <= W else 0.0 for i in range(128)])
+        return w / w.sum()
+    b1 = synth.Asm(0xF000, 4096)
+    b1.at(0x100)
+    b1.op("LDA", "imm", 0x3C)
+    b1.op("STA", "abs", 0x1005)
+    b1.op("LDA", "abs", 0x1085)
+    b1.op("STA", "zp", 0x80)
+    b1.op("LDA", "abs", 0x1086)
+    b1.op("STA", "zp", 0x81)
+    b1.label("HALT")
+    b1.op("JMP", "abs", "HALT")
+    b1.at(4096 - 6)
+    b1.word(0xF100), b1.word(0xF100), b1.word(0xF100)
+    b0 = synth.Asm(0xF000, 4096)
+    b0.at(4096 - 6)
+    b0.word(0xF100), b0.word(0xF100), b0.word(0xF100)
+    rom = bytes(b0.resolve()) + bytes(b1.resolve())
+    o = oracle.Oracle(rom, synth.MAPPER_F8SC)
+    gr = np.zeros((1, 128))
+    gr[0, 0], gr[0, 1] = 1.0, 2.0
+    g, ram_out, _ = o.soft_rollout(np.zeros((1, 5)), 1, tau, 6.0, gr, None)
+    assert ram_out[0, 0] == 0x3C and ram_out[0, 1] == 0
+    g_rom, g_ram0, g_u, g_cram0 = g.reverse(cart_ram=True)
+    w = weights(5) + 2 * weights(6)
+    # the imm byte's own read is relaxed over its 4 KB bank (an interior
+    # index: the same window shape, centred on offset $101)
+    imm = 4096 + 0x101
+    w_rom = np.zeros(g.rom_size)
+    w_rom[imm - W:imm + W + 1] = [math.exp(-abs(d) / tau) for d in range(-W, W + 1)]
+    w_rom /= w_rom.sum()
+    assert np.allclose(g_rom, w[5] * w_rom, rtol=0, atol=1e-12)
+    want = w.copy()
+    want[5] = 0.0
+    assert np.allclose(g_cram0, want, rtol=0, atol=1e-12)
+    assert not g_ram0.any() and not g_u.any()
+
+
+def test_superchip_reverse_equals_tangent_and_finite_differences():
+    """The transpose identity and central differences on a generated F6SC
+    cart, including the initial cartridge RAM's leaves."""
+    g = _soft_case(0.3, mapper=synth.MAPPER_F6SC)
+    g_rom, g_ram0, g_u, g_cram0 = g.reverse(cart_ram=True)
+    assert np.abs(g_cram0).max() > 0
+    rng = np.random.default_rng(9)
+    d_rom = rng.standard_normal(g.rom_size)
+    d_ram0 = rng.standard_normal(256)
+    d_u = rng.standard_normal((g.n_steps, 5))
+    lhs = float(g_rom @ d_rom + np.concatenate([g_ram0, g_cram0]) @ d_ram0 + (g_u * d_u).sum())
+    rhs = g.tangent(d_rom, d_ram0, d_u)
+    assert abs(lhs - rhs) <= 1e-9 * max(1.0, abs(lhs)), (lhs, rhs)
+    h = 1e-4
+    for i in np.argsort(-np.abs(g_cram0))[:6]:
+        d = np.zeros(256)
+        d[128 + i] = h
+        fd = (g.eval(d_ram0=d) - g.eval(d_ram0=-d)) / (2 * h)
+        assert abs(fd - g_cram0[i]) <= 1e-6 * max(1.0, abs(g_cram0).max())
