@@ -50,14 +50,16 @@ typedef enum {
   VCS_ERR_STATE = 7      /* call out of order (e.g. backward of a freed tape) */
 } vcs_status;
 
-/* Cartridge mappers (the 2K, 4K and F8 formats of the paper's per-game
- * conformance table, supplement).  F8 = 8 KB in two 4 KB banks, selected by
- * any access to $1FF8 (bank 0) or $1FF9 (bank 1); power-on selects bank 1. */
 /* Cartridge formats: 2K and 4K images; F8 (8 KB), F6 (16 KB) and F4 (32 KB)
  * bank-switched in 4 KB banks, an access (read or write) to hotspot j
  * ($1FF8 + j for F8, $1FF6 + j for F6, $1FF4 + j for F4) selecting bank j,
- * power-on in the last bank. */
-enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2, VCS_MAPPER_F6 = 3, VCS_MAPPER_F4 = 4 };
+ * power-on in the last bank; and their Superchip variants F8SC, F6SC, F4SC
+ * (the paper's mapper list, Section 4): the same banking plus 128 bytes of
+ * cartridge RAM, written at $1000-$107F and read at $1080-$10FF of the
+ * cartridge window in every bank (a read of the write port returns the ROM
+ * byte there; a write to the read port does nothing), zero at power-on. */
+enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2, VCS_MAPPER_F6 = 3, VCS_MAPPER_F4 = 4,
+       VCS_MAPPER_F8SC = 5, VCS_MAPPER_F6SC = 6, VCS_MAPPER_F4SC = 7 };
 
 /* Per-env status bits reported by vcs_step / vcs_rollout. */
 enum {
@@ -148,8 +150,8 @@ vcs_status vcs_config_default(vcs_config* cfg);
 /* Create a batch of n_envs machines over n_carts cartridges (Section 2.2;
  * "ROM as a weight tensor", Section 3.1).
  *  roms[c]      host pointer to cart c's image (rom_sizes[c] bytes: 2048,
- *               4096, 8192, 16384 or 32768 for mapper 2K, 4K, F8, F6, F4);
- *               copied.
+ *               4096, 8192, 16384 or 32768 for mapper 2K, 4K, F8, F6, F4;
+ *               8192, 16384, 32768 for F8SC, F6SC, F4SC); copied.
  *  mappers[c]   VCS_MAPPER_* of cart c.
  *  env_cart     host int32[n_envs]: the cart of each env (0..n_carts-1).
  *  cfg          nullable (defaults).
@@ -368,6 +370,10 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
  * screen_out (or of the broadcast loss weights `w`) with respect to
  *   grad_rom           device float[n_envs][rom_stride] per env (nullable)
  *   grad_ram0          device float[n_envs][128] (nullable)
+ *   grad_cart_ram0     device float[n_envs][128] (nullable): the Superchip
+ *                      RAM at the start of the rollout (a second RAM tensor:
+ *                      relaxed reads within it, one-hot writes); zero for
+ *                      envs of other carts
  *   grad_u             device float[n_steps][n_envs][5] (nullable)
  *   grad_rom_per_cart  device float[n_carts][rom_stride] summed over each cart's
  *                      envs (nullable)
@@ -378,7 +384,7 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
  * and allocates the tape's scratch (after one stream synchronisation). */
 vcs_status vcs_backward(vcs_tape* tape, const float* grad_ram, const float* grad_screen,
                         const vcs_loss_weights* w, float* grad_rom, float* grad_ram0,
-                        float* grad_u, float* grad_rom_per_cart, void* stream);
+                        float* grad_cart_ram0, float* grad_u, float* grad_rom_per_cart, void* stream);
 vcs_status vcs_tape_free(vcs_tape* tape);
 
 /* vcs_backward without any device allocation (the paper has no counterpart:
@@ -403,12 +409,16 @@ vcs_status vcs_tape_free(vcs_tape* tape);
  *  - It synchronises `stream` once to read the tape's sizes. */
 vcs_status vcs_backward_static(vcs_tape* tape, const float* grad_ram, const float* grad_screen,
                                const vcs_loss_weights* w, float* grad_rom, float* grad_ram0,
-                               float* grad_u, float* grad_rom_per_cart, void* stream);
+                               float* grad_cart_ram0, float* grad_u, float* grad_rom_per_cart,
+                               void* stream);
 
 /* Copy the machine state out / in as an opaque blob (checkpoint/resume).
  * vcs_state_bytes gives the size; blob is a host pointer; both calls
  * synchronise `stream`. */
 vcs_status vcs_state_bytes(const vcs_batch* b, size_t* bytes);
+/* The Superchip RAM of every env: out is device uint8[n_envs][128] (4-byte
+ * aligned), zero for envs of other carts.  Asynchronous on `stream`. */
+vcs_status vcs_cart_ram(vcs_batch* b, uint8_t* out, void* stream);
 vcs_status vcs_save_state(vcs_batch* b, void* blob_host, void* stream);
 vcs_status vcs_load_state(vcs_batch* b, const void* blob_host, void* stream);
 

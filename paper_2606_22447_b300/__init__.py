@@ -13,7 +13,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import ENV_DONE, ENV_JAMMED, ENV_WATCHDOG, Config, VcsError
-from .synth import MAPPER_2K, MAPPER_4K, MAPPER_F4, MAPPER_F6, MAPPER_F8, MAPPER_SIZE
+from .synth import (MAPPER_2K, MAPPER_4K, MAPPER_F4, MAPPER_F4SC, MAPPER_F6, MAPPER_F6SC, MAPPER_F8, MAPPER_F8SC,
+                    MAPPER_SIZE)
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 
@@ -194,6 +195,15 @@ class Batch:
         self._check(_lib.load().vcs_digest(self.h, _ptr(ram), _ptr(screen), n_steps, _ptr(out), _stream(stream)))
         return out
 
+    def cart_ram(self, out=None, stream=None):
+        """The Superchip RAM of every env (vcs_cart_ram): a torch uint8 CUDA
+        tensor [n_envs][128], zero for envs of other carts."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n_envs, 128), dtype=torch.uint8, device="cuda")
+        self._check(_lib.load().vcs_cart_ram(self.h, _ptr(out), _stream(stream)))
+        return out
+
     def full_divergence(self, T: float, alpha: float, n_instr: int, actions=None, counts=True, ram=True,
                         stream=None):
         """The fully relaxed forward study (vcs_full_divergence): returns
@@ -231,13 +241,13 @@ class Tape:
         self.n_steps = n_steps
 
     def backward(self, grad_ram=None, grad_screen=None, w_ram=None, w_screen=None, grad_rom=None,
-                 grad_ram0=None, grad_u=None, grad_rom_per_cart=None, stream=None):
+                 grad_ram0=None, grad_u=None, grad_rom_per_cart=None, grad_cart_ram0=None, stream=None):
         w = None
         if w_ram is not None or w_screen is not None:
             w = _lib.LossWeights(_ptr(w_ram), _ptr(w_screen))
         st = _lib.load().vcs_backward(self.h, _ptr(grad_ram), _ptr(grad_screen), C.byref(w) if w else None,
-                                      _ptr(grad_rom), _ptr(grad_ram0), _ptr(grad_u), _ptr(grad_rom_per_cart),
-                                      _stream(stream))
+                                      _ptr(grad_rom), _ptr(grad_ram0), _ptr(grad_cart_ram0), _ptr(grad_u),
+                                      _ptr(grad_rom_per_cart), _stream(stream))
         _lib.check(st, self.batch.h)
 
     def free(self):

@@ -68,9 +68,10 @@ SIGNATURES = {
     "vcs_save_state": (C.c_int, [vp, vp, vp]),
     "vcs_load_state": (C.c_int, [vp, vp, vp]),
     "vcs_soft_rollout": (C.c_int, [vp, C.c_float, vp, vp, vp, i32, i32, vp, vp, C.POINTER(vp), vp]),
-    "vcs_backward": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "vcs_backward": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "vcs_tape_free": (C.c_int, [vp]),
-    "vcs_backward_static": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "vcs_backward_static": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "vcs_cart_ram": (C.c_int, [vp, vp, vp]),
     "vcs_autotune": (C.c_int, [vp, i32, i32, vp, vp, vp, C.POINTER(Tune), vp]),
     "vcs_graph_create": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, C.POINTER(vp)]),
     "vcs_graph_launch": (C.c_int, [vp, vp]),

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdint>
 #include <map>
 #include <mutex>
 #include <cstdio>
@@ -57,6 +58,7 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.perm = b->perm;
   p.roms = b->roms;
   p.cart_banks = b->cart_banks;
+  p.ram_words = b->ram_words;
   p.rom_stride = b->rom_stride;
   p.dt = b->dt;
   p.ystart = b->cfg.ystart;
@@ -225,10 +227,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if (!roms || !rom_sizes || !mappers || !env_cart)
     return vcs_fail(nullptr, VCS_ERR_ARG, "null roms / rom_sizes / mappers / env_cart");
   if (n_carts <= 0 || n_envs <= 0) return vcs_fail(nullptr, VCS_ERR_ARG, "n_carts and n_envs must be positive");
-  static const uint32_t want[5] = {2048, 4096, 8192, 16384, 32768};
+  static const uint32_t want[8] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768};
   uint32_t rom_stride = 8192;   // the largest image, at least 8 KB
   for (int c = 0; c < n_carts; c++) {
-    if (mappers[c] > VCS_MAPPER_F4)
+    if (mappers[c] > VCS_MAPPER_F4SC)
       return vcs_fail(nullptr, VCS_ERR_MAPPER, "cart %d: unknown mapper %d", c, mappers[c]);
     if (rom_sizes[c] != want[mappers[c]])
       return vcs_fail(nullptr, VCS_ERR_ROM_SIZE, "cart %d: %u bytes for mapper %d (want %u)", c, rom_sizes[c],
@@ -310,6 +312,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
       memcpy(d, roms[c], rom_sizes[c]);
     }
     banks[c] = mappers[c] >= VCS_MAPPER_F8 ? (uint8_t)(rom_sizes[c] / 4096) : 0;
+    if (mappers[c] >= VCS_MAPPER_F8SC) {
+      banks[c] |= (uint8_t)kCartSC;
+      b->ram_words = 64;   // every block reserves room for the Superchip's RAM
+    }
     is2k[c] = mappers[c] == VCS_MAPPER_2K;
   }
   std::vector<int32_t> cart_begin(n_carts + 1, 0);
@@ -514,6 +520,14 @@ vcs_status vcs_rollout_host(vcs_batch* b, const uint8_t* actions_host, int32_t n
     if ((e = cudaEventRecord(b->ev_copy[k], c))) return vcs_cuda_fail(b, e, "rollout_host");
   }
   if ((e = cudaStreamSynchronize(c)) || (e = cudaStreamSynchronize(s))) return vcs_cuda_fail(b, e, "rollout_host");
+  return VCS_OK;
+}
+
+vcs_status vcs_cart_ram(vcs_batch* b, uint8_t* out, void* stream) {
+  if (!b || !out) return VCS_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(out) & 3) return vcs_fail(b, VCS_ERR_ARG, "out must be 4-byte aligned");
+  const int e = launch_cart_ram(b->soa(), b->n_envs, out, stream);
+  if (e) return vcs_cuda_fail(b, (cudaError_t)e, "cart RAM kernel launch");
   return VCS_OK;
 }
 

@@ -18,7 +18,9 @@ struct vcs_batch {
   uint32_t* state = nullptr;      // kStateWords x n_envs
   uint8_t* roms = nullptr;        // n_carts x rom_stride
   uint32_t rom_stride = 8192;     // bytes per cart image: the largest image, at least 8 KB
-  uint8_t* cart_banks = nullptr;  // 4 KB banks of each bank-switched cart, else 0
+  uint8_t* cart_banks = nullptr;  // bank byte of each cart: 4 KB banks of a bank-switched cart, else 0,
+                                  // | kCartSC for a Superchip cart
+  int32_t ram_words = 32;         // RAM words per env in shared memory: 64 when a cart is Superchip
   uint8_t* cart_2k = nullptr;
   int32_t* env_cart_dev = nullptr;
   int32_t* cart_begin = nullptr;  // [n_carts + 1] first perm slot of each cart

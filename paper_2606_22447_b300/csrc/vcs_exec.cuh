@@ -109,6 +109,10 @@ __device__ __forceinline__ uint32_t rom_relaxed(const Ctx& c, const Regs& r, uin
 __device__ __forceinline__ uint32_t ram_relaxed(const Ctx& c, uint32_t addr) {
   return relaxed_byte(*c.fp, 128, (int32_t)(addr & 0x7F), [&](int32_t k) { return ram_rd(c, (uint32_t)k); });
 }
+// The Superchip's RAM is a 128-byte tensor of its own.
+__device__ __forceinline__ uint32_t cram_relaxed(const Ctx& c, uint32_t addr) {
+  return relaxed_byte(*c.fp, 128, (int32_t)(addr & 0x7F), [&](int32_t k) { return cram_rd(c, (uint32_t)k); });
+}
 // A cast of a read whose hard value is `exact`: counted in probe and FULL
 // machines, applied in FULL.
 template <int FM>
@@ -120,9 +124,10 @@ __device__ __forceinline__ uint32_t cast_read(Regs& r, uint32_t exact, uint32_t 
 
 // One bus read at cycle index idx of the current instruction, for any
 // address.  Every source is read and the result selected, which costs fewer
-// cycles than branching on the address region.  Side effects: a read of an
-// bank-switch hotspot switches the bank, and a read of INTIM records whether the timer
-// had underflowed (r.intim_live, kept by the soft path's tape).
+// cycles than branching on the address region (the Superchip's read port,
+// a block-uniform case, is the exception).  Side effects: a read of a
+// bank-switch hotspot switches the bank, and a read of INTIM records whether
+// the timer had underflowed (r.intim_live, kept by the soft path's tape).
 template <int FM = 0>
 __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& st, uint32_t addr, int idx) {
   const uint32_t a = addr & 0x1FFF;
@@ -140,11 +145,14 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
   const uint32_t vtim = (a & 1) ? (live ? 0u : 0x80u) : vint;
   const bool timer = (a & 0x1284) == 0x0284;
   r.intim_live = (timer && !(a & 1)) ? (live ? 1u : 0u) : r.intim_live;
+  const bool cport = sc_read_port(c, a);
+  const uint32_t vcart = cport ? cram_rd(c, a) : vrom;
   if constexpr (FM >= 1) {
+    if (cport) return cast_read<FM>(r, vcart, cram_relaxed(c, a));
     if (a & 0x1000) return cast_read<FM>(r, vrom, rom_relaxed(c, r, a));
     if ((a & 0x280) == 0x080) return cast_read<FM>(r, vram, ram_relaxed(c, a));
   }
-  return (a & 0x1000) ? vrom : !(a & 0x80) ? vtia : !(a & 0x200) ? vram : !(a & 4) ? vio : vtim;
+  return (a & 0x1000) ? vcart : !(a & 0x80) ? vtia : !(a & 0x200) ? vram : !(a & 4) ? vio : vtim;
 }
 
 // A read inside page zero or one (zero-page modes, the stack): RAM or the
@@ -165,6 +173,7 @@ __device__ __forceinline__ void bus_write(const Ctx& c, Regs& r, Render& rd, Ste
                                           uint32_t v, int idx) {
   const uint32_t a = addr & 0x1FFF;
   r.bank = a - c.hot < c.nb ? a - c.hot : r.bank;   // bank-switch hotspots
+  if (sc_write_port(c, a)) cram_wr(c, a, v);
   if ((a & 0x1080) == 0) {   // TIA
     tia_write(c, r, rd, st, tape, a & 0x3F, v & 0xFF, r.fc + idx + st.stall);
     return;
@@ -595,14 +604,16 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
 // Instruction bytes at the program counter, fetched ahead: opcode | first
 // operand << 8 | second operand << 16, or kSlowFetch when the bytes must be
 // read through the bus at execution time (outside the cartridge window, near
-// its end or the bank-switch hotspots).  Fetching from the cartridge has no side
+// its end or the bank-switch hotspots, or in a Superchip's RAM ports at its
+// start).  Fetching from the cartridge ROM has no side
 // effect and does not depend on time, so it may happen as soon as the
 // program counter and bank are known.
 constexpr uint32_t kSlowFetch = 1u << 24;
 
 __device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
   const uint32_t off = r.PC & 0xFFF;
-  const bool fast = (r.PC & 0x1000) != 0 && off <= 0xFF1;   // no hotspot ($1FF4 on) among the three bytes
+  // no hotspot ($1FF4 on) among the three bytes, no Superchip port before them
+  const bool fast = (r.PC & 0x1000) != 0 && off <= 0xFF1 && off >= (c.sc << 8);
   const uint8_t* q = c.rom + ((r.bank << 12) | (fast ? off : 0u));
   return (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) | (fast ? 0u : kSlowFetch);
 }

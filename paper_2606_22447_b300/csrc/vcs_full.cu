@@ -9,7 +9,8 @@
 // to bytes and whose conditional branches take the rounded blend of
 // Eq. branch (the interpreter's FM template argument).  The first slot after
 // which the two states differ (registers and flags, clocks, timer, TIA
-// registers, bank, jam flag, RAM) is the env's first divergence.  One thread
+// registers, bank, jam flag, RAM and a Superchip's RAM) is the env's first
+// divergence.  One thread
 // per env; the batch state is read, never written.
 #include <cuda_runtime.h>
 
@@ -28,7 +29,8 @@ struct FullDivParams {
   const int4* blocks;
   const int32_t* perm;
   const uint8_t* roms;
-  const uint8_t* cart_banks;
+  const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC)
+  int32_t ram_words;          // RAM words per env in shared memory (32 or 64)
   const uint8_t* cart_2k;
   uint32_t rom_stride;
   const DecodeTables* dt;
@@ -37,12 +39,12 @@ struct FullDivParams {
   int32_t ystart;
   int32_t* n_div;           // [n_envs]
   uint32_t* counts;         // [n_envs][4] or null
-  uint8_t* ram_full;        // [n_envs][128] or null
+  uint8_t* ram_full;        // [n_envs][128] or null (the RIOT RAM)
   int32_t* err;
 };
 
-__host__ __device__ constexpr size_t full_smem_bytes(int E, uint32_t rom_stride) {
-  return smem_bytes(E, rom_stride) + (size_t)32 * 4 * E + sizeof(FullParams);
+__host__ __device__ constexpr size_t full_smem_bytes(int E, uint32_t rom_stride, int ram_words) {
+  return smem_bytes(E, rom_stride, ram_words) + (size_t)ram_words * 4 * E + sizeof(FullParams);
 }
 
 __device__ __forceinline__ bool machines_differ(const Ctx& ch, const Regs& a, const Ctx& cf, const Regs& b) {
@@ -54,7 +56,7 @@ __device__ __forceinline__ bool machines_differ(const Ctx& ch, const Regs& a, co
            a.vsync != b.vsync || a.hml != b.hml;
   const uint32_t* wa = reinterpret_cast<const uint32_t*>(ch.ram);
   const uint32_t* wb = reinterpret_cast<const uint32_t*>(cf.ram);
-  for (uint32_t w = 0; w < 32 && !d; w++) d = wa[w * ch.E] != wb[w * cf.E];
+  for (uint32_t w = 0; w < ch.rw && !d; w++) d = wa[w * ch.E] != wb[w * cf.E];
   return d;
 }
 
@@ -72,12 +74,13 @@ __device__ __forceinline__ void full_slot(const Ctx& c, Regs& r, Render& rd, Ste
 __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x, slot = threadIdx.x;
-  BlockSmem bs = carve_smem(smem, E, p.rom_stride);
-  uint32_t* ram_f = reinterpret_cast<uint32_t*>(smem + smem_bytes(E, p.rom_stride));   // the FULL machine's RAM [32][E]
-  FullParams* fp = reinterpret_cast<FullParams*>(ram_f + 32 * E);
+  BlockSmem bs = carve_smem(smem, E, p.rom_stride, p.ram_words);
+  // the FULL machine's RAM [ram_words][E]
+  uint32_t* ram_f = reinterpret_cast<uint32_t*>(smem + smem_bytes(E, p.rom_stride, p.ram_words));
+  FullParams* fp = reinterpret_cast<FullParams*>(ram_f + p.ram_words * E);
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t nb = p.cart_banks[cart];
+  const uint32_t cb = p.cart_banks[cart], nb = cart_banks_of(cb);
   if (slot == 0) {
     *fp = fp0;
     fp->rom_m = p.cart_2k[cart] ? 2048 : 4096;
@@ -89,13 +92,15 @@ __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
   if (slot >= bi.z) return;
   const int env = p.perm[bi.y + slot];
   const int n = p.n_envs;
-  Ctx ch = make_ctx(bs, E, slot, 0, 1, nb, p.ystart);
+  // the study is not a hot path: one instantiation serves every batch, the
+  // Superchip ports decoded at run time (off for other carts)
+  Ctx ch = make_ctx<true>(bs, E, slot, 0, 1, cb, p.ystart);
   ch.fp = fp;
   Ctx cf = ch;
   cf.ram = reinterpret_cast<uint8_t*>(ram_f + slot);
   Regs rh;
   load_env(p.s, n, env, ch, rh);
-  for (int w = 0; w < 32; w++) ram_f[w * E + slot] = reinterpret_cast<const uint32_t*>(ch.ram)[w * E];
+  for (uint32_t w = 0; w < ch.rw; w++) ram_f[w * E + slot] = reinterpret_cast<const uint32_t*>(ch.ram)[w * E];
   set_inputs(rh, p.actions ? p.actions[env] : 0u);
   rh.fr_reads = rh.fr_exact = rh.fr_br = rh.fr_br_exact = 0;
   Regs rf = rh;
@@ -162,6 +167,7 @@ extern "C" vcs_status vcs_full_divergence(vcs_batch* b, float T, float alpha, co
   p.perm = b->perm;
   p.roms = b->roms;
   p.cart_banks = b->cart_banks;
+  p.ram_words = b->ram_words;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.dt = b->dt;
@@ -172,7 +178,7 @@ extern "C" vcs_status vcs_full_divergence(vcs_batch* b, float T, float alpha, co
   p.counts = counts;
   p.ram_full = ram_full;
   p.err = b->err;
-  const size_t smem = full_smem_bytes(b->E, b->rom_stride);
+  const size_t smem = full_smem_bytes(b->E, b->rom_stride, b->ram_words);
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return vcs_cuda_fail(b, e, "FULL kernel shared memory");

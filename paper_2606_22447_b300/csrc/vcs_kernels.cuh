@@ -21,10 +21,16 @@ struct SoA {
   uint32_t* t3;    // scanline of the last early HMOVE (int32, -1 = none)
   uint32_t* epf;   // frames elapsed in the current episode
   uint32_t* epi;   // episode index
-  uint32_t* ram;   // RAM words [32][n_envs]
+  uint32_t* ram;   // RAM words [64][n_envs]: RIOT RAM, then the Superchip's RAM (zero for other carts)
 };
 constexpr int kSoAFields = 12;
-constexpr int kStateWords = kSoAFields + 32;   // per env
+constexpr int kStateWords = kSoAFields + 64;   // per env
+
+// Per-cart bank byte: the 4 KB banks of a bank-switched cart (2, 4, 8; 0 for
+// 2K and 4K images) | kCartSC for the Superchip variants.
+constexpr uint32_t kCartSC = 0x80;
+__host__ __device__ constexpr uint32_t cart_banks_of(uint32_t cb) { return cb & 0x0F; }
+__host__ __device__ constexpr uint32_t cart_is_sc(uint32_t cb) { return cb >> 7; }
 
 struct StepParams {
   SoA s;
@@ -32,7 +38,9 @@ struct StepParams {
   const int4* blocks;       // per block: {cart, first slot, env count, 0}
   const int32_t* perm;      // slot -> env (envs grouped by cart)
   const uint8_t* roms;      // [n_carts][rom_stride]; 2K images mirrored to 4 KB
-  const uint8_t* cart_banks;  // [n_carts] 4 KB banks of bank-switched carts (2, 4, 8), else 0
+  const uint8_t* cart_banks;  // [n_carts] bank byte: 4 KB banks of bank-switched carts (2, 4, 8), else 0,
+                              // | kCartSC for a Superchip cart
+  int32_t ram_words;        // RAM words per env in shared memory: 32, or 64 when a cart is Superchip
   uint32_t rom_stride;      // bytes per cart image (8, 16 or 32 KB): also the shared-memory ROM region
   const DecodeTables* dt;
   const uint8_t* actions;   // [n_steps][n_envs] or null (NOOP)
@@ -76,12 +84,16 @@ __host__ __device__ inline SoA soa_at(uint32_t* base, int32_t n_envs) {
 }
 
 void build_decode_tables(DecodeTables* t);
-size_t step_smem_bytes(int envs_per_block, uint32_t rom_stride);
+size_t step_smem_bytes(int envs_per_block, uint32_t rom_stride, int ram_words);
+int launch_cart_ram(const SoA& s, int32_t n_envs, uint8_t* out, void* stream);
 int launch_int_peak(int sms, int32_t iters, uint32_t* sink, void* stream);
 int launch_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests, uint64_t* out, void* stream);
 // Launch the step kernel over `n_blocks` blocks of `envs_per_block`
 // (soft = the SOFT-STE forward: float inputs / outputs and checkpoints).
 int launch_step(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_soft_forward(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+// The same for batches with Superchip carts (p.ram_words = 64).
+int launch_step_sc(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+int launch_soft_forward_sc(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 
 }  // namespace vcs

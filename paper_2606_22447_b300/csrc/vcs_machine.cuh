@@ -18,8 +18,9 @@
 // The TIA is rendered lazily: on each write that changes what is drawn,
 // pixels from the render cursor up to the write's colour clock are drawn
 // with the old registers (span catch-up), and only on the frame a step
-// returns.  Memory lives in shared memory: the cart ROM image (4 or 8 KB,
-// 2K carts mirrored), RAM as 32 words per env interleaved across the block
+// returns.  Memory lives in shared memory: the cart ROM image (4 to 32 KB,
+// 2K carts mirrored), RAM as 32 words per env (64 when the batch holds a
+// Superchip cart: its cartridge RAM follows) interleaved across the block
 // (word w of env j at word w * E + j, so a warp touching the same address
 // hits 32 different banks), and a 160-byte line buffer per env laid out
 // the same way.
@@ -255,6 +256,9 @@ struct Ctx {
   uint32_t E;                // envs per block
   uint32_t nb;               // 4 KB banks of a bank-switched cart (F8 2, F6 4, F4 8), else 0
   uint32_t hot;              // its first hotspot: an access to hot + j selects bank j
+  uint32_t sc;               // 1: Superchip cart, whose 128 bytes of cartridge RAM are RAM
+                             // words 32..63 (written at $1000-$107F, read at $1080-$10FF)
+  uint32_t rw;               // RAM words of this env: 32, or 64 with the Superchip's RAM
   int32_t ystart;
   // Threads per env: T lanes run one env's machine in lockstep (identical
   // registers; their identical shared-memory writes coincide) and split the
@@ -281,6 +285,20 @@ __device__ __forceinline__ void ram_wr(const Ctx& c, uint32_t a, uint32_t v) {
   a &= 0x7F;
   c.ram[(a >> 2) * c.e4 + (a & 3)] = (uint8_t)v;
 }
+// The Superchip's RAM byte a & 0x7F (RAM words 32..63).
+__device__ __forceinline__ uint32_t cram_rd(const Ctx& c, uint32_t a) {
+  a &= 0x7F;
+  return c.ram[(32 + (a >> 2)) * c.e4 + (a & 3)];
+}
+__device__ __forceinline__ void cram_wr(const Ctx& c, uint32_t a, uint32_t v) {
+  a &= 0x7F;
+  c.ram[(32 + (a >> 2)) * c.e4 + (a & 3)] = (uint8_t)v;
+}
+// Superchip ports of a 13-bit address: the read port $1080-$10FF and the
+// write port $1000-$107F (a read there returns the ROM byte, a write to the
+// read port does nothing).
+__device__ __forceinline__ bool sc_read_port(const Ctx& c, uint32_t a) { return c.sc && (a & 0x1F80) == 0x1080; }
+__device__ __forceinline__ bool sc_write_port(const Ctx& c, uint32_t a) { return c.sc && (a & 0x1F80) == 0x1000; }
 
 __device__ __forceinline__ uint32_t div76(uint32_t x) { return x / 76u; }
 __device__ __forceinline__ uint32_t div228(uint32_t x) { return x / 228u; }

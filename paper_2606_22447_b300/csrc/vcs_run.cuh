@@ -13,21 +13,22 @@ struct BlockSmem {
   uint8_t* rom;         // cartridge image (rom_bytes)
   DecodeTables* dt;     // 512 B
   uint64_t* mbar;       // TMA completion barrier
-  uint32_t* ram;        // [32][E] words
+  uint32_t* ram;        // [ram_words][E] words: RIOT RAM, then the Superchip's RAM
   uint32_t* line;       // [40][E] words
 };
 
-__host__ __device__ constexpr size_t smem_bytes(int E, uint32_t rom_bytes) {
-  return rom_bytes + 512 + 16 + (size_t)(32 + 40) * 4 * E;
+// ram_words: 32, or 64 in a batch that holds a Superchip cart.
+__host__ __device__ constexpr size_t smem_bytes(int E, uint32_t rom_bytes, int ram_words) {
+  return rom_bytes + 512 + 16 + (size_t)(ram_words + 40) * 4 * E;
 }
 
-__device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E, uint32_t rom_bytes) {
+__device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E, uint32_t rom_bytes, int ram_words) {
   BlockSmem b;
   b.rom = smem;
   b.dt = reinterpret_cast<DecodeTables*>(smem + rom_bytes);
   b.mbar = reinterpret_cast<uint64_t*>(smem + rom_bytes + 512);
   b.ram = reinterpret_cast<uint32_t*>(smem + rom_bytes + 512 + 16);
-  b.line = b.ram + 32 * E;
+  b.line = b.ram + ram_words * E;
   return b;
 }
 
@@ -69,9 +70,12 @@ __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTabl
 }
 
 // Context of one replica: env slot `slot` of the block (E envs), replica
-// `rank` of T.
-__device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int rank, int T, uint32_t nb,
+// `rank` of T, of a cart whose bank byte is cb (banks | kCartSC).  SC: the
+// batch may hold Superchip carts; without it the ports are compiled out.
+template <bool SC>
+__device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int rank, int T, uint32_t cb,
                                         int32_t ystart) {
+  const uint32_t nb = cart_banks_of(cb);
   Ctx c;
   c.rom = b.rom;
   c.ram = reinterpret_cast<uint8_t*>(b.ram + slot);
@@ -81,6 +85,8 @@ __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int
   c.E = (uint32_t)E;
   c.nb = nb;
   c.hot = first_hotspot(nb);
+  c.sc = SC ? cart_is_sc(cb) : 0u;
+  c.rw = c.sc ? 64u : 32u;
   c.ystart = ystart;
   c.rank = (uint32_t)rank;
   c.T = (uint32_t)T;
@@ -113,7 +119,7 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
   r.hmp0 = v & 0xFF; r.pos = (v >> 8) & 0xFF; r.vblank = (v >> 16) & 0xFF; r.vsync = v >> 24;
   r.hml = (int32_t)s.t3[e];
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
-  for (int i = 0; i < 32; i++) w[i * c.E] = s.ram[(size_t)i * n + e];
+  for (uint32_t i = 0; i < c.rw; i++) w[i * c.E] = s.ram[(size_t)i * n + e];
   for (uint32_t q = c.rank; q < 10; q += c.T)
     for (uint32_t k = 0; k < 4; k++) c.line[(4 * q + k) * c.E] = 0;
   __syncwarp(c.gmask);
@@ -131,12 +137,12 @@ __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx&
   s.t2[e] = r.hmp0 | (r.pos << 8) | (r.vblank << 16) | (r.vsync << 24);
   s.t3[e] = (uint32_t)r.hml;
   const uint32_t* w = reinterpret_cast<const uint32_t*>(c.ram);
-  for (int i = 0; i < 32; i++) s.ram[(size_t)i * n + e] = w[i * c.E];
+  for (uint32_t i = 0; i < c.rw; i++) s.ram[(size_t)i * n + e] = w[i * c.E];
 }
 
-// Power-on state: A = X = Y = 0, SP = $FD, P = $34, RAM and TIA zero, timer
-// as if 0 had been written to T1024T at cycle 0, banked carts in their last
-// bank, PC from the reset vector.
+// Power-on state: A = X = Y = 0, SP = $FD, P = $34, RAM (and the
+// Superchip's RAM) and TIA zero, timer as if 0 had been written to T1024T at
+// cycle 0, banked carts in their last bank, PC from the reset vector.
 __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.A = r.X = r.Y = 0;
   r.SP = 0xFD;
@@ -151,7 +157,7 @@ __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.pos = 0; r.vblank = 0; r.vsync = 0;
   r.hml = -1;
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
-  for (int i = 0; i < 32; i++) w[i * c.E] = 0;
+  for (uint32_t i = 0; i < c.rw; i++) w[i * c.E] = 0;
   r.PC = c.rom[(r.bank << 12) | 0xFFC] | ((uint32_t)c.rom[(r.bank << 12) | 0xFFD] << 8);
 }
 

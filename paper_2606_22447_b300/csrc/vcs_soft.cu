@@ -10,8 +10,8 @@
 //      colour-register version (the stored priority switch);
 //   2. k_soft_sweep, segment by segment from the last, sweeps the tape
 //      backwards (one env per warp), carrying adjoints of A, X, Y, the timer
-//      value, the three colour registers and the 128 RAM cells (in shared
-//      memory), with the surrogate rules:
+//      value, the three colour registers and the 128 RAM cells (256 with a
+//      Superchip's cartridge RAM; in shared memory), with the surrogate rules:
 //        reads   relaxed read of Eq. s-read w.r.t. memory contents: RAM reads
 //                spread the adjoint over |i - a| <= W with weights
 //                exp(-|i - a| / tau) normalised in the clipped window; ROM
@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <new>
 #include <vector>
 
@@ -43,9 +44,11 @@
 namespace vcs {
 
 // carried adjoints: aA aX aY aV aC0 aC1 aC2, aRAM[128] and its compensation,
-// then those of player 0's position and of HMP0 (position sampler)
-constexpr int kCarry = 7 + 256 + 2;
+// those of player 0's position and of HMP0 (position sampler), then the
+// Superchip RAM's adjoints [128] and their compensation
 constexpr int kCarryPos = 7 + 256;
+constexpr int kCarryCram = kCarryPos + 2;
+constexpr int kCarry = kCarryCram + 256;
 constexpr int kMaxW = 120;        // window half-width limit (tau <= 10)
 
 // Compensated (Neumaier) sum: s + c carries the running total.
@@ -127,7 +130,8 @@ struct BwdParams {
   const int4* blocks;
   const int32_t* perm;
   const uint8_t* roms;        // rounded ROM images of the rollout [n_carts][rom_stride]
-  const uint8_t* cart_banks;
+  const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC)
+  int32_t ram_words;          // RAM words per env in the recompute's shared memory (32 or 64)
   uint32_t rom_stride;
   const uint8_t* cart_2k;
   const int32_t* env_cart;    // [n_envs]
@@ -148,6 +152,7 @@ struct BwdParams {
   float* imp;                 // ROM impulses [n_envs][rom_stride] x (value, compensation) pairs
   float* grad_u;              // [n_steps][n_envs][5] or null
   float* grad_ram0;           // [n_envs][128] or null (segment 0)
+  float* grad_cart_ram0;      // [n_envs][128] or null (segment 0): the Superchip's RAM
   float tau;
   int32_t W;
   uint32_t sched_policy, sched_window;
@@ -171,26 +176,42 @@ struct RomQueue {
   uint32_t n;
 };
 
+// Cart kind bits of the sweep: the 2K image (ROM index within 2 KB) and the
+// Superchip's RAM ports.
+enum : uint32_t { kKind2K = 1, kKindSC = 2 };
+
+// Relaxed read of cell i of a 128-cell RAM tensor whose adjoints start at
+// cell `base` (0: RIOT RAM, 128: the Superchip's RAM).
+__device__ __forceinline__ void spread_ram(float* aram, float* aramc, uint32_t E, const float* ek, const float* izr,
+                                           int W, int base, int i, float g) {
+  const int lo = i - W < 0 ? 0 : i - W, hi = i + W > 127 ? 127 : i + W;
+  const float gz = g * izr[i];
+  for (int j = lo; j <= hi; j++)
+    comp_add(aram[(base + j) * E], aramc[(base + j) * E], __fmul_rn(gz, ek[j > i ? j - i : i - j]));
+}
+
 // Adjoint of a value read from `ref` (13-bit bus address) flows back to the
 // memory it came from.  RAM cells, ROM impulses and joystick adjoints are
 // compensated sums (value + compensation), since long rollouts add many
 // terms of both signs into them.
+// SC: the sweep's batch may hold Superchip carts (their ports are compiled
+// out otherwise).
+template <bool SC>
 __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                              const float* izr, int W, RomQueue& rq,
-                                             uint32_t is2k, uint32_t ref, uint32_t fl, float g) {
+                                             uint32_t kind, uint32_t ref, uint32_t fl, float g) {
   const uint32_t ad = ref & 0x1FFF;
   if (g == 0.f) return;
-  if (ad & 0x1000) {
-    rq.idx[rq.n] = is2k ? (ad & 0x7FF) : ((((fl >> 2) & 7u) << 12) | (ad & 0xFFF));   // the read's bank
+  if (SC && (kind & kKindSC) && (ad & 0x1F80) == 0x1080) {   // the Superchip's read port
+    spread_ram(aram, aramc, E, ek, izr, W, 128, (int)(ad & 0x7F), g);
+  } else if (ad & 0x1000) {
+    rq.idx[rq.n] = (kind & kKind2K) ? (ad & 0x7FF) : ((((fl >> 2) & 7u) << 12) | (ad & 0xFFF));   // the read's bank
     rq.g[rq.n] = g;
     rq.n++;
   } else if (!(ad & 0x80)) {
     if ((ad & 0xF) == 0xC) comp_add(a.u[4], a.uc[4], -128.f * g);
   } else if (!(ad & 0x200)) {
-    const int i = (int)(ad & 0x7F);
-    const int lo = i - W < 0 ? 0 : i - W, hi = i + W > 127 ? 127 : i + W;
-    const float gz = g * izr[i];
-    for (int j = lo; j <= hi; j++) comp_add(aram[j * E], aramc[j * E], __fmul_rn(gz, ek[j > i ? j - i : i - j]));
+    spread_ram(aram, aramc, E, ek, izr, W, 0, (int)(ad & 0x7F), g);
   } else if (!(ad & 4)) {
     if ((ad & 3) == 0) {
       comp_add(a.u[0], a.uc[0], -128.f * g);
@@ -205,11 +226,18 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
 
 // Adjoint of the value written to `ref`: taken from the cell (which is then
 // cleared, the write being one-hot).
-template <bool SAMPLER>
+template <bool SAMPLER, bool SC>
 __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
-                                            uint32_t& j, uint32_t ref) {
+                                            uint32_t& j, uint32_t kind, uint32_t ref) {
   const uint32_t ad = ref & 0x1FFF;
-  if (ad & 0x1000) return 0.f;
+  if (ad & 0x1000) {
+    if (!SC || !(kind & kKindSC) || (ad & 0x1F80) != 0x1000) return 0.f;
+    const uint32_t o = (128 + (ad & 0x7F)) * E;   // the Superchip's write port
+    const float g = aram[o] + aramc[o];
+    aram[o] = 0.f;
+    aramc[o] = 0.f;
+    return g;
+  }
   if (!(ad & 0x80)) {
     const uint32_t reg = ad & 0x3F;
     float g;
@@ -252,61 +280,61 @@ __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, u
 
 __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
 
-template <bool SAMPLER>
+template <bool SAMPLER, bool SC>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                             const float* izr, int W, RomQueue& rq,
-                                            uint32_t is2k, const float* cw, uint32_t& j, uint32_t rec) {
+                                            uint32_t kind, const float* cw, uint32_t& j, uint32_t rec) {
   const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
   switch (op) {
     case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
       float g = a.X;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
       float g = a.Y;
       a.Y = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x09: case 0x05: case 0x15: case 0x0D: case 0x1D: case 0x19: case 0x01: case 0x11:
     case 0x29: case 0x25: case 0x35: case 0x2D: case 0x3D: case 0x39: case 0x21: case 0x31:
     case 0x49: case 0x45: case 0x55: case 0x4D: case 0x5D: case 0x59: case 0x41: case 0x51:
     case 0x69: case 0x65: case 0x75: case 0x6D: case 0x7D: case 0x79: case 0x61: case 0x71:
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, a.A);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, a.A);
       break;
     case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
     case 0xEB:                                                      // USBC: SBC's alias
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, -a.A);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, -a.A);
       break;
     case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   // LAX: A = X = M
       float g = a.A + a.X;
       a.A = 0.f;
       a.X = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
-      const float g = take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
+      const float g = take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
       a.A += g;
       a.X += g;
       break;
     }
     case 0x85: case 0x95: case 0x8D: case 0x9D: case 0x99: case 0x81: case 0x91:
-      a.A += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
+      a.A += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x86: case 0x96: case 0x8E:
-      a.X += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
+      a.X += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x84: case 0x94: case 0x8C:
-      a.Y += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
+      a.Y += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x06: case 0x16: case 0x0E: case 0x1E:
     case 0x26: case 0x36: case 0x2E: case 0x3E:
@@ -314,8 +342,8 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x66: case 0x76: case 0x6E: case 0x7E:
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
-      float g = take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref);
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
+      float g = take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xAA: a.A += a.X; a.X = 0.f; break;   // TAX
@@ -323,22 +351,22 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xA8: a.A += a.Y; a.Y = 0.f; break;   // TAY
     case 0x98: a.Y += a.A; a.A = 0.f; break;   // TYA
     case 0xBA: a.X = 0.f; break;               // TSX: SP carries nothing
-    case 0x48: a.A += take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref); break;   // PHA
-    case 0x08: take_write<SAMPLER>(a, aram, aramc, E, cw, j, ref); break;           // PHP
+    case 0x48: a.A += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref); break;   // PHA
+    case 0x08: take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref); break;           // PHP
     case 0x68: {                                                    // PLA
       float g = a.A;
       a.A = 0.f;
-      scatter_read(a, aram, aramc, E, ek, izr, W, rq, is2k, ref, fl, g);
+      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x20:                                                      // JSR: two pushes
-      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
-      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
+      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
+      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
       break;
     case 0x00:                                                      // BRK: three pushes
-      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 2));
-      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 1));
-      take_write<SAMPLER>(a, aram, aramc, E, cw, j, stack_addr(ref, 0));
+      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 2));
+      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
+      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
       break;
     default:
       break;
@@ -372,10 +400,12 @@ constexpr int kMeta = 8;
 
 // Recompute shared memory: the step kernel's layout, then the staged
 // gradient rows (16-byte aligned).
-__host__ __device__ constexpr size_t rc_row_offset(int E, uint32_t rom_stride) {
-  return (smem_bytes(E, rom_stride) + 15) & ~(size_t)15;
+__host__ __device__ constexpr size_t rc_row_offset(int E, uint32_t rom_stride, int ram_words) {
+  return (smem_bytes(E, rom_stride, ram_words) + 15) & ~(size_t)15;
 }
-size_t rc_smem_bytes(int E, uint32_t rom_stride) { return rc_row_offset(E, rom_stride) + (size_t)40 * 16 * E; }
+size_t rc_smem_bytes(int E, uint32_t rom_stride, int ram_words) {
+  return rc_row_offset(E, rom_stride, ram_words) + (size_t)40 * 16 * E;
+}
 // The sweep runs one env per warp: envs' tapes differ, so lanes of one warp
 // walking different tapes would serialise over their different records,
 // while one env per warp lets each SM sub-partition interleave several envs
@@ -384,19 +414,23 @@ constexpr int kSweepEnvs = 4;   // envs (warps) per block
 constexpr int kSweepBlock = 128;   // records a warp stages at a time (32 lanes x 4)
 constexpr int kSweepWarpWords = 3 * kSweepBlock;   // staged records, then the ROM queue's indices and adjoints
 // Sweep shared memory: the RAM adjoints and their compensation
-// [2][128][kSweepEnvs], the read tables, then each warp's staging words.
-__host__ __device__ constexpr size_t sw_tables_end() { return ((size_t)2 * 128 * 4 * kSweepEnvs + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15; }
+// [2][256][kSweepEnvs] (RIOT RAM, then the Superchip's RAM), the read
+// tables, then each warp's staging words.
+constexpr int kSweepCells = 256;
+__host__ __device__ constexpr size_t sw_tables_end() {
+  return ((size_t)2 * kSweepCells * 4 * kSweepEnvs + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
+}
 __host__ __device__ constexpr size_t sw_smem_bytes() { return sw_tables_end() + (size_t)kSweepEnvs * kSweepWarpWords * 4; }
 
-template <int T, bool SAMPLER, bool INSTR = false>
+template <int T, bool SAMPLER, bool INSTR, bool SC>
 __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
-  BlockSmem bs = carve_smem(smem, E, p.rom_stride);
-  float4* grow = reinterpret_cast<float4*>(smem + rc_row_offset(E, p.rom_stride));  // [40][E] staged gradient rows
+  BlockSmem bs = carve_smem(smem, E, p.rom_stride, p.ram_words);
+  float4* grow = reinterpret_cast<float4*>(smem + rc_row_offset(E, p.rom_stride, p.ram_words));  // [40][E] staged gradient rows
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t nb = p.cart_banks[cart];
+  const uint32_t cb = p.cart_banks[cart], nb = cart_banks_of(cb);
   const int g = blockIdx.y, seg = p.seg0 + g;
   if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {
     if (tid == 0) atomicExch(p.err, 1);
@@ -406,7 +440,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
-  Ctx c = make_ctx(bs, E, slot, rank, T, nb, p.ystart);
+  Ctx c = make_ctx<SC>(bs, E, slot, rank, T, cb, p.ystart);
   Regs r;
   if (active) {
     load_env(soa_at(const_cast<uint32_t*>(p.ckpt + (size_t)seg * kStateWords * n), n), n, env, c, r);
@@ -464,16 +498,16 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
 
 // The reverse sweep of segment p.seg (slot p.seg - p.seg0 of the group), one
 // env per warp (lane 0): adjoints of A, X, Y, the timer value, the colour
-// registers, player 0's position and HMP0 in registers, the 128 RAM cells
-// (compensated) in shared memory.
-template <bool SAMPLER>
+// registers, player 0's position and HMP0 in registers, the 128 RAM cells and
+// the Superchip's 128 (compensated) in shared memory.
+template <bool SAMPLER, bool SC>
 __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr int E = kSweepEnvs;
   const int slot = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* aram_s = reinterpret_cast<float*>(smem);   // [128][E]
-  float* aramc_s = aram_s + 128 * E;                 // [128][E] compensation
-  float* ek = aramc_s + 128 * E;                     // [kMaxW + 1]
+  float* aram_s = reinterpret_cast<float*>(smem);   // [256][E]
+  float* aramc_s = aram_s + kSweepCells * E;         // [256][E] compensation
+  float* ek = aramc_s + kSweepCells * E;             // [kMaxW + 1]
   float* izr = ek + (kMaxW + 1);                     // [128]
   uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem + sw_tables_end()) + slot * kSweepWarpWords;
   uint32_t* recs = wbuf;                             // [kSweepBlock] records of the current block
@@ -484,7 +518,9 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   read_tables(ek, izr, p.tau, p.W);
   const int env = blockIdx.x * E + slot;
   if (env >= p.n_envs) return;   // whole warps leave together
-  const uint32_t is2k = p.cart_2k[p.env_cart[env]];
+  const uint32_t cart = (uint32_t)p.env_cart[env];
+  const uint32_t kind = (p.cart_2k[cart] ? kKind2K : 0u) | (SC && cart_is_sc(p.cart_banks[cart]) ? kKindSC : 0u);
+  constexpr int cells = SC ? kSweepCells : 128;   // adjoint cells the sweep keeps
   const int n = p.n_envs, g = p.seg - p.seg0;
   const float* m = p.meta + ((size_t)g * n + env) * kMeta;
   if (m[1] != 0.f) return;   // overflow: the error word is set
@@ -495,8 +531,8 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   if (lead) {
     if (p.first) {
       a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.P = a.H = 0.f;
-      for (int i = 0; i < 128; i++) aram[i * E] = 0.f;
-      for (int i = 0; i < 128; i++) aramc[i * E] = 0.f;
+      for (int i = 0; i < cells; i++) aram[i * E] = 0.f;
+      for (int i = 0; i < cells; i++) aramc[i * E] = 0.f;
     } else {
       const float* cr = p.carry;
       a.A = cr[0 * n + env]; a.X = cr[1 * n + env]; a.Y = cr[2 * n + env]; a.V = cr[3 * n + env];
@@ -505,6 +541,12 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
       for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
       for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
+      if constexpr (SC) {
+        for (int i = 0; i < 128; i++) {
+          aram[(128 + i) * E] = (kind & kKindSC) ? cr[(size_t)(kCarryCram + i) * n + env] : 0.f;
+          aramc[(128 + i) * E] = (kind & kKindSC) ? cr[(size_t)(kCarryCram + 128 + i) * n + env] : 0.f;
+        }
+      }
     }
   }
   float2* imp = reinterpret_cast<float2*>(p.imp) + (size_t)env * p.rom_stride;
@@ -549,7 +591,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       }
       if (lead)
         for (uint32_t q = k; q > lo; q--)
-          reverse_one<SAMPLER>(a, aram, aramc, E, ek, izr, p.W, rq, is2k, cw, j, recs[q - 1 - 4 * c0]);
+          reverse_one<SAMPLER, SC>(a, aram, aramc, E, ek, izr, p.W, rq, kind, cw, j, recs[q - 1 - 4 * c0]);
       // the warp adds the block's ROM impulses: lane l takes the indices
       // congruent to l mod 32, each in queue order
       const uint32_t qn = __shfl_sync(0xFFFFFFFFu, rq.n, 0);
@@ -581,6 +623,9 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   if (p.seg == 0) {
     if (p.grad_ram0)
       for (int i = 0; i < 128; i++) p.grad_ram0[(size_t)env * 128 + i] = aram[i * E] + aramc[i * E];
+    if (p.grad_cart_ram0)
+      for (int i = 0; i < 128; i++)
+        p.grad_cart_ram0[(size_t)env * 128 + i] = SC ? aram[(128 + i) * E] + aramc[(128 + i) * E] : 0.f;
   } else {
     float* cr = p.carry;
     cr[0 * n + env] = a.A; cr[1 * n + env] = a.X; cr[2 * n + env] = a.Y; cr[3 * n + env] = a.V;
@@ -588,6 +633,10 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
     cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
+    if (SC && (kind & kKindSC)) {
+      for (int i = 0; i < 128; i++) cr[(size_t)(kCarryCram + i) * n + env] = aram[(128 + i) * E];
+      for (int i = 0; i < 128; i++) cr[(size_t)(kCarryCram + 128 + i) * n + env] = aramc[(128 + i) * E];
+    }
   }
 }
 
@@ -606,32 +655,40 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
   auto go = [&](auto kern, int threads) {
     if ((e = allow_smem(kern, smem)) == cudaSuccess) kern<<<grid, threads, smem, s>>>(p);
   };
-  // instruction-granular steps draw nothing (no pixel sums, no position
-  // sampler), so one lane per env serves them
-  if (p.step_instr > 0) {
-    go(k_soft_recompute<1, false, true>, E);
-  } else if (p.sampler) {
-    switch (T) {
-      case 1: go(k_soft_recompute<1, true>, E); break;
-      case 2: go(k_soft_recompute<2, true>, 2 * E); break;
-      case 4: go(k_soft_recompute<4, true>, 4 * E); break;
-      default: go(k_soft_recompute<8, true>, 8 * E); break;
+  auto pick = [&](auto sc) {
+    constexpr bool SC = decltype(sc)::value;
+    // instruction-granular steps draw nothing (no pixel sums, no position
+    // sampler), so one lane per env serves them
+    if (p.step_instr > 0) {
+      go(k_soft_recompute<1, false, true, SC>, E);
+    } else if (p.sampler) {
+      switch (T) {
+        case 1: go(k_soft_recompute<1, true, false, SC>, E); break;
+        case 2: go(k_soft_recompute<2, true, false, SC>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, true, false, SC>, 4 * E); break;
+        default: go(k_soft_recompute<8, true, false, SC>, 8 * E); break;
+      }
+    } else {
+      switch (T) {
+        case 1: go(k_soft_recompute<1, false, false, SC>, E); break;
+        case 2: go(k_soft_recompute<2, false, false, SC>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, false, false, SC>, 4 * E); break;
+        default: go(k_soft_recompute<8, false, false, SC>, 8 * E); break;
+      }
     }
-  } else {
-    switch (T) {
-      case 1: go(k_soft_recompute<1, false>, E); break;
-      case 2: go(k_soft_recompute<2, false>, 2 * E); break;
-      case 4: go(k_soft_recompute<4, false>, 4 * E); break;
-      default: go(k_soft_recompute<8, false>, 8 * E); break;
-    }
-  }
+  };
+  if (p.ram_words > 32) pick(std::true_type{});
+  else pick(std::false_type{});
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 static cudaError_t launch_sweep(const BwdParams& p, cudaStream_t s) {
   const int n_blocks = (p.n_envs + kSweepEnvs - 1) / kSweepEnvs;
-  if (p.sampler && p.step_instr <= 0) k_soft_sweep<true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
-  else k_soft_sweep<false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  const bool sampler = p.sampler && p.step_instr <= 0, sc = p.ram_words > 32;
+  if (sampler && sc) k_soft_sweep<true, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  else if (sampler) k_soft_sweep<true, false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  else if (sc) k_soft_sweep<false, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  else k_soft_sweep<false, false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
   return cudaGetLastError();
 }
 
@@ -663,7 +720,8 @@ __global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_ca
   const int cart = env_cart[env];
   const int M = cart_2k[cart] ? 2048 : 4096;
   float* o = out + (size_t)env * rom_stride;
-  if (i >= (cart_banks[cart] ? (int)cart_banks[cart] * 4096 : M)) {
+  const int nb = (int)cart_banks_of(cart_banks[cart]);
+  if (i >= (nb ? nb * 4096 : M)) {
     o[i] = 0.f;
     return;
   }
@@ -777,7 +835,7 @@ static vcs_status run_backward_groups(vcs_batch* b, const vcs_tape* t, BwdParams
   }
   p.blocks = blocks;
   p.ckpt = t->ckpt;
-  const size_t smem = rc_smem_bytes(E, b->rom_stride);
+  const size_t smem = rc_smem_bytes(E, b->rom_stride, b->ram_words);
   cudaError_t e;
   for (int hi = t->n_seg - 1; hi >= 0; hi -= G) {
     const int lo = hi - G + 1 > 0 ? hi - G + 1 : 0;
@@ -880,7 +938,8 @@ vcs_status vcs_tape_free(vcs_tape* t) {
 }
 
 vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_screen, const vcs_loss_weights* w,
-                        float* grad_rom, float* grad_ram0, float* grad_u, float* grad_rom_per_cart, void* stream) {
+                        float* grad_rom, float* grad_ram0, float* grad_cart_ram0, float* grad_u,
+                        float* grad_rom_per_cart, void* stream) {
   if (!t || !t->b) return VCS_ERR_ARG;
   vcs_batch* b = t->b;
   if ((grad_ram || grad_screen) && w && (w->ram || w->screen))
@@ -950,6 +1009,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.perm = b->perm;
   p.roms = t->rom_bytes;
   p.cart_banks = b->cart_banks;
+  p.ram_words = b->ram_words;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.env_cart = b->env_cart_dev;
@@ -969,6 +1029,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.imp = t->imp;
   p.grad_u = grad_u;
   p.grad_ram0 = grad_ram0;
+  p.grad_cart_ram0 = grad_cart_ram0;
   p.tau = t->tau;
   p.W = t->W;
   p.tpe = b->tpe;
@@ -1038,7 +1099,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, const float* grad_screen,
                                           const vcs_loss_weights* w, float* grad_rom, float* grad_ram0,
-                                          float* grad_u, float* grad_rom_per_cart, void* stream) {
+                                          float* grad_cart_ram0, float* grad_u, float* grad_rom_per_cart,
+                                          void* stream) {
   if (!t || !t->b) return VCS_ERR_ARG;
   vcs_batch* b = t->b;
   if ((grad_ram || grad_screen) && w && (w->ram || w->screen))
@@ -1102,6 +1164,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.perm = b->perm;
   p.roms = t->rom_bytes;
   p.cart_banks = b->cart_banks;
+  p.ram_words = b->ram_words;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.env_cart = b->env_cart_dev;
@@ -1121,6 +1184,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.imp = imp;
   p.grad_u = grad_u;
   p.grad_ram0 = grad_ram0;
+  p.grad_cart_ram0 = grad_cart_ram0;
   p.tau = t->tau;
   p.W = t->W;
   p.tpe = b->tpe;

@@ -62,7 +62,7 @@ def test_argument_errors_before_device_work(lib):
     rom4 = synth.generate_cart(1, 0, synth.MAPPER_4K)
     st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0, 1])
     assert st == _lib.VCS_ERR_ARG and "out of range" in msg and not h.value
-    st, h, msg = _create(lib, [rom4], [4096], [7], [0])
+    st, h, msg = _create(lib, [rom4], [4096], [200], [0])
     assert st == _lib.VCS_ERR_MAPPER and not h.value
     st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_2K], [0])
     assert st == _lib.VCS_ERR_ROM_SIZE and "want 2048" in msg

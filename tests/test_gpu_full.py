@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 MAPPERS = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
 BANKED = [synth.MAPPER_F6, synth.MAPPER_F4, synth.MAPPER_F8]
+SUPERCHIP = [synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC]
 
 
 def _oracle_study(rom, mapper, warm, action, T, alpha, n):
@@ -31,7 +32,8 @@ def _oracle_study(rom, mapper, warm, action, T, alpha, n):
     for k in range(1, n + 1):
         h.trace(action, 1)
         f.trace(action, 1)
-        if not n_div and not (np.array_equal(h.state(), f.state()) and np.array_equal(h.ram(), f.ram())):
+        if not n_div and not (np.array_equal(h.state(), f.state()) and np.array_equal(h.ram(), f.ram()) and
+                              np.array_equal(h.cart_ram(), f.cart_ram())):
             n_div = k
     p.trace(action, n)
     c = p.counters()
@@ -42,7 +44,8 @@ def _oracle_study(rom, mapper, warm, action, T, alpha, n):
                                                   (0.2, 6.0, 2, MAPPERS), (0.14, 2.0, 0, MAPPERS),
                                                   (0.14, 3.0, 2, MAPPERS), (0.01, 20.0, 0, MAPPERS),
                                                   (1.0, 6.0, 0, MAPPERS), (0.15, 6.0, 2, BANKED),
-                                                  (0.14, 2.0, 0, BANKED)])
+                                                  (0.14, 2.0, 0, BANKED), (0.15, 6.0, 2, SUPERCHIP),
+                                                  (0.14, 6.0, 0, SUPERCHIP)])
 def test_full_divergence_matches_oracle(T, alpha, warm, mappers):
     torch = torch_cuda()
     MAPPERS = mappers

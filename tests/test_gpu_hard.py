@@ -551,3 +551,62 @@ def test_step_host_and_state_roundtrip():
     ram2, _, _ = gpu_rollout(b, acts[:1], 2, screens=False)
     r3, _, _ = oracle_rollout(rom, synth.MAPPER_F8, acts[:1, 3], 2, screens=False)
     assert np.array_equal(ram2[0, 3], r3[0])
+
+
+SC_MAPPERS = [synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC]
+
+
+@pytest.mark.parametrize("epb,tpe", [(16, 1), (128, 1), (32, 4)])
+def test_superchip_carts_match_oracle(epb, tpe):
+    """F8SC, F6SC and F4SC carts next to plain ones in one batch: RAM,
+    screens, status and the cartridge RAM (vcs_cart_ram) bit-exact, envs
+    unsorted over several blocks and a ragged tail; a state blob round trip
+    carries the cartridge RAM."""
+    torch = torch_cuda()
+    mappers = SC_MAPPERS + [synth.MAPPER_4K, synth.MAPPER_F8]
+    roms = synth.config_carts(307, mappers)
+    n_envs = 45
+    env_cart = np.random.default_rng(7).permutation(np.arange(n_envs) % len(mappers)).astype(np.int32)
+    acts = synth.actions(307, n_envs, 6)
+    b = make_batch(roms, mappers, env_cart, envs_per_block=epb, threads_per_env=tpe)
+    blob = b.save_state()
+    ram, scr, st = gpu_rollout(b, acts, 2)
+    cram = b.cart_ram().cpu().numpy()
+    for e in range(n_envs):
+        c = int(env_cart[e])
+        o = oracle.Oracle(roms[c], mappers[c])
+        for t in range(acts.shape[0]):
+            r, s, stt = o.step(int(acts[t, e]), 2)
+            assert_env_equal(e, ram[t, e], r, f"RAM step {t}")
+            assert_env_equal(e, scr[t, e], s, f"screen step {t}")
+            assert st[t, e] == stt
+        assert_env_equal(e, cram[e], o.cart_ram(), "cartridge RAM")
+        if mappers[c] in SC_MAPPERS:
+            assert cram[e].any()
+    b.load_state(blob)
+    assert not b.cart_ram().cpu().numpy().any()
+    ram2, _, _ = gpu_rollout(b, acts, 2, screens=False)
+    assert np.array_equal(ram2, ram) and np.array_equal(b.cart_ram().cpu().numpy(), cram)
+
+
+def test_superchip_ports_on_the_gpu():
+    """The oracle's port pin on the GPU: writes through $1000-$107F, reads
+    through $1080-$10FF plain and indexed, the write port reading ROM, the
+    read port ignoring writes, a routine run from the cartridge RAM (fetched
+    through the bus), in every Superchip format and as plain banked carts."""
+    from tests.test_oracle_machine import _superchip_image
+    for mapper in SC_MAPPERS:
+        rom = _superchip_image(mapper)
+        base = synth.MAPPER_SC_BASE[mapper]
+        b = make_batch([rom, rom], [mapper, base], [0, 1, 0, 1])
+        acts = synth.actions(308, 4, 2)
+        ram, _, st = gpu_rollout(b, acts, 1, screens=False)
+        cram = b.cart_ram().cpu().numpy()
+        for e, m in enumerate((mapper, base, mapper, base)):
+            r, _, s = oracle_rollout(rom, m, acts[:, e], 1, screens=False)
+            assert_env_equal(e, ram[:, e], r, "RAM")
+            assert_env_equal(e, st[:, e], s, "status")
+        o = oracle.Oracle(rom, mapper)
+        o.rollout(acts[:, 0], 1, screens=False)
+        assert np.array_equal(cram[0], o.cart_ram()) and cram[0, 0x20] == 0xA9
+        assert not cram[1].any()

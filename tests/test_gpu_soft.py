@@ -354,3 +354,42 @@ def test_wide_recompute_of_a_large_segment_group():
         for g_rom, g_u in res:
             assert_grad_close(g_rom[e, :len(roms[c])], o_rom, f"grad_rom env {e}")
             assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+
+
+@pytest.mark.parametrize("tpe,seg", [(1, 64), (4, 2)])
+def test_gradients_on_superchip_carts(tpe, seg):
+    """F8SC / F6SC / F4SC carts: the cartridge RAM is a second RAM tensor
+    (relaxed reads within it, one-hot writes), so its adjoints ride the
+    sweep and the checkpoint carry; grad_cart_ram0, ROM, initial RAM and
+    input gradients against the FP64 oracle, over one and several segments."""
+    mappers = [synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_4K]
+    n_envs, n_steps, tau = 8, 4, 0.3
+    torch, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 75, envs_per_block=8,
+                                                   threads_per_env=tpe, segment_frames=seg)
+    gr = synth.normal_f32(75, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(75, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, b.rom_stride), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_cram0 = torch.full((n_envs, 128), 7.0, device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u, grad_cart_ram0=g_cram0)
+    b.sync()
+    g_rom, g_ram0, g_cram0, g_u = (x.cpu().numpy() for x in (g_rom, g_ram0, g_cram0, g_u))
+    for e in range(n_envs):
+        c = env_cart[e]
+        o = oracle.Oracle(roms[c], mappers[c])
+        o.rollout(wa[:, e], 1, screens=False)
+        g, _, _ = o.soft_rollout(u[:, e].astype(np.float64), 1, tau, 6.0, gr[:, e].astype(np.float64),
+                                 gs[:, e].astype(np.float64))
+        o_rom, o_ram0, o_u, o_cram0 = g.reverse(cart_ram=True)
+        size = len(roms[c])
+        assert_grad_close(g_rom[e, :size], o_rom, f"grad_rom env {e}")
+        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
+        assert_grad_close(g_cram0[e], o_cram0, f"grad_cart_ram0 env {e}")
+        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+        if mappers[c] == synth.MAPPER_4K:
+            assert not g_cram0[e].any()
+        else:
+            assert np.abs(o_cram0).max() > 0

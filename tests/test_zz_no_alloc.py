@@ -29,7 +29,8 @@ def _close(got, want, what):
 def _grads(entry, tape, gr, gs, n_envs, n_steps, n_carts):
     torch = torch_cuda()
     out = [torch.full((n_envs, 8192), 7.0, device="cuda"), torch.full((n_envs, 128), 7.0, device="cuda"),
-           torch.full((n_steps, n_envs, 5), 7.0, device="cuda"), torch.full((n_carts, 8192), 7.0, device="cuda")]
+           torch.full((n_envs, 128), 7.0, device="cuda"), torch.full((n_steps, n_envs, 5), 7.0, device="cuda"),
+           torch.full((n_carts, 8192), 7.0, device="cuda")]
     p = lambda t: C.c_void_p(t.data_ptr())
     st = getattr(_lib.load(), entry)(tape.h, p(gr), p(gs), None, *[p(t) for t in out],
                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -40,7 +41,7 @@ def _grads(entry, tape, gr, gs, n_envs, n_steps, n_carts):
 
 def test_static_backward_matches_backward_on_two_calls():
     torch = torch_cuda()
-    mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
+    mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8SC]
     n_envs, n_steps = 12, 5
     roms = synth.config_carts(71, mappers)
     env_cart = (np.arange(n_envs) % 3).astype(np.int32)
@@ -51,10 +52,10 @@ def test_static_backward_matches_backward_on_two_calls():
     gr = torch.from_numpy(synth.normal_f32(71, (n_steps, n_envs, 128), 1)).cuda()
     gs = torch.from_numpy(synth.normal_f32(71, (n_steps, n_envs, 210, 160), 2)).cuda()
     want = _grads("vcs_backward", tape, gr, gs, n_envs, n_steps, 3)
-    assert np.abs(want[0]).max() > 0 and np.abs(want[3]).max() > 0
+    assert np.abs(want[0]).max() > 0 and np.abs(want[4]).max() > 0 and np.abs(want[2]).max() > 0
     for call in range(2):
         got = _grads("vcs_backward_static", tape, gr, gs, n_envs, n_steps, 3)
-        for g, w, name in zip(got, want, ("grad_rom", "grad_ram0", "grad_u", "grad_rom_per_cart")):
+        for g, w, name in zip(got, want, ("grad_rom", "grad_ram0", "grad_cart_ram0", "grad_u", "grad_rom_per_cart")):
             _close(g, w, f"call {call}: {name}")
 
 
@@ -68,6 +69,6 @@ def test_static_backward_rejects_oversized_problems():
     b.sync()
     g = torch.empty((n_envs, 128), device="cuda")
     st = _lib.load().vcs_backward_static(tape.h, None, None, None, None, C.c_void_p(g.data_ptr()), None, None,
-                                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
+                                         None, C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == _lib.VCS_ERR_ARG
     assert "fixed" in _lib.load().vcs_last_error(b.h).decode()
