@@ -30,6 +30,11 @@
  *  A11 NMOS decimal mode per the published note on decimal mode;
  *  A12 pushed P always has bits 4 and 5 set (PHP and BRK are the only
  *     pushes of P on a 6507); BRK vectors through $1FFE.
+ *  E0 carts (8 KB in eight 1 KB slices): the cartridge window is four 1 KB
+ *  segments; an access (read or write) to $1FE0+j, $1FE8+j or $1FF0+j maps
+ *  slice j into segment 0, 1 or 2, and segment 3 always shows slice 7; at
+ *  power-on segments 0..2 show slices 4, 5, 6.  A relaxed ROM read's tensor
+ *  is the 1 KB slice the read's segment shows.
  *  Superchip carts (F8SC, F6SC, F4SC: the banked formats plus 128 bytes of
  *  cartridge RAM) write that RAM at $1000-$107F and read it at $1080-$10FF
  *  of the cartridge window, in every bank; a read of the write port returns
@@ -105,6 +110,8 @@ struct ovcs {
   uint32_t rom_size;
   int mapper, bank;
   int sc;                  /* Superchip variant (cartridge RAM at $1000-$10FF) */
+  int e0;                  /* E0 cart: e0seg[k] = the slice segment k (0..2) shows */
+  int e0seg[3];
   /* RIOT */
   uint8_t intim;
   uint32_t interval, phase;
@@ -364,6 +371,10 @@ static void idle(ovcs* s) { tick(s); }
 static int base_mapper(const ovcs* s) { return s->sc ? s->mapper - 3 : s->mapper; }
 
 static void hotspot(ovcs* s, uint16_t a) {
+  if (s->e0) {   /* $1FE0-$1FE7, $1FE8-$1FEF, $1FF0-$1FF7: segment 0, 1, 2 */
+    if (a >= 0x1FE0 && a <= 0x1FF7) s->e0seg[(a - 0x1FE0) / 8] = (a - 0x1FE0) % 8;
+    return;
+  }
   /* F8: $1FF8-$1FF9, F6: $1FF6-$1FF9, F4: $1FF4-$1FFB select banks 0.. */
   static const int first[5] = {0, 0, 0x1FF8, 0x1FF6, 0x1FF4}, count[5] = {0, 0, 2, 4, 8};
   const int m = base_mapper(s);
@@ -382,6 +393,13 @@ static int sc_write_cell(const ovcs* s, uint16_t a) {
 }
 
 static void rom_map(const ovcs* s, uint16_t a, int* base, int* M, int* idx) {
+  if (s->e0) {
+    const int seg = (a >> 10) & 3;
+    *base = 1024 * (seg == 3 ? 7 : s->e0seg[seg]);
+    *M = 1024;
+    *idx = a & 0x3FF;
+    return;
+  }
   if (base_mapper(s) == 0) { *base = 0; *M = 2048; *idx = a & 0x7FF; }
   else if (base_mapper(s) == 1) { *base = 0; *M = 4096; *idx = a & 0xFFF; }
   else { *base = s->bank * 4096; *M = 4096; *idx = a & 0xFFF; }
@@ -994,14 +1012,15 @@ static int step_instruction(ovcs* s) {
 /* ------------------------------------------------------------------ */
 
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
-  static const uint32_t sz[8] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768};
-  if (mapper < 0 || mapper > 7 || rom_size != sz[mapper]) return NULL;
+  static const uint32_t sz[9] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768, 8192};
+  if (mapper < 0 || mapper > 8 || rom_size != sz[mapper]) return NULL;
   ovcs* s = (ovcs*)calloc(1, sizeof(ovcs));
   s->rom = (uint8_t*)malloc(rom_size);
   memcpy(s->rom, rom, rom_size);
   s->rom_size = rom_size;
   s->mapper = mapper;
-  s->sc = mapper >= 5;
+  s->sc = mapper >= 5 && mapper <= 7;
+  s->e0 = mapper == 8;
   s->ystart = ystart;
   ovcs_reset(s);
   return s;
@@ -1034,7 +1053,10 @@ void ovcs_reset(ovcs* s) {
   s->cyc = 0;
   s->jammed = 0;
   memset(s->ram, 0, sizeof s->ram);
-  s->bank = s->mapper >= 2 ? (int)(s->rom_size / 4096) - 1 : 0;   /* banked carts: the last bank */
+  s->bank = s->mapper >= 2 && !s->e0 ? (int)(s->rom_size / 4096) - 1 : 0;   /* banked carts: the last bank */
+  s->e0seg[0] = 4;
+  s->e0seg[1] = 5;
+  s->e0seg[2] = 6;
   s->intim = 0;
   s->interval = 1024;
   s->phase = 0;
@@ -1112,7 +1134,7 @@ void ovcs_get_state(const ovcs* s, uint32_t* o) {
   memset(o, 0, 32 * sizeof(uint32_t));
   o[0] = s->A; o[1] = s->X; o[2] = s->Y; o[3] = s->SP; o[4] = s->P; o[5] = s->pc;
   o[6] = (uint32_t)s->cyc; o[7] = (uint32_t)(s->cyc >> 32);
-  o[8] = s->bank; o[9] = s->intim; o[10] = s->interval; o[11] = s->phase; o[12] = s->underflow;
+  o[8] = (uint32_t)ovcs_bank(s); o[9] = s->intim; o[10] = s->interval; o[11] = s->phase; o[12] = s->underflow;
   o[13] = s->vsync; o[14] = s->vblank; o[15] = s->colup0; o[16] = s->colupf; o[17] = s->colubk;
   o[18] = s->ctrlpf; o[19] = s->pf0; o[20] = s->pf1; o[21] = s->pf2; o[22] = s->grp0;
   o[23] = s->hmp0; o[24] = (uint32_t)s->p0pos; o[25] = (uint32_t)s->hclk; o[26] = (uint32_t)s->line;
@@ -1144,7 +1166,10 @@ void ovcs_set_regs(ovcs* s, int A, int X, int Y, int SP, int P, int PC) {
 void ovcs_set_ram(ovcs* s, const uint8_t* ram128) { memcpy(s->ram, ram128, 128); }
 int ovcs_exec_one(ovcs* s) { return step_instruction(s); }
 uint8_t ovcs_peek(ovcs* s, uint16_t addr) { return peek_raw(s, addr); }
-int ovcs_bank(const ovcs* s) { return s->bank; }
+int ovcs_bank(const ovcs* s) {
+  /* E0: the three switchable segments' slices, 3 bits each */
+  return s->e0 ? s->e0seg[0] | (s->e0seg[1] << 3) | (s->e0seg[2] << 6) : s->bank;
+}
 
 /* ------------------------------------------------------------------ */
 /* soft mode                                                           */

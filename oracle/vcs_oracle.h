@@ -58,8 +58,10 @@ typedef struct {
 /* mapper: 0 = 2K, 1 = 4K, 2 = F8 (8 KB, hotspots $1FF8-9), 3 = F6 (16 KB,
  * $1FF6-9), 4 = F4 (32 KB, $1FF4-B): any access to hotspot j selects 4 KB
  * bank j; 5, 6, 7 = F8SC, F6SC, F4SC: the same with 128 bytes of cartridge
- * RAM written at $1000-$107F and read at $1080-$10FF.  rom is copied.  NULL
- * on a bad size. */
+ * RAM written at $1000-$107F and read at $1080-$10FF; 8 = E0 (8 KB in eight
+ * 1 KB slices; an access to $1FE0+j / $1FE8+j / $1FF0+j maps slice j into
+ * segment 0 / 1 / 2 of the window, segment 3 shows slice 7).  rom is
+ * copied.  NULL on a bad size. */
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart);
 void ovcs_free(ovcs* s);
 /* Power-on state (A7 of the design notes). */

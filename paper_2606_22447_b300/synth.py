@@ -31,8 +31,13 @@ MAPPER_2K, MAPPER_4K, MAPPER_F8, MAPPER_F6, MAPPER_F4 = 0, 1, 2, 3, 4
 # written at $1000-$107F and read at $1080-$10FF
 MAPPER_F8SC, MAPPER_F6SC, MAPPER_F4SC = 5, 6, 7
 MAPPER_SC_BASE = {MAPPER_F8SC: MAPPER_F8, MAPPER_F6SC: MAPPER_F6, MAPPER_F4SC: MAPPER_F4}
+# E0: 8 KB in eight 1 KB slices; an access to $1FE0+j / $1FE8+j / $1FF0+j
+# maps slice j into segment 0 / 1 / 2 of the cartridge window, segment 3
+# always shows slice 7
+MAPPER_E0 = 8
+E0_HOTSPOT = (0x1FE0, 0x1FE8, 0x1FF0)
 MAPPER_SIZE = {MAPPER_2K: 2048, MAPPER_4K: 4096, MAPPER_F8: 8192, MAPPER_F6: 16384, MAPPER_F4: 32768,
-               MAPPER_F8SC: 8192, MAPPER_F6SC: 16384, MAPPER_F4SC: 32768}
+               MAPPER_F8SC: 8192, MAPPER_F6SC: 16384, MAPPER_F4SC: 32768, MAPPER_E0: 8192}
 # banked mappers: number of 4 KB banks and the first hotspot (bank j at hot + j)
 MAPPER_BANKS = {MAPPER_F8: 2, MAPPER_F6: 4, MAPPER_F4: 8, MAPPER_F8SC: 2, MAPPER_F6SC: 4, MAPPER_F4SC: 8}
 MAPPER_HOTSPOT = {MAPPER_F8: 0x1FF8, MAPPER_F6: 0x1FF6, MAPPER_F4: 0x1FF4,
@@ -671,6 +676,8 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     F4SC) are the banked images with their code moved past the cartridge
     RAM ports ($1000-$10FF) and random reads and stores of that RAM.
     """
+    if mapper == MAPPER_E0:
+        return _generate_e0(seed, cart)
     sc = mapper in MAPPER_SC_BASE
     mapper = MAPPER_SC_BASE.get(mapper, mapper)
     if mapper in (MAPPER_F6, MAPPER_F4):
@@ -958,6 +965,145 @@ def _generate_multibank(seed: int, cart: int, mapper: int, sc: bool = False) -> 
         b.word("IRQ")
         banks[k] = bytes(b.resolve())
     return b"".join(banks[k] for k in range(nb))
+
+
+def _generate_e0(seed: int, cart: int) -> bytes:
+    """E0 image: slice 7 (segment 3, $FC00, always mapped) holds a table,
+    the init, the frame loop and the leaf subroutines; each frame the loop
+    maps a VBLANK-work slice (0 or 1) into segment 0, a visible-kernel slice
+    (2, 3 or 4) into segment 1 and an overscan-work slice (5 or 6) into
+    segment 2, picked from the joystick and a work cell, and calls or jumps
+    there.  Every slice is assembled for the segment it is mapped into; the
+    shared table, subroutines and BRK handler are addressed in slice 7."""
+    r = SplitMix64(seed, cart, 0x0CE0)
+    n_lines, vb_budget, vb_loops, os_budget = 12, 1000, 2, 900
+    seg_base = (0xF000, 0xF400, 0xF800, 0xFC00)
+    a = Asm(seg_base[3], 1024)
+    g = _Gen(r, a)
+    _emit_table(a, r)                       # $FC00..: reads of TABLE + 319 stay below the hotspots
+    g.emit_subs(3)
+    a.label("RESET")
+    a.op("SEI")
+    a.op("CLD")
+    a.op("LDX", "imm", 0xFF)
+    a.op("TXS")
+    a.op("LDA", "imm", 0)
+    a.op("LDX", "imm", 0x7F)
+    a.label("CLR")
+    a.op("STA", "zpx", 0x80)
+    a.op("DEX")
+    a.op("BPL", "rel", "CLR")
+    a.op("LDA", "imm", RAM_PTR_TARGET & 0xFF)
+    a.op("STA", "zp", RAM_PTR)
+    a.op("LDA", "imm", RAM_PTR_TARGET >> 8)
+    a.op("STA", "zp", RAM_PTR + 1)
+    a.op("LDA", "imm", ("<", "TABLE"))
+    a.op("STA", "zp", ROM_PTR)
+    a.op("LDA", "imm", (">", "TABLE"))
+    a.op("STA", "zp", ROM_PTR + 1)
+    for _ in range(r.range(4, 10)):
+        a.op("LDA", "imm", r.below(256))
+        a.op("STA", "zp", g.work_cell())
+    for reg in (COLUP0, COLUPF, COLUBK):
+        a.op("LDA", "imm", r.below(256))
+        a.op("STA", "zp", reg)
+    a.op("LDA", "imm", r.pick((0, 1, 4, 5)))
+    a.op("STA", "zp", CTRLPF)
+    a.label("FRAME")
+    a.op("LDA", "imm", 2)
+    a.op("STA", "zp", VBLANK)
+    a.op("STA", "zp", WSYNC)
+    a.op("STA", "zp", VSYNC)
+    for _ in range(3):
+        a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 0)
+    a.op("STA", "zp", VSYNC)
+    a.op("LDA", "imm", VBLANK_TIMER)
+    a.op("STA", "abs", TIM64T)
+    # segment 0 <- slice 0 or 1 (joystick up)
+    a.op("LDA", "abs", SWCHA)
+    a.op("AND", "imm", 0x10)
+    a.op("BEQ", "rel", "V1")
+    a.op("LDA", "abs", E0_HOTSPOT[0] + 0)
+    a.op("JMP", "abs", "VGO")
+    a.label("V1")
+    a.op("LDA", "abs", E0_HOTSPOT[0] + 1)
+    a.label("VGO")
+    a.op("LDA", "imm", vb_loops)
+    a.op("STA", "zp", WORK_CTR)
+    a.label("VBL")
+    a.op("JSR", "abs", seg_base[0])
+    a.op("DEC", "zp", WORK_CTR)
+    a.op("BNE", "rel", "VBL")
+    a.label("VBWAIT")
+    a.op("LDA", "abs", INTIM)
+    a.op("BNE", "rel", "VBWAIT")
+    a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 0)
+    a.op("STA", "zp", VBLANK)
+    # segment 1 <- slice 2, 3 or 4 (joystick high nibble ^ a work cell, mod 4; 0 and 3 pick slice 2)
+    a.op("LDA", "abs", SWCHA)
+    for _ in range(4):
+        a.op("LSR", "acc")
+    a.op("EOR", "zp", WORK_LO)
+    a.op("AND", "imm", 3)
+    a.op("CMP", "imm", 1)
+    a.op("BNE", "rel", "K2")
+    a.op("LDA", "abs", E0_HOTSPOT[1] + 3)
+    a.op("JMP", "abs", seg_base[1])
+    a.label("K2")
+    a.op("CMP", "imm", 2)
+    a.op("BNE", "rel", "K0")
+    a.op("LDA", "abs", E0_HOTSPOT[1] + 4)
+    a.op("JMP", "abs", seg_base[1])
+    a.label("K0")
+    a.op("LDA", "abs", E0_HOTSPOT[1] + 2)
+    a.op("JMP", "abs", seg_base[1])
+    a.label("KEXIT")                        # the kernels end here
+    a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 2)
+    a.op("STA", "zp", VBLANK)
+    a.op("LDA", "imm", OVERSCAN_TIMER)
+    a.op("STA", "abs", TIM64T)
+    # segment 2 <- slice 5 or 6 (a work cell's low bit)
+    a.op("LDA", "zp", WORK_LO)
+    a.op("LSR", "acc")
+    a.op("BCC", "rel", "O5")
+    a.op("LDA", "abs", E0_HOTSPOT[2] + 6)
+    a.op("JMP", "abs", "OGO")
+    a.label("O5")
+    a.op("LDA", "abs", E0_HOTSPOT[2] + 5)
+    a.label("OGO")
+    a.op("JSR", "abs", seg_base[2])
+    a.label("OSWAIT")
+    a.op("LDA", "abs", INTIM)
+    a.op("BNE", "rel", "OSWAIT")
+    a.op("JMP", "abs", "FRAME")
+    a.label("IRQ")
+    a.op("RTI")
+    a.at(0x3E0)                             # the hotspots $1FE0-$1FF7 hold no code
+    a.at(1024 - 6)
+    a.word("IRQ")
+    a.word("RESET")
+    a.word("IRQ")
+    slices = {7: bytes(a.resolve())}
+    shared = {name: a.labels[name] for name in ("TABLE", "IRQ", "KEXIT")}
+    shared.update({name: a.labels[name] for name, _ in g.subs})
+    for k in range(7):
+        seg = 0 if k < 2 else (1 if k < 5 else 2)
+        b = Asm(seg_base[seg], 1024)
+        gk = _Gen(SplitMix64(seed, cart, 0x0CE8 + k), b)
+        b.labels.update(shared)
+        gk.subs = list(g.subs)
+        if seg == 1:
+            _emit_kernel(b, gk, n_lines, "KEXIT")
+        else:
+            b.cycles = 0
+            gk.random_work(vb_budget if seg == 0 else os_budget)
+            b.op("RTS")
+        gk.emit_ptrs()
+        slices[k] = bytes(b.resolve())
+    return b"".join(slices[k] for k in range(8))
 
 
 def config_carts(seed: int, mappers) -> list:

@@ -498,3 +498,78 @@ def test_superchip_carts_use_their_ram():
         c = o.counters()
         assert c["watchdog"] == 0 and c["frames"] == 24
         assert np.count_nonzero(o.cart_ram()) >= 4
+
+
+# ---------------------------------------------------------------------------
+# E0 slices
+# ---------------------------------------------------------------------------
+
+def _e0_image(program):
+    """8 KB E0 image: byte i of slice k is $A0 + k at offsets 0..3 and
+    $10 * k + (i & 15) elsewhere; slice 7 (segment 3, $FC00) holds the
+    program at $FD00 and the vectors."""
+    slices = []
+    for k in range(8):
+        a = synth.Asm(0xFC00 if k == 7 else 0xF000, 1024)
+        for i in range(4):
+            a.byte(0xA0 + k)
+        while len(a.buf) < 0x100:
+            a.byte((0x10 * k + (len(a.buf) & 15)) & 0xFF)
+        if k == 7:
+            program(a)
+            a.at(1024 - 6)
+            a.word(0xFD00), a.word(0xFD00), a.word(0xFD00)
+        slices.append(bytes(a.resolve()))
+    return b"".join(slices)
+
+
+def test_e0_hotspots_map_slices():
+    """Power-on shows slices 4, 5, 6 in segments 0..2 and slice 7 in segment
+    3; an access (read or write) to $1FE0+j, $1FE8+j, $1FF0+j maps slice j
+    into segment 0, 1, 2; $1FDF, $1FF8 and the hotspots' image below A12
+    change nothing."""
+    def program(a):
+        a.at(0x100)
+        for seg, dst in ((0, 0x80), (1, 0x81), (2, 0x82), (3, 0x83)):
+            a.op("LDA", "abs", 0x1000 + 0x400 * seg)
+            a.op("STA", "zp", dst)
+        a.op("LDA", "abs", 0x1FE2)             # segment 0 <- slice 2
+        a.op("STA", "abs", 0x1FEF)             # segment 1 <- slice 7 (a write)
+        a.op("LDA", "abs", 0xFFF1)             # segment 2 <- slice 1 (A13-A15 ignored)
+        a.op("LDA", "abs", 0x1FDF)             # not a hotspot
+        a.op("LDA", "abs", 0x1FF8)             # not a hotspot
+        a.op("LDA", "abs", 0x0FE3)             # A12 = 0: not the cartridge
+        for seg, dst in ((0, 0x84), (1, 0x85), (2, 0x86), (3, 0x87)):
+            a.op("LDA", "abs", 0x1000 + 0x400 * seg)
+            a.op("STA", "zp", dst)
+        a.op("LDA", "abs", 0x1004)              # segment 0 (slice 2), offset 4: $10 * 2 + 4
+        a.op("STA", "zp", 0x88)
+        a.label("HALT")
+        a.op("JMP", "abs", "HALT")
+    o = oracle.Oracle(_e0_image(program), synth.MAPPER_E0)
+    assert o.bank() == 4 | 5 << 3 | 6 << 6
+    for _ in range(40):
+        o.exec_one()
+    ram = o.ram()
+    assert list(ram[:9]) == [0xA4, 0xA5, 0xA6, 0xA7, 0xA2, 0xA7, 0xA1, 0xA7, 0x24]
+    assert o.bank() == 2 | 7 << 3 | 1 << 6
+
+
+def test_e0_carts_map_several_slices():
+    """The generated E0 carts run well-formed frames (no jam, no watchdog)
+    and map every slice of each segment's set over a few frames of random
+    input."""
+    rom = synth.config_carts(21, [synth.MAPPER_E0])[0]
+    assert len(rom) == 8192
+    o = oracle.Oracle(rom, synth.MAPPER_E0)
+    seen = [set(), set(), set()]
+    for a in synth.actions(22, 1, 60)[:, 0]:
+        for _ in range(400):
+            o.trace(int(a), 1)
+            b = int(o.state()[8])
+            for k in range(3):
+                seen[k].add((b >> (3 * k)) & 7)
+    c = o.counters()
+    assert c["watchdog"] == 0 and o.state()[28] == 0
+    assert 1500 < c["instructions"] / c["frames"] < 4000
+    assert {0, 1} <= seen[0] and {2, 3, 4} <= seen[1] and {5, 6} <= seen[2]

@@ -281,3 +281,31 @@ def test_superchip_reverse_equals_tangent_and_finite_differences():
         d[128 + i] = h
         fd = (g.eval(d_ram0=d) - g.eval(d_ram0=-d)) / (2 * h)
         assert abs(fd - g_cram0[i]) <= 1e-6 * max(1.0, abs(g_cram0).max())
+
+
+def test_e0_read_is_relaxed_within_its_slice():
+    """LDA $1002 with slice 3 in segment 0, L = RAM[$80]: the read's tensor
+    is the 1 KB slice (the window is clipped at the slice's first byte and
+    renormalised there; nothing reaches slice 2's last bytes, which precede
+    it in the image)."""
+    tau = 0.5
+    W = max(1, math.ceil(12 * tau))
+    def program(a):
+        a.at(0x100)
+        a.op("LDA", "abs", 0x1FE3)
+        a.op("LDA", "abs", 0x1002)
+        a.op("STA", "zp", 0x80)
+        a.label("HALT")
+        a.op("JMP", "abs", "HALT")
+    from tests.test_oracle_machine import _e0_image
+    rom = _e0_image(program)
+    o = oracle.Oracle(rom, synth.MAPPER_E0)
+    gr = np.zeros((1, 128))
+    gr[0, 0] = 1.0
+    g, ram_out, _ = o.soft_rollout(np.zeros((1, 5)), 1, tau, 6.0, gr, None)
+    assert ram_out[0, 0] == 0xA3
+    g_rom, _, _ = g.reverse()
+    w = np.array([math.exp(-abs(i - 2) / tau) for i in range(0, 2 + W + 1)])
+    want = np.zeros(8192)
+    want[3 * 1024:3 * 1024 + len(w)] = w / w.sum()
+    assert np.allclose(g_rom, want, rtol=0, atol=1e-12)
