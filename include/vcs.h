@@ -58,8 +58,12 @@ typedef enum {
  * cartridge RAM, written at $1000-$107F and read at $1080-$10FF of the
  * cartridge window in every bank (a read of the write port returns the ROM
  * byte there; a write to the read port does nothing), zero at power-on. */
+/* E0 (8 KB, eight 1 KB slices): the cartridge window is four 1 KB segments;
+ * an access to $1FE0+j, $1FE8+j or $1FF0+j maps slice j into segment 0, 1
+ * or 2, segment 3 always shows slice 7, and power-on shows slices 4, 5, 6.
+ * A relaxed ROM read's tensor is the slice its segment shows. */
 enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2, VCS_MAPPER_F6 = 3, VCS_MAPPER_F4 = 4,
-       VCS_MAPPER_F8SC = 5, VCS_MAPPER_F6SC = 6, VCS_MAPPER_F4SC = 7 };
+       VCS_MAPPER_F8SC = 5, VCS_MAPPER_F6SC = 6, VCS_MAPPER_F4SC = 7, VCS_MAPPER_E0 = 8 };
 
 /* Per-env status bits reported by vcs_step / vcs_rollout. */
 enum {
@@ -151,7 +155,8 @@ vcs_status vcs_config_default(vcs_config* cfg);
  * "ROM as a weight tensor", Section 3.1).
  *  roms[c]      host pointer to cart c's image (rom_sizes[c] bytes: 2048,
  *               4096, 8192, 16384 or 32768 for mapper 2K, 4K, F8, F6, F4;
- *               8192, 16384, 32768 for F8SC, F6SC, F4SC); copied.
+ *               8192, 16384, 32768 for F8SC, F6SC, F4SC; 8192 for E0);
+ *               copied.
  *  mappers[c]   VCS_MAPPER_* of cart c.
  *  env_cart     host int32[n_envs]: the cart of each env (0..n_carts-1).
  *  cfg          nullable (defaults).

@@ -13,8 +13,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import ENV_DONE, ENV_JAMMED, ENV_WATCHDOG, Config, VcsError
-from .synth import (MAPPER_2K, MAPPER_4K, MAPPER_F4, MAPPER_F4SC, MAPPER_F6, MAPPER_F6SC, MAPPER_F8, MAPPER_F8SC,
-                    MAPPER_SIZE)
+from .synth import (MAPPER_2K, MAPPER_4K, MAPPER_E0, MAPPER_F4, MAPPER_F4SC, MAPPER_F6, MAPPER_F6SC, MAPPER_F8,
+                    MAPPER_F8SC, MAPPER_SIZE)
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 

@@ -59,6 +59,7 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.roms = b->roms;
   p.cart_banks = b->cart_banks;
   p.ram_words = b->ram_words;
+  p.xmap = b->xmap;
   p.rom_stride = b->rom_stride;
   p.dt = b->dt;
   p.ystart = b->cfg.ystart;
@@ -227,10 +228,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if (!roms || !rom_sizes || !mappers || !env_cart)
     return vcs_fail(nullptr, VCS_ERR_ARG, "null roms / rom_sizes / mappers / env_cart");
   if (n_carts <= 0 || n_envs <= 0) return vcs_fail(nullptr, VCS_ERR_ARG, "n_carts and n_envs must be positive");
-  static const uint32_t want[8] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768};
+  static const uint32_t want[9] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768, 8192};
   uint32_t rom_stride = 8192;   // the largest image, at least 8 KB
   for (int c = 0; c < n_carts; c++) {
-    if (mappers[c] > VCS_MAPPER_F4SC)
+    if (mappers[c] > VCS_MAPPER_E0)
       return vcs_fail(nullptr, VCS_ERR_MAPPER, "cart %d: unknown mapper %d", c, mappers[c]);
     if (rom_sizes[c] != want[mappers[c]])
       return vcs_fail(nullptr, VCS_ERR_ROM_SIZE, "cart %d: %u bytes for mapper %d (want %u)", c, rom_sizes[c],
@@ -311,10 +312,15 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     } else {
       memcpy(d, roms[c], rom_sizes[c]);
     }
-    banks[c] = mappers[c] >= VCS_MAPPER_F8 ? (uint8_t)(rom_sizes[c] / 4096) : 0;
-    if (mappers[c] >= VCS_MAPPER_F8SC) {
+    banks[c] = mappers[c] >= VCS_MAPPER_F8 && mappers[c] != VCS_MAPPER_E0 ? (uint8_t)(rom_sizes[c] / 4096) : 0;
+    if (mappers[c] >= VCS_MAPPER_F8SC && mappers[c] <= VCS_MAPPER_F4SC) {
       banks[c] |= (uint8_t)kCartSC;
       b->ram_words = 64;   // every block reserves room for the Superchip's RAM
+      b->xmap = 1;
+    }
+    if (mappers[c] == VCS_MAPPER_E0) {
+      banks[c] = (uint8_t)kCartE0;
+      b->xmap = 1;
     }
     is2k[c] = mappers[c] == VCS_MAPPER_2K;
   }

@@ -19,8 +19,9 @@ struct vcs_batch {
   uint8_t* roms = nullptr;        // n_carts x rom_stride
   uint32_t rom_stride = 8192;     // bytes per cart image: the largest image, at least 8 KB
   uint8_t* cart_banks = nullptr;  // bank byte of each cart: 4 KB banks of a bank-switched cart, else 0,
-                                  // | kCartSC for a Superchip cart
+                                  // | kCartSC for a Superchip cart | kCartE0 for an E0 cart
   int32_t ram_words = 32;         // RAM words per env in shared memory: 64 when a cart is Superchip
+  int32_t xmap = 0;               // a cart is Superchip or E0: launch the kernels built for them
   uint8_t* cart_2k = nullptr;
   int32_t* env_cart_dev = nullptr;
   int32_t* cart_begin = nullptr;  // [n_carts + 1] first perm slot of each cart

@@ -100,10 +100,11 @@ __device__ __forceinline__ uint32_t relaxed_byte(const FullParams& fp, int32_t M
   const float v = rintf(__fdiv_rn(num, den));
   return (uint32_t)fminf(fmaxf(v, 0.f), 255.f);
 }
-// The ROM tensor is the cart image (2K) or the current 4K bank.
+// The ROM tensor is the cart image (2K), the current 4K bank, or the E0
+// slice the address's segment shows.
 __device__ __forceinline__ uint32_t rom_relaxed(const Ctx& c, const Regs& r, uint32_t addr) {
   const int32_t M = c.fp->rom_m;
-  const uint32_t base = r.bank << 12;
+  const uint32_t base = rom_off(c, r, addr & 0x1FFF) & ~(uint32_t)(M - 1);
   return relaxed_byte(*c.fp, M, (int32_t)(addr & (uint32_t)(M - 1)), [&](int32_t k) { return (uint32_t)c.rom[base | (uint32_t)k]; });
 }
 __device__ __forceinline__ uint32_t ram_relaxed(const Ctx& c, uint32_t addr) {
@@ -131,8 +132,8 @@ __device__ __forceinline__ uint32_t cast_read(Regs& r, uint32_t exact, uint32_t 
 template <int FM = 0>
 __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& st, uint32_t addr, int idx) {
   const uint32_t a = addr & 0x1FFF;
-  r.bank = a - c.hot < c.nb ? a - c.hot : r.bank;   // bank-switch hotspots
-  const uint32_t vrom = c.rom[(r.bank << 12) | (a & 0xFFF)];
+  hotspot(c, r, a);
+  const uint32_t vrom = c.rom[rom_off(c, r, a)];
   const uint32_t vram = ram_rd(c, a);
   const uint32_t q = a & 0xF;
   const uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
@@ -172,7 +173,7 @@ template <class Tape>
 __device__ __forceinline__ void bus_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t addr,
                                           uint32_t v, int idx) {
   const uint32_t a = addr & 0x1FFF;
-  r.bank = a - c.hot < c.nb ? a - c.hot : r.bank;   // bank-switch hotspots
+  hotspot(c, r, a);
   if (sc_write_port(c, a)) cram_wr(c, a, v);
   if ((a & 0x1080) == 0) {   // TIA
     tia_write(c, r, rd, st, tape, a & 0x3F, v & 0xFF, r.fc + idx + st.stall);
@@ -352,8 +353,8 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
                                         Pend& p) {
   if constexpr (OP == 0xAD && FM == 0) {   // the skip assumes exact operand bytes
     const uint32_t off = opaddr & 0xFFF;
-    if (b1 == 0x84 && b2 == 0x02 && (opaddr & 0x1000) && off <= 0xFFA) {
-      const uint8_t* q = c.rom + ((r.bank << 12) | off);
+    if (b1 == 0x84 && b2 == 0x02 && (opaddr & 0x1000) && plain_rom(c, off, 5)) {
+      const uint8_t* q = c.rom + rom_off(c, r, opaddr & 0x1FFF);
       if (q[3] == 0xD0 && q[4] == 0xFB) skip_timer_poll(r, opaddr, st.instr_left);
     }
   }
@@ -590,7 +591,7 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
     p.wv = r.A & r.X;
   } else if (mode == AM_ABS || mode == AM_ABX) {   // NOP abs / abs,X: only a hotspot read matters
     if constexpr (FM >= 1) (void)bus_read<FM>(c, r, st, ea, (int)n);   // the read is a cast to count
-    else r.bank = (ea & 0x1FFF) - c.hot < c.nb ? (ea & 0x1FFF) - c.hot : r.bank;
+    else hotspot(c, r, ea & 0x1FFF);
   } else if (FM >= 1 && (mode == AM_ZP || mode == AM_ZPX)) {
     (void)zp_read<FM>(c, r, ea);
   }
@@ -604,17 +605,17 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
 // Instruction bytes at the program counter, fetched ahead: opcode | first
 // operand << 8 | second operand << 16, or kSlowFetch when the bytes must be
 // read through the bus at execution time (outside the cartridge window, near
-// its end or the bank-switch hotspots, or in a Superchip's RAM ports at its
-// start).  Fetching from the cartridge ROM has no side
+// its end or the bank-switch hotspots, in a Superchip's RAM ports at its
+// start, across an E0 segment boundary).  Fetching from the cartridge ROM
+// has no side
 // effect and does not depend on time, so it may happen as soon as the
 // program counter and bank are known.
 constexpr uint32_t kSlowFetch = 1u << 24;
 
 __device__ __forceinline__ uint32_t prefetch(const Ctx& c, const Regs& r) {
   const uint32_t off = r.PC & 0xFFF;
-  // no hotspot ($1FF4 on) among the three bytes, no Superchip port before them
-  const bool fast = (r.PC & 0x1000) != 0 && off <= 0xFF1 && off >= (c.sc << 8);
-  const uint8_t* q = c.rom + ((r.bank << 12) | (fast ? off : 0u));
+  const bool fast = (r.PC & 0x1000) != 0 && plain_rom(c, off, 3);
+  const uint8_t* q = c.rom + (fast ? rom_off(c, r, r.PC & 0x1FFF) : 0u);
   return (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) | (fast ? 0u : kSlowFetch);
 }
 
@@ -688,7 +689,7 @@ __device__ __forceinline__ bool exec_one(const Ctx& c, Regs& r, Render& rd, Step
       bus_write(c, r, rd, st, tape, addr, (p.wv >> (8 * i)) & 0xFF, (int)(p.widx + i));
     } while (++i < p.nw);
   }
-  if (p.rec) tape.rec(op, p.tref, p.tfl | (r.intim_live << 1) | (r.bank << 2));
+  if (p.rec) tape.rec(op, p.tref, p.tfl | (r.intim_live << 1) | (rec_unit(c, r, p.tref & 0x1FFF) << 2));
   r.cyc += p.n + (uint32_t)st.stall;
   r.fc += (int32_t)p.n + st.stall;
   st.stall = 0;

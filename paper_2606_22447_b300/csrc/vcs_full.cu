@@ -29,7 +29,7 @@ struct FullDivParams {
   const int4* blocks;
   const int32_t* perm;
   const uint8_t* roms;
-  const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC)
+  const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC | kCartE0)
   int32_t ram_words;          // RAM words per env in shared memory (32 or 64)
   const uint8_t* cart_2k;
   uint32_t rom_stride;
@@ -80,12 +80,12 @@ __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
   FullParams* fp = reinterpret_cast<FullParams*>(ram_f + p.ram_words * E);
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t cb = p.cart_banks[cart], nb = cart_banks_of(cb);
+  const uint32_t cb = p.cart_banks[cart];
   if (slot == 0) {
     *fp = fp0;
-    fp->rom_m = p.cart_2k[cart] ? 2048 : 4096;
+    fp->rom_m = p.cart_2k[cart] ? 2048 : (cart_is_e0(cb) ? 1024 : 4096);
   }
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {   // synchronises the block
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb))) {   // synchronises the block
     if (slot == 0) atomicExch(p.err, 1);
     return;
   }
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
   const int env = p.perm[bi.y + slot];
   const int n = p.n_envs;
   // the study is not a hot path: one instantiation serves every batch, the
-  // Superchip ports decoded at run time (off for other carts)
+  // Superchip ports and E0 slices decoded at run time (off for other carts)
   Ctx ch = make_ctx<true>(bs, E, slot, 0, 1, cb, p.ystart);
   ch.fp = fp;
   Ctx cf = ch;

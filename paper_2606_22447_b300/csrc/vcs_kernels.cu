@@ -2,8 +2,8 @@
 // (hard mode, and the SOFT-STE forward, which is the same machine on rounded
 // inputs; the kernel template is in vcs_step.cuh), and the small kernels
 // beside it (output digests, the integer-issue peak, the cartridge-RAM
-// readout).  Batches with Superchip carts launch the instantiations of
-// vcs_kernels_sc.cu.
+// readout).  Batches with Superchip or E0 carts launch the instantiations of
+// vcs_kernels_xm.cu.
 #include <cuda_runtime.h>
 
 #include "vcs_step.cuh"
@@ -112,12 +112,12 @@ int launch_cart_ram(const SoA& s, int32_t n_envs, uint8_t* out, void* stream) {
 size_t step_smem_bytes(int E, uint32_t rom_stride, int ram_words) { return smem_bytes(E, rom_stride, ram_words); }
 
 int launch_step(const StepParams& p, int n_blocks, int E, void* stream) {
-  if (p.ram_words > 32) return launch_step_sc(p, n_blocks, E, stream);
+  if (p.xmap) return launch_step_xm(p, n_blocks, E, stream);
   return launch_run<false, false>(p, n_blocks, E, stream);
 }
 
 int launch_soft_forward(const StepParams& p, int n_blocks, int E, void* stream) {
-  if (p.ram_words > 32) return launch_soft_forward_sc(p, n_blocks, E, stream);
+  if (p.xmap) return launch_soft_forward_xm(p, n_blocks, E, stream);
   return launch_run<true, false>(p, n_blocks, E, stream);
 }
 

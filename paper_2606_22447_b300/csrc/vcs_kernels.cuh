@@ -10,11 +10,11 @@ namespace vcs {
 // (u32 [n_envs]), so a warp's loads and stores of a field are coalesced.
 struct SoA {
   uint32_t* reg;   // A | X << 8 | Y << 16 | SP << 24
-  uint32_t* pcp;   // PC | P << 16 | bank << 24 (3 bits) | jam << 27
+  uint32_t* pcp;   // PC | P << 16 | jam << 24
   uint32_t* cyc;   // CPU cycles mod 2^32
   uint32_t* fcs;   // fc | fs << 16
   uint32_t* tw;    // timer write cycle
-  uint32_t* tv;    // timer value | log2 interval << 8
+  uint32_t* tv;    // timer value | log2 interval << 8 | bank << 16 (E0: three 3-bit slices)
   uint32_t* t0;    // COLUP0 | COLUPF << 8 | COLUBK << 16 | CTRLPF << 24
   uint32_t* t1;    // PF0 | PF1 << 8 | PF2 << 16 | GRP0 << 24
   uint32_t* t2;    // HMP0 | P0 position << 8 | VBLANK << 16 | VSYNC << 24
@@ -27,10 +27,16 @@ constexpr int kSoAFields = 12;
 constexpr int kStateWords = kSoAFields + 64;   // per env
 
 // Per-cart bank byte: the 4 KB banks of a bank-switched cart (2, 4, 8; 0 for
-// 2K and 4K images) | kCartSC for the Superchip variants.
-constexpr uint32_t kCartSC = 0x80;
+// 2K, 4K and E0 images) | kCartSC for the Superchip variants | kCartE0 for
+// E0 (eight 1 KB slices).
+constexpr uint32_t kCartSC = 0x80, kCartE0 = 0x40;
 __host__ __device__ constexpr uint32_t cart_banks_of(uint32_t cb) { return cb & 0x0F; }
 __host__ __device__ constexpr uint32_t cart_is_sc(uint32_t cb) { return cb >> 7; }
+__host__ __device__ constexpr uint32_t cart_is_e0(uint32_t cb) { return (cb >> 6) & 1u; }
+// Bytes of the device image a block stages (2K images are mirrored to 4 KB).
+__host__ __device__ constexpr uint32_t cart_image_bytes(uint32_t cb) {
+  return cart_is_e0(cb) ? 8192u : (cart_banks_of(cb) ? cart_banks_of(cb) * 4096u : 4096u);
+}
 
 struct StepParams {
   SoA s;
@@ -39,8 +45,9 @@ struct StepParams {
   const int32_t* perm;      // slot -> env (envs grouped by cart)
   const uint8_t* roms;      // [n_carts][rom_stride]; 2K images mirrored to 4 KB
   const uint8_t* cart_banks;  // [n_carts] bank byte: 4 KB banks of bank-switched carts (2, 4, 8), else 0,
-                              // | kCartSC for a Superchip cart
+                              // | kCartSC for a Superchip cart | kCartE0 for an E0 cart
   int32_t ram_words;        // RAM words per env in shared memory: 32, or 64 when a cart is Superchip
+  int32_t xmap;             // the batch holds Superchip or E0 carts: launch the kernels built for them
   uint32_t rom_stride;      // bytes per cart image (8, 16 or 32 KB): also the shared-memory ROM region
   const DecodeTables* dt;
   const uint8_t* actions;   // [n_steps][n_envs] or null (NOOP)
@@ -92,8 +99,8 @@ int launch_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests,
 // (soft = the SOFT-STE forward: float inputs / outputs and checkpoints).
 int launch_step(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_soft_forward(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
-// The same for batches with Superchip carts (p.ram_words = 64).
-int launch_step_sc(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
-int launch_soft_forward_sc(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+// The same for batches with Superchip or E0 carts (p.xmap).
+int launch_step_xm(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+int launch_soft_forward_xm(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 
 }  // namespace vcs

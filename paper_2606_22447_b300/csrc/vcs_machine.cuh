@@ -230,8 +230,9 @@ __device__ __forceinline__ void unpack_p(Regs& r, uint32_t p) {
 // The fully relaxed forward's constants (Section 4's temperature-limit
 // study): float32 weights e^{-k/T} of the temperature read for k <= W, the
 // float32 gate values sigma(alpha) and sigma(-alpha) of a crisp-flag branch,
-// and the size of the block's ROM tensor (2048 for 2K carts, else 4096: an
-// F8 read is relaxed within its bank).
+// and the size of the block's ROM tensor (2048 for 2K carts, 1024 for E0
+// carts, whose reads are relaxed within their slice, else 4096: a banked
+// read is relaxed within its bank).
 constexpr int kMaxFullW = 120;
 struct FullParams {
   float ek[kMaxFullW + 1];
@@ -258,6 +259,8 @@ struct Ctx {
   uint32_t hot;              // its first hotspot: an access to hot + j selects bank j
   uint32_t sc;               // 1: Superchip cart, whose 128 bytes of cartridge RAM are RAM
                              // words 32..63 (written at $1000-$107F, read at $1080-$10FF)
+  uint32_t e0;               // 1: E0 cart: Regs::bank holds the slices of segments 0..2
+                             // (3 bits each); segment 3 shows slice 7
   uint32_t rw;               // RAM words of this env: 32, or 64 with the Superchip's RAM
   int32_t ystart;
   // Threads per env: T lanes run one env's machine in lockstep (identical
@@ -294,6 +297,44 @@ __device__ __forceinline__ void cram_wr(const Ctx& c, uint32_t a, uint32_t v) {
   a &= 0x7F;
   c.ram[(32 + (a >> 2)) * c.e4 + (a & 3)] = (uint8_t)v;
 }
+// Offset in the block's cart image of cartridge address a (13-bit): the
+// bank's 4 KB (2K images are mirrored, 4K images have bank 0), or for E0 the
+// 1 KB slice its segment shows.
+__device__ __forceinline__ uint32_t rom_off(const Ctx& c, const Regs& r, uint32_t a) {
+  if (c.e0) {
+    const uint32_t seg = (a >> 10) & 3u;
+    const uint32_t slice = seg == 3u ? 7u : (r.bank >> (3u * seg)) & 7u;
+    return (slice << 10) | (a & 0x3FFu);
+  }
+  return (r.bank << 12) | (a & 0xFFFu);
+}
+// The bank (E0: slice) a tape record keeps for a cartridge reference: the
+// backward maps a ROM read at `a` back to its image byte with it.
+__device__ __forceinline__ uint32_t rec_unit(const Ctx& c, const Regs& r, uint32_t a) {
+  return c.e0 ? (rom_off(c, r, a) >> 10) & 7u : r.bank;
+}
+// Bank switching on an access (read or write) to 13-bit address a: F8 / F6
+// / F4 hotspot j selects bank j; E0's $1FE0+j / $1FE8+j / $1FF0+j map slice
+// j into segment 0 / 1 / 2.
+__device__ __forceinline__ void hotspot(const Ctx& c, Regs& r, uint32_t a) {
+  r.bank = a - c.hot < c.nb ? a - c.hot : r.bank;
+  if (c.e0) {
+    const uint32_t j = a - 0x1FE0u;
+    if (j < 24u) {
+      const uint32_t sh = 3u * (j >> 3);
+      r.bank = (r.bank & ~(7u << sh)) | ((j & 7u) << sh);
+    }
+  }
+}
+// The n (<= 5) cartridge bytes from window offset `off` are plain ROM under
+// one mapping: no bank-switch hotspot ($1FF4 on; E0 $1FE0 on) and no
+// Superchip port among them, and for E0 all in one segment.  Fetch-ahead
+// and the timer-poll check read only such bytes.
+__device__ __forceinline__ bool plain_rom(const Ctx& c, uint32_t off, uint32_t n) {
+  if (c.e0) return (off & 0x3FFu) + n <= 0x400u && off + n <= 0xFE0u;
+  return off + n <= 0xFF4u && off >= (c.sc << 8);
+}
+
 // Superchip ports of a 13-bit address: the read port $1080-$10FF and the
 // write port $1000-$107F (a read there returns the ROM byte, a write to the
 // read port does nothing).

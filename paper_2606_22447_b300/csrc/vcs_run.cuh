@@ -70,9 +70,10 @@ __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTabl
 }
 
 // Context of one replica: env slot `slot` of the block (E envs), replica
-// `rank` of T, of a cart whose bank byte is cb (banks | kCartSC).  SC: the
-// batch may hold Superchip carts; without it the ports are compiled out.
-template <bool SC>
+// `rank` of T, of a cart whose bank byte is cb (banks | kCartSC | kCartE0).
+// XM: the batch may hold Superchip or E0 carts; without it their ports and
+// slices are compiled out.
+template <bool XM>
 __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int rank, int T, uint32_t cb,
                                         int32_t ystart) {
   const uint32_t nb = cart_banks_of(cb);
@@ -85,7 +86,8 @@ __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int
   c.E = (uint32_t)E;
   c.nb = nb;
   c.hot = first_hotspot(nb);
-  c.sc = SC ? cart_is_sc(cb) : 0u;
+  c.sc = XM ? cart_is_sc(cb) : 0u;
+  c.e0 = XM ? cart_is_e0(cb) : 0u;
   c.rw = c.sc ? 64u : 32u;
   c.ystart = ystart;
   c.rank = (uint32_t)rank;
@@ -102,15 +104,14 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
   v = s.pcp[e];
   r.PC = v & 0xFFFF;
   unpack_p(r, (v >> 16) & 0xFF);
-  r.bank = (v >> 24) & 7;
-  r.jam = (v >> 27) & 1;
+  r.jam = (v >> 24) & 1;
   r.cyc = s.cyc[e];
   v = s.fcs[e];
   r.fc = (int32_t)(v & 0xFFFF);
   r.fs = v >> 16;
   r.tw = s.tw[e];
   v = s.tv[e];
-  r.tv = v & 0xFF; r.tsh = (v >> 8) & 0xFF;
+  r.tv = v & 0xFF; r.tsh = (v >> 8) & 0xFF; r.bank = v >> 16;
   v = s.t0[e];
   r.col0 = v & 0xFF; r.colpf = (v >> 8) & 0xFF; r.colbk = (v >> 16) & 0xFF; r.ctrl = v >> 24;
   v = s.t1[e];
@@ -127,11 +128,11 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
 
 __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx& c, const Regs& r) {
   s.reg[e] = r.A | (r.X << 8) | (r.Y << 16) | (r.SP << 24);
-  s.pcp[e] = r.PC | (pack_p(r) << 16) | (r.bank << 24) | (r.jam << 27);
+  s.pcp[e] = r.PC | (pack_p(r) << 16) | (r.jam << 24);
   s.cyc[e] = r.cyc;
   s.fcs[e] = ((uint32_t)r.fc & 0xFFFF) | (r.fs << 16);
   s.tw[e] = r.tw;
-  s.tv[e] = r.tv | (r.tsh << 8);
+  s.tv[e] = r.tv | (r.tsh << 8) | (r.bank << 16);
   s.t0[e] = r.col0 | (r.colpf << 8) | (r.colbk << 16) | (r.ctrl << 24);
   s.t1[e] = r.pf0 | (r.pf1 << 8) | (r.pf2 << 16) | (r.grp0 << 24);
   s.t2[e] = r.hmp0 | (r.pos << 8) | (r.vblank << 16) | (r.vsync << 24);
@@ -142,12 +143,13 @@ __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx&
 
 // Power-on state: A = X = Y = 0, SP = $FD, P = $34, RAM (and the
 // Superchip's RAM) and TIA zero, timer as if 0 had been written to T1024T at
-// cycle 0, banked carts in their last bank, PC from the reset vector.
+// cycle 0, banked carts in their last bank, E0 segments 0..2 showing slices
+// 4, 5, 6, PC from the reset vector.
 __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.A = r.X = r.Y = 0;
   r.SP = 0xFD;
   unpack_p(r, 0x34);
-  r.bank = c.nb ? c.nb - 1u : 0u;
+  r.bank = c.e0 ? (4u | 5u << 3 | 6u << 6) : (c.nb ? c.nb - 1u : 0u);
   r.jam = 0;
   r.cyc = 0;
   r.fc = 0;
@@ -158,7 +160,7 @@ __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.hml = -1;
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
   for (uint32_t i = 0; i < c.rw; i++) w[i * c.E] = 0;
-  r.PC = c.rom[(r.bank << 12) | 0xFFC] | ((uint32_t)c.rom[(r.bank << 12) | 0xFFD] << 8);
+  r.PC = c.rom[rom_off(c, r, 0x1FFC)] | ((uint32_t)c.rom[rom_off(c, r, 0x1FFD)] << 8);
 }
 
 // ALE action -> joystick bits: bit0 right, bit1 left, bit2 down, bit3 up,

@@ -130,8 +130,9 @@ struct BwdParams {
   const int4* blocks;
   const int32_t* perm;
   const uint8_t* roms;        // rounded ROM images of the rollout [n_carts][rom_stride]
-  const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC)
+  const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC | kCartE0)
   int32_t ram_words;          // RAM words per env in the recompute's shared memory (32 or 64)
+  int32_t xmap;               // the batch holds Superchip or E0 carts (their kernels' instantiation)
   uint32_t rom_stride;
   const uint8_t* cart_2k;
   const int32_t* env_cart;    // [n_envs]
@@ -176,9 +177,10 @@ struct RomQueue {
   uint32_t n;
 };
 
-// Cart kind bits of the sweep: the 2K image (ROM index within 2 KB) and the
-// Superchip's RAM ports.
-enum : uint32_t { kKind2K = 1, kKindSC = 2 };
+// Cart kind bits of the sweep: the 2K image (ROM index within 2 KB), the
+// Superchip's RAM ports and E0's 1 KB slices (a record's bank field is then
+// the slice its reference's segment showed).
+enum : uint32_t { kKind2K = 1, kKindSC = 2, kKindE0 = 4 };
 
 // Relaxed read of cell i of a 128-cell RAM tensor whose adjoints start at
 // cell `base` (0: RIOT RAM, 128: the Superchip's RAM).
@@ -194,18 +196,20 @@ __device__ __forceinline__ void spread_ram(float* aram, float* aramc, uint32_t E
 // memory it came from.  RAM cells, ROM impulses and joystick adjoints are
 // compensated sums (value + compensation), since long rollouts add many
 // terms of both signs into them.
-// SC: the sweep's batch may hold Superchip carts (their ports are compiled
-// out otherwise).
-template <bool SC>
+// XM: the sweep's batch may hold Superchip or E0 carts (their ports and
+// slices are compiled out otherwise).
+template <bool XM>
 __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                              const float* izr, int W, RomQueue& rq,
                                              uint32_t kind, uint32_t ref, uint32_t fl, float g) {
   const uint32_t ad = ref & 0x1FFF;
   if (g == 0.f) return;
-  if (SC && (kind & kKindSC) && (ad & 0x1F80) == 0x1080) {   // the Superchip's read port
+  if (XM && (kind & kKindSC) && (ad & 0x1F80) == 0x1080) {   // the Superchip's read port
     spread_ram(aram, aramc, E, ek, izr, W, 128, (int)(ad & 0x7F), g);
   } else if (ad & 0x1000) {
-    rq.idx[rq.n] = (kind & kKind2K) ? (ad & 0x7FF) : ((((fl >> 2) & 7u) << 12) | (ad & 0xFFF));   // the read's bank
+    const uint32_t unit = (fl >> 2) & 7u;   // the read's bank (E0: slice)
+    rq.idx[rq.n] = (kind & kKind2K) ? (ad & 0x7FF)
+                   : (XM && (kind & kKindE0)) ? ((unit << 10) | (ad & 0x3FF)) : ((unit << 12) | (ad & 0xFFF));
     rq.g[rq.n] = g;
     rq.n++;
   } else if (!(ad & 0x80)) {
@@ -226,12 +230,12 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
 
 // Adjoint of the value written to `ref`: taken from the cell (which is then
 // cleared, the write being one-hot).
-template <bool SAMPLER, bool SC>
+template <bool SAMPLER, bool XM>
 __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
                                             uint32_t& j, uint32_t kind, uint32_t ref) {
   const uint32_t ad = ref & 0x1FFF;
   if (ad & 0x1000) {
-    if (!SC || !(kind & kKindSC) || (ad & 0x1F80) != 0x1000) return 0.f;
+    if (!XM || !(kind & kKindSC) || (ad & 0x1F80) != 0x1000) return 0.f;
     const uint32_t o = (128 + (ad & 0x7F)) * E;   // the Superchip's write port
     const float g = aram[o] + aramc[o];
     aram[o] = 0.f;
@@ -280,7 +284,7 @@ __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, u
 
 __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
 
-template <bool SAMPLER, bool SC>
+template <bool SAMPLER, bool XM>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                             const float* izr, int W, RomQueue& rq,
                                             uint32_t kind, const float* cw, uint32_t& j, uint32_t rec) {
@@ -289,52 +293,52 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
       float g = a.A;
       a.A = 0.f;
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
       float g = a.X;
       a.X = 0.f;
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
       float g = a.Y;
       a.Y = 0.f;
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x09: case 0x05: case 0x15: case 0x0D: case 0x1D: case 0x19: case 0x01: case 0x11:
     case 0x29: case 0x25: case 0x35: case 0x2D: case 0x3D: case 0x39: case 0x21: case 0x31:
     case 0x49: case 0x45: case 0x55: case 0x4D: case 0x5D: case 0x59: case 0x41: case 0x51:
     case 0x69: case 0x65: case 0x75: case 0x6D: case 0x7D: case 0x79: case 0x61: case 0x71:
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, a.A);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, a.A);
       break;
     case 0xE9: case 0xE5: case 0xF5: case 0xED: case 0xFD: case 0xF9: case 0xE1: case 0xF1:
     case 0xEB:                                                      // USBC: SBC's alias
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, -a.A);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, -a.A);
       break;
     case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   // LAX: A = X = M
       float g = a.A + a.X;
       a.A = 0.f;
       a.X = 0.f;
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
-      const float g = take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
+      const float g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
       a.A += g;
       a.X += g;
       break;
     }
     case 0x85: case 0x95: case 0x8D: case 0x9D: case 0x99: case 0x81: case 0x91:
-      a.A += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
+      a.A += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x86: case 0x96: case 0x8E:
-      a.X += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
+      a.X += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x84: case 0x94: case 0x8C:
-      a.Y += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
+      a.Y += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x06: case 0x16: case 0x0E: case 0x1E:
     case 0x26: case 0x36: case 0x2E: case 0x3E:
@@ -342,8 +346,8 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x66: case 0x76: case 0x6E: case 0x7E:
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
-      float g = take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref);
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
+      float g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xAA: a.A += a.X; a.X = 0.f; break;   // TAX
@@ -351,22 +355,22 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xA8: a.A += a.Y; a.Y = 0.f; break;   // TAY
     case 0x98: a.Y += a.A; a.A = 0.f; break;   // TYA
     case 0xBA: a.X = 0.f; break;               // TSX: SP carries nothing
-    case 0x48: a.A += take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref); break;   // PHA
-    case 0x08: take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, ref); break;           // PHP
+    case 0x48: a.A += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref); break;   // PHA
+    case 0x08: take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref); break;           // PHP
     case 0x68: {                                                    // PLA
       float g = a.A;
       a.A = 0.f;
-      scatter_read<SC>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
+      scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x20:                                                      // JSR: two pushes
-      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
-      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
+      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
+      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
       break;
     case 0x00:                                                      // BRK: three pushes
-      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 2));
-      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
-      take_write<SAMPLER, SC>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
+      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 2));
+      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
+      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
       break;
     default:
       break;
@@ -422,7 +426,7 @@ __host__ __device__ constexpr size_t sw_tables_end() {
 }
 __host__ __device__ constexpr size_t sw_smem_bytes() { return sw_tables_end() + (size_t)kSweepEnvs * kSweepWarpWords * 4; }
 
-template <int T, bool SAMPLER, bool INSTR, bool SC>
+template <int T, bool SAMPLER, bool INSTR, bool XM>
 __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
@@ -430,9 +434,9 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   float4* grow = reinterpret_cast<float4*>(smem + rc_row_offset(E, p.rom_stride, p.ram_words));  // [40][E] staged gradient rows
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t cb = p.cart_banks[cart], nb = cart_banks_of(cb);
+  const uint32_t cb = p.cart_banks[cart];
   const int g = blockIdx.y, seg = p.seg0 + g;
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb))) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
   }
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
-  Ctx c = make_ctx<SC>(bs, E, slot, rank, T, cb, p.ystart);
+  Ctx c = make_ctx<XM>(bs, E, slot, rank, T, cb, p.ystart);
   Regs r;
   if (active) {
     load_env(soa_at(const_cast<uint32_t*>(p.ckpt + (size_t)seg * kStateWords * n), n), n, env, c, r);
@@ -500,7 +504,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
 // env per warp (lane 0): adjoints of A, X, Y, the timer value, the colour
 // registers, player 0's position and HMP0 in registers, the 128 RAM cells and
 // the Superchip's 128 (compensated) in shared memory.
-template <bool SAMPLER, bool SC>
+template <bool SAMPLER, bool XM>
 __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr int E = kSweepEnvs;
@@ -519,8 +523,9 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   const int env = blockIdx.x * E + slot;
   if (env >= p.n_envs) return;   // whole warps leave together
   const uint32_t cart = (uint32_t)p.env_cart[env];
-  const uint32_t kind = (p.cart_2k[cart] ? kKind2K : 0u) | (SC && cart_is_sc(p.cart_banks[cart]) ? kKindSC : 0u);
-  constexpr int cells = SC ? kSweepCells : 128;   // adjoint cells the sweep keeps
+  const uint32_t kind = (p.cart_2k[cart] ? kKind2K : 0u) | (XM && cart_is_sc(p.cart_banks[cart]) ? kKindSC : 0u) |
+                        (XM && cart_is_e0(p.cart_banks[cart]) ? kKindE0 : 0u);
+  constexpr int cells = XM ? kSweepCells : 128;   // adjoint cells the sweep keeps
   const int n = p.n_envs, g = p.seg - p.seg0;
   const float* m = p.meta + ((size_t)g * n + env) * kMeta;
   if (m[1] != 0.f) return;   // overflow: the error word is set
@@ -541,7 +546,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
       for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
       for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
-      if constexpr (SC) {
+      if constexpr (XM) {
         for (int i = 0; i < 128; i++) {
           aram[(128 + i) * E] = (kind & kKindSC) ? cr[(size_t)(kCarryCram + i) * n + env] : 0.f;
           aramc[(128 + i) * E] = (kind & kKindSC) ? cr[(size_t)(kCarryCram + 128 + i) * n + env] : 0.f;
@@ -591,7 +596,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       }
       if (lead)
         for (uint32_t q = k; q > lo; q--)
-          reverse_one<SAMPLER, SC>(a, aram, aramc, E, ek, izr, p.W, rq, kind, cw, j, recs[q - 1 - 4 * c0]);
+          reverse_one<SAMPLER, XM>(a, aram, aramc, E, ek, izr, p.W, rq, kind, cw, j, recs[q - 1 - 4 * c0]);
       // the warp adds the block's ROM impulses: lane l takes the indices
       // congruent to l mod 32, each in queue order
       const uint32_t qn = __shfl_sync(0xFFFFFFFFu, rq.n, 0);
@@ -625,7 +630,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       for (int i = 0; i < 128; i++) p.grad_ram0[(size_t)env * 128 + i] = aram[i * E] + aramc[i * E];
     if (p.grad_cart_ram0)
       for (int i = 0; i < 128; i++)
-        p.grad_cart_ram0[(size_t)env * 128 + i] = SC ? aram[(128 + i) * E] + aramc[(128 + i) * E] : 0.f;
+        p.grad_cart_ram0[(size_t)env * 128 + i] = XM ? aram[(128 + i) * E] + aramc[(128 + i) * E] : 0.f;
   } else {
     float* cr = p.carry;
     cr[0 * n + env] = a.A; cr[1 * n + env] = a.X; cr[2 * n + env] = a.Y; cr[3 * n + env] = a.V;
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
     cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
-    if (SC && (kind & kKindSC)) {
+    if (XM && (kind & kKindSC)) {
       for (int i = 0; i < 128; i++) cr[(size_t)(kCarryCram + i) * n + env] = aram[(128 + i) * E];
       for (int i = 0; i < 128; i++) cr[(size_t)(kCarryCram + 128 + i) * n + env] = aramc[(128 + i) * E];
     }
@@ -655,46 +660,47 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
   auto go = [&](auto kern, int threads) {
     if ((e = allow_smem(kern, smem)) == cudaSuccess) kern<<<grid, threads, smem, s>>>(p);
   };
-  auto pick = [&](auto sc) {
-    constexpr bool SC = decltype(sc)::value;
+  auto pick = [&](auto xm) {
+    constexpr bool XM = decltype(xm)::value;
     // instruction-granular steps draw nothing (no pixel sums, no position
     // sampler), so one lane per env serves them
     if (p.step_instr > 0) {
-      go(k_soft_recompute<1, false, true, SC>, E);
+      go(k_soft_recompute<1, false, true, XM>, E);
     } else if (p.sampler) {
       switch (T) {
-        case 1: go(k_soft_recompute<1, true, false, SC>, E); break;
-        case 2: go(k_soft_recompute<2, true, false, SC>, 2 * E); break;
-        case 4: go(k_soft_recompute<4, true, false, SC>, 4 * E); break;
-        default: go(k_soft_recompute<8, true, false, SC>, 8 * E); break;
+        case 1: go(k_soft_recompute<1, true, false, XM>, E); break;
+        case 2: go(k_soft_recompute<2, true, false, XM>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, true, false, XM>, 4 * E); break;
+        default: go(k_soft_recompute<8, true, false, XM>, 8 * E); break;
       }
     } else {
       switch (T) {
-        case 1: go(k_soft_recompute<1, false, false, SC>, E); break;
-        case 2: go(k_soft_recompute<2, false, false, SC>, 2 * E); break;
-        case 4: go(k_soft_recompute<4, false, false, SC>, 4 * E); break;
-        default: go(k_soft_recompute<8, false, false, SC>, 8 * E); break;
+        case 1: go(k_soft_recompute<1, false, false, XM>, E); break;
+        case 2: go(k_soft_recompute<2, false, false, XM>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, false, false, XM>, 4 * E); break;
+        default: go(k_soft_recompute<8, false, false, XM>, 8 * E); break;
       }
     }
   };
-  if (p.ram_words > 32) pick(std::true_type{});
+  if (p.xmap) pick(std::true_type{});
   else pick(std::false_type{});
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 static cudaError_t launch_sweep(const BwdParams& p, cudaStream_t s) {
   const int n_blocks = (p.n_envs + kSweepEnvs - 1) / kSweepEnvs;
-  const bool sampler = p.sampler && p.step_instr <= 0, sc = p.ram_words > 32;
-  if (sampler && sc) k_soft_sweep<true, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  const bool sampler = p.sampler && p.step_instr <= 0, xm = p.xmap != 0;
+  if (sampler && xm) k_soft_sweep<true, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
   else if (sampler) k_soft_sweep<true, false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
-  else if (sc) k_soft_sweep<false, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  else if (xm) k_soft_sweep<false, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
   else k_soft_sweep<false, false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
   return cudaGetLastError();
 }
 
 // ROM impulses -> ROM gradient: spread each impulse at a over the read
-// window of its tensor (the 2K image, the 4K image, or one 4 KB bank of a
-// bank-switched cart) with the relaxed read's weights.  One thread per (env,
+// window of its tensor (the 2K image, the 4K image, one 4 KB bank of a
+// bank-switched cart or one 1 KB slice of an E0 cart) with the relaxed
+// read's weights.  One thread per (env,
 // ROM byte); rows are rom_stride floats.
 __global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_cart, const uint8_t* cart_banks,
                              const uint8_t* cart_2k, int32_t n_envs, uint32_t rom_stride, float tau, int32_t W) {
@@ -718,10 +724,10 @@ __global__ void k_rom_spread(const float* imp, float* out, const int32_t* env_ca
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (env >= n_envs || i >= (int)rom_stride) return;
   const int cart = env_cart[env];
-  const int M = cart_2k[cart] ? 2048 : 4096;
+  const uint32_t cb = cart_banks[cart];
+  const int M = cart_2k[cart] ? 2048 : (cart_is_e0(cb) ? 1024 : 4096);   // the read tensor
   float* o = out + (size_t)env * rom_stride;
-  const int nb = (int)cart_banks_of(cart_banks[cart]);
-  if (i >= (nb ? nb * 4096 : M)) {
+  if (i >= (cart_2k[cart] ? 2048 : (int)cart_image_bytes(cb))) {
     o[i] = 0.f;
     return;
   }
@@ -1010,6 +1016,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.roms = t->rom_bytes;
   p.cart_banks = b->cart_banks;
   p.ram_words = b->ram_words;
+  p.xmap = b->xmap;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.env_cart = b->env_cart_dev;
@@ -1165,6 +1172,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.roms = t->rom_bytes;
   p.cart_banks = b->cart_banks;
   p.ram_words = b->ram_words;
+  p.xmap = b->xmap;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.env_cart = b->env_cart_dev;

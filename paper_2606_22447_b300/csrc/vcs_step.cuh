@@ -1,7 +1,8 @@
 // The step kernel (hard mode and the SOFT-STE forward) as a template, shared
 // by the translation units that instantiate it: vcs_kernels.cu for batches
-// without Superchip carts, vcs_kernels_sc.cu for batches with them (SC), so
-// that the cartridge-RAM ports cost the other batches nothing.
+// without Superchip or E0 carts, vcs_kernels_xm.cu for batches with them
+// (XM), so that the cartridge-RAM ports and the slice mapping cost the other
+// batches nothing.
 //
 // One thread per env, one block per run of envs of the same cartridge (the
 // host groups envs by cart), so the block stages exactly one ROM image into
@@ -41,9 +42,9 @@ __device__ __forceinline__ uint32_t round_byte(float v) {
 // forward: joystick bits come from rounded float inputs, outputs are float,
 // the RAM may be overridden from float values first, and the full state is
 // checkpointed at the start of every segment of seg_steps steps.
-// SC: the batch holds Superchip carts (blocks of other carts run with the
-// ports off all the same).
-template <bool SOFT, int T, bool BOOT, bool INSTR, bool SC>
+// XM: the batch holds Superchip or E0 carts (blocks of other carts run with
+// those features off all the same).
+template <bool SOFT, int T, bool BOOT, bool INSTR, bool XM>
 __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   // T threads per env (a compile-time constant, so T = 1 carries no replica
@@ -52,8 +53,8 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   BlockSmem bs = carve_smem(smem, E, p.rom_stride, p.ram_words);
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
-  const uint32_t cb = p.cart_banks[cart], nb = cart_banks_of(cb);
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, nb ? nb * 4096u : 4096u)) {
+  const uint32_t cb = p.cart_banks[cart];
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb))) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
   }
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
-  Ctx c = make_ctx<SC>(bs, E, slot, rank, T, cb, p.ystart);
+  Ctx c = make_ctx<XM>(bs, E, slot, rank, T, cb, p.ystart);
   const bool lead = rank == 0;   // the replica that writes per-env results
 
   Regs r;
@@ -219,7 +220,7 @@ static void launch_kernel(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStr
   kern<<<grid, block, smem, s>>>(p);
 }
 
-template <bool SOFT, bool SC>
+template <bool SOFT, bool XM>
 static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   if (n_blocks <= 0) return 0;
   const dim3 grid(n_blocks), block(E * p.tpe);
@@ -227,21 +228,21 @@ static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   // instruction-granular steps draw nothing, so one lane per env serves them
   if (p.step_instr > 0) {
-    launch_kernel(k_run<SOFT, 1, false, true, SC>, grid, dim3(E), smem, s, p);
+    launch_kernel(k_run<SOFT, 1, false, true, XM>, grid, dim3(E), smem, s, p);
     return (int)cudaGetLastError();
   }
   // the boot sequence exists in the hard step kernel only when a batch asks
   // for it, so that default launches carry none of its code
   const bool boot = !SOFT && p.boot_frames;
   switch (p.tpe * 2 + (boot ? 1 : 0)) {
-    case 2: launch_kernel(k_run<SOFT, 1, false, false, SC>, grid, block, smem, s, p); break;
-    case 4: launch_kernel(k_run<SOFT, 2, false, false, SC>, grid, block, smem, s, p); break;
-    case 8: launch_kernel(k_run<SOFT, 4, false, false, SC>, grid, block, smem, s, p); break;
-    case 16: launch_kernel(k_run<SOFT, 8, false, false, SC>, grid, block, smem, s, p); break;
-    case 3: launch_kernel(k_run<false, 1, true, false, SC>, grid, block, smem, s, p); break;
-    case 5: launch_kernel(k_run<false, 2, true, false, SC>, grid, block, smem, s, p); break;
-    case 9: launch_kernel(k_run<false, 4, true, false, SC>, grid, block, smem, s, p); break;
-    case 17: launch_kernel(k_run<false, 8, true, false, SC>, grid, block, smem, s, p); break;
+    case 2: launch_kernel(k_run<SOFT, 1, false, false, XM>, grid, block, smem, s, p); break;
+    case 4: launch_kernel(k_run<SOFT, 2, false, false, XM>, grid, block, smem, s, p); break;
+    case 8: launch_kernel(k_run<SOFT, 4, false, false, XM>, grid, block, smem, s, p); break;
+    case 16: launch_kernel(k_run<SOFT, 8, false, false, XM>, grid, block, smem, s, p); break;
+    case 3: launch_kernel(k_run<false, 1, true, false, XM>, grid, block, smem, s, p); break;
+    case 5: launch_kernel(k_run<false, 2, true, false, XM>, grid, block, smem, s, p); break;
+    case 9: launch_kernel(k_run<false, 4, true, false, XM>, grid, block, smem, s, p); break;
+    case 17: launch_kernel(k_run<false, 8, true, false, XM>, grid, block, smem, s, p); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 MAPPERS = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
 BANKED = [synth.MAPPER_F6, synth.MAPPER_F4, synth.MAPPER_F8]
 SUPERCHIP = [synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC]
+E0 = [synth.MAPPER_E0, synth.MAPPER_4K, synth.MAPPER_E0]
 
 
 def _oracle_study(rom, mapper, warm, action, T, alpha, n):
@@ -45,7 +46,8 @@ def _oracle_study(rom, mapper, warm, action, T, alpha, n):
                                                   (0.14, 3.0, 2, MAPPERS), (0.01, 20.0, 0, MAPPERS),
                                                   (1.0, 6.0, 0, MAPPERS), (0.15, 6.0, 2, BANKED),
                                                   (0.14, 2.0, 0, BANKED), (0.15, 6.0, 2, SUPERCHIP),
-                                                  (0.14, 6.0, 0, SUPERCHIP)])
+                                                  (0.14, 6.0, 0, SUPERCHIP), (0.15, 6.0, 2, E0),
+                                                  (0.14, 3.0, 0, E0)])
 def test_full_divergence_matches_oracle(T, alpha, warm, mappers):
     torch = torch_cuda()
     MAPPERS = mappers

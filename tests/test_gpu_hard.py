@@ -610,3 +610,53 @@ def test_superchip_ports_on_the_gpu():
         o.rollout(acts[:, 0], 1, screens=False)
         assert np.array_equal(cram[0], o.cart_ram()) and cram[0, 0x20] == 0xA9
         assert not cram[1].any()
+
+
+@pytest.mark.parametrize("epb,tpe", [(16, 1), (64, 2)])
+def test_e0_carts_match_oracle(epb, tpe):
+    """E0 carts (slices mapped per frame from the joystick) next to
+    Superchip and plain carts in one batch: RAM, screens and status
+    bit-exact against the oracle, envs unsorted, several blocks."""
+    mappers = [synth.MAPPER_E0, synth.MAPPER_E0, synth.MAPPER_F8SC, synth.MAPPER_2K]
+    roms = synth.config_carts(309, mappers)
+    env_cart = np.random.default_rng(9).permutation(np.arange(40) % len(mappers)).astype(np.int32)
+    acts = synth.actions(309, 40, 8)
+    _check_all(roms, mappers, env_cart, acts, 2, envs_per_block=epb, threads_per_env=tpe)
+
+
+def test_e0_hotspots_on_the_gpu():
+    """The oracle's E0 hotspot pin on the GPU (reads and writes of each
+    segment's hotspots, neighbours and the image below A12 ignored), then
+    a frame loop that remaps segments 0..2 through indexed hotspot reads
+    and reads the mapped slices."""
+    from tests.test_oracle_machine import _e0_image
+
+    def program(a):
+        a.at(0x100)
+        a.op("LDA", "abs", 0x1FE2)
+        a.op("STA", "abs", 0x1FEF)
+        a.op("LDA", "abs", 0xFFF1)
+        a.op("LDA", "abs", 0x1FDF)
+        a.op("LDA", "abs", 0x1FF8)
+        a.op("LDA", "abs", 0x0FE3)
+        for seg, dst in ((0, 0x84), (1, 0x85), (2, 0x86), (3, 0x87)):
+            a.op("LDA", "abs", 0x1000 + 0x400 * seg)
+            a.op("STA", "zp", dst)
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("LDX", "imm", 0)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("LDA", "absx", 0x1FE0)             # X < 24: segment X / 8 <- slice X % 8
+        a.op("LDA", "absx", 0x1000)             # byte X of segment 0
+        a.op("STA", "zp", 0x09)
+        a.op("INX")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "FRAME")
+    rom = _e0_image(program)
+    acts = synth.actions(310, 3, 3)
+    _check_all([rom], [synth.MAPPER_E0], [0, 0, 0], acts, 1)

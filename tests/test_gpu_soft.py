@@ -393,3 +393,40 @@ def test_gradients_on_superchip_carts(tpe, seg):
             assert not g_cram0[e].any()
         else:
             assert np.abs(o_cram0).max() > 0
+
+
+@pytest.mark.parametrize("tpe", [1, 4])
+def test_gradients_on_e0_carts(tpe):
+    """E0 carts: ROM reads are relaxed within the 1 KB slice their segment
+    shows (the tape keeps the slice per record); ROM, initial RAM and input
+    gradients against the FP64 oracle, with Superchip and plain carts in
+    the same batch and several checkpoint segments."""
+    mappers = [synth.MAPPER_E0, synth.MAPPER_F6SC, synth.MAPPER_E0, synth.MAPPER_2K]
+    n_envs, n_steps, tau = 8, 4, 0.1
+    torch, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 77, envs_per_block=8,
+                                                   threads_per_env=tpe, segment_frames=2)
+    gr = synth.normal_f32(77, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(77, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, b.rom_stride), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    g_pc = torch.empty((len(mappers), b.rom_stride), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u, grad_rom_per_cart=g_pc)
+    b.sync()
+    g_rom, g_ram0, g_u, g_pc = (x.cpu().numpy() for x in (g_rom, g_ram0, g_u, g_pc))
+    want_pc = np.zeros_like(g_pc)
+    for e in range(n_envs):
+        c = env_cart[e]
+        (o_rom, o_ram0, o_u), _, _ = _oracle_grads(roms[c], mappers[c], wa[:, e], u[:, e], 1, tau, gr[:, e],
+                                                   gs[:, e])
+        size = len(roms[c])
+        assert_grad_close(g_rom[e, :size], o_rom, f"grad_rom env {e}")
+        assert np.all(g_rom[e, size:] == 0)
+        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
+        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+        want_pc[c, :size] += o_rom
+        if mappers[c] == synth.MAPPER_E0:
+            assert np.count_nonzero(np.abs(o_rom.reshape(8, 1024)).sum(1)) >= 3   # several slices read
+    assert_grad_close(g_pc, want_pc, "per-cart ROM gradient")
