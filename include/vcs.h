@@ -148,6 +148,20 @@ typedef struct vcs_loss_weights {
   const float* screen;   /* [210 * 160] */
 } vcs_loss_weights;
 
+/* Content-based mapper detection (the paper's ports detect the format from
+ * the image, Section 4).  Rules, from the formats' definitions:
+ *   2048 -> 2K; 4096 -> 4K;
+ *   8192 -> E0 when the image holds an absolute load, store, BIT or NOP
+ *           (opcodes $AD $8D $2C $0C) of a cartridge mirror of an E0
+ *           hotspot ($1FE0-$1FF7 after masking to 13 bits) and no such
+ *           access to the F8 hotspots $1FF8-$1FF9; else F8SC or F8;
+ *   16384 -> F6SC or F6; 32768 -> F4SC or F4;
+ * where the Superchip variant is chosen when every 4 KB bank repeats its
+ * first 128 bytes in the next 128 (the RAM ports hide those 256 bytes, so
+ * images fill them with one pattern).  Any other size: VCS_ERR_ROM_SIZE.
+ * A host-only call (no device work); rom is a host pointer. */
+vcs_status vcs_detect_mapper(const uint8_t* rom, uint32_t size, uint8_t* mapper);
+
 /* Fill *cfg with the defaults listed above. */
 vcs_status vcs_config_default(vcs_config* cfg);
 

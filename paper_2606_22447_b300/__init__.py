@@ -18,8 +18,9 @@ from .synth import (MAPPER_2K, MAPPER_4K, MAPPER_E0, MAPPER_F4, MAPPER_F4SC, MAP
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 
-__all__ = ["Batch", "Tape", "Graph", "Config", "VcsError", "default_config", "autotune_cache_clear", "MAPPER_2K",
-           "MAPPER_F8", "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
+__all__ = ["Batch", "Tape", "Graph", "Config", "VcsError", "default_config", "autotune_cache_clear", "detect_mapper",
+           "MAPPER_2K", "MAPPER_4K", "MAPPER_F8", "MAPPER_F6", "MAPPER_F4", "MAPPER_F8SC", "MAPPER_F6SC", "MAPPER_F4SC",
+           "MAPPER_E0", "MAPPER_SIZE", "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
 
 
 def default_config(**overrides) -> Config:
@@ -57,6 +58,15 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
+
+
+def detect_mapper(rom: bytes) -> int:
+    """The cartridge format of an image (vcs_detect_mapper): one of the
+    MAPPER_* codes, from its size and content."""
+    buf = np.frombuffer(bytes(rom), dtype=np.uint8).copy()
+    out = C.c_uint8()
+    _lib.check(_lib.load().vcs_detect_mapper(buf.ctypes.data_as(_lib.u8p), len(buf), C.byref(out)), None)
+    return int(out.value)
 
 
 class Batch:

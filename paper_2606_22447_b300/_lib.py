@@ -72,6 +72,7 @@ SIGNATURES = {
     "vcs_tape_free": (C.c_int, [vp]),
     "vcs_backward_static": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "vcs_cart_ram": (C.c_int, [vp, vp, vp]),
+    "vcs_detect_mapper": (C.c_int, [u8p, C.c_uint32, u8p]),
     "vcs_autotune": (C.c_int, [vp, i32, i32, vp, vp, vp, C.POINTER(Tune), vp]),
     "vcs_graph_create": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, C.POINTER(vp)]),
     "vcs_graph_launch": (C.c_int, [vp, vp]),

@@ -206,6 +206,44 @@ vcs_status vcs_rom_stride(const vcs_batch* b, int32_t* rom_stride) {
   return VCS_OK;
 }
 
+// Whether every 4 KB bank repeats its first 128 bytes in the next 128.
+static bool superchip_filler(const uint8_t* rom, uint32_t size) {
+  for (uint32_t b = 0; b < size; b += 4096)
+    if (memcmp(rom + b, rom + b + 128, 128) != 0) return false;
+  return true;
+}
+
+// Absolute-mode accesses (LDA, STA, BIT, NOP abs) whose address is a
+// cartridge mirror of [lo, hi].
+static int abs_accesses(const uint8_t* rom, uint32_t size, uint32_t lo, uint32_t hi) {
+  int n = 0;
+  for (uint32_t i = 0; i + 2 < size; i++) {
+    const uint8_t op = rom[i];
+    if (op != 0xAD && op != 0x8D && op != 0x2C && op != 0x0C) continue;
+    const uint32_t a = ((uint32_t)rom[i + 1] | ((uint32_t)rom[i + 2] << 8)) & 0x1FFF;
+    n += a >= lo && a <= hi;
+  }
+  return n;
+}
+
+vcs_status vcs_detect_mapper(const uint8_t* rom, uint32_t size, uint8_t* mapper) {
+  if (!rom || !mapper) return vcs_fail(nullptr, VCS_ERR_ARG, "rom and mapper must not be NULL");
+  switch (size) {
+    case 2048: *mapper = VCS_MAPPER_2K; return VCS_OK;
+    case 4096: *mapper = VCS_MAPPER_4K; return VCS_OK;
+    case 8192:
+      if (abs_accesses(rom, size, 0x1FE0, 0x1FF7) > 0 && abs_accesses(rom, size, 0x1FF8, 0x1FF9) == 0) {
+        *mapper = VCS_MAPPER_E0;
+        return VCS_OK;
+      }
+      *mapper = superchip_filler(rom, size) ? VCS_MAPPER_F8SC : VCS_MAPPER_F8;
+      return VCS_OK;
+    case 16384: *mapper = superchip_filler(rom, size) ? VCS_MAPPER_F6SC : VCS_MAPPER_F6; return VCS_OK;
+    case 32768: *mapper = superchip_filler(rom, size) ? VCS_MAPPER_F4SC : VCS_MAPPER_F4; return VCS_OK;
+    default: return vcs_fail(nullptr, VCS_ERR_ROM_SIZE, "no cartridge format of %u bytes", size);
+  }
+}
+
 vcs_status vcs_batch_info(const vcs_batch* b, int32_t* n_envs, int32_t* n_carts, int32_t* epb) {
   if (!b) return VCS_ERR_ARG;
   if (n_envs) *n_envs = b->n_envs;

@@ -77,3 +77,36 @@ def test_argument_errors_before_device_work(lib):
     assert st == _lib.VCS_ERR_ARG and "envs_per_block" in msg
     assert lib.vcs_step(None, None, 1, None, None, None, None) == _lib.VCS_ERR_ARG
     assert lib.vcs_destroy(None) == _lib.VCS_ERR_ARG
+
+
+def test_detect_mapper(lib):
+    """Content-based detection (host only): every generated format is
+    recognised from its image; an 8 KB image with E0-hotspot accesses is E0
+    unless it also touches the F8 hotspots; Superchip filler in every bank
+    picks the SC variant; other sizes are refused."""
+    from paper_2606_22447_b300 import detect_mapper
+    all_mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
+                   synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0]
+    for seed in (31, 32):
+        for m, rom in zip(all_mappers, synth.config_carts(seed, all_mappers)):
+            assert detect_mapper(rom) == m, (seed, m)
+    f8 = bytearray(synth.generate_cart(33, 0, synth.MAPPER_F8))
+    f8[0x200:0x203] = bytes((0xAD, 0xE5, 0xFF))       # LDA $FFE5: an E0 hotspot mirror, in a cart
+    assert detect_mapper(bytes(f8)) == synth.MAPPER_F8  # that also switches through $1FF8-9
+    e0 = bytearray(synth.generate_cart(33, 0, synth.MAPPER_E0))
+    e0[0x300:0x303] = bytes((0x2C, 0xF9, 0x1F))       # BIT $1FF9: an F8 hotspot
+    assert detect_mapper(bytes(e0)) == synth.MAPPER_F8
+    blank = bytearray(range(256)) * 32                  # no hotspot access, no Superchip filler
+    assert detect_mapper(bytes(blank)) == synth.MAPPER_F8
+    blank[0x1000:0x1003] = bytes((0x8D, 0xF3, 0x3F))  # STA $3FF3 -> $1FF3
+    assert detect_mapper(bytes(blank)) == synth.MAPPER_E0
+    sc = bytearray(synth.generate_cart(34, 0, synth.MAPPER_F6))
+    for b in range(0, len(sc), 4096):
+        sc[b:b + 256] = bytes(range(128)) * 2
+    assert detect_mapper(bytes(sc)) == synth.MAPPER_F6SC
+    sc[4096 + 200] ^= 1                                 # one bank without the repeat
+    assert detect_mapper(bytes(sc)) == synth.MAPPER_F6
+    out = C.c_uint8()
+    buf = np.zeros(3000, np.uint8)
+    assert lib.vcs_detect_mapper(buf.ctypes.data_as(_lib.u8p), 3000, C.byref(out)) == _lib.VCS_ERR_ROM_SIZE
+    assert lib.vcs_detect_mapper(None, 4096, C.byref(out)) == _lib.VCS_ERR_ARG
