@@ -215,7 +215,7 @@ class Oracle:
         return {n: getattr(c, n) for n, _ in Counters._fields_}
 
     def state(self) -> np.ndarray:
-        o = np.zeros(32, np.uint32)
+        o = np.zeros(64, np.uint32)
         lib().ovcs_get_state(self.h, _p(o, C.c_uint32))
         return o
 

@@ -12,11 +12,17 @@
  *     first 8 pixels of a line whose HMOVE strobe hit line clock <= 9;
  *  A5 a write takes effect at colour clock 3 x (cycle count after the cycle
  *     of the write is charged): clocks rendered before it see the old value;
- *  A6 RESP0 -> position 3 during HBLANK, else (clock - 68 + 5) mod 160;
- *     HMOVE subtracts the signed HMP0 high nibble; WSYNC halts the CPU until
- *     the cycle count is a multiple of 76; playfield 20 bits x 4 clocks with
- *     the right half repeated or reflected (CTRLPF bit 0); priority
- *     P0 > PF > BK unless CTRLPF bit 2 (PF > P0 > BK);
+ *  A6 RESP0 / RESP1 -> position 3 during HBLANK, else (clock - 68 + 5) mod
+ *     160; RESM0 / RESM1 / RESBL -> 2, else (clock - 68 + 4) mod 160; HMOVE
+ *     subtracts each object's signed motion nibble; WSYNC halts the CPU
+ *     until the cycle count is a multiple of 76; playfield 20 bits x 4
+ *     clocks with the right half repeated or reflected (CTRLPF bit 0);
+ *     players of 8 bits (REFP bit 3 reflects; GRP delayed by VDELP), sized
+ *     and copied by NUSIZ (copies at +16 / +32 / +64, double and quad
+ *     width), missiles and ball 1 / 2 / 4 / 8 wide (NUSIZ bits 4-5, CTRLPF
+ *     bits 4-5), RESMP hides a missile at its player's position + 4 x width
+ *     - 1; priority P0/M0 > P1/M1 > PF/BL > BK (score mode: the playfield in
+ *     COLUP0 / COLUP1 by half) unless CTRLPF bit 2 (PF/BL first);
  *  A7 power-on: A=X=Y=0, SP=$FD, P=$34, PC from $1FFC/D, RAM and TIA zero,
  *     the timer as if 0 had been written to T1024T at cycle 0, banked carts
  *     (F8, F6, F4 and their Superchip variants) in their last bank, the
@@ -26,7 +32,9 @@
  *     (0xFF - (k - k_u)) & 0xFF and TIMINT bit 7 is set;
  *  A9 only architectural accesses have side effects (dummy reads and the
  *     RMW dummy write are idle cycles);
- *  A10 undriven TIA read bits are 0; collision registers read 0;
+ *  A10 undriven TIA read bits are 0; collisions latch on every visible
+ *     column of every line (blanked or not) until CXCLR and read in D7 / D6
+ *     of CXM0P .. CXPPMM;
  *  A11 NMOS decimal mode per the published note on decimal mode;
  *  A12 pushed P always has bits 4 and 5 set (PHP and BRK are the only
  *     pushes of P on a 6507); BRK vectors through $1FFE.
@@ -120,6 +128,11 @@ struct ovcs {
   /* TIA */
   uint8_t vsync, vblank, colup0, colupf, colubk, ctrlpf, pf0, pf1, pf2, grp0, hmp0;
   int p0pos;
+  /* the rest of the TIA: player 1, the missiles and the ball */
+  uint8_t colup1, nusiz[2], refp[2], grp1, grpo[2], enam[2], enabl, enablo;
+  uint8_t hmp1, hmm[2], hmbl, vdelp[2], vdelbl, resmp[2];
+  int p1pos, mpos[2], blpos;
+  uint16_t cx;             /* collision latches: bit 2 r + 1 = D7 and bit 2 r = D6 of read register r */
   int hclk, line;
   int hmove_line;
   int wsync;
@@ -130,7 +143,7 @@ struct ovcs {
   ovcs_counters cnt;
   /* soft mode */
   ogrf* g;
-  int32_t nA, nX, nY, nV, nC[3], nRAM[256];
+  int32_t nA, nX, nY, nV, nC[4], nRAM[256];   /* nC: COLUP0, COLUPF, COLUBK, COLUP1 */
   int32_t nPos, nHM;       /* deviations of the P0 position and of HMP0 (sampler) */
   int sampler;             /* 1: the differentiable position sampler is on */
   int step_instr;          /* > 0: a step is this many instruction slots, not frames */
@@ -235,51 +248,128 @@ static int pf_bit(const ovcs* s, int x) {
   return (s->pf2 >> (i - 12)) & 1;
 }
 
-static int p0_bit(const ovcs* s, int x) {
-  int d = ((x - s->p0pos) % 160 + 160) % 160;
-  return d < 8 ? (s->grp0 >> (7 - d)) & 1 : 0;
+/* NUSIZ number-and-size field (bits 0-2): the copies' offsets in columns
+ * and the player's pixel width. */
+static int nusiz_copies(int mode, int off[3]) {
+  static const int n[8] = {1, 2, 2, 3, 2, 1, 3, 1};
+  static const int o[8][3] = {{0, 0, 0}, {0, 16, 0}, {0, 32, 0}, {0, 16, 32},
+                              {0, 64, 0}, {0, 0, 0}, {0, 32, 64}, {0, 0, 0}};
+  for (int k = 0; k < 3; k++) off[k] = o[mode][k];
+  return n[mode];
+}
+static int player_scale(int mode) { return mode == 5 ? 2 : (mode == 7 ? 4 : 1); }
+
+/* Player i at visible column x: graphic GRPi (the delayed copy when VDELPi
+ * is set), bit 7 leftmost unless REFPi bit 3 reflects it, each bit
+ * `scale` columns wide, in every copy NUSIZi asks for, wrapping at 160. */
+static int player_bit(const ovcs* s, int i, int x) {
+  const int mode = s->nusiz[i] & 7, sc = player_scale(mode);
+  const int g = (s->vdelp[i] & 1) ? s->grpo[i] : (i ? s->grp1 : s->grp0);
+  const int pos = i ? s->p1pos : s->p0pos;
+  int off[3];
+  const int n = nusiz_copies(mode, off);
+  for (int k = 0; k < n; k++) {
+    const int d = ((x - pos - off[k]) % 160 + 160) % 160;
+    if (d < 8 * sc) {
+      const int b = d / sc;
+      if ((s->refp[i] & 8) ? (g >> b) & 1 : (g >> (7 - b)) & 1) return 1;
+    }
+  }
+  return 0;
+}
+static int p0_bit(const ovcs* s, int x) { return player_bit(s, 0, x); }
+
+/* Missile i: ENAMi bit 1 and not locked to its player (RESMPi bit 1),
+ * 1 << NUSIZi bits 4-5 columns wide, in the player's copies (one copy for
+ * the double and quad sizes). */
+static int missile_bit(const ovcs* s, int i, int x) {
+  if (!(s->enam[i] & 2) || (s->resmp[i] & 2)) return 0;
+  const int mode = s->nusiz[i] & 7, w = 1 << ((s->nusiz[i] >> 4) & 3);
+  int off[3];
+  const int n = nusiz_copies(mode, off);
+  for (int k = 0; k < n; k++)
+    if (((x - s->mpos[i] - off[k]) % 160 + 160) % 160 < w) return 1;
+  return 0;
+}
+
+/* The ball: ENABL bit 1 (the delayed copy when VDELBL is set), 1 << CTRLPF
+ * bits 4-5 columns wide. */
+static int ball_bit(const ovcs* s, int x) {
+  const int en = (s->vdelbl & 1) ? s->enablo : s->enabl;
+  if (!(en & 2)) return 0;
+  return ((x - s->blpos) % 160 + 160) % 160 < (1 << ((s->ctrlpf >> 4) & 3));
+}
+
+/* Colour owner of a column from the objects present there: 0 = COLUP0
+ * (P0, M0), 3 = COLUP1 (P1, M1), 1 = COLUPF (PF, BL), 2 = COLUBK.  CTRLPF
+ * bit 2 clear: P0/M0 > P1/M1 > PF/BL > BK, the playfield taking COLUP0 in
+ * the left half and COLUP1 in the right one in score mode (bit 1); bit 2
+ * set: PF/BL > P0/M0 > P1/M1 > BK. */
+static int owner_of(const ovcs* s, int x, int p0, int m0, int p1, int m1, int pf, int bl) {
+  if (s->ctrlpf & 4) {
+    if (pf || bl) return 1;
+    if (p0 || m0) return 0;
+    if (p1 || m1) return 3;
+    return 2;
+  }
+  if (p0 || m0) return 0;
+  if (p1 || m1) return 3;
+  if (pf) return (s->ctrlpf & 2) ? (x < 80 ? 0 : 3) : 1;
+  if (bl) return 1;
+  return 2;
+}
+static uint8_t owner_colour(const ovcs* s, int o) {
+  return o == 0 ? s->colup0 : (o == 1 ? s->colupf : (o == 2 ? s->colubk : s->colup1));
+}
+
+/* Collisions at column x (every visible column of every line, whether or
+ * not VBLANK or the HMOVE blank hides it): latch each overlapping pair. */
+static void collide(ovcs* s, int x) {
+  const int p0 = player_bit(s, 0, x), p1 = player_bit(s, 1, x), m0 = missile_bit(s, 0, x);
+  const int m1 = missile_bit(s, 1, x), bl = ball_bit(s, x), pf = pf_bit(s, x);
+  const int pair[16] = {m0 && p0, m0 && p1, m1 && p1, m1 && p0, p0 && bl, p0 && pf, p1 && bl, p1 && pf,
+                        m0 && bl, m0 && pf, m1 && bl, m1 && pf, 0, bl && pf, m0 && m1, p0 && p1};
+  for (int k = 0; k < 16; k++)
+    if (pair[k]) s->cx |= (uint16_t)(1u << k);
 }
 
 /* Differentiable position sampler (Section 3, the sub-pixel bilinear kernel
- * over sprite position): the player's coverage of column x relaxed with a
- * triangular kernel, cov(x) = sum_k b_k tri(x - pos - k).  Its derivative
- * with respect to pos at the integer hard point, taken symmetrically, is
- * (b(d - 1) - b(d + 1)) / 2 with d = x - pos (mod 160), so
- * d pixel / d pos = (C_P0 - C_under) (b(d - 1) - b(d + 1)) / 2, where
- * C_under is the colour the pixel has without the player.  Zero where the
- * playfield has priority over a playfield pixel (the player is hidden
- * there), and on blanked pixels (the caller skips those). */
-static int p0_bit_at(const ovcs* s, int d) {
-  d = ((d % 160) + 160) % 160;
-  return d < 8 ? (s->grp0 >> (7 - d)) & 1 : 0;
-}
+ * over sprite position): player 0's coverage of column x relaxed with a
+ * triangular kernel, cov(x) = sum_k b_k tri(x - pos - k) over its drawn
+ * columns (copies, size and reflection included).  Its derivative with
+ * respect to pos at the integer hard point, taken symmetrically, is
+ * (b(x - 1) - b(x + 1)) / 2 with b the hard coverage, so d pixel / d pos =
+ * (C_with - C_without) (b(x - 1) - b(x + 1)) / 2, where C_with and
+ * C_without are the colours the pixel has with and without a player-0
+ * pixel there (the priority logic decides both; zero where the player is
+ * hidden).  Blanked pixels carry nothing (the caller skips them). */
 static double sampler_slope(const ovcs* s, int x) {
-  int pf = pf_bit(s, x);
-  if ((s->ctrlpf & 4) && pf) return 0.0;
-  int d = x - s->p0pos;
-  int db = p0_bit_at(s, d - 1) - p0_bit_at(s, d + 1);
+  /* the player's relaxed coverage slope at x, times the colour the pixel
+   * has with a player pixel there minus the colour without one */
+  const int db = p0_bit(s, ((x - 1) % 160 + 160) % 160) - p0_bit(s, (x + 1) % 160);
   if (!db) return 0.0;
-  int under = (pf ? s->colupf : s->colubk) & 0xFE;
-  return 0.5 * (double)db * (double)((s->colup0 & 0xFE) - under);
+  const int p1 = player_bit(s, 1, x), m0 = missile_bit(s, 0, x), m1 = missile_bit(s, 1, x);
+  const int bl = ball_bit(s, x), pf = pf_bit(s, x);
+  const int with = owner_colour(s, owner_of(s, x, 1, m0, p1, m1, pf, bl)) & 0xFE;
+  const int without = owner_colour(s, owner_of(s, x, 0, m0, p1, m1, pf, bl)) & 0xFE;
+  return 0.5 * (double)db * (double)(with - without);
 }
 
-/* Pixel at visible column x of the current scanline; *owner = 0 (P0),
- * 1 (PF), 2 (BK) or -1 (blanked). */
+/* Pixel at visible column x of the current scanline; *owner = the colour
+ * register that owns it (owner_of) or -1 (blanked). */
 static uint8_t pixel(const ovcs* s, int x, int* owner) {
   if (s->vblank & 2) { *owner = -1; return 0; }
   if (s->hmove_line == s->line && x < 8) { *owner = -1; return 0; }
-  int pf = pf_bit(s, x), p0 = p0_bit(s, x);
-  int o;
-  if (s->ctrlpf & 4) o = pf ? 1 : (p0 ? 0 : 2);
-  else o = p0 ? 0 : (pf ? 1 : 2);
+  const int o = owner_of(s, x, player_bit(s, 0, x), missile_bit(s, 0, x), player_bit(s, 1, x),
+                         missile_bit(s, 1, x), pf_bit(s, x), ball_bit(s, x));
   *owner = o;
-  uint8_t c = o == 0 ? s->colup0 : (o == 1 ? s->colupf : s->colubk);
-  return c & 0xFE;
+  return owner_colour(s, o) & 0xFE;
 }
 
 static void tia_clock(ovcs* s) {
   if (s->hclk >= 68) {
     int x = s->hclk - 68, row = s->line - s->ystart;
+    collide(s, x);
     if (row >= 0 && row < SCR_H) {
       int owner;
       s->fb[row * SCR_W + x] = pixel(s, x, &owner);
@@ -294,6 +384,14 @@ static void tia_clock(ovcs* s) {
   if (++s->hclk == 228) { s->hclk = 0; s->line++; }
 }
 
+/* RESMPi bit 1 set: missile i is hidden and sits at its player's position
+ * plus 4 x the player's pixel width minus 1 (near the player's centre). */
+static void lock_missiles(ovcs* s) {
+  for (int i = 0; i < 2; i++)
+    if (s->resmp[i] & 2)
+      s->mpos[i] = ((i ? s->p1pos : s->p0pos) + 4 * player_scale(s->nusiz[i] & 7) - 1) % 160;
+}
+
 static void tia_write(ovcs* s, int reg, val x) {
   uint8_t v = x.v;
   s->cnt.tia_writes++;
@@ -304,29 +402,63 @@ static void tia_write(ovcs* s, int reg, val x) {
       break;
     case 0x01: s->vblank = v; break;
     case 0x02: s->wsync = 1; break;
+    case 0x04: s->nusiz[0] = v; lock_missiles(s); break;
+    case 0x05: s->nusiz[1] = v; lock_missiles(s); break;
     case 0x06: s->colup0 = v; s->nC[0] = x.n; break;
+    case 0x07: s->colup1 = v; s->nC[3] = x.n; break;
     case 0x08: s->colupf = v; s->nC[1] = x.n; break;
     case 0x09: s->colubk = v; s->nC[2] = x.n; break;
     case 0x0A: s->ctrlpf = v; break;
+    case 0x0B: s->refp[0] = v; break;
+    case 0x0C: s->refp[1] = v; break;
     case 0x0D: s->pf0 = v; break;
     case 0x0E: s->pf1 = v; break;
     case 0x0F: s->pf2 = v; break;
     case 0x10:   /* RESP0: a position from strobe timing carries no deviation */
       s->p0pos = s->hclk < 68 ? 3 : (s->hclk - 68 + 5) % 160;
       s->nPos = 0;
+      lock_missiles(s);
       break;
-    case 0x1B: s->grp0 = v; break;
+    case 0x11: s->p1pos = s->hclk < 68 ? 3 : (s->hclk - 68 + 5) % 160; lock_missiles(s); break;
+    /* RESM0, RESM1, RESBL: 2 in HBLANK, else the beam position plus 4 */
+    case 0x12: s->mpos[0] = s->hclk < 68 ? 2 : (s->hclk - 68 + 4) % 160; lock_missiles(s); break;
+    case 0x13: s->mpos[1] = s->hclk < 68 ? 2 : (s->hclk - 68 + 4) % 160; lock_missiles(s); break;
+    case 0x14: s->blpos = s->hclk < 68 ? 2 : (s->hclk - 68 + 4) % 160; break;
+    /* vertical delay: a GRP0 write copies GRP1 to its delayed register, a
+     * GRP1 write copies GRP0 and ENABL to theirs */
+    case 0x1B: s->grp0 = v; s->grpo[1] = s->grp1; break;
+    case 0x1C: s->grp1 = v; s->grpo[0] = s->grp0; s->enablo = s->enabl; break;
+    case 0x1D: s->enam[0] = v; break;
+    case 0x1E: s->enam[1] = v; break;
+    case 0x1F: s->enabl = v; break;
     case 0x20: s->hmp0 = v; s->nHM = x.n; break;
-    case 0x2A: {
+    case 0x21: s->hmp1 = v; break;
+    case 0x22: s->hmm[0] = v; break;
+    case 0x23: s->hmm[1] = v; break;
+    case 0x24: s->hmbl = v; break;
+    case 0x25: s->vdelp[0] = v; break;
+    case 0x26: s->vdelp[1] = v; break;
+    case 0x27: s->vdelbl = v; break;
+    case 0x28: s->resmp[0] = v; lock_missiles(s); break;
+    case 0x29: s->resmp[1] = v; lock_missiles(s); break;
+    case 0x2A: {   /* HMOVE: every object moves by minus its signed motion nibble */
       int m = ((int8_t)s->hmp0) >> 4;
       s->p0pos = ((s->p0pos - m) % 160 + 160) % 160;
       /* the motion is minus the high nibble of HMP0: a deviation of HMP0
        * moves the player by minus a sixteenth of it (straight-through) */
       if (s->sampler) s->nPos = lin2(s, s->nPos, 1.0, s->nHM, -1.0 / 16.0);
+      s->p1pos = ((s->p1pos - (((int8_t)s->hmp1) >> 4)) % 160 + 160) % 160;
+      for (int i = 0; i < 2; i++) s->mpos[i] = ((s->mpos[i] - (((int8_t)s->hmm[i]) >> 4)) % 160 + 160) % 160;
+      s->blpos = ((s->blpos - (((int8_t)s->hmbl) >> 4)) % 160 + 160) % 160;
+      lock_missiles(s);
       if (s->hclk <= 9) s->hmove_line = s->line;
       break;
     }
-    case 0x2B: s->hmp0 = 0; s->nHM = 0; break;
+    case 0x2B:   /* HMCLR */
+      s->hmp0 = 0; s->nHM = 0;
+      s->hmp1 = s->hmm[0] = s->hmm[1] = s->hmbl = 0;
+      break;
+    case 0x2C: s->cx = 0; break;   /* CXCLR */
     default: break;
   }
 }
@@ -434,6 +566,9 @@ static uint8_t full_cast(ovcs* s, const uint8_t* t, int M, int a) {
   return s->full == 2 ? v : t[a];
 }
 
+/* Collision read register r (CXM0P .. CXPPMM): its two latches in D7, D6. */
+static uint8_t collision_reg(const ovcs* s, int r) { return (uint8_t)(((s->cx >> (2 * r)) & 3) << 6); }
+
 /* One bus read cycle. */
 static val rd(ovcs* s, uint16_t addr) {
   tick(s);
@@ -455,7 +590,7 @@ static val rd(ovcs* s, uint16_t addr) {
     switch (a & 0x0F) {
       case 0x0C: r.v = s->inpt4; r.n = s->g ? lin1(s, s->u_leaf + 4, -128.0) : 0; break;
       case 0x0D: r.v = 0x80; break;
-      default: r.v = 0; break;
+      default: r.v = (a & 0x0F) < 8 ? collision_reg(s, a & 7) : 0; break;   /* no gradient: latched switches */
     }
   } else if (!(a & 0x200)) {
     r.v = s->full ? full_cast(s, s->ram, 128, a & 0x7F) : s->ram[a & 0x7F];
@@ -492,7 +627,8 @@ static uint8_t peek_raw(ovcs* s, uint16_t addr) {
     rom_map(s, a, &base, &M, &idx);
     return s->rom[base + idx];
   }
-  if (!(a & 0x80)) return (a & 0x0F) == 0x0C ? s->inpt4 : ((a & 0x0F) == 0x0D ? 0x80 : 0);
+  if (!(a & 0x80))
+    return (a & 0x0F) == 0x0C ? s->inpt4 : ((a & 0x0F) == 0x0D ? 0x80 : ((a & 0x0F) < 8 ? collision_reg(s, a & 7) : 0));
   if (!(a & 0x200)) return s->ram[a & 0x7F];
   if (!(a & 0x04)) return (a & 3) == 0 ? s->swcha : ((a & 3) == 2 ? s->swchb : 0);
   return (a & 1) ? (s->underflow ? 0x80 : 0) : s->intim;
@@ -1067,6 +1203,13 @@ void ovcs_reset(ovcs* s) {
   s->vsync = s->vblank = s->colup0 = s->colupf = s->colubk = 0;
   s->ctrlpf = s->pf0 = s->pf1 = s->pf2 = s->grp0 = s->hmp0 = 0;
   s->p0pos = 0;
+  s->colup1 = s->grp1 = s->enabl = s->enablo = s->hmp1 = s->hmbl = s->vdelbl = 0;
+  for (int i = 0; i < 2; i++) {
+    s->nusiz[i] = s->refp[i] = s->grpo[i] = s->enam[i] = s->hmm[i] = s->vdelp[i] = s->resmp[i] = 0;
+    s->mpos[i] = 0;
+  }
+  s->p1pos = s->blpos = 0;
+  s->cx = 0;
   s->hclk = 0;
   s->line = 0;
   s->hmove_line = -1;
@@ -1131,7 +1274,7 @@ int ovcs_step(ovcs* s, int action, int frame_skip, uint8_t* ram_out, uint8_t* sc
 void ovcs_get_counters(const ovcs* s, ovcs_counters* out) { *out = s->cnt; }
 
 void ovcs_get_state(const ovcs* s, uint32_t* o) {
-  memset(o, 0, 32 * sizeof(uint32_t));
+  memset(o, 0, 64 * sizeof(uint32_t));
   o[0] = s->A; o[1] = s->X; o[2] = s->Y; o[3] = s->SP; o[4] = s->P; o[5] = s->pc;
   o[6] = (uint32_t)s->cyc; o[7] = (uint32_t)(s->cyc >> 32);
   o[8] = (uint32_t)ovcs_bank(s); o[9] = s->intim; o[10] = s->interval; o[11] = s->phase; o[12] = s->underflow;
@@ -1139,6 +1282,12 @@ void ovcs_get_state(const ovcs* s, uint32_t* o) {
   o[18] = s->ctrlpf; o[19] = s->pf0; o[20] = s->pf1; o[21] = s->pf2; o[22] = s->grp0;
   o[23] = s->hmp0; o[24] = (uint32_t)s->p0pos; o[25] = (uint32_t)s->hclk; o[26] = (uint32_t)s->line;
   o[27] = (uint32_t)s->hmove_line; o[28] = (uint32_t)s->jammed;
+  o[29] = s->colup1; o[30] = s->nusiz[0]; o[31] = s->nusiz[1]; o[32] = s->refp[0]; o[33] = s->refp[1];
+  o[34] = s->grp1; o[35] = s->grpo[0]; o[36] = s->grpo[1]; o[37] = s->enam[0]; o[38] = s->enam[1];
+  o[39] = s->enabl; o[40] = s->enablo; o[41] = s->hmp1; o[42] = s->hmm[0]; o[43] = s->hmm[1];
+  o[44] = s->hmbl; o[45] = s->vdelp[0]; o[46] = s->vdelp[1]; o[47] = s->vdelbl; o[48] = s->resmp[0];
+  o[49] = s->resmp[1]; o[50] = (uint32_t)s->p1pos; o[51] = (uint32_t)s->mpos[0]; o[52] = (uint32_t)s->mpos[1];
+  o[53] = (uint32_t)s->blpos; o[54] = s->cx;
 }
 
 void ovcs_get_ram(const ovcs* s, uint8_t* out128) { memcpy(out128, s->ram, 128); }
@@ -1242,7 +1391,7 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   /* ROM-read nodes address ROM leaves at rom0 + base + index */
   for (int i = 0; i < 256; i++) s->nRAM[i] = g->ram0 + i;
   s->nA = s->nX = s->nY = s->nV = 0;
-  s->nC[0] = s->nC[1] = s->nC[2] = 0;
+  s->nC[0] = s->nC[1] = s->nC[2] = s->nC[3] = 0;
   s->nPos = s->nHM = 0;
   s->gs_all = grad_screen;
   for (int t = 0; t < n_steps; t++) {
@@ -1263,7 +1412,7 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   s->gs = s->gs_all = NULL;
   for (int i = 0; i < 256; i++) s->nRAM[i] = 0;
   s->nA = s->nX = s->nY = s->nV = 0;
-  s->nC[0] = s->nC[1] = s->nC[2] = 0;
+  s->nC[0] = s->nC[1] = s->nC[2] = s->nC[3] = 0;
   s->nPos = s->nHM = 0;
   return g;
 }

@@ -95,7 +95,7 @@ void ovcs_set_full(ovcs* s, int mode, double T, double alpha);
 int ovcs_step(ovcs* s, int action, int frame_skip, uint8_t* ram_out, uint8_t* screen_out);
 void ovcs_get_counters(const ovcs* s, ovcs_counters* out);
 /* Machine state as 32 words (layout in the .c file). */
-void ovcs_get_state(const ovcs* s, uint32_t* out32);
+void ovcs_get_state(const ovcs* s, uint32_t* out64);   /* registers, clocks, TIA (64 words) */
 void ovcs_get_ram(const ovcs* s, uint8_t* out128);
 void ovcs_get_cart_ram(const ovcs* s, uint8_t* out128);   /* Superchip RAM (zero otherwise) */
 /* Run n instructions, recording per instruction: pc, opcode, A, X, Y, SP,

@@ -364,6 +364,15 @@ TABLE_LEN = 64 + 256
 
 VISUAL_REGS = (COLUP0, COLUP0, COLUPF, COLUPF, COLUBK, PF0, PF1, PF2, PF1, GRP0,
                GRP0, GRP0, RESP0, RESP0, HMP0, CTRLPF)
+# the rest of the TIA (full-TIA carts): player 1, missiles, ball, sizes,
+# reflection, motion, vertical delay, missile locks, collision clear
+NUSIZ0, NUSIZ1, COLUP1, REFP0, REFP1 = 0x04, 0x05, 0x07, 0x0B, 0x0C
+RESP1, RESM0, RESM1, RESBL, GRP1, ENAM0, ENAM1, ENABL = 0x11, 0x12, 0x13, 0x14, 0x1C, 0x1D, 0x1E, 0x1F
+HMP1, HMM0, HMM1, HMBL, VDELP0, VDELP1, VDELBL, RESMP0, RESMP1, HMCLR, CXCLR = (
+    0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x28, 0x29, 0x2B, 0x2C)
+FULL_TIA_REGS = VISUAL_REGS + (COLUP1, COLUP1, GRP1, GRP1, NUSIZ0, NUSIZ1, REFP0, REFP1, RESP1, RESM0,
+                               RESM1, RESBL, ENAM0, ENAM1, ENABL, ENABL, HMP1, HMM0, HMM1, HMBL, VDELP0,
+                               VDELP1, VDELBL, RESMP0, RESMP1, HMCLR, CXCLR)
 VBLANK_TIMER = 43    # x64 cycles
 OVERSCAN_TIMER = 35
 
@@ -374,6 +383,7 @@ class _Gen:
     def __init__(self, rng: SplitMix64, asm: Asm):
         self.r = rng
         self.a = asm
+        self.full_tia = _FULL_TIA[0]   # store to every TIA object register, read the collision latches
         self.subs = []          # (label, budget cycles of body + RTS)
         self.ptrs = []          # (pointer label, target label) for JMP (ind)
         self.n_lbl = 0
@@ -394,7 +404,9 @@ class _Gen:
         if mode == "imm":
             a.op(mnem, "imm", r.below(256))
         elif mode == "zp":
-            if allow_io and r.chance(0.1):
+            if allow_io and self.full_tia and r.chance(0.15):
+                a.op(mnem, "zp", r.below(8))        # a collision latch register
+            elif allow_io and r.chance(0.1):
                 a.op(mnem, "zp", r.pick((INPT4, INPT5, 0x00, 0x03)))
             else:
                 a.op(mnem, "zp", r.range(0x80, 0xFF))
@@ -638,7 +650,7 @@ class _Gen:
                 a.op("NOP")
             if a.cycles + 3 > budget:
                 break
-            a.op(r.pick(("STA", "STA", "STX", "STY")), "zp", r.pick(VISUAL_REGS))
+            a.op(r.pick(("STA", "STA", "STX", "STY")), "zp", r.pick(FULL_TIA_REGS if self.full_tia else VISUAL_REGS))
         assert a.cycles <= budget
 
 
@@ -663,7 +675,7 @@ def _emit_table(a: Asm, r: SplitMix64):
         a.byte(r.below(256))
 
 
-def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
+def generate_cart(seed: int, cart: int, mapper: int, full_tia: bool = False) -> bytes:
     """Seed -> ROM image (2048, 4096, 8192, 16384 or 32768 bytes) of a well-formed frame loop.
 
     Layout: reset vector -> init (SEI, CLD, stack, RAM clear, pointers) ->
@@ -675,7 +687,21 @@ def generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     at the same offsets in both banks.  Superchip variants (F8SC, F6SC,
     F4SC) are the banked images with their code moved past the cartridge
     RAM ports ($1000-$10FF) and random reads and stores of that RAM.
+    full_tia: the scanline stores also reach player 1, the missiles, the
+    ball and their size / motion / delay / lock registers and CXCLR, and
+    the random work also reads the collision latches (into RAM).
     """
+    _FULL_TIA[0] = full_tia
+    try:
+        return _generate_cart(seed, cart, mapper)
+    finally:
+        _FULL_TIA[0] = False
+
+
+_FULL_TIA = [False]
+
+
+def _generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     if mapper == MAPPER_E0:
         return _generate_e0(seed, cart)
     sc = mapper in MAPPER_SC_BASE
@@ -1106,9 +1132,9 @@ def _generate_e0(seed: int, cart: int) -> bytes:
     return b"".join(slices[k] for k in range(8))
 
 
-def config_carts(seed: int, mappers) -> list:
+def config_carts(seed: int, mappers, full_tia: bool = False) -> list:
     """ROM images for a list of mappers, cart index = position."""
-    return [generate_cart(seed, i, m) for i, m in enumerate(mappers)]
+    return [generate_cart(seed, i, m, full_tia) for i, m in enumerate(mappers)]
 
 
 MIX16 = [MAPPER_2K] * 6 + [MAPPER_4K] * 6 + [MAPPER_F8] * 4

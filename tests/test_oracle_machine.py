@@ -573,3 +573,159 @@ def test_e0_carts_map_several_slices():
     assert c["watchdog"] == 0 and o.state()[28] == 0
     assert 1500 < c["instructions"] / c["frames"] < 4000
     assert {0, 1} <= seen[0] and {2, 3, 4} <= seen[1] and {5, 6} <= seen[2]
+
+
+# ---------------------------------------------------------------------------
+# the rest of the TIA: player 1, missiles, ball, sizes, delays, collisions
+# (expected pixels worked out by hand from the register definitions)
+# ---------------------------------------------------------------------------
+
+T = dict(NUSIZ0=0x04, NUSIZ1=0x05, COLUP0=0x06, COLUP1=0x07, COLUPF=0x08, COLUBK=0x09, CTRLPF=0x0A,
+         REFP0=0x0B, REFP1=0x0C, PF0=0x0D, PF1=0x0E, PF2=0x0F, RESP0=0x10, RESP1=0x11, RESM0=0x12,
+         RESM1=0x13, RESBL=0x14, GRP0=0x1B, GRP1=0x1C, ENAM0=0x1D, ENAM1=0x1E, ENABL=0x1F, HMP0=0x20,
+         HMP1=0x21, HMM0=0x22, HMM1=0x23, HMBL=0x24, VDELP0=0x25, VDELP1=0x26, VDELBL=0x27, RESMP0=0x28,
+         RESMP1=0x29, HMOVE=0x2A, HMCLR=0x2B, CXCLR=0x2C)
+
+
+def _frame_setup(a, writes):
+    """One scanline per register write, each stored right after WSYNC (line
+    clock 15, inside HBLANK: RESPx -> 3, RESMx / RESBL -> 2); value None is
+    a strobe."""
+    for reg, v in writes:
+        a.op("STA", "zp", WSYNC)
+        if v is not None:
+            a.op("LDA", "imm", v)
+        a.op("STA", "zp", T[reg])
+
+
+def _screen_after(writes):
+    """Row 100 of a frame whose first lines make `writes` (then plain
+    lines)."""
+    def build(a):
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", VBLANK)
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", WSYNC)
+        a.op("STA", "zp", VSYNC)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", VSYNC)
+        _frame_setup(a, writes)
+        a.op("LDX", "imm", 200)
+        a.label("LINE")
+        a.op("STA", "zp", WSYNC)
+        a.op("DEX")
+        a.op("BNE", "rel", "LINE")
+        a.op("JMP", "abs", "FRAME")
+    o = oracle.Oracle(rom4k(build), synth.MAPPER_4K, ystart=0)
+    for _ in range(2):
+        _, scr, st = o.step(0, 1)
+    assert st == 0
+    return scr[100]
+
+
+def _lit(row, colour):
+    return sorted(np.where(row == colour)[0].tolist())
+
+
+@pytest.mark.parametrize("refl", [0, 8])
+def test_player1_copies_and_reflection(refl):
+    """GRP1 = %11000001, NUSIZ1 = 3 (three copies 16 apart), RESP1 in HBLANK
+    (position 3): bits 7, 6, 0 at +0, +1, +7 of each copy, or with REFP1 bit 3
+    set (bit k at +k) at +7, +6, +0."""
+    row = _screen_after([("COLUBK", 0x12), ("GRP1", 0xC1), ("NUSIZ1", 3), ("COLUP1", 0x44),
+                         ("REFP1", refl), ("RESP1", None)])
+    rel = (0, 1, 7) if not refl else (7, 6, 0)
+    assert _lit(row, 0x44) == sorted(3 + c + r for c in (0, 16, 32) for r in rel)
+    assert set(row.tolist()) == {0x12, 0x44}
+
+
+@pytest.mark.parametrize("mode,scale", [(5, 2), (7, 4)])
+def test_player_double_and_quad_width(mode, scale):
+    row = _screen_after([("GRP0", 0xC1), ("NUSIZ0", mode), ("COLUP0", 0x44), ("RESP0", None)])
+    assert _lit(row, 0x44) == sorted(3 + b * scale + j for b in (0, 1, 7) for j in range(scale))
+
+
+def test_missiles_ball_widths_copies_and_priority():
+    """M0 4 wide at 2; M1 2 wide, two copies 32 apart (NUSIZ1 mode 2) at 2 and
+    34; the ball 8 wide at 2: M0 > M1 > BL where they overlap."""
+    row = _screen_after([("COLUBK", 0x12), ("COLUP0", 0x44), ("COLUP1", 0x66), ("COLUPF", 0x88),
+                         ("ENAM0", 2), ("NUSIZ0", 0x20), ("ENAM1", 2), ("NUSIZ1", 0x12),
+                         ("ENABL", 2), ("CTRLPF", 0x30), ("RESM0", None), ("RESM1", None), ("RESBL", None)])
+    assert _lit(row, 0x44) == [2, 3, 4, 5]
+    assert _lit(row, 0x66) == [34, 35]
+    assert _lit(row, 0x88) == [6, 7, 8, 9]
+
+
+@pytest.mark.parametrize("ctrl,left,right", [(2, 0x44, 0x66), (6, 0x88, 0x88), (0, 0x88, 0x88)])
+def test_score_mode(ctrl, left, right):
+    """PF1 = $FF covers columns 16..47 and (repeated) 96..127; score mode
+    (CTRLPF bit 1) colours them COLUP0 / COLUP1 by half, unless the
+    playfield has priority (bit 2)."""
+    row = _screen_after([("COLUBK", 0x12), ("COLUP0", 0x44), ("COLUP1", 0x66), ("COLUPF", 0x88),
+                         ("PF1", 0xFF), ("CTRLPF", ctrl)])
+    if left != right:
+        assert _lit(row, left) == list(range(16, 48)) and _lit(row, right) == list(range(96, 128))
+    else:
+        assert _lit(row, left) == list(range(16, 48)) + list(range(96, 128))
+
+
+@pytest.mark.parametrize("copy", [False, True])
+def test_vertical_delay(copy):
+    """VDELP0 set: player 0 shows the delayed GRP0, which only a GRP1 write
+    updates (from GRP0)."""
+    writes = [("COLUP0", 0x44), ("VDELP0", 1), ("GRP0", 0xFF)] + ([("GRP1", 0)] if copy else [])
+    row = _screen_after(writes + [("RESP0", None)])
+    assert _lit(row, 0x44) == (list(range(3, 11)) if copy else [])
+
+
+def test_hmove_moves_every_object_and_resmp_locks():
+    """HMOVE moves P1 by -(-1), M0 by -1 and the ball by -2 from their strobe
+    positions 3, 2, 2 (then HMCLR: a second HMOVE moves nothing); a missile
+    locked with RESMP0 is hidden and, once released, sits at its player's
+    position + 3."""
+    row = _screen_after([("COLUBK", 0x12), ("COLUP0", 0x44), ("COLUP1", 0x66), ("COLUPF", 0x88),
+                         ("GRP1", 0x80), ("ENAM0", 2), ("ENABL", 2), ("HMP1", 0xF0), ("HMM0", 0x10),
+                         ("HMBL", 0x20), ("RESP1", None), ("RESM0", None), ("RESBL", None),
+                         ("HMOVE", None), ("HMCLR", None), ("HMOVE", None)])
+    assert _lit(row, 0x66) == [4] and _lit(row, 0x44) == [1] and _lit(row, 0x88) == [0]
+    row = _screen_after([("COLUP0", 0x44), ("ENAM0", 2), ("RESP0", None), ("RESMP0", 2)])
+    assert _lit(row, 0x44) == []
+    row = _screen_after([("COLUP0", 0x44), ("ENAM0", 2), ("RESP0", None), ("RESMP0", 2), ("RESMP0", 0)])
+    assert _lit(row, 0x44) == [6]
+
+
+def test_collision_latches():
+    """Each frame reads CXP0FB, CXPPMM, CXM0P into RAM, then CXCLR; every
+    line P0 (columns 3..10) overlaps PF0 (0..15) and M0 overlaps M1 (both 1
+    wide at 2, off the player): D7 of CXP0FB, D6 of CXPPMM, nothing in
+    CXM0P.  Without the playfield, CXP0FB stays clear."""
+    def run(pf0):
+        def build(a):
+            a.label("FRAME")
+            a.op("LDA", "imm", 2)
+            a.op("STA", "zp", WSYNC)
+            a.op("STA", "zp", VSYNC)
+            a.op("LDA", "imm", 0)
+            a.op("STA", "zp", VSYNC)
+            for reg, dst in ((0x02, 0x80), (0x07, 0x81), (0x00, 0x82)):
+                a.op("LDA", "zp", reg)
+                a.op("STA", "zp", dst)
+            a.op("STA", "zp", T["CXCLR"])
+            a.op("LDX", "imm", 230)
+            a.label("LINE")
+            a.op("STA", "zp", WSYNC)
+            for reg in ("RESP0", "RESM0", "RESM1"):   # strobes first, inside HBLANK: 3, 2, 2
+                a.op("STA", "zp", T[reg])
+            for reg, v in (("GRP0", 0xFF), ("PF0", pf0), ("ENAM0", 2), ("ENAM1", 2)):
+                a.op("LDA", "imm", v)
+                a.op("STA", "zp", T[reg])
+            a.op("DEX")
+            a.op("BNE", "rel", "LINE")
+            a.op("JMP", "abs", "FRAME")
+        o = oracle.Oracle(rom4k(build), synth.MAPPER_4K)
+        for _ in range(3):
+            o.step(0, 1)
+        return list(o.ram()[:3])
+    assert run(0xF0) == [0x80, 0x40, 0x00]
+    assert run(0x00) == [0x00, 0x40, 0x00]

@@ -309,3 +309,50 @@ def test_e0_read_is_relaxed_within_its_slice():
     want = np.zeros(8192)
     want[3 * 1024:3 * 1024 + len(w)] = w / w.sum()
     assert np.allclose(g_rom, want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("score", [False, True])
+def test_colup1_owns_player1_and_score_pixels(score):
+    """LDA #k; STA COLUP1 with GRP1 = $FF, NUSIZ1 = 7 (quad width: 32
+    columns) and no playfield: 32 x 210 COLUP1-owned pixels per frame; in
+    score mode with PF2 = $FF (columns 48..79, repeated at 128..159) the
+    right half's 32 columns are COLUP1's too, and the left half's COLUP0's."""
+    def build(a):
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x01)
+        a.op("LDA", "imm", 0xFF)
+        a.op("STA", "zp", 0x1C)                 # GRP1
+        a.op("LDA", "imm", 7)
+        a.op("STA", "zp", 0x05)                 # NUSIZ1: quad width
+        if score:
+            a.op("LDA", "imm", 0xFF)
+            a.op("STA", "zp", 0x0F)             # PF2
+            a.op("LDA", "imm", 2)
+            a.op("STA", "zp", 0x0A)             # CTRLPF: score mode
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x11)                 # RESP1 in HBLANK: position 3
+        a.label("IMM")
+        a.op("LDA", "imm", 0x57)
+        a.op("STA", "zp", 0x07)                 # COLUP1
+        a.op("LDX", "imm", 0)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("DEX")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "FRAME")
+        imm.append(a.labels["IMM"] + 1 - 0xF000)
+    imm = []
+    rom = rom4k(build)
+    o = oracle.Oracle(rom, synth.MAPPER_4K)
+    n = 4
+    g, _, scr = o.soft_rollout(np.zeros((n, 5)), 1, 0.01, 6.0, None, np.ones((n, 210, 160)))
+    per_frame = 210 * (32 + (32 if score else 0))
+    assert (scr[1:] == 0x56).sum() == 3 * per_frame
+    g_rom, _, _ = g.reverse()
+    assert g_rom[imm[0]] == pytest.approx(3 * per_frame, rel=1e-12)
