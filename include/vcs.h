@@ -136,6 +136,18 @@ typedef struct vcs_config {
                                more segments per group, more parallel
                                recompute.  vcs_backward_static uses its fixed
                                array instead. */
+  int32_t full_tia;         /* 1 = the whole TIA (Section 2.2): player 1, the
+                               missiles and the ball (NUSIZ copies and sizes,
+                               REFP, VDEL, RESMP, HMOVE of every object),
+                               score mode and collision latches (CXCLR; read
+                               in D7 / D6 of CXM0P .. CXPPMM), COLUP1 as a
+                               fourth differentiable colour; 0 (default) = the
+                               subset machine: player 0, playfield and
+                               background, the other object registers
+                               ignored and the collision registers read 0.
+                               The subset runs in kernels without the rest
+                               (about a quarter faster on the synthetic
+                               carts). */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

@@ -77,6 +77,7 @@ def lib():
         L.ogrf_nodes.argtypes = [vp]
         L.ovcs_set_switches.argtypes = [vp, C.c_uint8]
         L.ovcs_set_sampler.argtypes = [vp, C.c_int]
+        L.ovcs_set_full_tia.argtypes = [vp, C.c_int]
         L.ovcs_set_step_instructions.argtypes = [vp, C.c_int]
         L.ovcs_set_full.argtypes = [vp, C.c_int, C.c_double, C.c_double]
         L.ovcs_digest.restype = C.c_uint64
@@ -147,12 +148,13 @@ class SoftGraph:
 class Oracle:
     """One emulated VCS (hard mode, optional soft rollouts)."""
 
-    def __init__(self, rom: bytes, mapper: int, ystart: int = 34):
+    def __init__(self, rom: bytes, mapper: int, ystart: int = 34, full_tia: bool = False):
         self.rom = np.frombuffer(bytes(rom), dtype=np.uint8).copy()
         self.mapper = mapper
         self.h = lib().ovcs_new(_p(self.rom, C.c_uint8), len(self.rom), mapper, ystart)
         if not self.h:
             raise ValueError("bad ROM size for mapper")
+        lib().ovcs_set_full_tia(self.h, 1 if full_tia else 0)
 
     def __del__(self):
         if getattr(self, "h", None):

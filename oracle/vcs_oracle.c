@@ -133,6 +133,8 @@ struct ovcs {
   uint8_t hmp1, hmm[2], hmbl, vdelp[2], vdelbl, resmp[2];
   int p1pos, mpos[2], blpos;
   uint16_t cx;             /* collision latches: bit 2 r + 1 = D7 and bit 2 r = D6 of read register r */
+  int full_tia;            /* 1: the whole TIA; 0: the subset machine (player 0, playfield,
+                            * background; other object registers ignored, collisions read 0) */
   int hclk, line;
   int hmove_line;
   int wsync;
@@ -306,6 +308,7 @@ static int ball_bit(const ovcs* s, int x) {
  * the left half and COLUP1 in the right one in score mode (bit 1); bit 2
  * set: PF/BL > P0/M0 > P1/M1 > BK. */
 static int owner_of(const ovcs* s, int x, int p0, int m0, int p1, int m1, int pf, int bl) {
+  if (!s->full_tia && !(s->ctrlpf & 4)) return p0 ? 0 : (pf ? 1 : 2);   /* no score mode in the subset */
   if (s->ctrlpf & 4) {
     if (pf || bl) return 1;
     if (p0 || m0) return 0;
@@ -331,6 +334,14 @@ static void collide(ovcs* s, int x) {
                         m0 && bl, m0 && pf, m1 && bl, m1 && pf, 0, bl && pf, m0 && m1, p0 && p1};
   for (int k = 0; k < 16; k++)
     if (pair[k]) s->cx |= (uint16_t)(1u << k);
+}
+
+/* Registers only the whole TIA has (the subset machine ignores writes to
+ * them): NUSIZ0/1, COLUP1, REFP0/1, RESP1, RESM0/1, RESBL, GRP1, ENAM0/1,
+ * ENABL, HMP1, HMM0/1, HMBL, VDELP0/1, VDELBL, RESMP0/1, CXCLR. */
+static int full_tia_reg(int reg) {
+  return reg == 0x04 || reg == 0x05 || reg == 0x07 || reg == 0x0B || reg == 0x0C || (reg >= 0x11 && reg <= 0x14) ||
+         (reg >= 0x1C && reg <= 0x1F) || (reg >= 0x21 && reg <= 0x29) || reg == 0x2C;
 }
 
 /* Differentiable position sampler (Section 3, the sub-pixel bilinear kernel
@@ -369,7 +380,7 @@ static uint8_t pixel(const ovcs* s, int x, int* owner) {
 static void tia_clock(ovcs* s) {
   if (s->hclk >= 68) {
     int x = s->hclk - 68, row = s->line - s->ystart;
-    collide(s, x);
+    if (s->full_tia) collide(s, x);
     if (row >= 0 && row < SCR_H) {
       int owner;
       s->fb[row * SCR_W + x] = pixel(s, x, &owner);
@@ -395,6 +406,7 @@ static void lock_missiles(ovcs* s) {
 static void tia_write(ovcs* s, int reg, val x) {
   uint8_t v = x.v;
   s->cnt.tia_writes++;
+  if (!s->full_tia && full_tia_reg(reg)) return;
   switch (reg) {
     case 0x00:
       if (!(s->vsync & 2) && (v & 2)) frame_end(s);
@@ -441,7 +453,7 @@ static void tia_write(ovcs* s, int reg, val x) {
     case 0x27: s->vdelbl = v; break;
     case 0x28: s->resmp[0] = v; lock_missiles(s); break;
     case 0x29: s->resmp[1] = v; lock_missiles(s); break;
-    case 0x2A: {   /* HMOVE: every object moves by minus its signed motion nibble */
+    case 0x2A: {   /* HMOVE: every object moves by minus its signed motion nibble (the subset: player 0) */
       int m = ((int8_t)s->hmp0) >> 4;
       s->p0pos = ((s->p0pos - m) % 160 + 160) % 160;
       /* the motion is minus the high nibble of HMP0: a deviation of HMP0
@@ -1164,6 +1176,7 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
 
 void ovcs_set_switches(ovcs* s, uint8_t swchb) { s->swchb = swchb; }
 void ovcs_set_sampler(ovcs* s, int on) { s->sampler = on != 0; }
+void ovcs_set_full_tia(ovcs* s, int on) { s->full_tia = on != 0; }
 void ovcs_set_step_instructions(ovcs* s, int n) { s->step_instr = n > 0 ? n : 0; }
 
 static int half_width(double tau);

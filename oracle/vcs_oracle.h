@@ -97,6 +97,11 @@ void ovcs_get_counters(const ovcs* s, ovcs_counters* out);
 /* Machine state as 32 words (layout in the .c file). */
 void ovcs_get_state(const ovcs* s, uint32_t* out64);   /* registers, clocks, TIA (64 words) */
 void ovcs_get_ram(const ovcs* s, uint8_t* out128);
+/* on = 1: the whole TIA (player 1, missiles, ball, NUSIZ, REFP, VDEL,
+ * RESMP, score mode, collisions); 0 (default): the subset machine (player
+ * 0, playfield, background; the other object registers ignored, the
+ * collision registers read 0). */
+void ovcs_set_full_tia(ovcs* s, int on);
 void ovcs_get_cart_ram(const ovcs* s, uint8_t* out128);   /* Superchip RAM (zero otherwise) */
 /* Run n instructions, recording per instruction: pc, opcode, A, X, Y, SP,
  * P, cycle (low 32 bits), scanline, line clock.  Returns instructions run. */

@@ -60,6 +60,7 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.cart_banks = b->cart_banks;
   p.ram_words = b->ram_words;
   p.xmap = b->xmap;
+  p.full_tia = b->cfg.full_tia;
   p.rom_stride = b->rom_stride;
   p.dt = b->dt;
   p.ystart = b->cfg.ystart;
@@ -195,6 +196,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->position_sampler = 0;
   cfg->step_instructions = 0;
   cfg->tape_budget_mb = 0;
+  cfg->full_tia = 0;
   return VCS_OK;
 }
 
@@ -326,6 +328,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
       (b->cfg.step_instructions > 0 && b->cfg.boot_noop_frames + b->cfg.boot_reset_frames > 0)) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "step_instructions must be >= 0, and 0 with boot frames");
+  }
+  if (b->cfg.full_tia < 0 || b->cfg.full_tia > 1) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "full_tia must be 0 or 1");
   }
   if (b->cfg.position_sampler < 0 || b->cfg.position_sampler > 1) {
     free_batch(b);

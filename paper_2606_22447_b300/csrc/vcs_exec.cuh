@@ -17,9 +17,11 @@
 // writes that can follow a VSYNC write in one instruction land on TIA
 // register $3F or in RAM, neither of which is drawn.
 #pragma once
+#include <initializer_list>
 #include <type_traits>
 
 #include "vcs_machine.cuh"
+#include "vcs_tia.cuh"
 
 namespace vcs {
 
@@ -33,15 +35,42 @@ struct Step {
   int32_t instr_left;  // instruction-granular steps: slots left in the step
 };
 
-// TIA write registers whose value changes the picture.
-constexpr uint64_t kVisualRegs = (1ull << 0x01) | (1ull << 0x06) | (1ull << 0x08) | (1ull << 0x09) |
-                                 (1ull << 0x0A) | (1ull << 0x0D) | (1ull << 0x0E) | (1ull << 0x0F) |
-                                 (1ull << 0x10) | (1ull << 0x1B) | (1ull << 0x2A);
+constexpr uint64_t reg_bits(std::initializer_list<int> regs) {
+  uint64_t m = 0;
+  for (int r : regs) m |= 1ull << r;
+  return m;
+}
+
+// TIA write registers whose value changes the picture: of the subset
+// machine, and of the whole TIA.
+constexpr uint64_t kVisualSubset = reg_bits({0x01, 0x06, 0x08, 0x09, 0x0A, 0x0D, 0x0E, 0x0F, 0x10, 0x1B, 0x2A});
+constexpr uint64_t kVisualRegs = reg_bits({0x01, 0x04, 0x05, 0x06, 0x07, 0x08, 0x09, 0x0A, 0x0B, 0x0C, 0x0D, 0x0E,
+                                           0x0F, 0x10, 0x11, 0x12, 0x13, 0x14, 0x1B, 0x1C, 0x1D, 0x1E, 0x1F, 0x25,
+                                           0x26, 0x27, 0x28, 0x29, 0x2A});
+
+// TIA write registers that can change which objects overlap (collisions
+// are evaluated up to such a write first).
+constexpr uint64_t kObjRegs = reg_bits({0x04, 0x05, 0x0A, 0x0B, 0x0C, 0x0D, 0x0E, 0x0F, 0x10, 0x11, 0x12, 0x13,
+                                        0x14, 0x1B, 0x1C, 0x1D, 0x1E, 0x1F, 0x25, 0x26, 0x27, 0x28, 0x29, 0x2A});
+
+// Registers kept only in the cold words (vcs_tia.cuh), and the hot ones
+// whose write may also touch them (GRP0's vertical-delay copy, HMOVE and
+// RESP0 for moved or locked cold objects, HMCLR).
+constexpr uint64_t kColdRegs = reg_bits({0x04, 0x05, 0x07, 0x0B, 0x0C, 0x11, 0x12, 0x13, 0x14, 0x1C, 0x1D, 0x1E,
+                                         0x1F, 0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x28, 0x29, 0x2C});
+constexpr uint64_t kColdMaybe = reg_bits({0x10, 0x1B, 0x2A, 0x2B});
 
 // TIA write registers whose write opens a new version of a differentiable
-// quantity (the soft path's tapes): the three colour registers, and player
+// quantity (the soft path's tapes): the four colour registers, and player
 // 0's position (RESP0, HMOVE) for the position sampler.
-constexpr uint64_t kVersionRegs = (1ull << 0x06) | (1ull << 0x08) | (1ull << 0x09) | (1ull << 0x10) | (1ull << 0x2A);
+constexpr uint64_t kVersionRegs = reg_bits({0x06, 0x07, 0x08, 0x09, 0x10, 0x2A});
+
+// A write to a cold register (or a hot one with cold effects) at line clock
+// h: updates the cold words at tx (stride E) and returns the new summary
+// bits and collision word (x: Regs::xo, y: Regs::cx).  Out of line and
+// called with plain values, so the interpreter's registers stay registers.
+static __device__ __noinline__ uint2 tia_write_cold(uint32_t* tx, uint32_t E, uint32_t reg, uint32_t v, uint32_t h,
+                                             uint32_t grp0, uint32_t pos0, uint32_t cx);
 
 // A TIA register write at frame cycle fcw.  A write that changes the picture
 // first draws the pending span with the old registers.  The register update
@@ -50,7 +79,8 @@ constexpr uint64_t kVersionRegs = (1ull << 0x06) | (1ull << 0x08) | (1ull << 0x0
 template <class Tape>
 __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t reg,
                                           uint32_t v, int32_t fcw) {
-  if (((kVisualRegs >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
+  if ((((c.ft ? kVisualRegs : kVisualSubset) >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
+  if (c.ft && ((kObjRegs >> reg) & 1)) cx_catchup(c, r, 3 * fcw);
   tape.version_write(reg);
   const uint32_t line = div76((uint32_t)fcw);
   const uint32_t m = (uint32_t)fcw - 76u * line;   // CPU cycle within the line
@@ -75,6 +105,78 @@ __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Ste
   r.pos = reg == 0x10 ? resp : (reg == 0x2A ? hmov : r.pos);
   r.hml = (reg == 0x2A && h <= 9) ? (int32_t)line : r.hml;
   r.hmp0 = reg == 0x20 ? v : (reg == 0x2B ? 0u : r.hmp0);
+  if (!c.ft) return;   // the subset machine ignores the rest of the TIA
+  if ((kObjRegs >> reg) & 1) mirror_hot(c, r);
+  if (((kColdRegs >> reg) & 1) || (((kColdMaybe >> reg) & 1) && (r.xo & (kXoG1 | kXoMove | kXoLock)))) {
+    const uint2 o = tia_write_cold(c.tx, c.E, reg, v, h, r.grp0, r.pos, r.cx);
+    r.xo = o.x;
+    r.cx = o.y;
+    if (reg == 0x2C) r.cxc = 3 * fcw;   // CXCLR: nothing before the clear counts
+  }
+}
+
+// Missiles locked to their players (RESMP bit 1): at the player's position
+// + 4 x its width - 1.
+__device__ __forceinline__ void relock(uint32_t pos0, uint32_t& w3, uint32_t w0) {
+  if (w0 & kW0Resmp0) {
+    const uint32_t p = (pos0 + 4u * player_scale((w0 >> 8) & 7) - 1u) % 160u;
+    w3 = (w3 & ~0xFF00u) | (p << 8);
+  }
+  if (w0 & kW0Resmp1) {
+    const uint32_t p = ((w3 & 0xFF) + 4u * player_scale((w0 >> 16) & 7) - 1u) % 160u;
+    w3 = (w3 & ~0xFF0000u) | (p << 16);
+  }
+}
+
+static __device__ __noinline__ uint2 tia_write_cold(uint32_t* tx, uint32_t E, uint32_t reg, uint32_t v, uint32_t h,
+                                             uint32_t grp0, uint32_t pos0, uint32_t cx) {
+  uint32_t w0 = tx[0], w1 = tx[E], w2 = tx[2 * E], w3 = tx[3 * E];
+  auto set = [](uint32_t& w, uint32_t shift, uint32_t mask, uint32_t x) { w = (w & ~(mask << shift)) | ((x & mask) << shift); };
+  auto flag = [](uint32_t& w, uint32_t bit, bool on) { w = on ? (w | bit) : (w & ~bit); };
+  const uint32_t resp = h < 68 ? 3u : (h - 68u + 5u) % 160u, resm = h < 68 ? 2u : (h - 68u + 4u) % 160u;
+  auto moved = [](uint32_t p, uint32_t hm) { return (uint32_t)(((int32_t)p - (((int32_t)(int8_t)(uint8_t)hm) >> 4) + 160) % 160); };
+  switch (reg) {
+    case 0x04: set(w0, 8, 0xFF, v); break;                           // NUSIZ0
+    case 0x05: set(w0, 16, 0xFF, v); break;                          // NUSIZ1
+    case 0x07: set(w0, 0, 0xFF, v); break;                           // COLUP1
+    case 0x0B: flag(w0, kW0Refp0, v & 8); break;                     // REFP0
+    case 0x0C: flag(w0, kW0Refp1, v & 8); break;                     // REFP1
+    case 0x11: set(w3, 0, 0xFF, resp); break;                        // RESP1
+    case 0x12: set(w3, 8, 0xFF, resm); break;                        // RESM0
+    case 0x13: set(w3, 16, 0xFF, resm); break;                       // RESM1
+    case 0x14: set(w3, 24, 0xFF, resm); break;                       // RESBL
+    case 0x1B: set(w1, 16, 0xFF, w1 & 0xFF); break;                  // GRP0: delayed GRP1 <- GRP1
+    case 0x1C:                                                       // GRP1: delayed GRP0 <- GRP0, delayed ENABL <- ENABL
+      set(w1, 0, 0xFF, v);
+      set(w1, 8, 0xFF, grp0);
+      flag(w1, kW1EnablOld, (w1 & kW1Enabl) != 0);
+      break;
+    case 0x1D: flag(w1, kW1Enam0, v & 2); break;                     // ENAM0
+    case 0x1E: flag(w1, kW1Enam1, v & 2); break;                     // ENAM1
+    case 0x1F: flag(w1, kW1Enabl, v & 2); break;                     // ENABL
+    case 0x21: set(w2, 0, 0xFF, v); break;                           // HMP1
+    case 0x22: set(w2, 8, 0xFF, v); break;                           // HMM0
+    case 0x23: set(w2, 16, 0xFF, v); break;                          // HMM1
+    case 0x24: set(w2, 24, 0xFF, v); break;                          // HMBL
+    case 0x25: flag(w0, kW0Vdelp0, v & 1); break;                    // VDELP0
+    case 0x26: flag(w0, kW0Vdelp1, v & 1); break;                    // VDELP1
+    case 0x27: flag(w0, kW0Vdelbl, v & 1); break;                    // VDELBL
+    case 0x28: flag(w0, kW0Resmp0, v & 2); break;                    // RESMP0
+    case 0x29: flag(w0, kW0Resmp1, v & 2); break;                    // RESMP1
+    case 0x2A:                                                       // HMOVE: the cold objects move too
+      w3 = moved(w3 & 0xFF, w2) | (moved((w3 >> 8) & 0xFF, w2 >> 8) << 8) |
+           (moved((w3 >> 16) & 0xFF, w2 >> 16) << 16) | (moved(w3 >> 24, w2 >> 24) << 24);
+      break;
+    case 0x2B: w2 = 0; break;                                        // HMCLR
+    case 0x2C: cx &= 0xFFFF0000u; break;                            // CXCLR
+    default: break;
+  }
+  relock(pos0, w3, w0);
+  tx[0] = w0;
+  tx[E] = w1;
+  tx[2 * E] = w2;
+  tx[3 * E] = w3;
+  return cold_summary_of(w0, w1, w2, cx);
 }
 
 // Fully relaxed casts (FM template argument of the interpreter): 0 = the
@@ -136,7 +238,8 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
   const uint32_t vrom = c.rom[rom_off(c, r, a)];
   const uint32_t vram = ram_rd(c, a);
   const uint32_t q = a & 0xF;
-  const uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
+  uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
+  if (c.ft && !(a & 0x1080) && q < 8) vtia = cx_read(c, r, q, 3 * (r.fc + idx + st.stall));   // a collision latch
   const uint32_t q3 = a & 3;
   const uint32_t vio = q3 == 0 ? r.swcha : (q3 == 2 ? 0x0Bu ^ (r.inpt4 >> 8) : 0u);
   const uint32_t k = r.cyc + (uint32_t)(idx + st.stall) - r.tw;
@@ -156,13 +259,15 @@ __device__ __forceinline__ uint32_t bus_read(const Ctx& c, Regs& r, const Step& 
   return (a & 0x1000) ? vcart : !(a & 0x80) ? vtia : !(a & 0x200) ? vram : !(a & 4) ? vio : vtim;
 }
 
-// A read inside page zero or one (zero-page modes, the stack): RAM or the
-// TIA read registers, no side effects.
+// A read inside page zero or one (zero-page modes, the stack) at cycle idx
+// of the instruction: RAM or the TIA read registers (a collision latch is
+// brought up to that cycle first), no other side effects.
 template <int FM = 0>
-__device__ __forceinline__ uint32_t zp_read(const Ctx& c, Regs& r, uint32_t a) {
+__device__ __forceinline__ uint32_t zp_read(const Ctx& c, Regs& r, const Step& st, uint32_t a, int idx) {
   const uint32_t vram = ram_rd(c, a);
   const uint32_t q = a & 0xF;
-  const uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
+  uint32_t vtia = q == 0xC ? (r.inpt4 & 0xFF) : (q == 0xD ? 0x80u : 0u);
+  if (c.ft && !(a & 0x80) && q < 8) vtia = cx_read(c, r, q, 3 * (r.fc + idx + st.stall));
   if constexpr (FM >= 1) {
     if (a & 0x80) return cast_read<FM>(r, vram, ram_relaxed(c, a));
   }
@@ -253,9 +358,9 @@ __device__ __forceinline__ uint32_t do_shift(Regs& r, uint32_t k, uint32_t v) {
 }
 
 template <int FM = 0>
-__device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r) {
+__device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r, const Step& st, int idx) {
   r.SP = (r.SP + 1) & 0xFF;
-  return zp_read<FM>(c, r, 0x100u | r.SP);
+  return zp_read<FM>(c, r, st, 0x100u | r.SP, idx);
 }
 
 // Tape hook: called for each executed instruction the backward sweep acts on
@@ -266,7 +371,7 @@ struct NoTape {
   static constexpr bool sampler = false;
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) {}
   __device__ __forceinline__ void version_write(uint32_t) {}
-  __device__ __forceinline__ void pixels(float, float, float, float) {}
+  __device__ __forceinline__ void pixels(float, float, float, float, float) {}
 };
 
 // Instruction length of each addressing mode, two bits per mode.
@@ -382,9 +487,9 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     cross = ((base ^ ea) & 0xFF00) != 0;
   } else if constexpr (mode == AM_INX) {
     const uint32_t q = (b1 + r.X) & 0xFF;
-    ea = zp_read<FM>(c, r, q) | (zp_read<FM>(c, r, (q + 1) & 0xFF) << 8);
+    ea = zp_read<FM>(c, r, st, q, 4) | (zp_read<FM>(c, r, st, (q + 1) & 0xFF, 5) << 8);
   } else if constexpr (mode == AM_INY) {
-    const uint32_t base = zp_read<FM>(c, r, b1) | (zp_read<FM>(c, r, (b1 + 1) & 0xFF) << 8);
+    const uint32_t base = zp_read<FM>(c, r, st, b1, 3) | (zp_read<FM>(c, r, st, (b1 + 1) & 0xFF, 4) << 8);
     ea = (base + r.Y) & 0xFFFF;
     cross = ((base ^ ea) & 0xFF00) != 0;
   }
@@ -397,11 +502,11 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
       m = b1;
     } else {
       n += cross ? 1u : 0u;
-      if constexpr (page_zero_mode<mode>()) m = zp_read<FM>(c, r, ea);
+      if constexpr (page_zero_mode<mode>()) m = zp_read<FM>(c, r, st, ea, (int)n);
       else m = bus_read<FM>(c, r, st, ea, (int)n);
     }
   } else if constexpr (cls == CL_RMW) {
-    if constexpr (page_zero_mode<mode>()) m = zp_read<FM>(c, r, ea);
+    if constexpr (page_zero_mode<mode>()) m = zp_read<FM>(c, r, st, ea, (int)n - 2);
     else m = bus_read<FM>(c, r, st, ea, (int)n - 2);
   }
   p.tref = ea;
@@ -485,14 +590,14 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     p.nw = 2; p.wstack = true; p.wv = (ret >> 8) | ((ret & 0xFF) << 8); p.widx = 4;
   }
   else if constexpr (id == OP_RTS) {
-    const uint32_t lo = pull<FM>(c, r);
-    const uint32_t hi = pull<FM>(c, r);
+    const uint32_t lo = pull<FM>(c, r, st, 4);
+    const uint32_t hi = pull<FM>(c, r, st, 5);
     r.PC = ((lo | (hi << 8)) + 1) & 0xFFFF;
   }
   else if constexpr (id == OP_RTI) {
-    const uint32_t pp = pull<FM>(c, r);
-    const uint32_t lo = pull<FM>(c, r);
-    const uint32_t hi = pull<FM>(c, r);
+    const uint32_t pp = pull<FM>(c, r, st, 4);
+    const uint32_t lo = pull<FM>(c, r, st, 5);
+    const uint32_t hi = pull<FM>(c, r, st, 6);
     unpack_p(r, pp | 0x30);
     r.PC = lo | (hi << 8);
   }
@@ -507,11 +612,11 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
   else if constexpr (id == OP_PHA) { p.nw = 1; p.wstack = true; p.wv = r.A; p.widx = 3; }
   else if constexpr (id == OP_PHP) { p.nw = 1; p.wstack = true; p.wv = pack_p(r); p.widx = 3; }
   else if constexpr (id == OP_PLA) {
-    r.A = pull<FM>(c, r);
+    r.A = pull<FM>(c, r, st, 4);
     set_nz(r, r.A);
     p.tref = 0x100u | r.SP;
   }
-  else if constexpr (id == OP_PLP) { unpack_p(r, pull<FM>(c, r) | 0x30); }
+  else if constexpr (id == OP_PLP) { unpack_p(r, pull<FM>(c, r, st, 4) | 0x30); }
   else if constexpr (id == OP_CLC) { r.fC = 0; }
   else if constexpr (id == OP_SEC) { r.fC = 1; }
   else if constexpr (id == OP_CLI) { r.fI = 0; }
@@ -572,7 +677,8 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
     ea = (b1 + idx) & 0xFF;
   } else if (mode == AM_INX || mode == AM_INY) {
     const uint32_t q = mode == AM_INX ? (b1 + r.X) & 0xFF : b1;
-    const uint32_t base = zp_read<FM>(c, r, q) | (zp_read<FM>(c, r, (q + 1) & 0xFF) << 8);
+    const int i0 = mode == AM_INX ? 4 : 3;   // the pointer's cycles
+    const uint32_t base = zp_read<FM>(c, r, st, q, i0) | (zp_read<FM>(c, r, st, (q + 1) & 0xFF, i0 + 1) << 8);
     ea = (base + (mode == AM_INY ? r.Y : 0u)) & 0xFFFF;
     cross = mode == AM_INY && ((base ^ ea) & 0xFF00) != 0;
   } else {
@@ -582,7 +688,7 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
   }
   if (mode != AM_IMM && mode != AM_IMP && id != OP_SAX) n += cross ? 1u : 0u;   // reads pay the page cross
   if (id == OP_LAX) {   // the data read on the last cycle
-    const uint32_t m = (mode == AM_ZP || mode == AM_ZPY) ? zp_read<FM>(c, r, ea) : bus_read<FM>(c, r, st, ea, (int)n);
+    const uint32_t m = (mode == AM_ZP || mode == AM_ZPY) ? zp_read<FM>(c, r, st, ea, (int)n) : bus_read<FM>(c, r, st, ea, (int)n);
     r.A = m;
     r.X = m;
     set_nz(r, m);
@@ -593,7 +699,7 @@ __device__ __forceinline__ void exec_extra(const Ctx& c, Regs& r, Step& st, uint
     if constexpr (FM >= 1) (void)bus_read<FM>(c, r, st, ea, (int)n);   // the read is a cast to count
     else hotspot(c, r, ea & 0x1FFF);
   } else if (FM >= 1 && (mode == AM_ZP || mode == AM_ZPX)) {
-    (void)zp_read<FM>(c, r, ea);
+    (void)zp_read<FM>(c, r, st, ea, (int)n);
   }
   p.widx = n;
   p.rec = id == OP_LAX || id == OP_SAX;   // reverse_needed of these bytes

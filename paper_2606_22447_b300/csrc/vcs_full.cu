@@ -31,6 +31,7 @@ struct FullDivParams {
   const uint8_t* roms;
   const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC | kCartE0)
   int32_t ram_words;          // RAM words per env in shared memory (32 or 64)
+  int32_t full_tia;           // the whole TIA, or the subset machine
   const uint8_t* cart_2k;
   uint32_t rom_stride;
   const DecodeTables* dt;
@@ -44,7 +45,7 @@ struct FullDivParams {
 };
 
 __host__ __device__ constexpr size_t full_smem_bytes(int E, uint32_t rom_stride, int ram_words) {
-  return smem_bytes(E, rom_stride, ram_words) + (size_t)ram_words * 4 * E + sizeof(FullParams);
+  return smem_bytes(E, rom_stride, ram_words) + (size_t)(ram_words + 6) * 4 * E + sizeof(FullParams);
 }
 
 __device__ __forceinline__ bool machines_differ(const Ctx& ch, const Regs& a, const Ctx& cf, const Regs& b) {
@@ -54,6 +55,8 @@ __device__ __forceinline__ bool machines_differ(const Ctx& ch, const Regs& a, co
            a.colbk != b.colbk || a.ctrl != b.ctrl || a.pf0 != b.pf0 || a.pf1 != b.pf1 || a.pf2 != b.pf2 ||
            a.grp0 != b.grp0 || a.hmp0 != b.hmp0 || a.pos != b.pos || a.vblank != b.vblank ||
            a.vsync != b.vsync || a.hml != b.hml;
+  d = d || a.cx != b.cx || a.cxc != b.cxc;
+  for (uint32_t w = 0; w < 4 && !d; w++) d = tx_rd(ch, w) != tx_rd(cf, w);
   const uint32_t* wa = reinterpret_cast<const uint32_t*>(ch.ram);
   const uint32_t* wb = reinterpret_cast<const uint32_t*>(cf.ram);
   for (uint32_t w = 0; w < ch.rw && !d; w++) d = wa[w * ch.E] != wb[w * cf.E];
@@ -77,7 +80,8 @@ __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
   BlockSmem bs = carve_smem(smem, E, p.rom_stride, p.ram_words);
   // the FULL machine's RAM [ram_words][E]
   uint32_t* ram_f = reinterpret_cast<uint32_t*>(smem + smem_bytes(E, p.rom_stride, p.ram_words));
-  FullParams* fp = reinterpret_cast<FullParams*>(ram_f + p.ram_words * E);
+  uint32_t* tx_f = ram_f + p.ram_words * E;   // and its cold TIA words [6][E]
+  FullParams* fp = reinterpret_cast<FullParams*>(tx_f + 6 * E);
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
   const uint32_t cb = p.cart_banks[cart];
@@ -94,13 +98,16 @@ __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
   const int n = p.n_envs;
   // the study is not a hot path: one instantiation serves every batch, the
   // Superchip ports and E0 slices decoded at run time (off for other carts)
-  Ctx ch = make_ctx<true>(bs, E, slot, 0, 1, cb, p.ystart);
+  Ctx ch = make_ctx<true, true>(bs, E, slot, 0, 1, cb, p.ystart);
+  ch.ft = (uint32_t)p.full_tia;   // decided at run time here
   ch.fp = fp;
   Ctx cf = ch;
   cf.ram = reinterpret_cast<uint8_t*>(ram_f + slot);
+  cf.tx = tx_f + slot;
   Regs rh;
   load_env(p.s, n, env, ch, rh);
   for (uint32_t w = 0; w < ch.rw; w++) ram_f[w * E + slot] = reinterpret_cast<const uint32_t*>(ch.ram)[w * E];
+  for (uint32_t w = 0; w < 6; w++) tx_f[w * E + slot] = tx_rd(ch, w);
   set_inputs(rh, p.actions ? p.actions[env] : 0u);
   rh.fr_reads = rh.fr_exact = rh.fr_br = rh.fr_br_exact = 0;
   Regs rf = rh;
@@ -168,6 +175,7 @@ extern "C" vcs_status vcs_full_divergence(vcs_batch* b, float T, float alpha, co
   p.roms = b->roms;
   p.cart_banks = b->cart_banks;
   p.ram_words = b->ram_words;
+  p.full_tia = b->cfg.full_tia;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.dt = b->dt;

@@ -21,9 +21,12 @@ struct SoA {
   uint32_t* t3;    // scanline of the last early HMOVE (int32, -1 = none)
   uint32_t* epf;   // frames elapsed in the current episode
   uint32_t* epi;   // episode index
+  uint32_t* tx;    // the cold TIA words [4][n_envs] (player 1, missiles, ball; vcs_tia.cuh)
+  uint32_t* cx;    // collision latches (16 bits)
+  uint32_t* cxc;   // colour clock (frame coordinates) up to which collisions are evaluated
   uint32_t* ram;   // RAM words [64][n_envs]: RIOT RAM, then the Superchip's RAM (zero for other carts)
 };
-constexpr int kSoAFields = 12;
+constexpr int kSoAFields = 18;
 constexpr int kStateWords = kSoAFields + 64;   // per env
 
 // Per-cart bank byte: the 4 KB banks of a bank-switched cart (2, 4, 8; 0 for
@@ -48,6 +51,7 @@ struct StepParams {
                               // | kCartSC for a Superchip cart | kCartE0 for an E0 cart
   int32_t ram_words;        // RAM words per env in shared memory: 32, or 64 when a cart is Superchip
   int32_t xmap;             // the batch holds Superchip or E0 carts: launch the kernels built for them
+  int32_t full_tia;         // the whole TIA (player 1, missiles, ball, collisions): its own kernels
   uint32_t rom_stride;      // bytes per cart image (8, 16 or 32 KB): also the shared-memory ROM region
   const DecodeTables* dt;
   const uint8_t* actions;   // [n_steps][n_envs] or null (NOOP)
@@ -86,7 +90,8 @@ __host__ __device__ inline SoA soa_at(uint32_t* base, int32_t n_envs) {
   const size_t n = (size_t)n_envs;
   s.reg = base; s.pcp = base + n; s.cyc = base + 2 * n; s.fcs = base + 3 * n; s.tw = base + 4 * n;
   s.tv = base + 5 * n; s.t0 = base + 6 * n; s.t1 = base + 7 * n; s.t2 = base + 8 * n; s.t3 = base + 9 * n;
-  s.epf = base + 10 * n; s.epi = base + 11 * n; s.ram = base + kSoAFields * n;
+  s.epf = base + 10 * n; s.epi = base + 11 * n; s.tx = base + 12 * n; s.cx = base + 16 * n;
+  s.cxc = base + 17 * n; s.ram = base + kSoAFields * n;
   return s;
 }
 
@@ -99,8 +104,12 @@ int launch_digest(const uint8_t* ram, const uint8_t* screen, uint64_t n_digests,
 // (soft = the SOFT-STE forward: float inputs / outputs and checkpoints).
 int launch_step(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_soft_forward(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
-// The same for batches with Superchip or E0 carts (p.xmap).
+// The same for batches with Superchip or E0 carts (p.xmap), and for
+// batches with the whole TIA (p.full_tia; those kernels also take every
+// cartridge format).
 int launch_step_xm(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_soft_forward_xm(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+int launch_step_ft(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
+int launch_soft_forward_ft(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 
 }  // namespace vcs

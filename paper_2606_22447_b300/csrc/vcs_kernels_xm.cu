@@ -10,11 +10,11 @@
 namespace vcs {
 
 int launch_step_xm(const StepParams& p, int n_blocks, int E, void* stream) {
-  return launch_run<false, true>(p, n_blocks, E, stream);
+  return launch_run<false, true, false>(p, n_blocks, E, stream);
 }
 
 int launch_soft_forward_xm(const StepParams& p, int n_blocks, int E, void* stream) {
-  return launch_run<true, true>(p, n_blocks, E, stream);
+  return launch_run<true, true, false>(p, n_blocks, E, stream);
 }
 
 }  // namespace vcs

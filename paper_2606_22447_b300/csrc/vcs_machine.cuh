@@ -203,6 +203,11 @@ struct Regs {
   uint32_t tw, tv, tsh;      // timer: write cycle, value, log2 interval
   uint32_t col0, colpf, colbk, ctrl, pf0, pf1, pf2, grp0, hmp0, pos, vblank, vsync;
   int32_t hml;               // scanline of the last early HMOVE (-1 none)
+  // the rest of the TIA lives in shared memory (vcs_tia.cuh); here only its
+  // summary bits, the collision latches and possible pairs, and the colour
+  // clock up to which collisions have been evaluated
+  uint32_t xo, cx;
+  int32_t cxc;
   uint32_t swcha;
   uint32_t inpt4;            // INPT4 in bits 0-7; bit 8 holds the console RESET switch down
                              // (SWCHB then reads $0A instead of $0B)
@@ -252,6 +257,9 @@ struct Ctx {
   const uint8_t* rom;        // shared: cart image (4 KB, or 8 KB for F8)
   uint8_t* ram;              // shared: this env's RAM byte 0 (stride e4 per word)
   uint32_t* line;            // shared: this env's line-buffer word 0 (stride E)
+  uint32_t* tx;              // shared: this env's cold TIA words (6, stride E; vcs_tia.cuh)
+  uint32_t ft;               // 1: the whole TIA; 0: the subset machine (player 0, playfield,
+                             // background; the other object registers ignored, collisions read 0)
   const DecodeTables* dt;    // shared
   uint32_t e4;               // 4 * envs per block
   uint32_t E;                // envs per block
@@ -356,6 +364,14 @@ __device__ __forceinline__ uint32_t timint_at(const Regs& r, uint32_t t) {
   return k > (r.tv << r.tsh) ? 0x80u : 0u;
 }
 
+}  // namespace vcs
+
+// The rest of the TIA (player 1, missiles, ball, collisions) needs Ctx and
+// Regs above; the span renderer below needs its general path.
+#include "vcs_tia.cuh"
+
+namespace vcs {
+
 // ----------------------------------------------------------------------------
 // TIA rendering (span catch-up)
 // ----------------------------------------------------------------------------
@@ -430,14 +446,27 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
                  cbk = (r.colbk & 0xFE) * 0x01010101u;
   // colour where the player bit is set / clear, over playfield / background
   const bool pf_first = (r.ctrl & 4) != 0;
-  const uint32_t on_pf = pf_first ? cpf : cp0, off_pf = cpf, on_bk = cp0, off_bk = cbk;
+  // score mode (CTRLPF bit 1 without bit 2): the playfield takes COLUP0 in
+  // the left half (groups 0..19) and COLUP1 in the right one
+  const bool score = c.ft && (r.ctrl & 6) == 2;
+  const uint32_t col1 = score ? tx_rd(c, 0) & 0xFF : 0u;
+  const uint32_t cpfL = score ? cp0 : cpf, cpfR = score ? (col1 & 0xFE) * 0x01010101u : cpf;
+  const uint32_t on_pf = pf_first ? cpf : cp0, on_bk = cp0, off_bk = cbk;
   const uint32_t blank_g = (line == r.hml) ? 2u : 0u;
+  // objects beyond player 0 and the playfield (or a copied, sized, reflected
+  // or delayed player 0) take the general path, out of line
+  const bool general = c.ft && (r.xo & kXoGen) != 0;
   if constexpr (Tape::kAcc) {
     // Sum the span's pixel gradients per owning colour register: plain FP32
     // within the span (at most 160 terms), one compensated add per owner per
     // span into the version sums.  A group without player pixels belongs
     // wholly to the playfield or the background colour.
     if (blank_all || !rd.gs) return;
+    if (general) {
+      const OwnerSums s = sums_general(make_view(c, r), rd.grow, c.E, c.rank, c.T, x0, x1, blank_g, tape.sampler);
+      tape.pixels(s.s0, s.s1, s.s2, s.pos, s.s3);
+      return;
+    }
     const float4* gl = rd.grow;   // this line's gradients, staged by render_to
     const uint32_t gs0 = g0 < blank_g ? blank_g : g0;
     // Bulk pass: whole groups inside the span that hold no player pixel
@@ -451,9 +480,12 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       const bool player = grev != 0 && dp < 3u;
       return player || 4 * g < x0 || 4 * g + 4 > x1;
     };
-    float s_p0 = 0.f, s_pf = 0.f, s_bk = 0.f, s_pf2 = 0.f, s_bk2 = 0.f;
+    // s_pf: the playfield (its left half in score mode), s_pfR: the right
+    // half in score mode
+    float s_p0 = 0.f, s_pf = 0.f, s_bk = 0.f, s_pf2 = 0.f, s_bk2 = 0.f, s_pfR = 0.f;
     for (uint32_t ch = first_owned_chunk(c, gs0 >> 2); 4 * ch < g1; ch += c.T) {
       const uint32_t g = 4 * ch;
+      const bool right = score && g >= 20;   // a chunk lies wholly in one half
       float4 q[4];
 #pragma unroll
       for (uint32_t k = 0; k < 4; k++)
@@ -463,7 +495,10 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
         const uint32_t gg = g + k;
         const float t = (gg < gs0 || gg >= g1 || special(gg)) ? 0.f : (q[k].x + q[k].y) + (q[k].z + q[k].w);
         const bool pf = (pfm >> gg) & 1;
-        if (k & 1) {
+        if (right) {
+          s_pfR += pf ? t : 0.f;
+          (k & 1 ? s_bk2 : s_bk) += pf ? 0.f : t;
+        } else if (k & 1) {
           s_pf2 += pf ? t : 0.f;
           s_bk2 += pf ? 0.f : t;
         } else {
@@ -502,7 +537,7 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       }
       const bool pf_wins = pf_first && pf;
       s_p0 += pf_wins ? 0.f : tp;
-      s_pf += (pf ? tn : 0.f) + (pf_wins ? tp : 0.f);
+      (score && g >= 20 ? s_pfR : s_pf) += (pf ? tn : 0.f) + (pf_wins ? tp : 0.f);
       s_bk += pf ? 0.f : tn;
     }
     // Position sampler (Section 3): the player's coverage relaxed with a
@@ -530,11 +565,14 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
         const float4 q = gl[g * c.E];
         const uint32_t k = ux & 3;
         const float w = k == 0 ? q.x : (k == 1 ? q.y : (k == 2 ? q.z : q.w));
-        const int32_t under = (int32_t)((pf ? r.colpf : r.colbk) & 0xFE);
+        const uint32_t cpfx = score ? (ux < 80 ? r.col0 : col1) : r.colpf;   // the playfield's colour here
+        const int32_t under = (int32_t)((pf ? cpfx : r.colbk) & 0xFE);
         s_pos += (0.5f * (float)((bl - br) * (cp - under))) * w;
       }
     }
-    tape.pixels(s_p0, s_pf, s_bk, s_pos);
+    // score mode: the playfield sums belong to COLUP0 (left) and COLUP1 (right)
+    if (score) tape.pixels(s_p0 + s_pf, 0.f, s_bk, s_pos, s_pfR);
+    else tape.pixels(s_p0, s_pf, s_bk, s_pos, 0.f);
   } else {
     // Groups g0 and gl may be partly inside [x0, x1); the ones between are
     // whole words.  Background and playfield first (one select per group,
@@ -560,11 +598,16 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
           if (4 * ch + k > g0 && 4 * ch + k < gl) line[(4 * ch + k) * E] = 0u;
       return;
     }
-    if (owns_chunk(c, g0 >> 2)) put(g0, ((pfm >> g0) & 1) ? cpf : cbk);
-    if (gl > g0 && owns_chunk(c, gl >> 2)) put(gl, ((pfm >> gl) & 1) ? cpf : cbk);
+    if (general) {
+      draw_general(make_view(c, r), c.line, c.E, c.rank, c.T, x0, x1, blank_g);
+      return;
+    }
+    if (owns_chunk(c, g0 >> 2)) put(g0, ((pfm >> g0) & 1) ? (g0 < 20 ? cpfL : cpfR) : cbk);
+    if (gl > g0 && owns_chunk(c, gl >> 2)) put(gl, ((pfm >> gl) & 1) ? (gl < 20 ? cpfL : cpfR) : cbk);
     for (uint32_t ch = first_owned_chunk(c, (g0 + 1) >> 2); 4 * ch < gl; ch += c.T) {
       const uint32_t g = 4 * ch;
       const uint32_t pfs = (uint32_t)(pfm >> g) & 0xF;
+      const uint32_t cpf = g < 20 ? cpfL : cpfR;   // a chunk lies wholly in one half
       if (g > g0 && g + 4 <= gl) {   // the whole chunk is interior
 #pragma unroll
         for (uint32_t k = 0; k < 4; k++) line[(g + k) * E] = ((pfs >> k) & 1) ? cpf : cbk;
@@ -581,7 +624,7 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
         uint32_t g = gp + k;
         g -= g >= 40 ? 40u : 0u;
         if (g >= g0 && g < g1 && owns_chunk(c, g >> 2))
-          put(g, group_pixels(g, pfm, grev, r.pos, on_pf, off_pf, on_bk, off_bk));
+          put(g, group_pixels(g, pfm, grev, r.pos, on_pf, g < 20 ? cpfL : cpfR, on_bk, off_bk));
       }
     }
     for (uint32_t g = g0; g < blank_g && g < g1; g++)

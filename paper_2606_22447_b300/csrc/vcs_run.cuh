@@ -4,6 +4,7 @@
 
 #include "vcs_exec.cuh"
 #include "vcs_kernels.cuh"
+#include "vcs_tia.cuh"
 
 namespace vcs {
 
@@ -15,11 +16,12 @@ struct BlockSmem {
   uint64_t* mbar;       // TMA completion barrier
   uint32_t* ram;        // [ram_words][E] words: RIOT RAM, then the Superchip's RAM
   uint32_t* line;       // [40][E] words
+  uint32_t* tx;         // [6][E] words: the cold TIA registers and the hot copy (vcs_tia.cuh)
 };
 
 // ram_words: 32, or 64 in a batch that holds a Superchip cart.
 __host__ __device__ constexpr size_t smem_bytes(int E, uint32_t rom_bytes, int ram_words) {
-  return rom_bytes + 512 + 16 + (size_t)(ram_words + 40) * 4 * E;
+  return rom_bytes + 512 + 16 + (size_t)(ram_words + 40 + 6) * 4 * E;
 }
 
 __device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E, uint32_t rom_bytes, int ram_words) {
@@ -29,6 +31,7 @@ __device__ __forceinline__ BlockSmem carve_smem(uint8_t* smem, int E, uint32_t r
   b.mbar = reinterpret_cast<uint64_t*>(smem + rom_bytes + 512);
   b.ram = reinterpret_cast<uint32_t*>(smem + rom_bytes + 512 + 16);
   b.line = b.ram + ram_words * E;
+  b.tx = b.line + 40 * E;
   return b;
 }
 
@@ -72,8 +75,8 @@ __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTabl
 // Context of one replica: env slot `slot` of the block (E envs), replica
 // `rank` of T, of a cart whose bank byte is cb (banks | kCartSC | kCartE0).
 // XM: the batch may hold Superchip or E0 carts; without it their ports and
-// slices are compiled out.
-template <bool XM>
+// slices are compiled out.  FT: the whole TIA (compiled out without it).
+template <bool XM, bool FT>
 __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int rank, int T, uint32_t cb,
                                         int32_t ystart) {
   const uint32_t nb = cart_banks_of(cb);
@@ -81,6 +84,7 @@ __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int
   c.rom = b.rom;
   c.ram = reinterpret_cast<uint8_t*>(b.ram + slot);
   c.line = b.line + slot;
+  c.tx = b.tx + slot;
   c.dt = b.dt;
   c.e4 = 4u * (uint32_t)E;
   c.E = (uint32_t)E;
@@ -89,6 +93,7 @@ __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int
   c.sc = XM ? cart_is_sc(cb) : 0u;
   c.e0 = XM ? cart_is_e0(cb) : 0u;
   c.rw = c.sc ? 64u : 32u;
+  c.ft = FT ? 1u : 0u;
   c.ystart = ystart;
   c.rank = (uint32_t)rank;
   c.T = (uint32_t)T;
@@ -119,6 +124,15 @@ __device__ __forceinline__ void load_env(const SoA& s, int n, int e, const Ctx& 
   v = s.t2[e];
   r.hmp0 = v & 0xFF; r.pos = (v >> 8) & 0xFF; r.vblank = (v >> 16) & 0xFF; r.vsync = v >> 24;
   r.hml = (int32_t)s.t3[e];
+  r.xo = r.cx = 0;
+  r.cxc = 0;
+  if (c.ft) {
+    for (uint32_t k = 0; k < 4; k++) tx_wr(c, k, s.tx[(size_t)k * n + e]);
+    r.cx = s.cx[e];
+    r.cxc = (int32_t)s.cxc[e];
+    cold_summary(c, r);
+    mirror_hot(c, r);
+  }
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
   for (uint32_t i = 0; i < c.rw; i++) w[i * c.E] = s.ram[(size_t)i * n + e];
   for (uint32_t q = c.rank; q < 10; q += c.T)
@@ -137,6 +151,11 @@ __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx&
   s.t1[e] = r.pf0 | (r.pf1 << 8) | (r.pf2 << 16) | (r.grp0 << 24);
   s.t2[e] = r.hmp0 | (r.pos << 8) | (r.vblank << 16) | (r.vsync << 24);
   s.t3[e] = (uint32_t)r.hml;
+  if (c.ft) {
+    for (uint32_t k = 0; k < 4; k++) s.tx[(size_t)k * n + e] = tx_rd(c, k);
+    s.cx[e] = r.cx & 0xFFFFu;
+    s.cxc[e] = (uint32_t)r.cxc;
+  }
   const uint32_t* w = reinterpret_cast<const uint32_t*>(c.ram);
   for (uint32_t i = 0; i < c.rw; i++) s.ram[(size_t)i * n + e] = w[i * c.E];
 }
@@ -158,6 +177,13 @@ __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.col0 = r.colpf = r.colbk = r.ctrl = r.pf0 = r.pf1 = r.pf2 = r.grp0 = r.hmp0 = 0;
   r.pos = 0; r.vblank = 0; r.vsync = 0;
   r.hml = -1;
+  r.xo = r.cx = 0;
+  r.cxc = 0;
+  if (c.ft) {
+    for (uint32_t k = 0; k < 4; k++) tx_wr(c, k, 0u);
+    cold_summary(c, r);
+    mirror_hot(c, r);
+  }
   uint32_t* w = reinterpret_cast<uint32_t*>(c.ram);
   for (uint32_t i = 0; i < c.rw; i++) w[i * c.E] = 0;
   r.PC = c.rom[rom_off(c, r, 0x1FFC)] | ((uint32_t)c.rom[rom_off(c, r, 0x1FFD)] << 8);
@@ -195,10 +221,12 @@ __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Ste
     finish_frame(c, r, rd, tape, 3 * fcw);
     rd.on = false;
   }
+  if (c.ft) cx_catchup(c, r, 3 * fcw);   // collisions up to the frame end, then in the new frame's clocks
   st.frames_done++;
   int32_t l = (int32_t)div76((uint32_t)fcw);
   r.fc -= 76 * l;
   r.fs = (uint32_t)(fcw - 76 * l);
+  if (c.ft) r.cxc = 3 * (int32_t)r.fs;
   r.hml = -1;
   if (st.want_screen && st.frames_done == st.frame_skip - 1) {
     rd.on = true;

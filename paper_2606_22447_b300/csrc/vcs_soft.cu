@@ -10,7 +10,7 @@
 //      colour-register version (the stored priority switch);
 //   2. k_soft_sweep, segment by segment from the last, sweeps the tape
 //      backwards (one env per warp), carrying adjoints of A, X, Y, the timer
-//      value, the three colour registers and the 128 RAM cells (256 with a
+//      value, the four colour registers and the 128 RAM cells (256 with a
 //      Superchip's cartridge RAM; in shared memory), with the surrogate rules:
 //        reads   relaxed read of Eq. s-read w.r.t. memory contents: RAM reads
 //                spread the adjoint over |i - a| <= W with weights
@@ -44,11 +44,12 @@
 namespace vcs {
 
 // carried adjoints: aA aX aY aV aC0 aC1 aC2, aRAM[128] and its compensation,
-// those of player 0's position and of HMP0 (position sampler), then the
-// Superchip RAM's adjoints [128] and their compensation
+// those of player 0's position and of HMP0 (position sampler), the Superchip
+// RAM's adjoints [128] and their compensation, then COLUP1's
 constexpr int kCarryPos = 7 + 256;
 constexpr int kCarryCram = kCarryPos + 2;
-constexpr int kCarry = kCarryCram + 256;
+constexpr int kCarryC3 = kCarryCram + 256;
+constexpr int kCarry = kCarryC3 + 1;
 constexpr int kMaxW = 120;        // window half-width limit (tau <= 10)
 
 // Compensated (Neumaier) sum: s + c carries the running total.
@@ -69,10 +70,11 @@ struct RecTape {
   float* cw;
   uint32_t n, cap, ncw, capcw;
   // versions 0..2: the colour registers COLUP0, COLUPF, COLUBK; version 3:
-  // player 0's position (its pixel sums are the sampler's, zero when off)
-  int32_t slot0, slot1, slot2, slot3;  // float slot of each live version
-  float s0, s1, s2, s3, c0, c1, c2, c3;  // compensated pixel-gradient sums of the live versions
-  float p0, p1, p2, p3;            // sums of the versions alive at the segment start
+  // player 0's position (its pixel sums are the sampler's, zero when off);
+  // version 4: COLUP1
+  int32_t slot0, slot1, slot2, slot3, slot4;  // float slot of each live version
+  float s0, s1, s2, s3, s4, c0, c1, c2, c3, c4;  // compensated pixel-gradient sums of the live versions
+  float p0, p1, p2, p3, p4;        // sums of the versions alive at the segment start
   bool overflow;
   uint32_t T, gmask;               // replicas of this env and their warp lanes
   // The replicas of an env each sum the pixel chunks they own; a version's
@@ -99,27 +101,32 @@ struct RecTape {
     if (r == 0) { close_version(slot0, s0 + c0, p0); s0 = c0 = 0.f; slot0 = fresh; }
     else if (r == 1) { close_version(slot1, s1 + c1, p1); s1 = c1 = 0.f; slot1 = fresh; }
     else if (r == 2) { close_version(slot2, s2 + c2, p2); s2 = c2 = 0.f; slot2 = fresh; }
-    else { close_version(slot3, s3 + c3, p3); s3 = c3 = 0.f; slot3 = fresh; }
+    else if (r == 3) { close_version(slot3, s3 + c3, p3); s3 = c3 = 0.f; slot3 = fresh; }
+    else { close_version(slot4, s4 + c4, p4); s4 = c4 = 0.f; slot4 = fresh; }
   }
   __device__ __forceinline__ void version_write(uint32_t reg) {
     if (reg == 0x06) colour_write(0);
     else if (reg == 0x08) colour_write(1);
     else if (reg == 0x09) colour_write(2);
     else if (reg == 0x10 || reg == 0x2A) colour_write(3);
+    else if (reg == 0x07) colour_write(4);
   }
-  // pixel-gradient sums of one drawn span, per owner, and the sampler's sum
-  __device__ __forceinline__ void pixels(float v0, float v1, float v2, float v3) {
+  // pixel-gradient sums of one drawn span, per owner (COLUP0, COLUPF,
+  // COLUBK, COLUP1), and the sampler's sum
+  __device__ __forceinline__ void pixels(float v0, float v1, float v2, float v3, float v4) {
     comp_add(s0, c0, v0);
     comp_add(s1, c1, v1);
     comp_add(s2, c2, v2);
     if constexpr (SAMPLER) comp_add(s3, c3, v3);
+    if (v4 != 0.f) comp_add(s4, c4, v4);
   }
   __device__ __forceinline__ void finish() {
     close_version(slot0, s0 + c0, p0);
     close_version(slot1, s1 + c1, p1);
     close_version(slot2, s2 + c2, p2);
     close_version(slot3, s3 + c3, p3);
-    s0 = s1 = s2 = s3 = c0 = c1 = c2 = c3 = 0.f;
+    close_version(slot4, s4 + c4, p4);
+    s0 = s1 = s2 = s3 = s4 = c0 = c1 = c2 = c3 = c4 = 0.f;
   }
 };
 
@@ -133,6 +140,7 @@ struct BwdParams {
   const uint8_t* cart_banks;  // bank byte per cart (banks | kCartSC | kCartE0)
   int32_t ram_words;          // RAM words per env in the recompute's shared memory (32 or 64)
   int32_t xmap;               // the batch holds Superchip or E0 carts (their kernels' instantiation)
+  int32_t full_tia;           // the whole TIA (its kernels' instantiation)
   uint32_t rom_stride;
   const uint8_t* cart_2k;
   const int32_t* env_cart;    // [n_envs]
@@ -163,7 +171,7 @@ struct BwdParams {
 };
 
 struct Adj {
-  float A, X, Y, V, C0, C1, C2;
+  float A, X, Y, V, C0, C1, C2, C3;   // C3: COLUP1
   float P, H;          // player 0's position and HMP0 (position sampler)
   float u[5], uc[5];   // joystick-input adjoints of the current step (compensated)
 };
@@ -248,6 +256,7 @@ __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, u
     if (reg == 0x06) { g = a.C0 + (j ? cw[--j] : 0.f); a.C0 = 0.f; return g; }
     if (reg == 0x08) { g = a.C1 + (j ? cw[--j] : 0.f); a.C1 = 0.f; return g; }
     if (reg == 0x09) { g = a.C2 + (j ? cw[--j] : 0.f); a.C2 = 0.f; return g; }
+    if (reg == 0x07) { g = a.C3 + (j ? cw[--j] : 0.f); a.C3 = 0.f; return g; }
     // RESP0 and HMOVE open a position version (its slot pops either way)
     if (reg == 0x2A || reg == 0x10) {
       const float sv = j ? cw[--j] : 0.f;
@@ -426,7 +435,7 @@ __host__ __device__ constexpr size_t sw_tables_end() {
 }
 __host__ __device__ constexpr size_t sw_smem_bytes() { return sw_tables_end() + (size_t)kSweepEnvs * kSweepWarpWords * 4; }
 
-template <int T, bool SAMPLER, bool INSTR, bool XM>
+template <int T, bool SAMPLER, bool INSTR, bool XM, bool FT>
 __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
@@ -444,7 +453,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
-  Ctx c = make_ctx<XM>(bs, E, slot, rank, T, cb, p.ystart);
+  Ctx c = make_ctx<XM, FT>(bs, E, slot, rank, T, cb, p.ystart);
   Regs r;
   if (active) {
     load_env(soa_at(const_cast<uint32_t*>(p.ckpt + (size_t)seg * kStateWords * n), n), n, env, c, r);
@@ -456,10 +465,10 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   tape.cw = p.cw + ((size_t)g * n + env) * p.cap_cw;
   tape.n = 0; tape.cap = p.cap_rec;
   tape.ncw = 0; tape.capcw = p.cap_cw;
-  tape.slot0 = tape.slot1 = tape.slot2 = tape.slot3 = -1;
-  tape.s0 = tape.s1 = tape.s2 = tape.s3 = 0.f;
-  tape.c0 = tape.c1 = tape.c2 = tape.c3 = 0.f;
-  tape.p0 = tape.p1 = tape.p2 = tape.p3 = 0.f;
+  tape.slot0 = tape.slot1 = tape.slot2 = tape.slot3 = tape.slot4 = -1;
+  tape.s0 = tape.s1 = tape.s2 = tape.s3 = tape.s4 = 0.f;
+  tape.c0 = tape.c1 = tape.c2 = tape.c3 = tape.c4 = 0.f;
+  tape.p0 = tape.p1 = tape.p2 = tape.p3 = tape.p4 = 0.f;
   tape.overflow = false;
   tape.T = (uint32_t)T;
   tape.gmask = c.gmask;
@@ -497,6 +506,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   m[3] = tape.p1;
   m[4] = tape.p2;
   m[5] = tape.p3;
+  m[6] = tape.p4;
   if (tape.overflow) atomicExch(p.err, 2);
 }
 
@@ -535,13 +545,14 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   Adj a;
   if (lead) {
     if (p.first) {
-      a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.P = a.H = 0.f;
+      a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.C3 = a.P = a.H = 0.f;
       for (int i = 0; i < cells; i++) aram[i * E] = 0.f;
       for (int i = 0; i < cells; i++) aramc[i * E] = 0.f;
     } else {
       const float* cr = p.carry;
       a.A = cr[0 * n + env]; a.X = cr[1 * n + env]; a.Y = cr[2 * n + env]; a.V = cr[3 * n + env];
       a.C0 = cr[4 * n + env]; a.C1 = cr[5 * n + env]; a.C2 = cr[6 * n + env];
+      a.C3 = cr[(size_t)kCarryC3 * n + env];
       a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
       a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
       for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
@@ -624,6 +635,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   a.C0 += m[2];
   a.C1 += m[3];
   a.C2 += m[4];
+  a.C3 += m[6];
   if constexpr (SAMPLER) a.P += m[5];
   if (p.seg == 0) {
     if (p.grad_ram0)
@@ -635,6 +647,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
     float* cr = p.carry;
     cr[0 * n + env] = a.A; cr[1 * n + env] = a.X; cr[2 * n + env] = a.Y; cr[3 * n + env] = a.V;
     cr[4 * n + env] = a.C0; cr[5 * n + env] = a.C1; cr[6 * n + env] = a.C2;
+    cr[(size_t)kCarryC3 * n + env] = a.C3;
     cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
@@ -660,30 +673,31 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
   auto go = [&](auto kern, int threads) {
     if ((e = allow_smem(kern, smem)) == cudaSuccess) kern<<<grid, threads, smem, s>>>(p);
   };
-  auto pick = [&](auto xm) {
-    constexpr bool XM = decltype(xm)::value;
+  auto pick = [&](auto xm, auto ft) {
+    constexpr bool XM = decltype(xm)::value, FT = decltype(ft)::value;
     // instruction-granular steps draw nothing (no pixel sums, no position
     // sampler), so one lane per env serves them
     if (p.step_instr > 0) {
-      go(k_soft_recompute<1, false, true, XM>, E);
+      go(k_soft_recompute<1, false, true, XM, FT>, E);
     } else if (p.sampler) {
       switch (T) {
-        case 1: go(k_soft_recompute<1, true, false, XM>, E); break;
-        case 2: go(k_soft_recompute<2, true, false, XM>, 2 * E); break;
-        case 4: go(k_soft_recompute<4, true, false, XM>, 4 * E); break;
-        default: go(k_soft_recompute<8, true, false, XM>, 8 * E); break;
+        case 1: go(k_soft_recompute<1, true, false, XM, FT>, E); break;
+        case 2: go(k_soft_recompute<2, true, false, XM, FT>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, true, false, XM, FT>, 4 * E); break;
+        default: go(k_soft_recompute<8, true, false, XM, FT>, 8 * E); break;
       }
     } else {
       switch (T) {
-        case 1: go(k_soft_recompute<1, false, false, XM>, E); break;
-        case 2: go(k_soft_recompute<2, false, false, XM>, 2 * E); break;
-        case 4: go(k_soft_recompute<4, false, false, XM>, 4 * E); break;
-        default: go(k_soft_recompute<8, false, false, XM>, 8 * E); break;
+        case 1: go(k_soft_recompute<1, false, false, XM, FT>, E); break;
+        case 2: go(k_soft_recompute<2, false, false, XM, FT>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, false, false, XM, FT>, 4 * E); break;
+        default: go(k_soft_recompute<8, false, false, XM, FT>, 8 * E); break;
       }
     }
   };
-  if (p.xmap) pick(std::true_type{});
-  else pick(std::false_type{});
+  if (p.full_tia) pick(std::true_type{}, std::true_type{});
+  else if (p.xmap) pick(std::true_type{}, std::false_type{});
+  else pick(std::false_type{}, std::false_type{});
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1017,6 +1031,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.cart_banks = b->cart_banks;
   p.ram_words = b->ram_words;
   p.xmap = b->xmap;
+  p.full_tia = b->cfg.full_tia;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.env_cart = b->env_cart_dev;
@@ -1173,6 +1188,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.cart_banks = b->cart_banks;
   p.ram_words = b->ram_words;
   p.xmap = b->xmap;
+  p.full_tia = b->cfg.full_tia;
   p.rom_stride = b->rom_stride;
   p.cart_2k = b->cart_2k;
   p.env_cart = b->env_cart_dev;

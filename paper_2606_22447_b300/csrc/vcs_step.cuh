@@ -30,7 +30,7 @@ struct CountTape {
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) { n++; }
   static constexpr bool sampler = false;
   __device__ __forceinline__ void version_write(uint32_t reg) { ncw += (uint32_t)(kVersionRegs >> reg) & 1u; }
-  __device__ __forceinline__ void pixels(float, float, float, float) {}
+  __device__ __forceinline__ void pixels(float, float, float, float, float) {}
 };
 
 __device__ __forceinline__ uint32_t round_byte(float v) {
@@ -43,8 +43,8 @@ __device__ __forceinline__ uint32_t round_byte(float v) {
 // the RAM may be overridden from float values first, and the full state is
 // checkpointed at the start of every segment of seg_steps steps.
 // XM: the batch holds Superchip or E0 carts (blocks of other carts run with
-// those features off all the same).
-template <bool SOFT, int T, bool BOOT, bool INSTR, bool XM>
+// those features off all the same); FT: the whole TIA.
+template <bool SOFT, int T, bool BOOT, bool INSTR, bool XM, bool FT>
 __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   // T threads per env (a compile-time constant, so T = 1 carries no replica
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
   const uint32_t lanes = warp_lanes(E * T);
-  Ctx c = make_ctx<XM>(bs, E, slot, rank, T, cb, p.ystart);
+  Ctx c = make_ctx<XM, FT>(bs, E, slot, rank, T, cb, p.ystart);
   const bool lead = rank == 0;   // the replica that writes per-env results
 
   Regs r;
@@ -220,7 +220,7 @@ static void launch_kernel(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStr
   kern<<<grid, block, smem, s>>>(p);
 }
 
-template <bool SOFT, bool XM>
+template <bool SOFT, bool XM, bool FT>
 static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   if (n_blocks <= 0) return 0;
   const dim3 grid(n_blocks), block(E * p.tpe);
@@ -228,21 +228,21 @@ static int launch_run(const StepParams& p, int n_blocks, int E, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   // instruction-granular steps draw nothing, so one lane per env serves them
   if (p.step_instr > 0) {
-    launch_kernel(k_run<SOFT, 1, false, true, XM>, grid, dim3(E), smem, s, p);
+    launch_kernel(k_run<SOFT, 1, false, true, XM, FT>, grid, dim3(E), smem, s, p);
     return (int)cudaGetLastError();
   }
   // the boot sequence exists in the hard step kernel only when a batch asks
   // for it, so that default launches carry none of its code
   const bool boot = !SOFT && p.boot_frames;
   switch (p.tpe * 2 + (boot ? 1 : 0)) {
-    case 2: launch_kernel(k_run<SOFT, 1, false, false, XM>, grid, block, smem, s, p); break;
-    case 4: launch_kernel(k_run<SOFT, 2, false, false, XM>, grid, block, smem, s, p); break;
-    case 8: launch_kernel(k_run<SOFT, 4, false, false, XM>, grid, block, smem, s, p); break;
-    case 16: launch_kernel(k_run<SOFT, 8, false, false, XM>, grid, block, smem, s, p); break;
-    case 3: launch_kernel(k_run<false, 1, true, false, XM>, grid, block, smem, s, p); break;
-    case 5: launch_kernel(k_run<false, 2, true, false, XM>, grid, block, smem, s, p); break;
-    case 9: launch_kernel(k_run<false, 4, true, false, XM>, grid, block, smem, s, p); break;
-    case 17: launch_kernel(k_run<false, 8, true, false, XM>, grid, block, smem, s, p); break;
+    case 2: launch_kernel(k_run<SOFT, 1, false, false, XM, FT>, grid, block, smem, s, p); break;
+    case 4: launch_kernel(k_run<SOFT, 2, false, false, XM, FT>, grid, block, smem, s, p); break;
+    case 8: launch_kernel(k_run<SOFT, 4, false, false, XM, FT>, grid, block, smem, s, p); break;
+    case 16: launch_kernel(k_run<SOFT, 8, false, false, XM, FT>, grid, block, smem, s, p); break;
+    case 3: launch_kernel(k_run<false, 1, true, false, XM, FT>, grid, block, smem, s, p); break;
+    case 5: launch_kernel(k_run<false, 2, true, false, XM, FT>, grid, block, smem, s, p); break;
+    case 9: launch_kernel(k_run<false, 4, true, false, XM, FT>, grid, block, smem, s, p); break;
+    case 17: launch_kernel(k_run<false, 8, true, false, XM, FT>, grid, block, smem, s, p); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

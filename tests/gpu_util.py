@@ -25,12 +25,12 @@ def gpu_rollout(batch, actions, frame_skip, screens=True):
 
 
 def oracle_rollout(rom, mapper, actions, frame_skip, ystart=34, ep_len=None, screens=True, boot=None,
-                   start=None):
+                   start=None, full_tia=False):
     """One env through the oracle; ep_len (frames per episode, cyclic)
     reproduces the library's auto-reset at step ends; boot = (noop frames,
     reset frames) and start (this env's start-NOOP counts, cyclic) reproduce
     the boot sequence after every power-on."""
-    o = oracle.Oracle(rom, mapper, ystart)
+    o = oracle.Oracle(rom, mapper, ystart, full_tia=full_tia)
 
     def do_boot(episode):
         if boot is not None or start is not None:

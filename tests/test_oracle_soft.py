@@ -349,7 +349,7 @@ def test_colup1_owns_player1_and_score_pixels(score):
         imm.append(a.labels["IMM"] + 1 - 0xF000)
     imm = []
     rom = rom4k(build)
-    o = oracle.Oracle(rom, synth.MAPPER_4K)
+    o = oracle.Oracle(rom, synth.MAPPER_4K, full_tia=True)
     n = 4
     g, _, scr = o.soft_rollout(np.zeros((n, 5)), 1, 0.01, 6.0, None, np.ones((n, 210, 160)))
     per_frame = 210 * (32 + (32 if score else 0))
