@@ -37,7 +37,7 @@ WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+sc
 # DRAM bytes (read + write) of one step launch on the bench workload, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernel; to be taken again whenever the kernel changes
-TRAFFIC_BYTES_PER_LAUNCH = 1_022_464 + 83_100_672
+TRAFFIC_BYTES_PER_LAUNCH = 1_205_504 + 83_224_064
 OPS_PER_INSTRUCTION = 12
 OPS_PER_PIXEL = 6
 PIXELS_PER_STEP = 210 * 160
@@ -317,19 +317,24 @@ def full_leg(n_envs=4096, n_instr=3000):
             "grid": rows}
 
 
-def mixed_leg(n_envs, steps, reps):
+def mixed_leg(n_envs, steps, reps, full_tia=False):
     """The batched mixed-cartridge workload: n_envs envs over 16 carts (6 x 2K,
     6 x 4K, 4 x F8, round-robin then grouped by cart), geometric episode
     lengths (mean 2,000 frames) with auto-reset, frame-skip 4, RAM + screen
     written per step.  The launch geometry is autotuned on the workload
     first (outside the timing); each timed unit is one replay of a CUDA graph
-    of `steps` env-steps.  Returns env-steps/s (median over reps)."""
+    of `steps` env-steps.  Returns env-steps/s (median over reps).
+    full_tia: the same shape over carts of all nine formats that draw with
+    every TIA object and read the collision latches, in a full-TIA batch."""
     import torch
 
-    from paper_2606_22447_b300 import Batch, synth
-    roms = synth.config_carts(SEED, synth.MIX16)
-    ec = synth.env_cart_round_robin(n_envs, len(synth.MIX16))
-    b = Batch(roms, synth.MIX16, ec)
+    from paper_2606_22447_b300 import Batch, default_config, synth
+    mappers = ([synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
+                synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0] if full_tia
+               else synth.MIX16)
+    roms = synth.config_carts(SEED, mappers, full_tia=full_tia)
+    ec = synth.env_cart_round_robin(n_envs, len(mappers))
+    b = Batch(roms, mappers, ec, default_config(full_tia=1 if full_tia else 0))
     b.set_episodes(synth.episode_lengths(SEED, n_envs, 16))
     acts = torch.from_numpy(synth.actions(SEED + 3, n_envs, steps)).cuda()
     ram = torch.empty((steps, n_envs, 128), dtype=torch.uint8, device="cuda")
@@ -357,7 +362,9 @@ def mixed_leg(n_envs, steps, reps):
     k = tune["steps_per_launch"] or steps
     g.destroy()
     return {"env_steps_per_s": n_envs * steps / (ms / 1e3), "ms_per_graph": ms, "n_envs": n_envs,
-            "steps_per_graph": steps, "carts": "6x2K + 6x4K + 4xF8", "episodes_ended": done,
+            "steps_per_graph": steps, "episodes_ended": done,
+            "carts": ("full-TIA carts of the nine formats (2K 4K F8 F6 F4 F8SC F6SC F4SC E0), full_tia = 1"
+                      if full_tia else "6x2K + 6x4K + 4xF8"),
             "autotune": tune, "gpu_launches_per_graph": -(-steps // k),
             "outputs": "RAM + screen per step (2.2 GB per step at 65,536 envs), larger than L2"}
 
@@ -471,8 +478,10 @@ def gpu_arm(args):
         if not args.no_soft_long:
             soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, 1, "soft_long_4096xmix8_instructions_per_frame")
     mixed = None
+    full_tia = None
     if not args.no_mixed:
         mixed = mixed_leg(args.mixed_envs, 8, 5)
+        full_tia = mixed_leg(16384, 8, 3, full_tia=True)
     instr = None
     if not args.no_instr:
         instr = instr_leg([1, 64, 256, 1024, 4096, 16384, 65536])
@@ -494,6 +503,7 @@ def gpu_arm(args):
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "soft_fwd_bwd": soft,
             "mixed_carts": mixed,
+            "full_tia_carts": full_tia,
             "instruction_granular": instr,
             "full_relaxed": full,
         }
