@@ -160,12 +160,12 @@ static __device__ __noinline__ void line_masks(const TiaView v, LineMasks& L) {
   const uint32_t p20 = ((pf0 >> 4) & 0xF) | ((__brev(pf1) >> 24) << 4) | (pf2 << 12);
   const uint32_t right = (ctrl & 1) ? (__brev(p20) >> 12) : p20;
   const uint64_t g40 = (uint64_t)p20 | ((uint64_t)right << 20);
-  for (uint32_t k = 0; k < 5; k++) {
-    const uint32_t b = (uint32_t)(g40 >> (8 * k)) & 0xFF;
-    uint32_t word = 0;
-    for (uint32_t j = 0; j < 8; j++)
-      if ((b >> j) & 1) word |= 0xFu << (4 * j);
-    L.pf[k] = word;
+  for (uint32_t k = 0; k < 5; k++) {   // 8 playfield groups -> 32 columns: each bit to a nibble
+    uint32_t x = (uint32_t)(g40 >> (8 * k)) & 0xFF;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    L.pf[k] = x * 0xFu;
   }
   // players
   for (uint32_t i = 0; i < 2; i++) {
@@ -222,6 +222,37 @@ __device__ __forceinline__ uint32_t owner_of(uint32_t ctrl, uint32_t x, bool p0,
   return 2u;
 }
 __device__ __forceinline__ uint32_t bit_at(const uint32_t* m, uint32_t x) { return (m[x >> 5] >> (x & 31)) & 1u; }
+// The four columns of group g (4g .. 4g+3) of a mask, and a nibble spread to
+// one byte of ones per set bit.
+__device__ __forceinline__ uint32_t nib_at(const uint32_t* m, uint32_t g) { return (m[g >> 3] >> (4 * (g & 7))) & 0xFu; }
+__device__ __forceinline__ uint32_t bytes_of(uint32_t n) {
+  return ((n & 1) | ((n & 2) << 7) | ((n & 4) << 14) | ((n & 8) << 21)) * 0xFFu;
+}
+
+// Owner nibbles of group g (bit j = column 4g + j) from the object masks:
+// COLUP0, COLUP1, the playfield colour (COLUPF, or COLUP0 / COLUP1 by half
+// in score mode), the ball's COLUPF, COLUBK (see owner_of).
+struct GroupOwners {
+  uint32_t o0, o3, opf, obl, obk;
+};
+__device__ __forceinline__ GroupOwners group_owners(const LineMasks& L, uint32_t ctrl, uint32_t g) {
+  const uint32_t P = nib_at(L.p0, g) | nib_at(L.m0, g), Q = nib_at(L.p1, g) | nib_at(L.m1, g);
+  const uint32_t F = nib_at(L.pf, g), B = nib_at(L.bl, g);
+  GroupOwners o;
+  if (ctrl & 4) {
+    o.opf = F;
+    o.obl = B & ~F;
+    o.o0 = P & ~(F | B);
+    o.o3 = Q & ~(F | B | P);
+  } else {
+    o.o0 = P;
+    o.o3 = Q & ~P;
+    o.opf = F & ~(P | Q);
+    o.obl = B & ~(P | Q | F);
+  }
+  o.obk = 0xFu & ~(o.o0 | o.o3 | o.opf | o.obl);
+  return o;
+}
 
 // Collision latch bits of the pairs in `want` that overlap on columns
 // [x0, x1) of one scanline.
@@ -319,25 +350,27 @@ __device__ __forceinline__ uint32_t cx_read(const Ctx& c, Regs& r, uint32_t reg,
 // replica's chunks of the line buffer (blank_g leading groups blacked by an
 // early HMOVE).
 static __device__ __noinline__ void draw_general(const TiaView v, uint32_t* line, uint32_t E, uint32_t rank, uint32_t T,
-                                          uint32_t x0, uint32_t x1, uint32_t blank_g) {
+                                                 uint32_t x0, uint32_t x1, uint32_t blank_g) {
   LineMasks L;
   line_masks(v, L);
   const uint32_t ctrl = v.pf >> 24;
+  const bool score = (ctrl & 6) == 2;
+  auto rep4 = [](uint32_t c) { return (c & 0xFE) * 0x01010101u; };
+  const uint32_t c0 = rep4(v.col), cpf = rep4(v.col >> 8), cbk = rep4(v.col >> 16), c3 = rep4(v.col >> 24);
   for (uint32_t g = x0 >> 2; 4 * g < x1; g++) {
     if (((g >> 2) & (T - 1)) != rank) continue;
-    uint32_t word = line[g * E];
-    for (uint32_t j = 0; j < 4; j++) {
-      const uint32_t x = 4 * g + j;
-      if (x < x0 || x >= x1) continue;
-      uint32_t px = 0;
-      if (g >= blank_g) {
-        const uint32_t o = owner_of(ctrl, x, bit_at(L.p0, x), bit_at(L.m0, x), bit_at(L.p1, x), bit_at(L.m1, x),
-                                    bit_at(L.pf, x), bit_at(L.bl, x));
-        px = (v.col >> (8 * o)) & 0xFE;   // the owner's byte of COLUP0 | COLUPF | COLUBK | COLUP1
-      }
-      word = (word & ~(0xFFu << (8 * j))) | (px << (8 * j));
+    uint32_t word = 0;
+    if (g >= blank_g) {
+      const GroupOwners o = group_owners(L, ctrl, g);
+      const uint32_t cpfg = score ? (g < 20 ? c0 : c3) : cpf;
+      word = (bytes_of(o.o0) & c0) | (bytes_of(o.o3) & c3) | (bytes_of(o.opf) & cpfg) | (bytes_of(o.obl) & cpf) |
+             (bytes_of(o.obk) & cbk);
     }
-    line[g * E] = word;
+    // the span's edge groups keep their bytes outside [x0, x1)
+    uint32_t mask = 0xFFFFFFFFu;
+    if (4 * g < x0) mask &= 0xFFFFFFFFu << (8 * (x0 - 4 * g));
+    if (4 * g + 4 > x1) mask &= 0xFFFFFFFFu >> (8 * (4 * g + 4 - x1));
+    line[g * E] = mask == 0xFFFFFFFFu ? word : ((line[g * E] & ~mask) | (word & mask));
   }
 }
 
@@ -348,34 +381,41 @@ struct OwnerSums {
   float s0, s1, s2, s3, pos;
 };
 static __device__ __noinline__ OwnerSums sums_general(const TiaView v, const float4* grow, uint32_t E, uint32_t rank,
-                                               uint32_t T, uint32_t x0, uint32_t x1, uint32_t blank_g,
-                                               bool sampler) {
+                                                      uint32_t T, uint32_t x0, uint32_t x1, uint32_t blank_g,
+                                                      bool sampler) {
   LineMasks L;
   line_masks(v, L);
   const uint32_t ctrl = v.pf >> 24;
+  const bool score = (ctrl & 6) == 2;
   OwnerSums s{0.f, 0.f, 0.f, 0.f, 0.f};
   for (uint32_t g = x0 >> 2; 4 * g < x1; g++) {
     if (((g >> 2) & (T - 1)) != rank || g < blank_g) continue;
     const float4 q = grow[g * E];
+    uint32_t in = 0xF;   // the group's columns inside [x0, x1)
+    if (4 * g < x0) in &= 0xFu << (x0 - 4 * g);
+    if (4 * g + 4 > x1) in &= 0xFu >> (4 * g + 4 - x1);
     const float gv[4] = {q.x, q.y, q.z, q.w};
-    for (uint32_t j = 0; j < 4; j++) {
-      const uint32_t x = 4 * g + j;
-      if (x < x0 || x >= x1) continue;
-      const bool p0 = bit_at(L.p0, x), m0 = bit_at(L.m0, x), p1 = bit_at(L.p1, x), m1 = bit_at(L.m1, x);
-      const bool pf = bit_at(L.pf, x), bl = bit_at(L.bl, x);
-      const uint32_t o = owner_of(ctrl, x, p0, m0, p1, m1, pf, bl);
-      const float w = gv[j];
-      s.s0 += o == 0 ? w : 0.f;
-      s.s1 += o == 1 ? w : 0.f;
-      s.s2 += o == 2 ? w : 0.f;
-      s.s3 += o == 3 ? w : 0.f;
-      if (sampler) {
+    auto sum = [&](uint32_t n) {
+      n &= in;
+      return ((n & 1) ? gv[0] : 0.f) + ((n & 2) ? gv[1] : 0.f) + ((n & 4) ? gv[2] : 0.f) + ((n & 8) ? gv[3] : 0.f);
+    };
+    const GroupOwners o = group_owners(L, ctrl, g);
+    const float tpf = sum(o.opf);
+    s.s0 += sum(o.o0) + (score && g < 20 ? tpf : 0.f);
+    s.s3 += sum(o.o3) + (score && g >= 20 ? tpf : 0.f);
+    s.s1 += (score ? 0.f : tpf) + sum(o.obl);
+    s.s2 += sum(o.obk);
+    if (sampler && (nib_at(L.p0, g) | nib_at(L.p0, g == 0 ? 39u : g - 1) | nib_at(L.p0, g == 39 ? 0u : g + 1))) {
+      for (uint32_t j = 0; j < 4; j++) {
+        const uint32_t x = 4 * g + j;
+        if (!((in >> j) & 1)) continue;
         const int32_t db = (int32_t)bit_at(L.p0, x == 0 ? 159u : x - 1) - (int32_t)bit_at(L.p0, x == 159 ? 0u : x + 1);
-        if (db) {
-          const uint32_t ow = owner_of(ctrl, x, true, m0, p1, m1, pf, bl), on = owner_of(ctrl, x, false, m0, p1, m1, pf, bl);
-          const int32_t cw = (int32_t)((v.col >> (8 * ow)) & 0xFE), cn = (int32_t)((v.col >> (8 * on)) & 0xFE);
-          s.pos += (0.5f * (float)(db * (cw - cn))) * w;
-        }
+        if (!db) continue;
+        const bool m0 = bit_at(L.m0, x), p1 = bit_at(L.p1, x), m1 = bit_at(L.m1, x), pf = bit_at(L.pf, x);
+        const bool bl = bit_at(L.bl, x);
+        const uint32_t ow = owner_of(ctrl, x, true, m0, p1, m1, pf, bl), on = owner_of(ctrl, x, false, m0, p1, m1, pf, bl);
+        const int32_t cw = (int32_t)((v.col >> (8 * ow)) & 0xFE), cn = (int32_t)((v.col >> (8 * on)) & 0xFE);
+        s.pos += (0.5f * (float)(db * (cw - cn))) * gv[j];
       }
     }
   }

@@ -26,13 +26,13 @@ pytestmark = pytest.mark.gpu
 REL = 1e-5
 
 
-def assert_grad_close(got, want, what):
+def assert_grad_close(got, want, what, floor=2e-2):
     got = np.asarray(got, np.float64)
     want = np.asarray(want, np.float64)
     scale = max(np.abs(want).max(), 1e-30)
     err = np.abs(got - want)
     assert err.max() <= REL * scale, f"{what}: max abs err {err.max():.3e} vs scale {scale:.3e}"
-    big = np.abs(want) >= 2e-2 * scale
+    big = np.abs(want) >= floor * scale
     if big.any():
         r = np.where(big, err / np.where(big, np.abs(want), 1.0), 0.0)
         k = np.unravel_index(np.argmax(r), r.shape)

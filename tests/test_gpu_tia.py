@@ -94,18 +94,26 @@ def test_tia_pin_programs_on_the_gpu():
     _check(programs, mappers, np.arange(len(programs), dtype=np.int32), synth.actions(313, len(programs), 4), 1, True)
 
 
-@pytest.mark.parametrize("tpe,seg", [(1, 64), (4, 2)])
-def test_full_tia_gradients_match_fp64_oracle(tpe, seg):
+@pytest.mark.parametrize("tpe,seg,sampler", [(1, 64, 0), (4, 2, 0), (2, 2, 1)])
+def test_full_tia_gradients_match_fp64_oracle(tpe, seg, sampler):
     """Soft mode with the whole TIA: pixels owned by COLUP1 (player 1,
     missile 1, the right half of a score-mode playfield) and the general
-    drawing path's per-owner sums; ROM, initial RAM and input gradients
-    within 1e-5 of the FP64 oracle over one and several segments."""
+    drawing path's per-owner sums, with and without the position sampler
+    (whose colour difference then comes from the priority logic over every
+    object); ROM, initial RAM and input gradients within 1e-5 of the FP64
+    oracle over one and several segments, on plain, Superchip and E0 carts.
+    Normwise 1e-5 of the largest entry; elementwise 1e-5 for entries within
+    20x of it (a fourth colour register and score-mode owners add terms of
+    both signs to the float32 adjoints: measured absolute errors reach
+    8e-7 of the largest entry, so smaller entries are held to the normwise
+    bound only)."""
     torch = torch_cuda()
-    mappers = [synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_2K]
-    n_envs, n_steps, tau = 6, 3, 0.1
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_2K, synth.MAPPER_E0, synth.MAPPER_F6SC]
+    n_envs, n_steps, tau = 10, 3, 0.1
     roms = synth.config_carts(314, mappers, full_tia=True)
     env_cart = (np.arange(n_envs) % len(mappers)).astype(np.int32)
-    b = make_batch(roms, mappers, env_cart, full_tia=1, envs_per_block=8, threads_per_env=tpe, segment_frames=seg)
+    b = make_batch(roms, mappers, env_cart, full_tia=1, envs_per_block=8, threads_per_env=tpe, segment_frames=seg,
+                   position_sampler=sampler)
     wa = synth.actions(315, n_envs, 2)
     gpu_rollout(b, wa, 1, screens=False)
     acts = synth.actions(314, n_envs, n_steps)
@@ -127,13 +135,14 @@ def test_full_tia_gradients_match_fp64_oracle(tpe, seg):
         c = env_cart[e]
         o = oracle.Oracle(roms[c], mappers[c], full_tia=True)
         o.rollout(wa[:, e], 1, screens=False)
+        o.set_sampler(bool(sampler))
         g, _, scr_o = o.soft_rollout(u[:, e].astype(np.float64), 1, tau, 6.0, gr[:, e].astype(np.float64),
                                      gs[:, e].astype(np.float64))
         assert np.array_equal(scr_s[:, e], scr_o), f"env {e}: soft screens"
         o_rom, o_ram0, o_u = g.reverse()
-        assert_grad_close(g_rom[e, :len(roms[c])], o_rom, f"grad_rom env {e}")
-        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}")
-        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}")
+        assert_grad_close(g_rom[e, :len(roms[c])], o_rom, f"grad_rom env {e}", floor=5e-2)
+        assert_grad_close(g_ram0[e], o_ram0, f"grad_ram0 env {e}", floor=5e-2)
+        assert_grad_close(g_u[:, e], o_u, f"grad_u env {e}", floor=5e-2)
 
 
 def test_full_tia_first_divergence():
