@@ -609,8 +609,9 @@ vcs_status vcs_load_state(vcs_batch* b, const void* blob_host, void* stream) {
 
 }  // extern "C"
 
-// Tuning results of this process, keyed by GPU, batch shape and cartridge mix
-// (envs per mapper), frame-skip and which outputs the rollouts write.
+// Tuning results of this process, keyed by GPU, batch shape, cartridge mix
+// (envs per format), frame-skip, which outputs the rollouts write,
+// instruction-granular steps and the TIA mode.
 static std::mutex g_tune_mu;
 static std::map<std::string, vcs_tune> g_tune_cache;
 
@@ -619,12 +620,14 @@ static std::string tune_key(const vcs_batch* b, int32_t frame_skip, bool ram, bo
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "?";
-  int per_mapper[3] = {0, 0, 0};
-  for (int e = 0; e < b->n_envs; e++) per_mapper[b->mapper[b->env_cart[e]] % 3]++;
+  int per_mapper[VCS_MAPPER_E0 + 1] = {};
+  for (int e = 0; e < b->n_envs; e++) per_mapper[b->mapper[b->env_cart[e]]]++;
+  std::string mix;
+  for (int m = 0; m <= VCS_MAPPER_E0; m++) mix += "|" + std::to_string(per_mapper[m]);
   char buf[256];
-  snprintf(buf, sizeof buf, "|%d|%d|%d|%d|%d|%d|%d|%d|%d", b->sms, b->n_envs, b->n_carts, per_mapper[0], per_mapper[1],
-           per_mapper[2], frame_skip, (ram ? 1 : 0) | (screen ? 2 : 0), b->cfg.step_instructions);
-  return name + buf;
+  snprintf(buf, sizeof buf, "|%d|%d|%d|%d|%d|%d|%d", b->sms, b->n_envs, b->n_carts, frame_skip,
+           (ram ? 1 : 0) | (screen ? 2 : 0), b->cfg.step_instructions, b->cfg.full_tia);
+  return name + buf + mix;
 }
 
 static vcs_status apply_tune(vcs_batch* b, const vcs_tune& t) {
