@@ -152,7 +152,8 @@ struct LineMasks {
   uint32_t p0[5], p1[5], m0[5], m1[5], bl[5], pf[5];
 };
 
-static __device__ __noinline__ void line_masks(const TiaView v, LineMasks& L) {
+// objs: the kOb* objects whose masks are wanted (the others stay empty).
+static __device__ __noinline__ void line_masks(const TiaView v, LineMasks& L, uint32_t objs = 0x3F) {
   for (int k = 0; k < 5; k++) L.p0[k] = L.p1[k] = L.m0[k] = L.m1[k] = L.bl[k] = L.pf[k] = 0;
   const uint32_t ctrl = v.pf >> 24, w0 = v.w0, w1 = v.w1, w3 = v.w3;
   // playfield: 20 bits x 4 columns, right half repeated or reflected
@@ -160,7 +161,7 @@ static __device__ __noinline__ void line_masks(const TiaView v, LineMasks& L) {
   const uint32_t p20 = ((pf0 >> 4) & 0xF) | ((__brev(pf1) >> 24) << 4) | (pf2 << 12);
   const uint32_t right = (ctrl & 1) ? (__brev(p20) >> 12) : p20;
   const uint64_t g40 = (uint64_t)p20 | ((uint64_t)right << 20);
-  for (uint32_t k = 0; k < 5; k++) {   // 8 playfield groups -> 32 columns: each bit to a nibble
+  for (uint32_t k = 0; k < 5 && (objs & kObPF); k++) {   // 8 playfield groups -> 32 columns: each bit to a nibble
     uint32_t x = (uint32_t)(g40 >> (8 * k)) & 0xFF;
     x = (x | (x << 12)) & 0x000F000Fu;
     x = (x | (x << 6)) & 0x03030303u;
@@ -173,7 +174,7 @@ static __device__ __noinline__ void line_masks(const TiaView v, LineMasks& L) {
     const bool vdel = (w0 & (i ? kW0Vdelp1 : kW0Vdelp0)) != 0, refl = (w0 & (i ? kW0Refp1 : kW0Refp0)) != 0;
     const uint32_t g = vdel ? (w1 >> (i ? 16 : 8)) & 0xFF : (i ? w1 & 0xFF : v.p0 & 0xFF);
     const uint32_t pos = i ? w3 & 0xFF : (v.p0 >> 8) & 0xFF;
-    if (!g) continue;
+    if (!g || !(objs & (i ? kObP1 : kObP0))) continue;
     const uint32_t cols = refl ? g : (__brev(g) >> 24);   // bit j = column j of the copy
     const uint32_t sc = player_scale(mode), pat = scale_bits(cols, sc), cp = nusiz_copies(mode);
     uint32_t* m = i ? L.p1 : L.p0;
@@ -186,7 +187,7 @@ static __device__ __noinline__ void line_masks(const TiaView v, LineMasks& L) {
   // missiles: in the player's copies (one for the double and quad sizes)
   for (uint32_t i = 0; i < 2; i++) {
     const bool on = (w1 & (i ? kW1Enam1 : kW1Enam0)) && !(w0 & (i ? kW0Resmp1 : kW0Resmp0));
-    if (!on) continue;
+    if (!on || !(objs & (i ? kObM1 : kObM0))) continue;
     const uint32_t nus = i ? (w0 >> 16) & 0xFF : (w0 >> 8) & 0xFF;
     const uint32_t wid = 1u << ((nus >> 4) & 3), cp = nusiz_copies(nus & 7);
     const uint32_t pos = (w3 >> (i ? 16 : 8)) & 0xFF;
@@ -199,7 +200,7 @@ static __device__ __noinline__ void line_masks(const TiaView v, LineMasks& L) {
   }
   // ball
   const bool bl = (w0 & kW0Vdelbl) ? (w1 & kW1EnablOld) != 0 : (w1 & kW1Enabl) != 0;
-  if (bl) {
+  if (bl && (objs & kObBL)) {
     const uint32_t wid = 1u << ((ctrl >> 4) & 3);
     place(L.bl, (1u << wid) - 1u, wid, (w3 >> 24) & 0xFF);
   }
@@ -254,11 +255,15 @@ __device__ __forceinline__ GroupOwners group_owners(const LineMasks& L, uint32_t
   return o;
 }
 
+// The objects in the pairs of a set of latch bits.
+__host__ __device__ constexpr uint32_t pair_objects(uint32_t pairs) {
+  return ((pairs & 0x8039u) ? kObP0 : 0u) | ((pairs & 0x80C6u) ? kObP1 : 0u) | ((pairs & 0x4303u) ? kObM0 : 0u) |
+         ((pairs & 0x4C0Cu) ? kObM1 : 0u) | ((pairs & 0x2550u) ? kObBL : 0u) | ((pairs & 0x2AA0u) ? kObPF : 0u);
+}
+
 // Collision latch bits of the pairs in `want` that overlap on columns
-// [x0, x1) of one scanline.
-static __device__ __noinline__ uint32_t collide_span(const TiaView v, uint32_t want, uint32_t x0, uint32_t x1) {
-  LineMasks L;
-  line_masks(v, L);
+// [x0, x1) of one scanline, from its column masks.
+__device__ __forceinline__ uint32_t collide_span(const LineMasks& L, uint32_t want, uint32_t x0, uint32_t x1) {
   uint32_t got = 0;
   for (uint32_t k = 0; k < 5; k++) {
     const uint32_t c0 = 32 * k;
@@ -310,6 +315,10 @@ static __device__ __noinline__ uint32_t cx_advance(const uint32_t* tx, uint32_t 
   v.w1 = tx[E];
   v.w3 = tx[3 * E];
   const bool simple = !(xo & kXoGen) && want == (1u << 5);   // player 0 against the playfield only
+  // the registers are constant over the catch-up: one set of masks, of the
+  // objects in the wanted pairs only
+  LineMasks L;
+  if (!simple) line_masks(v, L, pair_objects(want));
   uint32_t got = 0;
   int32_t cur = cxc;
   while (cur < target && (want & ~got)) {
@@ -319,7 +328,7 @@ static __device__ __noinline__ uint32_t cx_advance(const uint32_t* tx, uint32_t 
     const uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u, x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
     if (x1 > x0) {
       if (simple) got |= p0_pf_overlap(v, x0, x1) ? want : 0u;
-      else got |= collide_span(v, want & ~got, x0, x1);
+      else got |= collide_span(L, want & ~got, x0, x1);
     }
     cur = seg;
   }
