@@ -43,6 +43,7 @@ def test_config_defaults(lib):
     assert lib.vcs_config_default(C.byref(cfg)) == 0
     assert cfg.alpha == 6.0 and cfg.ystart == 34 and cfg.boot_noop_frames == 0
     assert cfg.segment_frames == 64
+    assert cfg.full_tia == 0 and cfg.position_sampler == 0 and cfg.step_instructions == 0
 
 
 def _create(lib, roms, sizes, mappers, env_cart, n_carts=None, cfg=None):

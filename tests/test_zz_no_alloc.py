@@ -39,13 +39,16 @@ def _grads(entry, tape, gr, gs, n_envs, n_steps, n_carts):
     return [t.cpu().numpy() for t in out]
 
 
-def test_static_backward_matches_backward_on_two_calls():
+@pytest.mark.parametrize("full_tia", [0, 1])
+def test_static_backward_matches_backward_on_two_calls(full_tia):
+    """Plain, Superchip and E0 carts; with the whole TIA the carry also holds
+    COLUP1's adjoint."""
     torch = torch_cuda()
-    mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8SC]
+    mappers = [synth.MAPPER_2K, synth.MAPPER_E0, synth.MAPPER_F8SC]
     n_envs, n_steps = 12, 5
-    roms = synth.config_carts(71, mappers)
+    roms = synth.config_carts(71, mappers, full_tia=bool(full_tia))
     env_cart = (np.arange(n_envs) % 3).astype(np.int32)
-    b = make_batch(roms, mappers, env_cart, segment_frames=2)
+    b = make_batch(roms, mappers, env_cart, segment_frames=2, full_tia=full_tia)
     gpu_rollout(b, synth.actions(72, n_envs, 2), 1, screens=False)
     u = torch.from_numpy(synth.action_inputs(synth.actions(71, n_envs, n_steps))).cuda()
     tape = b.soft_rollout(0.3, u, 1)
