@@ -1,5 +1,5 @@
-"""Digests of RAM and screens (the parity-at-scale check of the survey's
-measurement plan): the GPU digest kernel against the oracle's digest of the
+"""Digests of RAM and screens (parity at scale, where full outputs are too
+large to compare): the GPU digest kernel against the oracle's digest of the
 oracle's own outputs, on a small mixed batch for every env and on the
 4096-env bench workload for a seeded sample of envs."""
 from concurrent.futures import ThreadPoolExecutor
