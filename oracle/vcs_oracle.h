@@ -2,12 +2,20 @@
  * CPU oracle for the VCS hot path: TEST INFRASTRUCTURE ONLY.
  *
  * A plain, slow, cycle-by-cycle emulator of the Atari VCS (6507 CPU, RIOT,
- * TIA video subset, 2K/4K/F8 cartridges) written from the paper's machine
- * description (Section 2.2 and the architecture figure) and the public chip
- * documentation (MOS 6500 manuals, 6532 datasheet, TIA programmer's guide,
- * the published note on NMOS decimal mode).  Every CPU cycle is charged
- * before its bus access; the RIOT timer ticks once per cycle and the TIA is
- * advanced one colour clock at a time, three per cycle.
+ * TIA video: by default the subset of player 0, playfield and background,
+ * or with ovcs_set_full_tia the whole TIA with player 1, missiles, ball and
+ * collisions; 2K, 4K, F8, F6, F4, the Superchip variants of the last three
+ * and E0 cartridges) written from the paper's machine description (Section
+ * 2.2 and the architecture figure) and the public chip documentation (MOS
+ * 6500 manuals, 6532 datasheet, TIA programmer's guide, the published note
+ * on NMOS decimal mode).  Every CPU cycle is charged before its bus access;
+ * the RIOT timer ticks once per cycle and the TIA is advanced one colour
+ * clock at a time, three per cycle.
+ *
+ * Parity unpinned against real hardware and the paper's reference emulator
+ * (neither is available): the timing constants and the TIA's object rules
+ * are this oracle's readings of the documentation, pinned by the test
+ * suite's hand-derived values, closed forms and exhaustive tables.
  *
  * Soft mode (SOFT-STE, Section 3.1; Theorem 1; Corollary 1): the same
  * interpreter optionally records a deviation graph.  Every value carries a
