@@ -2,10 +2,12 @@
  * libvcs: batched Atari VCS emulation on one GPU (sm_103a), hard and soft.
  *
  * The machine is the paper's VCS (Section 2.2, the architecture figure): a
- * 6507 CPU executing a cartridge ROM (2K, 4K or F8 bank-switched), the RIOT
- * (128 B of RAM, interval timer, joystick and console-switch ports) and the
- * TIA, which turns register writes into 160x210 palette-index frames one
- * colour clock at a time.  Many independent machines run in lockstep, one
+ * 6507 CPU executing a cartridge ROM (2K, 4K, the F8 / F6 / F4 bank-switched
+ * formats, their Superchip variants with 128 B of cartridge RAM, or E0), the
+ * RIOT (128 B of RAM, interval timer, joystick and console-switch ports) and
+ * the TIA, which turns register writes into 160x210 palette-index frames one
+ * colour clock at a time (player 0, playfield and background by default;
+ * the whole TIA with vcs_config.full_tia).  Many independent machines run in lockstep, one
  * per CUDA thread.
  *
  * Modes (supplement, table of execution modes):

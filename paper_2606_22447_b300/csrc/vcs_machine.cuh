@@ -1,16 +1,16 @@
 // Per-thread VCS machine for sm_103a: one thread emulates one env.
 //
 // The machine follows the paper's VCS (Section 2.2): 6507 CPU, RIOT (RAM,
-// timer, ports), TIA video, 2K/4K/F8 cartridges.  Where the paper is silent
-// the readings are: frames end at a VSYNC write that sets D1 or after 512
-// scanlines; screen row r is scanline ystart + r over line clocks 68..227;
-// pixel = colour & 0xFE, black under VBLANK D1 and for 8 pixels after an
-// HMOVE at line clock <= 9; a write at the k-th cycle of an instruction
-// starting at cycle t takes effect at colour clock 3 (t + k); RESP0 puts P0
-// at 3 in HBLANK else (clock - 68 + 5) mod 160; WSYNC halts to the next
-// multiple of 76 cycles; the RIOT timer reads V - ceil(k / I) k cycles after
-// a write of V, then (0xFF - (k - V I - 1)) & 0xFF with TIMINT bit 7 set;
-// power-on A=X=Y=0, SP=$FD, P=$34; NMOS decimal mode.
+// timer, ports), TIA video, 2K/4K/F8/F6/F4, Superchip and E0 cartridges.
+// Where the paper is silent the readings are: frames end at a VSYNC write
+// that sets D1 or after 512 scanlines; screen row r is scanline ystart + r
+// over line clocks 68..227; pixel = colour & 0xFE, black under VBLANK D1 and
+// for 8 pixels after an HMOVE at line clock <= 9; a write at the k-th cycle
+// of an instruction starting at cycle t takes effect at colour clock 3 (t +
+// k); RESP0 puts P0 at 3 in HBLANK else (clock - 68 + 5) mod 160; WSYNC
+// halts to the next multiple of 76 cycles; the RIOT timer reads V - ceil(k /
+// I) k cycles after a write of V, then (0xFF - (k - V I - 1)) & 0xFF with
+// TIMINT bit 7 set; power-on A=X=Y=0, SP=$FD, P=$34; NMOS decimal mode.
 //
 // Time is kept per thread as two counters: `cyc`, the CPU cycle count
 // modulo 2^32 (only differences are used, for the timer), and `fc`, the
