@@ -15,8 +15,8 @@ increment 0x9E3779B97F4A7C15 passed through the variant-13 finaliser.
 
 Cartridge shapes follow the paper's workloads: the 2K, 4K and F8 mappers of
 the conformance set (per-game table, supplement; F6, F4, the Superchip
-variants and E0 widen it to the nine mappers of Section 3), 128 B of RIOT RAM, a
-160x210 screen window and NTSC frames of about 262 scanlines (Section 2.2).
+variants and E0 widen it to the nine mappers of Section 3), 128 B of RIOT
+RAM, a 160x210 screen window and NTSC frames of about 262 scanlines (Section 2.2).
 """
 from __future__ import annotations
 
