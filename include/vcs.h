@@ -399,6 +399,25 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
                             const float* u, int32_t n_steps, int32_t frame_skip,
                             float* ram_out, float* screen_out, vcs_tape** tape, void* stream);
 
+/* vcs_soft_step: the soft step of the problem statement, n_steps SOFT-STE
+ * env-steps of frame_skip frames from the batch's current state with the
+ * batch's own ROM images and RAM (Section 3.1; Theorem 1: the forward is
+ * bit-exact with vcs_rollout at every temperature; Corollary 1: tau only
+ * sets the relaxation that vcs_backward differentiates).  It is
+ * vcs_soft_rollout with rom_f32 = NULL and ram0 = NULL:
+ *   action_inputs  device float[n_steps][n_envs][5] (right, left, down, up,
+ *                  fire; a button counts as pressed when >= 0.5);
+ *   tau            in (0, 10], else VCS_ERR_ARG;
+ *   ram_out        device float[n_steps][n_envs][128] (nullable);
+ *   screen_out     device float[n_steps][n_envs][210][160] (nullable);
+ *   *tape          receives the tape (caller-owned until vcs_tape_free).
+ * vcs_backward on the tape gives the surrogate gradients with respect to
+ * the ROM bytes (at the batch's images), the RAM at the start and the
+ * action inputs.  Errors as vcs_soft_rollout. */
+vcs_status vcs_soft_step(vcs_batch* b, float tau, const float* action_inputs, int32_t n_steps,
+                         int32_t frame_skip, float* ram_out, float* screen_out, vcs_tape** tape,
+                         void* stream);
+
 /* Surrogate gradients of L = sum grad_ram . ram_out + sum grad_screen .
  * screen_out (or of the broadcast loss weights `w`) with respect to
  *   grad_rom           device float[n_envs][rom_stride] per env (nullable)
@@ -430,16 +449,26 @@ vcs_status vcs_tape_free(vcs_tape* tape);
  * inputs and outputs, and all scratch (tape entries, adjoint carries, ROM
  * impulses) comes from one fixed 64 MiB array compiled into the library,
  * which every GPU that loads the library keeps until the process exits.
- *  - Problems whose scratch does not fit (roughly n_envs x instructions per
- *    checkpoint segment x 4 bytes, plus 64 KB per env) are rejected with
+ *  - The scratch a call needs, per env: 2,088 bytes of adjoint carries
+ *    plus 8 x rom_stride bytes of ROM impulses (64 KB for 8 KB images),
+ *    plus 4 x rom_stride more (32 KB) when grad_rom_per_cart is asked for
+ *    without grad_rom; and per env and checkpoint segment held at once
+ *    (at least one): 4 x (tape records + colour versions + steps per
+ *    segment + 8) bytes, the records being about one per instruction of
+ *    the segment.  Problems that do not fit are rejected with
  *    VCS_ERR_ARG and a message giving the size needed.
- *  - The first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before any
- *    stream capture.
+ *  - The first call on a device (and the first after that device's
+ *    context was destroyed and made again) looks up the array's device
+ *    address, with that device current, and keeps it; make that first call
+ *    before any stream capture.
  *  - All calls share the array and it keeps the last call's contents (the
  *    call clears what must start at zero); calls whose GPU work overlaps,
  *    on two streams or two host threads, race with each other.
- *  - It synchronises `stream` once to read the tape's sizes. */
+ *  - It synchronises `stream` on every call, to read the tape's sizes.
+ *  - Its gradients equal vcs_backward's bit for bit when both recompute
+ *    the same number of segments at once, or both fewer or both more than
+ *    16,384 machines (segments x envs) per group; across that line the
+ *    recompute sums pixel gradients in another order (last-bit changes). */
 vcs_status vcs_backward_static(vcs_tape* tape, const float* grad_ram, const float* grad_screen,
                                const vcs_loss_weights* w, float* grad_rom, float* grad_ram0,
                                float* grad_cart_ram0, float* grad_u, float* grad_rom_per_cart,

@@ -181,6 +181,15 @@ class Batch:
                                                  _stream(stream)))
         return Tape(self, h, n_steps)
 
+    def soft_step(self, tau: float, u, frame_skip: int, ram_out=None, screen_out=None, stream=None) -> "Tape":
+        """vcs_soft_step: SOFT-STE forward over u [n_steps][n_envs][5] from
+        the batch's own ROMs and current RAM; returns the tape."""
+        h = C.c_void_p()
+        n_steps = int(u.shape[0])
+        self._check(_lib.load().vcs_soft_step(self.h, float(tau), _ptr(u), n_steps, frame_skip, _ptr(ram_out),
+                                              _ptr(screen_out), C.byref(h), _stream(stream)))
+        return Tape(self, h, n_steps)
+
     def autotune(self, frame_skip: int, n_steps: int, actions=None, ram_out=None, screen_out=None,
                  stream=None) -> dict:
         """Time launch geometries on the current state (restored after each

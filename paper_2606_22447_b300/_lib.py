@@ -68,6 +68,7 @@ SIGNATURES = {
     "vcs_save_state": (C.c_int, [vp, vp, vp]),
     "vcs_load_state": (C.c_int, [vp, vp, vp]),
     "vcs_soft_rollout": (C.c_int, [vp, C.c_float, vp, vp, vp, i32, i32, vp, vp, C.POINTER(vp), vp]),
+    "vcs_soft_step": (C.c_int, [vp, C.c_float, vp, i32, i32, vp, vp, C.POINTER(vp), vp]),
     "vcs_backward": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "vcs_tape_free": (C.c_int, [vp]),
     "vcs_backward_static": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),

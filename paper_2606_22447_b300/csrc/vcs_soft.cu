@@ -26,6 +26,7 @@
 // A final pass spreads the ROM impulses with the read window and optionally
 // sums the per-env ROM gradients per cartridge (a segmented reduction over
 // the envs of each cart, no atomics).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -951,6 +952,12 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
   return VCS_OK;
 }
 
+vcs_status vcs_soft_step(vcs_batch* b, float tau, const float* action_inputs, int32_t n_steps, int32_t frame_skip,
+                         float* ram_out, float* screen_out, vcs_tape** tape_out, void* stream) {
+  return vcs_soft_rollout(b, tau, nullptr, nullptr, action_inputs, n_steps, frame_skip, ram_out, screen_out,
+                          tape_out, stream);
+}
+
 vcs_status vcs_tape_free(vcs_tape* t) {
   if (!t) return VCS_ERR_ARG;
   free_tape(t);
@@ -1097,23 +1104,62 @@ static constexpr size_t kStaticScratchBytes = 64ull << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_backward_scratch[kStaticScratchBytes];
 
 static std::mutex g_scratch_mutex;
-static void* g_scratch_ptr[64] = {};
+struct ScratchSlot {
+  unsigned long long ctx_id;   // the context the address belongs to (0 = none looked up yet)
+  void* ptr;
+};
+static ScratchSlot g_scratch_slot[64] = {};
 
-// Device address of the static scratch on the current device; looked up once
-// per device (the array's host-side name is not a device address).
+// Unique id of the calling thread's current context (0 if none is current
+// or the driver cannot say).  A context that is destroyed and made again
+// (cudaDeviceReset, or another library resetting the primary context) gets
+// a new id, and its module, with the array, is loaded again at a new
+// address; the ids keep a stale address from being used.
+static unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrent)(CUcontext*);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the static scratch on the current device.  The array's
+// host-side name is not a device address: the address is looked up with
+// cudaGetSymbolAddress, with the device current, once per device and
+// context (the first call on a device, and the first after its context was
+// made again), and kept for later calls.
 static cudaError_t static_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
+  ScratchSlot& slot = g_scratch_slot[dev];
+  unsigned long long id = current_context_id();
+  if (!slot.ptr || id == 0 || slot.ctx_id != id) {
     void* p = nullptr;
+    // binds the device's context to this thread if no runtime call has yet
     e = cudaGetSymbolAddress(&p, g_backward_scratch);
     if (e) return e;
-    g_scratch_ptr[dev] = p;
+    if (id == 0) id = current_context_id();
+    slot.ptr = p;
+    slot.ctx_id = id;
   }
-  *out = g_scratch_ptr[dev];
+  *out = slot.ptr;
   return cudaSuccess;
 }
 

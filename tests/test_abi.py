@@ -77,6 +77,8 @@ def test_argument_errors_before_device_work(lib):
     st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0], cfg=C.byref(cfg))
     assert st == _lib.VCS_ERR_ARG and "envs_per_block" in msg
     assert lib.vcs_step(None, None, 1, None, None, None, None) == _lib.VCS_ERR_ARG
+    tape = C.c_void_p()
+    assert lib.vcs_soft_step(None, 0.1, None, 1, 1, None, None, C.byref(tape), None) == _lib.VCS_ERR_ARG
     assert lib.vcs_destroy(None) == _lib.VCS_ERR_ARG
 
 

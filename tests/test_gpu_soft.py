@@ -430,3 +430,58 @@ def test_gradients_on_e0_carts(tpe):
         if mappers[c] == synth.MAPPER_E0:
             assert np.count_nonzero(np.abs(o_rom.reshape(8, 1024)).sum(1)) >= 3   # several slices read
     assert_grad_close(g_pc, want_pc, "per-cart ROM gradient")
+
+
+def test_soft_step_entry_point():
+    """vcs_soft_step (the problem statement's soft step) through the C ABI:
+    its forward equals vcs_soft_rollout's from the batch's own ROMs and RAM
+    bit for bit (and so the hard path's, Theorem 1); the backward of its
+    tape equals that of vcs_soft_rollout's bit for bit and the FP64
+    oracle's within the gradient tolerance; tau <= 0 is refused."""
+    import ctypes as C
+
+    from paper_2606_22447_b300 import _lib
+    torch = torch_cuda()
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8]
+    n_envs, n_steps = 6, 3
+    _, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 67)
+    L = _lib.load()
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = lambda t: C.c_void_p(t.data_ptr())
+    u_t = torch.from_numpy(u).cuda()
+    blob = b.save_state()
+    outs = []
+    for entry in ("vcs_soft_step", "vcs_soft_rollout"):
+        b.load_state(blob)
+        ram = torch.empty((n_steps, n_envs, 128), device="cuda")
+        scr = torch.empty((n_steps, n_envs, 210, 160), device="cuda")
+        h = C.c_void_p()
+        if entry == "vcs_soft_step":
+            st = L.vcs_soft_step(b.h, 0.1, p(u_t), n_steps, 1, p(ram), p(scr), C.byref(h), s)
+        else:
+            st = L.vcs_soft_rollout(b.h, 0.1, None, None, p(u_t), n_steps, 1, p(ram), p(scr), C.byref(h), s)
+        _lib.check(st, b.h)
+        g_ram0 = torch.zeros((n_envs, 128), device="cuda")
+        g_u = torch.zeros((n_steps, n_envs, 5), device="cuda")
+        g_rom = torch.zeros((n_envs, b.rom_stride), device="cuda")
+        gr = torch.from_numpy(synth.normal_f32(67, (n_steps, n_envs, 128), 1)).cuda()
+        _lib.check(L.vcs_backward(h, p(gr), None, None, p(g_rom), p(g_ram0), None, p(g_u), None, s), b.h)
+        b.sync()
+        outs.append([x.cpu().numpy() for x in (ram, scr, g_rom, g_ram0, g_u)])
+        L.vcs_tape_free(h)
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+    ram, scr, g_rom, g_ram0, g_u = outs[0]
+    gr = synth.normal_f32(67, (n_steps, n_envs, 128), 1)
+    for e in range(n_envs):
+        c = env_cart[e]
+        (o_rom, o_ram0, o_u), ram_o, scr_o = _oracle_grads(roms[c], mappers[c], wa[:, e], u[:, e], 1, 0.1,
+                                                           gr[:, e], None)
+        assert np.array_equal(ram[:, e], ram_o.astype(np.float32))
+        assert np.array_equal(scr[:, e], scr_o.astype(np.float32))
+        assert_grad_close(g_ram0[e], o_ram0, f"env {e}: grad_ram0")
+        assert_grad_close(g_u[:, e], o_u, f"env {e}: grad_u")
+        assert_grad_close(g_rom[e, :len(o_rom)], o_rom, f"env {e}: grad_rom")
+    h = C.c_void_p()
+    assert L.vcs_soft_step(b.h, 0.0, p(u_t), n_steps, 1, None, None, C.byref(h), s) == _lib.VCS_ERR_ARG
+    assert not h.value
