@@ -77,6 +77,7 @@ def lib():
         L.ogrf_nodes.argtypes = [vp]
         L.ovcs_set_switches.argtypes = [vp, C.c_uint8]
         L.ovcs_set_sampler.argtypes = [vp, C.c_int]
+        L.ovcs_set_graphics.argtypes = [vp, C.c_int]
         L.ovcs_set_full_tia.argtypes = [vp, C.c_int]
         L.ovcs_set_step_instructions.argtypes = [vp, C.c_int]
         L.ovcs_set_full.argtypes = [vp, C.c_int, C.c_double, C.c_double]
@@ -181,6 +182,11 @@ class Oracle:
         """Switch the differentiable position sampler (Section 3) on or off for
         the soft rollouts that follow."""
         lib().ovcs_set_sampler(self.h, 1 if on else 0)
+
+    def set_graphics(self, on: bool):
+        """Switch the graphics-bit surrogate (Section 3.1's stored-switch
+        paragraph) on or off for the soft rollouts that follow."""
+        lib().ovcs_set_graphics(self.h, 1 if on else 0)
 
     def set_step_instructions(self, n: int):
         """Make every following step run n instruction slots (n > 0) instead

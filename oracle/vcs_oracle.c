@@ -43,6 +43,12 @@
  *  slice j into segment 0, 1 or 2, and segment 3 always shows slice 7; at
  *  power-on segments 0..2 show slices 4, 5, 6.  A relaxed ROM read's tensor
  *  is the 1 KB slice the read's segment shows.
+ *  FE carts (8 KB in two 4 KB banks, the first at power-on): a JSR made
+ *  with the stack pointer at $FF (the return address's low byte pushed to
+ *  $01FE) or an RTS made with it at $FD (the low byte pulled from $01FE)
+ *  selects the bank from bit 5 of the bus byte of the next cycle (the
+ *  target's or the return address's high byte): set -> the first 4 KB,
+ *  clear -> the second.  Other accesses to $01FE switch nothing.
  *  Superchip carts (F8SC, F6SC, F4SC: the banked formats plus 128 bytes of
  *  cartridge RAM) write that RAM at $1000-$107F and read it at $1080-$10FF
  *  of the cartridge window, in every bank; a read of the write port returns
@@ -119,6 +125,7 @@ struct ovcs {
   int mapper, bank;
   int sc;                  /* Superchip variant (cartridge RAM at $1000-$10FF) */
   int e0;                  /* E0 cart: e0seg[k] = the slice segment k (0..2) shows */
+  int fe;                  /* FE cart: two 4 KB banks chosen through JSR and RTS */
   int e0seg[3];
   /* RIOT */
   uint8_t intim;
@@ -148,6 +155,10 @@ struct ovcs {
   int32_t nA, nX, nY, nV, nC[4], nRAM[256];   /* nC: COLUP0, COLUPF, COLUBK, COLUP1 */
   int32_t nPos, nHM;       /* deviations of the P0 position and of HMP0 (sampler) */
   int sampler;             /* 1: the differentiable position sampler is on */
+  /* graphics-bit surrogate: the written values of GRP0, GRP1, ENAM0, ENAM1,
+   * ENABL, PF0, PF1, PF2 (nG) and of the delayed GRP0, GRP1, ENABL (nGo) */
+  int32_t nG[8], nGo[3];
+  int graphics;            /* 1: graphics bits carry gradient */
   int step_instr;          /* > 0: a step is this many instruction slots, not frames */
   /* fully relaxed casts (Section 4's temperature-limit study): 0 = off,
    * 1 = probe (count the casts that would round off the hard value), 2 =
@@ -366,6 +377,72 @@ static double sampler_slope(const ovcs* s, int x) {
   return 0.5 * (double)db * (double)(with - without);
 }
 
+/* Graphics-bit surrogate (Section 3.1, the stored-switch paragraph: sprite
+ * colours and graphics bits are differentiable with the switch stored).
+ * Reading: the pixel's colour is relaxed in the graphics bit that decides
+ * whether object k covers column x, as C_without + (C_with - C_without) b,
+ * where C_with and C_without are the colours the priority logic gives
+ * with that bit forced to 1 and to 0 (the other objects as drawn, colours
+ * & 0xFE); the bit's derivative with respect to its register byte is 1
+ * (the straight-through rule for the shift and mask that extract it, as
+ * for LSR and AND).  So every drawn pixel adds (C_with - C_without) x its
+ * gradient to the byte of each bit in play there: the player's GRP bit at
+ * that column (the delayed copy when VDELP is set), the missile's ENAM and
+ * the ball's ENABL byte where the object's span covers x (the delayed
+ * ENABL with VDELBL; a missile locked to its player is not in play), and
+ * the playfield byte (PF0, PF1 or PF2) of x.  The subset machine has only
+ * player 0 and the playfield. */
+static int player_span(const ovcs* s, int i, int x) {
+  const int mode = s->nusiz[i] & 7, w = 8 * player_scale(mode);
+  const int pos = i ? s->p1pos : s->p0pos;
+  int off[3];
+  const int n = nusiz_copies(mode, off);
+  for (int k = 0; k < n; k++)
+    if (((x - pos - off[k]) % 160 + 160) % 160 < w) return 1;
+  return 0;
+}
+static int missile_span(const ovcs* s, int i, int x) {
+  if (s->resmp[i] & 2) return 0;
+  const int mode = s->nusiz[i] & 7, w = 1 << ((s->nusiz[i] >> 4) & 3);
+  int off[3];
+  const int n = nusiz_copies(mode, off);
+  for (int k = 0; k < n; k++)
+    if (((x - s->mpos[i] - off[k]) % 160 + 160) % 160 < w) return 1;
+  return 0;
+}
+static int ball_span(const ovcs* s, int x) {
+  return ((x - s->blpos) % 160 + 160) % 160 < (1 << ((s->ctrlpf >> 4) & 3));
+}
+/* The playfield register (0 PF0, 1 PF1, 2 PF2) of column x. */
+static int pf_reg(const ovcs* s, int x) {
+  int i = x < 80 ? x / 4 : (x - 80) / 4;
+  if (x >= 80 && (s->ctrlpf & 1)) i = 19 - i;
+  return i < 4 ? 0 : (i < 12 ? 1 : 2);
+}
+static void graphics_seed(ovcs* s, int x, double w) {
+  int b[6] = {player_bit(s, 0, x), missile_bit(s, 0, x), player_bit(s, 1, x), missile_bit(s, 1, x),
+              pf_bit(s, x), ball_bit(s, x)};   /* P0, M0, P1, M1, PF, BL */
+  int32_t node[6] = {0, 0, 0, 0, 0, 0};
+  if (player_span(s, 0, x)) node[0] = (s->vdelp[0] & 1) ? s->nGo[0] : s->nG[0];
+  node[4] = s->nG[5 + pf_reg(s, x)];
+  if (s->full_tia) {
+    if (missile_span(s, 0, x)) node[1] = s->nG[2];
+    if (player_span(s, 1, x)) node[2] = (s->vdelp[1] & 1) ? s->nGo[1] : s->nG[1];
+    if (missile_span(s, 1, x)) node[3] = s->nG[3];
+    if (ball_span(s, x)) node[5] = (s->vdelbl & 1) ? s->nGo[2] : s->nG[4];
+  }
+  for (int k = 0; k < 6; k++) {
+    if (!node[k]) continue;
+    const int keep = b[k];
+    b[k] = 1;
+    const int with = owner_colour(s, owner_of(s, x, b[0], b[1], b[2], b[3], b[4], b[5])) & 0xFE;
+    b[k] = 0;
+    const int without = owner_colour(s, owner_of(s, x, b[0], b[1], b[2], b[3], b[4], b[5])) & 0xFE;
+    b[k] = keep;
+    if (with != without) s->g->seed[node[k]] += w * (double)(with - without);
+  }
+}
+
 /* Pixel at visible column x of the current scanline; *owner = the colour
  * register that owns it (owner_of) or -1 (blanked). */
 static uint8_t pixel(const ovcs* s, int x, int* owner) {
@@ -389,6 +466,7 @@ static void tia_clock(ovcs* s) {
         double w = s->gs[row * SCR_W + x];
         if (s->nC[owner]) s->g->seed[s->nC[owner]] += w;
         if (s->sampler && s->nPos) s->g->seed[s->nPos] += w * sampler_slope(s, x);
+        if (s->graphics) graphics_seed(s, x, w);
       }
     }
   }
@@ -423,9 +501,9 @@ static void tia_write(ovcs* s, int reg, val x) {
     case 0x0A: s->ctrlpf = v; break;
     case 0x0B: s->refp[0] = v; break;
     case 0x0C: s->refp[1] = v; break;
-    case 0x0D: s->pf0 = v; break;
-    case 0x0E: s->pf1 = v; break;
-    case 0x0F: s->pf2 = v; break;
+    case 0x0D: s->pf0 = v; s->nG[5] = x.n; break;
+    case 0x0E: s->pf1 = v; s->nG[6] = x.n; break;
+    case 0x0F: s->pf2 = v; s->nG[7] = x.n; break;
     case 0x10:   /* RESP0: a position from strobe timing carries no deviation */
       s->p0pos = s->hclk < 68 ? 3 : (s->hclk - 68 + 5) % 160;
       s->nPos = 0;
@@ -438,11 +516,14 @@ static void tia_write(ovcs* s, int reg, val x) {
     case 0x14: s->blpos = s->hclk < 68 ? 2 : (s->hclk - 68 + 4) % 160; break;
     /* vertical delay: a GRP0 write copies GRP1 to its delayed register, a
      * GRP1 write copies GRP0 and ENABL to theirs */
-    case 0x1B: s->grp0 = v; s->grpo[1] = s->grp1; break;
-    case 0x1C: s->grp1 = v; s->grpo[0] = s->grp0; s->enablo = s->enabl; break;
-    case 0x1D: s->enam[0] = v; break;
-    case 0x1E: s->enam[1] = v; break;
-    case 0x1F: s->enabl = v; break;
+    case 0x1B: s->grp0 = v; s->grpo[1] = s->grp1; s->nG[0] = x.n; s->nGo[1] = s->nG[1]; break;
+    case 0x1C:
+      s->grp1 = v; s->grpo[0] = s->grp0; s->enablo = s->enabl;
+      s->nG[1] = x.n; s->nGo[0] = s->nG[0]; s->nGo[2] = s->nG[4];
+      break;
+    case 0x1D: s->enam[0] = v; s->nG[2] = x.n; break;
+    case 0x1E: s->enam[1] = v; s->nG[3] = x.n; break;
+    case 0x1F: s->enabl = v; s->nG[4] = x.n; break;
     case 0x20: s->hmp0 = v; s->nHM = x.n; break;
     case 0x21: s->hmp1 = v; break;
     case 0x22: s->hmm[0] = v; break;
@@ -512,9 +593,10 @@ static void tick(ovcs* s) {
 static void idle(ovcs* s) { tick(s); }
 
 /* The banked format under a Superchip variant (F8SC -> F8, ...). */
-static int base_mapper(const ovcs* s) { return s->sc ? s->mapper - 3 : s->mapper; }
+static int base_mapper(const ovcs* s) { return s->fe ? 2 : s->sc ? s->mapper - 3 : s->mapper; }
 
 static void hotspot(ovcs* s, uint16_t a) {
+  if (s->fe) return;   /* FE has no hotspot: see fe_switch */
   if (s->e0) {   /* $1FE0-$1FE7, $1FE8-$1FEF, $1FF0-$1FF7: segment 0, 1, 2 */
     if (a >= 0x1FE0 && a <= 0x1FF7) s->e0seg[(a - 0x1FE0) / 8] = (a - 0x1FE0) % 8;
     return;
@@ -526,6 +608,18 @@ static void hotspot(ovcs* s, uint16_t a) {
     s->bank = a - first[m];
   }
 }
+
+/* FE (8 KB, two 4 KB banks): the cartridge watches the bus for an access
+ * to $01FE and takes the bank from bit 5 of the byte on the data bus in the
+ * next cycle: set (a high address byte $Fx) shows the image's first 4 KB,
+ * clear ($Dx) the second.  Reading: the accesses modelled are the two that
+ * the format's carts switch with, made at the top of the stack: a JSR
+ * whose push of the return address's low byte lands on $01FE (the stack
+ * pointer was $FF; the next cycle fetches the target's high byte) and an
+ * RTS whose pull of the low byte reads $01FE (the stack pointer was $FD;
+ * the next cycle pulls the high byte).  The byte decides the bank from the
+ * cycle after it on; power-on shows the first 4 KB. */
+static void fe_switch(ovcs* s, uint8_t next_byte) { s->bank = (next_byte & 0x20) ? 0 : 1; }
 
 /* Superchip ports: cell of the cartridge RAM read (write) at cartridge
  * address a, or -1. */
@@ -1033,17 +1127,21 @@ static void exec(ovcs* s) {
       idle(s);
       val ph = {(uint8_t)(s->pc >> 8), 0};
       val pl = {(uint8_t)(s->pc & 0xFF), 0};
+      const int fe = s->fe && s->SP == 0xFF;   /* the low byte goes to $01FE */
       push(s, ph);
       push(s, pl);
       uint8_t hi = rd(s, s->pc).v;
+      if (fe) fe_switch(s, hi);
       s->pc = (uint16_t)(lo | (hi << 8));
       return;
     }
     case 0x60: {
       idle(s);
       idle(s);
+      const int fe = s->fe && s->SP == 0xFD;   /* the low byte comes from $01FE */
       uint8_t lo = pull(s).v;
       uint8_t hi = pull(s).v;
+      if (fe) fe_switch(s, hi);
       idle(s);
       s->pc = (uint16_t)((lo | (hi << 8)) + 1);
       return;
@@ -1160,8 +1258,8 @@ static int step_instruction(ovcs* s) {
 /* ------------------------------------------------------------------ */
 
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
-  static const uint32_t sz[9] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768, 8192};
-  if (mapper < 0 || mapper > 8 || rom_size != sz[mapper]) return NULL;
+  static const uint32_t sz[10] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768, 8192, 8192};
+  if (mapper < 0 || mapper > 9 || rom_size != sz[mapper]) return NULL;
   ovcs* s = (ovcs*)calloc(1, sizeof(ovcs));
   s->rom = (uint8_t*)malloc(rom_size);
   memcpy(s->rom, rom, rom_size);
@@ -1169,6 +1267,7 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
   s->mapper = mapper;
   s->sc = mapper >= 5 && mapper <= 7;
   s->e0 = mapper == 8;
+  s->fe = mapper == 9;
   s->ystart = ystart;
   ovcs_reset(s);
   return s;
@@ -1176,6 +1275,7 @@ ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart) {
 
 void ovcs_set_switches(ovcs* s, uint8_t swchb) { s->swchb = swchb; }
 void ovcs_set_sampler(ovcs* s, int on) { s->sampler = on != 0; }
+void ovcs_set_graphics(ovcs* s, int on) { s->graphics = on != 0; }
 void ovcs_set_full_tia(ovcs* s, int on) { s->full_tia = on != 0; }
 void ovcs_set_step_instructions(ovcs* s, int n) { s->step_instr = n > 0 ? n : 0; }
 
@@ -1202,7 +1302,8 @@ void ovcs_reset(ovcs* s) {
   s->cyc = 0;
   s->jammed = 0;
   memset(s->ram, 0, sizeof s->ram);
-  s->bank = s->mapper >= 2 && !s->e0 ? (int)(s->rom_size / 4096) - 1 : 0;   /* banked carts: the last bank */
+  /* F8 / F6 / F4 and their Superchip variants: the last bank; FE: the first */
+  s->bank = s->mapper >= 2 && !s->e0 && !s->fe ? (int)(s->rom_size / 4096) - 1 : 0;
   s->e0seg[0] = 4;
   s->e0seg[1] = 5;
   s->e0seg[2] = 6;
@@ -1406,6 +1507,8 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   s->nA = s->nX = s->nY = s->nV = 0;
   s->nC[0] = s->nC[1] = s->nC[2] = s->nC[3] = 0;
   s->nPos = s->nHM = 0;
+  memset(s->nG, 0, sizeof s->nG);
+  memset(s->nGo, 0, sizeof s->nGo);
   s->gs_all = grad_screen;
   for (int t = 0; t < n_steps; t++) {
     int bits[5];
@@ -1427,6 +1530,8 @@ ogrf* ovcs_soft_rollout(ovcs* s, const double* u, int n_steps, int frame_skip,
   s->nA = s->nX = s->nY = s->nV = 0;
   s->nC[0] = s->nC[1] = s->nC[2] = s->nC[3] = 0;
   s->nPos = s->nHM = 0;
+  memset(s->nG, 0, sizeof s->nG);
+  memset(s->nGo, 0, sizeof s->nGo);
   return g;
 }
 

@@ -4,8 +4,8 @@
  * A plain, slow, cycle-by-cycle emulator of the Atari VCS (6507 CPU, RIOT,
  * TIA video: by default the subset of player 0, playfield and background,
  * or with ovcs_set_full_tia the whole TIA with player 1, missiles, ball and
- * collisions; 2K, 4K, F8, F6, F4, the Superchip variants of the last three
- * and E0 cartridges) written from the paper's machine description (Section
+ * collisions; 2K, 4K, F8, F6, F4, the Superchip variants of the last three,
+ * E0 and FE cartridges) written from the paper's machine description (Section
  * 2.2 and the architecture figure) and the public chip documentation (MOS
  * 6500 manuals, 6532 datasheet, TIA programmer's guide, the published note
  * on NMOS decimal mode).  Every CPU cycle is charged before its bus access;
@@ -68,8 +68,11 @@ typedef struct {
  * bank j; 5, 6, 7 = F8SC, F6SC, F4SC: the same with 128 bytes of cartridge
  * RAM written at $1000-$107F and read at $1080-$10FF; 8 = E0 (8 KB in eight
  * 1 KB slices; an access to $1FE0+j / $1FE8+j / $1FF0+j maps slice j into
- * segment 0 / 1 / 2 of the window, segment 3 shows slice 7).  rom is
- * copied.  NULL on a bad size. */
+ * segment 0 / 1 / 2 of the window, segment 3 shows slice 7); 9 = FE (8 KB
+ * in two 4 KB banks, the first shown at power-on: a JSR made with the stack
+ * pointer at $FF or an RTS made with it at $FD selects the bank from bit 5
+ * of the high address byte it moves next: set -> the first 4 KB, clear ->
+ * the second).  rom is copied.  NULL on a bad size. */
 ovcs* ovcs_new(const uint8_t* rom, uint32_t rom_size, int mapper, int ystart);
 void ovcs_free(ovcs* s);
 /* Power-on state (A7 of the design notes). */
@@ -80,6 +83,14 @@ void ovcs_set_switches(ovcs* s, uint8_t swchb);
 /* Differentiable position sampler (Section 3) in soft rollouts: 1 = on.
  * Off by default; the hard outputs do not depend on it. */
 void ovcs_set_sampler(ovcs* s, int on);
+/* Graphics-bit surrogate (Section 3.1's stored-switch paragraph) in soft
+ * rollouts: 1 = on.  Every drawn pixel adds (C_with - C_without) x its
+ * gradient to the register byte of each graphics bit deciding an object's
+ * coverage there (GRP0 / GRP1 or their delayed copies, ENAM0 / ENAM1,
+ * ENABL or its delayed copy, PF0 / PF1 / PF2), C_with and C_without being
+ * the pixel's colours with that bit forced to 1 and to 0.  Off by default;
+ * the hard outputs do not depend on it. */
+void ovcs_set_graphics(ovcs* s, int on);
 /* Instruction-granular steps (the paper's throughput unit: one step = one
  * emulated instruction): n > 0 makes every following step (ovcs_step, soft
  * rollouts) run n instruction slots (an executed instruction, or a jammed

@@ -15,7 +15,8 @@ increment 0x9E3779B97F4A7C15 passed through the variant-13 finaliser.
 
 Cartridge shapes follow the paper's workloads: the 2K, 4K and F8 mappers of
 the conformance set (per-game table, supplement; F6, F4, the Superchip
-variants and E0 widen it to the nine mappers of Section 3), 128 B of RIOT
+variants and E0 widen it to the nine mappers of Section 3, and FE to the
+ten formats the conformance table's caption counts), 128 B of RIOT
 RAM, a 160x210 screen window and NTSC frames of about 262 scanlines (Section 2.2).
 """
 from __future__ import annotations
@@ -37,8 +38,14 @@ MAPPER_SC_BASE = {MAPPER_F8SC: MAPPER_F8, MAPPER_F6SC: MAPPER_F6, MAPPER_F4SC: M
 # always shows slice 7
 MAPPER_E0 = 8
 E0_HOTSPOT = (0x1FE0, 0x1FE8, 0x1FF0)
+# FE: 8 KB in two 4 KB banks; a JSR made with the stack pointer at $FF (its
+# return address's low byte pushed to $01FE) or an RTS made with it at $FD
+# (the low byte pulled from $01FE) selects the bank from bit 5 of the next
+# byte on the bus (the target's or the return address's high byte): set
+# ($Fx) the image's first 4 KB, clear ($Dx) the second
+MAPPER_FE = 9
 MAPPER_SIZE = {MAPPER_2K: 2048, MAPPER_4K: 4096, MAPPER_F8: 8192, MAPPER_F6: 16384, MAPPER_F4: 32768,
-               MAPPER_F8SC: 8192, MAPPER_F6SC: 16384, MAPPER_F4SC: 32768, MAPPER_E0: 8192}
+               MAPPER_F8SC: 8192, MAPPER_F6SC: 16384, MAPPER_F4SC: 32768, MAPPER_E0: 8192, MAPPER_FE: 8192}
 # banked mappers: number of 4 KB banks and the first hotspot (bank j at hot + j)
 MAPPER_BANKS = {MAPPER_F8: 2, MAPPER_F6: 4, MAPPER_F4: 8, MAPPER_F8SC: 2, MAPPER_F6SC: 4, MAPPER_F4SC: 8}
 MAPPER_HOTSPOT = {MAPPER_F8: 0x1FF8, MAPPER_F6: 0x1FF6, MAPPER_F4: 0x1FF4,
@@ -705,6 +712,8 @@ _FULL_TIA = [False]
 def _generate_cart(seed: int, cart: int, mapper: int) -> bytes:
     if mapper == MAPPER_E0:
         return _generate_e0(seed, cart)
+    if mapper == MAPPER_FE:
+        return _generate_fe(seed, cart)
     sc = mapper in MAPPER_SC_BASE
     mapper = MAPPER_SC_BASE.get(mapper, mapper)
     if mapper in (MAPPER_F6, MAPPER_F4):
@@ -992,6 +1001,130 @@ def _generate_multibank(seed: int, cart: int, mapper: int, sc: bool = False) -> 
         b.word("IRQ")
         banks[k] = bytes(b.resolve())
     return b"".join(banks[k] for k in range(nb))
+
+
+def _generate_fe(seed: int, cart: int) -> bytes:
+    """FE image: bank 0 (the image's first 4 KB, addressed $F000-$FFFF,
+    shown at power-on) holds the init, the frame loop, the VBLANK and
+    overscan work and one visible kernel; bank 1 (addressed $D000-$DFFF)
+    holds another visible kernel.  Each frame the loop, at the top of the
+    stack, calls one of the two kernels as a subroutine, picked from the
+    joystick and a work cell: JSR $D000 switches to bank 1 (the target's
+    high byte has bit 5 clear), and the kernel's RTS switches back (the
+    return address's high byte, $Fx, has it set); JSR to the bank-0 kernel
+    keeps bank 0.  The random work's own subroutine calls run deeper in the
+    stack and switch nothing."""
+    r = SplitMix64(seed, cart, 0x0CA7)
+    n_lines, vb_budget, vb_loops, os_budget = 16, 1000, 2, 900
+    bank_size, irq = 4096, 4096 - 0x20
+    a = Asm(0xF000, bank_size)
+    g = _Gen(r, a)
+    g.emit_subs(4)
+    a.label("RESET")
+    a.op("SEI")
+    a.op("CLD")
+    a.op("LDX", "imm", 0xFF)
+    a.op("TXS")
+    a.op("LDA", "imm", 0)
+    a.op("LDX", "imm", 0x7F)
+    a.label("CLR")
+    a.op("STA", "zpx", 0x80)
+    a.op("DEX")
+    a.op("BPL", "rel", "CLR")
+    a.op("LDA", "imm", RAM_PTR_TARGET & 0xFF)
+    a.op("STA", "zp", RAM_PTR)
+    a.op("LDA", "imm", RAM_PTR_TARGET >> 8)
+    a.op("STA", "zp", RAM_PTR + 1)
+    a.op("LDA", "imm", ("<", "TABLE"))
+    a.op("STA", "zp", ROM_PTR)
+    a.op("LDA", "imm", (">", "TABLE"))
+    a.op("STA", "zp", ROM_PTR + 1)
+    for _ in range(r.range(4, 10)):
+        a.op("LDA", "imm", r.below(256))
+        a.op("STA", "zp", g.work_cell())
+    for reg in (COLUP0, COLUPF, COLUBK):
+        a.op("LDA", "imm", r.below(256))
+        a.op("STA", "zp", reg)
+    a.op("LDA", "imm", r.pick((0, 1, 4, 5)))
+    a.op("STA", "zp", CTRLPF)
+    a.label("FRAME")
+    a.op("LDA", "imm", 2)
+    a.op("STA", "zp", VBLANK)
+    a.op("STA", "zp", WSYNC)
+    a.op("STA", "zp", VSYNC)
+    for _ in range(3):
+        a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 0)
+    a.op("STA", "zp", VSYNC)
+    a.op("LDA", "imm", VBLANK_TIMER)
+    a.op("STA", "abs", TIM64T)
+    a.op("LDA", "imm", vb_loops)
+    a.op("STA", "zp", WORK_CTR)
+    a.label("VBL")
+    a.op("JSR", "abs", "VBWORK")
+    a.op("DEC", "zp", WORK_CTR)
+    a.op("BNE", "rel", "VBL")
+    a.label("VBWAIT")
+    a.op("LDA", "abs", INTIM)
+    a.op("BNE", "rel", "VBWAIT")
+    a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 0)
+    a.op("STA", "zp", VBLANK)
+    # this frame's kernel: bank 1's (through the FE switch) or bank 0's
+    a.op("LDA", "abs", SWCHA)
+    a.op("EOR", "zp", WORK_LO)
+    a.op("AND", "imm", 0x30)
+    a.op("BEQ", "rel", "KF")
+    a.op("JSR", "abs", 0xD000)
+    a.op("JMP", "abs", "OVERSCAN")
+    a.label("KF")
+    a.op("JSR", "abs", "KERNEL")
+    a.label("OVERSCAN")
+    a.op("STA", "zp", WSYNC)
+    a.op("LDA", "imm", 2)
+    a.op("STA", "zp", VBLANK)
+    a.op("LDA", "imm", OVERSCAN_TIMER)
+    a.op("STA", "abs", TIM64T)
+    a.cycles = 0
+    g.random_work(os_budget)
+    a.label("OSWAIT")
+    a.op("LDA", "abs", INTIM)
+    a.op("BNE", "rel", "OSWAIT")
+    a.op("JMP", "abs", "FRAME")
+    a.label("VBWORK")
+    a.cycles = 0
+    g.random_work(vb_budget)
+    a.op("RTS")
+    g.emit_ptrs()
+    a.label("KERNEL")
+    _emit_kernel(a, g, n_lines, "KRET")
+    a.label("KRET")
+    a.op("RTS")
+    _emit_table(a, r)
+    a.at(irq)
+    a.label("IRQ")
+    a.op("RTI")
+    a.at(bank_size - 6)
+    a.word("IRQ")
+    a.word("RESET")
+    a.word("IRQ")
+    bank0 = bytes(a.resolve())
+
+    b = Asm(0xD000, bank_size)
+    g1 = _Gen(SplitMix64(seed, cart, 0x0CA8), b)
+    b.label("KERNEL1")
+    _emit_kernel(b, g1, n_lines, "KRET1")
+    b.label("KRET1")
+    b.op("RTS")
+    _emit_table(b, g1.r)
+    b.at(irq)
+    b.label("IRQ")
+    b.op("RTI")
+    b.at(bank_size - 6)
+    b.word("IRQ")
+    b.word("IRQ")
+    b.word("IRQ")
+    return bank0 + bytes(b.resolve())
 
 
 def _generate_e0(seed: int, cart: int) -> bytes:

@@ -254,3 +254,49 @@ def full_branch_rom(offset, taken):
     a.word(0xF000)
     a.word(0xF000)
     return bytes(a.resolve())
+
+
+GRAPHICS_COLOURS = {"bk": 0x20, "pf": 0x44, "p0": 0x86}
+GRAPHICS_PF = (0xA0, 0x5C, 0x93)   # PF0, PF1, PF2
+
+
+def graphics_rom(ctrlpf=0):
+    """Player 0 over a playfield, both drawn on every visible line: each
+    frame strobes RESP0 mid-way through scanline 1 (a fixed position),
+    copies SWCHA into GRP0 (the joystick drives the sprite's bits) and
+    stores PF0, PF1 and PF2 from immediates.  Returns (image, the ROM
+    offsets of the PF0, PF1 and PF2 immediates)."""
+    offs = []
+
+    def build(a):
+        a.op("LDA", "imm", GRAPHICS_COLOURS["bk"])
+        a.op("STA", "zp", 0x09)
+        a.op("LDA", "imm", GRAPHICS_COLOURS["pf"])
+        a.op("STA", "zp", 0x08)
+        a.op("LDA", "imm", GRAPHICS_COLOURS["p0"])
+        a.op("STA", "zp", 0x06)
+        a.op("LDA", "imm", ctrlpf)
+        a.op("STA", "zp", 0x0A)
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)            # VSYNC on: the frame boundary
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        a.op("STA", "zp", 0x02)            # WSYNC
+        for _ in range(20):
+            a.op("NOP")
+        a.op("STA", "zp", 0x10)            # RESP0
+        a.op("LDA", "abs", 0x0280)         # SWCHA
+        a.op("STA", "zp", 0x1B)            # GRP0
+        for reg, v in zip((0x0D, 0x0E, 0x0F), GRAPHICS_PF):
+            offs.append(a.pc + 1 - 0xF000)
+            a.op("LDA", "imm", v)
+            a.op("STA", "zp", reg)
+        a.op("LDX", "imm", 0)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("DEX")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "FRAME")
+    return rom4k(build, table=False), offs

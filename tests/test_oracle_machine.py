@@ -575,6 +575,101 @@ def test_e0_carts_map_several_slices():
     assert {0, 1} <= seen[0] and {2, 3, 4} <= seen[1] and {5, 6} <= seen[2]
 
 
+def _fe_image():
+    """Bank 0 ($F000, the image's first 4 KB) and bank 1 ($D000): each has
+    the marker A0 / B1 at offset $800, read as LDA $F800 (the address's top
+    bits do not reach the cartridge)."""
+    b0 = synth.Asm(0xF000, 4096)
+    b0.op("JMP", "abs", 0xF100)
+    b0.at(0x010)                       # $D010 seen through bank 0
+    b0.op("LDA", "abs", 0xF800)
+    b0.op("STA", "zp", 0x84)
+    b0.op("RTS")
+    b0.at(0x100)
+    b0.op("LDX", "imm", 0xFF)
+    b0.op("TXS")
+    b0.op("LDA", "abs", 0xF800)        # power-on: bank 0
+    b0.op("STA", "zp", 0x80)
+    b0.op("JSR", "abs", 0xD000)        # S = $FF, target high byte $D0: bank 1
+    b0.op("LDA", "abs", 0xF800)        # its RTS (S = $FD, return high byte $F1): bank 0
+    b0.op("STA", "zp", 0x83)
+    b0.op("LDA", "imm", 0)
+    b0.op("PHA")
+    b0.op("PHA")                       # S = $FD
+    b0.op("JSR", "abs", 0xD010)        # not from the top of the stack: no switch
+    b0.op("PLA")
+    b0.op("PLA")
+    b0.op("LDX", "imm", 0xFE)
+    b0.op("TXS")
+    b0.op("PHA")                       # a push to $01FE (then STA's opcode $8D, bit 5 clear)
+    b0.op("STA", "zp", 0x87)
+    b0.op("LDA", "abs", 0xF800)        # not a JSR or RTS: no switch
+    b0.op("STA", "zp", 0x88)
+    b0.op("LDX", "imm", 0xFF)
+    b0.op("TXS")
+    b0.op("LDA", "imm", 0xD0)
+    b0.op("PHA")
+    b0.op("LDA", "imm", 0x1F)
+    b0.op("PHA")                       # S = $FD; $01FE holds $1F, $01FF $D0
+    b0.op("RTS")                       # pulls $D01F: bank 1, continues at $D020
+    b0.at(0x200)
+    b0.op("LDA", "abs", 0xF800)        # reached from bank 1 by JSR $F200 (high byte $F2)
+    b0.op("STA", "zp", 0x86)
+    b0.label("HALT")
+    b0.op("JMP", "abs", "HALT")
+    b0.at(0x800)
+    b0.byte(0xA0)
+    b0.at(4096 - 6)
+    b0.word(0xF100), b0.word(0xF100), b0.word(0xF100)
+    b1 = synth.Asm(0xD000, 4096)
+    b1.op("LDA", "abs", 0xF800)
+    b1.op("STA", "zp", 0x81)
+    b1.op("RTS")
+    b1.at(0x020)
+    b1.op("LDA", "abs", 0xF800)
+    b1.op("STA", "zp", 0x85)
+    b1.op("JSR", "abs", 0xF200)        # S = $FF again, high byte $F2: bank 0
+    b1.at(0x800)
+    b1.byte(0xB1)
+    b1.at(4096 - 6)
+    b1.word(0xD000), b1.word(0xD000), b1.word(0xD000)
+    return bytes(b0.resolve()) + bytes(b1.resolve())
+
+
+def test_fe_switches_through_jsr_and_rts_at_the_top_of_the_stack():
+    """FE (two 4 KB banks, the image's first shown at power-on): a JSR with
+    the stack pointer at $FF and an RTS with it at $FD select the bank from
+    bit 5 of the next bus byte (the target's, or the return address's, high
+    byte: set -> the first 4 KB, clear -> the second); a JSR deeper in the
+    stack and a plain push to $01FE switch nothing."""
+    o = oracle.Oracle(_fe_image(), synth.MAPPER_FE)
+    assert o.bank() == 0
+    for _ in range(60):
+        o.exec_one()
+    ram = o.ram()
+    assert list(ram[0:2]) == [0xA0, 0xB1]
+    assert list(ram[3:7]) == [0xA0, 0xA0, 0xB1, 0xA0]
+    assert ram[8] == 0xA0
+    assert o.bank() == 0
+
+
+def test_fe_carts_use_both_banks():
+    """The generated FE carts run well-formed frames and spend frames in
+    both banks' kernels."""
+    rom = synth.config_carts(23, [synth.MAPPER_FE])[0]
+    assert len(rom) == 8192
+    o = oracle.Oracle(rom, synth.MAPPER_FE)
+    seen = set()
+    for a in synth.actions(24, 1, 40)[:, 0]:
+        for _ in range(400):
+            o.trace(int(a), 1)
+            seen.add(int(o.state()[8]))
+    c = o.counters()
+    assert c["watchdog"] == 0 and o.state()[28] == 0
+    assert 1500 < c["instructions"] / c["frames"] < 4000
+    assert seen == {0, 1}
+
+
 # ---------------------------------------------------------------------------
 # the rest of the TIA: player 1, missiles, ball, sizes, delays, collisions
 # (expected pixels worked out by hand from the register definitions)
