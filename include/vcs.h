@@ -3,7 +3,7 @@
  *
  * The machine is the paper's VCS (Section 2.2, the architecture figure): a
  * 6507 CPU executing a cartridge ROM (2K, 4K, the F8 / F6 / F4 bank-switched
- * formats, their Superchip variants with 128 B of cartridge RAM, or E0), the
+ * formats, their Superchip variants with 128 B of cartridge RAM, E0 or FE), the
  * RIOT (128 B of RAM, interval timer, joystick and console-switch ports) and
  * the TIA, which turns register writes into 160x210 palette-index frames one
  * colour clock at a time (player 0, playfield and background by default;
@@ -64,8 +64,18 @@ typedef enum {
  * an access to $1FE0+j, $1FE8+j or $1FF0+j maps slice j into segment 0, 1
  * or 2, segment 3 always shows slice 7, and power-on shows slices 4, 5, 6.
  * A relaxed ROM read's tensor is the slice its segment shows. */
+/* FE (8 KB, two 4 KB banks; the conformance table of Section 5 counts it
+ * among the implemented formats): the cartridge takes the bank from bit 5
+ * of the bus byte that follows an access to $01FE.  Reading: the accesses
+ * modelled are a JSR made with the stack pointer at $FF (it pushes the
+ * return address's low byte to $01FE, then fetches the target's high byte)
+ * and an RTS made with it at $FD (it pulls the low byte from $01FE, then
+ * the high byte); bit 5 set ($Fx) shows the image's first 4 KB, clear ($Dx)
+ * the second; power-on shows the first.  A relaxed ROM read's tensor is
+ * the current 4 KB bank. */
 enum { VCS_MAPPER_2K = 0, VCS_MAPPER_4K = 1, VCS_MAPPER_F8 = 2, VCS_MAPPER_F6 = 3, VCS_MAPPER_F4 = 4,
-       VCS_MAPPER_F8SC = 5, VCS_MAPPER_F6SC = 6, VCS_MAPPER_F4SC = 7, VCS_MAPPER_E0 = 8 };
+       VCS_MAPPER_F8SC = 5, VCS_MAPPER_F6SC = 6, VCS_MAPPER_F4SC = 7, VCS_MAPPER_E0 = 8,
+       VCS_MAPPER_FE = 9 };
 
 /* Per-env status bits reported by vcs_step / vcs_rollout. */
 enum {
@@ -168,7 +178,10 @@ typedef struct vcs_loss_weights {
  *   8192 -> E0 when the image holds an absolute load, store, BIT or NOP
  *           (opcodes $AD $8D $2C $0C) of a cartridge mirror of an E0
  *           hotspot ($1FE0-$1FF7 after masking to 13 bits) and no such
- *           access to the F8 hotspots $1FF8-$1FF9; else F8SC or F8;
+ *           access to the F8 hotspots $1FF8-$1FF9; else FE when it holds
+ *           no such access to the F8 hotspots and a JSR ($20) to
+ *           $D000-$DFFF (a call into an FE image's second bank); else F8SC
+ *           or F8;
  *   16384 -> F6SC or F6; 32768 -> F4SC or F4;
  * where the Superchip variant is chosen when every 4 KB bank repeats its
  * first 128 bytes in the next 128 (the RAM ports hide those 256 bytes, so
@@ -183,7 +196,8 @@ vcs_status vcs_config_default(vcs_config* cfg);
  * "ROM as a weight tensor", Section 3.1).
  *  roms[c]      host pointer to cart c's image (rom_sizes[c] bytes: 2048,
  *               4096, 8192, 16384 or 32768 for mapper 2K, 4K, F8, F6, F4;
- *               8192, 16384, 32768 for F8SC, F6SC, F4SC; 8192 for E0);
+ *               8192, 16384, 32768 for F8SC, F6SC, F4SC; 8192 for E0 and
+ *               FE);
  *               copied.
  *  mappers[c]   VCS_MAPPER_* of cart c.
  *  env_cart     host int32[n_envs]: the cart of each env (0..n_carts-1).

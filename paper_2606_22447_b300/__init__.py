@@ -13,14 +13,14 @@ import numpy as np
 
 from . import _lib
 from ._lib import ENV_DONE, ENV_JAMMED, ENV_WATCHDOG, Config, VcsError
-from .synth import (MAPPER_2K, MAPPER_4K, MAPPER_E0, MAPPER_F4, MAPPER_F4SC, MAPPER_F6, MAPPER_F6SC, MAPPER_F8,
+from .synth import (MAPPER_2K, MAPPER_4K, MAPPER_E0, MAPPER_F4, MAPPER_F4SC, MAPPER_F6, MAPPER_F6SC, MAPPER_F8, MAPPER_FE,
                     MAPPER_F8SC, MAPPER_SIZE)
 
 SCREEN_H, SCREEN_W, RAM_BYTES = 210, 160, 128
 
 __all__ = ["Batch", "Tape", "Graph", "Config", "VcsError", "default_config", "autotune_cache_clear", "detect_mapper",
            "MAPPER_2K", "MAPPER_4K", "MAPPER_F8", "MAPPER_F6", "MAPPER_F4", "MAPPER_F8SC", "MAPPER_F6SC", "MAPPER_F4SC",
-           "MAPPER_E0", "MAPPER_SIZE", "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
+           "MAPPER_E0", "MAPPER_FE", "MAPPER_SIZE", "ENV_WATCHDOG", "ENV_JAMMED", "ENV_DONE"]
 
 
 def default_config(**overrides) -> Config:

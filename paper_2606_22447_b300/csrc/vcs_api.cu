@@ -228,6 +228,15 @@ static int abs_accesses(const uint8_t* rom, uint32_t size, uint32_t lo, uint32_t
   return n;
 }
 
+// JSR instructions whose target's high byte is $D0-$DF: a call into the
+// second bank of an FE image (its first bank is addressed at $F000, its
+// second at $D000; bit 5 of the high byte selects the bank).
+static int fe_calls(const uint8_t* rom, uint32_t size) {
+  int n = 0;
+  for (uint32_t i = 0; i + 2 < size; i++) n += rom[i] == 0x20 && (rom[i + 2] & 0xF0) == 0xD0;
+  return n;
+}
+
 vcs_status vcs_detect_mapper(const uint8_t* rom, uint32_t size, uint8_t* mapper) {
   if (!rom || !mapper) return vcs_fail(nullptr, VCS_ERR_ARG, "rom and mapper must not be NULL");
   switch (size) {
@@ -236,6 +245,10 @@ vcs_status vcs_detect_mapper(const uint8_t* rom, uint32_t size, uint8_t* mapper)
     case 8192:
       if (abs_accesses(rom, size, 0x1FE0, 0x1FF7) > 0 && abs_accesses(rom, size, 0x1FF8, 0x1FF9) == 0) {
         *mapper = VCS_MAPPER_E0;
+        return VCS_OK;
+      }
+      if (abs_accesses(rom, size, 0x1FF8, 0x1FF9) == 0 && fe_calls(rom, size) > 0) {
+        *mapper = VCS_MAPPER_FE;
         return VCS_OK;
       }
       *mapper = superchip_filler(rom, size) ? VCS_MAPPER_F8SC : VCS_MAPPER_F8;
@@ -268,10 +281,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if (!roms || !rom_sizes || !mappers || !env_cart)
     return vcs_fail(nullptr, VCS_ERR_ARG, "null roms / rom_sizes / mappers / env_cart");
   if (n_carts <= 0 || n_envs <= 0) return vcs_fail(nullptr, VCS_ERR_ARG, "n_carts and n_envs must be positive");
-  static const uint32_t want[9] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768, 8192};
+  static const uint32_t want[10] = {2048, 4096, 8192, 16384, 32768, 8192, 16384, 32768, 8192, 8192};
   uint32_t rom_stride = 8192;   // the largest image, at least 8 KB
   for (int c = 0; c < n_carts; c++) {
-    if (mappers[c] > VCS_MAPPER_E0)
+    if (mappers[c] > VCS_MAPPER_FE)
       return vcs_fail(nullptr, VCS_ERR_MAPPER, "cart %d: unknown mapper %d", c, mappers[c]);
     if (rom_sizes[c] != want[mappers[c]])
       return vcs_fail(nullptr, VCS_ERR_ROM_SIZE, "cart %d: %u bytes for mapper %d (want %u)", c, rom_sizes[c],
@@ -364,6 +377,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     }
     if (mappers[c] == VCS_MAPPER_E0) {
       banks[c] = (uint8_t)kCartE0;
+      b->xmap = 1;
+    }
+    if (mappers[c] == VCS_MAPPER_FE) {   // two banks, switched by JSR / RTS: the extended kernels
+      banks[c] = (uint8_t)(2u | kCartFE);
       b->xmap = 1;
     }
     is2k[c] = mappers[c] == VCS_MAPPER_2K;
@@ -620,10 +637,10 @@ static std::string tune_key(const vcs_batch* b, int32_t frame_skip, bool ram, bo
   cudaGetDevice(&dev);
   cudaDeviceProp prop;
   std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "?";
-  int per_mapper[VCS_MAPPER_E0 + 1] = {};
+  int per_mapper[VCS_MAPPER_FE + 1] = {};
   for (int e = 0; e < b->n_envs; e++) per_mapper[b->mapper[b->env_cart[e]]]++;
   std::string mix;
-  for (int m = 0; m <= VCS_MAPPER_E0; m++) mix += "|" + std::to_string(per_mapper[m]);
+  for (int m = 0; m <= VCS_MAPPER_FE; m++) mix += "|" + std::to_string(per_mapper[m]);
   char buf[256];
   snprintf(buf, sizeof buf, "|%d|%d|%d|%d|%d|%d|%d", b->sms, b->n_envs, b->n_carts, frame_skip,
            (ram ? 1 : 0) | (screen ? 2 : 0), b->cfg.step_instructions, b->cfg.full_tia);

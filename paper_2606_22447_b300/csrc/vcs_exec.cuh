@@ -588,11 +588,16 @@ __device__ __forceinline__ void exec_op(const Ctx& c, Regs& r, Step& st, uint32_
     const uint32_t ret = (opaddr + 2) & 0xFFFF;
     r.PC = b1 | (b2 << 8);
     p.nw = 2; p.wstack = true; p.wv = (ret >> 8) | ((ret & 0xFF) << 8); p.widx = 4;
+    // FE: the return address's low byte goes to $01FE and the next cycle
+    // fetches the target's high byte, whose bit 5 picks the bank
+    if (c.fe && r.SP == 0xFFu) r.bank = (b2 & 0x20u) ? 0u : 1u;
   }
   else if constexpr (id == OP_RTS) {
+    const bool fe = c.fe && r.SP == 0xFDu;   // FE: the low byte comes from $01FE
     const uint32_t lo = pull<FM>(c, r, st, 4);
     const uint32_t hi = pull<FM>(c, r, st, 5);
     r.PC = ((lo | (hi << 8)) + 1) & 0xFFFF;
+    if (fe) r.bank = (hi & 0x20u) ? 0u : 1u;
   }
   else if constexpr (id == OP_RTI) {
     const uint32_t pp = pull<FM>(c, r, st, 4);

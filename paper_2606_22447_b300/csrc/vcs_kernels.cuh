@@ -31,11 +31,13 @@ constexpr int kStateWords = kSoAFields + 64;   // per env
 
 // Per-cart bank byte: the 4 KB banks of a bank-switched cart (2, 4, 8; 0 for
 // 2K, 4K and E0 images) | kCartSC for the Superchip variants | kCartE0 for
-// E0 (eight 1 KB slices).
-constexpr uint32_t kCartSC = 0x80, kCartE0 = 0x40;
+// E0 (eight 1 KB slices) | kCartFE for FE (2 banks chosen through JSR and
+// RTS, no hotspot).
+constexpr uint32_t kCartSC = 0x80, kCartE0 = 0x40, kCartFE = 0x20;
 __host__ __device__ constexpr uint32_t cart_banks_of(uint32_t cb) { return cb & 0x0F; }
 __host__ __device__ constexpr uint32_t cart_is_sc(uint32_t cb) { return cb >> 7; }
 __host__ __device__ constexpr uint32_t cart_is_e0(uint32_t cb) { return (cb >> 6) & 1u; }
+__host__ __device__ constexpr uint32_t cart_is_fe(uint32_t cb) { return (cb >> 5) & 1u; }
 // Bytes of the device image a block stages (2K images are mirrored to 4 KB).
 __host__ __device__ constexpr uint32_t cart_image_bytes(uint32_t cb) {
   return cart_is_e0(cb) ? 8192u : (cart_banks_of(cb) ? cart_banks_of(cb) * 4096u : 4096u);

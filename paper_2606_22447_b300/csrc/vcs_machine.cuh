@@ -269,6 +269,8 @@ struct Ctx {
                              // words 32..63 (written at $1000-$107F, read at $1080-$10FF)
   uint32_t e0;               // 1: E0 cart: Regs::bank holds the slices of segments 0..2
                              // (3 bits each); segment 3 shows slice 7
+  uint32_t fe;               // 1: FE cart: two 4 KB banks chosen by JSR and RTS made at the
+                             // top of the stack (exec_op), no hotspot
   uint32_t rw;               // RAM words of this env: 32, or 64 with the Superchip's RAM
   int32_t ystart;
   // Threads per env: T lanes run one env's machine in lockstep (identical

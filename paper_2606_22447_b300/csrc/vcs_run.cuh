@@ -89,7 +89,8 @@ __device__ __forceinline__ Ctx make_ctx(const BlockSmem& b, int E, int slot, int
   c.e4 = 4u * (uint32_t)E;
   c.E = (uint32_t)E;
   c.nb = nb;
-  c.hot = first_hotspot(nb);
+  c.fe = XM ? cart_is_fe(cb) : 0u;
+  c.hot = c.fe ? 0xFFFFu : first_hotspot(nb);
   c.sc = XM ? cart_is_sc(cb) : 0u;
   c.e0 = XM ? cart_is_e0(cb) : 0u;
   c.rw = c.sc ? 64u : 32u;
@@ -162,13 +163,13 @@ __device__ __forceinline__ void store_env(const SoA& s, int n, int e, const Ctx&
 
 // Power-on state: A = X = Y = 0, SP = $FD, P = $34, RAM (and the
 // Superchip's RAM) and TIA zero, timer as if 0 had been written to T1024T at
-// cycle 0, banked carts in their last bank, E0 segments 0..2 showing slices
-// 4, 5, 6, PC from the reset vector.
+// cycle 0, banked carts in their last bank (FE in its first), E0 segments
+// 0..2 showing slices 4, 5, 6, PC from the reset vector.
 __device__ __forceinline__ void power_on(const Ctx& c, Regs& r) {
   r.A = r.X = r.Y = 0;
   r.SP = 0xFD;
   unpack_p(r, 0x34);
-  r.bank = c.e0 ? (4u | 5u << 3 | 6u << 6) : (c.nb ? c.nb - 1u : 0u);
+  r.bank = c.e0 ? (4u | 5u << 3 | 6u << 6) : (c.nb && !c.fe ? c.nb - 1u : 0u);
   r.jam = 0;
   r.cyc = 0;
   r.fc = 0;

@@ -85,11 +85,12 @@ def test_argument_errors_before_device_work(lib):
 def test_detect_mapper(lib):
     """Content-based detection (host only): every generated format is
     recognised from its image; an 8 KB image with E0-hotspot accesses is E0
-    unless it also touches the F8 hotspots; Superchip filler in every bank
-    picks the SC variant; other sizes are refused."""
+    unless it also touches the F8 hotspots; one without either and with a
+    JSR into $D000-$DFFF is FE; Superchip filler in every bank picks the SC
+    variant; other sizes are refused."""
     from paper_2606_22447_b300 import detect_mapper
     all_mappers = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
-                   synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0]
+                   synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0, synth.MAPPER_FE]
     for seed in (31, 32):
         for m, rom in zip(all_mappers, synth.config_carts(seed, all_mappers)):
             assert detect_mapper(rom) == m, (seed, m)
@@ -101,6 +102,11 @@ def test_detect_mapper(lib):
     assert detect_mapper(bytes(e0)) == synth.MAPPER_F8
     blank = bytearray(range(256)) * 32                  # no hotspot access, no Superchip filler
     assert detect_mapper(bytes(blank)) == synth.MAPPER_F8
+    fe = bytearray(blank)
+    fe[0x100:0x103] = bytes((0x20, 0x00, 0xD4))        # JSR $D400: a call into FE's second bank
+    assert detect_mapper(bytes(fe)) == synth.MAPPER_FE
+    fe[0x300:0x303] = bytes((0x2C, 0xF8, 0x1F))        # BIT $1FF8: an F8 hotspot
+    assert detect_mapper(bytes(fe)) == synth.MAPPER_F8
     blank[0x1000:0x1003] = bytes((0x8D, 0xF3, 0x3F))  # STA $3FF3 -> $1FF3
     assert detect_mapper(bytes(blank)) == synth.MAPPER_E0
     sc = bytearray(synth.generate_cart(34, 0, synth.MAPPER_F6))

@@ -17,6 +17,7 @@ MAPPERS = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8]
 BANKED = [synth.MAPPER_F6, synth.MAPPER_F4, synth.MAPPER_F8]
 SUPERCHIP = [synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC]
 E0 = [synth.MAPPER_E0, synth.MAPPER_4K, synth.MAPPER_E0]
+FE = [synth.MAPPER_FE, synth.MAPPER_F8, synth.MAPPER_FE]
 
 
 def _oracle_study(rom, mapper, warm, action, T, alpha, n):
@@ -47,7 +48,7 @@ def _oracle_study(rom, mapper, warm, action, T, alpha, n):
                                                   (1.0, 6.0, 0, MAPPERS), (0.15, 6.0, 2, BANKED),
                                                   (0.14, 2.0, 0, BANKED), (0.15, 6.0, 2, SUPERCHIP),
                                                   (0.14, 6.0, 0, SUPERCHIP), (0.15, 6.0, 2, E0),
-                                                  (0.14, 3.0, 0, E0)])
+                                                  (0.14, 3.0, 0, E0), (0.15, 6.0, 2, FE), (0.14, 3.0, 0, FE)])
 def test_full_divergence_matches_oracle(T, alpha, warm, mappers):
     torch = torch_cuda()
     MAPPERS = mappers

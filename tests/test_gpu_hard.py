@@ -624,6 +624,28 @@ def test_e0_carts_match_oracle(epb, tpe):
     _check_all(roms, mappers, env_cart, acts, 2, envs_per_block=epb, threads_per_env=tpe)
 
 
+@pytest.mark.parametrize("epb,tpe", [(16, 1), (32, 4)])
+def test_fe_carts_match_oracle(epb, tpe):
+    """FE carts (a bank-1 or bank-0 kernel called each frame from the top
+    of the stack, picked by the joystick) next to E0 and plain carts in one
+    batch: RAM, screens and status bit-exact against the oracle."""
+    mappers = [synth.MAPPER_FE, synth.MAPPER_FE, synth.MAPPER_E0, synth.MAPPER_4K]
+    roms = synth.config_carts(311, mappers)
+    env_cart = np.random.default_rng(11).permutation(np.arange(40) % len(mappers)).astype(np.int32)
+    acts = synth.actions(311, 40, 8)
+    _check_all(roms, mappers, env_cart, acts, 2, envs_per_block=epb, threads_per_env=tpe)
+
+
+def test_fe_switching_on_the_gpu():
+    """The oracle's FE pin on the GPU: JSR at the top of the stack, RTS,
+    a deeper JSR and a plain push to $01FE, checked through the RAM each
+    step leaves."""
+    from tests.test_oracle_machine import _fe_image
+    rom = _fe_image()
+    acts = synth.actions(312, 2, 2)
+    _check_all([rom], [synth.MAPPER_FE], [0, 0], acts, 1)
+
+
 def test_e0_hotspots_on_the_gpu():
     """The oracle's E0 hotspot pin on the GPU (reads and writes of each
     segment's hotspots, neighbours and the image below A12 ignored), then

@@ -30,11 +30,13 @@ def _oracle_steps(rom, mapper, actions, n_instr):
 
 
 @pytest.mark.parametrize("n_instr,spl,epb,banked", [(1000, 0, 0, False), (997, 2, 8, False), (3001, 0, 32, False),
-                                                    (1, 0, 0, False), (1999, 0, 0, True), (1501, 0, 0, "ext")])
+                                                    (1, 0, 0, False), (1999, 0, 0, True), (1501, 0, 0, "ext"),
+                                                    (777, 0, 0, "fe")])
 def test_hard_instruction_steps_match_oracle(n_instr, spl, epb, banked):
     n_envs = 33
     steps = 6 if n_instr > 1 else 40
     mappers = ([synth.MAPPER_F8SC, synth.MAPPER_E0, synth.MAPPER_F4SC] if banked == "ext" else
+               [synth.MAPPER_FE, synth.MAPPER_4K, synth.MAPPER_FE] if banked == "fe" else
                [synth.MAPPER_F6, synth.MAPPER_F4, synth.MAPPER_F8] if banked else MAPPERS)
     roms = synth.config_carts(81, mappers)
     ec = (np.arange(n_envs) % 3).astype(np.int32)

@@ -15,8 +15,8 @@ from tests.test_gpu_soft import assert_grad_close
 
 pytestmark = pytest.mark.gpu
 
-ALL9 = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
-        synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0]
+ALL10 = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
+         synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0, synth.MAPPER_FE]
 
 
 def _check(roms, mappers, env_cart, acts, frame_skip, full, **cfg):
@@ -33,14 +33,14 @@ def _check(roms, mappers, env_cart, acts, frame_skip, full, **cfg):
 
 @pytest.mark.parametrize("epb,tpe", [(16, 1), (32, 4), (64, 2)])
 def test_full_tia_carts_match_oracle(epb, tpe):
-    """Full-TIA carts of all nine formats, envs unsorted over several blocks
+    """Full-TIA carts of all ten formats, envs unsorted over several blocks
     and a ragged tail, in both machine modes."""
-    roms = synth.config_carts(311, ALL9, full_tia=True)
-    env_cart = np.random.default_rng(11).permutation(np.arange(45) % len(ALL9)).astype(np.int32)
+    roms = synth.config_carts(311, ALL10, full_tia=True)
+    env_cart = np.random.default_rng(11).permutation(np.arange(45) % len(ALL10)).astype(np.int32)
     acts = synth.actions(311, 45, 6)
-    _check(roms, ALL9, env_cart, acts, 2, True, envs_per_block=epb, threads_per_env=tpe)
+    _check(roms, ALL10, env_cart, acts, 2, True, envs_per_block=epb, threads_per_env=tpe)
     if tpe == 1:
-        _check(roms, ALL9, env_cart, acts, 2, False, envs_per_block=epb)
+        _check(roms, ALL10, env_cart, acts, 2, False, envs_per_block=epb)
 
 
 def test_plain_carts_in_full_tia_mode():
