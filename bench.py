@@ -37,7 +37,13 @@ WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+sc
 # DRAM bytes (read + write) of one step launch on the bench workload, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernel; to be taken again whenever the kernel changes
-TRAFFIC_BYTES_PER_LAUNCH = 1_205_504 + 83_224_064
+TRAFFIC_BYTES_PER_LAUNCH = 1_065_984 + 83_931_648
+# Counters of the same ncu capture (one k_run<0, 1, 0, 0, 0, 0> launch, 4096
+# envs in 256 blocks of 16, one lane per env): the GPU-wide fraction of issue
+# slots used (smsp__issue_active.avg.pct_of_peak_sustained_elapsed) and the
+# thread instructions executed (smsp__thread_inst_executed.sum)
+MEASURED_ISSUE_ACTIVE = 0.0974
+MEASURED_THREAD_INST = 5_537_312_497
 OPS_PER_INSTRUCTION = 12
 OPS_PER_PIXEL = 6
 PIXELS_PER_STEP = 210 * 160
@@ -52,31 +58,64 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    """SM clock and clock-event reasons sampled during the timed region:
+    through NVML every 5 ms (read-only queries, no subprocess, so the timed
+    launches are not held up by a fork), or through nvidia-smi every 200 ms
+    when NVML cannot be opened."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits of the four reasons the timing rules name
+    REASON_BITS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+                   ("sw_power_cap", 0x4))
 
     def __init__(self, index: int):
         self.index = index
-        self.samples = []
+        self.samples = []   # (sm MHz, max sm MHz, set of reason names)
         self._stop = threading.Event()
         self._t = None
+        self._nvml = None
+
+    def _open_nvml(self):
+        try:
+            import pynvml
+            import torch
+            pynvml.nvmlInit()
+            uuid = torch.cuda.get_device_properties(self.index).uuid
+            h = pynvml.nvmlDeviceGetHandleByUUID(f"GPU-{uuid}")
+            return pynvml, h
+        except Exception:
+            return None
+
+    def _sample_nvml(self):
+        nv, h = self._nvml
+        sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        bits = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+        self.samples.append((float(sm), float(mx), {n for n, b in self.REASON_BITS if bits & b}))
+
+    def _sample_smi(self):
+        out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=5).stdout.strip()
+        if out:
+            f = [x.strip() for x in out.split(",")]
+            num = lambda x: float(x) if x.replace(".", "").isdigit() else None
+            names = [n for n, _ in self.REASON_BITS]
+            self.samples.append((num(f[1]), num(f[2]),
+                                 {names[i] for i in range(4) if len(f) > 5 + i and f[5 + i].lower() in ("active", "1", "yes")}))
 
     def _run(self):
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
+                self._sample_nvml() if self._nvml else self._sample_smi()
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(0.005 if self._nvml else 0.2)
 
     def __enter__(self):
+        self._nvml = self._open_nvml()
         self._t = threading.Thread(target=self._run, daemon=True)
         self._t.start()
         return self
@@ -86,13 +125,11 @@ class ClockSampler:
         self._t.join(timeout=10)
 
     def summary(self):
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
-                          if len(s) > 5 + i and s[5 + i].lower() in ("active", "1", "yes")})
+        sm = [x[0] for x in self.samples if x[0] is not None]
+        mx = [x[1] for x in self.samples if x[1] is not None]
+        reasons = sorted(set().union(*[x[2] for x in self.samples])) if self.samples else []
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(self.samples), "source": "nvml" if self._nvml else "nvidia-smi"}
 
 
 def oracle_sample(n_envs: int, n_steps: int, threads: int):
@@ -324,13 +361,13 @@ def mixed_leg(n_envs, steps, reps, full_tia=False):
     written per step.  The launch geometry is autotuned on the workload
     first (outside the timing); each timed unit is one replay of a CUDA graph
     of `steps` env-steps.  Returns env-steps/s (median over reps).
-    full_tia: the same shape over carts of all nine formats that draw with
+    full_tia: the same shape over carts of all ten formats that draw with
     every TIA object and read the collision latches, in a full-TIA batch."""
     import torch
 
     from paper_2606_22447_b300 import Batch, default_config, synth
     mappers = ([synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
-                synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0] if full_tia
+                synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0, synth.MAPPER_FE] if full_tia
                else synth.MIX16)
     roms = synth.config_carts(SEED, mappers, full_tia=full_tia)
     ec = synth.env_cart_round_robin(n_envs, len(mappers))
@@ -363,7 +400,7 @@ def mixed_leg(n_envs, steps, reps, full_tia=False):
     g.destroy()
     return {"env_steps_per_s": n_envs * steps / (ms / 1e3), "ms_per_graph": ms, "n_envs": n_envs,
             "steps_per_graph": steps, "episodes_ended": done,
-            "carts": ("full-TIA carts of the nine formats (2K 4K F8 F6 F4 F8SC F6SC F4SC E0), full_tia = 1"
+            "carts": ("full-TIA carts of the ten formats (2K 4K F8 F6 F4 F8SC F6SC F4SC E0 FE), full_tia = 1"
                       if full_tia else "6x2K + 6x4K + 4xF8"),
             "autotune": tune, "gpu_launches_per_graph": -(-steps // k),
             "outputs": "RAM + screen per step (2.2 GB per step at 65,536 envs), larger than L2"}
@@ -385,8 +422,10 @@ def gpu_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         es, dt, ipe = oracle_sample(4 * cores, 8, cores)
+        es1, dt1, _ = oracle_sample(8, 8, 1)
         cpu = {"value": es / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{4 * cores} envs x 8 env-steps of the workload (frame-skip 4), {ipe:.0f} instr/env-step"}
+               "sample": f"{4 * cores} envs x 8 env-steps of the workload (frame-skip 4), {ipe:.0f} instr/env-step",
+               "value_1core": es1 / dt1, "sample_1core": "8 envs x 8 env-steps on one thread"}
 
     from paper_2606_22447_b300 import Batch, build, default_config, synth
     build.build()
@@ -417,11 +456,15 @@ def gpu_arm(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
+        # an NVTX range marks the timed launches, so that a profiler can
+        # capture exactly these (ncu --nvtx --nvtx-include "timed/")
+        torch.cuda.nvtx.range_push("timed")
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
             ev[k][0].record(stream)
             batch.step(acts[args.warmup + k], FRAME_SKIP, ram, scr)
             ev[k][1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     batch.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -459,13 +502,18 @@ def gpu_arm(args):
     peak_ops = max(int_peak() for _ in range(3))
     roofline = {"bound": "alu", "achieved": ops / mean_s / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                 "frac": ops / mean_s / peak_ops, "traffic": TRAFFIC_BYTES_PER_LAUNCH if n == N_ENVS else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_run launch at 4096 envs; "
-                                  f"algorithmic bytes per launch {n * (PIXELS_PER_STEP + 128 + 1)}",
+                "traffic_source": "ncu dram read+write, one k_run launch at 4096 envs",
+                "algorithmic_bytes": n * (PIXELS_PER_STEP + 128 + 1),
                 "peak_source": "measured: vcs_int_peak, independent 32-bit add/shift/logic chains at full "
                                "occupancy (best of 3)",
                 "peak_derived": derived_ops / 1e12,
                 "peak_derived_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int lanes x "
                                        f"{max_mhz:.0f} MHz",
+                "traffic_note": "below the algorithmic bytes: part of the screens is still in L2 when the kernel ends",
+                "issue_frac_measured": MEASURED_ISSUE_ACTIVE if n == N_ENVS else None,
+                "lane_frac_measured": (MEASURED_THREAD_INST / (mean_s * derived_ops)) if n == N_ENVS else None,
+                "measured_source": "ncu smsp__issue_active (GPU-wide) and smsp__thread_inst_executed / "
+                                   "(SMs x 128 lanes x max clock x this run's launch time)",
                 "ops_per_env_step": ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL,
                 "instructions_per_env_step": ipe,
                 "hbm_gbs_written": n * (128 + PIXELS_PER_STEP) / mean_s / 1e9}
@@ -508,6 +556,9 @@ def gpu_arm(args):
             "full_relaxed": full,
         }
         print(json.dumps(line), flush=True)
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(line, f, indent=1)
     if dist:
         dist.destroy_process_group()
 
@@ -529,6 +580,7 @@ def main():
                     help="skip the fully relaxed forward's bit-exactness grid")
     ap.add_argument("--no-instr", action="store_true",
                     help="skip the 3,000-instruction rollouts at 1..65,536 envs (the paper's throughput unit)")
+    ap.add_argument("--out", default=None, help="also write the JSON line (indented) to this file")
     ap.add_argument("--no-soft-long", action="store_true",
                     help="skip the 4096-env x 2048-frame soft rollout (about 20 s)")
     args = ap.parse_args()
