@@ -524,7 +524,7 @@ def gpu_arm(args):
                 "short_1024x64_sampler": soft_leg(1024, 64, [_s.MAPPER_4K], 3,
                                                   "soft_short_1024x4k_instructions_per_frame", sampler=True)}
         if not args.no_soft_long:
-            soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, 1, "soft_long_4096xmix8_instructions_per_frame")
+            soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, 2, "soft_long_4096xmix8_instructions_per_frame")
     mixed = None
     full_tia = None
     if not args.no_mixed:

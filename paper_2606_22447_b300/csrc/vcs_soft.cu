@@ -171,8 +171,33 @@ struct BwdParams {
   int32_t* err;
 };
 
+// A compensated adjoint (Neumaier): s + c is its value.  Over a long
+// rollout an adjoint can pass thousands of times between a RAM cell and a
+// register (a byte loaded, updated and stored back every frame); one
+// float32 rounding per hop would then add up to more than the gradient
+// tolerance, so the registers hold such pairs and a write hands its cell's
+// pair to the register whole.
+struct Acc {
+  float s, c;
+  __device__ __forceinline__ float v() const { return s + c; }
+  __device__ __forceinline__ void operator+=(float x) { comp_add(s, c, x); }
+  __device__ __forceinline__ void operator+=(const Acc& o) {
+    s += o.s;
+    c += o.c;
+  }
+  __device__ __forceinline__ Acc take() {
+    const Acc r = *this;
+    s = c = 0.f;
+    return r;
+  }
+  __device__ __forceinline__ void clear() { s = c = 0.f; }
+  __device__ __forceinline__ bool zero() const { return s == 0.f && c == 0.f; }
+};
+__device__ __forceinline__ Acc acc(float x) { return Acc{x, 0.f}; }
+__device__ __forceinline__ Acc operator-(const Acc& x) { return Acc{-x.s, -x.c}; }
+
 struct Adj {
-  float A, X, Y, V, C0, C1, C2, C3;   // C3: COLUP1
+  Acc A, X, Y, V, C0, C1, C2, C3;   // C3: COLUP1
   float P, H;          // player 0's position and HMP0 (position sampler)
   float u[5], uc[5];   // joystick-input adjoints of the current step (compensated)
 };
@@ -192,13 +217,32 @@ struct RomQueue {
 enum : uint32_t { kKind2K = 1, kKindSC = 2, kKindE0 = 4 };
 
 // Relaxed read of cell i of a 128-cell RAM tensor whose adjoints start at
-// cell `base` (0: RIOT RAM, 128: the Superchip's RAM).
+// cell `base` (0: RIOT RAM, 128: the Superchip's RAM).  The read cell's own
+// weight, 1 / z_i, is close to 1 at small temperatures, and an adjoint that
+// passes through the same read every frame is multiplied by it thousands of
+// times: a float32 rounding of the weight would then compound into a bias
+// (2,048 frames x up to 3e-8 per factor).  So the read cell takes
+// g - g (z_i - 1) / z_i, the small complement being accurate to float32's
+// relative precision (izr[128 + i]); its neighbours take
+// g e^{-|j - i| / tau} / z_i.
 __device__ __forceinline__ void spread_ram(float* aram, float* aramc, uint32_t E, const float* ek, const float* izr,
-                                           int W, int base, int i, float g) {
+                                           int W, int base, int i, const Acc& g) {
   const int lo = i - W < 0 ? 0 : i - W, hi = i + W > 127 ? 127 : i + W;
-  const float gz = g * izr[i];
-  for (int j = lo; j <= hi; j++)
-    comp_add(aram[(base + j) * E], aramc[(base + j) * E], __fmul_rn(gz, ek[j > i ? j - i : i - j]));
+  const float gv = g.v(), gz = gv * izr[i];
+  for (int j = lo; j <= hi; j++) {
+    float* cs = aram + (base + j) * E;
+    float* cc = aramc + (base + j) * E;
+    float s = *cs, c = *cc;
+    if (j == i) {   // the read cell: the pair whole, less its neighbours' share
+      comp_add(s, c, g.s);
+      c += g.c;
+      comp_add(s, c, -__fmul_rn(gv, izr[128 + i]));
+    } else {
+      comp_add(s, c, __fmul_rn(gz, ek[j > i ? j - i : i - j]));
+    }
+    *cs = s;
+    *cc = c;
+  }
 }
 
 // Adjoint of a value read from `ref` (13-bit bus address) flows back to the
@@ -210,11 +254,12 @@ __device__ __forceinline__ void spread_ram(float* aram, float* aramc, uint32_t E
 template <bool XM>
 __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                              const float* izr, int W, RomQueue& rq,
-                                             uint32_t kind, uint32_t ref, uint32_t fl, float g) {
+                                             uint32_t kind, uint32_t ref, uint32_t fl, const Acc& ga) {
   const uint32_t ad = ref & 0x1FFF;
-  if (g == 0.f) return;
+  if (ga.zero()) return;
+  const float g = ga.v();   // ROM impulses and joystick sums are compensated where they accumulate
   if (XM && (kind & kKindSC) && (ad & 0x1F80) == 0x1080) {   // the Superchip's read port
-    spread_ram(aram, aramc, E, ek, izr, W, 128, (int)(ad & 0x7F), g);
+    spread_ram(aram, aramc, E, ek, izr, W, 128, (int)(ad & 0x7F), ga);
   } else if (ad & 0x1000) {
     const uint32_t unit = (fl >> 2) & 7u;   // the read's bank (E0: slice)
     rq.idx[rq.n] = (kind & kKind2K) ? (ad & 0x7FF)
@@ -224,7 +269,7 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
   } else if (!(ad & 0x80)) {
     if ((ad & 0xF) == 0xC) comp_add(a.u[4], a.uc[4], -128.f * g);
   } else if (!(ad & 0x200)) {
-    spread_ram(aram, aramc, E, ek, izr, W, 0, (int)(ad & 0x7F), g);
+    spread_ram(aram, aramc, E, ek, izr, W, 0, (int)(ad & 0x7F), ga);
   } else if (!(ad & 4)) {
     if ((ad & 3) == 0) {
       comp_add(a.u[0], a.uc[0], -128.f * g);
@@ -233,31 +278,30 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
       comp_add(a.u[3], a.uc[3], -16.f * g);
     }
   } else if (!(ad & 1) && (fl & 2)) {
-    a.V += g;
+    a.V += ga;
   }
 }
 
 // Adjoint of the value written to `ref`: taken from the cell (which is then
 // cleared, the write being one-hot).
 template <bool SAMPLER, bool XM>
-__device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
-                                            uint32_t& j, uint32_t kind, uint32_t ref) {
+__device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
+                                          uint32_t& j, uint32_t kind, uint32_t ref) {
   const uint32_t ad = ref & 0x1FFF;
   if (ad & 0x1000) {
-    if (!XM || !(kind & kKindSC) || (ad & 0x1F80) != 0x1000) return 0.f;
+    if (!XM || !(kind & kKindSC) || (ad & 0x1F80) != 0x1000) return acc(0.f);
     const uint32_t o = (128 + (ad & 0x7F)) * E;   // the Superchip's write port
-    const float g = aram[o] + aramc[o];
+    const Acc g{aram[o], aramc[o]};
     aram[o] = 0.f;
     aramc[o] = 0.f;
     return g;
   }
   if (!(ad & 0x80)) {
     const uint32_t reg = ad & 0x3F;
-    float g;
-    if (reg == 0x06) { g = a.C0 + (j ? cw[--j] : 0.f); a.C0 = 0.f; return g; }
-    if (reg == 0x08) { g = a.C1 + (j ? cw[--j] : 0.f); a.C1 = 0.f; return g; }
-    if (reg == 0x09) { g = a.C2 + (j ? cw[--j] : 0.f); a.C2 = 0.f; return g; }
-    if (reg == 0x07) { g = a.C3 + (j ? cw[--j] : 0.f); a.C3 = 0.f; return g; }
+    if (reg == 0x06) { if (j) a.C0 += cw[--j]; return a.C0.take(); }
+    if (reg == 0x08) { if (j) a.C1 += cw[--j]; return a.C1.take(); }
+    if (reg == 0x09) { if (j) a.C2 += cw[--j]; return a.C2.take(); }
+    if (reg == 0x07) { if (j) a.C3 += cw[--j]; return a.C3.take(); }
     // RESP0 and HMOVE open a position version (its slot pops either way)
     if (reg == 0x2A || reg == 0x10) {
       const float sv = j ? cw[--j] : 0.f;
@@ -269,27 +313,27 @@ __device__ __forceinline__ float take_write(Adj& a, float* aram, float* aramc, u
           a.P = 0.f;
         }
       }
-      return 0.f;
+      return acc(0.f);
     }
     if constexpr (SAMPLER) {
-      if (reg == 0x20) { g = a.H; a.H = 0.f; return g; }   // HMP0
-      if (reg == 0x2B) { a.H = 0.f; return 0.f; }           // HMCLR
+      if (reg == 0x20) {   // HMP0
+        const float g = a.H;
+        a.H = 0.f;
+        return acc(g);
+      }
+      if (reg == 0x2B) { a.H = 0.f; return acc(0.f); }   // HMCLR
     }
-    return 0.f;
+    return acc(0.f);
   }
   if (!(ad & 0x200)) {
     const uint32_t o = (ad & 0x7F) * E;
-    float g = aram[o] + aramc[o];
+    const Acc g{aram[o], aramc[o]};
     aram[o] = 0.f;
     aramc[o] = 0.f;
     return g;
   }
-  if ((ad & 0x14) == 0x14) {
-    float g = a.V;
-    a.V = 0.f;
-    return g;
-  }
-  return 0.f;
+  if ((ad & 0x14) == 0x14) return a.V.take();
+  return acc(0.f);
 }
 
 __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
@@ -301,20 +345,17 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
   const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
   switch (op) {
     case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
-      float g = a.A;
-      a.A = 0.f;
+      const Acc g = a.A.take();
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xA2: case 0xA6: case 0xB6: case 0xAE: case 0xBE: {
-      float g = a.X;
-      a.X = 0.f;
+      const Acc g = a.X.take();
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0xA0: case 0xA4: case 0xB4: case 0xAC: case 0xBC: {
-      float g = a.Y;
-      a.Y = 0.f;
+      const Acc g = a.Y.take();
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
@@ -329,14 +370,13 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, -a.A);
       break;
     case 0xA7: case 0xB7: case 0xAF: case 0xBF: case 0xA3: case 0xB3: {   // LAX: A = X = M
-      float g = a.A + a.X;
-      a.A = 0.f;
-      a.X = 0.f;
+      Acc g = a.A.take();
+      g += a.X.take();
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
-      const float g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      const Acc g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
       a.A += g;
       a.X += g;
       break;
@@ -356,20 +396,19 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x66: case 0x76: case 0x6E: case 0x7E:
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
-      float g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      const Acc g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
-    case 0xAA: a.A += a.X; a.X = 0.f; break;   // TAX
-    case 0x8A: a.X += a.A; a.A = 0.f; break;   // TXA
-    case 0xA8: a.A += a.Y; a.Y = 0.f; break;   // TAY
-    case 0x98: a.Y += a.A; a.A = 0.f; break;   // TYA
-    case 0xBA: a.X = 0.f; break;               // TSX: SP carries nothing
+    case 0xAA: a.A += a.X.take(); break;   // TAX
+    case 0x8A: a.X += a.A.take(); break;   // TXA
+    case 0xA8: a.A += a.Y.take(); break;   // TAY
+    case 0x98: a.Y += a.A.take(); break;   // TYA
+    case 0xBA: a.X.clear(); break;         // TSX: SP carries nothing
     case 0x48: a.A += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref); break;   // PHA
     case 0x08: take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref); break;           // PHP
     case 0x68: {                                                    // PLA
-      float g = a.A;
-      a.A = 0.f;
+      const Acc g = a.A.take();
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
@@ -387,16 +426,21 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
   }
 }
 
-// Shared tables of the relaxed read: ek[k] = exp(-k / tau) for k <= W and the
-// inverse window normaliser of every RAM cell.
+// Shared tables of the relaxed read: ek[k] = exp(-k / tau) for k <= W; for
+// every RAM cell i the inverse window normaliser 1 / z_i (izr[i]) and the
+// complement of the cell's own weight, (z_i - 1) / z_i (izr[128 + i]),
+// computed from the off-centre terms so that it keeps float32's relative
+// precision however small it is.
 __device__ __forceinline__ void read_tables(float* ek, float* izr, float tau, int W) {
   for (int k = threadIdx.x; k <= W; k += blockDim.x) ek[k] = expf(-(float)k / tau);
   __syncthreads();
   for (int i = threadIdx.x; i < 128; i += blockDim.x) {
     const int lo = i - W < 0 ? 0 : i - W, hi = i + W > 127 ? 127 : i + W;
-    float z = 0.f;
-    for (int q = lo; q <= hi; q++) z += ek[q > i ? q - i : i - q];
+    float off = 0.f;
+    for (int q = lo; q <= hi; q++) off += q == i ? 0.f : ek[q > i ? q - i : i - q];
+    const float z = 1.f + off;
     izr[i] = 1.f / z;
+    izr[128 + i] = off / z;
   }
   __syncthreads();
 }
@@ -432,7 +476,7 @@ constexpr int kSweepWarpWords = 3 * kSweepBlock;   // staged records, then the R
 // tables, then each warp's staging words.
 constexpr int kSweepCells = 256;
 __host__ __device__ constexpr size_t sw_tables_end() {
-  return ((size_t)2 * kSweepCells * 4 * kSweepEnvs + (kMaxW + 1 + 128) * 4 + 15) & ~(size_t)15;
+  return ((size_t)2 * kSweepCells * 4 * kSweepEnvs + (kMaxW + 1 + 256) * 4 + 15) & ~(size_t)15;
 }
 __host__ __device__ constexpr size_t sw_smem_bytes() { return sw_tables_end() + (size_t)kSweepEnvs * kSweepWarpWords * 4; }
 
@@ -523,7 +567,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   float* aram_s = reinterpret_cast<float*>(smem);   // [256][E]
   float* aramc_s = aram_s + kSweepCells * E;         // [256][E] compensation
   float* ek = aramc_s + kSweepCells * E;             // [kMaxW + 1]
-  float* izr = ek + (kMaxW + 1);                     // [128]
+  float* izr = ek + (kMaxW + 1);                     // [256]: 1 / z_i, then (z_i - 1) / z_i
   uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem + sw_tables_end()) + slot * kSweepWarpWords;
   uint32_t* recs = wbuf;                             // [kSweepBlock] records of the current block
   RomQueue rq;
@@ -546,14 +590,16 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   Adj a;
   if (lead) {
     if (p.first) {
-      a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.C3 = a.P = a.H = 0.f;
+      a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.C3 = acc(0.f);
+      a.P = a.H = 0.f;
       for (int i = 0; i < cells; i++) aram[i * E] = 0.f;
       for (int i = 0; i < cells; i++) aramc[i * E] = 0.f;
     } else {
       const float* cr = p.carry;
-      a.A = cr[0 * n + env]; a.X = cr[1 * n + env]; a.Y = cr[2 * n + env]; a.V = cr[3 * n + env];
-      a.C0 = cr[4 * n + env]; a.C1 = cr[5 * n + env]; a.C2 = cr[6 * n + env];
-      a.C3 = cr[(size_t)kCarryC3 * n + env];
+      a.A = acc(cr[0 * n + env]); a.X = acc(cr[1 * n + env]); a.Y = acc(cr[2 * n + env]);
+      a.V = acc(cr[3 * n + env]);
+      a.C0 = acc(cr[4 * n + env]); a.C1 = acc(cr[5 * n + env]); a.C2 = acc(cr[6 * n + env]);
+      a.C3 = acc(cr[(size_t)kCarryC3 * n + env]);
       a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
       a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
       for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
@@ -646,9 +692,9 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
         p.grad_cart_ram0[(size_t)env * 128 + i] = XM ? aram[(128 + i) * E] + aramc[(128 + i) * E] : 0.f;
   } else {
     float* cr = p.carry;
-    cr[0 * n + env] = a.A; cr[1 * n + env] = a.X; cr[2 * n + env] = a.Y; cr[3 * n + env] = a.V;
-    cr[4 * n + env] = a.C0; cr[5 * n + env] = a.C1; cr[6 * n + env] = a.C2;
-    cr[(size_t)kCarryC3 * n + env] = a.C3;
+    cr[0 * n + env] = a.A.v(); cr[1 * n + env] = a.X.v(); cr[2 * n + env] = a.Y.v(); cr[3 * n + env] = a.V.v();
+    cr[4 * n + env] = a.C0.v(); cr[5 * n + env] = a.C1.v(); cr[6 * n + env] = a.C2.v();
+    cr[(size_t)kCarryC3 * n + env] = a.C3.v();
     cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
