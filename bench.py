@@ -213,7 +213,7 @@ def bench_counts() -> dict:
         return json.load(f)
 
 
-def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False):
+def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False, graphics=False):
     """SOFT-STE forward + backward over n_frames (frame-skip 1, 64-frame
     checkpoint segments, loss weights on 8 RAM bytes and 256 pixels at every
     step), optionally with the differentiable position sampler.  Returns
@@ -229,7 +229,8 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False)
     # replicas share; the forward and large recompute groups run one lane per
     # env whatever this is
     b = Batch(roms, mappers, ec, default_config(segment_frames=64, threads_per_env=8,
-                                                position_sampler=1 if sampler else 0))
+                                                position_sampler=1 if sampler else 0,
+                                                graphics_bits=1 if graphics else 0))
     u = torch.from_numpy(synth.action_inputs(synth.actions(SEED, n_envs, n_frames))).cuda()
     rng = np.random.default_rng(SEED)
     w_ram = torch.zeros(128, device="cuda")
@@ -262,6 +263,7 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False)
             "instructions_per_s": n_envs * n_frames * ipf / ((fwd + bwd) / 1e3),
             "instructions_per_frame": ipf, "fwd_ms": fwd, "bwd_ms": bwd,
             "n_envs": n_envs, "frames": n_frames, "tau": tau, "position_sampler": sampler,
+            "graphics_bits": graphics,
             "tape_device_gb": used / 1e9,
             "gpu_launches": 1 + 2 * ((n_frames + 63) // 64) + 2}
 
@@ -522,7 +524,9 @@ def gpu_arm(args):
         from paper_2606_22447_b300 import synth as _s
         soft = {"short_1024x64": soft_leg(1024, 64, [_s.MAPPER_4K], 3, "soft_short_1024x4k_instructions_per_frame"),
                 "short_1024x64_sampler": soft_leg(1024, 64, [_s.MAPPER_4K], 3,
-                                                  "soft_short_1024x4k_instructions_per_frame", sampler=True)}
+                                                  "soft_short_1024x4k_instructions_per_frame", sampler=True),
+                "short_1024x64_graphics": soft_leg(1024, 64, [_s.MAPPER_4K], 3,
+                                                   "soft_short_1024x4k_instructions_per_frame", graphics=True)}
         if not args.no_soft_long:
             soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, 2, "soft_long_4096xmix8_instructions_per_frame")
     mixed = None

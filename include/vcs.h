@@ -160,6 +160,20 @@ typedef struct vcs_config {
                                The subset runs in kernels without the rest
                                (about a quarter faster on the synthetic
                                carts). */
+  int32_t graphics_bits;    /* 1 = the graphics-bit surrogate of Section 3.1
+                               (with the switch stored, graphics bits are
+                               differentiable) in soft backward passes: each
+                               drawn pixel adds (C_with - C_without) times
+                               its gradient to GRP0 where player 0's 8-pixel
+                               span covers it and to the playfield register
+                               (PF0, PF1 or PF2) of its column, C_with and
+                               C_without being the pixel's colours with that
+                               bit forced to 1 and to 0 (the bit's derivative
+                               with respect to its byte is 1); the written
+                               values of GRP0 and PF0-2 then receive these
+                               sums.  0 = off (default).  The subset machine
+                               only: with full_tia, VCS_ERR_ARG.  Forward
+                               outputs do not depend on it. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;
@@ -463,7 +477,7 @@ vcs_status vcs_tape_free(vcs_tape* tape);
  * inputs and outputs, and all scratch (tape entries, adjoint carries, ROM
  * impulses) comes from one fixed 64 MiB array compiled into the library,
  * which every GPU that loads the library keeps until the process exits.
- *  - The scratch a call needs, per env: 2,088 bytes of adjoint carries
+ *  - The scratch a call needs, per env: 2,104 bytes of adjoint carries
  *    plus 8 x rom_stride bytes of ROM impulses (64 KB for 8 KB images),
  *    plus 4 x rom_stride more (32 KB) when grad_rom_per_cart is asked for
  *    without grad_rom; and per env and checkpoint segment held at once

@@ -61,6 +61,7 @@ StepParams vcs_base_params(vcs_batch* b) {
   p.ram_words = b->ram_words;
   p.xmap = b->xmap;
   p.full_tia = b->cfg.full_tia;
+  p.graphics = b->cfg.graphics_bits && b->cfg.step_instructions <= 0;   // instruction steps draw nothing
   p.rom_stride = b->rom_stride;
   p.dt = b->dt;
   p.ystart = b->cfg.ystart;
@@ -197,6 +198,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->step_instructions = 0;
   cfg->tape_budget_mb = 0;
   cfg->full_tia = 0;
+  cfg->graphics_bits = 0;
   return VCS_OK;
 }
 
@@ -349,6 +351,12 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if (b->cfg.position_sampler < 0 || b->cfg.position_sampler > 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "position_sampler must be 0 or 1");
+  }
+  if (b->cfg.graphics_bits < 0 || b->cfg.graphics_bits > 1 || (b->cfg.graphics_bits && b->cfg.full_tia)) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG,
+                    "graphics_bits must be 0 or 1, and 0 with full_tia (graphics-bit gradients are built for "
+                    "the subset machine: player 0 and the playfield)");
   }
   if (b->cfg.sched_policy < 0 || b->cfg.sched_policy > 1) {
     free_batch(b);

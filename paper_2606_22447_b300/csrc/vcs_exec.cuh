@@ -64,6 +64,9 @@ constexpr uint64_t kColdMaybe = reg_bits({0x10, 0x1B, 0x2A, 0x2B});
 // quantity (the soft path's tapes): the four colour registers, and player
 // 0's position (RESP0, HMOVE) for the position sampler.
 constexpr uint64_t kVersionRegs = reg_bits({0x06, 0x07, 0x08, 0x09, 0x10, 0x2A});
+// With the graphics-bit surrogate, GRP0 and the playfield registers open
+// versions too.
+constexpr uint64_t kGraphicsRegs = reg_bits({0x0D, 0x0E, 0x0F, 0x1B});
 
 // A write to a cold register (or a hot one with cold effects) at line clock
 // h: updates the cold words at tx (stride E) and returns the new summary

@@ -54,6 +54,7 @@ struct StepParams {
   int32_t ram_words;        // RAM words per env in shared memory: 32, or 64 when a cart is Superchip
   int32_t xmap;             // the batch holds Superchip or E0 carts: launch the kernels built for them
   int32_t full_tia;         // the whole TIA (player 1, missiles, ball, collisions): its own kernels
+  int32_t graphics;         // soft forward: count GRP0 / PF0-2 writes as versions (graphics-bit surrogate)
   uint32_t rom_stride;      // bytes per cart image (8, 16 or 32 KB): also the shared-memory ROM region
   const DecodeTables* dt;
   const uint8_t* actions;   // [n_steps][n_envs] or null (NOOP)

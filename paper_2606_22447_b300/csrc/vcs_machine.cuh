@@ -471,6 +471,11 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
     }
     const float4* gl = rd.grow;   // this line's gradients, staged by render_to
     const uint32_t gs0 = g0 < blank_g ? blank_g : g0;
+    // graphics-bit surrogate: the player's groups are summed pixel by pixel
+    // even when GRP0 is zero (its bits' with-minus-without colours still
+    // count there), and each playfield register gets the sum of its
+    // columns' gradients times (C_with - C_without)
+    constexpr bool kGB = Tape::graphics;
     // Bulk pass: whole groups inside the span that hold no player pixel
     // belong wholly to COLUPF (playfield bit set) or COLUBK; four groups per
     // turn (g1 <= 40 keeps every guarded load inside the row).  The at most five other groups (the span's two
@@ -479,9 +484,17 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
     auto special = [&](uint32_t g) {
       uint32_t dp = g + 40u - gp;
       dp -= dp >= 40u ? 40u : 0u;
-      const bool player = grev != 0 && dp < 3u;
+      const bool player = (kGB || grev != 0) && dp < 3u;
       return player || 4 * g < x0 || 4 * g + 4 > x1;
     };
+    // the playfield register of group g: PF0 bits cover groups 0-3 of a
+    // half, PF1 4-11, PF2 12-19; the right half mirrors with CTRLPF bit 0
+    auto pf_reg = [&](uint32_t g) -> uint32_t {
+      uint32_t i = g < 20u ? g : ((r.ctrl & 1) ? 39u - g : g - 20u);
+      return i < 4u ? 0u : (i < 12u ? 1u : 2u);
+    };
+    float gb_pf[3] = {0.f, 0.f, 0.f};   // plain groups' gradient sums per playfield register
+    float gb_g = 0.f, gb_f[3] = {0.f, 0.f, 0.f};   // pixel-by-pixel graphics-bit sums
     // s_pf: the playfield (its left half in score mode), s_pfR: the right
     // half in score mode
     float s_p0 = 0.f, s_pf = 0.f, s_bk = 0.f, s_pf2 = 0.f, s_bk2 = 0.f, s_pfR = 0.f;
@@ -497,6 +510,12 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
         const uint32_t gg = g + k;
         const float t = (gg < gs0 || gg >= g1 || special(gg)) ? 0.f : (q[k].x + q[k].y) + (q[k].z + q[k].w);
         const bool pf = (pfm >> gg) & 1;
+        if constexpr (kGB) {
+          const uint32_t rg = pf_reg(gg);
+          gb_pf[0] += rg == 0u ? t : 0.f;
+          gb_pf[1] += rg == 1u ? t : 0.f;
+          gb_pf[2] += rg == 2u ? t : 0.f;
+        }
         if (right) {
           s_pfR += pf ? t : 0.f;
           (k & 1 ? s_bk2 : s_bk) += pf ? 0.f : t;
@@ -541,6 +560,25 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       s_p0 += pf_wins ? 0.f : tp;
       (score && g >= 20 ? s_pfR : s_pf) += (pf ? tn : 0.f) + (pf_wins ? tp : 0.f);
       s_bk += pf ? 0.f : tn;
+      if constexpr (kGB) {
+        // C_with - C_without of the pixel's GRP0 bit (inside the player's
+        // 8-pixel span) and of its playfield bit, from the priority logic
+        const uint32_t span = d0 < 8 ? (0xFFu >> d0) & 0xF : (d0 > 156 ? (0xFFu << (160 - d0)) & 0xF : 0u);
+        const float c0 = (float)(r.col0 & 0xFE), cf = (float)(r.colpf & 0xFE), cb = (float)(r.colbk & 0xFE);
+        const float dgrp = pf_wins ? 0.f : (pf ? c0 - cf : c0 - cb);
+        float tg = 0.f, tf = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const bool p0 = (nib >> j) & 1;
+          tg += ((span >> j) & 1) ? v[j] * dgrp : 0.f;
+          tf += v[j] * (p0 ? (pf_first ? cf - c0 : 0.f) : cf - cb);
+        }
+        gb_g += tg;
+        const uint32_t rg = pf_reg(g);
+        gb_f[0] += rg == 0u ? tf : 0.f;
+        gb_f[1] += rg == 1u ? tf : 0.f;
+        gb_f[2] += rg == 2u ? tf : 0.f;
+      }
     }
     // Position sampler (Section 3): the player's coverage relaxed with a
     // triangular kernel has, at the integer position, the symmetric slope
@@ -575,6 +613,12 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
     // score mode: the playfield sums belong to COLUP0 (left) and COLUP1 (right)
     if (score) tape.pixels(s_p0 + s_pf, 0.f, s_bk, s_pos, s_pfR);
     else tape.pixels(s_p0, s_pf, s_bk, s_pos, 0.f);
+    if constexpr (kGB) {
+      // a plain group holds no player column: its playfield bit's colours
+      // are COLUPF with the bit and COLUBK without
+      const float dpf = (float)(r.colpf & 0xFE) - (float)(r.colbk & 0xFE);
+      tape.gbits(gb_g, gb_f[0] + dpf * gb_pf[0], gb_f[1] + dpf * gb_pf[1], gb_f[2] + dpf * gb_pf[2]);
+    }
   } else {
     // Groups g0 and gl may be partly inside [x0, x1); the ones between are
     // whole words.  Background and playfield first (one select per group,

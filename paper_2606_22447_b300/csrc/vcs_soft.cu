@@ -46,11 +46,13 @@ namespace vcs {
 
 // carried adjoints: aA aX aY aV aC0 aC1 aC2, aRAM[128] and its compensation,
 // those of player 0's position and of HMP0 (position sampler), the Superchip
-// RAM's adjoints [128] and their compensation, then COLUP1's
+// RAM's adjoints [128] and their compensation, COLUP1's, then those of
+// GRP0 and PF0-2 (graphics-bit surrogate)
 constexpr int kCarryPos = 7 + 256;
 constexpr int kCarryCram = kCarryPos + 2;
 constexpr int kCarryC3 = kCarryCram + 256;
-constexpr int kCarry = kCarryC3 + 1;
+constexpr int kCarryGB = kCarryC3 + 1;   // GRP0, PF0, PF1, PF2 (graphics-bit surrogate)
+constexpr int kCarry = kCarryGB + 4;
 constexpr int kMaxW = 120;        // window half-width limit (tau <= 10)
 
 // Compensated (Neumaier) sum: s + c carries the running total.
@@ -63,10 +65,14 @@ __device__ __forceinline__ void comp_add(float& s, float& c, float x) {
 
 // SAMPLER: the position sampler is on (its pixel sums are compiled out of
 // the other instantiation, which then carries zero position adjoints).
-template <bool SAMPLER>
+// GB: the graphics-bit surrogate is on: GRP0, PF0, PF1 and PF2 are
+// versioned quantities too (versions 5..8), their pixel sums the
+// renderer's with-minus-without colours.
+template <bool SAMPLER, bool GB>
 struct RecTape {
   static constexpr bool kAcc = true;
   static constexpr bool sampler = SAMPLER;
+  static constexpr bool graphics = GB;
   uint32_t* buf;
   float* cw;
   uint32_t n, cap, ncw, capcw;
@@ -76,6 +82,9 @@ struct RecTape {
   int32_t slot0, slot1, slot2, slot3, slot4;  // float slot of each live version
   float s0, s1, s2, s3, s4, c0, c1, c2, c3, c4;  // compensated pixel-gradient sums of the live versions
   float p0, p1, p2, p3, p4;        // sums of the versions alive at the segment start
+  // versions 5..8 (GB): GRP0, PF0, PF1, PF2
+  int32_t slot5, slot6, slot7, slot8;
+  float s5, s6, s7, s8, c5, c6, c7, c8, p5, p6, p7, p8;
   bool overflow;
   uint32_t T, gmask;               // replicas of this env and their warp lanes
   // The replicas of an env each sum the pixel chunks they own; a version's
@@ -103,7 +112,11 @@ struct RecTape {
     else if (r == 1) { close_version(slot1, s1 + c1, p1); s1 = c1 = 0.f; slot1 = fresh; }
     else if (r == 2) { close_version(slot2, s2 + c2, p2); s2 = c2 = 0.f; slot2 = fresh; }
     else if (r == 3) { close_version(slot3, s3 + c3, p3); s3 = c3 = 0.f; slot3 = fresh; }
-    else { close_version(slot4, s4 + c4, p4); s4 = c4 = 0.f; slot4 = fresh; }
+    else if (r == 4) { close_version(slot4, s4 + c4, p4); s4 = c4 = 0.f; slot4 = fresh; }
+    else if (r == 5) { close_version(slot5, s5 + c5, p5); s5 = c5 = 0.f; slot5 = fresh; }
+    else if (r == 6) { close_version(slot6, s6 + c6, p6); s6 = c6 = 0.f; slot6 = fresh; }
+    else if (r == 7) { close_version(slot7, s7 + c7, p7); s7 = c7 = 0.f; slot7 = fresh; }
+    else { close_version(slot8, s8 + c8, p8); s8 = c8 = 0.f; slot8 = fresh; }
   }
   __device__ __forceinline__ void version_write(uint32_t reg) {
     if (reg == 0x06) colour_write(0);
@@ -111,6 +124,8 @@ struct RecTape {
     else if (reg == 0x09) colour_write(2);
     else if (reg == 0x10 || reg == 0x2A) colour_write(3);
     else if (reg == 0x07) colour_write(4);
+    else if (GB && reg == 0x1B) colour_write(5);
+    else if (GB && reg >= 0x0D && reg <= 0x0F) colour_write(6 + (int)(reg - 0x0D));
   }
   // pixel-gradient sums of one drawn span, per owner (COLUP0, COLUPF,
   // COLUBK, COLUP1), and the sampler's sum
@@ -121,6 +136,13 @@ struct RecTape {
     if constexpr (SAMPLER) comp_add(s3, c3, v3);
     if (v4 != 0.f) comp_add(s4, c4, v4);
   }
+  // graphics-bit sums of one drawn span: GRP0, PF0, PF1, PF2
+  __device__ __forceinline__ void gbits(float g, float f0, float f1, float f2) {
+    comp_add(s5, c5, g);
+    comp_add(s6, c6, f0);
+    comp_add(s7, c7, f1);
+    comp_add(s8, c8, f2);
+  }
   __device__ __forceinline__ void finish() {
     close_version(slot0, s0 + c0, p0);
     close_version(slot1, s1 + c1, p1);
@@ -128,6 +150,13 @@ struct RecTape {
     close_version(slot3, s3 + c3, p3);
     close_version(slot4, s4 + c4, p4);
     s0 = s1 = s2 = s3 = s4 = c0 = c1 = c2 = c3 = c4 = 0.f;
+    if constexpr (GB) {
+      close_version(slot5, s5 + c5, p5);
+      close_version(slot6, s6 + c6, p6);
+      close_version(slot7, s7 + c7, p7);
+      close_version(slot8, s8 + c8, p8);
+      s5 = s6 = s7 = s8 = c5 = c6 = c7 = c8 = 0.f;
+    }
   }
 };
 
@@ -167,6 +196,7 @@ struct BwdParams {
   int32_t W;
   uint32_t sched_policy, sched_window;
   int32_t sampler;            // the position sampler is on
+  int32_t graphics;           // the graphics-bit surrogate is on
   int32_t step_instr;         // > 0: instruction-granular steps of this many slots
   int32_t* err;
 };
@@ -198,6 +228,7 @@ __device__ __forceinline__ Acc operator-(const Acc& x) { return Acc{-x.s, -x.c};
 
 struct Adj {
   Acc A, X, Y, V, C0, C1, C2, C3;   // C3: COLUP1
+  Acc G[4];            // GRP0, PF0, PF1, PF2 (graphics-bit surrogate)
   float P, H;          // player 0's position and HMP0 (position sampler)
   float u[5], uc[5];   // joystick-input adjoints of the current step (compensated)
 };
@@ -284,7 +315,7 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
 
 // Adjoint of the value written to `ref`: taken from the cell (which is then
 // cleared, the write being one-hot).
-template <bool SAMPLER, bool XM>
+template <bool SAMPLER, bool GB, bool XM>
 __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
                                           uint32_t& j, uint32_t kind, uint32_t ref) {
   const uint32_t ad = ref & 0x1FFF;
@@ -302,6 +333,12 @@ __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uin
     if (reg == 0x08) { if (j) a.C1 += cw[--j]; return a.C1.take(); }
     if (reg == 0x09) { if (j) a.C2 += cw[--j]; return a.C2.take(); }
     if (reg == 0x07) { if (j) a.C3 += cw[--j]; return a.C3.take(); }
+    if constexpr (GB) {   // GRP0 and PF0-2 (graphics-bit surrogate)
+      if (reg == 0x1B) { if (j) a.G[0] += cw[--j]; return a.G[0].take(); }
+      if (reg == 0x0D) { if (j) a.G[1] += cw[--j]; return a.G[1].take(); }
+      if (reg == 0x0E) { if (j) a.G[2] += cw[--j]; return a.G[2].take(); }
+      if (reg == 0x0F) { if (j) a.G[3] += cw[--j]; return a.G[3].take(); }
+    }
     // RESP0 and HMOVE open a position version (its slot pops either way)
     if (reg == 0x2A || reg == 0x10) {
       const float sv = j ? cw[--j] : 0.f;
@@ -338,7 +375,7 @@ __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uin
 
 __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
 
-template <bool SAMPLER, bool XM>
+template <bool SAMPLER, bool GB, bool XM>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                             const float* izr, int W, RomQueue& rq,
                                             uint32_t kind, const float* cw, uint32_t& j, uint32_t rec) {
@@ -376,19 +413,19 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
       break;
     }
     case 0x87: case 0x97: case 0x8F: case 0x83: {                   // SAX: M = A & X, the (1, 1) rule
-      const Acc g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      const Acc g = take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, ref);
       a.A += g;
       a.X += g;
       break;
     }
     case 0x85: case 0x95: case 0x8D: case 0x9D: case 0x99: case 0x81: case 0x91:
-      a.A += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      a.A += take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x86: case 0x96: case 0x8E:
-      a.X += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      a.X += take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x84: case 0x94: case 0x8C:
-      a.Y += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      a.Y += take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, ref);
       break;
     case 0x06: case 0x16: case 0x0E: case 0x1E:
     case 0x26: case 0x36: case 0x2E: case 0x3E:
@@ -396,7 +433,7 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0x66: case 0x76: case 0x6E: case 0x7E:
     case 0xC6: case 0xD6: case 0xCE: case 0xDE:
     case 0xE6: case 0xF6: case 0xEE: case 0xFE: {
-      const Acc g = take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref);
+      const Acc g = take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, ref);
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
@@ -405,21 +442,21 @@ __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, u
     case 0xA8: a.A += a.Y.take(); break;   // TAY
     case 0x98: a.Y += a.A.take(); break;   // TYA
     case 0xBA: a.X.clear(); break;         // TSX: SP carries nothing
-    case 0x48: a.A += take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref); break;   // PHA
-    case 0x08: take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, ref); break;           // PHP
+    case 0x48: a.A += take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, ref); break;   // PHA
+    case 0x08: take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, ref); break;           // PHP
     case 0x68: {                                                    // PLA
       const Acc g = a.A.take();
       scatter_read<XM>(a, aram, aramc, E, ek, izr, W, rq, kind, ref, fl, g);
       break;
     }
     case 0x20:                                                      // JSR: two pushes
-      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
-      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
+      take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
+      take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
       break;
     case 0x00:                                                      // BRK: three pushes
-      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 2));
-      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
-      take_write<SAMPLER, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
+      take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 2));
+      take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 1));
+      take_write<SAMPLER, GB, XM>(a, aram, aramc, E, cw, j, kind, stack_addr(ref, 0));
       break;
     default:
       break;
@@ -452,9 +489,9 @@ __device__ __forceinline__ void read_tables(float* ek, float* izr, float tau, in
 // run one segment at a time, last to first, each handing its adjoints to
 // the next.  Per (segment slot g, env) the recompute leaves the tape rows,
 // the colour / position version sums, the step ends and a small record
-// (kMeta words: version count, overflow flag, the sums of the versions
-// alive at the segment start).
-constexpr int kMeta = 8;
+// (kMeta words: version count, overflow flag, the sums of the nine
+// versions alive at the segment start).
+constexpr int kMeta = 12;
 
 // Recompute shared memory: the step kernel's layout, then the staged
 // gradient rows (16-byte aligned).
@@ -480,7 +517,7 @@ __host__ __device__ constexpr size_t sw_tables_end() {
 }
 __host__ __device__ constexpr size_t sw_smem_bytes() { return sw_tables_end() + (size_t)kSweepEnvs * kSweepWarpWords * 4; }
 
-template <int T, bool SAMPLER, bool INSTR, bool XM, bool FT>
+template <int T, bool SAMPLER, bool GB, bool INSTR, bool XM, bool FT>
 __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int E = blockDim.x / T, tid = threadIdx.x, slot = tid / T, rank = tid % T;
@@ -505,7 +542,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   } else {
     power_on(c, r);
   }
-  RecTape<SAMPLER> tape;
+  RecTape<SAMPLER, GB> tape;
   tape.buf = p.rec + ((size_t)g * n + env) * p.cap_rec;
   tape.cw = p.cw + ((size_t)g * n + env) * p.cap_cw;
   tape.n = 0; tape.cap = p.cap_rec;
@@ -514,6 +551,9 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   tape.s0 = tape.s1 = tape.s2 = tape.s3 = tape.s4 = 0.f;
   tape.c0 = tape.c1 = tape.c2 = tape.c3 = tape.c4 = 0.f;
   tape.p0 = tape.p1 = tape.p2 = tape.p3 = tape.p4 = 0.f;
+  tape.slot5 = tape.slot6 = tape.slot7 = tape.slot8 = -1;
+  tape.s5 = tape.s6 = tape.s7 = tape.s8 = tape.c5 = tape.c6 = tape.c7 = tape.c8 = 0.f;
+  tape.p5 = tape.p6 = tape.p7 = tape.p8 = 0.f;
   tape.overflow = false;
   tape.T = (uint32_t)T;
   tape.gmask = c.gmask;
@@ -552,6 +592,10 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   m[4] = tape.p2;
   m[5] = tape.p3;
   m[6] = tape.p4;
+  m[7] = tape.p5;
+  m[8] = tape.p6;
+  m[9] = tape.p7;
+  m[10] = tape.p8;
   if (tape.overflow) atomicExch(p.err, 2);
 }
 
@@ -559,7 +603,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
 // env per warp (lane 0): adjoints of A, X, Y, the timer value, the colour
 // registers, player 0's position and HMP0 in registers, the 128 RAM cells and
 // the Superchip's 128 (compensated) in shared memory.
-template <bool SAMPLER, bool XM>
+template <bool SAMPLER, bool GB, bool XM>
 __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr int E = kSweepEnvs;
@@ -591,6 +635,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   if (lead) {
     if (p.first) {
       a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.C3 = acc(0.f);
+      a.G[0] = a.G[1] = a.G[2] = a.G[3] = acc(0.f);
       a.P = a.H = 0.f;
       for (int i = 0; i < cells; i++) aram[i * E] = 0.f;
       for (int i = 0; i < cells; i++) aramc[i * E] = 0.f;
@@ -600,6 +645,8 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       a.V = acc(cr[3 * n + env]);
       a.C0 = acc(cr[4 * n + env]); a.C1 = acc(cr[5 * n + env]); a.C2 = acc(cr[6 * n + env]);
       a.C3 = acc(cr[(size_t)kCarryC3 * n + env]);
+#pragma unroll
+      for (int k = 0; k < 4; k++) a.G[k] = acc(GB ? cr[(size_t)(kCarryGB + k) * n + env] : 0.f);
       a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
       a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
       for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
@@ -654,7 +701,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       }
       if (lead)
         for (uint32_t q = k; q > lo; q--)
-          reverse_one<SAMPLER, XM>(a, aram, aramc, E, ek, izr, p.W, rq, kind, cw, j, recs[q - 1 - 4 * c0]);
+          reverse_one<SAMPLER, GB, XM>(a, aram, aramc, E, ek, izr, p.W, rq, kind, cw, j, recs[q - 1 - 4 * c0]);
       // the warp adds the block's ROM impulses: lane l takes the indices
       // congruent to l mod 32, each in queue order
       const uint32_t qn = __shfl_sync(0xFFFFFFFFu, rq.n, 0);
@@ -684,6 +731,10 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   a.C2 += m[4];
   a.C3 += m[6];
   if constexpr (SAMPLER) a.P += m[5];
+  if constexpr (GB) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) a.G[k] += m[7 + k];
+  }
   if (p.seg == 0) {
     if (p.grad_ram0)
       for (int i = 0; i < 128; i++) p.grad_ram0[(size_t)env * 128 + i] = aram[i * E] + aramc[i * E];
@@ -695,6 +746,10 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
     cr[0 * n + env] = a.A.v(); cr[1 * n + env] = a.X.v(); cr[2 * n + env] = a.Y.v(); cr[3 * n + env] = a.V.v();
     cr[4 * n + env] = a.C0.v(); cr[5 * n + env] = a.C1.v(); cr[6 * n + env] = a.C2.v();
     cr[(size_t)kCarryC3 * n + env] = a.C3.v();
+    if constexpr (GB) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) cr[(size_t)(kCarryGB + k) * n + env] = a.G[k].v();
+    }
     cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
@@ -725,20 +780,30 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
     // instruction-granular steps draw nothing (no pixel sums, no position
     // sampler), so one lane per env serves them
     if (p.step_instr > 0) {
-      go(k_soft_recompute<1, false, true, XM, FT>, E);
+      go(k_soft_recompute<1, false, false, true, XM, FT>, E);
+    } else if (!FT && p.graphics) {
+      // the graphics-bit surrogate (subset machine only) is built for one
+      // lane per env and for four replicas: 2 runs as 1 and 8 as 4
+      if (p.sampler) {
+        if (T >= 4) go(k_soft_recompute<4, true, true, false, XM, false>, 4 * E);
+        else go(k_soft_recompute<1, true, true, false, XM, false>, E);
+      } else {
+        if (T >= 4) go(k_soft_recompute<4, false, true, false, XM, false>, 4 * E);
+        else go(k_soft_recompute<1, false, true, false, XM, false>, E);
+      }
     } else if (p.sampler) {
       switch (T) {
-        case 1: go(k_soft_recompute<1, true, false, XM, FT>, E); break;
-        case 2: go(k_soft_recompute<2, true, false, XM, FT>, 2 * E); break;
-        case 4: go(k_soft_recompute<4, true, false, XM, FT>, 4 * E); break;
-        default: go(k_soft_recompute<8, true, false, XM, FT>, 8 * E); break;
+        case 1: go(k_soft_recompute<1, true, false, false, XM, FT>, E); break;
+        case 2: go(k_soft_recompute<2, true, false, false, XM, FT>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, true, false, false, XM, FT>, 4 * E); break;
+        default: go(k_soft_recompute<8, true, false, false, XM, FT>, 8 * E); break;
       }
     } else {
       switch (T) {
-        case 1: go(k_soft_recompute<1, false, false, XM, FT>, E); break;
-        case 2: go(k_soft_recompute<2, false, false, XM, FT>, 2 * E); break;
-        case 4: go(k_soft_recompute<4, false, false, XM, FT>, 4 * E); break;
-        default: go(k_soft_recompute<8, false, false, XM, FT>, 8 * E); break;
+        case 1: go(k_soft_recompute<1, false, false, false, XM, FT>, E); break;
+        case 2: go(k_soft_recompute<2, false, false, false, XM, FT>, 2 * E); break;
+        case 4: go(k_soft_recompute<4, false, false, false, XM, FT>, 4 * E); break;
+        default: go(k_soft_recompute<8, false, false, false, XM, FT>, 8 * E); break;
       }
     }
   };
@@ -750,11 +815,20 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
 
 static cudaError_t launch_sweep(const BwdParams& p, cudaStream_t s) {
   const int n_blocks = (p.n_envs + kSweepEnvs - 1) / kSweepEnvs;
-  const bool sampler = p.sampler && p.step_instr <= 0, xm = p.xmap != 0;
-  if (sampler && xm) k_soft_sweep<true, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
-  else if (sampler) k_soft_sweep<true, false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
-  else if (xm) k_soft_sweep<false, true><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
-  else k_soft_sweep<false, false><<<n_blocks, 32 * kSweepEnvs, sw_smem_bytes(), s>>>(p);
+  const bool sampler = p.sampler && p.step_instr <= 0, gb = p.graphics != 0, xm = p.xmap != 0;
+  const dim3 grid(n_blocks), block(32 * kSweepEnvs);
+  const size_t sm = sw_smem_bytes();
+  if (gb) {
+    if (sampler && xm) k_soft_sweep<true, true, true><<<grid, block, sm, s>>>(p);
+    else if (sampler) k_soft_sweep<true, true, false><<<grid, block, sm, s>>>(p);
+    else if (xm) k_soft_sweep<false, true, true><<<grid, block, sm, s>>>(p);
+    else k_soft_sweep<false, true, false><<<grid, block, sm, s>>>(p);
+  } else {
+    if (sampler && xm) k_soft_sweep<true, false, true><<<grid, block, sm, s>>>(p);
+    else if (sampler) k_soft_sweep<true, false, false><<<grid, block, sm, s>>>(p);
+    else if (xm) k_soft_sweep<false, false, true><<<grid, block, sm, s>>>(p);
+    else k_soft_sweep<false, false, false><<<grid, block, sm, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
@@ -1109,6 +1183,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.W = t->W;
   p.tpe = b->tpe;
   p.sampler = b->cfg.position_sampler;
+  p.graphics = b->cfg.graphics_bits && b->cfg.step_instructions <= 0;
   p.step_instr = b->cfg.step_instructions;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
@@ -1305,6 +1380,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.W = t->W;
   p.tpe = b->tpe;
   p.sampler = b->cfg.position_sampler;
+  p.graphics = b->cfg.graphics_bits && b->cfg.step_instructions <= 0;
   p.step_instr = b->cfg.step_instructions;
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;

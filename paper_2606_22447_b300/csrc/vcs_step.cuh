@@ -27,9 +27,10 @@ namespace vcs {
 struct CountTape {
   static constexpr bool kAcc = false;
   uint32_t n = 0, ncw = 0;
+  uint64_t vregs = kVersionRegs;   // | kGraphicsRegs with the graphics-bit surrogate
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) { n++; }
   static constexpr bool sampler = false;
-  __device__ __forceinline__ void version_write(uint32_t reg) { ncw += (uint32_t)(kVersionRegs >> reg) & 1u; }
+  __device__ __forceinline__ void version_write(uint32_t reg) { ncw += (uint32_t)(vregs >> reg) & 1u; }
   __device__ __forceinline__ void pixels(float, float, float, float, float) {}
 };
 
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   }
 
   typename std::conditional<SOFT, CountTape, NoTape>::type tape;
+  if constexpr (SOFT) tape.vregs = kVersionRegs | (p.graphics ? kGraphicsRegs : 0ull);
   Render rd;
   rd.on = false;
   rd.cur = 0;

@@ -515,3 +515,78 @@ def test_soft_step_entry_point():
     h = C.c_void_p()
     assert L.vcs_soft_step(b.h, 0.0, p(u_t), n_steps, 1, None, None, C.byref(h), s) == _lib.VCS_ERR_ARG
     assert not h.value
+
+
+@pytest.mark.parametrize("ctrlpf,tpe", [(0, 1), (1, 4), (4, 4), (4, 1)])
+def test_graphics_bit_gradients_on_the_graphics_cart(ctrlpf, tpe):
+    """The graphics-bit surrogate on the GPU (vcs_config.graphics_bits): the
+    oracle's pin cart (GRP0 from the joystick, PF0-2 from immediates, plain,
+    reflected and playfield-first priority), joystick and ROM gradients
+    against the FP64 oracle."""
+    from tests.microrom import graphics_rom
+    torch = torch_cuda()
+    rom, _ = graphics_rom(ctrlpf)
+    n_envs, n_steps, tau = 6, 4, 0.01
+    b = make_batch([rom], [synth.MAPPER_4K], np.zeros(n_envs, np.int32), graphics_bits=1, threads_per_env=tpe,
+                   envs_per_block=8, segment_frames=2)
+    acts = synth.actions(91 + ctrlpf, n_envs, n_steps)
+    u = synth.action_inputs(acts)
+    gs = synth.normal_f32(91, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, b.rom_stride), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(None, torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_u=g_u)
+    b.sync()
+    g_rom, g_u = g_rom.cpu().numpy(), g_u.cpu().numpy()
+    for e in range(n_envs):
+        o = oracle.Oracle(rom, synth.MAPPER_4K)
+        o.set_graphics(True)
+        g, _, _ = o.soft_rollout(u[:, e].astype(np.float64), 1, tau, 6.0, None, gs[:, e].astype(np.float64),
+                                 outputs=False)
+        o_rom, _, o_u = g.reverse()
+        assert np.abs(o_u).max() > 1.0
+        assert_grad_close(g_u[:, e], o_u, f"env {e} grad_u")
+        assert_grad_close(g_rom[e, :4096], o_rom, f"env {e} grad_rom")
+
+
+@pytest.mark.parametrize("tpe,seg", [(1, 64), (4, 2)])
+def test_graphics_bit_gradients_on_synthetic_carts(tpe, seg):
+    """Generated carts of several formats (their kernels store GRP0 and the
+    playfield on every line) with the graphics-bit surrogate on and the
+    position sampler on in one case: ROM, initial RAM and input gradients
+    against the FP64 oracle over one and several checkpoint segments."""
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_2K, synth.MAPPER_FE]
+    n_envs, n_steps, tau = 8, 4, 0.1
+    sampler = seg == 2
+    torch, roms, env_cart, b, wa, acts, u = _setup(mappers, n_envs, n_steps, 93, envs_per_block=8,
+                                                   threads_per_env=tpe, segment_frames=seg, graphics_bits=1,
+                                                   position_sampler=1 if sampler else 0)
+    gr = synth.normal_f32(93, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(93, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, b.rom_stride), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u)
+    b.sync()
+    g_rom, g_ram0, g_u = g_rom.cpu().numpy(), g_ram0.cpu().numpy(), g_u.cpu().numpy()
+    for e in range(n_envs):
+        c = env_cart[e]
+        o = oracle.Oracle(roms[c], mappers[c])
+        o.rollout(wa[:, e], 1, screens=False)
+        o.set_graphics(True)
+        o.set_sampler(sampler)
+        g, _, _ = o.soft_rollout(u[:, e].astype(np.float64), 1, tau, 6.0, gr[:, e].astype(np.float64),
+                                 gs[:, e].astype(np.float64), outputs=False)
+        o_rom, o_ram0, o_u = g.reverse()
+        assert_grad_close(g_rom[e, :len(roms[c])], o_rom, f"env {e} grad_rom")
+        assert_grad_close(g_ram0[e], o_ram0, f"env {e} grad_ram0")
+        assert_grad_close(g_u[:, e], o_u, f"env {e} grad_u")
+
+
+def test_graphics_bits_refused_with_the_whole_tia():
+    from paper_2606_22447_b300 import VcsError
+    rom = synth.generate_cart(95, 0, synth.MAPPER_4K)
+    with pytest.raises(VcsError, match="graphics"):
+        make_batch([rom], [synth.MAPPER_4K], np.zeros(2, np.int32), graphics_bits=1, full_tia=1)
