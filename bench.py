@@ -213,7 +213,7 @@ def bench_counts() -> dict:
         return json.load(f)
 
 
-def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False, graphics=False):
+def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False, graphics=False, budget_mb=0):
     """SOFT-STE forward + backward over n_frames (frame-skip 1, 64-frame
     checkpoint segments, loss weights on 8 RAM bytes and 256 pixels at every
     step), optionally with the differentiable position sampler.  Returns
@@ -230,7 +230,7 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False,
     # env whatever this is
     b = Batch(roms, mappers, ec, default_config(segment_frames=64, threads_per_env=8,
                                                 position_sampler=1 if sampler else 0,
-                                                graphics_bits=1 if graphics else 0))
+                                                graphics_bits=1 if graphics else 0, tape_budget_mb=budget_mb))
     u = torch.from_numpy(synth.action_inputs(synth.actions(SEED, n_envs, n_frames))).cuda()
     rng = np.random.default_rng(SEED)
     w_ram = torch.zeros(128, device="cuda")
@@ -263,8 +263,8 @@ def soft_leg(n_envs, n_frames, mappers, reps, count_key, tau=0.1, sampler=False,
             "instructions_per_s": n_envs * n_frames * ipf / ((fwd + bwd) / 1e3),
             "instructions_per_frame": ipf, "fwd_ms": fwd, "bwd_ms": bwd,
             "n_envs": n_envs, "frames": n_frames, "tau": tau, "position_sampler": sampler,
-            "graphics_bits": graphics,
-            "tape_device_gb": used / 1e9,
+            "graphics_bits": graphics, "tape_budget_mb": budget_mb or "a quarter of free memory",
+            "tape_device_gb": used / 1e9,   # held by the rollout and its backward: checkpoints, tapes, impulses
             "gpu_launches": 1 + 2 * ((n_frames + 63) // 64) + 2}
 
 
@@ -529,6 +529,10 @@ def gpu_arm(args):
                                                    "soft_short_1024x4k_instructions_per_frame", graphics=True)}
         if not args.no_soft_long:
             soft["long_4096x2048"] = soft_leg(4096, 2048, _s.MIX8, 2, "soft_long_4096xmix8_instructions_per_frame")
+            # the same run with the backward's tapes held to 8 GB (fewer
+            # segments recomputed at once): its peak memory and speed
+            soft["long_4096x2048_budget8g"] = soft_leg(4096, 2048, _s.MIX8, 2,
+                                                       "soft_long_4096xmix8_instructions_per_frame", budget_mb=8192)
     mixed = None
     full_tia = None
     if not args.no_mixed:

@@ -399,8 +399,9 @@ vcs_status vcs_full_divergence(vcs_batch* b, float T, float alpha, const uint8_t
                                int32_t* n_div, uint32_t* counts, uint8_t* ram_full, void* stream);
 
 /* Wait for `stream` and report device-side failures: VCS_ERR_WATCHDOG if a
- * kernel's bounded wait gave up (the batch is then unusable), VCS_ERR_CUDA
- * for an asynchronous CUDA error. */
+ * kernel's bounded wait gave up (the batch is then unusable: destroy it;
+ * a block whose ROM staging timed out waited once more, also bounded, for
+ * its copy before leaving), VCS_ERR_CUDA for an asynchronous CUDA error. */
 vcs_status vcs_sync(vcs_batch* b, void* stream);
 
 /* ---------------------------------------------------------------------------

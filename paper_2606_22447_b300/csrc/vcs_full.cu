@@ -89,10 +89,7 @@ __global__ void __launch_bounds__(128) k_full(FullDivParams p, FullParams fp0) {
     *fp = fp0;
     fp->rom_m = p.cart_2k[cart] ? 2048 : (cart_is_e0(cb) ? 1024 : 4096);
   }
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb))) {   // synchronises the block
-    if (slot == 0) atomicExch(p.err, 1);
-    return;
-  }
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb), p.err)) return;   // synchronises the block
   if (slot >= bi.z) return;
   const int env = p.perm[bi.y + slot];
   const int n = p.n_envs;

@@ -366,6 +366,14 @@ __device__ __forceinline__ uint32_t timint_at(const Regs& r, uint32_t t) {
   return k > (r.tv << r.tsh) ? 0x80u : 0u;
 }
 
+// Shared-memory index of the staged gradients of 4-pixel group g (0..39) of
+// env slot `slot` in a block of E envs (a power of two): row g, the slot
+// rotated by g's chunk (g / 4).  The T replicas of an env read different
+// chunks at once; without the rotation they all hit the same four banks.
+__device__ __forceinline__ uint32_t grow_at(uint32_t g, uint32_t E, uint32_t slot) {
+  return g * E + (slot ^ ((g >> 2) & (E - 1)));
+}
+
 }  // namespace vcs
 
 // The rest of the TIA (player 1, missiles, ball, collisions) needs Ctx and
@@ -385,9 +393,11 @@ struct Render {
   float* out_f32;            // screen of this env (f32) or null
   const float* gs;           // pixel gradients of the returned frame [210][160]
                              // (backward recompute only) or null
-  float4* grow;              // shared: this env's staged gradient row, 40 float4 at stride E
+  float4* grow;              // shared: the block's staged gradient rows (grow_at)
+  uint32_t gslot;            // this env's slot in the block
   int32_t gline;             // frame line held in grow, or -1
 };
+
 
 // Stage the gradient row of frame line `line` into shared memory: the 40
 // loads go out in four batches of ten, so a row costs a few memory latencies
@@ -403,10 +413,10 @@ __device__ __forceinline__ void stage_grad_row(const Ctx& c, Render& rd, int32_t
 #pragma unroll
     for (int k = 0; k < 4; k++) t[4 + k] = q2 < 10 ? __ldg(src + 4 * q2 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 4; k++) rd.grow[(4 * q + k) * c.E] = t[k];
+    for (int k = 0; k < 4; k++) rd.grow[grow_at(4 * q + k, c.E, rd.gslot)] = t[k];
     if (q2 < 10) {
 #pragma unroll
-      for (int k = 0; k < 4; k++) rd.grow[(4 * q2 + k) * c.E] = t[4 + k];
+      for (int k = 0; k < 4; k++) rd.grow[grow_at(4 * q2 + k, c.E, rd.gslot)] = t[4 + k];
     }
   }
   rd.gline = line;
@@ -465,7 +475,8 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
     // wholly to the playfield or the background colour.
     if (blank_all || !rd.gs) return;
     if (general) {
-      const OwnerSums s = sums_general(make_view(c, r), rd.grow, c.E, c.rank, c.T, x0, x1, blank_g, tape.sampler);
+      const OwnerSums s = sums_general(make_view(c, r), rd.grow, c.E, rd.gslot, c.rank, c.T, x0, x1, blank_g,
+                                       tape.sampler);
       tape.pixels(s.s0, s.s1, s.s2, s.pos, s.s3);
       return;
     }
@@ -504,7 +515,7 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
       float4 q[4];
 #pragma unroll
       for (uint32_t k = 0; k < 4; k++)
-        q[k] = (g + k >= gs0 && g + k < g1) ? gl[(g + k) * c.E] : make_float4(0.f, 0.f, 0.f, 0.f);
+        q[k] = (g + k >= gs0 && g + k < g1) ? gl[grow_at(g + k, c.E, rd.gslot)] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (uint32_t k = 0; k < 4; k++) {
         const uint32_t gg = g + k;
@@ -539,7 +550,7 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
 #pragma unroll
       for (int cj = 0; cj < ci; cj++) dup |= cand[cj] == g;
       if (dup || g < gs0 || g >= g1 || !special(g) || !owns_chunk(c, g >> 2)) continue;
-      const float4 q = gl[g * c.E];
+      const float4 q = gl[grow_at(g, c.E, rd.gslot)];
       const uint32_t xb = 4 * g;
       const float v[4] = {(xb + 0 >= x0 && xb + 0 < x1) ? q.x : 0.f, (xb + 1 >= x0 && xb + 1 < x1) ? q.y : 0.f,
                           (xb + 2 >= x0 && xb + 2 < x1) ? q.z : 0.f, (xb + 3 >= x0 && xb + 3 < x1) ? q.w : 0.f};
@@ -602,7 +613,7 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
         const uint32_t g = ux >> 2;
         const bool pf = (pfm >> g) & 1;
         if (pf_first && pf) continue;
-        const float4 q = gl[g * c.E];
+        const float4 q = gl[grow_at(g, c.E, rd.gslot)];
         const uint32_t k = ux & 3;
         const float w = k == 0 ? q.x : (k == 1 ? q.y : (k == 2 ? q.z : q.w));
         const uint32_t cpfx = score ? (ux < 80 ? r.col0 : col1) : r.colpf;   // the playfield's colour here

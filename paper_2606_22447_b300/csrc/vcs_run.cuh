@@ -41,9 +41,12 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 
 // Stage the decode table (plain loads) and the cartridge image (one TMA bulk
 // copy completing on an mbarrier).  Returns false if the copy did not land
-// within the wait budget; every thread then leaves the kernel.
+// within the wait budget: the block then raises the device error word
+// (*err = 1, which the host reports as VCS_ERR_WATCHDOG; the batch is then
+// unusable), waits once more, again bounded, for the copy still in flight
+// to this block's shared memory, and every thread leaves the kernel.
 __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTables* dt, const uint8_t* src,
-                                            uint32_t bytes) {
+                                            uint32_t bytes, int32_t* err) {
   const uint32_t bar = smem_addr(b.mbar);
   for (int i = threadIdx.x; i < (int)(sizeof(DecodeTables) / 4); i += blockDim.x)
     reinterpret_cast<uint32_t*>(b.dt)[i] = reinterpret_cast<const uint32_t*>(dt)[i];
@@ -60,16 +63,24 @@ __device__ __forceinline__ bool stage_block(const BlockSmem& b, const DecodeTabl
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
   }
-  uint32_t done = 0;
-  for (uint32_t spin = 0; spin < (1u << 24) && !done; spin++) {
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(bar)
-        : "memory");
+  auto wait = [&](uint32_t polls) {
+    uint32_t done = 0;
+    for (uint32_t spin = 0; spin < polls && !done; spin++) {
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+          : "=r"(done)
+          : "r"(bar)
+          : "memory");
+    }
+    return done != 0;
+  };
+  const bool done = wait(1u << 24);
+  if (!done) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    (void)wait(1u << 24);   // let the copy in flight land before the block's shared memory is released
   }
   __syncthreads();
-  return done != 0;
+  return done;
 }
 
 // Context of one replica: env slot `slot` of the block (E envs), replica

@@ -527,10 +527,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   const int cart = bi.x;
   const uint32_t cb = p.cart_banks[cart];
   const int g = blockIdx.y, seg = p.seg0 + g;
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb))) {
-    if (tid == 0) atomicExch(p.err, 1);
-    return;
-  }
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb), p.err)) return;
   const bool active = slot < bi.z;
   const int env = active ? p.perm[bi.y + slot] : 0;
   const int n = p.n_envs;
@@ -565,7 +562,8 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   rd.cur = 0;
   rd.out_u8 = nullptr;
   rd.out_f32 = nullptr;
-  rd.grow = grow + slot;
+  rd.grow = grow;
+  rd.gslot = (uint32_t)slot;
   for (int t = t0; t < t1; t++) {
     set_input_bits(r, active ? p.act_bits[(size_t)t * n + env] : 0u);
     Step st;

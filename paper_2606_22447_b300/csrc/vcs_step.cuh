@@ -55,10 +55,7 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   const int4 bi = p.blocks[blockIdx.x];
   const int cart = bi.x;
   const uint32_t cb = p.cart_banks[cart];
-  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb))) {
-    if (tid == 0) atomicExch(p.err, 1);
-    return;
-  }
+  if (!stage_block(bs, p.dt, p.roms + (size_t)cart * p.rom_stride, cart_image_bytes(cb), p.err)) return;
   // lanes past the block's env count idle but stay for the warp reductions
   const bool active = slot < bi.z;
   const int env = active ? p.perm[bi.y + slot] : 0;

@@ -389,7 +389,8 @@ static __device__ __noinline__ void draw_general(const TiaView v, uint32_t* line
 struct OwnerSums {
   float s0, s1, s2, s3, pos;
 };
-static __device__ __noinline__ OwnerSums sums_general(const TiaView v, const float4* grow, uint32_t E, uint32_t rank,
+static __device__ __noinline__ OwnerSums sums_general(const TiaView v, const float4* grow, uint32_t E, uint32_t slot,
+                                                      uint32_t rank,
                                                       uint32_t T, uint32_t x0, uint32_t x1, uint32_t blank_g,
                                                       bool sampler) {
   LineMasks L;
@@ -399,7 +400,7 @@ static __device__ __noinline__ OwnerSums sums_general(const TiaView v, const flo
   OwnerSums s{0.f, 0.f, 0.f, 0.f, 0.f};
   for (uint32_t g = x0 >> 2; 4 * g < x1; g++) {
     if (((g >> 2) & (T - 1)) != rank || g < blank_g) continue;
-    const float4 q = grow[g * E];
+    const float4 q = grow[grow_at(g, E, slot)];
     uint32_t in = 0xF;   // the group's columns inside [x0, x1)
     if (4 * g < x0) in &= 0xFu << (x0 - 4 * g);
     if (4 * g + 4 > x1) in &= 0xFu >> (4 * g + 4 - x1);
