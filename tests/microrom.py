@@ -300,3 +300,59 @@ def graphics_rom(ctrlpf=0):
         a.op("BNE", "rel", "L")
         a.op("JMP", "abs", "FRAME")
     return rom4k(build, table=False), offs
+
+
+GRAPHICS_FT_COLOURS = {"bk": 0x20, "pf": 0x44, "p0": 0x86, "p1": 0xC8}
+GRAPHICS_FT_PF = (0x30, 0x81, 0x0C)
+
+
+def graphics_full_tia_rom(ctrlpf=0, vdel=False):
+    """Every object of the whole TIA on every visible line: player 0, player
+    1, missile 0 (2 wide), the ball (4 wide) and a playfield, each strobed to
+    its own position on the scanlines above the visible rows.  Each frame
+    copies SWCHA into GRP1 (the joystick drives player 1's bits) and stores
+    GRP0, ENAM0, ENABL and PF0-2 from immediates.  With `vdel` player 1 shows
+    its delayed graphic (VDELP1): SWCHA is stored to GRP1, then GRP0's store
+    copies it to the delayed register, then an immediate is stored to GRP1
+    (which the screen then does not show).  Returns (image, ROM offsets of
+    the immediates by name)."""
+    offs = {}
+
+    def imm(a, name, v, reg):
+        offs[name] = a.pc + 1 - 0xF000
+        a.op("LDA", "imm", v)
+        a.op("STA", "zp", reg)
+
+    def build(a):
+        for reg, v in ((0x09, GRAPHICS_FT_COLOURS["bk"]), (0x08, GRAPHICS_FT_COLOURS["pf"]),
+                       (0x06, GRAPHICS_FT_COLOURS["p0"]), (0x07, GRAPHICS_FT_COLOURS["p1"]),
+                       (0x0A, ctrlpf | 0x20), (0x04, 0x10), (0x26, 1 if vdel else 0)):
+            a.op("LDA", "imm", v)
+            a.op("STA", "zp", reg)
+        a.label("FRAME")
+        a.op("LDA", "imm", 2)
+        a.op("STA", "zp", 0x02)
+        a.op("STA", "zp", 0x00)            # VSYNC on: the frame boundary
+        a.op("LDA", "imm", 0)
+        a.op("STA", "zp", 0x00)
+        for reg, nops in ((0x10, 12), (0x11, 22), (0x12, 26), (0x14, 17)):   # RESP0 RESP1 RESM0 RESBL
+            a.op("STA", "zp", 0x02)        # WSYNC
+            for _ in range(nops):
+                a.op("NOP")
+            a.op("STA", "zp", reg)
+        a.op("LDA", "abs", 0x0280)         # SWCHA
+        a.op("STA", "zp", 0x1C)            # GRP1
+        imm(a, "grp0", 0xA5, 0x1B)
+        if vdel:
+            imm(a, "grp1", 0x3C, 0x1C)
+        imm(a, "enam0", 0x02, 0x1D)
+        imm(a, "enabl", 0x02, 0x1F)
+        for name, reg, v in zip(("pf0", "pf1", "pf2"), (0x0D, 0x0E, 0x0F), GRAPHICS_FT_PF):
+            imm(a, name, v, reg)
+        a.op("LDX", "imm", 0)
+        a.label("L")
+        a.op("STA", "zp", 0x02)
+        a.op("DEX")
+        a.op("BNE", "rel", "L")
+        a.op("JMP", "abs", "FRAME")
+    return rom4k(build, table=False), offs
