@@ -37,13 +37,13 @@ WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+sc
 # DRAM bytes (read + write) of one step launch on the bench workload, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
 # kernel; to be taken again whenever the kernel changes
-TRAFFIC_BYTES_PER_LAUNCH = 1_065_984 + 83_931_648
+TRAFFIC_BYTES_PER_LAUNCH = 950_016 + 83_741_696
 # Counters of the same ncu capture (one k_run<0, 1, 0, 0, 0, 0> launch, 4096
 # envs in 256 blocks of 16, one lane per env): the GPU-wide fraction of issue
 # slots used (smsp__issue_active.avg.pct_of_peak_sustained_elapsed) and the
 # thread instructions executed (smsp__thread_inst_executed.sum)
-MEASURED_ISSUE_ACTIVE = 0.0974
-MEASURED_THREAD_INST = 5_537_312_497
+MEASURED_ISSUE_ACTIVE = 0.0981
+MEASURED_THREAD_INST = 5_537_316_593
 OPS_PER_INSTRUCTION = 12
 OPS_PER_PIXEL = 6
 PIXELS_PER_STEP = 210 * 160
