@@ -164,16 +164,20 @@ typedef struct vcs_config {
                                (with the switch stored, graphics bits are
                                differentiable) in soft backward passes: each
                                drawn pixel adds (C_with - C_without) times
-                               its gradient to GRP0 where player 0's 8-pixel
-                               span covers it and to the playfield register
-                               (PF0, PF1 or PF2) of its column, C_with and
-                               C_without being the pixel's colours with that
-                               bit forced to 1 and to 0 (the bit's derivative
-                               with respect to its byte is 1); the written
-                               values of GRP0 and PF0-2 then receive these
-                               sums.  0 = off (default).  The subset machine
-                               only: with full_tia, VCS_ERR_ARG.  Forward
-                               outputs do not depend on it. */
+                               its gradient to the byte of each graphics bit
+                               deciding an object's coverage there, C_with
+                               and C_without being the pixel's colours with
+                               that bit forced to 1 and to 0 (the bit's
+                               derivative with respect to its byte is 1):
+                               GRP0 over player 0's span and the playfield
+                               register (PF0, PF1 or PF2) of the column; with
+                               full_tia also GRP1 over player 1's copies,
+                               ENAM0 / ENAM1 and ENABL over the missiles' and
+                               the ball's spans, a delayed graphic's sum going
+                               to the value its copy took.  The written values
+                               of these registers then receive the sums.
+                               0 = off (default).  Forward outputs do not
+                               depend on it. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

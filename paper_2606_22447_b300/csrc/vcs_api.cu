@@ -352,11 +352,9 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "position_sampler must be 0 or 1");
   }
-  if (b->cfg.graphics_bits < 0 || b->cfg.graphics_bits > 1 || (b->cfg.graphics_bits && b->cfg.full_tia)) {
+  if (b->cfg.graphics_bits < 0 || b->cfg.graphics_bits > 1) {
     free_batch(b);
-    return vcs_fail(nullptr, VCS_ERR_ARG,
-                    "graphics_bits must be 0 or 1, and 0 with full_tia (graphics-bit gradients are built for "
-                    "the subset machine: player 0 and the playfield)");
+    return vcs_fail(nullptr, VCS_ERR_ARG, "graphics_bits must be 0 or 1");
   }
   if (b->cfg.sched_policy < 0 || b->cfg.sched_policy > 1) {
     free_batch(b);

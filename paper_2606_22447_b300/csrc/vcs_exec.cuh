@@ -67,6 +67,10 @@ constexpr uint64_t kVersionRegs = reg_bits({0x06, 0x07, 0x08, 0x09, 0x10, 0x2A})
 // With the graphics-bit surrogate, GRP0 and the playfield registers open
 // versions too.
 constexpr uint64_t kGraphicsRegs = reg_bits({0x0D, 0x0E, 0x0F, 0x1B});
+// With the whole TIA also GRP1, ENAM0, ENAM1 and ENABL; a GRP0 write opens
+// one more version (GRP1's delayed copy) and a GRP1 write two more (GRP0's
+// and ENABL's).
+constexpr uint64_t kGraphicsRegsFT = reg_bits({0x1C, 0x1D, 0x1E, 0x1F});
 
 // A write to a cold register (or a hot one with cold effects) at line clock
 // h: updates the cold words at tx (stride E) and returns the new summary

@@ -474,10 +474,16 @@ __device__ __forceinline__ void render_span(const Ctx& c, const Regs& r, const R
     // span into the version sums.  A group without player pixels belongs
     // wholly to the playfield or the background colour.
     if (blank_all || !rd.gs) return;
-    if (general) {
+    // with the graphics-bit surrogate every object of the whole TIA has bits
+    // in play somewhere, drawn or not: the general path sums them
+    if (general || (c.ft && Tape::graphics)) {
       const OwnerSums s = sums_general(make_view(c, r), rd.grow, c.E, rd.gslot, c.rank, c.T, x0, x1, blank_g,
                                        tape.sampler);
       tape.pixels(s.s0, s.s1, s.s2, s.pos, s.s3);
+      if constexpr (Tape::graphics) {
+        const GbSums gb = gbits_general(make_view(c, r), rd.grow, c.E, rd.gslot, c.rank, c.T, x0, x1, blank_g);
+        tape.gbits_all(gb.v);
+      }
       return;
     }
     const float4* gl = rd.grow;   // this line's gradients, staged by render_to

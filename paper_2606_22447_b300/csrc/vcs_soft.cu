@@ -47,12 +47,13 @@ namespace vcs {
 // carried adjoints: aA aX aY aV aC0 aC1 aC2, aRAM[128] and its compensation,
 // those of player 0's position and of HMP0 (position sampler), the Superchip
 // RAM's adjoints [128] and their compensation, COLUP1's, then those of
-// GRP0 and PF0-2 (graphics-bit surrogate)
+// the graphics-bit surrogate's quantities (GRP0, PF0-2, GRP1, ENAM0,
+// ENAM1, ENABL and the three delayed copies)
 constexpr int kCarryPos = 7 + 256;
 constexpr int kCarryCram = kCarryPos + 2;
 constexpr int kCarryC3 = kCarryCram + 256;
-constexpr int kCarryGB = kCarryC3 + 1;   // GRP0, PF0, PF1, PF2 (graphics-bit surrogate)
-constexpr int kCarry = kCarryGB + 4;
+constexpr int kCarryGB = kCarryC3 + 1;   // the graphics-bit surrogate's eleven quantities
+constexpr int kCarry = kCarryGB + 11;
 constexpr int kMaxW = 120;        // window half-width limit (tau <= 10)
 
 // Compensated (Neumaier) sum: s + c carries the running total.
@@ -65,14 +66,15 @@ __device__ __forceinline__ void comp_add(float& s, float& c, float x) {
 
 // SAMPLER: the position sampler is on (its pixel sums are compiled out of
 // the other instantiation, which then carries zero position adjoints).
-// GB: the graphics-bit surrogate is on: GRP0, PF0, PF1 and PF2 are
-// versioned quantities too (versions 5..8), their pixel sums the
-// renderer's with-minus-without colours.
-template <bool SAMPLER, bool GB>
+// GB: the graphics-bit surrogate is on: its quantities are versioned too,
+// their pixel sums the renderer's with-minus-without colours; FT: the whole
+// TIA (the surrogate's eleven quantities, else its first four).
+template <bool SAMPLER, bool GB, bool FT = false>
 struct RecTape {
   static constexpr bool kAcc = true;
   static constexpr bool sampler = SAMPLER;
   static constexpr bool graphics = GB;
+  static constexpr int kNG = GB ? (FT ? kGbN : 4) : 0;   // graphics-bit quantities
   uint32_t* buf;
   float* cw;
   uint32_t n, cap, ncw, capcw;
@@ -82,9 +84,10 @@ struct RecTape {
   int32_t slot0, slot1, slot2, slot3, slot4;  // float slot of each live version
   float s0, s1, s2, s3, s4, c0, c1, c2, c3, c4;  // compensated pixel-gradient sums of the live versions
   float p0, p1, p2, p3, p4;        // sums of the versions alive at the segment start
-  // versions 5..8 (GB): GRP0, PF0, PF1, PF2
-  int32_t slot5, slot6, slot7, slot8;
-  float s5, s6, s7, s8, c5, c6, c7, c8, p5, p6, p7, p8;
+  // the graphics-bit quantities' live versions (slot, compensated sum, sum of
+  // the version alive at the segment start); indices are compile-time
+  int32_t gsl[kGbN];
+  float gs[kGbN], gc[kGbN], gp[kGbN];
   bool overflow;
   uint32_t T, gmask;               // replicas of this env and their warp lanes
   // The replicas of an env each sum the pixel chunks they own; a version's
@@ -104,19 +107,26 @@ struct RecTape {
     if (slot >= 0) cw[slot] = tot;
     else if (slot == -1) pinit += tot;
   }
-  __device__ __forceinline__ void colour_write(int r) {
+  __device__ __forceinline__ int32_t fresh_slot() {
     int32_t fresh = ncw < capcw ? (int32_t)ncw : -2;
     if (fresh == -2) overflow = true;
     ncw++;
+    return fresh;
+  }
+  __device__ __forceinline__ void colour_write(int r) {
+    const int32_t fresh = fresh_slot();
     if (r == 0) { close_version(slot0, s0 + c0, p0); s0 = c0 = 0.f; slot0 = fresh; }
     else if (r == 1) { close_version(slot1, s1 + c1, p1); s1 = c1 = 0.f; slot1 = fresh; }
     else if (r == 2) { close_version(slot2, s2 + c2, p2); s2 = c2 = 0.f; slot2 = fresh; }
     else if (r == 3) { close_version(slot3, s3 + c3, p3); s3 = c3 = 0.f; slot3 = fresh; }
-    else if (r == 4) { close_version(slot4, s4 + c4, p4); s4 = c4 = 0.f; slot4 = fresh; }
-    else if (r == 5) { close_version(slot5, s5 + c5, p5); s5 = c5 = 0.f; slot5 = fresh; }
-    else if (r == 6) { close_version(slot6, s6 + c6, p6); s6 = c6 = 0.f; slot6 = fresh; }
-    else if (r == 7) { close_version(slot7, s7 + c7, p7); s7 = c7 = 0.f; slot7 = fresh; }
-    else { close_version(slot8, s8 + c8, p8); s8 = c8 = 0.f; slot8 = fresh; }
+    else { close_version(slot4, s4 + c4, p4); s4 = c4 = 0.f; slot4 = fresh; }
+  }
+  template <int K>
+  __device__ __forceinline__ void graphics_write() {
+    const int32_t fresh = fresh_slot();
+    close_version(gsl[K], gs[K] + gc[K], gp[K]);
+    gs[K] = gc[K] = 0.f;
+    gsl[K] = fresh;
   }
   __device__ __forceinline__ void version_write(uint32_t reg) {
     if (reg == 0x06) colour_write(0);
@@ -124,8 +134,23 @@ struct RecTape {
     else if (reg == 0x09) colour_write(2);
     else if (reg == 0x10 || reg == 0x2A) colour_write(3);
     else if (reg == 0x07) colour_write(4);
-    else if (GB && reg == 0x1B) colour_write(5);
-    else if (GB && reg >= 0x0D && reg <= 0x0F) colour_write(6 + (int)(reg - 0x0D));
+    if constexpr (GB) {
+      if (reg == 0x1B) {                      // GRP0 (with the whole TIA: GRP1's delayed copy too)
+        graphics_write<kGbGrp0>();
+        if constexpr (FT) graphics_write<kGbGrp1Old>();
+      } else if (reg == 0x0D) graphics_write<kGbPf0>();
+      else if (reg == 0x0E) graphics_write<kGbPf0 + 1>();
+      else if (reg == 0x0F) graphics_write<kGbPf0 + 2>();
+      if constexpr (FT) {
+        if (reg == 0x1C) {                    // GRP1, GRP0's and ENABL's delayed copies
+          graphics_write<kGbGrp1>();
+          graphics_write<kGbGrp0Old>();
+          graphics_write<kGbEnablOld>();
+        } else if (reg == 0x1D) graphics_write<kGbEnam0>();
+        else if (reg == 0x1E) graphics_write<kGbEnam1>();
+        else if (reg == 0x1F) graphics_write<kGbEnabl>();
+      }
+    }
   }
   // pixel-gradient sums of one drawn span, per owner (COLUP0, COLUPF,
   // COLUBK, COLUP1), and the sampler's sum
@@ -138,10 +163,15 @@ struct RecTape {
   }
   // graphics-bit sums of one drawn span: GRP0, PF0, PF1, PF2
   __device__ __forceinline__ void gbits(float g, float f0, float f1, float f2) {
-    comp_add(s5, c5, g);
-    comp_add(s6, c6, f0);
-    comp_add(s7, c7, f1);
-    comp_add(s8, c8, f2);
+    comp_add(gs[kGbGrp0], gc[kGbGrp0], g);
+    comp_add(gs[kGbPf0], gc[kGbPf0], f0);
+    comp_add(gs[kGbPf0 + 1], gc[kGbPf0 + 1], f1);
+    comp_add(gs[kGbPf0 + 2], gc[kGbPf0 + 2], f2);
+  }
+  // the whole TIA's graphics-bit sums of one drawn span, all eleven
+  __device__ __forceinline__ void gbits_all(const float (&v)[kGbN]) {
+#pragma unroll
+    for (int k = 0; k < kNG; k++) comp_add(gs[k], gc[k], v[k]);
   }
   __device__ __forceinline__ void finish() {
     close_version(slot0, s0 + c0, p0);
@@ -150,12 +180,10 @@ struct RecTape {
     close_version(slot3, s3 + c3, p3);
     close_version(slot4, s4 + c4, p4);
     s0 = s1 = s2 = s3 = s4 = c0 = c1 = c2 = c3 = c4 = 0.f;
-    if constexpr (GB) {
-      close_version(slot5, s5 + c5, p5);
-      close_version(slot6, s6 + c6, p6);
-      close_version(slot7, s7 + c7, p7);
-      close_version(slot8, s8 + c8, p8);
-      s5 = s6 = s7 = s8 = c5 = c6 = c7 = c8 = 0.f;
+#pragma unroll
+    for (int k = 0; k < kNG; k++) {
+      close_version(gsl[k], gs[k] + gc[k], gp[k]);
+      gs[k] = gc[k] = 0.f;
     }
   }
 };
@@ -228,7 +256,8 @@ __device__ __forceinline__ Acc operator-(const Acc& x) { return Acc{-x.s, -x.c};
 
 struct Adj {
   Acc A, X, Y, V, C0, C1, C2, C3;   // C3: COLUP1
-  Acc G[4];            // GRP0, PF0, PF1, PF2 (graphics-bit surrogate)
+  Acc G[kGbN];         // the graphics-bit surrogate's quantities (kGb*)
+  bool ft;             // the whole TIA (its graphics-bit quantities are versioned)
   float P, H;          // player 0's position and HMP0 (position sampler)
   float u[5], uc[5];   // joystick-input adjoints of the current step (compensated)
 };
@@ -333,11 +362,40 @@ __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uin
     if (reg == 0x08) { if (j) a.C1 += cw[--j]; return a.C1.take(); }
     if (reg == 0x09) { if (j) a.C2 += cw[--j]; return a.C2.take(); }
     if (reg == 0x07) { if (j) a.C3 += cw[--j]; return a.C3.take(); }
-    if constexpr (GB) {   // GRP0 and PF0-2 (graphics-bit surrogate)
-      if (reg == 0x1B) { if (j) a.G[0] += cw[--j]; return a.G[0].take(); }
-      if (reg == 0x0D) { if (j) a.G[1] += cw[--j]; return a.G[1].take(); }
-      if (reg == 0x0E) { if (j) a.G[2] += cw[--j]; return a.G[2].take(); }
-      if (reg == 0x0F) { if (j) a.G[3] += cw[--j]; return a.G[3].take(); }
+    if constexpr (GB) {
+      // graphics-bit surrogate: a version's sum goes to the written value.
+      // A delayed copy's versions open at the other player's GRP write (the
+      // later slots of its record, popped first) and belong to the value
+      // the copy took: the source register's live version.
+      auto pop = [&](int k) { if (j) a.G[k] += cw[--j]; };
+      if (reg == 0x1B) {
+        if (a.ft) {
+          pop(kGbGrp1Old);
+          a.G[kGbGrp1] += a.G[kGbGrp1Old].take();
+        }
+        pop(kGbGrp0);
+        return a.G[kGbGrp0].take();
+      }
+      if (reg >= 0x0D && reg <= 0x0F) {
+        const int k = kGbPf0 + (int)(reg - 0x0D);
+        pop(k);
+        return a.G[k].take();
+      }
+      if (a.ft) {
+        if (reg == 0x1C) {
+          pop(kGbEnablOld);
+          a.G[kGbEnabl] += a.G[kGbEnablOld].take();
+          pop(kGbGrp0Old);
+          a.G[kGbGrp0] += a.G[kGbGrp0Old].take();
+          pop(kGbGrp1);
+          return a.G[kGbGrp1].take();
+        }
+        if (reg >= 0x1D && reg <= 0x1F) {
+          const int k = kGbEnam0 + (int)(reg - 0x1D);
+          pop(k);
+          return a.G[k].take();
+        }
+      }
     }
     // RESP0 and HMOVE open a position version (its slot pops either way)
     if (reg == 0x2A || reg == 0x10) {
@@ -489,9 +547,9 @@ __device__ __forceinline__ void read_tables(float* ek, float* izr, float tau, in
 // run one segment at a time, last to first, each handing its adjoints to
 // the next.  Per (segment slot g, env) the recompute leaves the tape rows,
 // the colour / position version sums, the step ends and a small record
-// (kMeta words: version count, overflow flag, the sums of the nine
+// (kMeta words: version count, overflow flag, the sums of the sixteen
 // versions alive at the segment start).
-constexpr int kMeta = 12;
+constexpr int kMeta = 18;
 
 // Recompute shared memory: the step kernel's layout, then the staged
 // gradient rows (16-byte aligned).
@@ -539,7 +597,7 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   } else {
     power_on(c, r);
   }
-  RecTape<SAMPLER, GB> tape;
+  RecTape<SAMPLER, GB, FT> tape;
   tape.buf = p.rec + ((size_t)g * n + env) * p.cap_rec;
   tape.cw = p.cw + ((size_t)g * n + env) * p.cap_cw;
   tape.n = 0; tape.cap = p.cap_rec;
@@ -548,9 +606,11 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   tape.s0 = tape.s1 = tape.s2 = tape.s3 = tape.s4 = 0.f;
   tape.c0 = tape.c1 = tape.c2 = tape.c3 = tape.c4 = 0.f;
   tape.p0 = tape.p1 = tape.p2 = tape.p3 = tape.p4 = 0.f;
-  tape.slot5 = tape.slot6 = tape.slot7 = tape.slot8 = -1;
-  tape.s5 = tape.s6 = tape.s7 = tape.s8 = tape.c5 = tape.c6 = tape.c7 = tape.c8 = 0.f;
-  tape.p5 = tape.p6 = tape.p7 = tape.p8 = 0.f;
+#pragma unroll
+  for (int k = 0; k < kGbN; k++) {
+    tape.gsl[k] = -1;
+    tape.gs[k] = tape.gc[k] = tape.gp[k] = 0.f;
+  }
   tape.overflow = false;
   tape.T = (uint32_t)T;
   tape.gmask = c.gmask;
@@ -590,10 +650,8 @@ __global__ void __launch_bounds__(128) k_soft_recompute(BwdParams p) {
   m[4] = tape.p2;
   m[5] = tape.p3;
   m[6] = tape.p4;
-  m[7] = tape.p5;
-  m[8] = tape.p6;
-  m[9] = tape.p7;
-  m[10] = tape.p8;
+#pragma unroll
+  for (int k = 0; k < kGbN; k++) m[7 + k] = tape.gp[k];
   if (tape.overflow) atomicExch(p.err, 2);
 }
 
@@ -630,10 +688,12 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   float* aram = aram_s + slot;
   float* aramc = aramc_s + slot;
   Adj a;
+  a.ft = p.full_tia != 0;
   if (lead) {
     if (p.first) {
       a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.C3 = acc(0.f);
-      a.G[0] = a.G[1] = a.G[2] = a.G[3] = acc(0.f);
+#pragma unroll
+      for (int k = 0; k < kGbN; k++) a.G[k] = acc(0.f);
       a.P = a.H = 0.f;
       for (int i = 0; i < cells; i++) aram[i * E] = 0.f;
       for (int i = 0; i < cells; i++) aramc[i * E] = 0.f;
@@ -644,7 +704,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
       a.C0 = acc(cr[4 * n + env]); a.C1 = acc(cr[5 * n + env]); a.C2 = acc(cr[6 * n + env]);
       a.C3 = acc(cr[(size_t)kCarryC3 * n + env]);
 #pragma unroll
-      for (int k = 0; k < 4; k++) a.G[k] = acc(GB ? cr[(size_t)(kCarryGB + k) * n + env] : 0.f);
+      for (int k = 0; k < kGbN; k++) a.G[k] = acc(GB ? cr[(size_t)(kCarryGB + k) * n + env] : 0.f);
       a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
       a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
       for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
@@ -731,7 +791,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   if constexpr (SAMPLER) a.P += m[5];
   if constexpr (GB) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) a.G[k] += m[7 + k];
+    for (int k = 0; k < kGbN; k++) a.G[k] += m[7 + k];
   }
   if (p.seg == 0) {
     if (p.grad_ram0)
@@ -746,7 +806,7 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
     cr[(size_t)kCarryC3 * n + env] = a.C3.v();
     if constexpr (GB) {
 #pragma unroll
-      for (int k = 0; k < 4; k++) cr[(size_t)(kCarryGB + k) * n + env] = a.G[k].v();
+      for (int k = 0; k < kGbN; k++) cr[(size_t)(kCarryGB + k) * n + env] = a.G[k].v();
     }
     cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
     for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
@@ -779,15 +839,15 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
     // sampler), so one lane per env serves them
     if (p.step_instr > 0) {
       go(k_soft_recompute<1, false, false, true, XM, FT>, E);
-    } else if (!FT && p.graphics) {
-      // the graphics-bit surrogate (subset machine only) is built for one
-      // lane per env and for four replicas: 2 runs as 1 and 8 as 4
+    } else if (p.graphics) {
+      // the graphics-bit surrogate is built for one lane per env and for
+      // four replicas: 2 runs as 1 and 8 as 4
       if (p.sampler) {
-        if (T >= 4) go(k_soft_recompute<4, true, true, false, XM, false>, 4 * E);
-        else go(k_soft_recompute<1, true, true, false, XM, false>, E);
+        if (T >= 4) go(k_soft_recompute<4, true, true, false, XM, FT>, 4 * E);
+        else go(k_soft_recompute<1, true, true, false, XM, FT>, E);
       } else {
-        if (T >= 4) go(k_soft_recompute<4, false, true, false, XM, false>, 4 * E);
-        else go(k_soft_recompute<1, false, true, false, XM, false>, E);
+        if (T >= 4) go(k_soft_recompute<4, false, true, false, XM, FT>, 4 * E);
+        else go(k_soft_recompute<1, false, true, false, XM, FT>, E);
       }
     } else if (p.sampler) {
       switch (T) {

@@ -27,10 +27,14 @@ namespace vcs {
 struct CountTape {
   static constexpr bool kAcc = false;
   uint32_t n = 0, ncw = 0;
-  uint64_t vregs = kVersionRegs;   // | kGraphicsRegs with the graphics-bit surrogate
+  uint64_t vregs = kVersionRegs;   // | kGraphicsRegs (| kGraphicsRegsFT) with the graphics-bit surrogate
+  bool ftgb = false;               // the surrogate with the whole TIA: the delayed copies' versions
   __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) { n++; }
   static constexpr bool sampler = false;
-  __device__ __forceinline__ void version_write(uint32_t reg) { ncw += (uint32_t)(vregs >> reg) & 1u; }
+  __device__ __forceinline__ void version_write(uint32_t reg) {
+    ncw += (uint32_t)(vregs >> reg) & 1u;
+    if (ftgb) ncw += reg == 0x1B ? 1u : (reg == 0x1C ? 2u : 0u);
+  }
   __device__ __forceinline__ void pixels(float, float, float, float, float) {}
 };
 
@@ -89,7 +93,10 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   }
 
   typename std::conditional<SOFT, CountTape, NoTape>::type tape;
-  if constexpr (SOFT) tape.vregs = kVersionRegs | (p.graphics ? kGraphicsRegs : 0ull);
+  if constexpr (SOFT) {
+    tape.vregs = kVersionRegs | (p.graphics ? kGraphicsRegs | (FT ? kGraphicsRegsFT : 0ull) : 0ull);
+    tape.ftgb = FT && p.graphics;
+  }
   Render rd;
   rd.on = false;
   rd.cur = 0;

@@ -383,6 +383,13 @@ static __device__ __noinline__ void draw_general(const TiaView v, uint32_t* line
   }
 }
 
+// Graphics-bit quantities (graphics-bit surrogate): GRP0, PF0, PF1, PF2,
+// and with the whole TIA GRP1, ENAM0, ENAM1, ENABL and the delayed copies
+// of GRP0, GRP1 and ENABL (a GRP1 write copies GRP0 and ENABL into theirs,
+// a GRP0 write copies GRP1).
+enum : int { kGbGrp0 = 0, kGbPf0 = 1, kGbGrp1 = 4, kGbEnam0 = 5, kGbEnam1 = 6, kGbEnabl = 7, kGbGrp0Old = 8,
+             kGbGrp1Old = 9, kGbEnablOld = 10, kGbN = 11 };
+
 // Pixel-gradient sums of pixels [x0, x1) by owning colour register (COLUP0,
 // COLUPF, COLUBK, COLUP1) and, with the position sampler, player 0's
 // position sum: (C_with - C_without) (b(x - 1) - b(x + 1)) / 2 per pixel.
@@ -430,6 +437,87 @@ static __device__ __noinline__ OwnerSums sums_general(const TiaView v, const flo
     }
   }
   return s;
+}
+
+// Graphics-bit surrogate over pixels [x0, x1) of the whole TIA: for each
+// drawn pixel and each object whose graphics bit decides its coverage there
+// (a player's GRP bit over its copies' spans, a missile's ENAM byte over
+// its span unless it is locked to its player, the ball's ENABL byte over
+// its span, the playfield register of the column), the pixel's gradient
+// times the colour with that bit set minus the colour with it clear (the
+// priority logic decides both, the other objects as drawn), summed per
+// quantity (kGb*; a delayed graphic's sum goes to its delayed copy).
+struct GbSums {
+  float v[kGbN];
+};
+static __device__ __noinline__ GbSums gbits_general(const TiaView v, const float4* grow, uint32_t E, uint32_t slot,
+                                                    uint32_t rank, uint32_t T, uint32_t x0, uint32_t x1,
+                                                    uint32_t blank_g) {
+  LineMasks L;
+  line_masks(v, L);
+  const uint32_t ctrl = v.pf >> 24, w0 = v.w0, w3 = v.w3;
+  // the objects' spans: where their graphics bits are in play
+  uint32_t S[5][5];   // P0, M0, P1, M1, BL
+  for (int k = 0; k < 5; k++)
+    for (int q = 0; q < 5; q++) S[k][q] = 0;
+  for (uint32_t i = 0; i < 2; i++) {
+    const uint32_t mode = i ? (w0 >> 16) & 7 : (w0 >> 8) & 7;
+    const uint32_t sc = player_scale(mode), cp = nusiz_copies(mode);
+    const uint32_t pos = i ? w3 & 0xFF : (v.p0 >> 8) & 0xFF;
+    const uint32_t pat = sc == 4 ? 0xFFFFFFFFu : (1u << (8 * sc)) - 1u;
+    for (uint32_t k = 0; k < 4; k++)
+      if ((cp >> k) & 1) {
+        const uint32_t p = pos + (k == 3 ? 64u : 16u * k);
+        place(S[i ? 2 : 0], pat, 8 * sc, p >= 160 ? p - 160 : p);
+      }
+    if (!(w0 & (i ? kW0Resmp1 : kW0Resmp0))) {
+      const uint32_t nus = i ? (w0 >> 16) & 0xFF : (w0 >> 8) & 0xFF;
+      const uint32_t wid = 1u << ((nus >> 4) & 3), mcp = nusiz_copies(nus & 7);
+      const uint32_t mpos = (w3 >> (i ? 16 : 8)) & 0xFF;
+      for (uint32_t k = 0; k < 4; k++)
+        if ((mcp >> k) & 1) {
+          const uint32_t p = mpos + (k == 3 ? 64u : 16u * k);
+          place(S[i ? 3 : 1], (1u << wid) - 1u, wid, p >= 160 ? p - 160 : p);
+        }
+    }
+  }
+  {
+    const uint32_t wid = 1u << ((ctrl >> 4) & 3);
+    place(S[4], (1u << wid) - 1u, wid, (w3 >> 24) & 0xFF);
+  }
+  const int dst[6] = {(w0 & kW0Vdelp0) ? kGbGrp0Old : kGbGrp0, kGbEnam0, (w0 & kW0Vdelp1) ? kGbGrp1Old : kGbGrp1,
+                      kGbEnam1, kGbPf0, (w0 & kW0Vdelbl) ? kGbEnablOld : kGbEnabl};
+  GbSums out;
+  for (int k = 0; k < kGbN; k++) out.v[k] = 0.f;
+  for (uint32_t g = x0 >> 2; 4 * g < x1; g++) {
+    if (((g >> 2) & (T - 1)) != rank || g < blank_g) continue;
+    const float4 q = grow[grow_at(g, E, slot)];
+    const float gv[4] = {q.x, q.y, q.z, q.w};
+    for (uint32_t j = 0; j < 4; j++) {
+      const uint32_t x = 4 * g + j;
+      if (x < x0 || x >= x1 || gv[j] == 0.f) continue;
+      bool b[6] = {bit_at(L.p0, x) != 0, bit_at(L.m0, x) != 0, bit_at(L.p1, x) != 0, bit_at(L.m1, x) != 0,
+                   bit_at(L.pf, x) != 0, bit_at(L.bl, x) != 0};
+      const bool in[6] = {bit_at(S[0], x) != 0, bit_at(S[1], x) != 0, bit_at(S[2], x) != 0, bit_at(S[3], x) != 0,
+                          true, bit_at(S[4], x) != 0};
+      // the playfield register of the column (right half mirrored with CTRLPF bit 0)
+      uint32_t i = x < 80 ? x >> 2 : (x - 80) >> 2;
+      if (x >= 80 && (ctrl & 1)) i = 19 - i;
+      const int pfk = kGbPf0 + (i < 4 ? 0 : (i < 12 ? 1 : 2));
+      for (int k = 0; k < 6; k++) {
+        if (!in[k]) continue;
+        const bool keep = b[k];
+        b[k] = true;
+        const uint32_t ow = owner_of(ctrl, x, b[0], b[1], b[2], b[3], b[4], b[5]);
+        b[k] = false;
+        const uint32_t on = owner_of(ctrl, x, b[0], b[1], b[2], b[3], b[4], b[5]);
+        b[k] = keep;
+        const int32_t d = (int32_t)((v.col >> (8 * ow)) & 0xFE) - (int32_t)((v.col >> (8 * on)) & 0xFE);
+        if (d) out.v[k == 4 ? pfk : dst[k]] += (float)d * gv[j];
+      }
+    }
+  }
+  return out;
 }
 
 }  // namespace vcs

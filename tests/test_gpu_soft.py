@@ -585,8 +585,71 @@ def test_graphics_bit_gradients_on_synthetic_carts(tpe, seg):
         assert_grad_close(g_u[:, e], o_u, f"env {e} grad_u")
 
 
-def test_graphics_bits_refused_with_the_whole_tia():
-    from paper_2606_22447_b300 import VcsError
-    rom = synth.generate_cart(95, 0, synth.MAPPER_4K)
-    with pytest.raises(VcsError, match="graphics"):
-        make_batch([rom], [synth.MAPPER_4K], np.zeros(2, np.int32), graphics_bits=1, full_tia=1)
+@pytest.mark.parametrize("ctrlpf,vdel,tpe", [(0, False, 1), (4, False, 4), (0, True, 4)])
+def test_whole_tia_graphics_bits_on_the_pin_cart(ctrlpf, vdel, tpe):
+    """The graphics-bit surrogate with the whole TIA: the oracle's pin cart
+    (player 1 from the joystick, GRP0, ENAM0, ENABL and PF0-2 from
+    immediates; playfield-first priority; player 1 through its delayed
+    copy), joystick and ROM gradients against the FP64 oracle."""
+    from tests.microrom import graphics_full_tia_rom
+    torch = torch_cuda()
+    rom, _ = graphics_full_tia_rom(ctrlpf, vdel)
+    n_envs, n_steps, tau = 8, 4, 0.01
+    b = make_batch([rom], [synth.MAPPER_4K], np.zeros(n_envs, np.int32), graphics_bits=1, full_tia=1,
+                   threads_per_env=tpe, envs_per_block=8, segment_frames=2)
+    acts = synth.actions(97 + ctrlpf + vdel, n_envs, n_steps)
+    u = synth.action_inputs(acts)
+    gs = synth.normal_f32(97, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, b.rom_stride), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(None, torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_u=g_u)
+    b.sync()
+    g_rom, g_u = g_rom.cpu().numpy(), g_u.cpu().numpy()
+    for e in range(n_envs):
+        o = oracle.Oracle(rom, synth.MAPPER_4K, full_tia=True)
+        o.set_graphics(True)
+        g, _, _ = o.soft_rollout(u[:, e].astype(np.float64), 1, tau, 6.0, None, gs[:, e].astype(np.float64),
+                                 outputs=False)
+        o_rom, _, o_u = g.reverse()
+        assert np.abs(o_u).max() > 1.0
+        assert_grad_close(g_u[:, e], o_u, f"env {e} grad_u")
+        assert_grad_close(g_rom[e, :4096], o_rom, f"env {e} grad_rom")
+
+
+@pytest.mark.parametrize("tpe,seg", [(1, 64), (4, 2)])
+def test_whole_tia_graphics_bits_on_synthetic_carts(tpe, seg):
+    """Full-TIA carts (players, missiles, ball, sizes, delays, collisions)
+    with the graphics-bit surrogate: ROM, initial RAM and input gradients
+    against the FP64 oracle over one and several segments."""
+    torch = torch_cuda()
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_E0, synth.MAPPER_F6SC]
+    n_envs, n_steps, tau = 8, 3, 0.1
+    roms = synth.config_carts(99, mappers, full_tia=True)
+    env_cart = (np.arange(n_envs) % len(mappers)).astype(np.int32)
+    b = make_batch(roms, mappers, env_cart, full_tia=1, graphics_bits=1, envs_per_block=8, threads_per_env=tpe,
+                   segment_frames=seg)
+    wa = synth.actions(100, n_envs, 2)
+    gpu_rollout(b, wa, 1, screens=False)
+    u = synth.action_inputs(synth.actions(99, n_envs, n_steps))
+    gr = synth.normal_f32(99, (n_steps, n_envs, 128), 1)
+    gs = synth.normal_f32(99, (n_steps, n_envs, 210, 160), 2)
+    tape = b.soft_rollout(tau, torch.from_numpy(u).cuda(), 1)
+    g_rom = torch.empty((n_envs, b.rom_stride), device="cuda")
+    g_ram0 = torch.empty((n_envs, 128), device="cuda")
+    g_u = torch.empty((n_steps, n_envs, 5), device="cuda")
+    tape.backward(torch.from_numpy(gr).cuda(), torch.from_numpy(gs).cuda(), grad_rom=g_rom, grad_ram0=g_ram0,
+                  grad_u=g_u)
+    b.sync()
+    g_rom, g_ram0, g_u = g_rom.cpu().numpy(), g_ram0.cpu().numpy(), g_u.cpu().numpy()
+    for e in range(n_envs):
+        c = env_cart[e]
+        o = oracle.Oracle(roms[c], mappers[c], full_tia=True)
+        o.rollout(wa[:, e], 1, screens=False)
+        o.set_graphics(True)
+        g, _, _ = o.soft_rollout(u[:, e].astype(np.float64), 1, tau, 6.0, gr[:, e].astype(np.float64),
+                                 gs[:, e].astype(np.float64), outputs=False)
+        o_rom, o_ram0, o_u = g.reverse()
+        assert_grad_close(g_rom[e, :len(roms[c])], o_rom, f"env {e} grad_rom")
+        assert_grad_close(g_ram0[e], o_ram0, f"env {e} grad_ram0")
+        assert_grad_close(g_u[:, e], o_u, f"env {e} grad_u")
