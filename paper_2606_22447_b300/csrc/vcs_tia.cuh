@@ -315,10 +315,13 @@ static __device__ __noinline__ uint32_t cx_advance(const uint32_t* tx, uint32_t 
   v.w1 = tx[E];
   v.w3 = tx[3 * E];
   const bool simple = !(xo & kXoGen) && want == (1u << 5);   // player 0 against the playfield only
-  // the registers are constant over the catch-up: one set of masks, of the
-  // objects in the wanted pairs only
+  // The registers are constant over the catch-up: one set of masks, of the
+  // objects in the wanted pairs only, built at the first visible column (a
+  // catch-up inside the horizontal blank, as between the writes that follow
+  // a WSYNC, builds none); once a whole line has been seen the lines after
+  // it, being the same, latch nothing new.
   LineMasks L;
-  if (!simple) line_masks(v, L, pair_objects(want));
+  bool built = false;
   uint32_t got = 0;
   int32_t cur = cxc;
   while (cur < target && (want & ~got)) {
@@ -327,8 +330,16 @@ static __device__ __noinline__ uint32_t cx_advance(const uint32_t* tx, uint32_t 
     const int32_t h0 = cur - lbeg, h1 = seg - lbeg;
     const uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u, x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
     if (x1 > x0) {
-      if (simple) got |= p0_pf_overlap(v, x0, x1) ? want : 0u;
-      else got |= collide_span(L, want & ~got, x0, x1);
+      if (simple) {
+        got |= p0_pf_overlap(v, x0, x1) ? want : 0u;
+      } else {
+        if (!built) {
+          line_masks(v, L, pair_objects(want));
+          built = true;
+        }
+        got |= collide_span(L, want & ~got, x0, x1);
+      }
+      if (x0 == 0 && x1 == 160) break;
     }
     cur = seg;
   }
