@@ -2,8 +2,9 @@
 envs (digests of RAM and screen per env-step where the outputs are too
 large to keep), and the ALU exhaustively on the GPU:
 
-* 4096 envs of one 4 KB cart, frame-skip 4, 2,500 steps: every env's
-  digests for the first 16 steps and a seeded 64-env sample for all 2,500;
+* 4096 envs of one 4 KB cart, frame-skip 4, 10,000 steps (the bench
+  workload's full length): every env's digests for the first 16 steps and a
+  seeded 32-env sample for all 10,000;
 * 65,536 envs over 16 carts (6 x 2K, 6 x 4K, 4 x F8) with the seeded
   geometric episode table (mean 2,000 frames, no lengths forced short),
   1,250 steps of frame-skip 4 (5,000 frames): a 32-env sample whose envs
@@ -62,13 +63,13 @@ def _gpu_digests(b, acts, frame_skip, chunk, keep=None):
     return np.concatenate(digs), np.concatenate(stats)
 
 
-def test_bench_workload_2500_steps():
-    n, steps, first = 4096, 2500, 16
+def test_bench_workload_10000_steps():
+    n, steps, first = 4096, 10000, 16
     rom = synth.generate_cart(2, 0, synth.MAPPER_4K)
     acts = synth.actions(2, n, steps)
     b = make_batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32))
     dig, _ = _gpu_digests(b, acts, 4, 50)
-    sample = np.random.default_rng(2500).choice(n, 64, replace=False)
+    sample = np.random.default_rng(10000).choice(n, 32, replace=False)
     with ThreadPoolExecutor(THREADS) as ex:
         long = list(ex.map(lambda e: _oracle_digests(rom, synth.MAPPER_4K, acts[:, e], 4)[0], sample))
         short = list(ex.map(lambda e: _oracle_digests(rom, synth.MAPPER_4K, acts[:first, e], 4)[0], range(n)))
