@@ -101,21 +101,26 @@ static vcs_status set_geometry(vcs_batch* b, int E) {
   const std::vector<int4> blocks = cut(E);
   const std::vector<int4> bwd = E > kBwdMaxEnvsPerBlock ? cut(kBwdMaxEnvsPerBlock) : std::vector<int4>();
   const std::vector<int4> wide = cut(kWideEnvsPerBlock);
+  const std::vector<int4> widef = cut(kWideFwdEnvsPerBlock);
   int4* dblocks = nullptr;
   int4* dbwd = nullptr;
   int4* dwide = nullptr;
+  int4* dwidef = nullptr;
   int32_t* dperm = nullptr;
   cudaError_t e;
   if ((e = cudaMalloc(&dblocks, blocks.size() * sizeof(int4))) || (e = cudaMalloc(&dperm, n_envs * sizeof(int32_t))) ||
       (!bwd.empty() && (e = cudaMalloc(&dbwd, bwd.size() * sizeof(int4)))) ||
       (e = cudaMalloc(&dwide, wide.size() * sizeof(int4))) ||
       (e = cudaMemcpy(dwide, wide.data(), wide.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
+      (e = cudaMalloc(&dwidef, widef.size() * sizeof(int4))) ||
+      (e = cudaMemcpy(dwidef, widef.data(), widef.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(dblocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
       (!bwd.empty() && (e = cudaMemcpy(dbwd, bwd.data(), bwd.size() * sizeof(int4), cudaMemcpyHostToDevice))) ||
       (e = cudaMemcpy(dperm, perm.data(), n_envs * sizeof(int32_t), cudaMemcpyHostToDevice))) {
     cudaFree(dblocks);
     cudaFree(dbwd);
     cudaFree(dwide);
+    cudaFree(dwidef);
     cudaFree(dperm);
     return vcs_cuda_fail(b, e, "launch geometry");
   }
@@ -124,6 +129,9 @@ static vcs_status set_geometry(vcs_batch* b, int E) {
   cudaFree(b->wide_blocks);
   b->wide_blocks = dwide;
   b->wide_n_blocks = (int)wide.size();
+  cudaFree(b->wide_fwd_blocks);
+  b->wide_fwd_blocks = dwidef;
+  b->wide_fwd_n_blocks = (int)widef.size();
   cudaFree(b->perm);
   b->blocks = dblocks;
   b->bwd_blocks = dbwd;
@@ -160,6 +168,7 @@ static void free_batch(vcs_batch* b) {
   cudaFree(b->blocks);
   cudaFree(b->bwd_blocks);
   cudaFree(b->wide_blocks);
+  cudaFree(b->wide_fwd_blocks);
   cudaFree(b->perm);
   cudaFree(b->ep_len);
   cudaFree(b->start_noops);

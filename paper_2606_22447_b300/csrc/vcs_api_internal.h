@@ -36,6 +36,10 @@ struct vcs_batch {
   // recompute of a large group of segments, one lane per env
   int4* wide_blocks = nullptr;
   int32_t wide_n_blocks = 0;
+  // blocks of kWideFwdEnvsPerBlock envs (same permutation): the soft
+  // forward without screens, one lane per env
+  int4* wide_fwd_blocks = nullptr;
+  int32_t wide_fwd_n_blocks = 0;
   uint32_t* ep_len = nullptr;
   int32_t n_episodes = 0;
   uint8_t* start_noops = nullptr;  // [n_envs][n_start] NOOP frames starting each episode
@@ -72,7 +76,12 @@ vcs::StepParams vcs_base_params(vcs_batch* b);
 // Largest envs per block whose backward shared memory (about 9.7 KB +
 // 1.9 KB per env) fits in a block.
 constexpr int kBwdMaxEnvsPerBlock = 64;
-constexpr int kWideEnvsPerBlock = 32;
+// One lane per env: the recompute of large segment groups runs in blocks of
+// kWideEnvsPerBlock envs, the soft forward without screens in blocks of
+// kWideFwdEnvsPerBlock (each the fastest of 8 / 16 / 32 / 64 / 128 on 4096
+// envs of the 4K / F8 mix over 2,048 frames).
+constexpr int kWideEnvsPerBlock = 64;
+constexpr int kWideFwdEnvsPerBlock = 128;
 
 // The backward's launch geometry (its own block table past
 // kBwdMaxEnvsPerBlock envs per block).

@@ -1111,13 +1111,13 @@ vcs_status vcs_soft_rollout(vcs_batch* b, float tau, const float* rom_f32, const
   p.seg_steps = t->seg_steps;
   p.seg_counts = t->seg_counts;
   // Without screen outputs the forward draws nothing, so replicas have no
-  // work to share: one lane per env in blocks of kWideEnvsPerBlock (measured
-  // 31 % faster than four replicas on 4096 envs of the 4K / F8 mix)
+  // work to share: one lane per env in blocks of kWideFwdEnvsPerBlock
+  // (measured 31 % faster than four replicas on 4096 envs of the 4K / F8 mix)
   int le;
   if (!screen_out) {
-    p.blocks = b->wide_blocks;
+    p.blocks = b->wide_fwd_blocks;
     p.tpe = 1;
-    le = launch_soft_forward(p, b->wide_n_blocks, kWideEnvsPerBlock, stream);
+    le = launch_soft_forward(p, b->wide_fwd_n_blocks, kWideFwdEnvsPerBlock, stream);
   } else {
     le = launch_soft_forward(p, b->n_blocks, b->E, stream);
   }
