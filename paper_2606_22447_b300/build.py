@@ -9,7 +9,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvcs.so")
-SOURCES = ["vcs_kernels.cu", "vcs_kernels_xm.cu", "vcs_kernels_ft.cu", "vcs_soft.cu", "vcs_api.cu", "vcs_full.cu"]
+SOURCES = ["vcs_kernels.cu", "vcs_kernels_xm.cu", "vcs_kernels_ft.cu", "vcs_soft.cu", "vcs_api.cu", "vcs_full.cu",
+           "vcs_raster.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"]

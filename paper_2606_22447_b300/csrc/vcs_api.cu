@@ -150,7 +150,56 @@ static bool valid_tpe(int E, int T) { return (T == 1 || T == 2 || T == 4 || T ==
 
 
 
+// Deferred rasterisation serves hard frame steps of the subset machine that
+// return screens, unless the batch asks for drawing in the step kernel.
+static bool raster_applies(const vcs_batch* b, const StepParams& p) {
+  return p.screen_out && p.n_steps > 0 && !p.full_tia && p.step_instr <= 0 && b->cfg.inline_render == 0;
+}
+
+// The logs take kRasterLogCap entries per env (67 KB, the most picture-
+// register writes a frame can make: the log never fills).
+static vcs_status ensure_raster(vcs_batch* b) {
+  if (b->dr_log) return VCS_OK;
+  const size_t n = (size_t)b->n_envs;
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->dr_log, n * (size_t)kRasterLogCap * sizeof(uint32_t))) ||
+      (e = cudaMalloc(&b->dr_hdr, n * kRasterHdr * sizeof(uint32_t)))) {
+    cudaFree(b->dr_log);
+    b->dr_log = nullptr;
+    b->dr_hdr = nullptr;
+    return vcs_cuda_fail(b, e, "raster logs");
+  }
+  return VCS_OK;
+}
+
+// One launch of the step kernel over p.n_steps steps; with deferred
+// rasterisation one step per launch, each followed by the raster kernel
+// that draws its screens from the logs.
 static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
+  if (raster_applies(b, p)) {
+    vcs_status st = ensure_raster(b);
+    if (st != VCS_OK) return st;
+    const size_t n = (size_t)b->n_envs;
+    for (int32_t t = 0; t < p.n_steps; t++) {
+      StepParams q = p;
+      q.n_steps = 1;
+      if (t > 0) {   // power-on requests belong to the first launch
+        q.reset_all = 0;
+        q.reset_mask = nullptr;
+      }
+      q.actions = p.actions ? p.actions + (size_t)t * n : nullptr;
+      q.ram_out = p.ram_out ? p.ram_out + (size_t)t * n * 128 : nullptr;
+      q.screen_out = p.screen_out + (size_t)t * n * kScreenH * kScreenW;
+      q.status_out = p.status_out ? p.status_out + (size_t)t * n : nullptr;
+      q.dr_log = b->dr_log;
+      q.dr_hdr = b->dr_hdr;
+      int e = launch_step(q, b->n_blocks, b->E, stream);
+      if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
+      e = launch_raster(b->dr_hdr, b->dr_log, b->n_envs, b->cfg.ystart, q.screen_out, stream);
+      if (e) return vcs_cuda_fail(b, (cudaError_t)e, "raster kernel launch");
+    }
+    return VCS_OK;
+  }
   int e = launch_step(p, b->n_blocks, b->E, stream);
   if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
   return VCS_OK;
@@ -171,6 +220,8 @@ static void free_batch(vcs_batch* b) {
   cudaFree(b->wide_fwd_blocks);
   cudaFree(b->perm);
   cudaFree(b->ep_len);
+  cudaFree(b->dr_log);
+  cudaFree(b->dr_hdr);
   cudaFree(b->start_noops);
   cudaFree(b->err);
   cudaFree(b->h_actions);
@@ -208,6 +259,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->tape_budget_mb = 0;
   cfg->full_tia = 0;
   cfg->graphics_bits = 0;
+  cfg->inline_render = 0;
   return VCS_OK;
 }
 
@@ -317,6 +369,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
       b->cfg.segment_frames < 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "config out of range (ystart 0..400, boot frames >= 0, segment >= 1)");
+  }
+  if (b->cfg.inline_render < 0 || b->cfg.inline_render > 1) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "inline_render must be 0 or 1");
   }
   b->n_envs = n_envs;
   b->n_carts = n_carts;
@@ -820,6 +876,10 @@ vcs_status vcs_graph_create(vcs_batch* b, const uint8_t* actions, int32_t n_step
   *out = nullptr;
   if (!actions || n_steps < 1 || frame_skip < 1)
     return vcs_fail(b, VCS_ERR_ARG, "actions, n_steps >= 1 and frame_skip >= 1 required");
+  if (screen_out && !b->cfg.full_tia && b->cfg.step_instructions <= 0 && b->cfg.inline_render == 0) {
+    vcs_status st = ensure_raster(b);   // allocated before the capture, not inside it
+    if (st != VCS_OK) return st;
+  }
   vcs_graph* g = new (std::nothrow) vcs_graph;
   if (!g) return vcs_fail(b, VCS_ERR_OOM, "host allocation failed");
   cudaStream_t s = nullptr;
@@ -910,6 +970,7 @@ vcs_status vcs_sync(vcs_batch* b, void* stream) {
   int32_t err = 0;
   if ((e = cudaMemcpy(&err, b->err, sizeof err, cudaMemcpyDeviceToHost))) return vcs_cuda_fail(b, e, "error word");
   if (err == 2) return vcs_fail(b, VCS_ERR_STATE, "backward tape overflow (recompute diverged from the forward)");
+  if (err == kErrRasterLog) return vcs_fail(b, VCS_ERR_STATE, "a raster log passed its bound");
   if (err) return vcs_fail(b, VCS_ERR_WATCHDOG, "a device wait gave up (code %d); batch unusable", err);
   return VCS_OK;
 }

@@ -40,6 +40,11 @@ struct vcs_batch {
   // forward without screens, one lane per env
   int4* wide_fwd_blocks = nullptr;
   int32_t wide_fwd_n_blocks = 0;
+  // deferred rasterisation (vcs_raster.cu): per env a log of the returned
+  // frame's picture-register writes and a header, made at the first step
+  // that returns screens
+  uint32_t* dr_log = nullptr;      // [n_envs][kRasterLogCap]
+  uint32_t* dr_hdr = nullptr;      // [n_envs][kRasterHdr]
   uint32_t* ep_len = nullptr;
   int32_t n_episodes = 0;
   uint8_t* start_noops = nullptr;  // [n_envs][n_start] NOOP frames starting each episode

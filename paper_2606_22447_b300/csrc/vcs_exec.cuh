@@ -72,6 +72,46 @@ constexpr uint64_t kGraphicsRegs = reg_bits({0x0D, 0x0E, 0x0F, 0x1B});
 // and ENABL's).
 constexpr uint64_t kGraphicsRegsFT = reg_bits({0x1C, 0x1D, 0x1E, 0x1F});
 
+// Tape hook: called for each executed instruction the backward sweep acts on
+// (reverse_needed) with its opcode, a reference address and flag bits (the
+// soft path records these; the hard path compiles the hook away).
+struct NoTape {
+  static constexpr bool kAcc = false;
+  static constexpr bool sampler = false;
+  __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) {}
+  __device__ __forceinline__ void version_write(uint32_t) {}
+  __device__ __forceinline__ void pixels(float, float, float, float, float) {}
+};
+
+// The hard machine with deferred rasterisation (vcs_machine.cuh): the
+// returned frame's picture-register writes go to the env's log instead of
+// being drawn.
+struct DeferTape : NoTape {
+  uint32_t* log;   // this env's log entries (kRasterLogCap of them)
+  uint32_t* hdr;   // this env's header (kRasterHdr words)
+  int32_t* err;    // the batch's device error word
+  uint32_t n;
+};
+template <class Tape>
+constexpr bool kDefers = std::is_same<Tape, DeferTape>::value;
+
+// The returned frame starts: its drawing registers and first colour clock
+// go to the header, and the log starts empty.
+__device__ __forceinline__ void raster_begin(const Regs& r, const Render& rd, DeferTape& tape) {
+  tape.n = 0;
+  tape.hdr[1] = (uint32_t)rd.cur;
+  raster_snapshot(r, tape.hdr);
+}
+
+// The returned frame ends at colour clock `end`.  kRasterLogCap bounds the
+// picture-register writes of any frame; a log past it would mean a broken
+// bound, so the entries past it are dropped and the batch's error word set.
+__device__ __forceinline__ void raster_end(DeferTape& tape, int32_t end) {
+  tape.hdr[0] = tape.n < (uint32_t)kRasterLogCap ? tape.n : (uint32_t)kRasterLogCap;
+  tape.hdr[2] = (uint32_t)end;
+  if (tape.n > (uint32_t)kRasterLogCap) atomicExch(tape.err, kErrRasterLog);
+}
+
 // A write to a cold register (or a hot one with cold effects) at line clock
 // h: updates the cold words at tx (stride E) and returns the new summary
 // bits and collision word (x: Regs::xo, y: Regs::cx).  Out of line and
@@ -86,8 +126,10 @@ static __device__ __noinline__ uint2 tia_write_cold(uint32_t* tx, uint32_t E, ui
 template <class Tape>
 __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t reg,
                                           uint32_t v, int32_t fcw) {
-  if ((((c.ft ? kVisualRegs : kVisualSubset) >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
-  if (c.ft && ((kObjRegs >> reg) & 1)) cx_catchup(c, r, 3 * fcw);
+  if constexpr (!kDefers<Tape>) {
+    if ((((c.ft ? kVisualRegs : kVisualSubset) >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
+    if (c.ft && ((kObjRegs >> reg) & 1)) cx_catchup(c, r, 3 * fcw);
+  }
   tape.version_write(reg);
   const uint32_t line = div76((uint32_t)fcw);
   const uint32_t m = (uint32_t)fcw - 76u * line;   // CPU cycle within the line
@@ -112,6 +154,14 @@ __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Ste
   r.pos = reg == 0x10 ? resp : (reg == 0x2A ? hmov : r.pos);
   r.hml = (reg == 0x2A && h <= 9) ? (int32_t)line : r.hml;
   r.hmp0 = reg == 0x20 ? v : (reg == 0x2B ? 0u : r.hmp0);
+  if constexpr (kDefers<Tape>) {
+    if (((kVisualSubset >> reg) & 1) && rd.on) {
+      if (tape.n < (uint32_t)kRasterLogCap)
+        tape.log[tape.n] = ((uint32_t)fcw << 16) | ((reg == 0x2A && h <= 9) ? kRasterEarly : 0u) | (reg << 8) |
+                           ((reg == 0x10 || reg == 0x2A) ? r.pos : v);
+      tape.n++;
+    }
+  }
   if (!c.ft) return;   // the subset machine ignores the rest of the TIA
   if ((kObjRegs >> reg) & 1) mirror_hot(c, r);
   if (((kColdRegs >> reg) & 1) || (((kColdMaybe >> reg) & 1) && (r.xo & (kXoG1 | kXoMove | kXoLock)))) {
@@ -369,17 +419,6 @@ __device__ __forceinline__ uint32_t pull(const Ctx& c, Regs& r, const Step& st, 
   r.SP = (r.SP + 1) & 0xFF;
   return zp_read<FM>(c, r, st, 0x100u | r.SP, idx);
 }
-
-// Tape hook: called for each executed instruction the backward sweep acts on
-// (reverse_needed) with its opcode, a reference address and flag bits (the
-// soft path records these; the hard path compiles the hook away).
-struct NoTape {
-  static constexpr bool kAcc = false;
-  static constexpr bool sampler = false;
-  __device__ __forceinline__ void rec(uint32_t, uint32_t, uint32_t) {}
-  __device__ __forceinline__ void version_write(uint32_t) {}
-  __device__ __forceinline__ void pixels(float, float, float, float, float) {}
-};
 
 // Instruction length of each addressing mode, two bits per mode.
 constexpr uint32_t kModeLen = 1u | (1u << 2) | (2u << 4) | (2u << 6) | (2u << 8) | (2u << 10) | (3u << 12) |

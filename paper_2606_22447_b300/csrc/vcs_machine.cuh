@@ -783,4 +783,65 @@ __device__ __forceinline__ void finish_frame(const Ctx& c, const Regs& r, Render
   __syncwarp(c.gmask);
 }
 
+// ----------------------------------------------------------------------------
+// Deferred rasterisation (hard mode, subset machine, steps that return screens)
+// ----------------------------------------------------------------------------
+// The interpreter does not draw the frame a step returns.  It appends each
+// write to a register that changes the picture (VBLANK, COLUP0, COLUPF,
+// COLUBK, CTRLPF, PF0-2, GRP0, RESP0, HMOVE) to a log of its env in global
+// memory, after the state of those registers when the frame began, and the
+// raster kernel (vcs_raster.cu) then draws every scanline of every env in
+// parallel.  The interpreter's dependent chain loses the drawing work.
+//
+// A log entry: frame cycle of the write << 16 | early-HMOVE flag (bit 14) |
+// register << 8 | value; for RESP0 and HMOVE the value is player 0's new
+// position, which the interpreter has computed, so the raster only assigns.
+// The header of an env (kRasterHdr words): [0] entries logged; [1] the
+// colour clock at which the frame began; [2] the one at which it ended; [3]
+// COLUP0 | COLUPF << 8 | COLUBK << 16 | CTRLPF << 24, [4] PF0 | PF1 << 8 |
+// PF2 << 16 | GRP0 << 24, [5] player 0's position | VBLANK << 8 and [6] the
+// early-HMOVE line (int32, -1 none), all when the frame began.
+//
+// The log never fills: a frame's instructions start before cycle kLineCap x
+// kLineCycles (the watchdog ends it after the first that reaches it), the
+// last one writes within 7 cycles plus a WSYNC halt of at most 75, and no
+// instruction writes more than 3 times in 7 cycles (BRK pushes 3 bytes in 7,
+// which land on TIA registers when the stack pointer is below $80; JSR 2 in
+// 6; stores and pushes 1 in 3 or more).
+constexpr int kRasterHdr = 8;
+constexpr int kRasterLogCap = ((kLineCap * kLineCycles + 7 + 75) * 3 + 6) / 7;
+constexpr uint32_t kRasterEarly = 1u << 14;
+constexpr int32_t kErrRasterLog = 3;   // device error word: a log passed kRasterLogCap
+
+__device__ __forceinline__ void raster_snapshot(const Regs& r, uint32_t* h) {
+  h[3] = (r.col0 & 0xFF) | ((r.colpf & 0xFF) << 8) | ((r.colbk & 0xFF) << 16) | ((r.ctrl & 0xFF) << 24);
+  h[4] = (r.pf0 & 0xFF) | ((r.pf1 & 0xFF) << 8) | ((r.pf2 & 0xFF) << 16) | ((r.grp0 & 0xFF) << 24);
+  h[5] = (r.pos & 0xFF) | ((r.vblank & 0xFF) << 8);
+  h[6] = (uint32_t)r.hml;
+}
+
+// The drawing registers from header words 3..6.
+__device__ __forceinline__ void raster_restore(Regs& r, uint32_t w3, uint32_t w4, uint32_t w5, uint32_t w6) {
+  r.col0 = w3 & 0xFF; r.colpf = (w3 >> 8) & 0xFF; r.colbk = (w3 >> 16) & 0xFF; r.ctrl = w3 >> 24;
+  r.pf0 = w4 & 0xFF; r.pf1 = (w4 >> 8) & 0xFF; r.pf2 = (w4 >> 16) & 0xFF; r.grp0 = w4 >> 24;
+  r.pos = w5 & 0xFF; r.vblank = (w5 >> 8) & 0xFF;
+  r.hml = (int32_t)w6;
+}
+
+// Apply one log entry to the drawing registers.
+__device__ __forceinline__ void raster_apply(Regs& r, uint32_t e) {
+  const uint32_t reg = (e >> 8) & 0x3F, v = e & 0xFF;
+  r.vblank = reg == 0x01 ? v : r.vblank;
+  r.col0 = reg == 0x06 ? v : r.col0;
+  r.colpf = reg == 0x08 ? v : r.colpf;
+  r.colbk = reg == 0x09 ? v : r.colbk;
+  r.ctrl = reg == 0x0A ? v : r.ctrl;
+  r.pf0 = reg == 0x0D ? v : r.pf0;
+  r.pf1 = reg == 0x0E ? v : r.pf1;
+  r.pf2 = reg == 0x0F ? v : r.pf2;
+  r.grp0 = reg == 0x1B ? v : r.grp0;
+  r.pos = (reg == 0x10 || reg == 0x2A) ? v : r.pos;
+  r.hml = (e & kRasterEarly) ? (int32_t)div76(e >> 16) : r.hml;
+}
+
 }  // namespace vcs

@@ -230,7 +230,11 @@ __device__ __forceinline__ void set_inputs(Regs& r, uint32_t action) { set_input
 template <class Tape>
 __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, int32_t fcw) {
   if (rd.on) {
-    finish_frame(c, r, rd, tape, 3 * fcw);
+    if constexpr (kDefers<Tape>) {   // the raster kernel draws it
+      raster_end(tape, 3 * fcw);
+    } else {
+      finish_frame(c, r, rd, tape, 3 * fcw);
+    }
     rd.on = false;
   }
   if (c.ft) cx_catchup(c, r, 3 * fcw);   // collisions up to the frame end, then in the new frame's clocks
@@ -243,6 +247,7 @@ __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Ste
   if (st.want_screen && st.frames_done == st.frame_skip - 1) {
     rd.on = true;
     rd.cur = 3 * (int32_t)r.fs;
+    if constexpr (kDefers<Tape>) raster_begin(r, rd, tape);
   }
 }
 
@@ -276,6 +281,9 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
   if constexpr (!INSTR) st.instr_left = 0x7FFFFFFF;
   rd.on = active && st.want_screen && st.frame_skip == 1;
   rd.cur = 3 * (int32_t)r.fs;
+  if constexpr (kDefers<Tape>) {
+    if (rd.on) raster_begin(r, rd, tape);
+  }
   uint32_t pf = prefetch(c, r);
   while (true) {
     const bool live = active && (INSTR ? st.instr_left > 0 : st.frames_done < st.frame_skip);

@@ -356,3 +356,32 @@ def graphics_full_tia_rom(ctrlpf=0, vdel=False):
         a.op("BNE", "rel", "L")
         a.op("JMP", "abs", "FRAME")
     return rom4k(build, table=False), offs
+
+
+def dense_writes_rom():
+    """Writes a picture register every three cycles, never ending a frame by
+    VSYNC (the 512-line watchdog ends each one): every register the raster
+    log records (VBLANK, colours, CTRLPF, playfield, GRP0, RESP0, HMOVE) with
+    a value that changes each turn, over ten thousand writes per frame."""
+    def build(a):
+        a.op("SEI")
+        a.op("CLD")
+        a.op("LDA", "imm", 0x11)
+        a.label("L")
+        for reg in (0x09, 0x06, 0x08, 0x0D, 0x0E, 0x0F, 0x1B, 0x0A, 0x10, 0x20, 0x2A, 0x01):
+            a.op("STA", "zp", reg)
+        a.op("ADC", "imm", 0x07)
+        a.op("JMP", "abs", "L")
+    return rom4k(build)
+
+
+def brk_pushes_rom():
+    """BRK with the stack pointer at $0F: each BRK pushes its three bytes to
+    $010F, $010E and $010D, the TIA's PF2, PF1 and PF0 (the densest writer: 3
+    writes in 7 cycles), and its vector (the reset address) runs LDX #$0F;
+    TXS; BRK again: 3 writes every 11 cycles."""
+    def build(a):
+        a.op("LDX", "imm", 0x0F)
+        a.op("TXS")
+        a.op("BRK")
+    return rom4k(build)

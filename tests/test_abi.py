@@ -44,6 +44,16 @@ def test_config_defaults(lib):
     assert cfg.alpha == 6.0 and cfg.ystart == 34 and cfg.boot_noop_frames == 0
     assert cfg.segment_frames == 64
     assert cfg.full_tia == 0 and cfg.position_sampler == 0 and cfg.step_instructions == 0
+    assert cfg.inline_render == 0   # deferred rasterisation
+
+
+def test_binding_config_matches_header():
+    """The ctypes Config lists the header's vcs_config fields in order."""
+    src = open(os.path.join(ROOT, "include", "vcs.h")).read()
+    body = re.search(r"typedef struct vcs_config \{(.*?)\} vcs_config;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(?:float|int32_t)\s+(\w+)\s*;", body)
+    assert fields == [f for f, _ in _lib.Config._fields_]
 
 
 def _create(lib, roms, sizes, mappers, env_cart, n_carts=None, cfg=None):
@@ -76,6 +86,10 @@ def test_argument_errors_before_device_work(lib):
     cfg.envs_per_block = 48
     st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0], cfg=C.byref(cfg))
     assert st == _lib.VCS_ERR_ARG and "envs_per_block" in msg
+    lib.vcs_config_default(C.byref(cfg))
+    cfg.inline_render = 2
+    st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0], cfg=C.byref(cfg))
+    assert st == _lib.VCS_ERR_ARG and "inline_render" in msg
     assert lib.vcs_step(None, None, 1, None, None, None, None) == _lib.VCS_ERR_ARG
     tape = C.c_void_p()
     assert lib.vcs_soft_step(None, 0.1, None, 1, 1, None, None, C.byref(tape), None) == _lib.VCS_ERR_ARG

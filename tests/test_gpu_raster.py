@@ -1,0 +1,111 @@
+"""Deferred rasterisation: the step kernel logs the returned frame's
+picture-register writes and the raster kernel draws the screens from the
+logs.  Its screens must equal, bit for bit, both the step kernel's own
+drawing (inline_render = 1) and the oracle's, including frames that write
+a picture register every few cycles for 512 lines, boot frames, auto-resets
+and CUDA-graph replays."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_22447_b300 import synth
+from tests.gpu_util import assert_env_equal, gpu_rollout, make_batch, oracle_rollout, torch_cuda
+from tests.microrom import brk_pushes_rom, dense_writes_rom
+
+pytestmark = pytest.mark.gpu
+
+# every cartridge format of the subset machine's kernels, two carts each
+MAPPERS = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
+           synth.MAPPER_F8SC, synth.MAPPER_E0, synth.MAPPER_FE] * 2
+
+
+def _pair(roms, mappers, env_cart, acts, frame_skip, setup=None, **cfg):
+    """The same rollout with deferred and with inline drawing."""
+    out = []
+    for inline in (0, 1):
+        b = make_batch(roms, mappers, env_cart, inline_render=inline, **cfg)
+        if setup:
+            setup(b)
+        out.append(gpu_rollout(b, acts, frame_skip))
+        b.close()
+    return out
+
+
+@pytest.mark.parametrize("frame_skip", [1, 4])
+@pytest.mark.parametrize("epb", [16, 128])
+def test_deferred_equals_inline_every_format(frame_skip, epb):
+    roms = synth.config_carts(707, MAPPERS)
+    n = 150   # ragged blocks
+    env_cart = np.random.default_rng(7).permutation(np.arange(n) % len(MAPPERS)).astype(np.int32)
+    acts = synth.actions(707, n, 6)
+    (r0, s0, t0), (r1, s1, t1) = _pair(roms, MAPPERS, env_cart, acts, frame_skip, envs_per_block=epb)
+    assert np.array_equal(r0, r1) and np.array_equal(t0, t1)
+    bad = np.argwhere(s0 != s1)
+    assert bad.size == 0, f"{len(bad)} pixels differ, first at {bad[0].tolist()}"
+
+
+@pytest.mark.parametrize("which", ["dense", "brk"])
+@pytest.mark.parametrize("frame_skip", [1, 2])
+def test_frames_with_ten_thousand_writes(which, frame_skip):
+    """Frames that write a picture register every three cycles (or three
+    in seven, BRK pushing onto the TIA) for 512 lines: logs of over ten
+    thousand entries, drawn bit-exact with the oracle."""
+    rom = dense_writes_rom() if which == "dense" else brk_pushes_rom()
+    o = oracle.Oracle(rom, synth.MAPPER_4K)
+    o.step(0, 1)
+    assert o.counters()["tia_writes"] > 10000
+    n = 8
+    acts = synth.actions(808, n, 3)
+    b = make_batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32))
+    ram, scr, st = gpu_rollout(b, acts, frame_skip)
+    for e in range(n):
+        r2, s2, st2 = oracle_rollout(rom, synth.MAPPER_4K, acts[:, e], frame_skip)
+        assert_env_equal(e, ram[:, e], r2, "RAM")
+        assert_env_equal(e, scr[:, e], s2, "screen")
+        assert_env_equal(e, st[:, e], st2, "status")
+
+
+def test_boot_frames_and_auto_reset():
+    """Episodes end inside the rollout and power on again with a boot
+    sequence (frames without screens) before the next step."""
+    mappers = [synth.MAPPER_4K, synth.MAPPER_F8]
+    roms = synth.config_carts(909, mappers)
+    n = 24
+    env_cart = (np.arange(n) % 2).astype(np.int32)
+    acts = synth.actions(909, n, 10)
+    ep = np.random.default_rng(9).integers(2, 9, size=(n, 3)).astype(np.uint32)
+    b = make_batch(roms, mappers, env_cart, boot_noop_frames=3, boot_reset_frames=2)
+    b.set_episodes(ep)
+    ram, scr, st = gpu_rollout(b, acts, 2)
+    assert (st & 4).any()
+    for e in range(n):
+        c = int(env_cart[e])
+        r2, s2, st2 = oracle_rollout(roms[c], mappers[c], acts[:, e], 2, ep_len=ep[e], boot=(3, 2))
+        assert_env_equal(e, ram[:, e], r2, "RAM")
+        assert_env_equal(e, scr[:, e], s2, "screen")
+        assert_env_equal(e, st[:, e], st2, "status")
+
+
+def test_graph_replay_with_deferred_raster():
+    torch = torch_cuda()
+    roms = synth.config_carts(1010, synth.MIX16)
+    n = 256
+    env_cart = synth.env_cart_round_robin(n, 16)
+    acts = torch.from_numpy(synth.actions(1010, n, 3)).cuda()
+    outs = []
+    for use_graph in (False, True):
+        b = make_batch(roms, synth.MIX16, env_cart)
+        ram = torch.empty((3, n, 128), dtype=torch.uint8, device="cuda")
+        scr = torch.empty((3, n, 210, 160), dtype=torch.uint8, device="cuda")
+        if use_graph:
+            g = b.graph(acts, 4, ram, scr)
+            g.launch()
+            torch.cuda.synchronize()
+            g.destroy()
+        else:
+            b.rollout(acts, 4, ram, scr)
+        b.sync()
+        outs.append((ram.cpu().numpy(), scr.cpu().numpy()))
+        b.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
