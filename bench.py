@@ -33,17 +33,21 @@ SEED = 2
 METRIC = "env-steps/s per B300 (hard fwd; soft fwd+bwd), bit-exact vs CPU oracle"
 WORKLOAD = "hard: 4096 envs x one seed-generated 4 KB cart, frame-skip 4, RAM+screen per step"
 # algorithmic integer work per env-step: 12 operations per emulated instruction
-# and 6 per output pixel; peak = SMs x 128 integer lanes x maximum SM clock
-# DRAM bytes (read + write) of one step launch on the bench workload, from an
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the current
-# kernel; to be taken again whenever the kernel changes
-TRAFFIC_BYTES_PER_LAUNCH = 950_016 + 83_741_696
-# Counters of the same ncu capture (one k_run<0, 1, 0, 0, 0, 0> launch, 4096
-# envs in 256 blocks of 16, one lane per env): the GPU-wide fraction of issue
-# slots used (smsp__issue_active.avg.pct_of_peak_sustained_elapsed) and the
-# thread instructions executed (smsp__thread_inst_executed.sum)
-MEASURED_ISSUE_ACTIVE = 0.0981
-MEASURED_THREAD_INST = 5_537_316_593
+# (and 6 per output pixel when the step kernel draws the screen itself);
+# peak = the measured integer issue rate (vcs_int_peak)
+# DRAM bytes (read + write) of one step-kernel launch on the bench workload,
+# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernel; to be taken again whenever the kernel changes
+TRAFFIC_BYTES_PER_LAUNCH = 904_192 + 13_824
+# Counters of the same ncu capture (one k_run<0, 1, 0, 0, 0, 0, 1> launch,
+# 4096 envs in 256 blocks of 16, one lane per env, deferred rasterisation):
+# the GPU-wide fraction of issue slots used
+# (smsp__issue_active.avg.pct_of_peak_sustained_elapsed) and the thread
+# instructions executed (smsp__thread_inst_executed.sum)
+MEASURED_ISSUE_ACTIVE = 0.0956
+MEASURED_THREAD_INST = 4_837_174_222
+# DRAM bytes of the raster-kernel launch that follows it in the same capture
+RASTER_TRAFFIC_BYTES = 8_435_968 + 83_234_304
 OPS_PER_INSTRUCTION = 12
 OPS_PER_PIXEL = 6
 PIXELS_PER_STEP = 210 * 160
@@ -457,6 +461,7 @@ def gpu_arm(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    batch.time_kernels(True)   # events around each kernel of each step, on the same stream
     with ClockSampler(local) as clocks:
         # an NVTX range marks the timed launches, so that a profiler can
         # capture exactly these (ncu --nvtx --nvtx-include "timed/")
@@ -469,6 +474,8 @@ def gpu_arm(args):
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     batch.sync()
+    kt = batch.kernel_times()
+    batch.time_kernels(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     elapsed = sum(step_ms) / 1e3
     elapsed = max_over_ranks(elapsed, dist, "cuda")
@@ -489,12 +496,19 @@ def gpu_arm(args):
            "call": "vcs_rollout_host, pinned host buffers, downloads overlapping the next step"}
     del ram_h, scr_h
 
-    # roofline: algorithmic integer work of one launch / mean launch time
+    # roofline of the dominant kernel, the step kernel (the interpreter):
+    # algorithmic integer work of one launch / its mean launch time (CUDA
+    # events around it on its stream, inside the timed region); with deferred
+    # rasterisation the pixels are the raster kernel's, whose bound is HBM
     ipe = args.instr_per_step
     if ipe is None:
         ipe = bench_counts()["hard_4096x4k_instructions_per_env_step"]
-    ops = n * (ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL)
+    deferred = kt["launches"] == args.steps and kt["raster_ms"] > 0
+    # picture-register writes logged per env-step (counted by the raster kernel)
+    logged = kt["log_entries"] / max(1, kt["launches"]) / n
+    ops = n * (ipe * OPS_PER_INSTRUCTION + (0 if deferred else PIXELS_PER_STEP * OPS_PER_PIXEL))
     mean_s = elapsed / args.steps
+    k_s = kt["step_ms"] / 1e3 / max(1, kt["launches"])
     props = torch.cuda.get_device_properties(local)
     peaks = _peaks()
     clk = clocks.summary()
@@ -502,23 +516,37 @@ def gpu_arm(args):
     derived_ops = props.multi_processor_count * INT_LANES_PER_SM * max_mhz * 1e6
     from paper_2606_22447_b300 import int_peak
     peak_ops = max(int_peak() for _ in range(3))
-    roofline = {"bound": "alu", "achieved": ops / mean_s / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                "frac": ops / mean_s / peak_ops, "traffic": TRAFFIC_BYTES_PER_LAUNCH if n == N_ENVS else None,
-                "traffic_source": "ncu dram read+write, one k_run launch at 4096 envs",
-                "algorithmic_bytes": n * (PIXELS_PER_STEP + 128 + 1),
+    roofline = {"kernel": "k_run (step kernel, deferred rasterisation)" if deferred else "k_run (step kernel)",
+                "bound": "alu", "achieved": ops / k_s / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": ops / k_s / peak_ops, "traffic": TRAFFIC_BYTES_PER_LAUNCH if n == N_ENVS else None,
+                "traffic_source": "ncu dram read+write, one step-kernel launch at 4096 envs",
+                "algorithmic_bytes": n * (128 + 1 + 4 * logged + 32) if deferred
+                else n * (PIXELS_PER_STEP + 128 + 1),
+                "kernel_ms": k_s * 1e3, "kernel_timing": "CUDA events around the step kernel on its stream, "
+                                                         "every timed step",
                 "peak_source": "measured: vcs_int_peak, independent 32-bit add/shift/logic chains at full "
                                "occupancy (best of 3)",
                 "peak_derived": derived_ops / 1e12,
                 "peak_derived_source": f"{props.multi_processor_count} SMs x {INT_LANES_PER_SM} int lanes x "
                                        f"{max_mhz:.0f} MHz",
-                "traffic_note": "below the algorithmic bytes: part of the screens is still in L2 when the kernel ends",
                 "issue_frac_measured": MEASURED_ISSUE_ACTIVE if n == N_ENVS else None,
-                "lane_frac_measured": (MEASURED_THREAD_INST / (mean_s * derived_ops)) if n == N_ENVS else None,
+                "lane_frac_measured": (MEASURED_THREAD_INST / (k_s * derived_ops)) if n == N_ENVS else None,
                 "measured_source": "ncu smsp__issue_active (GPU-wide) and smsp__thread_inst_executed / "
-                                   "(SMs x 128 lanes x max clock x this run's launch time)",
-                "ops_per_env_step": ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL,
-                "instructions_per_env_step": ipe,
-                "hbm_gbs_written": n * (128 + PIXELS_PER_STEP) / mean_s / 1e9}
+                                   "(SMs x 128 lanes x max clock x this run's kernel time)",
+                "ops_per_env_step": ops / n,
+                "instructions_per_env_step": ipe}
+    raster = None
+    if deferred:
+        r_s = kt["raster_ms"] / 1e3 / kt["launches"]
+        r_bytes = n * (PIXELS_PER_STEP + 4 * logged + 32)
+        hbm = peaks.get("hbm_gbs")
+        raster = {"kernel": "k_raster", "bound": "hbm", "achieved": r_bytes / r_s / 1e9, "unit": "GB/s",
+                  "peak": hbm, "frac": (r_bytes / r_s / 1e9 / hbm) if hbm else None,
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)" if hbm else None,
+                  "traffic": RASTER_TRAFFIC_BYTES if n == N_ENVS else None,
+                  "algorithmic_bytes": r_bytes, "kernel_ms": r_s * 1e3, "log_entries_per_env": logged,
+                  "bytes_note": "screens written, log entries and headers read; the DRAM writes fall short of "
+                                "the screens because part of them is still in the 126 MB L2 when the kernel ends"}
     soft = None
     if not args.no_soft:
         from paper_2606_22447_b300 import synth as _s
@@ -555,7 +583,8 @@ def gpu_arm(args):
                        "frames_per_s": value * FRAME_SKIP, "instructions_per_s": value * ipe,
                        "parallelism": f"replicas x{world}"},
             "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
-            "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": args.steps * (2 if deferred else 1), "roofline": roofline,
+            "raster": raster, "cpu_baseline": cpu,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
             "soft_fwd_bwd": soft,
             "mixed_carts": mixed,

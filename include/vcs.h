@@ -381,6 +381,19 @@ vcs_status vcs_rollout_host(vcs_batch* b, const uint8_t* actions_host, int32_t n
  * *ops_per_s receives operations per second.  Synchronises `stream`. */
 vcs_status vcs_int_peak(double* ops_per_s, void* stream);
 
+/* Kernel timing (a measurement aid with no counterpart in the paper): while
+ * on, every frame-step launch of the batch records CUDA events on its
+ * stream around the step kernel and, with deferred rasterisation, the raster
+ * kernel; launches inside a stream capture are not timed.  `on` = 1 starts
+ * (clearing the sums; allocates an 8-byte counter the first time), 0 stops.
+ * vcs_kernel_times waits for the recorded events and returns the summed
+ * milliseconds of each kernel, the number of launches timed and (when
+ * log_entries is non-null) the raster log entries those launches drew,
+ * then clears the sums. */
+vcs_status vcs_time_kernels(vcs_batch* b, int32_t on);
+vcs_status vcs_kernel_times(vcs_batch* b, float* step_ms, float* raster_ms, int32_t* n_launches,
+                            double* log_entries);
+
 /* Fully relaxed forward, the temperature-limit study of Section 4 (Theorem 2
  * and the supplement's forward bit-exactness table).  From each env's
  * current state (read, not modified) two machines run n_instr instruction

@@ -157,6 +157,19 @@ class Batch:
         self._check(_lib.load().vcs_rollout_host(self.h, C.c_void_p(a.ctypes.data), int(a.shape[0]), frame_skip,
                                                  p(ram_out), p(screen_out), p(status_out), _stream(stream)))
 
+    def time_kernels(self, on: bool = True):
+        """Record CUDA events around each step-launch's kernels (the step
+        kernel and the raster kernel) from now on, or stop."""
+        self._check(_lib.load().vcs_time_kernels(self.h, 1 if on else 0))
+
+    def kernel_times(self) -> dict:
+        """Summed milliseconds of the step and raster kernels since
+        time_kernels(True), the launches timed and the raster log entries
+        they drew."""
+        s, r, n, k = C.c_float(), C.c_float(), C.c_int32(), C.c_double()
+        self._check(_lib.load().vcs_kernel_times(self.h, C.byref(s), C.byref(r), C.byref(n), C.byref(k)))
+        return {"step_ms": s.value, "raster_ms": r.value, "launches": n.value, "log_entries": k.value}
+
     def sync(self, stream=None):
         self._check(_lib.load().vcs_sync(self.h, _stream(stream)))
 

@@ -58,6 +58,9 @@ SIGNATURES = {
     "vcs_rom_stride": (C.c_int, [vp, C.POINTER(i32)]),
     "vcs_full_divergence": (C.c_int, [vp, C.c_float, C.c_float, vp, i32, vp, vp, vp, vp]),
     "vcs_last_error": (C.c_char_p, [vp]),
+    "vcs_time_kernels": (C.c_int, [vp, i32]),
+    "vcs_kernel_times": (C.c_int, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(i32),
+                                   C.POINTER(C.c_double)]),
     "vcs_batch_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     "vcs_set_episodes": (C.c_int, [vp, C.POINTER(C.c_uint32), i32]),
     "vcs_reset": (C.c_int, [vp, vp, vp]),

@@ -172,6 +172,23 @@ static vcs_status ensure_raster(vcs_batch* b) {
   return VCS_OK;
 }
 
+// The next three timing events of a timed launch (null when not timing or
+// the stream is being captured).
+static cudaEvent_t* timing_events(vcs_batch* b, void* stream) {
+  if (!b->timing) return nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return nullptr;
+  while (b->tk_events.size() < b->tk_used + 3) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    b->tk_events.push_back(e);
+  }
+  cudaEvent_t* ev = &b->tk_events[b->tk_used];
+  b->tk_used += 3;
+  return ev;
+}
+
 // One launch of the step kernel over p.n_steps steps; with deferred
 // rasterisation one step per launch, each followed by the raster kernel
 // that draws its screens from the logs.
@@ -193,15 +210,26 @@ static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
       q.status_out = p.status_out ? p.status_out + (size_t)t * n : nullptr;
       q.dr_log = b->dr_log;
       q.dr_hdr = b->dr_hdr;
+      cudaEvent_t* ev = timing_events(b, stream);
+      if (ev) cudaEventRecord(ev[0], (cudaStream_t)stream);
       int e = launch_step(q, b->n_blocks, b->E, stream);
       if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
-      e = launch_raster(b->dr_hdr, b->dr_log, b->n_envs, b->cfg.ystart, q.screen_out, stream);
+      if (ev) cudaEventRecord(ev[1], (cudaStream_t)stream);
+      e = launch_raster(b->dr_hdr, b->dr_log, b->n_envs, b->cfg.ystart, q.screen_out, ev ? b->tk_entries : nullptr,
+                        stream);
       if (e) return vcs_cuda_fail(b, (cudaError_t)e, "raster kernel launch");
+      if (ev) cudaEventRecord(ev[2], (cudaStream_t)stream);
     }
     return VCS_OK;
   }
+  cudaEvent_t* ev = p.n_steps > 0 ? timing_events(b, stream) : nullptr;
+  if (ev) cudaEventRecord(ev[0], (cudaStream_t)stream);
   int e = launch_step(p, b->n_blocks, b->E, stream);
   if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
+  if (ev) {
+    cudaEventRecord(ev[1], (cudaStream_t)stream);
+    cudaEventRecord(ev[2], (cudaStream_t)stream);
+  }
   return VCS_OK;
 }
 
@@ -237,6 +265,8 @@ static void free_batch(vcs_batch* b) {
     if (b->ev_copy[k]) cudaEventDestroy(b->ev_copy[k]);
   }
   if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
+  for (cudaEvent_t e : b->tk_events) cudaEventDestroy(e);
+  cudaFree(b->tk_entries);
   delete b;
 }
 
@@ -960,6 +990,48 @@ vcs_status vcs_digest(vcs_batch* b, const uint8_t* ram, const uint8_t* screen, i
     return vcs_fail(b, VCS_ERR_ARG, "ram and screen must be 16-byte aligned, out 8-byte aligned");
   int e = launch_digest(ram, screen, (uint64_t)n_steps * (uint64_t)b->n_envs, out, stream);
   if (e) return vcs_cuda_fail(b, (cudaError_t)e, "digest kernel launch");
+  return VCS_OK;
+}
+
+vcs_status vcs_time_kernels(vcs_batch* b, int32_t on) {
+  if (!b || (on != 0 && on != 1)) return VCS_ERR_ARG;
+  b->timing = on != 0;
+  if (on) {
+    b->tk_used = 0;
+    cudaError_t e;
+    if (!b->tk_entries && (e = cudaMalloc(&b->tk_entries, sizeof(unsigned long long))))
+      return vcs_cuda_fail(b, e, "timing counter");
+    if ((e = cudaMemset(b->tk_entries, 0, sizeof(unsigned long long)))) return vcs_cuda_fail(b, e, "timing counter");
+  }
+  return VCS_OK;
+}
+
+vcs_status vcs_kernel_times(vcs_batch* b, float* step_ms, float* raster_ms, int32_t* n_launches,
+                            double* log_entries) {
+  if (!b || !step_ms || !raster_ms || !n_launches) return VCS_ERR_ARG;
+  double s = 0.0, r = 0.0;
+  for (size_t i = 0; i + 3 <= b->tk_used; i += 3) {
+    float a = 0.f, c = 0.f;
+    cudaError_t e;
+    if ((e = cudaEventSynchronize(b->tk_events[i + 2])) ||
+        (e = cudaEventElapsedTime(&a, b->tk_events[i], b->tk_events[i + 1])) ||
+        (e = cudaEventElapsedTime(&c, b->tk_events[i + 1], b->tk_events[i + 2])))
+      return vcs_cuda_fail(b, e, "kernel timing events");
+    s += a;
+    r += c;
+  }
+  *step_ms = (float)s;
+  *raster_ms = (float)r;
+  *n_launches = (int32_t)(b->tk_used / 3);
+  b->tk_used = 0;
+  if (log_entries) {
+    unsigned long long c = 0;
+    cudaError_t e;
+    if (b->tk_entries && (e = cudaMemcpy(&c, b->tk_entries, sizeof c, cudaMemcpyDeviceToHost)))
+      return vcs_cuda_fail(b, e, "timing counter");
+    *log_entries = (double)c;
+    if (b->tk_entries) cudaMemset(b->tk_entries, 0, sizeof c);
+  }
   return VCS_OK;
 }
 

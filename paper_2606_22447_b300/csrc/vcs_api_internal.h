@@ -45,6 +45,12 @@ struct vcs_batch {
   // that returns screens
   uint32_t* dr_log = nullptr;      // [n_envs][kRasterLogCap]
   uint32_t* dr_hdr = nullptr;      // [n_envs][kRasterHdr]
+  // kernel timing (vcs_time_kernels): three events per timed launch (before
+  // the step kernel, after it, after the raster kernel), reused
+  bool timing = false;
+  std::vector<cudaEvent_t> tk_events;
+  size_t tk_used = 0;
+  unsigned long long* tk_entries = nullptr;   // device: log entries the timed raster launches drew
   uint32_t* ep_len = nullptr;
   int32_t n_episodes = 0;
   uint8_t* start_noops = nullptr;  // [n_envs][n_start] NOOP frames starting each episode

@@ -119,10 +119,11 @@ int launch_soft_forward_xm(const StepParams& p, int n_blocks, int envs_per_block
 int launch_step_ft(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 // The hard step kernel with deferred rasterisation (p.dr_log set; one step),
 // and the raster kernel that then draws the step's screens [n_envs][210][160]
-// from the logs (vcs_raster.cu).
+// from the logs (vcs_raster.cu), adding the entries it draws to *entries
+// when that is non-null.
 int launch_step_dr(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_raster(const uint32_t* hdr, const uint32_t* log, int32_t n_envs, int32_t ystart, uint8_t* screen,
-                  void* stream);
+                  unsigned long long* entries, void* stream);
 int launch_soft_forward_ft(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 
 }  // namespace vcs

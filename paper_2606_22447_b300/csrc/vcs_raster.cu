@@ -7,9 +7,9 @@
 // of dependent instructions; drawing the returned frame inside that chain
 // cost about an eighth of it.  Scanlines are independent once the register
 // state at each line start is known, so they are drawn here with a warp per
-// env: the warp first walks the env's log once (every lane the same walk,
-// the entries fetched 32 at a time and broadcast by shuffles) to record each
-// screen row's starting registers and first entry in shared memory, then
+// env: the warp first walks the env's log 32 entries at a time (warp ballots
+// find each register's last writer) to record each screen row's starting
+// registers and first entry in shared memory, then
 // each lane draws whole rows with the interpreter's own span renderer and
 // stores them as ten 16-byte words.
 #include <cuda_runtime.h>
@@ -24,62 +24,93 @@ int launch_step_dr(const StepParams& p, int n_blocks, int E, void* stream) {
 
 constexpr int kRasterWarps = 4;   // envs per block
 
+// Per screen row: the ten drawing registers when the row starts (bytes 0..9
+// in the order of header words 3..5: COLUP0, COLUPF, COLUBK, CTRLPF, PF0, PF1,
+// PF2, GRP0, player 0's position, VBLANK) and the row's first log entry
+// (bytes 10..11; a log holds at most kRasterLogCap < 2^16 entries).  12 bytes
+// a row and 160 bytes of line buffer a lane keep a warp under 7.7 KB, so 28
+// warps fit an SM and 4096 envs run in one wave.
 struct RasterSmem {
   uint32_t line[kRasterWarps][40][32];           // line buffers: word g of lane l at [g][l]
-  uint8_t snap[kRasterWarps][kScreenH][12];      // registers at each screen row's start (header words 3..5)
-  uint32_t first[kRasterWarps][kScreenH + 1];    // each row's first log entry
+  uint32_t row[kRasterWarps][kScreenH][3];
 };
+static_assert(kRasterLogCap < 65536, "row starts are 16-bit");
 
-// The register lane k of the log walk follows, and its byte in a row's
-// snapshot (header words 3..5): COLUP0, COLUPF, COLUBK, CTRLPF, PF0, PF1,
-// PF2, GRP0, player 0's position (RESP0 and HMOVE), VBLANK.
-__constant__ uint8_t kWalkReg[10] = {0x06, 0x08, 0x09, 0x0A, 0x0D, 0x0E, 0x0F, 0x1B, 0x10, 0x01};
+// Log register of each walked register (HMOVE also moves player 0).
+__device__ __forceinline__ bool walk_match(uint32_t reg, int k) {
+  constexpr uint8_t regs[10] = {0x06, 0x08, 0x09, 0x0A, 0x0D, 0x0E, 0x0F, 0x1B, 0x10, 0x01};
+  return reg == regs[k] || (k == 8 && reg == 0x2A);
+}
 
+// entries: when non-null, the log entries drawn are added to it (kernel
+// timing's count of the bytes read).
 __global__ void __launch_bounds__(32 * kRasterWarps) k_raster(const uint32_t* hdr, const uint32_t* log,
-                                                               int32_t n_envs, int32_t ystart, uint8_t* screen) {
+                                                               int32_t n_envs, int32_t ystart, uint8_t* screen,
+                                                               unsigned long long* entries) {
   __shared__ RasterSmem sm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int env = blockIdx.x * kRasterWarps + w;
   if (env >= n_envs) return;   // whole warps leave together
   const uint32_t* h = hdr + (size_t)env * kRasterHdr;
   const uint32_t n = h[0];
+  if (entries && lane == 0) atomicAdd(entries, (unsigned long long)n);
   const int32_t start = (int32_t)h[1], end = (int32_t)h[2];
   const uint32_t* lg = log + (size_t)env * kRasterLogCap;
+  const uint32_t below = (1u << lane) - 1u;
 
-  // Walk the log once: row r starts with the registers left by every entry
-  // before its first colour clock 228 (ystart + r); an entry at exactly that
-  // clock belongs to the row (it takes effect before the row's first pixel).
-  // Lane k < 10 follows register k alone, so an entry costs each lane one
-  // compare and select; the entries are fetched 32 at a time and broadcast.
-  // The early-HMOVE line needs no snapshot: at a row's start it names an
-  // earlier line, which does not blank this one.
-  const uint32_t myreg = lane < 10 ? kWalkReg[lane] : 0xFFu;
-  const uint32_t alt = lane == 8 ? 0x2Au : 0xFFu;   // HMOVE moves player 0 too
-  uint32_t val = lane < 10 ? (h[3 + lane / 4] >> (8 * (lane & 3))) & 0xFF : 0u;
-  uint32_t row = 0;
-  auto record = [&](uint32_t j) {
-    if (lane < 10) sm.snap[w][row][lane] = (uint8_t)val;
-    if (lane == 0) sm.first[w][row] = j;
-    row++;
+  // Walk the log 32 entries at a time.  Row r starts with the registers left
+  // by every entry before its first colour clock 228 (ystart + r); an entry
+  // at exactly that clock belongs to the row (it takes effect before the
+  // row's first pixel).  Lane j holds entry j of the chunk; for each register
+  // a ballot finds the last lane below j that writes it, so each lane knows
+  // the registers just before its entry, and records the rows its entry
+  // opens (the rows after the previous entry's row, up to its own).  The
+  // early-HMOVE line needs no snapshot: at a row's start it names an earlier
+  // line, which does not blank this one.
+  uint32_t carry[10];
+#pragma unroll
+  for (int k = 0; k < 10; k++) carry[k] = (h[3 + k / 4] >> (8 * (k & 3))) & 0xFF;
+  int32_t next = 0;   // first row not yet recorded
+  auto put_row = [&](int32_t r, const uint32_t* v, uint32_t first) {
+    uint32_t* d = sm.row[w][r];
+    d[0] = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
+    d[1] = v[4] | (v[5] << 8) | (v[6] << 16) | (v[7] << 24);
+    d[2] = v[8] | (v[9] << 8) | (first << 16);
   };
-  for (uint32_t j0 = 0; j0 < n && row < (uint32_t)kScreenH; j0 += 32) {
-    const uint32_t mine = j0 + lane < n ? lg[j0 + lane] : 0u;
-    const uint32_t m = n - j0 < 32u ? n - j0 : 32u;
-    for (uint32_t k = 0; k < m; k++) {
-      const uint32_t e = __shfl_sync(0xFFFFFFFFu, mine, (int)k);
-      const int32_t cc = 3 * (int32_t)(e >> 16);
-      while (row < (uint32_t)kScreenH && cc >= 228 * (ystart + (int32_t)row)) record(j0 + k);
-      const uint32_t reg = (e >> 8) & 0x3F;
-      val = (reg == myreg || reg == alt) ? e & 0xFF : val;
+  for (uint32_t j0 = 0; j0 < n && next < kScreenH; j0 += 32) {
+    const bool valid = j0 + lane < n;
+    const uint32_t e = valid ? lg[j0 + lane] : 0xFFFFFFFFu;
+    const uint32_t reg = (e >> 8) & 0x3F;
+    const int32_t line = valid ? (int32_t)div228(3 * (e >> 16)) : 0x7FFFFFF;
+    int32_t mine = line - ystart;                 // the row this entry falls in
+    mine = mine < -1 ? -1 : (mine > kScreenH ? kScreenH : mine);
+    int32_t prev = __shfl_up_sync(0xFFFFFFFFu, mine, 1);
+    if (lane == 0) prev = next - 1;
+    uint32_t v[10];
+#pragma unroll
+    for (int k = 0; k < 10; k++) {
+      const uint32_t writers = __ballot_sync(0xFFFFFFFFu, valid && walk_match(reg, k));
+      const uint32_t before = writers & below;
+      const uint32_t src = before ? 31u - __clz(before) : 0u;
+      const uint32_t got = __shfl_sync(0xFFFFFFFFu, e & 0xFF, (int)src);
+      v[k] = before ? got : carry[k];
+      carry[k] = writers ? __shfl_sync(0xFFFFFFFFu, e & 0xFF, 31 - __clz(writers)) : carry[k];
     }
+    // rows (prev, mine] inside the screen open at this entry
+    const int32_t r0 = prev + 1 > next ? prev + 1 : next;
+    for (int32_t r = r0; valid && r <= mine && r < kScreenH; r++) put_row(r, v, j0 + lane);
+    const int32_t hi = __reduce_max_sync(0xFFFFFFFFu, valid ? mine : -1);
+    next = hi + 1 > next ? hi + 1 : next;
   }
-  while (row < (uint32_t)kScreenH) record(n);
-  if (lane == 0) sm.first[w][kScreenH] = n;
+  // rows after the last entry keep the final registers
+  for (int32_t r = next + lane; r < kScreenH; r += 32) put_row(r, carry, n);
   __syncwarp();
 
   // Draw rows lane, lane + 32, ...: the colour clocks of the row inside the
   // frame, the row's entries applied at their clocks, into the lane's line
-  // buffer (zero where the frame drew nothing), then one 160-byte store.
+  // buffer, then one 160-byte store.  A row the frame covers from before its
+  // first visible column to its end is written whole by the spans; the
+  // others are zeroed first (where the frame drew nothing).
   Ctx c{};
   c.line = &sm.line[w][0][lane];
   c.E = 32;
@@ -93,13 +124,16 @@ __global__ void __launch_bounds__(32 * kRasterWarps) k_raster(const uint32_t* hd
   Regs r{};
   uint8_t* out = screen + (size_t)env * (kScreenH * kScreenW);
   for (uint32_t rr = (uint32_t)lane; rr < (uint32_t)kScreenH; rr += 32) {
-    const uint32_t* sn = reinterpret_cast<const uint32_t*>(sm.snap[w][rr]);
-    raster_restore(r, sn[0], sn[1], sn[2], 0xFFFFFFFFu);
+    const uint32_t* sn = sm.row[w][rr];
+    raster_restore(r, sn[0], sn[1], sn[2] & 0xFFFF, 0xFFFFFFFFu);
+    const uint32_t j0 = sn[2] >> 16, j1 = rr + 1 < (uint32_t)kScreenH ? sm.row[w][rr + 1][2] >> 16 : n;
     const int32_t line = ystart + (int32_t)rr, lbeg = 228 * line, lend = lbeg + 228;
     int32_t cur = start > lbeg ? start : lbeg;
     const int32_t stop = end < lend ? end : lend;
+    if (cur > lbeg + 68 || stop < lend) {
 #pragma unroll
-    for (uint32_t g = 0; g < 40; g++) c.line[g * 32] = 0u;
+      for (uint32_t g = 0; g < 40; g++) c.line[g * 32] = 0u;
+    }
     auto draw = [&](int32_t to) {
       if (to > stop) to = stop;
       if (to <= cur) return;
@@ -108,11 +142,17 @@ __global__ void __launch_bounds__(32 * kRasterWarps) k_raster(const uint32_t* hd
       if (x1 > x0) render_span(c, r, rd, nt, x0, x1, line);
       cur = to;
     };
-    const uint32_t j1 = sm.first[w][rr + 1];
-    for (uint32_t j = sm.first[w][rr]; j < j1; j++) {
-      const uint32_t e = lg[j];
-      draw(3 * (int32_t)(e >> 16));
-      raster_apply(r, e);
+    // the row's entries, four loads in flight at a time
+    for (uint32_t j = j0; j < j1; j += 4) {
+      uint32_t q[4];
+#pragma unroll
+      for (uint32_t k = 0; k < 4; k++) q[k] = j + k < j1 ? lg[j + k] : 0u;
+#pragma unroll
+      for (uint32_t k = 0; k < 4; k++) {
+        if (j + k >= j1) break;
+        draw(3 * (int32_t)(q[k] >> 16));
+        raster_apply(r, q[k]);
+      }
     }
     draw(stop);
     uint4* dst = reinterpret_cast<uint4*>(out + rr * kScreenW);
@@ -124,10 +164,10 @@ __global__ void __launch_bounds__(32 * kRasterWarps) k_raster(const uint32_t* hd
 }
 
 int launch_raster(const uint32_t* hdr, const uint32_t* log, int32_t n_envs, int32_t ystart, uint8_t* screen,
-                  void* stream) {
+                  unsigned long long* entries, void* stream) {
   if (n_envs <= 0) return 0;
   const int blocks = (n_envs + kRasterWarps - 1) / kRasterWarps;
-  k_raster<<<blocks, 32 * kRasterWarps, 0, (cudaStream_t)stream>>>(hdr, log, n_envs, ystart, screen);
+  k_raster<<<blocks, 32 * kRasterWarps, 0, (cudaStream_t)stream>>>(hdr, log, n_envs, ystart, screen, entries);
   return (int)cudaGetLastError();
 }
 
