@@ -402,13 +402,12 @@ def mixed_leg(n_envs, steps, reps, full_tia=False):
         done += int((st & 4).count_nonzero().item())
     b.sync()
     ms = statistics.median(times)
-    k = tune["steps_per_launch"] or steps
     g.destroy()
     return {"env_steps_per_s": n_envs * steps / (ms / 1e3), "ms_per_graph": ms, "n_envs": n_envs,
             "steps_per_graph": steps, "episodes_ended": done,
             "carts": ("full-TIA carts of the ten formats (2K 4K F8 F6 F4 F8SC F6SC F4SC E0 FE), full_tia = 1"
                       if full_tia else "6x2K + 6x4K + 4xF8"),
-            "autotune": tune, "gpu_launches_per_graph": -(-steps // k),
+            "autotune": tune, "gpu_launches_per_graph": 2 * steps,   # per step: the step kernel and the raster kernel
             "outputs": "RAM + screen per step (2.2 GB per step at 65,536 envs), larger than L2"}
 
 

@@ -179,16 +179,16 @@ typedef struct vcs_config {
                                0 = off (default).  Forward outputs do not
                                depend on it. */
   int32_t inline_render;    /* 0 (default) = deferred rasterisation for hard
-                               frame steps of the subset machine that return
-                               screens: the step kernel logs the returned
-                               frame's writes to picture registers (after the
-                               registers' state when the frame began) and a
-                               raster kernel draws all scanlines of all envs
-                               in parallel from the logs, one step per
-                               launch; the logs hold 67 KB per env, made at
-                               the first such step.  1 = the step kernel
-                               draws the frame itself as it runs.  Screens
-                               are the same either way. */
+                               frame steps that return screens: the step
+                               kernel logs the returned frame's TIA writes
+                               that drawing depends on (after the registers'
+                               state when the frame began) and a raster
+                               kernel draws all scanlines of all envs in
+                               parallel from the logs, one step per launch;
+                               the logs hold 67 KB per env, made at the first
+                               such step.  1 = the step kernel draws the
+                               frame itself as it runs.  Screens are the same
+                               either way. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

@@ -150,10 +150,11 @@ static bool valid_tpe(int E, int T) { return (T == 1 || T == 2 || T == 4 || T ==
 
 
 
-// Deferred rasterisation serves hard frame steps of the subset machine that
-// return screens, unless the batch asks for drawing in the step kernel.
+// Hard frame steps run the step kernel built without drawing (deferred
+// rasterisation), unless the batch asks for drawing in the step kernel;
+// with screens its logs go to the raster kernel, one step per launch.
 static bool raster_applies(const vcs_batch* b, const StepParams& p) {
-  return p.screen_out && p.n_steps > 0 && !p.full_tia && p.step_instr <= 0 && b->cfg.inline_render == 0;
+  return p.n_steps > 0 && p.step_instr <= 0 && b->cfg.inline_render == 0;
 }
 
 // The logs take kRasterLogCap entries per env (67 KB, the most picture-
@@ -193,6 +194,19 @@ static cudaEvent_t* timing_events(vcs_batch* b, void* stream) {
 // rasterisation one step per launch, each followed by the raster kernel
 // that draws its screens from the logs.
 static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
+  if (raster_applies(b, p) && !p.screen_out) {   // nothing to draw: the lean kernel, as many steps as asked
+    StepParams q = p;
+    q.dr = 1;
+    cudaEvent_t* ev = timing_events(b, stream);
+    if (ev) cudaEventRecord(ev[0], (cudaStream_t)stream);
+    int e = launch_step(q, b->n_blocks, b->E, stream);
+    if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
+    if (ev) {
+      cudaEventRecord(ev[1], (cudaStream_t)stream);
+      cudaEventRecord(ev[2], (cudaStream_t)stream);
+    }
+    return VCS_OK;
+  }
   if (raster_applies(b, p)) {
     vcs_status st = ensure_raster(b);
     if (st != VCS_OK) return st;
@@ -208,6 +222,7 @@ static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
       q.ram_out = p.ram_out ? p.ram_out + (size_t)t * n * 128 : nullptr;
       q.screen_out = p.screen_out + (size_t)t * n * kScreenH * kScreenW;
       q.status_out = p.status_out ? p.status_out + (size_t)t * n : nullptr;
+      q.dr = 1;
       q.dr_log = b->dr_log;
       q.dr_hdr = b->dr_hdr;
       cudaEvent_t* ev = timing_events(b, stream);
@@ -215,8 +230,8 @@ static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
       int e = launch_step(q, b->n_blocks, b->E, stream);
       if (e) return vcs_cuda_fail(b, (cudaError_t)e, "step kernel launch");
       if (ev) cudaEventRecord(ev[1], (cudaStream_t)stream);
-      e = launch_raster(b->dr_hdr, b->dr_log, b->n_envs, b->cfg.ystart, q.screen_out, ev ? b->tk_entries : nullptr,
-                        stream);
+      e = (p.full_tia ? launch_raster_ft : launch_raster)(b->dr_hdr, b->dr_log, b->n_envs, b->cfg.ystart,
+                                                         q.screen_out, ev ? b->tk_entries : nullptr, stream);
       if (e) return vcs_cuda_fail(b, (cudaError_t)e, "raster kernel launch");
       if (ev) cudaEventRecord(ev[2], (cudaStream_t)stream);
     }
@@ -906,7 +921,7 @@ vcs_status vcs_graph_create(vcs_batch* b, const uint8_t* actions, int32_t n_step
   *out = nullptr;
   if (!actions || n_steps < 1 || frame_skip < 1)
     return vcs_fail(b, VCS_ERR_ARG, "actions, n_steps >= 1 and frame_skip >= 1 required");
-  if (screen_out && !b->cfg.full_tia && b->cfg.step_instructions <= 0 && b->cfg.inline_render == 0) {
+  if (screen_out && b->cfg.step_instructions <= 0 && b->cfg.inline_render == 0) {
     vcs_status st = ensure_raster(b);   // allocated before the capture, not inside it
     if (st != VCS_OK) return st;
   }

@@ -72,6 +72,11 @@ constexpr uint64_t kGraphicsRegs = reg_bits({0x0D, 0x0E, 0x0F, 0x1B});
 // and ENABL's).
 constexpr uint64_t kGraphicsRegsFT = reg_bits({0x1C, 0x1D, 0x1E, 0x1F});
 
+// With the whole TIA and deferred rasterisation, the writes the raster
+// replays: every register drawing depends on, the motion registers included
+// (HMOVE reads them), not the collision clear.
+constexpr uint64_t kRasterRegsFT = (kVisualRegs | kColdRegs | kColdMaybe | reg_bits({0x20})) & ~reg_bits({0x2C});
+
 // Tape hook: called for each executed instruction the backward sweep acts on
 // (reverse_needed) with its opcode, a reference address and flag bits (the
 // soft path records these; the hard path compiles the hook away).
@@ -95,12 +100,17 @@ struct DeferTape : NoTape {
 template <class Tape>
 constexpr bool kDefers = std::is_same<Tape, DeferTape>::value;
 
-// The returned frame starts: its drawing registers and first colour clock
-// go to the header, and the log starts empty.
-__device__ __forceinline__ void raster_begin(const Regs& r, const Render& rd, DeferTape& tape) {
+// The returned frame starts: its drawing registers (with the whole TIA also
+// HMP0 and the cold words) and first colour clock go to the header, and the
+// log starts empty.
+__device__ __forceinline__ void raster_begin(const Ctx& c, const Regs& r, const Render& rd, DeferTape& tape) {
   tape.n = 0;
   tape.hdr[1] = (uint32_t)rd.cur;
   raster_snapshot(r, tape.hdr);
+  if (c.ft) {
+    tape.hdr[5] |= (r.hmp0 & 0xFF) << 16;
+    for (uint32_t k = 0; k < 4; k++) tape.hdr[7 + k] = c.tx[k * c.E];
+  }
 }
 
 // The returned frame ends at colour clock `end`.  kRasterLogCap bounds the
@@ -119,23 +129,10 @@ __device__ __forceinline__ void raster_end(DeferTape& tape, int32_t end) {
 static __device__ __noinline__ uint2 tia_write_cold(uint32_t* tx, uint32_t E, uint32_t reg, uint32_t v, uint32_t h,
                                              uint32_t grp0, uint32_t pos0, uint32_t cx);
 
-// A TIA register write at frame cycle fcw.  A write that changes the picture
-// first draws the pending span with the old registers.  The register update
-// itself is a set of selects rather than a switch: one indirect branch per
-// write costs more than the few dozen independent integer operations.
-template <class Tape>
-__device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t reg,
-                                          uint32_t v, int32_t fcw) {
-  if constexpr (!kDefers<Tape>) {
-    if ((((c.ft ? kVisualRegs : kVisualSubset) >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
-    if (c.ft && ((kObjRegs >> reg) & 1)) cx_catchup(c, r, 3 * fcw);
-  }
-  tape.version_write(reg);
-  const uint32_t line = div76((uint32_t)fcw);
-  const uint32_t m = (uint32_t)fcw - 76u * line;   // CPU cycle within the line
-  const uint32_t h = 3u * m;                       // colour clock within the line
-  st.fe_at = (reg == 0x00 && !(r.vsync & 2) && (v & 2)) ? fcw : st.fe_at;
-  st.stall += (reg == 0x02 && m != 0) ? (int32_t)(76u - m) : 0;
+// The hot registers' part of a write of v to TIA register reg at scanline
+// `line`, colour clock h within it (the interpreter's registers; the raster
+// kernels replay writes with it too).
+__device__ __forceinline__ void tia_hot(Regs& r, uint32_t reg, uint32_t v, uint32_t line, uint32_t h) {
   r.vsync = reg == 0x00 ? v : r.vsync;
   r.vblank = reg == 0x01 ? v : r.vblank;
   r.col0 = reg == 0x06 ? v : r.col0;
@@ -154,17 +151,47 @@ __device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Ste
   r.pos = reg == 0x10 ? resp : (reg == 0x2A ? hmov : r.pos);
   r.hml = (reg == 0x2A && h <= 9) ? (int32_t)line : r.hml;
   r.hmp0 = reg == 0x20 ? v : (reg == 0x2B ? 0u : r.hmp0);
+}
+
+// Whether a write to reg touches the cold words (vcs_tia.cuh) given the
+// summary bits xo.
+__device__ __forceinline__ bool cold_write(uint32_t reg, uint32_t xo) {
+  return ((kColdRegs >> reg) & 1) || (((kColdMaybe >> reg) & 1) && (xo & (kXoG1 | kXoMove | kXoLock)));
+}
+
+// A TIA register write at frame cycle fcw.  A write that changes the picture
+// first draws the pending span with the old registers (with deferred
+// rasterisation it goes to the log instead).  The register update itself is
+// a set of selects rather than a switch: one indirect branch per write costs
+// more than the few dozen independent integer operations.
+template <class Tape>
+__device__ __forceinline__ void tia_write(const Ctx& c, Regs& r, Render& rd, Step& st, Tape& tape, uint32_t reg,
+                                          uint32_t v, int32_t fcw) {
+  if constexpr (!kDefers<Tape>) {
+    if ((((c.ft ? kVisualRegs : kVisualSubset) >> reg) & 1) && rd.on) render_to(c, r, rd, tape, 3 * fcw);
+  }
+  if (c.ft && ((kObjRegs >> reg) & 1)) cx_catchup(c, r, 3 * fcw);
+  tape.version_write(reg);
+  const uint32_t line = div76((uint32_t)fcw);
+  const uint32_t m = (uint32_t)fcw - 76u * line;   // CPU cycle within the line
+  const uint32_t h = 3u * m;                       // colour clock within the line
+  st.fe_at = (reg == 0x00 && !(r.vsync & 2) && (v & 2)) ? fcw : st.fe_at;
+  st.stall += (reg == 0x02 && m != 0) ? (int32_t)(76u - m) : 0;
+  tia_hot(r, reg, v, line, h);
   if constexpr (kDefers<Tape>) {
-    if (((kVisualSubset >> reg) & 1) && rd.on) {
+    // the subset machine's entries carry player 0's new position for RESP0
+    // and HMOVE; the whole TIA's are the raw writes its raster replays
+    if ((((c.ft ? kRasterRegsFT : kVisualSubset) >> reg) & 1) && rd.on) {
       if (tape.n < (uint32_t)kRasterLogCap)
-        tape.log[tape.n] = ((uint32_t)fcw << 16) | ((reg == 0x2A && h <= 9) ? kRasterEarly : 0u) | (reg << 8) |
-                           ((reg == 0x10 || reg == 0x2A) ? r.pos : v);
+        tape.log[tape.n] = c.ft ? ((uint32_t)fcw << 16) | (reg << 8) | v
+                                : ((uint32_t)fcw << 16) | ((reg == 0x2A && h <= 9) ? kRasterEarly : 0u) |
+                                      (reg << 8) | ((reg == 0x10 || reg == 0x2A) ? r.pos : v);
       tape.n++;
     }
   }
   if (!c.ft) return;   // the subset machine ignores the rest of the TIA
   if ((kObjRegs >> reg) & 1) mirror_hot(c, r);
-  if (((kColdRegs >> reg) & 1) || (((kColdMaybe >> reg) & 1) && (r.xo & (kXoG1 | kXoMove | kXoLock)))) {
+  if (cold_write(reg, r.xo)) {
     const uint2 o = tia_write_cold(c.tx, c.E, reg, v, h, r.grp0, r.pos, r.cx);
     r.xo = o.x;
     r.cx = o.y;

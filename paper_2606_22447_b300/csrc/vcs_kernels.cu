@@ -112,7 +112,7 @@ int launch_cart_ram(const SoA& s, int32_t n_envs, uint8_t* out, void* stream) {
 size_t step_smem_bytes(int E, uint32_t rom_stride, int ram_words) { return smem_bytes(E, rom_stride, ram_words); }
 
 int launch_step(const StepParams& p, int n_blocks, int E, void* stream) {
-  if (p.dr_log) return launch_step_dr(p, n_blocks, E, stream);
+  if (p.dr) return launch_step_dr(p, n_blocks, E, stream);
   if (p.full_tia) return launch_step_ft(p, n_blocks, E, stream);
   if (p.xmap) return launch_step_xm(p, n_blocks, E, stream);
   return launch_run<false, false, false>(p, n_blocks, E, stream);

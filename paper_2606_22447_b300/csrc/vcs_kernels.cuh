@@ -86,9 +86,11 @@ struct StepParams {
   uint32_t* ckpt;           // [n_segments][kStateWords][n_envs]
   int32_t seg_steps;        // steps per checkpoint segment
   uint32_t* seg_counts;     // [n_segments][2]: max instructions, max colour writes
-  // deferred rasterisation (hard mode, subset machine, one step per launch;
-  // vcs_machine.cuh): non-null selects it
-  uint32_t* dr_log;         // [n_envs][kRasterLogCap] log entries
+  // deferred rasterisation (hard frame steps; vcs_machine.cuh): dr selects
+  // the step kernel that draws nothing; with screens it logs the returned
+  // frame (one step per launch) to dr_log / dr_hdr
+  int32_t dr;
+  uint32_t* dr_log;         // [n_envs][kRasterLogCap] log entries, or null without screens
   uint32_t* dr_hdr;         // [n_envs][kRasterHdr] headers
 };
 
@@ -117,13 +119,15 @@ int launch_soft_forward(const StepParams& p, int n_blocks, int envs_per_block, v
 int launch_step_xm(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_soft_forward_xm(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_step_ft(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
-// The hard step kernel with deferred rasterisation (p.dr_log set; one step),
+// The hard step kernel with deferred rasterisation (p.dr set; with screens one step),
 // and the raster kernel that then draws the step's screens [n_envs][210][160]
 // from the logs (vcs_raster.cu), adding the entries it draws to *entries
 // when that is non-null.
 int launch_step_dr(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 int launch_raster(const uint32_t* hdr, const uint32_t* log, int32_t n_envs, int32_t ystart, uint8_t* screen,
                   unsigned long long* entries, void* stream);
+int launch_raster_ft(const uint32_t* hdr, const uint32_t* log, int32_t n_envs, int32_t ystart, uint8_t* screen,
+                     unsigned long long* entries, void* stream);
 int launch_soft_forward_ft(const StepParams& p, int n_blocks, int envs_per_block, void* stream);
 
 }  // namespace vcs

@@ -799,8 +799,11 @@ __device__ __forceinline__ void finish_frame(const Ctx& c, const Regs& r, Render
 // The header of an env (kRasterHdr words): [0] entries logged; [1] the
 // colour clock at which the frame began; [2] the one at which it ended; [3]
 // COLUP0 | COLUPF << 8 | COLUBK << 16 | CTRLPF << 24, [4] PF0 | PF1 << 8 |
-// PF2 << 16 | GRP0 << 24, [5] player 0's position | VBLANK << 8 and [6] the
-// early-HMOVE line (int32, -1 none), all when the frame began.
+// PF2 << 16 | GRP0 << 24, [5] player 0's position | VBLANK << 8 (| HMP0 <<
+// 16 with the whole TIA) and [6] the early-HMOVE line (int32, -1 none), all
+// when the frame began; with the whole TIA [7..10] the cold words w0..w3.
+// The whole TIA's entries are raw writes (frame cycle << 16 | register << 8
+// | value) that its raster replays with the interpreter's own functions.
 //
 // The log never fills: a frame's instructions start before cycle kLineCap x
 // kLineCycles (the watchdog ends it after the first that reaches it), the
@@ -808,7 +811,7 @@ __device__ __forceinline__ void finish_frame(const Ctx& c, const Regs& r, Render
 // instruction writes more than 3 times in 7 cycles (BRK pushes 3 bytes in 7,
 // which land on TIA registers when the stack pointer is below $80; JSR 2 in
 // 6; stores and pushes 1 in 3 or more).
-constexpr int kRasterHdr = 8;
+constexpr int kRasterHdr = 12;
 constexpr int kRasterLogCap = ((kLineCap * kLineCycles + 7 + 75) * 3 + 6) / 7;
 constexpr uint32_t kRasterEarly = 1u << 14;
 constexpr int32_t kErrRasterLog = 3;   // device error word: a log passed kRasterLogCap

@@ -19,7 +19,9 @@
 namespace vcs {
 
 int launch_step_dr(const StepParams& p, int n_blocks, int E, void* stream) {
-  return p.xmap ? launch_run_dr<true>(p, n_blocks, E, stream) : launch_run_dr<false>(p, n_blocks, E, stream);
+  // the whole TIA's kernels take every cartridge format
+  if (p.full_tia) return launch_run_dr<true, true>(p, n_blocks, E, stream);
+  return p.xmap ? launch_run_dr<true, false>(p, n_blocks, E, stream) : launch_run_dr<false, false>(p, n_blocks, E, stream);
 }
 
 constexpr int kRasterWarps = 4;   // envs per block
@@ -161,6 +163,151 @@ __global__ void __launch_bounds__(32 * kRasterWarps) k_raster(const uint32_t* hd
       dst[q] = make_uint4(c.line[(4 * q) * 32], c.line[(4 * q + 1) * 32], c.line[(4 * q + 2) * 32],
                           c.line[(4 * q + 3) * 32]);
   }
+}
+
+// ---------------------------------------------------------------------------
+// The whole TIA.  Its logs hold the raw writes; a write's effect depends on
+// other registers (HMOVE on every motion register, GRP0 and GRP1 on each
+// other's delayed copies, missile locks on the players' positions), so the
+// walk replays them in order with the interpreter's own functions (tia_hot,
+// tia_write_cold) rather than by ballots: every lane of the warp replays the
+// same writes on the same registers (the entries fetched 32 at a time and
+// broadcast), lane 0 records each row's starting state (the hot words, HMP0
+// and the four cold words, 32 bytes), and then each lane draws its rows,
+// replaying the row's writes on its own copy of the cold words.
+// ---------------------------------------------------------------------------
+constexpr int kRasterFtWarps = 2;   // envs per block
+
+struct RasterFtSmem {
+  uint32_t line[kRasterFtWarps][40][32];      // line buffers: word g of lane l at [g][l]
+  uint32_t row[kRasterFtWarps][kScreenH][8];  // hot words 3..5 (| HMP0 << 16), w0..w3, first entry
+  uint32_t tx[kRasterFtWarps][6][32];         // each lane's cold words (stride 32)
+  uint32_t walk[kRasterFtWarps][6];           // the walk's cold words (stride 1)
+};
+
+// Replay one logged write of the whole TIA on r and the cold words at tx
+// (stride E).
+__device__ __forceinline__ void raster_replay(Regs& r, uint32_t* tx, uint32_t E, uint32_t e) {
+  const uint32_t fcw = e >> 16, reg = (e >> 8) & 0x3F, v = e & 0xFF;
+  const uint32_t line = div76(fcw), h = 3u * (fcw - 76u * line);
+  tia_hot(r, reg, v, line, h);
+  if (cold_write(reg, r.xo)) {
+    const uint2 o = tia_write_cold(tx, E, reg, v, h, r.grp0, r.pos, r.cx);
+    r.xo = o.x;
+    r.cx = o.y;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kRasterFtWarps) k_raster_ft(const uint32_t* hdr, const uint32_t* log,
+                                                                     int32_t n_envs, int32_t ystart, uint8_t* screen,
+                                                                     unsigned long long* entries) {
+  __shared__ RasterFtSmem sm;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int env = blockIdx.x * kRasterFtWarps + w;
+  if (env >= n_envs) return;   // whole warps leave together
+  const uint32_t* h = hdr + (size_t)env * kRasterHdr;
+  const uint32_t n = h[0];
+  if (entries && lane == 0) atomicAdd(entries, (unsigned long long)n);
+  const int32_t start = (int32_t)h[1], end = (int32_t)h[2];
+  const uint32_t* lg = log + (size_t)env * kRasterLogCap;
+
+  // the walk: rows start with the state left by every write before their
+  // first colour clock (a write at exactly that clock belongs to the row)
+  Regs r{};
+  raster_restore(r, h[3], h[4], h[5] & 0xFFFF, 0xFFFFFFFFu);
+  r.hmp0 = (h[5] >> 16) & 0xFF;
+  uint32_t* tw = sm.walk[w];
+  if (lane == 0)
+    for (int k = 0; k < 4; k++) tw[k] = h[7 + k];
+  __syncwarp();
+  r.cx = 0;
+  r.xo = cold_summary_of(tw[0], tw[1], tw[2], 0).x;
+  uint32_t row = 0;
+  auto record = [&](uint32_t j) {
+    if (lane == 0) {
+      uint32_t* d = sm.row[w][row];
+      d[0] = (r.col0 & 0xFF) | ((r.colpf & 0xFF) << 8) | ((r.colbk & 0xFF) << 16) | ((r.ctrl & 0xFF) << 24);
+      d[1] = (r.pf0 & 0xFF) | ((r.pf1 & 0xFF) << 8) | ((r.pf2 & 0xFF) << 16) | ((r.grp0 & 0xFF) << 24);
+      d[2] = (r.pos & 0xFF) | ((r.vblank & 0xFF) << 8) | ((r.hmp0 & 0xFF) << 16);
+      d[3] = tw[0];
+      d[4] = tw[1];
+      d[5] = tw[2];
+      d[6] = tw[3];
+      d[7] = j;
+    }
+    row++;
+  };
+  for (uint32_t j0 = 0; j0 < n && row < (uint32_t)kScreenH; j0 += 32) {
+    const uint32_t mine = j0 + lane < n ? lg[j0 + lane] : 0u;
+    const uint32_t m = n - j0 < 32u ? n - j0 : 32u;
+    for (uint32_t k = 0; k < m && row < (uint32_t)kScreenH; k++) {
+      const uint32_t e = __shfl_sync(0xFFFFFFFFu, mine, (int)k);
+      const int32_t cc = 3 * (int32_t)(e >> 16);
+      while (row < (uint32_t)kScreenH && cc >= 228 * (ystart + (int32_t)row)) record(j0 + k);
+      __syncwarp();
+      raster_replay(r, tw, 1, e);   // every lane writes the same words
+      __syncwarp();
+    }
+  }
+  while (row < (uint32_t)kScreenH) record(n);
+  __syncwarp();
+
+  // each lane's rows, drawn with the general renderer on its own cold words
+  Ctx c{};
+  c.line = &sm.line[w][0][lane];
+  c.tx = &sm.tx[w][0][lane];
+  c.E = 32;
+  c.ft = 1;
+  c.rank = 0;
+  c.T = 1;
+  c.gmask = 1u << lane;
+  c.ystart = ystart;
+  Render rd{};
+  NoTape nt;
+  uint8_t* out = screen + (size_t)env * (kScreenH * kScreenW);
+  for (uint32_t rr = (uint32_t)lane; rr < (uint32_t)kScreenH; rr += 32) {
+    const uint32_t* sn = sm.row[w][rr];
+    raster_restore(r, sn[0], sn[1], sn[2] & 0xFFFF, 0xFFFFFFFFu);
+    r.hmp0 = (sn[2] >> 16) & 0xFF;
+    for (uint32_t k = 0; k < 4; k++) c.tx[k * 32] = sn[3 + k];
+    r.cx = 0;
+    r.xo = cold_summary_of(sn[3], sn[4], sn[5], 0).x;
+    const uint32_t j0 = sn[7], j1 = rr + 1 < (uint32_t)kScreenH ? sm.row[w][rr + 1][7] : n;
+    const int32_t line = ystart + (int32_t)rr, lbeg = 228 * line, lend = lbeg + 228;
+    int32_t cur = start > lbeg ? start : lbeg;
+    const int32_t stop = end < lend ? end : lend;
+    if (cur > lbeg + 68 || stop < lend) {
+#pragma unroll
+      for (uint32_t g = 0; g < 40; g++) c.line[g * 32] = 0u;
+    }
+    auto draw = [&](int32_t to) {
+      if (to > stop) to = stop;
+      if (to <= cur) return;
+      const int32_t h0 = cur - lbeg, h1 = to - lbeg;
+      const uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u, x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
+      if (x1 > x0) render_span(c, r, rd, nt, x0, x1, line);
+      cur = to;
+    };
+    for (uint32_t j = j0; j < j1; j++) {
+      const uint32_t e = lg[j];
+      draw(3 * (int32_t)(e >> 16));
+      raster_replay(r, c.tx, 32, e);
+    }
+    draw(stop);
+    uint4* dst = reinterpret_cast<uint4*>(out + rr * kScreenW);
+#pragma unroll
+    for (uint32_t q = 0; q < 10; q++)
+      dst[q] = make_uint4(c.line[(4 * q) * 32], c.line[(4 * q + 1) * 32], c.line[(4 * q + 2) * 32],
+                          c.line[(4 * q + 3) * 32]);
+  }
+}
+
+int launch_raster_ft(const uint32_t* hdr, const uint32_t* log, int32_t n_envs, int32_t ystart, uint8_t* screen,
+                     unsigned long long* entries, void* stream) {
+  if (n_envs <= 0) return 0;
+  const int blocks = (n_envs + kRasterFtWarps - 1) / kRasterFtWarps;
+  k_raster_ft<<<blocks, 32 * kRasterFtWarps, 0, (cudaStream_t)stream>>>(hdr, log, n_envs, ystart, screen, entries);
+  return (int)cudaGetLastError();
 }
 
 int launch_raster(const uint32_t* hdr, const uint32_t* log, int32_t n_envs, int32_t ystart, uint8_t* screen,

@@ -247,7 +247,7 @@ __device__ __forceinline__ void frame_end(const Ctx& c, Regs& r, Render& rd, Ste
   if (st.want_screen && st.frames_done == st.frame_skip - 1) {
     rd.on = true;
     rd.cur = 3 * (int32_t)r.fs;
-    if constexpr (kDefers<Tape>) raster_begin(r, rd, tape);
+    if constexpr (kDefers<Tape>) raster_begin(c, r, rd, tape);
   }
 }
 
@@ -282,7 +282,7 @@ __device__ __forceinline__ void run_frames(const Ctx& c, Regs& r, Render& rd, St
   rd.on = active && st.want_screen && st.frame_skip == 1;
   rd.cur = 3 * (int32_t)r.fs;
   if constexpr (kDefers<Tape>) {
-    if (rd.on) raster_begin(r, rd, tape);
+    if (rd.on) raster_begin(c, r, rd, tape);
   }
   uint32_t pf = prefetch(c, r);
   while (true) {

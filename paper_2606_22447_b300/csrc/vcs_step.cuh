@@ -49,8 +49,9 @@ __device__ __forceinline__ uint32_t round_byte(float v) {
 // checkpointed at the start of every segment of seg_steps steps.
 // XM: the batch holds Superchip or E0 carts (blocks of other carts run with
 // those features off all the same); FT: the whole TIA.  DR: deferred
-// rasterisation (hard mode, subset machine, one lane per env): the returned
-// frames go to the raster logs p.dr_log / p.dr_hdr, drawn by k_raster.
+// rasterisation (hard mode, one lane per env, no drawing code): the returned
+// frames go to the raster logs p.dr_log / p.dr_hdr, drawn by the raster
+// kernels; without screens nothing is logged.
 template <bool SOFT, int T, bool BOOT, bool INSTR, bool XM, bool FT, bool DR = false>
 __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -96,8 +97,8 @@ __global__ void __launch_bounds__(128, 1) k_run(StepParams p) {
 
   typename std::conditional<SOFT, CountTape, typename std::conditional<DR, DeferTape, NoTape>::type>::type tape;
   if constexpr (DR) {
-    tape.log = p.dr_log + (size_t)env * kRasterLogCap;
-    tape.hdr = p.dr_hdr + (size_t)env * kRasterHdr;
+    tape.log = p.dr_log ? p.dr_log + (size_t)env * kRasterLogCap : nullptr;   // null: no screens, nothing logged
+    tape.hdr = p.dr_hdr ? p.dr_hdr + (size_t)env * kRasterHdr : nullptr;
     tape.err = p.err;
     tape.n = 0;
   }
@@ -237,13 +238,13 @@ static void launch_kernel(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStr
 // The hard step kernel with deferred rasterisation: one lane per env,
 // whatever the batch's threads per env (the drawing they would share is the
 // raster kernel's).
-template <bool XM>
+template <bool XM, bool FT>
 static int launch_run_dr(const StepParams& p, int n_blocks, int E, void* stream) {
   if (n_blocks <= 0) return 0;
   const size_t smem = step_smem_bytes(E, p.rom_stride, p.ram_words);
   cudaStream_t s = (cudaStream_t)stream;
-  if (p.boot_frames) launch_kernel(k_run<false, 1, true, false, XM, false, true>, dim3(n_blocks), dim3(E), smem, s, p);
-  else launch_kernel(k_run<false, 1, false, false, XM, false, true>, dim3(n_blocks), dim3(E), smem, s, p);
+  if (p.boot_frames) launch_kernel(k_run<false, 1, true, false, XM, FT, true>, dim3(n_blocks), dim3(E), smem, s, p);
+  else launch_kernel(k_run<false, 1, false, false, XM, FT, true>, dim3(n_blocks), dim3(E), smem, s, p);
   return (int)cudaGetLastError();
 }
 

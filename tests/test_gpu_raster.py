@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_2606_22447_b300 import synth
 from tests.gpu_util import assert_env_equal, gpu_rollout, make_batch, oracle_rollout, torch_cuda
-from tests.microrom import brk_pushes_rom, dense_writes_rom
+from tests.microrom import brk_pushes_rom, dense_writes_rom, graphics_full_tia_rom
 
 pytestmark = pytest.mark.gpu
 
@@ -109,3 +109,59 @@ def test_graph_replay_with_deferred_raster():
         b.close()
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+FT_MAPPERS = [synth.MAPPER_2K, synth.MAPPER_4K, synth.MAPPER_F8, synth.MAPPER_F6, synth.MAPPER_F4,
+              synth.MAPPER_F8SC, synth.MAPPER_F6SC, synth.MAPPER_F4SC, synth.MAPPER_E0, synth.MAPPER_FE]
+
+
+@pytest.mark.parametrize("frame_skip", [1, 4])
+@pytest.mark.parametrize("epb", [16, 64])
+def test_whole_tia_deferred_equals_inline(frame_skip, epb):
+    """The whole TIA: carts of all ten formats that draw with every object
+    and read the collision latches; the raster kernel replays the logged
+    writes (delayed graphics, missile locks, HMOVE of every object) and
+    draws with the general renderer, bit for bit as the step kernel does."""
+    roms = synth.config_carts(1111, FT_MAPPERS, full_tia=True)
+    n = 90
+    env_cart = np.random.default_rng(11).permutation(np.arange(n) % len(FT_MAPPERS)).astype(np.int32)
+    acts = synth.actions(1111, n, 5)
+    (r0, s0, t0), (r1, s1, t1) = _pair(roms, FT_MAPPERS, env_cart, acts, frame_skip, envs_per_block=epb,
+                                       full_tia=1)
+    assert np.array_equal(r0, r1) and np.array_equal(t0, t1)
+    bad = np.argwhere(s0 != s1)
+    assert bad.size == 0, f"{len(bad)} pixels differ, first at {bad[0].tolist()}"
+
+
+@pytest.mark.parametrize("ctrlpf,vdel", [(0, False), (4, True), (2, True)])
+def test_whole_tia_deferred_matches_oracle(ctrlpf, vdel):
+    """Every object, vertical delay, playfield priority and score mode,
+    deferred, against the oracle's colour-clock renderer."""
+    rom, _ = graphics_full_tia_rom(ctrlpf=ctrlpf, vdel=vdel)
+    n = 6
+    acts = synth.actions(1212, n, 4)
+    b = make_batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32), full_tia=1)
+    ram, scr, st = gpu_rollout(b, acts, 2)
+    for e in range(n):
+        r2, s2, st2 = oracle_rollout(rom, synth.MAPPER_4K, acts[:, e], 2, full_tia=True)
+        assert_env_equal(e, ram[:, e], r2, "RAM")
+        assert_env_equal(e, scr[:, e], s2, "screen")
+        assert_env_equal(e, st[:, e], st2, "status")
+
+
+@pytest.mark.parametrize("full_tia", [0, 1])
+def test_steps_without_screens_equal_inline(full_tia):
+    """Without screens the step kernel built without drawing runs the whole
+    rollout in one launch; RAM and status equal the drawing kernel's."""
+    mappers = FT_MAPPERS if full_tia else MAPPERS
+    roms = synth.config_carts(1313, mappers, full_tia=bool(full_tia))
+    n = 70
+    env_cart = (np.arange(n) % len(mappers)).astype(np.int32)
+    acts = synth.actions(1313, n, 6)
+    out = []
+    for inline in (0, 1):
+        b = make_batch(roms, mappers, env_cart, inline_render=inline, full_tia=full_tia)
+        b.set_episodes(np.full((n, 2), 9, np.uint32))
+        out.append(gpu_rollout(b, acts, 3, screens=False))
+        b.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
