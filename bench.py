@@ -533,7 +533,11 @@ def gpu_arm(args):
                 "measured_source": "ncu smsp__issue_active (GPU-wide) and smsp__thread_inst_executed / "
                                    "(SMs x 128 lanes x max clock x this run's kernel time)",
                 "ops_per_env_step": ops / n,
-                "instructions_per_env_step": ipe}
+                "instructions_per_env_step": ipe,
+                # both kernels' modelled operations (instructions and pixels)
+                # over the whole step time, comparable with drawing inline
+                "whole_step_frac": n * (ipe * OPS_PER_INSTRUCTION + PIXELS_PER_STEP * OPS_PER_PIXEL) / mean_s
+                / peak_ops}
     raster = None
     if deferred:
         r_s = kt["raster_ms"] / 1e3 / kt["launches"]
@@ -564,7 +568,7 @@ def gpu_arm(args):
     full_tia = None
     if not args.no_mixed:
         mixed = mixed_leg(args.mixed_envs, 8, 5)
-        full_tia = mixed_leg(16384, 8, 3, full_tia=True)
+        full_tia = mixed_leg(args.full_tia_envs, 8, 3, full_tia=True)
     instr = None
     if not args.no_instr:
         instr = instr_leg([1, 64, 256, 1024, 4096, 16384, 65536])
@@ -612,6 +616,7 @@ def main():
     ap.add_argument("--no-soft", action="store_true", help="skip the SOFT-STE fwd+bwd legs")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 65,536-env mixed-cartridge leg")
     ap.add_argument("--mixed-envs", type=int, default=65536)
+    ap.add_argument("--full-tia-envs", type=int, default=16384, help="envs of the full-TIA leg")
     ap.add_argument("--no-full", action="store_true",
                     help="skip the fully relaxed forward's bit-exactness grid")
     ap.add_argument("--no-instr", action="store_true",
