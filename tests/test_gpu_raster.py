@@ -165,3 +165,4 @@ def test_steps_without_screens_equal_inline(full_tia):
         out.append(gpu_rollout(b, acts, 3, screens=False))
         b.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
+
