@@ -832,16 +832,22 @@ vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const
     actions = noop;
   }
   int32_t trials = 0;
-  // one timed trial of the batch's current geometry; the state is restored after it
+  // one trial of the batch's current geometry: a warm-up rollout, then the
+  // faster of two timed ones, the state restored before each and after
   auto trial = [&](float* ms) -> vcs_status {
     vcs_status st;
     if ((st = vcs_rollout(b, actions, n_steps, frame_skip, ram_out, screen_out, nullptr, stream)) != VCS_OK) return st;
+    *ms = 1e30f;
+    for (int rep = 0; rep < 2; rep++) {
+      float t = 0.f;
+      if ((e = cudaMemcpyAsync(b->state, saved, nst, cudaMemcpyDeviceToDevice, s))) return vcs_cuda_fail(b, e, "autotune");
+      if ((e = cudaEventRecord(e0, s))) return vcs_cuda_fail(b, e, "autotune");
+      if ((st = vcs_rollout(b, actions, n_steps, frame_skip, ram_out, screen_out, nullptr, stream)) != VCS_OK) return st;
+      if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) || (e = cudaEventElapsedTime(&t, e0, e1)))
+        return vcs_cuda_fail(b, e, "autotune");
+      *ms = t < *ms ? t : *ms;
+    }
     if ((e = cudaMemcpyAsync(b->state, saved, nst, cudaMemcpyDeviceToDevice, s))) return vcs_cuda_fail(b, e, "autotune");
-    if ((e = cudaEventRecord(e0, s))) return vcs_cuda_fail(b, e, "autotune");
-    if ((st = vcs_rollout(b, actions, n_steps, frame_skip, ram_out, screen_out, nullptr, stream)) != VCS_OK) return st;
-    if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) || (e = cudaEventElapsedTime(ms, e0, e1)) ||
-        (e = cudaMemcpyAsync(b->state, saved, nst, cudaMemcpyDeviceToDevice, s)))
-      return vcs_cuda_fail(b, e, "autotune");
     trials++;
     return VCS_OK;
   };
@@ -852,10 +858,13 @@ vcs_status vcs_autotune(vcs_batch* b, int32_t frame_skip, int32_t n_steps, const
   b->steps_per_launch = 0;
   int bestE = b->E, bestT = b->tpe;
   const int cand_e[5] = {8, 16, 32, 64, 128};
+  // hard frame steps run the step kernel without drawing, one lane per env
+  // (deferred rasterisation), so replicas are not tried for them
+  const int maxT = (b->cfg.inline_render == 0 && b->cfg.step_instructions <= 0) ? 1 : 4;
   for (int E : cand_e) {
     if (E > 8 && (int)((n + E / 2 - 1) / (E / 2)) <= 1) break;   // no larger block helps a tiny batch
     if ((st = set_geometry(b, E)) != VCS_OK) break;
-    for (int T = 1; st == VCS_OK && valid_tpe(E, T) && T <= 4; T *= 2) {
+    for (int T = 1; st == VCS_OK && valid_tpe(E, T) && T <= maxT; T *= 2) {
       b->tpe = T;
       if ((st = trial(&ms)) != VCS_OK) break;
       if (ms < best) { best = ms; bestE = E; bestT = T; }
