@@ -94,6 +94,9 @@ def test_argument_errors_before_device_work(lib):
     tape = C.c_void_p()
     assert lib.vcs_soft_step(None, 0.1, None, 1, 1, None, None, C.byref(tape), None) == _lib.VCS_ERR_ARG
     assert lib.vcs_destroy(None) == _lib.VCS_ERR_ARG
+    assert lib.vcs_time_kernels(None, 1) == _lib.VCS_ERR_ARG
+    f, i, d = C.c_float(), C.c_int32(), C.c_double()
+    assert lib.vcs_kernel_times(None, C.byref(f), C.byref(f), C.byref(i), C.byref(d)) == _lib.VCS_ERR_ARG
 
 
 def test_detect_mapper(lib):
