@@ -172,15 +172,18 @@ __global__ void __launch_bounds__(32 * kRasterWarps) k_raster(const uint32_t* hd
 // walk replays them in order with the interpreter's own functions (tia_hot,
 // tia_write_cold) rather than by ballots: every lane of the warp replays the
 // same writes on the same registers (the entries fetched 32 at a time and
-// broadcast), lane 0 records each row's starting state (the hot words, HMP0
-// and the four cold words, 32 bytes), and then each lane draws its rows,
-// replaying the row's writes on its own copy of the cold words.
+// broadcast).  Rows go in groups of 32: the walk runs to the start of the
+// group's last row, lane l keeping row 32 g + l's starting state (the
+// drawing registers, HMP0, the four cold words, its first entry) in its own
+// registers as the walk passes it, and then every lane draws its row,
+// replaying the row's writes on its own copy of the cold words, before the
+// walk goes on.  Keeping the rows' states in registers leaves 5.8 KB of
+// shared memory per warp (36 warps an SM).
 // ---------------------------------------------------------------------------
-constexpr int kRasterFtWarps = 2;   // envs per block
+constexpr int kRasterFtWarps = 4;   // envs per block
 
 struct RasterFtSmem {
   uint32_t line[kRasterFtWarps][40][32];      // line buffers: word g of lane l at [g][l]
-  uint32_t row[kRasterFtWarps][kScreenH][8];  // hot words 3..5 (| HMP0 << 16), w0..w3, first entry
   uint32_t tx[kRasterFtWarps][6][32];         // each lane's cold words (stride 32)
   uint32_t walk[kRasterFtWarps][6];           // the walk's cold words (stride 1)
 };
@@ -198,7 +201,7 @@ __device__ __forceinline__ void raster_replay(Regs& r, uint32_t* tx, uint32_t E,
   }
 }
 
-__global__ void __launch_bounds__(32 * kRasterFtWarps) k_raster_ft(const uint32_t* hdr, const uint32_t* log,
+__global__ void __launch_bounds__(32 * kRasterFtWarps, 8) k_raster_ft(const uint32_t* hdr, const uint32_t* log,
                                                                      int32_t n_envs, int32_t ystart, uint8_t* screen,
                                                                      unsigned long long* entries) {
   __shared__ RasterFtSmem sm;
@@ -211,8 +214,8 @@ __global__ void __launch_bounds__(32 * kRasterFtWarps) k_raster_ft(const uint32_
   const int32_t start = (int32_t)h[1], end = (int32_t)h[2];
   const uint32_t* lg = log + (size_t)env * kRasterLogCap;
 
-  // the walk: rows start with the state left by every write before their
-  // first colour clock (a write at exactly that clock belongs to the row)
+  // the walk's state: rows start with the state left by every write before
+  // their first colour clock (a write at exactly that clock belongs to the row)
   Regs r{};
   raster_restore(r, h[3], h[4], h[5] & 0xFFFF, 0xFFFFFFFFu);
   r.hmp0 = (h[5] >> 16) & 0xFF;
@@ -222,37 +225,7 @@ __global__ void __launch_bounds__(32 * kRasterFtWarps) k_raster_ft(const uint32_
   __syncwarp();
   r.cx = 0;
   r.xo = cold_summary_of(tw[0], tw[1], tw[2], 0).x;
-  uint32_t row = 0;
-  auto record = [&](uint32_t j) {
-    if (lane == 0) {
-      uint32_t* d = sm.row[w][row];
-      d[0] = (r.col0 & 0xFF) | ((r.colpf & 0xFF) << 8) | ((r.colbk & 0xFF) << 16) | ((r.ctrl & 0xFF) << 24);
-      d[1] = (r.pf0 & 0xFF) | ((r.pf1 & 0xFF) << 8) | ((r.pf2 & 0xFF) << 16) | ((r.grp0 & 0xFF) << 24);
-      d[2] = (r.pos & 0xFF) | ((r.vblank & 0xFF) << 8) | ((r.hmp0 & 0xFF) << 16);
-      d[3] = tw[0];
-      d[4] = tw[1];
-      d[5] = tw[2];
-      d[6] = tw[3];
-      d[7] = j;
-    }
-    row++;
-  };
-  for (uint32_t j0 = 0; j0 < n && row < (uint32_t)kScreenH; j0 += 32) {
-    const uint32_t mine = j0 + lane < n ? lg[j0 + lane] : 0u;
-    const uint32_t m = n - j0 < 32u ? n - j0 : 32u;
-    for (uint32_t k = 0; k < m && row < (uint32_t)kScreenH; k++) {
-      const uint32_t e = __shfl_sync(0xFFFFFFFFu, mine, (int)k);
-      const int32_t cc = 3 * (int32_t)(e >> 16);
-      while (row < (uint32_t)kScreenH && cc >= 228 * (ystart + (int32_t)row)) record(j0 + k);
-      __syncwarp();
-      raster_replay(r, tw, 1, e);   // every lane writes the same words
-      __syncwarp();
-    }
-  }
-  while (row < (uint32_t)kScreenH) record(n);
-  __syncwarp();
 
-  // each lane's rows, drawn with the general renderer on its own cold words
   Ctx c{};
   c.line = &sm.line[w][0][lane];
   c.tx = &sm.tx[w][0][lane];
@@ -265,40 +238,85 @@ __global__ void __launch_bounds__(32 * kRasterFtWarps) k_raster_ft(const uint32_
   Render rd{};
   NoTape nt;
   uint8_t* out = screen + (size_t)env * (kScreenH * kScreenW);
-  for (uint32_t rr = (uint32_t)lane; rr < (uint32_t)kScreenH; rr += 32) {
-    const uint32_t* sn = sm.row[w][rr];
-    raster_restore(r, sn[0], sn[1], sn[2] & 0xFFFF, 0xFFFFFFFFu);
-    r.hmp0 = (sn[2] >> 16) & 0xFF;
-    for (uint32_t k = 0; k < 4; k++) c.tx[k * 32] = sn[3 + k];
-    r.cx = 0;
-    r.xo = cold_summary_of(sn[3], sn[4], sn[5], 0).x;
-    const uint32_t j0 = sn[7], j1 = rr + 1 < (uint32_t)kScreenH ? sm.row[w][rr + 1][7] : n;
-    const int32_t line = ystart + (int32_t)rr, lbeg = 228 * line, lend = lbeg + 228;
-    int32_t cur = start > lbeg ? start : lbeg;
-    const int32_t stop = end < lend ? end : lend;
-    if (cur > lbeg + 68 || stop < lend) {
-#pragma unroll
-      for (uint32_t g = 0; g < 40; g++) c.line[g * 32] = 0u;
+
+  uint32_t row = 0, j = 0, j0 = 0xFFFFFFFFu, mine = 0;
+  uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0, sfirst = 0;   // this lane's row's start
+  auto record = [&]() {   // the walk's state opens row `row`
+    if ((uint32_t)lane == (row & 31u)) {
+      s0 = (r.col0 & 0xFF) | ((r.colpf & 0xFF) << 8) | ((r.colbk & 0xFF) << 16) | ((r.ctrl & 0xFF) << 24);
+      s1 = (r.pf0 & 0xFF) | ((r.pf1 & 0xFF) << 8) | ((r.pf2 & 0xFF) << 16) | ((r.grp0 & 0xFF) << 24);
+      s2 = (r.pos & 0xFF) | ((r.vblank & 0xFF) << 8) | ((r.hmp0 & 0xFF) << 16);
+      s3 = tw[0];
+      s4 = tw[1];
+      s5 = tw[2];
+      s6 = tw[3];
+      sfirst = j;
     }
-    auto draw = [&](int32_t to) {
-      if (to > stop) to = stop;
-      if (to <= cur) return;
-      const int32_t h0 = cur - lbeg, h1 = to - lbeg;
-      const uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u, x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
-      if (x1 > x0) render_span(c, r, rd, nt, x0, x1, line);
-      cur = to;
-    };
-    for (uint32_t j = j0; j < j1; j++) {
-      const uint32_t e = lg[j];
-      draw(3 * (int32_t)(e >> 16));
-      raster_replay(r, c.tx, 32, e);
+    row++;
+  };
+  for (uint32_t g0 = 0; g0 < (uint32_t)kScreenH; g0 += 32) {
+    const uint32_t gend = g0 + 32 < (uint32_t)kScreenH ? g0 + 32 : (uint32_t)kScreenH;
+    // walk to the start of the group's last row
+    while (row < gend) {
+      if (j >= n) {
+        record();
+        continue;
+      }
+      if ((j & ~31u) != j0) {   // the next 32 entries, one a lane
+        j0 = j & ~31u;
+        mine = j0 + lane < n ? lg[j0 + lane] : 0u;
+      }
+      const uint32_t e = __shfl_sync(0xFFFFFFFFu, mine, (int)(j & 31u));
+      const int32_t cc = 3 * (int32_t)(e >> 16);
+      while (row < gend && cc >= 228 * (ystart + (int32_t)row)) record();
+      if (row >= gend) break;   // entry j belongs to a later row: the walk resumes there
+      __syncwarp();
+      raster_replay(r, tw, 1, e);   // every lane writes the same words
+      __syncwarp();
+      j++;
     }
-    draw(stop);
-    uint4* dst = reinterpret_cast<uint4*>(out + rr * kScreenW);
+    // draw row g0 + lane from its start, through its entries
+    const uint32_t rr = g0 + (uint32_t)lane;
+    if (rr < gend) {
+      Regs q{};
+      raster_restore(q, s0, s1, s2 & 0xFFFF, 0xFFFFFFFFu);
+      q.hmp0 = (s2 >> 16) & 0xFF;
+      c.tx[0] = s3;
+      c.tx[32] = s4;
+      c.tx[64] = s5;
+      c.tx[96] = s6;
+      q.cx = 0;
+      q.xo = cold_summary_of(s3, s4, s5, 0).x;
+      const int32_t line = ystart + (int32_t)rr, lbeg = 228 * line, lend = lbeg + 228;
+      int32_t cur = start > lbeg ? start : lbeg;
+      const int32_t stop = end < lend ? end : lend;
+      if (cur > lbeg + 68 || stop < lend) {
 #pragma unroll
-    for (uint32_t q = 0; q < 10; q++)
-      dst[q] = make_uint4(c.line[(4 * q) * 32], c.line[(4 * q + 1) * 32], c.line[(4 * q + 2) * 32],
-                          c.line[(4 * q + 3) * 32]);
+        for (uint32_t g = 0; g < 40; g++) c.line[g * 32] = 0u;
+      }
+      auto draw = [&](int32_t to) {
+        if (to > stop) to = stop;
+        if (to <= cur) return;
+        const int32_t h0 = cur - lbeg, h1 = to - lbeg;
+        const uint32_t x0 = (uint32_t)(h0 > 68 ? h0 : 68) - 68u, x1 = (uint32_t)(h1 > 68 ? h1 : 68) - 68u;
+        if (x1 > x0) render_span(c, q, rd, nt, x0, x1, line);
+        cur = to;
+      };
+      for (uint32_t k = sfirst; k < n; k++) {   // the row's entries: up to the next row's first clock
+        const uint32_t e = lg[k];
+        const int32_t cc = 3 * (int32_t)(e >> 16);
+        if (cc >= lend) break;
+        draw(cc);
+        raster_replay(q, c.tx, 32, e);
+      }
+      draw(stop);
+      uint4* dst = reinterpret_cast<uint4*>(out + rr * kScreenW);
+#pragma unroll
+      for (uint32_t qq = 0; qq < 10; qq++)
+        dst[qq] = make_uint4(c.line[(4 * qq) * 32], c.line[(4 * qq + 1) * 32], c.line[(4 * qq + 2) * 32],
+                             c.line[(4 * qq + 3) * 32]);
+    }
+    __syncwarp();
   }
 }
 
