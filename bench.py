@@ -523,6 +523,9 @@ def gpu_arm(args):
                 else n * (PIXELS_PER_STEP + 128 + 1),
                 "kernel_ms": k_s * 1e3, "kernel_timing": "CUDA events around the step kernel on its stream, "
                                                          "every timed step",
+                "traffic_note": ("DRAM sees the state and the actions; the RAM rows and the raster logs stay in "
+                                 "the 126 MB L2, where the raster kernel reads the logs") if deferred else
+                                "below the algorithmic bytes: part of the screens is still in L2 when the kernel ends",
                 "peak_source": "measured: vcs_int_peak, independent 32-bit add/shift/logic chains at full "
                                "occupancy (best of 3)",
                 "peak_derived": derived_ops / 1e12,
