@@ -166,3 +166,27 @@ def test_steps_without_screens_equal_inline(full_tia):
         b.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
 
+
+
+def test_kernel_timing_counts_the_two_kernels():
+    """vcs_time_kernels / vcs_kernel_times: every timed step records the step
+    kernel and the raster kernel, and the raster kernel counts the log
+    entries it drew (one per picture-register write of the returned frame)."""
+    torch = torch_cuda()
+    rom = synth.generate_cart(2, 0, synth.MAPPER_4K)
+    n = 64
+    b = make_batch([rom], [synth.MAPPER_4K], np.zeros(n, np.int32))
+    acts = torch.from_numpy(synth.actions(2, n, 3)).cuda()
+    ram = torch.empty((n, 128), dtype=torch.uint8, device="cuda")
+    scr = torch.empty((n, 210, 160), dtype=torch.uint8, device="cuda")
+    b.step(acts[0], 4, ram, scr)
+    b.time_kernels(True)
+    for t in (1, 2):
+        b.step(acts[t], 4, ram, scr)
+    kt = b.kernel_times()
+    b.time_kernels(False)
+    assert kt["launches"] == 2 and kt["step_ms"] > 0 and kt["raster_ms"] > 0
+    assert kt["log_entries"] > 100 * 2 * n   # a few hundred picture writes per env and frame
+    assert b.kernel_times()["launches"] == 0   # reading clears the sums
+    b.sync()
+    b.close()
