@@ -186,9 +186,10 @@ typedef struct vcs_config {
                                kernel draws all scanlines of all envs in
                                parallel from the logs, one step per launch;
                                the logs hold 67 KB per env, made at the first
-                               such step.  1 = the step kernel draws the
-                               frame itself as it runs.  Screens are the same
-                               either way. */
+                               such step (if the device cannot hold them the
+                               batch switches to 1).  1 = the step kernel
+                               draws the frame itself as it runs.  Screens
+                               are the same either way. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

@@ -161,7 +161,9 @@ static bool raster_applies(const vcs_batch* b, const StepParams& p) {
 }
 
 // The logs take kRasterLogCap entries per env (67 KB, the most picture-
-// register writes a frame can make: the log never fills).
+// register writes a frame can make: the log never fills).  If the device
+// cannot hold them the batch draws in the step kernel from then on
+// (inline_render = 1), which needs no logs: screens are the same.
 static vcs_status ensure_raster(vcs_batch* b) {
   if (b->dr_log) return VCS_OK;
   const size_t n = (size_t)b->n_envs;
@@ -171,6 +173,11 @@ static vcs_status ensure_raster(vcs_batch* b) {
     cudaFree(b->dr_log);
     b->dr_log = nullptr;
     b->dr_hdr = nullptr;
+    if (e == cudaErrorMemoryAllocation) {
+      (void)cudaGetLastError();   // the failed allocation leaves no sticky error
+      b->cfg.inline_render = 1;
+      return VCS_OK;
+    }
     return vcs_cuda_fail(b, e, "raster logs");
   }
   return VCS_OK;
@@ -213,6 +220,8 @@ static vcs_status launch(vcs_batch* b, StepParams& p, void* stream) {
   if (raster_applies(b, p) && p.screen_out) {
     vcs_status st = ensure_raster(b);
     if (st != VCS_OK) return st;
+  }
+  if (raster_applies(b, p) && p.screen_out) {   // still deferring: the logs are there
     const size_t n = (size_t)b->n_envs;
     for (int32_t t = 0; t < p.n_steps; t++) {
       StepParams q = p;
