@@ -190,6 +190,13 @@ typedef struct vcs_config {
                                batch switches to 1).  1 = the step kernel
                                draws the frame itself as it runs.  Screens
                                are the same either way. */
+  int32_t sweep_mode;       /* the soft backward's reverse sweep: 1 = one
+                               env per warp (its lane 0 walks the tape, the
+                               warp stages records and adds ROM impulses),
+                               2 = one env per lane (32 envs a warp, each
+                               lane walking its own tape), 0 (default) =
+                               2 from 8192 envs, else 1.  Gradients are the
+                               same bits either way. */
 } vcs_config;
 
 typedef struct vcs_batch vcs_batch;

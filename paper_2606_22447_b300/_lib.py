@@ -36,7 +36,8 @@ class Config(C.Structure):
                 ("sched_policy", C.c_int32), ("sched_window", C.c_int32), ("steps_per_launch", C.c_int32),
                 ("threads_per_env", C.c_int32), ("position_sampler", C.c_int32),
                 ("step_instructions", C.c_int32), ("tape_budget_mb", C.c_int32), ("full_tia", C.c_int32),
-                ("graphics_bits", C.c_int32), ("inline_render", C.c_int32)]
+                ("graphics_bits", C.c_int32), ("inline_render", C.c_int32),
+                ("sweep_mode", C.c_int32)]
 
 
 class Tune(C.Structure):

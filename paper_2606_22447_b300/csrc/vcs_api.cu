@@ -317,6 +317,7 @@ vcs_status vcs_config_default(vcs_config* cfg) {
   cfg->full_tia = 0;
   cfg->graphics_bits = 0;
   cfg->inline_render = 0;
+  cfg->sweep_mode = 0;
   return VCS_OK;
 }
 
@@ -430,6 +431,10 @@ vcs_status vcs_create_batch(const uint8_t* const* roms, const uint32_t* rom_size
   if (b->cfg.inline_render < 0 || b->cfg.inline_render > 1) {
     free_batch(b);
     return vcs_fail(nullptr, VCS_ERR_ARG, "inline_render must be 0 or 1");
+  }
+  if (b->cfg.sweep_mode < 0 || b->cfg.sweep_mode > 2) {
+    free_batch(b);
+    return vcs_fail(nullptr, VCS_ERR_ARG, "sweep_mode must be 0, 1 or 2");
   }
   b->n_envs = n_envs;
   b->n_carts = n_carts;

@@ -226,6 +226,7 @@ struct BwdParams {
   int32_t sampler;            // the position sampler is on
   int32_t graphics;           // the graphics-bit surrogate is on
   int32_t step_instr;         // > 0: instruction-granular steps of this many slots
+  int32_t sweep_lanes;        // the reverse sweep walks one env per lane (k_soft_sweep_lanes)
   int32_t* err;
 };
 
@@ -269,6 +270,24 @@ struct RomQueue {
   uint32_t* idx;
   float* g;
   uint32_t n;
+  __device__ __forceinline__ void push(uint32_t i, float v) {
+    idx[n] = i;
+    g[n] = v;
+    n++;
+  }
+};
+// The same queue for a sweep that walks one env per lane: lane l's entry e
+// sits at e * 32 + l (consecutive lanes in consecutive banks), and the lane
+// adds its own impulses.
+struct LaneQueue {
+  uint32_t* idx;
+  float* g;
+  uint32_t n;
+  __device__ __forceinline__ void push(uint32_t i, float v) {
+    idx[n * 32] = i;
+    g[n * 32] = v;
+    n++;
+  }
 };
 
 // Cart kind bits of the sweep: the 2K image (ROM index within 2 KB), the
@@ -311,9 +330,9 @@ __device__ __forceinline__ void spread_ram(float* aram, float* aramc, uint32_t E
 // terms of both signs into them.
 // XM: the sweep's batch may hold Superchip or E0 carts (their ports and
 // slices are compiled out otherwise).
-template <bool XM>
+template <bool XM, class Q>
 __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                             const float* izr, int W, RomQueue& rq,
+                                             const float* izr, int W, Q& rq,
                                              uint32_t kind, uint32_t ref, uint32_t fl, const Acc& ga) {
   const uint32_t ad = ref & 0x1FFF;
   if (ga.zero()) return;
@@ -322,10 +341,8 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
     spread_ram(aram, aramc, E, ek, izr, W, 128, (int)(ad & 0x7F), ga);
   } else if (ad & 0x1000) {
     const uint32_t unit = (fl >> 2) & 7u;   // the read's bank (E0: slice)
-    rq.idx[rq.n] = (kind & kKind2K) ? (ad & 0x7FF)
-                   : (XM && (kind & kKindE0)) ? ((unit << 10) | (ad & 0x3FF)) : ((unit << 12) | (ad & 0xFFF));
-    rq.g[rq.n] = g;
-    rq.n++;
+    rq.push((kind & kKind2K) ? (ad & 0x7FF)
+            : (XM && (kind & kKindE0)) ? ((unit << 10) | (ad & 0x3FF)) : ((unit << 12) | (ad & 0xFFF)), g);
   } else if (!(ad & 0x80)) {
     if ((ad & 0xF) == 0xC) comp_add(a.u[4], a.uc[4], -128.f * g);
   } else if (!(ad & 0x200)) {
@@ -433,9 +450,9 @@ __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uin
 
 __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
 
-template <bool SAMPLER, bool GB, bool XM>
+template <bool SAMPLER, bool GB, bool XM, class Q>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
-                                            const float* izr, int W, RomQueue& rq,
+                                            const float* izr, int W, Q& rq,
                                             uint32_t kind, const float* cw, uint32_t& j, uint32_t rec) {
   const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
   switch (op) {
@@ -818,6 +835,159 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   }
 }
 
+// The reverse sweep with one env per lane (32 envs a block of one warp):
+// each lane walks its own env's tape with the same per-record arithmetic as
+// k_soft_sweep and adds its own ROM impulses, so every env's sums take the
+// same terms in the same order and the gradients are the same bits.  Lanes
+// of a warp whose next records are of one kind share the instructions; for
+// batches of more envs than one wave of k_soft_sweep's warps, where that
+// kernel's issue slots go to its single walking lane, this is the faster.
+constexpr int kLaneQ = 8;   // ROM impulses a lane queues before adding them
+__host__ __device__ constexpr size_t swl_smem_bytes(int cells) {
+  return ((size_t)2 * cells * 32 + (kMaxW + 1 + 256) + (size_t)2 * kLaneQ * 32) * 4;
+}
+
+template <bool SAMPLER, bool GB, bool XM>
+__global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr int E = 32;
+  constexpr int cells = XM ? kSweepCells : 128;   // adjoint cells the sweep keeps
+  const int lane = threadIdx.x;
+  float* aram_s = reinterpret_cast<float*>(smem);   // [cells][32]
+  float* aramc_s = aram_s + cells * E;              // [cells][32] compensation
+  float* ek = aramc_s + cells * E;                  // [kMaxW + 1]
+  float* izr = ek + (kMaxW + 1);                    // [256]
+  uint32_t* q_idx = reinterpret_cast<uint32_t*>(izr + 256);   // [kLaneQ][32]
+  float* q_g = reinterpret_cast<float*>(q_idx + kLaneQ * 32);  // [kLaneQ][32]
+  read_tables(ek, izr, p.tau, p.W);
+  const int env = blockIdx.x * E + lane;
+  if (env >= p.n_envs) return;
+  const uint32_t cart = (uint32_t)p.env_cart[env];
+  const uint32_t kind = (p.cart_2k[cart] ? kKind2K : 0u) | (XM && cart_is_sc(p.cart_banks[cart]) ? kKindSC : 0u) |
+                        (XM && cart_is_e0(p.cart_banks[cart]) ? kKindE0 : 0u);
+  const int n = p.n_envs, g = p.seg - p.seg0;
+  const float* m = p.meta + ((size_t)g * n + env) * kMeta;
+  if (m[1] != 0.f) return;   // overflow: the error word is set
+  float* aram = aram_s + lane;
+  float* aramc = aramc_s + lane;
+  LaneQueue rq{q_idx + lane, q_g + lane, 0u};
+  Adj a;
+  a.ft = p.full_tia != 0;
+  if (p.first) {
+    a.A = a.X = a.Y = a.V = a.C0 = a.C1 = a.C2 = a.C3 = acc(0.f);
+#pragma unroll
+    for (int k = 0; k < kGbN; k++) a.G[k] = acc(0.f);
+    a.P = a.H = 0.f;
+    for (int i = 0; i < cells; i++) aram[i * E] = 0.f;
+    for (int i = 0; i < cells; i++) aramc[i * E] = 0.f;
+  } else {
+    const float* cr = p.carry;
+    a.A = acc(cr[0 * n + env]); a.X = acc(cr[1 * n + env]); a.Y = acc(cr[2 * n + env]);
+    a.V = acc(cr[3 * n + env]);
+    a.C0 = acc(cr[4 * n + env]); a.C1 = acc(cr[5 * n + env]); a.C2 = acc(cr[6 * n + env]);
+    a.C3 = acc(cr[(size_t)kCarryC3 * n + env]);
+#pragma unroll
+    for (int k = 0; k < kGbN; k++) a.G[k] = acc(GB ? cr[(size_t)(kCarryGB + k) * n + env] : 0.f);
+    a.P = SAMPLER ? cr[(size_t)kCarryPos * n + env] : 0.f;
+    a.H = SAMPLER ? cr[(size_t)(kCarryPos + 1) * n + env] : 0.f;
+    for (int i = 0; i < 128; i++) aram[i * E] = cr[(size_t)(7 + i) * n + env];
+    for (int i = 0; i < 128; i++) aramc[i * E] = cr[(size_t)(7 + 128 + i) * n + env];
+    if constexpr (XM) {
+      for (int i = 0; i < 128; i++) {
+        aram[(128 + i) * E] = (kind & kKindSC) ? cr[(size_t)(kCarryCram + i) * n + env] : 0.f;
+        aramc[(128 + i) * E] = (kind & kKindSC) ? cr[(size_t)(kCarryCram + 128 + i) * n + env] : 0.f;
+      }
+    }
+  }
+  float2* imp = reinterpret_cast<float2*>(p.imp) + (size_t)env * p.rom_stride;
+  auto flush = [&]() {   // the queued impulses, in queue order
+    for (uint32_t e = 0; e < rq.n; e++) {
+      const uint32_t ix = rq.idx[e * 32];
+      float2 w = imp[ix];
+      comp_add(w.x, w.y, rq.g[e * 32]);
+      imp[ix] = w;
+    }
+    rq.n = 0;
+  };
+  const uint4* rec4 = reinterpret_cast<const uint4*>(p.rec + ((size_t)g * n + env) * p.cap_rec);
+  const float* cw = p.cw + ((size_t)g * n + env) * p.cap_cw;
+  const uint32_t* step_end = p.step_end + (size_t)g * p.seg_steps * n;
+  uint32_t j = __float_as_uint(m[0]);
+  const int t0 = p.seg * p.seg_steps;
+  const int t1 = min(t0 + p.seg_steps, p.n_steps);
+  // records are read backwards four at a time (16-byte tape rows), the
+  // chunk below the current one in flight
+  uint4 cur = make_uint4(0u, 0u, 0u, 0u), nxt = cur;
+  uint32_t cc = 0xFFFFFFFFu;   // chunk held in cur
+  for (int t = t1 - 1; t >= t0; t--) {
+    const float* gr = p.grad_ram ? p.grad_ram + ((size_t)t * n + env) * 128 : p.w_ram;
+    if (gr)
+      for (int i = 0; i < 128; i++) comp_add(aram[i * E], aramc[i * E], gr[i]);
+    for (int q = 0; q < 5; q++) a.u[q] = a.uc[q] = 0.f;
+    const uint32_t k_end = step_end[(size_t)(t - t0) * n + env];
+    const uint32_t k_beg = t > t0 ? step_end[(size_t)(t - 1 - t0) * n + env] : 0u;
+    for (uint32_t k = k_end; k > k_beg; k--) {
+      const uint32_t c = (k - 1) >> 2;
+      if (c != cc) {
+        cur = c + 1 == cc ? nxt : __ldcs(rec4 + c);
+        nxt = c > 0 ? __ldcs(rec4 + c - 1) : make_uint4(0u, 0u, 0u, 0u);
+        cc = c;
+      }
+      const uint32_t w = (k - 1) & 3;
+      const uint32_t r = w == 0 ? cur.x : w == 1 ? cur.y : w == 2 ? cur.z : cur.w;
+      reverse_one<SAMPLER, GB, XM>(a, aram, aramc, E, ek, izr, p.W, rq, kind, cw, j, r);
+      if (rq.n == kLaneQ) flush();
+    }
+    if (p.grad_u) {
+      float* gu = p.grad_u + ((size_t)t * n + env) * 5;
+      for (int q = 0; q < 5; q++) gu[q] = a.u[q] + a.uc[q];
+    }
+  }
+  flush();
+  // versions alive at the segment start continue into the previous segment
+  a.C0 += m[2];
+  a.C1 += m[3];
+  a.C2 += m[4];
+  a.C3 += m[6];
+  if constexpr (SAMPLER) a.P += m[5];
+  if constexpr (GB) {
+#pragma unroll
+    for (int k = 0; k < kGbN; k++) a.G[k] += m[7 + k];
+  }
+  if (p.seg == 0) {
+    if (p.grad_ram0)
+      for (int i = 0; i < 128; i++) p.grad_ram0[(size_t)env * 128 + i] = aram[i * E] + aramc[i * E];
+    if (p.grad_cart_ram0)
+      for (int i = 0; i < 128; i++)
+        p.grad_cart_ram0[(size_t)env * 128 + i] = XM ? aram[(128 + i) * E] + aramc[(128 + i) * E] : 0.f;
+  } else {
+    float* cr = p.carry;
+    cr[0 * n + env] = a.A.v(); cr[1 * n + env] = a.X.v(); cr[2 * n + env] = a.Y.v(); cr[3 * n + env] = a.V.v();
+    cr[4 * n + env] = a.C0.v(); cr[5 * n + env] = a.C1.v(); cr[6 * n + env] = a.C2.v();
+    cr[(size_t)kCarryC3 * n + env] = a.C3.v();
+    if constexpr (GB) {
+#pragma unroll
+      for (int k = 0; k < kGbN; k++) cr[(size_t)(kCarryGB + k) * n + env] = a.G[k].v();
+    }
+    cr[(size_t)kCarryPos * n + env] = a.P; cr[(size_t)(kCarryPos + 1) * n + env] = a.H;
+    for (int i = 0; i < 128; i++) cr[(size_t)(7 + i) * n + env] = aram[i * E];
+    for (int i = 0; i < 128; i++) cr[(size_t)(7 + 128 + i) * n + env] = aramc[i * E];
+    if (XM && (kind & kKindSC)) {
+      for (int i = 0; i < 128; i++) cr[(size_t)(kCarryCram + i) * n + env] = aram[(128 + i) * E];
+      for (int i = 0; i < 128; i++) cr[(size_t)(kCarryCram + 128 + i) * n + env] = aramc[(128 + i) * E];
+    }
+  }
+}
+
+// Which sweep a batch runs (vcs_config.sweep_mode): 1 = k_soft_sweep (one
+// env per warp), 2 = k_soft_sweep_lanes (one env per lane), 0 = the lanes
+// from kSweepLanesFrom envs, past two waves of k_soft_sweep's warps
+// (28 an SM at its 72 registers).
+constexpr int kSweepLanesFrom = 8192;
+static int sweep_lanes(const vcs_batch* b) {
+  return b->cfg.sweep_mode == 2 || (b->cfg.sweep_mode == 0 && b->n_envs >= kSweepLanesFrom);
+}
+
 template <class Kern>
 static cudaError_t allow_smem(Kern kern, size_t smem) {
   return smem > 48u * 1024u ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
@@ -872,8 +1042,28 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
 }
 
 static cudaError_t launch_sweep(const BwdParams& p, cudaStream_t s) {
-  const int n_blocks = (p.n_envs + kSweepEnvs - 1) / kSweepEnvs;
   const bool sampler = p.sampler && p.step_instr <= 0, gb = p.graphics != 0, xm = p.xmap != 0;
+  if (p.sweep_lanes) {
+    const dim3 grid((p.n_envs + 31) / 32), block(32);
+    const size_t sm = swl_smem_bytes(xm ? kSweepCells : 128);
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kern) {
+      if ((e = allow_smem(kern, sm)) == cudaSuccess) kern<<<grid, block, sm, s>>>(p);
+    };
+    if (gb) {
+      if (sampler && xm) go(k_soft_sweep_lanes<true, true, true>);
+      else if (sampler) go(k_soft_sweep_lanes<true, true, false>);
+      else if (xm) go(k_soft_sweep_lanes<false, true, true>);
+      else go(k_soft_sweep_lanes<false, true, false>);
+    } else {
+      if (sampler && xm) go(k_soft_sweep_lanes<true, false, true>);
+      else if (sampler) go(k_soft_sweep_lanes<true, false, false>);
+      else if (xm) go(k_soft_sweep_lanes<false, false, true>);
+      else go(k_soft_sweep_lanes<false, false, false>);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+  const int n_blocks = (p.n_envs + kSweepEnvs - 1) / kSweepEnvs;
   const dim3 grid(n_blocks), block(32 * kSweepEnvs);
   const size_t sm = sw_smem_bytes();
   if (gb) {
@@ -1243,6 +1433,7 @@ vcs_status vcs_backward(vcs_tape* t, const float* grad_ram, const float* grad_sc
   p.sampler = b->cfg.position_sampler;
   p.graphics = b->cfg.graphics_bits && b->cfg.step_instructions <= 0;
   p.step_instr = b->cfg.step_instructions;
+  p.sweep_lanes = sweep_lanes(b);
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;
@@ -1440,6 +1631,7 @@ extern "C" vcs_status vcs_backward_static(vcs_tape* t, const float* grad_ram, co
   p.sampler = b->cfg.position_sampler;
   p.graphics = b->cfg.graphics_bits && b->cfg.step_instructions <= 0;
   p.step_instr = b->cfg.step_instructions;
+  p.sweep_lanes = sweep_lanes(b);
   p.sched_policy = b->sched_policy;
   p.sched_window = b->sched_window;
   p.err = b->err;

@@ -45,6 +45,7 @@ def test_config_defaults(lib):
     assert cfg.segment_frames == 64
     assert cfg.full_tia == 0 and cfg.position_sampler == 0 and cfg.step_instructions == 0
     assert cfg.inline_render == 0   # deferred rasterisation
+    assert cfg.sweep_mode == 0      # the sweep chosen by batch size
 
 
 def test_binding_config_matches_header():
@@ -90,6 +91,10 @@ def test_argument_errors_before_device_work(lib):
     cfg.inline_render = 2
     st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0], cfg=C.byref(cfg))
     assert st == _lib.VCS_ERR_ARG and "inline_render" in msg
+    lib.vcs_config_default(C.byref(cfg))
+    cfg.sweep_mode = 3
+    st, h, msg = _create(lib, [rom4], [4096], [synth.MAPPER_4K], [0], cfg=C.byref(cfg))
+    assert st == _lib.VCS_ERR_ARG and "sweep_mode" in msg
     assert lib.vcs_step(None, None, 1, None, None, None, None) == _lib.VCS_ERR_ARG
     tape = C.c_void_p()
     assert lib.vcs_soft_step(None, 0.1, None, 1, 1, None, None, C.byref(tape), None) == _lib.VCS_ERR_ARG
