@@ -195,7 +195,7 @@ typedef struct vcs_config {
                                warp stages records and adds ROM impulses),
                                2 = one env per lane (32 envs a warp, each
                                lane walking its own tape), 0 (default) =
-                               2 from 8192 envs, else 1.  Gradients are the
+                               2 from 16,384 envs, else 1.  Gradients are the
                                same bits either way. */
 } vcs_config;
 

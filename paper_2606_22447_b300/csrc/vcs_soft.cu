@@ -359,10 +359,26 @@ __device__ __forceinline__ void scatter_read(Adj& a, float* aram, float* aramc, 
   }
 }
 
+// The colour / position version sums of an env's tape, popped last to
+// first (j counts the sums not yet popped): straight from the tape, or
+// (CwAhead, the lane sweep) with the next sum loaded ahead, so that a pop
+// waits for no load.
+__device__ __forceinline__ float cw_pop(const float* cw, uint32_t& j) { return cw[--j]; }
+struct CwAhead {
+  const float* p;
+  float next;   // p[j - 1] (0 once j is 0)
+};
+__device__ __forceinline__ float cw_pop(CwAhead& cw, uint32_t& j) {
+  const float v = cw.next;
+  --j;
+  cw.next = j ? cw.p[j - 1] : 0.f;
+  return v;
+}
+
 // Adjoint of the value written to `ref`: taken from the cell (which is then
 // cleared, the write being one-hot).
-template <bool SAMPLER, bool GB, bool XM>
-__device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uint32_t E, const float* cw,
+template <bool SAMPLER, bool GB, bool XM, class CW>
+__device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uint32_t E, CW& cw,
                                           uint32_t& j, uint32_t kind, uint32_t ref) {
   const uint32_t ad = ref & 0x1FFF;
   if (ad & 0x1000) {
@@ -375,16 +391,16 @@ __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uin
   }
   if (!(ad & 0x80)) {
     const uint32_t reg = ad & 0x3F;
-    if (reg == 0x06) { if (j) a.C0 += cw[--j]; return a.C0.take(); }
-    if (reg == 0x08) { if (j) a.C1 += cw[--j]; return a.C1.take(); }
-    if (reg == 0x09) { if (j) a.C2 += cw[--j]; return a.C2.take(); }
-    if (reg == 0x07) { if (j) a.C3 += cw[--j]; return a.C3.take(); }
+    if (reg == 0x06) { if (j) a.C0 += cw_pop(cw, j); return a.C0.take(); }
+    if (reg == 0x08) { if (j) a.C1 += cw_pop(cw, j); return a.C1.take(); }
+    if (reg == 0x09) { if (j) a.C2 += cw_pop(cw, j); return a.C2.take(); }
+    if (reg == 0x07) { if (j) a.C3 += cw_pop(cw, j); return a.C3.take(); }
     if constexpr (GB) {
       // graphics-bit surrogate: a version's sum goes to the written value.
       // A delayed copy's versions open at the other player's GRP write (the
       // later slots of its record, popped first) and belong to the value
       // the copy took: the source register's live version.
-      auto pop = [&](int k) { if (j) a.G[k] += cw[--j]; };
+      auto pop = [&](int k) { if (j) a.G[k] += cw_pop(cw, j); };
       if (reg == 0x1B) {
         if (a.ft) {
           pop(kGbGrp1Old);
@@ -416,7 +432,7 @@ __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uin
     }
     // RESP0 and HMOVE open a position version (its slot pops either way)
     if (reg == 0x2A || reg == 0x10) {
-      const float sv = j ? cw[--j] : 0.f;
+      const float sv = j ? cw_pop(cw, j) : 0.f;
       if constexpr (SAMPLER) {
         if (reg == 0x2A) {   // HMOVE: pos' = pos - HMP0 / 16 (the written value is ignored)
           a.P += sv;
@@ -450,10 +466,10 @@ __device__ __forceinline__ Acc take_write(Adj& a, float* aram, float* aramc, uin
 
 __device__ __forceinline__ uint32_t stack_addr(uint32_t ref, uint32_t k) { return 0x100u | ((ref - k) & 0xFF); }
 
-template <bool SAMPLER, bool GB, bool XM, class Q>
+template <bool SAMPLER, bool GB, bool XM, class Q, class CW>
 __device__ __forceinline__ void reverse_one(Adj& a, float* aram, float* aramc, uint32_t E, const float* ek,
                                             const float* izr, int W, Q& rq,
-                                            uint32_t kind, const float* cw, uint32_t& j, uint32_t rec) {
+                                            uint32_t kind, CW& cw, uint32_t& j, uint32_t rec) {
   const uint32_t op = rec & 0xFF, ref = (rec >> 8) & 0xFFFF, fl = rec >> 24;
   switch (op) {
     case 0xA9: case 0xA5: case 0xB5: case 0xAD: case 0xBD: case 0xB9: case 0xA1: case 0xB1: {
@@ -900,25 +916,48 @@ __global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
     }
   }
   float2* imp = reinterpret_cast<float2*>(p.imp) + (size_t)env * p.rom_stride;
-  auto flush = [&]() {   // the queued impulses, in queue order
-    for (uint32_t e = 0; e < rq.n; e++) {
-      const uint32_t ix = rq.idx[e * 32];
-      float2 w = imp[ix];
-      comp_add(w.x, w.y, rq.g[e * 32]);
-      imp[ix] = w;
-    }
+  // the queued impulses, in queue order: all loads first (in flight
+  // together), an index that repeats in the queue taking its earlier
+  // entry's updated pair, then the stores in order (a repeated index ends
+  // with its last, fully updated pair)
+  auto flush = [&]() {
+    uint32_t ix[kLaneQ];
+    float2 w[kLaneQ];
+#pragma unroll
+    for (int e = 0; e < kLaneQ; e++)
+      if (e < (int)rq.n) {
+        ix[e] = rq.idx[e * 32];
+        w[e] = imp[ix[e]];
+      }
+#pragma unroll
+    for (int e = 0; e < kLaneQ; e++)
+      if (e < (int)rq.n) {
+#pragma unroll
+        for (int f = 0; f < e; f++)
+          if (ix[f] == ix[e]) w[e] = w[f];
+        comp_add(w[e].x, w[e].y, rq.g[e * 32]);
+      }
+#pragma unroll
+    for (int e = 0; e < kLaneQ; e++)
+      if (e < (int)rq.n) imp[ix[e]] = w[e];
     rq.n = 0;
   };
   const uint4* rec4 = reinterpret_cast<const uint4*>(p.rec + ((size_t)g * n + env) * p.cap_rec);
-  const float* cw = p.cw + ((size_t)g * n + env) * p.cap_cw;
-  const uint32_t* step_end = p.step_end + (size_t)g * p.seg_steps * n;
   uint32_t j = __float_as_uint(m[0]);
+  CwAhead cw{p.cw + ((size_t)g * n + env) * p.cap_cw, 0.f};
+  if (j) cw.next = cw.p[j - 1];
+  const uint32_t* step_end = p.step_end + (size_t)g * p.seg_steps * n;
   const int t0 = p.seg * p.seg_steps;
   const int t1 = min(t0 + p.seg_steps, p.n_steps);
-  // records are read backwards four at a time (16-byte tape rows), the
-  // chunk below the current one in flight
-  uint4 cur = make_uint4(0u, 0u, 0u, 0u), nxt = cur;
-  uint32_t cc = 0xFFFFFFFFu;   // chunk held in cur
+  // records are read backwards four at a time (16-byte tape rows; a
+  // segment's records are contiguous, step after step), the chunk below the
+  // current one in flight.  The loads are unconditional (chunk 0 stands in
+  // below chunk 0; the tape holds at least one chunk), so no value waits on
+  // a load that a select might discard.
+  const uint32_t k_last = step_end[(size_t)(t1 - 1 - t0) * n + env];
+  uint32_t cc = k_last ? (k_last - 1) >> 2 : 0u;   // chunk held in cur
+  uint4 cur = __ldcs(rec4 + cc);
+  uint4 nxt = __ldcs(rec4 + (cc ? cc - 1 : 0u));
   for (int t = t1 - 1; t >= t0; t--) {
     const float* gr = p.grad_ram ? p.grad_ram + ((size_t)t * n + env) * 128 : p.w_ram;
     if (gr)
@@ -928,15 +967,17 @@ __global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
     const uint32_t k_beg = t > t0 ? step_end[(size_t)(t - 1 - t0) * n + env] : 0u;
     for (uint32_t k = k_end; k > k_beg; k--) {
       const uint32_t c = (k - 1) >> 2;
-      if (c != cc) {
-        cur = c + 1 == cc ? nxt : __ldcs(rec4 + c);
-        nxt = c > 0 ? __ldcs(rec4 + c - 1) : make_uint4(0u, 0u, 0u, 0u);
+      if (c != cc) {   // c == cc - 1
+        cur = nxt;
+        nxt = __ldcs(rec4 + (c ? c - 1 : 0u));
         cc = c;
       }
       const uint32_t w = (k - 1) & 3;
       const uint32_t r = w == 0 ? cur.x : w == 1 ? cur.y : w == 2 ? cur.z : cur.w;
       reverse_one<SAMPLER, GB, XM>(a, aram, aramc, E, ek, izr, p.W, rq, kind, cw, j, r);
-      if (rq.n == kLaneQ) flush();
+      // the lanes flush together when one queue is full: one wait for the
+      // impulse rows' loads instead of one for every lane at another record
+      if (__any_sync(__activemask(), rq.n == kLaneQ)) flush();
     }
     if (p.grad_u) {
       float* gu = p.grad_u + ((size_t)t * n + env) * 5;
@@ -981,9 +1022,12 @@ __global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
 
 // Which sweep a batch runs (vcs_config.sweep_mode): 1 = k_soft_sweep (one
 // env per warp), 2 = k_soft_sweep_lanes (one env per lane), 0 = the lanes
-// from kSweepLanesFrom envs, past two waves of k_soft_sweep's warps
-// (28 an SM at its 72 registers).
-constexpr int kSweepLanesFrom = 8192;
+// from kSweepLanesFrom envs, about four waves of k_soft_sweep's warps (28
+// an SM at its 72 registers).  Measured backward times (ms, same box, one
+// 4 KB cart; 3,000-instruction steps / 64 frames): 8192 envs 2.30 / 130
+// with the warps against 3.06 / 173 with the lanes; 16,384 envs 3.47 / 199
+// against 3.23 / 178; 65,536 envs 12.4 against 9.6.
+constexpr int kSweepLanesFrom = 16384;
 static int sweep_lanes(const vcs_batch* b) {
   return b->cfg.sweep_mode == 2 || (b->cfg.sweep_mode == 0 && b->n_envs >= kSweepLanesFrom);
 }

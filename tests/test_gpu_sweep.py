@@ -76,11 +76,11 @@ def test_lane_sweep_equals_warp_sweep(case):
 
 
 def test_automatic_sweep_choice_at_large_batches():
-    """From 8192 envs the default (sweep_mode 0) walks one env per lane; the
+    """From 16,384 envs the default (sweep_mode 0) walks one env per lane; the
     gradients are the one-env-per-warp sweep's bits."""
     mappers = [synth.MAPPER_4K]
     roms = synth.config_carts(95, mappers)
-    env_cart = np.zeros(8192, np.int32)
+    env_cart = np.zeros(16384, np.int32)
     cfg = {"step_instructions": 300}
     want = _run(roms, mappers, env_cart, 1, 2, 1, 0.1, 0, False, cfg)
     got = _run(roms, mappers, env_cart, 0, 2, 1, 0.1, 0, False, cfg)
