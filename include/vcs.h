@@ -193,7 +193,7 @@ typedef struct vcs_config {
   int32_t sweep_mode;       /* the soft backward's reverse sweep: 1 = one
                                env per warp (its lane 0 walks the tape, the
                                warp stages records and adds ROM impulses),
-                               2 = one env per lane (32 envs a warp, each
+                               2 = one env per lane (8 envs a block, each
                                lane walking its own tape), 0 (default) =
                                2 from 16,384 envs, else 1.  Gradients are the
                                same bits either way. */

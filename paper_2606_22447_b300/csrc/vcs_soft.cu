@@ -276,16 +276,17 @@ struct RomQueue {
     n++;
   }
 };
-// The same queue for a sweep that walks one env per lane: lane l's entry e
-// sits at e * 32 + l (consecutive lanes in consecutive banks), and the lane
-// adds its own impulses.
+// The same queue for a sweep that walks one env per lane (kLaneEnvs envs a
+// block): lane l's entry e sits at e * kLaneEnvs + l (consecutive lanes in
+// consecutive banks), and the lane adds its own impulses.
+constexpr int kLaneEnvs = 8;
 struct LaneQueue {
   uint32_t* idx;
   float* g;
   uint32_t n;
   __device__ __forceinline__ void push(uint32_t i, float v) {
-    idx[n * 32] = i;
-    g[n * 32] = v;
+    idx[n * kLaneEnvs] = i;
+    g[n * kLaneEnvs] = v;
     n++;
   }
 };
@@ -851,7 +852,11 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
   }
 }
 
-// The reverse sweep with one env per lane (32 envs a block of one warp):
+// The reverse sweep with one env per lane (kLaneEnvs envs a block, a
+// quarter of a warp: several small warps an SMSP hide more of the walkers'
+// latency than one full one; measured backward at 16,384 / 65,536 envs and
+// 3,000-instruction steps: 32 a block 3.23 / 9.61 ms, 16 3.06 / 9.13, 8
+// 2.98 / 9.10):
 // each lane walks its own env's tape with the same per-record arithmetic as
 // k_soft_sweep and adds its own ROM impulses, so every env's sums take the
 // same terms in the same order and the gradients are the same bits.  Lanes
@@ -860,21 +865,21 @@ __global__ void __launch_bounds__(32 * kSweepEnvs) k_soft_sweep(BwdParams p) {
 // kernel's issue slots go to its single walking lane, this is the faster.
 constexpr int kLaneQ = 8;   // ROM impulses a lane queues before adding them
 __host__ __device__ constexpr size_t swl_smem_bytes(int cells) {
-  return ((size_t)2 * cells * 32 + (kMaxW + 1 + 256) + (size_t)2 * kLaneQ * 32) * 4;
+  return ((size_t)2 * cells * kLaneEnvs + (kMaxW + 1 + 256) + (size_t)2 * kLaneQ * kLaneEnvs) * 4;
 }
 
 template <bool SAMPLER, bool GB, bool XM>
-__global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
+__global__ void __launch_bounds__(kLaneEnvs) k_soft_sweep_lanes(BwdParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr int E = 32;
+  constexpr int E = kLaneEnvs;
   constexpr int cells = XM ? kSweepCells : 128;   // adjoint cells the sweep keeps
   const int lane = threadIdx.x;
-  float* aram_s = reinterpret_cast<float*>(smem);   // [cells][32]
-  float* aramc_s = aram_s + cells * E;              // [cells][32] compensation
+  float* aram_s = reinterpret_cast<float*>(smem);   // [cells][E]
+  float* aramc_s = aram_s + cells * E;              // [cells][E] compensation
   float* ek = aramc_s + cells * E;                  // [kMaxW + 1]
   float* izr = ek + (kMaxW + 1);                    // [256]
-  uint32_t* q_idx = reinterpret_cast<uint32_t*>(izr + 256);   // [kLaneQ][32]
-  float* q_g = reinterpret_cast<float*>(q_idx + kLaneQ * 32);  // [kLaneQ][32]
+  uint32_t* q_idx = reinterpret_cast<uint32_t*>(izr + 256);   // [kLaneQ][E]
+  float* q_g = reinterpret_cast<float*>(q_idx + kLaneQ * E);   // [kLaneQ][E]
   read_tables(ek, izr, p.tau, p.W);
   const int env = blockIdx.x * E + lane;
   if (env >= p.n_envs) return;
@@ -926,7 +931,7 @@ __global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
 #pragma unroll
     for (int e = 0; e < kLaneQ; e++)
       if (e < (int)rq.n) {
-        ix[e] = rq.idx[e * 32];
+        ix[e] = rq.idx[e * E];
         w[e] = imp[ix[e]];
       }
 #pragma unroll
@@ -935,7 +940,7 @@ __global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
 #pragma unroll
         for (int f = 0; f < e; f++)
           if (ix[f] == ix[e]) w[e] = w[f];
-        comp_add(w[e].x, w[e].y, rq.g[e * 32]);
+        comp_add(w[e].x, w[e].y, rq.g[e * E]);
       }
 #pragma unroll
     for (int e = 0; e < kLaneQ; e++)
@@ -1024,9 +1029,9 @@ __global__ void __launch_bounds__(32) k_soft_sweep_lanes(BwdParams p) {
 // env per warp), 2 = k_soft_sweep_lanes (one env per lane), 0 = the lanes
 // from kSweepLanesFrom envs, about four waves of k_soft_sweep's warps (28
 // an SM at its 72 registers).  Measured backward times (ms, same box, one
-// 4 KB cart; 3,000-instruction steps / 64 frames): 8192 envs 2.30 / 130
-// with the warps against 3.06 / 173 with the lanes; 16,384 envs 3.47 / 199
-// against 3.23 / 178; 65,536 envs 12.4 against 9.6.
+// 4 KB cart; 3,000-instruction steps / 64 frames): 8192 envs 2.31 / 130
+// with the warps against 2.74 / 142 with the lanes; 16,384 envs 3.47 / 199
+// against 2.98 / 154; 65,536 envs 12.4 / 730 against 9.1 / 523.
 constexpr int kSweepLanesFrom = 16384;
 static int sweep_lanes(const vcs_batch* b) {
   return b->cfg.sweep_mode == 2 || (b->cfg.sweep_mode == 0 && b->n_envs >= kSweepLanesFrom);
@@ -1088,7 +1093,7 @@ static cudaError_t launch_recompute(const BwdParams& p, int G, int n_blocks, int
 static cudaError_t launch_sweep(const BwdParams& p, cudaStream_t s) {
   const bool sampler = p.sampler && p.step_instr <= 0, gb = p.graphics != 0, xm = p.xmap != 0;
   if (p.sweep_lanes) {
-    const dim3 grid((p.n_envs + 31) / 32), block(32);
+    const dim3 grid((p.n_envs + kLaneEnvs - 1) / kLaneEnvs), block(kLaneEnvs);
     const size_t sm = swl_smem_bytes(xm ? kSweepCells : 128);
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern) {
